@@ -1,0 +1,509 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix.
+
+Each test names the pin it implements; none re-types an oracle formula.  The
+comparisons are against closed forms, textbook values (tests/golden), exact
+solutions, invariants (conservation, freestream, symmetry) and identities of
+the method (hybrid limits).  CPU only.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_2511_18042_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- P-1 exact Riemann
+def test_exact_riemann_matches_toro_table():
+    from oracle import riemann_exact as rx
+    rows = np.loadtxt(os.path.join(GOLDEN, "toro_exact_riemann.txt"))
+    for r in rows:
+        WL, WR = tuple(r[1:4]), tuple(r[4:7])
+        p, u, rl, rr = rx.star_densities(WL, WR, 1.4)
+        for got, want in ((p, r[7]), (u, r[8]), (rl, r[9]), (rr, r[10])):
+            assert abs(got - want) <= 6e-5 * max(1.0, abs(want)) + 1e-5, (r[0], got, want)
+
+
+def test_exact_riemann_rankine_hugoniot():
+    """Across the right-moving shock of Sod the exact profile satisfies the jump conditions."""
+    from oracle import riemann_exact as rx
+    WL, WR, g = (1.0, 0.0, 1.0), (0.125, 0.0, 0.1), 1.4
+    p, u, rl, rr = rx.star_densities(WL, WR, g)
+    # shock speed from mass conservation, then check momentum and energy jumps
+    S = (rr * u - WR[0] * WR[1]) / (rr - WR[0])
+    cons = lambda r, v, pp: np.array([r, r * v, pp / (g - 1) + 0.5 * r * v * v])
+    flux = lambda r, v, pp: np.array([r * v, r * v * v + pp, (pp / (g - 1) + 0.5 * r * v * v + pp) * v])
+    jump = flux(rr, u, p) - flux(*WR) - S * (cons(rr, u, p) - cons(*WR))
+    assert np.abs(jump).max() < 1e-12
+    assert abs(S - 1.75216) < 1e-4
+
+
+# ---------------------------------------------------------------- P-3 HLLC
+def _rand_state(rng, nd):
+    return np.concatenate([[rng.uniform(0.1, 3.0)], rng.uniform(-2, 2, nd), [rng.uniform(0.1, 3.0)]])
+
+
+def test_hllc_consistency_and_invariances(orc):
+    rng = np.random.default_rng(1)
+    for nd in (1, 2, 3):
+        for _ in range(300):
+            W = _rand_state(rng, nd)
+            xi = rng.uniform(-2, 2, nd)
+            xi[0] += 2.5 * np.sign(xi[0] + 1e-300)
+            F = orc.hllc(W, W, xi)
+            Fc = orc.euler_flux(W, xi)
+            assert np.allclose(F, Fc, rtol=1e-13, atol=1e-13 * np.abs(Fc).max())
+            WL, WR = _rand_state(rng, nd), _rand_state(rng, nd)
+            F1 = orc.hllc(WL, WR, xi)
+            # homogeneity of degree one in the metrics
+            assert np.allclose(orc.hllc(WL, WR, 2.5 * xi), 2.5 * F1, rtol=1e-12, atol=1e-12)
+            # reversing the face orientation and swapping the states negates the flux
+            assert np.allclose(orc.hllc(WR, WL, -xi), -F1, rtol=1e-12, atol=1e-12)
+
+
+def test_hllc_rotation_invariance(orc):
+    rng = np.random.default_rng(2)
+    for _ in range(200):
+        WL, WR = _rand_state(rng, 2), _rand_state(rng, 2)
+        xi = rng.uniform(-1, 1, 2)
+        th = rng.uniform(0, 2 * math.pi)
+        Q = np.array([[math.cos(th), -math.sin(th)], [math.sin(th), math.cos(th)]])
+        rot = lambda W: np.concatenate([[W[0]], Q @ W[1:3], [W[3]]])
+        F = orc.hllc(WL, WR, xi)
+        Fr = orc.hllc(rot(WL), rot(WR), Q @ xi)
+        assert np.allclose(Fr, rot(F), rtol=1e-12, atol=1e-12)
+
+
+def _toro_hllc_x(WL, WR, g):
+    """Textbook HLLC in the x-normal frame (Toro ch. 10) with Roe-average wave
+    speeds S_L = min(u_L - c_L, u~ - c~), S_R = max(u_R + c_R, u~ + c~)."""
+    def parts(W):
+        r, u, v, p = W
+        E = p / (g - 1) + 0.5 * r * (u * u + v * v)
+        return r, u, v, p, E, math.sqrt(g * p / r)
+    rL, uL, vL, pL, EL, cL = parts(WL)
+    rR, uR, vR, pR, ER, cR = parts(WR)
+    sl, sr = math.sqrt(rL), math.sqrt(rR)
+    ut = (sl * uL + sr * uR) / (sl + sr)
+    vt = (sl * vL + sr * vR) / (sl + sr)
+    Ht = (sl * (EL + pL) / rL + sr * (ER + pR) / rR) / (sl + sr)
+    ct = math.sqrt((g - 1) * (Ht - 0.5 * (ut * ut + vt * vt)))
+    SL, SR = min(uL - cL, ut - ct), max(uR + cR, ut + ct)
+    Ss = (pR - pL + rL * uL * (SL - uL) - rR * uR * (SR - uR)) / (rL * (SL - uL) - rR * (SR - uR))
+    F = lambda r, u, v, p, E: np.array([r * u, r * u * u + p, r * u * v, (E + p) * u])
+    Uc = lambda r, u, v, p, E: np.array([r, r * u, r * v, E])
+    def star(r, u, v, p, E, S):
+        f = r * (S - u) / (S - Ss)
+        return f * np.array([1.0, Ss, v, E / r + (Ss - u) * (Ss + p / (r * (S - u)))])
+    if SL >= 0:
+        return F(rL, uL, vL, pL, EL)
+    if Ss >= 0:
+        return F(rL, uL, vL, pL, EL) + SL * (star(rL, uL, vL, pL, EL, SL) - Uc(rL, uL, vL, pL, EL))
+    if SR >= 0:
+        return F(rR, uR, vR, pR, ER) + SR * (star(rR, uR, vR, pR, ER, SR) - Uc(rR, uR, vR, pR, ER))
+    return F(rR, uR, vR, pR, ER)
+
+
+def test_hllc_reduces_to_textbook_cartesian(orc):
+    rng = np.random.default_rng(3)
+    for _ in range(500):
+        WL, WR = _rand_state(rng, 2), _rand_state(rng, 2)
+        F = orc.hllc(WL, WR, np.array([1.0, 0.0]))
+        Ft = _toro_hllc_x(WL, WR, 1.4)
+        assert np.allclose(F, Ft, rtol=1e-12, atol=1e-12 * max(1.0, np.abs(Ft).max()))
+
+
+# ---------------------------------------------------------------- P-8 MP5
+def test_mp5_linear_part_is_fifth_order_exact(orc):
+    """The unlimited value is the interface value of the quartic through five cell averages."""
+    rng = np.random.default_rng(4)
+    for _ in range(50):
+        c = rng.normal(size=5)
+        P = np.polynomial.Polynomial(c)
+        Pi = P.integ()
+        avg = [Pi(j + 0.5) - Pi(j - 0.5) for j in range(-2, 3)]
+        ul = orc.mp5(*avg, alpha=4.0, eps=math.inf)
+        assert abs(ul - P(0.5)) < 1e-12 * max(1.0, abs(P(0.5)))
+
+
+def test_mp5_limiter_cases(orc):
+    # smooth monotone data: limiter inactive, the fifth-order value is returned
+    u = np.exp(0.3 * np.arange(-2, 3))
+    assert orc.mp5(*u) == orc.mp5(*u, eps=math.inf)
+    # a step: the interface value is clipped to the data range (hand computed: 1)
+    assert orc.mp5(0.0, 0.0, 1.0, 1.0, 1.0) == 1.0
+    assert orc.mp5(0.0, 0.0, 0.0, 1.0, 1.0) >= 0.0 and orc.mp5(0.0, 0.0, 0.0, 1.0, 1.0) <= 1.0
+    rng = np.random.default_rng(5)
+    for _ in range(2000):
+        v = np.sort(rng.uniform(-1, 1, 5))
+        v[rng.integers(0, 4):] += rng.uniform(0, 5)  # monotone data with a jump
+        r = orc.mp5(*v)
+        assert min(v[2], v[3]) - 1e-14 <= r <= max(v[2], v[3]) + 1e-14
+        w = rng.normal(size=5)
+        assert orc.mp5(*(-w)) == -orc.mp5(*w)
+
+
+# ---------------------------------------------------------------- P-7 operators
+def _kstar(kind, th):
+    if kind == "MEG6":
+        return 1.5 * np.sin(th) - 0.3 * np.sin(2 * th) + np.sin(3 * th) / 30.0
+    if kind == "E4":
+        return 4.0 / 3.0 * np.sin(th) - np.sin(2 * th) / 6.0
+    if kind == "MIG4":
+        return 1.5 * np.sin(th) / (1.0 + 0.5 * np.cos(th))
+    if kind == "C6":
+        return (14.0 / 9.0 * np.sin(th) + np.sin(2 * th) / 18.0) / (1.0 + 2.0 / 3.0 * np.cos(th))
+
+
+@pytest.mark.parametrize("kind", ["MEG6", "E4", "MIG4", "C6"])
+def test_derivative_modified_wavenumber(orc, kind):
+    n, ng = 32, 5
+    j = np.arange(-ng, n + ng)
+    for m in (1, 3, 7, 12, 15):
+        th = 2 * math.pi * m / n
+        f = np.cos(th * j)
+        d = orc.line_op(kind, f, ng, periodic=True)
+        sl = slice(ng, ng + n)
+        assert np.allclose(d[sl], -_kstar(kind, th) * np.sin(th * j[sl]), atol=2e-14)
+
+
+def test_gaussian_filter_weights(orc):
+    n, ng = 24, 5
+    j = np.arange(-ng, n + ng)
+    sl = slice(ng, ng + n)
+    assert np.allclose(orc.line_op("GAUSS", np.full(n + 2 * ng, 3.25), ng)[sl], 3.25, atol=1e-15)
+    assert np.abs(orc.line_op("GAUSS", (-1.0) ** j, ng)[sl]).max() < 1e-15
+
+
+def test_implicit_filter_transfer(orc):
+    n, ng, af = 32, 5, 0.45
+    j = np.arange(-ng, n + ng)
+    sl = slice(ng, ng + n)
+    # constants are preserved (periodic and bounded lines)
+    for per in (True, False):
+        assert np.allclose(orc.line_op("FILTER", np.full(n + 2 * ng, 1.7), ng, per, af)[sl], 1.7, atol=1e-14)
+    # the odd-even mode is removed
+    assert np.abs(orc.line_op("FILTER", (-1.0) ** j, ng, True, af)[sl]).max() < 1e-14
+    # eighth-order Pade filter transfer function (Gaitonde & Visbal)
+    a = [(93 + 70 * af) / 128, (7 + 18 * af) / 16, (-7 + 14 * af) / 32, (1 - 2 * af) / 16, (-1 + 2 * af) / 128]
+    for m in (2, 5, 9, 14):
+        th = 2 * math.pi * m / n
+        T = sum(a[q] * math.cos(q * th) for q in range(5)) / (1 + 2 * af * math.cos(th))
+        out = orc.line_op("FILTER", np.cos(th * j), ng, True, af)
+        assert np.allclose(out[sl], T * np.cos(th * j[sl]), atol=1e-13)
+
+
+def test_tridiagonal_solver_against_dense(orc):
+    rng = np.random.default_rng(6)
+    for cyc in (0, 1):
+        for m in (3, 7, 40):
+            a = rng.uniform(-0.45, 0.45)
+            r = rng.normal(size=m)
+            A = np.eye(m)
+            for i in range(m):
+                if cyc or 0 < i < m - 1:
+                    A[i, (i - 1) % m] += a
+                    A[i, (i + 1) % m] += a
+            x = orc.tridiag(a, r, cyc)
+            assert np.allclose(A @ x, r, atol=1e-13)
+
+
+# ---------------------------------------------------------------- P-6 design order
+def _symbolic_order(kind):
+    """Order of the linear (smooth-flow) scheme, derived from its stencils by
+    Fourier analysis with sympy: k* - k = O(k^(p+1)) for f = exp(i k j)."""
+    import sympy as sp
+    k = sp.symbols("k")
+    I = sp.I
+    N = 10
+    s = lambda e: sp.series(e, k, 0, N).removeO()
+    if kind in ("MEG6", "MIG4"):
+        if kind == "MEG6":
+            K1 = sp.Rational(3, 2) * sp.sin(k) - sp.Rational(3, 10) * sp.sin(2 * k) + sp.sin(3 * k) / 30
+        else:
+            K1 = sp.Rational(3, 2) * sp.sin(k) / (1 + sp.cos(k) / 2)
+        K1 = s(K1)
+        # f' = i K1 f; f'' from values and first derivatives (gradient-based second derivative)
+        K2 = s(2 * (2 * sp.cos(k) - 2) - sp.Rational(1, 2) * (I * K1) * (2 * I * sp.sin(k)))
+        E = s(sp.exp(I * k))
+        CL = 1 + I * K1 / 2 + K2 / 12          # left linear state at i+1/2, per unit f_i
+        CR = E * (1 - I * K1 / 2 + K2 / 12)    # right linear state from node i+1
+        h = (CL + CR) / 2                      # centralised interpolation
+        kstar = sp.expand(s(sp.expand(h * (1 - s(sp.exp(-I * k))) / I)))
+    elif kind == "E4":
+        kstar = s(sp.Rational(4, 3) * sp.sin(k) - sp.sin(2 * k) / 6)
+    else:
+        kstar = s((sp.Rational(14, 9) * sp.sin(k) + sp.sin(2 * k) / 18) / (1 + sp.Rational(2, 3) * sp.cos(k)))
+    err = sp.expand(kstar - k)
+    for pwr in range(2, N):
+        if err.coeff(k, pwr) != 0:
+            return pwr - 1
+    return N
+
+
+@pytest.mark.parametrize("scheme,kind", [("MEG6", "MEG6"), ("MIG4", "MIG4"), ("LAD_E4", "E4"), ("LAD_C6", "C6")])
+def test_design_order_shear_wave(orc, scheme, kind):
+    """A translating shear wave (u = 1, v = 0.1 sin 2pi(x - t), rho = p = 1) is smooth,
+    with constant pressure and no dilatation: the sensor is zero and the LAD
+    coefficients vanish, so every scheme runs its linear path."""
+    p_exp = _symbolic_order(kind)
+    errs = []
+    T = 0.02
+    for n in (16, 32, 64):
+        h = 1.0 / n
+        x = (np.arange(n) + 0.5) * h
+        W = np.zeros((4, 4, n))
+        W[0], W[1], W[3] = 1.0, 1.0, 1.0
+        W[2] = 0.1 * np.sin(2 * math.pi * x)[None, :]
+        prob = inputs._problem("shear", 2, [n, 4], [h, h], [[0, 0], [0, 0]], W, 1.4)
+        o = orc.Oracle(prob, scheme=scheme, filter_on=0)
+        nst = int(math.ceil(T / (0.05 * h * h * 16)))
+        U, _, _ = o.advance(prob["U"], nsteps=nst, dt_fixed=T / nst)
+        v = U[2] / U[0]
+        errs.append(np.abs(v - 0.1 * np.sin(2 * math.pi * (x - T))[None, :]).max())
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert abs(rates[-1] - p_exp) < 0.35, (scheme, p_exp, errs, rates)
+    assert p_exp >= 4
+
+
+def test_symbolic_orders_values():
+    assert _symbolic_order("E4") == 4 and _symbolic_order("C6") == 6
+    assert _symbolic_order("MEG6") == 4 and _symbolic_order("MIG4") == 4
+
+
+# ---------------------------------------------------------------- P-11 RK3
+def test_rk3_third_order_in_time(orc):
+    n = 16
+    prob = inputs.entropy_wave(1, n, amp=0.2)
+    o = orc.Oracle(prob, scheme="LAD_E4")
+    T = 0.4
+    ref, _, _ = o.advance(prob["U"], nsteps=2048, dt_fixed=T / 2048)
+    errs = []
+    for ns in (16, 32, 64):
+        U, _, _ = o.advance(prob["U"], nsteps=ns, dt_fixed=T / ns)
+        errs.append(np.abs(U - ref).max())
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert all(abs(r - 3.0) < 0.15 for r in rates), (errs, rates)
+
+
+# ---------------------------------------------------------------- P-2 Sod
+def test_sod_against_exact_solution(orc):
+    from oracle import riemann_exact as rx
+    l1 = []
+    for N in (100, 200, 400):
+        prob = inputs.shock_tube("sod", N)
+        o = orc.Oracle(prob, scheme="MEG6", cfl=0.5)
+        U, t, _ = o.advance(prob["U"], t_end=0.2)
+        r_ex, _, _ = rx.profile(prob["WL"], prob["WR"], prob["x"], 0.5, 0.2)
+        l1.append(np.abs(U[0] - r_ex).mean())
+        # no new extrema beyond 1 % (C-GBR resolves the contact without oscillation)
+        assert U[0].max() <= 1.0 * 1.01 and U[0].min() >= 0.125 * 0.99
+        # shock position within two cells: density crosses the mid value between rho*_R and rho_R
+        _, _, _, rr = rx.star_densities(prob["WL"], prob["WR"])
+        mid = 0.5 * (rr + 0.125)
+        xs = prob["x"][np.nonzero(U[0] > mid)[0].max()]
+        assert abs(xs - (0.5 + 1.75216 * 0.2)) <= 2.0 / N
+    assert l1[0] > l1[1] > l1[2]
+    assert math.log2(l1[0] / l1[2]) / 2 > 0.6
+
+
+@pytest.mark.parametrize("scheme,cfl", [("MIG4", 0.5), ("LAD_E4", 0.5), ("LAD_C6", 0.1)])
+def test_sod_other_schemes_converge(orc, scheme, cfl):
+    from oracle import riemann_exact as rx
+    prob = inputs.shock_tube("sod", 200)
+    o = orc.Oracle(prob, scheme=scheme, cfl=cfl)
+    U, t, _ = o.advance(prob["U"], t_end=0.2)
+    r_ex, _, _ = rx.profile(prob["WL"], prob["WR"], prob["x"], 0.5, 0.2)
+    assert np.abs(U[0] - r_ex).mean() < 1.2e-2
+    assert np.isfinite(U).all()
+
+
+# ---------------------------------------------------------------- P-4 conservation
+@pytest.mark.parametrize("scheme,extra", [("MEG6", {}), ("MIG4", {}), ("LAD_E4", {}), ("LAD_C6", {}),
+                                          ("HYBRID", dict(hybrid_mode=0, hyb_rho=1.5)),
+                                          ("HYBRID", dict(hybrid_mode=1, hyb_rho=1.5, hybrid_sensor=1))])
+def test_conservation_periodic(orc, scheme, extra):
+    prob = inputs.kelvin_helmholtz(32)
+    o = orc.Oracle(prob, scheme=scheme, **extra)
+    U, _, _ = o.advance(prob["U"], nsteps=12)
+    for v in range(4):
+        tot0 = prob["U"][v].sum()
+        assert abs(U[v].sum() - tot0) <= 2e-14 * np.abs(prob["U"][v]).sum() * 12, (scheme, v)
+
+
+def test_conservation_curvilinear_periodic(orc):
+    xyz, per = inputs.wavy_grid_2d(24, 20, amp=0.08)
+    x, y = xyz
+    W = np.stack([1.0 + 0.3 * np.sin(2 * math.pi * x) * np.cos(2 * math.pi * y), 0.5 + 0 * x,
+                  0.2 + 0.1 * np.cos(2 * math.pi * y), 1.0 + 0.2 * np.sin(2 * math.pi * (x + y))])
+    prob = inputs.field_on_curvilinear(xyz, per, W)
+    for scheme in ("MEG6", "LAD_E4"):
+        o = orc.Oracle(prob, scheme=scheme)
+        J = o.metrics()[0][-1]
+        U, _, _ = o.advance(prob["U"], nsteps=6)
+        for v in range(4):
+            a, b = (prob["U"][v] / J).sum(), (U[v] / J).sum()
+            assert abs(a - b) <= 1e-13 * np.abs(prob["U"][v] / J).sum(), (scheme, v)
+
+
+# ---------------------------------------------------------------- P-5 freestream
+@pytest.mark.parametrize("nd", [2, 3])
+def test_freestream_preservation(orc, nd):
+    if nd == 2:
+        xyz, per = inputs.wavy_grid_2d(24, 20, amp=0.1)
+        W0 = (1.0, 2.0 * math.sqrt(1.4) * math.cos(0.3), 2.0 * math.sqrt(1.4) * math.sin(0.3), 1.0)
+        schemes = ["MEG6", "MIG4", "LAD_E4", "HYBRID"]
+    else:
+        xyz, per = inputs.wavy_grid_3d((12, 12, 12), amp=0.06)
+        W0 = (1.0, 1.5, 0.7, -0.4, 1.0)
+        schemes = ["MEG6", "LAD_E4"]
+    prob = inputs.uniform_flow_curvilinear(xyz, per, W0)
+    for scheme in schemes:
+        for extra in ([{}] if scheme != "HYBRID" else [dict(hybrid_mode=1, hyb_rho=-1.0),
+                                                       dict(hybrid_mode=1, hyb_rho=5.0)]):
+            o = orc.Oracle(prob, scheme=scheme, **extra)
+            R = o.rhs(prob["U"])
+            J = o.metrics()[0][-1]
+            scale = J.max() * np.abs(prob["U"]).max() * 10
+            assert np.abs(R).max() <= 1e-14 * scale, (scheme, extra, np.abs(R).max(), scale)
+
+
+def test_metrics_exact_on_affine_grid(orc):
+    """On an affine grid the metric derivatives are exact: the curvilinear path
+    must reproduce the analytic metrics of the linear map."""
+    nx, ny = 16, 12
+    A = np.array([[0.9, 0.25], [-0.15, 1.1]])
+    I, J = np.meshgrid(np.arange(nx), np.arange(ny))
+    xyz = np.stack([A[0, 0] * I + A[0, 1] * J, A[1, 0] * I + A[1, 1] * J]).astype(float)
+    per = [[A[0, 0] * nx, A[1, 0] * nx], [A[0, 1] * ny, A[1, 1] * ny]]
+    W = np.ones((4, ny, nx))
+    prob = inputs.field_on_curvilinear(xyz, per, W)
+    for scheme in ("MEG6", "LAD_E4"):
+        node, ifc = orc.Oracle(prob, scheme=scheme).metrics()
+        # x = A xi: xi_hat = adj(A) (the metric divided by J), J = 1/det A
+        adj = np.array([[A[1, 1], -A[0, 1]], [-A[1, 0], A[0, 0]]])
+        for l in range(2):
+            for m in range(2):
+                assert np.allclose(node[l * 2 + m], adj[l, m], atol=1e-12)
+                assert np.allclose(ifc[l * 2 + m], adj[l, m], atol=1e-12)
+        assert np.allclose(node[4], 1.0 / np.linalg.det(A), atol=1e-12)
+
+
+# ---------------------------------------------------------------- P-9 symmetry
+@pytest.mark.parametrize("scheme", ["MEG6", "MIG4", "LAD_E4"])
+def test_riemann_c3_diagonal_symmetry(orc, scheme):
+    prob = inputs.riemann_c3(32)
+    o = orc.Oracle(prob, scheme=scheme)
+    U, _, _ = o.advance(prob["U"], nsteps=15)
+    assert np.abs(U[0] - U[0].T).max() <= 1e-13
+    assert np.abs(U[1] - U[2].T).max() <= 1e-13
+    assert np.abs(U[3] - U[3].T).max() <= 1e-13
+
+
+# ---------------------------------------------------------------- P-10 hybrid identities
+def test_hybrid_limits(orc):
+    prob = inputs.triple_point(64, 32)
+    U0 = prob["U"]
+    lad = orc.Oracle(prob, scheme="LAD_E4")
+    meg = orc.Oracle(prob, scheme="MEG6")
+    U_lad, _, _ = lad.advance(U0, nsteps=4)
+    U_meg, _, _ = meg.advance(U0, nsteps=4)
+    never = orc.Oracle(prob, scheme="HYBRID", hybrid_mode=0)
+    always = orc.Oracle(prob, scheme="HYBRID", hybrid_mode=0, hyb_rho=math.inf)
+    assert np.array_equal(never.advance(U0, nsteps=4)[0], U_lad)
+    assert np.array_equal(always.advance(U0, nsteps=4)[0], U_meg)
+    cell_all = orc.Oracle(prob, scheme="HYBRID", hybrid_mode=1, hyb_rho=math.inf)
+    assert np.array_equal(cell_all.rhs(U_meg), meg.rhs(U_meg))
+    cell_none = orc.Oracle(prob, scheme="HYBRID", hybrid_mode=1)
+    R1, R2 = cell_none.rhs(U_lad), lad.rhs(U_lad)
+    assert np.abs(R1 - R2).max() <= 1e-14 * np.abs(R2).max() * 100
+    # the troubled-cell criterion of Sec. 5: rho below half the minimum initial density
+    tp = orc.Oracle(prob, scheme="HYBRID", hybrid_mode=0, hyb_rho=0.5 * 0.125)
+    assert tp.hybrid_flag(U0) == 0
+    U_low = U0.copy()
+    U_low[:, 20, 40] *= 0.4  # a node of the rho = 0.125 region drops to 0.05
+    assert tp.hybrid_flag(U_low) == 1
+
+
+# ---------------------------------------------------------------- CFL
+def test_cfl_dt_closed_form(orc):
+    prob = inputs.triple_point(32, 16)
+    W = np.zeros((4, 16, 32))
+    W[0], W[1], W[2], W[3] = 1.3, 0.4, -0.7, 2.0
+    prob["U"] = inputs.prim_to_cons(W, 1.4)
+    o = orc.Oracle(prob, cfl=0.2)
+    c = math.sqrt(1.4 * 2.0 / 1.3)
+    hx, hy = prob["h"][0], prob["h"][1]
+    want = 0.2 / ((0.4 + c) / hx + (0.7 + c) / hy)
+    assert abs(o.cfl_dt(prob["U"]) - want) <= 1e-14 * want
+
+
+# ---------------------------------------------------------------- P-13 robustness
+def test_cgbr_positive_on_leblanc_and_triple_point(orc):
+    prob = inputs.shock_tube("leblanc", 900)
+    o = orc.Oracle(prob, scheme="MEG6", gamma=5.0 / 3.0, cfl=0.5)
+    U = prob["U"]
+    for _ in range(300):
+        U = o.rk3_step(U, o.cfl_dt(U))
+        p = (5.0 / 3.0 - 1) * (U[2] - 0.5 * U[1] ** 2 / U[0])
+        assert U[0].min() > 0 and p.min() > 0
+    prob = inputs.triple_point(112, 48)
+    o = orc.Oracle(prob, scheme="MEG6")
+    U, _, _ = o.advance(prob["U"], nsteps=30)
+    p = 0.4 * (U[3] - 0.5 * (U[1] ** 2 + U[2] ** 2) / U[0])
+    assert U[0].min() > 0 and p.min() > 0
+
+
+def test_entropy_criterion_reading_on_sod(orc):
+    """Reading of the entropy-wave criterion: limited (MP5) where the linear
+    state leaves the MP bounds, central linear inside them.  On Sod this gives a
+    density total variation within 2 % of the exact one (1 - 0.125); the
+    printed direction of the inequality gives a visibly larger variation."""
+    tv = {}
+    for printed in (0, 1):
+        prob = inputs.shock_tube("sod", 400)
+        o = orc.Oracle(prob, scheme="MEG6", cfl=0.5, read_mp_printed=printed)
+        U, _, _ = o.advance(prob["U"], t_end=0.2)
+        tv[printed] = np.abs(np.diff(U[0])).sum()
+    assert tv[0] <= 0.875 * 1.02
+    assert tv[1] > tv[0] * 1.02
+
+
+def test_lad_bulk_coefficient_hand_value(orc):
+    """beta* for u = -x^5, rho = 1 + x/10, p = 1 (1D, E4): E4 differentiates the
+    quintic with the constant error 4h^4, so div u = -5x^4 + 4h^4 < 0 (f_sw = 1);
+    its five-point fourth difference is -120 h^4; Delta_beta = h; the Gaussian
+    overbar keeps the linear density: beta* = C_beta * 120 h^6 * rho(x)."""
+    n = 48
+    h = 1.0 / n
+    x = 0.5 + (np.arange(n) + 0.5) * h
+    W = np.stack([1.0 + 0.1 * x, -x ** 5, np.ones(n)])
+    prob = inputs._problem("lad", 1, [n], [h], [[1, 1]], W, 1.4)
+    beta, _ = orc.Oracle(prob, scheme="LAD_E4").lad_coeffs(prob["U"])
+    want = 1.75 * 120.0 * h ** 6 * (1.0 + 0.1 * x)
+    sl = slice(10, n - 10)
+    assert np.allclose(beta[sl], want[sl], rtol=1e-7)
+
+
+def test_sensor_hand_values(orc):
+    """Omega^d at rest is the pressure sensor (the Ducros ratio is one without
+    dilatation or vorticity); a pure shear layer suppresses it."""
+    n = 16
+    p = np.where(np.arange(n) < 8, 1.0, 0.1)
+    W = np.stack([np.ones(n), np.zeros(n), p])
+    prob = inputs._problem("om", 1, [n], [1.0 / n], [[1, 1]], W, 1.4)
+    om = orc.Oracle(prob, scheme="MEG6").omega(prob["U"])
+    assert abs(om[7] - 0.9 / 3.1) < 1e-15 and abs(om[8] - 0.9 / 1.3) < 1e-15 and om[3] == 0.0
+    # u = y (vorticity, no dilatation) with the same pressure step along x
+    m = 12
+    y = (np.arange(m) + 0.5) / m
+    W2 = np.zeros((4, m, n))
+    W2[0] = 1.0
+    W2[1] = y[:, None]
+    W2[3] = p[None, :]
+    prob2 = inputs._problem("om2", 2, [n, m], [1.0 / n, 1.0 / m], [[1, 1], [1, 1]], W2, 1.4)
+    om2 = orc.Oracle(prob2, scheme="MEG6").omega(prob2["U"])
+    assert np.abs(om2).max() < 1e-28
