@@ -1,0 +1,155 @@
+/*
+ * cgflow: GB300-native right-hand side of the compressible Euler equations in
+ * curvilinear form with the shock-capturing families assessed in
+ * Kumar, Saini, Vadlamani & Chamarthi, arXiv 2511.18042:
+ *   C-GBR  centralised gradient-based reconstruction (MEG6 explicit / MIG4
+ *          compact gradients, MP5 limiting, wave-appropriate sensor, HLLC),
+ *          Sec. 2.3, Eq. (7)-(10);
+ *   LAD    local artificial diffusivity (E4 explicit / C6 compact central
+ *          differences, artificial bulk viscosity and conductivity smoothed by
+ *          a truncated Gaussian, implicit filter for C6), Sec. 2.2, Eq. (4)-(6);
+ *   HYBRID LAD-GBR switching on troubled cells, Sec. 5, Algorithm 3 (whole
+ *          stage) or per interface.
+ * plus TVD-RK3 time stepping (Sec. 2.1, Sec. 4 Algorithms 1-2), the CFL time
+ * step (Sec. 3) and grid metrics on the device (Sec. 2.1, Eq. 1-2).
+ *
+ * Conventions (every entry point):
+ *  - Arrays are FP64, device memory unless the name says _host, structure of
+ *    arrays: nv = ndim + 2 planes of n0*n1*n2 nodes, node (i,j,k) at
+ *    i + n0*(j + n1*k), no ghost nodes.  Conserved order (rho, rho*u_0, ..,
+ *    rho*u_{ndim-1}, E), E the total energy per unit volume.  Caller-owned;
+ *    borrowed for the duration of the call (stream-ordered).
+ *  - stream: a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    All work is enqueued on it; calls return before the GPU finishes unless
+ *    stated otherwise.
+ *  - Return: 0 (CG_OK) or a negative cg_status; cg_last_error() gives a
+ *    thread-local message.  No exception crosses the interface.
+ *  - Handles own their device scratch (allocated at create, freed at destroy).
+ *    One handle must not be used from two threads at once; separate handles
+ *    are independent.
+ */
+#ifndef CGFLOW_H
+#define CGFLOW_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CG_API __attribute__((visibility("default")))
+
+typedef enum {
+    CG_OK = 0,
+    CG_ERR_INVALID_ARG = -1,
+    CG_ERR_CUDA = -2,
+    CG_ERR_OOM = -3,
+    CG_ERR_NONPHYSICAL = -4, /* rho <= 0, p <= 0 or NaN produced; see cg_last_bad_index */
+    CG_ERR_UNSUPPORTED = -5,
+    CG_ERR_TIMEOUT = -6
+} cg_status;
+
+typedef enum { CG_BC_PERIODIC = 0, CG_BC_EXTRAP = 1, CG_BC_REFLECT = 2, CG_BC_INFLOW = 3 } cg_bc;
+typedef enum { CG_MEG6 = 0, CG_MIG4 = 1, CG_LAD_E4 = 2, CG_LAD_C6 = 3, CG_HYBRID = 4 } cg_scheme;
+typedef enum { CG_HYBRID_GLOBAL = 0, CG_HYBRID_CELL = 1 } cg_hybrid_mode;
+typedef enum { CG_FP64 = 0, CG_MIXED = 1 } cg_precision;
+
+typedef struct cg_grid cg_grid;
+typedef struct cg_solver cg_solver;
+
+/* Scheme parameters (Sec. 2.2-2.3, Sec. 3 "CFL 0.2", Sec. 5 thresholds). */
+typedef struct {
+    double gamma;         /* ratio of specific heats */
+    double minf;          /* reference Mach number in p = rho T / (gamma minf^2) */
+    int scheme;           /* cg_scheme */
+    int precision;        /* cg_precision */
+    int hybrid_mode;      /* cg_hybrid_mode (scheme == CG_HYBRID) */
+    int hybrid_sensor;    /* per-interface mode: nodes with Omega > sensor_thresh are troubled too */
+    double hyb_rho;       /* troubled where rho < hyb_rho (-inf: never) */
+    double hyb_p;         /* troubled where p < hyb_p   (-inf: never) */
+    double cfl;           /* Courant number of cg_cfl_dt */
+    double c_beta, c_kappa; /* LAD coefficients C_beta, C_kappa (Eq. 4-5) */
+    double alpha_f;       /* implicit filter parameter (LAD-C6) */
+    double sensor_thresh; /* Omega threshold of Eq. (8), 0.01 */
+    double mp_eps;        /* MP tolerance of Eq. (8), 1e-20 */
+    double mp_alpha;      /* MP5 alpha (Suresh & Huynh), 4 */
+    int filter_on;        /* LAD-C6: implicit filter after the last RK stage */
+    int omega_window;     /* interface sensor window half-width w (1..4): max over nodes i-w+1..i+w */
+    double inflow[3][2][5]; /* primitive (rho, u.., p) held on CG_BC_INFLOW faces [dir][side] */
+} cg_params;
+
+/* Fills the defaults: gamma 1.4, minf 1, MEG6, FP64, CFL 0.2, C_beta 1.75,
+ * C_kappa 0.01, alpha_f 0.45, Omega threshold 0.01, MP eps 1e-20, alpha 4,
+ * window 4, filter on, no hybrid thresholds. */
+CG_API void cg_params_default(cg_params *p);
+
+/* Uniform Cartesian grid, node spacing h[d] (Sec. 2.1 with x = xi h).
+ * n[d] >= 8 for non-periodic directions, >= 1 otherwise; unused directions 1.
+ * bc[2*d + side]: cg_bc.  The metrics are the exact constants. */
+CG_API int cg_grid_create_cartesian(int ndim, const int64_t n[3], const double h[3],
+                                    const int bc[6], cg_grid **out);
+/* Body-fitted grid from node coordinates xyz_dev (device, ndim planes laid out
+ * like one state plane).  period[3*d + m]: translation of coordinate m across
+ * periodic direction d.  The coordinates are copied; the metrics are computed
+ * on the device by cg_solver_create with the scheme's own derivative operator
+ * (Sec. 2.1, xi_hat = xi_x / J; conservative metric identities). */
+CG_API int cg_grid_create_curvilinear(int ndim, const int64_t n[3], const double *xyz_dev,
+                                      const double period[9], const int bc[6], cg_grid **out);
+CG_API void cg_grid_destroy(cg_grid *g);
+
+/* Solver = grid + parameters + scratch.  The grid must outlive the solver. */
+CG_API int cg_solver_create(const cg_grid *g, const cg_params *p, cg_solver **out);
+CG_API void cg_solver_destroy(cg_solver *s);
+
+/* Metrics on interior nodes: node_dev gets ndim*ndim planes xi_hat[l][m]
+ * then one plane J; iface_dev (may be NULL) gets ndim*ndim planes of the
+ * interface metrics of the l-interface i+1/2 stored at node i. */
+CG_API int cg_metrics(cg_solver *s, double *node_dev, double *iface_dev, void *stream);
+
+/* Right-hand side of Eq. (1): R = -J sum_l (F_{l,i+1/2} - F_{l,i-1/2}) for C-GBR,
+ * R = -J sum_l D_l F_l for LAD, the mixture for the hybrid (Sec. 2, Alg. 1-3). */
+CG_API int cg_rhs(cg_solver *s, const double *U, double *R, void *stream);
+
+/* One TVD-RK3 step in place with time step dt (host value); LAD-C6 applies the
+ * implicit filter after the third stage when filter_on.  Sets the sticky
+ * non-physical flag read by cg_sync_status. */
+CG_API int cg_rk3_step(cg_solver *s, double *U, double dt, void *stream);
+/* Same with dt read from device memory at run time (graph-capturable). */
+CG_API int cg_rk3_step_dev(cg_solver *s, double *U, const double *dt_dev, void *stream);
+
+/* CFL time step dt = cfl / max_i J sum_l (|xi_hat_l . u| + c |xi_hat_l|).
+ * dt_on_device = 1: *dt_out is device memory, nothing waits; 0: host memory,
+ * the call synchronises the stream. */
+CG_API int cg_cfl_dt(cg_solver *s, const double *U, double *dt_out, int dt_on_device, void *stream);
+
+/* March with CFL time steps until t_end (last step clipped) or nsteps steps,
+ * whichever comes first (t_end <= 0: nsteps only).  Synchronises; returns
+ * CG_ERR_NONPHYSICAL if a non-physical state appeared. */
+CG_API int cg_advance(cg_solver *s, double *U, int64_t nsteps, double t_end, double *t_out,
+                      int64_t *steps_out, void *stream);
+/* As cg_advance, but U_host is host memory: copied to the device, advanced,
+ * copied back. */
+CG_API int cg_advance_host(cg_solver *s, double *U_host, int64_t nsteps, double t_end,
+                           double *t_out, void *stream);
+
+/* Diagnostics. */
+CG_API int cg_omega(cg_solver *s, const double *U, double *omega, void *stream);
+CG_API int cg_lad_coeffs(cg_solver *s, const double *U, double *beta, double *kappa, void *stream);
+CG_API int cg_filter(cg_solver *s, double *U, void *stream);
+/* Interface fluxes of the C-GBR / per-interface hybrid schemes along dir for all
+ * interior lines, interfaces i = -1..n_dir-1: layout [v][line][n_dir+1]. */
+CG_API int cg_iface_flux(cg_solver *s, const double *U, int dir, double *F, void *stream);
+/* Hybrid: last global decision (0 LAD, 1 GBR) and troubled-node count of the
+ * last evaluated stage.  Synchronises. */
+CG_API int cg_hybrid_state(cg_solver *s, int *last_flag, int64_t *n_troubled, void *stream);
+/* Synchronises and reports (then clears) the sticky non-physical flag. */
+CG_API int cg_sync_status(cg_solver *s, void *stream);
+CG_API int64_t cg_last_bad_index(const cg_solver *s);
+CG_API const char *cg_last_error(void);
+/* Number of kernel launches this handle has enqueued since creation. */
+CG_API int64_t cg_launch_count(const cg_solver *s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

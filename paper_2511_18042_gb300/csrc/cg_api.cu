@@ -1,0 +1,902 @@
+// C ABI of the cgflow library (include/cgflow.h): handles, scratch, the
+// orchestration of one RK stage per scheme, RK3, CFL and diagnostics.
+// Host arithmetic that must reproduce the method's rounding (interface frames
+// of Cartesian grids, Thomas pivots) is compiled with contraction disabled.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/cgflow.h"
+#include "cg_kernels.cuh"
+#include "cg_lad.cuh"
+#include "cg_metrics.cuh"
+
+using namespace cgk;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define CG_CUDA(call)                                                                         \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess) return fail(CG_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+int grid_blocks(long long work, int threads) {
+  long long b = (work + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > 152LL * 32) b = 152LL * 32;
+  return (int)b;
+}
+
+// host copy of the oracle-independent Thomas pivots for a constant-coefficient
+// system (unit diagonal, off-diagonal a); closure rows 0 and m-1 decoupled
+// (non-periodic) or cyclic with the Sherman-Morrison modification.
+struct HostLine {
+  std::vector<double> cp, den, z;
+  double fden = 0.0, gam = -1.0;
+};
+HostLine make_line(int m, double a, bool cyclic) {
+  HostLine L;
+  L.cp.assign(m, 0.0);
+  L.den.assign(m, 1.0);
+  std::vector<double> A(m, a), B(m, 1.0), C(m, a);
+  if (!cyclic) {
+    A[0] = 0.0; C[0] = 0.0; A[m - 1] = 0.0; C[m - 1] = 0.0;
+  } else {
+    double gam = -B[0];
+    L.gam = gam;
+    B[0] = B[0] - gam;
+    B[m - 1] = B[m - 1] - a * a / gam;
+    A[0] = 0.0;
+    C[m - 1] = 0.0;
+  }
+  L.cp[0] = C[0] / B[0];
+  L.den[0] = B[0];
+  for (int i = 1; i < m; ++i) {
+    double den = B[i] - A[i] * L.cp[i - 1];
+    L.den[i] = den;
+    L.cp[i] = C[i] / den;
+  }
+  if (cyclic) {
+    std::vector<double> u(m, 0.0), dp(m);
+    u[0] = L.gam;
+    u[m - 1] = a;
+    dp[0] = u[0] / B[0];
+    for (int i = 1; i < m; ++i) dp[i] = (u[i] - A[i] * dp[i - 1]) / L.den[i];
+    L.z.assign(m, 0.0);
+    L.z[m - 1] = dp[m - 1];
+    for (int i = m - 2; i >= 0; --i) L.z[i] = dp[i] - L.cp[i] * L.z[i + 1];
+    L.fden = 1.0 + L.z[0] + a * L.z[m - 1] / L.gam;
+  }
+  return L;
+}
+
+struct DevLine {
+  LineCoef lc{};
+  double* buf = nullptr;
+};
+
+}  // namespace
+
+struct cg_grid {
+  int nd;
+  int n[3];
+  double h[3];
+  int bc[3][2];
+  int curv;
+  double* xyz = nullptr;  // device copy of the coordinates
+  double period[3][3];
+};
+
+struct cg_solver {
+  const cg_grid* grid;
+  cg_params p;
+  DevGrid dg;
+  int nd, nv;
+  long long N;
+  // metric planes (curvilinear)
+  double* metric = nullptr;
+  // stage scratch
+  double *W = nullptr, *acc = nullptr, *om = nullptr, *U1 = nullptr, *U2 = nullptr, *Rtmp = nullptr;
+  double* G[3] = {nullptr, nullptr, nullptr};
+  Box omBox, gdBox[3];
+  DevLine mig4[3];
+  // LAD scratch
+  LadBuffers lad;
+  // hybrid
+  unsigned char* mask = nullptr;
+  double* hflux[3] = {nullptr, nullptr, nullptr};
+  Box hBox[3];
+  int* hyb_flag = nullptr;          // device: decision of the last stage
+  unsigned long long* hyb_count = nullptr;
+  // scalars
+  double* dt = nullptr;             // device dt
+  double* t = nullptr;              // device time
+  unsigned long long* cflmax = nullptr;
+  unsigned int* bad_flag = nullptr;
+  unsigned long long* bad_idx = nullptr;
+  long long launches = 0;
+  long long last_bad = -1;
+  double* host_stage = nullptr;     // device state for cg_advance_host
+  int iface_dir = -1;               // diagnostics: direction whose interface fluxes are written
+  double* iface_out = nullptr;
+  DevLine c6grad[3], c6flux[3], filt[3];  // LAD-C6 line systems
+  double* work = nullptr;           // line scratch of the LAD-C6 solves
+  size_t work_elems = 0;
+};
+
+static void fill_devgrid(const cg_grid* g, const cg_params* p, DevGrid& d) {
+  memset(&d, 0, sizeof d);
+  d.nd = g->nd;
+  d.nv = g->nd + 2;
+  d.N = 1;
+  d.NP = 1;
+  for (int k = 0; k < 3; ++k) {
+    d.n[k] = g->n[k];
+    d.N *= g->n[k];
+    d.P[k] = g->n[k] + (k < g->nd ? 2 * PM : 0);
+    d.NP *= d.P[k];
+    d.bc[k][0] = g->bc[k][0];
+    d.bc[k][1] = g->bc[k][1];
+    for (int s = 0; s < 2; ++s) {
+      double W[5] = {0, 0, 0, 0, 0}, Q[5];
+      for (int v = 0; v < d.nv; ++v) W[v] = p->inflow[k][s][v];
+      // conserved form of the inflow state (ideal gas)
+      double q = 0.0;
+      Q[0] = W[0];
+      for (int m = 0; m < g->nd; ++m) {
+        Q[1 + m] = W[0] * W[1 + m];
+        q += W[1 + m] * W[1 + m];
+      }
+      Q[g->nd + 1] = W[g->nd + 1] / (p->gamma - 1.0) + 0.5 * W[0] * q;
+      for (int v = 0; v < 5; ++v) {
+        d.inflowW[k][s][v] = W[v];
+        d.inflowQ[k][s][v] = v < d.nv ? Q[v] : 0.0;
+      }
+    }
+  }
+  d.gamma = p->gamma;
+  d.gm1 = p->gamma - 1.0;
+  d.gm2 = p->gamma * p->minf * p->minf;
+  d.curv = g->curv;
+  int nd = g->nd;
+  if (!g->curv) {
+    double h0 = g->h[0], h1 = g->h[1], h2 = g->h[2];
+    if (nd == 1) { d.cxh[0] = 1.0; d.cjac = 1.0 / h0; }
+    if (nd == 2) { d.cxh[0] = h1; d.cxh[1] = h0; d.cjac = 1.0 / (h0 * h1); }
+    if (nd == 3) { d.cxh[0] = h1 * h2; d.cxh[1] = h0 * h2; d.cxh[2] = h0 * h1; d.cjac = 1.0 / (h0 * h1 * h2); }
+    for (int k = 0; k < 3; ++k) d.ch[k] = g->h[k];
+    // interface frame of each direction: the metric vector is (0..xi_dd..0)
+    for (int dir = 0; dir < nd; ++dir) {
+      double xi[3] = {0, 0, 0};
+      xi[dir] = d.cxh[dir];
+      double g2 = 0.0;
+      for (int m = 0; m < nd; ++m) g2 += xi[m] * xi[m];
+      double ig = 1.0 / sqrt(g2);
+      double n[3] = {0, 0, 0}, t1[3] = {0, 0, 0}, t2[3] = {0, 0, 0};
+      for (int m = 0; m < nd; ++m) n[m] = xi[m] * ig;
+      if (nd == 2) { t1[0] = -n[1]; t1[1] = n[0]; }
+      if (nd == 3) {
+        int s = 0;
+        if (fabs(n[1]) < fabs(n[s])) s = 1;
+        if (fabs(n[2]) < fabs(n[s])) s = 2;
+        int a = (s + 1) % 3, b = (s + 2) % 3;
+        double r = 1.0 / sqrt(n[a] * n[a] + n[b] * n[b]);
+        t1[s] = 0.0;
+        t1[a] = -n[b] * r;
+        t1[b] = n[a] * r;
+        t2[0] = n[1] * t1[2] - n[2] * t1[1];
+        t2[1] = n[2] * t1[0] - n[0] * t1[2];
+        t2[2] = n[0] * t1[1] - n[1] * t1[0];
+      }
+      d.cg2[dir] = g2;
+      d.cg[dir] = sqrt(g2);
+      d.cig[dir] = ig;
+      d.cig2[dir] = 1.0 / g2;
+      for (int m = 0; m < 3; ++m) { d.cn[dir][m] = n[m]; d.ct1[dir][m] = t1[m]; d.ct2[dir][m] = t2[m]; }
+    }
+  }
+}
+
+static Box make_box(const cg_solver* s, int grow_all, int dir, int grow_dir) {
+  Box b;
+  for (int k = 0; k < 3; ++k) {
+    int gr = k < s->nd ? (k == dir ? grow_dir : grow_all) : 0;
+    b.off[k] = gr;
+    b.ext[k] = s->dg.n[k] + 2 * gr;
+  }
+  return b;
+}
+
+template <typename T>
+static int dalloc(T** p, size_t count) {
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return fail(CG_ERR_OOM, "cudaMalloc of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
+  }
+  return CG_OK;
+}
+
+static int upload_line(DevLine& L, int m, double a, bool cyclic, int lo) {
+  HostLine h = make_line(m, a, cyclic);
+  int rc = dalloc(&L.buf, (size_t)3 * m);
+  if (rc) return rc;
+  std::vector<double> all(3 * (size_t)m, 0.0);
+  for (int i = 0; i < m; ++i) {
+    all[i] = h.cp[i];
+    all[m + i] = h.den[i];
+    all[2 * m + i] = cyclic ? h.z[i] : 0.0;
+  }
+  CG_CUDA(cudaMemcpy(L.buf, all.data(), all.size() * sizeof(double), cudaMemcpyHostToDevice));
+  L.lc.cp = L.buf;
+  L.lc.den = L.buf + m;
+  L.lc.z = L.buf + 2 * m;
+  L.lc.a = a;
+  L.lc.gam = h.gam;
+  L.lc.fden = h.fden;
+  L.lc.m = m;
+  L.lc.lo = lo;
+  L.lc.periodic = cyclic ? 1 : 0;
+  return CG_OK;
+}
+
+// ---------------------------------------------------------------- metrics
+static int compute_metrics(cg_solver* s, cudaStream_t st) {
+  const cg_grid* g = s->grid;
+  int nd = g->nd;
+  EBox eb;
+  eb.nd = nd;
+  eb.NE = 1;
+  for (int d = 0; d < 3; ++d) {
+    eb.n[d] = g->n[d];
+    eb.ge[d] = d < nd ? MGC : 0;
+    eb.PE[d] = eb.n[d] + 2 * eb.ge[d];
+    eb.NE *= eb.PE[d];
+  }
+  int six = (s->p.scheme == CG_MEG6 || s->p.scheme == CG_MIG4) ? 1 : 0;
+  std::vector<double*> tmp;
+  auto alloc = [&](double** p) -> int {
+    int rc = dalloc(p, (size_t)eb.NE);
+    if (!rc) tmp.push_back(*p);
+    return rc;
+  };
+  int threads = 256, blocks = grid_blocks(eb.NE, threads);
+  double* X[3] = {nullptr, nullptr, nullptr};
+  for (int m = 0; m < nd; ++m) {
+    if (alloc(&X[m])) return CG_ERR_OOM;
+    km_load<<<blocks, threads, 0, st>>>(eb, g->xyz, s->N, m, X[m]);
+    for (int d = 0; d < nd; ++d) {
+      int per = g->bc[d][0] == CG_BC_PERIODIC;
+      km_extend<<<blocks, threads, 0, st>>>(eb, d, per, g->period[d][m], X[m]);
+    }
+  }
+  double* dX[3][3] = {};
+  for (int l = 0; l < nd; ++l)
+    for (int m = 0; m < nd; ++m) {
+      if (alloc(&dX[l][m])) return CG_ERR_OOM;
+      km_op<<<blocks, threads, 0, st>>>(eb, X[m], l, 0, six, dX[l][m]);
+    }
+  double* node[3][3] = {};
+  double* vol;
+  if (alloc(&vol)) return CG_ERR_OOM;
+  for (int l = 0; l < nd; ++l)
+    for (int m = 0; m < nd; ++m)
+      if (alloc(&node[l][m])) return CG_ERR_OOM;
+  if (nd == 1) {
+    std::vector<double> ones(eb.NE, 1.0);
+    CG_CUDA(cudaMemcpyAsync(node[0][0], ones.data(), eb.NE * sizeof(double), cudaMemcpyHostToDevice, st));
+    CG_CUDA(cudaStreamSynchronize(st));
+  } else if (nd == 2) {
+    km_lin<<<blocks, threads, 0, st>>>(eb, dX[1][1], nullptr, 0, node[0][0]);
+    km_lin<<<blocks, threads, 0, st>>>(eb, dX[1][0], nullptr, 2, node[0][1]);
+    km_lin<<<blocks, threads, 0, st>>>(eb, dX[0][1], nullptr, 2, node[1][0]);
+    km_lin<<<blocks, threads, 0, st>>>(eb, dX[0][0], nullptr, 0, node[1][1]);
+  } else {
+    double* P[3][3];
+    for (int lp = 0; lp < 3; ++lp)
+      for (int m = 0; m < 3; ++m) {
+        if (alloc(&P[lp][m])) return CG_ERR_OOM;
+        km_lin<<<blocks, threads, 0, st>>>(eb, dX[lp][(m + 1) % 3], X[(m + 2) % 3], 1, P[lp][m]);
+      }
+    double *A, *B;
+    if (alloc(&A) || alloc(&B)) return CG_ERR_OOM;
+    for (int l = 0; l < 3; ++l) {
+      int l1 = (l + 1) % 3, l2 = (l + 2) % 3;
+      for (int m = 0; m < 3; ++m) {
+        km_op<<<blocks, threads, 0, st>>>(eb, P[l1][m], l2, 0, six, A);
+        km_op<<<blocks, threads, 0, st>>>(eb, P[l2][m], l1, 0, six, B);
+        km_lin<<<blocks, threads, 0, st>>>(eb, A, B, 3, node[l][m]);
+      }
+    }
+  }
+  km_vol<<<blocks, threads, 0, st>>>(eb, nd, dX[0][0], nd > 1 ? dX[0][1] : nullptr, nd > 2 ? dX[0][2] : nullptr,
+                                     nd > 1 ? dX[1][0] : nullptr, nd > 1 ? dX[1][1] : nullptr,
+                                     nd > 2 ? dX[1][2] : nullptr, nd > 2 ? dX[2][0] : nullptr,
+                                     nd > 2 ? dX[2][1] : nullptr, nd > 2 ? dX[2][2] : nullptr, vol);
+  double* ifc;
+  if (alloc(&ifc)) return CG_ERR_OOM;
+  // planes: xh (nd*nd), xt (nd*nd), jac (1), dxl (nd*nd)
+  long long NP = s->dg.NP;
+  int pb = grid_blocks(NP, threads);
+  double* xh = s->metric;
+  double* xt = xh + (size_t)nd * nd * NP;
+  double* jac = xt + (size_t)nd * nd * NP;
+  double* dxl = jac + NP;
+  for (int l = 0; l < nd; ++l)
+    for (int m = 0; m < nd; ++m) {
+      km_store<<<pb, threads, 0, st>>>(eb, s->dg, node[l][m], 0, xh + (size_t)(l * nd + m) * NP);
+      km_op<<<blocks, threads, 0, st>>>(eb, node[l][m], l, 1, six, ifc);
+      km_store<<<pb, threads, 0, st>>>(eb, s->dg, ifc, 0, xt + (size_t)(l * nd + m) * NP);
+      km_disp<<<pb, threads, 0, st>>>(eb, s->dg, X[m], l, dxl + (size_t)(l * nd + m) * NP);
+    }
+  km_store<<<pb, threads, 0, st>>>(eb, s->dg, vol, 1, jac);
+  CG_CUDA(cudaGetLastError());
+  CG_CUDA(cudaStreamSynchronize(st));
+  for (double* p : tmp) cudaFree(p);
+  s->dg.xh = xh;
+  s->dg.xt = xt;
+  s->dg.jac = jac;
+  s->dg.dxl = dxl;
+  return CG_OK;
+}
+
+// ---------------------------------------------------------------- launches
+template <int ND, bool CART, bool COMPACT>
+static void launch_omega(cg_solver* s, cudaStream_t st, const int* guard, int want) {
+  long long tot = s->omBox.size();
+  k_omega<ND, CART, COMPACT><<<grid_blocks(tot, 128), 128, 0, st>>>(
+      s->dg, s->W, s->G[0], s->G[1], s->G[2], s->gdBox[0], s->gdBox[1], s->gdBox[2], s->om, s->omBox, guard, want);
+  s->launches++;
+}
+
+static GbrCfg gbr_cfg(const cg_solver* s) {
+  GbrCfg q;
+  q.gamma = s->p.gamma;
+  q.gm1 = s->p.gamma - 1.0;
+  q.thr = s->p.sensor_thresh;
+  q.eps = s->p.mp_eps;
+  q.alpha = s->p.mp_alpha;
+  q.window = s->p.omega_window;
+  return q;
+}
+
+template <int ND, int DIR, bool CART, bool COMPACT>
+static int launch_sweep(cg_solver* s, const StageArgs& A, cudaStream_t st) {
+  constexpr int LW = sweep_lw(DIR);
+  size_t smem = sizeof(double) * sweep_smem_doubles<ND, DIR>();
+  static bool attr_set = false;
+  if (!attr_set) {
+    CG_CUDA(cudaFuncSetAttribute(k_gbr_sweep<ND, DIR, CART, COMPACT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
+    attr_set = true;
+  }
+  dim3 grid;
+  const int* n = s->dg.n;
+  if (DIR == 0) {
+    long long lines = (long long)n[1] * n[2];
+    grid = dim3((n[0] + SWEEP_TL - 2) / (SWEEP_TL - 1), (unsigned)((lines + LW - 1) / LW), 1);
+  } else {
+    int other = DIR == 1 ? n[2] : n[1];
+    grid = dim3((n[0] + LW - 1) / LW, (n[DIR] + SWEEP_TL - 2) / (SWEEP_TL - 1), other);
+  }
+  k_gbr_sweep<ND, DIR, CART, COMPACT><<<grid, 256, smem, st>>>(s->dg, gbr_cfg(s), A);
+  s->launches++;
+  return CG_OK;
+}
+
+template <int ND, bool CART, bool COMPACT>
+static int sweep_dir(cg_solver* s, int dir, const StageArgs& A, cudaStream_t st) {
+  if (dir == 0) return launch_sweep<ND, 0, CART, COMPACT>(s, A, st);
+  if (ND >= 2 && dir == 1) return launch_sweep<ND, (ND >= 2 ? 1 : 0), CART, COMPACT>(s, A, st);
+  if (ND >= 3 && dir == 2) return launch_sweep<ND, (ND >= 3 ? 2 : 0), CART, COMPACT>(s, A, st);
+  return fail(CG_ERR_INVALID_ARG, "bad direction");
+}
+
+// Primitives, sensor (and compact gradients) of the state Uc into W, om, G.
+template <int ND>
+static int stage_prep_gbr(cg_solver* s, const double* Uc, bool compact, cudaStream_t st, bool prim = true,
+                          const int* guard = nullptr, int want = 0) {
+  if (prim) {
+    k_prim<ND><<<grid_blocks(s->N, 256), 256, 0, st>>>(s->dg, Uc, s->W);
+    s->launches++;
+  }
+  if (compact) {
+    for (int d = 0; d < ND; ++d) {
+      int e1 = (d + 1) % 3 < ND ? s->dg.n[(d + 1) % 3] + 8 : 1;
+      int e2 = (d + 2) % 3 < ND ? s->dg.n[(d + 2) % 3] + 8 : 1;
+      long long lines = (long long)e1 * e2 * (ND + 2);
+      k_compact_grad<ND><<<(unsigned)((lines + 127) / 128), 128, 0, st>>>(s->dg, s->W, d, s->mig4[d].lc, s->G[d],
+                                                                         s->gdBox[d]);
+      s->launches++;
+    }
+  }
+  if (s->dg.curv) {
+    if (compact) launch_omega<ND, false, true>(s, st, guard, want);
+    else launch_omega<ND, false, false>(s, st, guard, want);
+  } else {
+    if (compact) launch_omega<ND, true, true>(s, st, guard, want);
+    else launch_omega<ND, true, false>(s, st, guard, want);
+  }
+  return CG_OK;
+}
+
+template <int ND>
+static int stage_prep_prim(cg_solver* s, const double* Uc, cudaStream_t st) {
+  k_prim<ND><<<grid_blocks(s->N, 256), 256, 0, st>>>(s->dg, Uc, s->W);
+  s->launches++;
+  return CG_OK;
+}
+
+static StageArgs base_args(cg_solver* s) {
+  StageArgs A;
+  memset(&A, 0, sizeof A);
+  A.W = s->W;
+  A.om = s->om;
+  A.omBox = s->omBox;
+  A.acc = s->acc;
+  A.bad_flag = s->bad_flag;
+  A.bad_idx = s->bad_idx;
+  A.dt = s->dt;
+  return A;
+}
+
+// One evaluation of the C-GBR fluxes over all directions with the epilogue of A.
+template <int ND>
+static int gbr_sweeps(cg_solver* s, bool compact, StageArgs A, cudaStream_t st) {
+  for (int d = 0; d < ND; ++d) {
+    A.first = d == 0;
+    A.last = d == ND - 1;
+    A.Gd = s->G[d];
+    A.gdBox = s->gdBox[d];
+    A.iface_out = (s->iface_out && s->iface_dir == d) ? s->iface_out : nullptr;
+    int rc;
+    if (s->dg.curv) rc = compact ? sweep_dir<ND, false, true>(s, d, A, st) : sweep_dir<ND, false, false>(s, d, A, st);
+    else rc = compact ? sweep_dir<ND, true, true>(s, d, A, st) : sweep_dir<ND, true, false>(s, d, A, st);
+    if (rc) return rc;
+  }
+  return CG_OK;
+}
+
+template <int ND>
+static int lad_stage(cg_solver* s, const double* Uc, StageArgs A, cudaStream_t st);
+template <int ND>
+static int lad_filter(cg_solver* s, double* U, cudaStream_t st);
+static int lad_alloc(cg_solver* s);
+static void lad_free(LadBuffers& b);
+
+// RHS or RK stage: out = R (rk = 0) or the stage combination (rk = 1)
+template <int ND>
+static int stage(cg_solver* s, const double* Uc, const double* Un, double* out, int rk, int stage_no,
+                 cudaStream_t st) {
+  int sch = s->p.scheme;
+  StageArgs A = base_args(s);
+  A.rk = rk;
+  A.stage = stage_no;
+  A.R = out;
+  A.Un = Un;
+  A.Uc = Uc;
+  A.Uout = out;
+  if (sch == CG_MEG6 || sch == CG_MIG4) {
+    bool compact = sch == CG_MIG4;
+    stage_prep_gbr<ND>(s, Uc, compact, st);
+    return gbr_sweeps<ND>(s, compact, A, st);
+  }
+  return lad_stage<ND>(s, Uc, A, st);
+}
+
+template <int ND>
+static int rk3(cg_solver* s, double* U, cudaStream_t st) {
+  int rc;
+  if ((rc = stage<ND>(s, U, U, s->U1, 1, 1, st))) return rc;
+  if ((rc = stage<ND>(s, s->U1, U, s->U2, 1, 2, st))) return rc;
+  if ((rc = stage<ND>(s, s->U2, U, U, 1, 3, st))) return rc;
+  if (s->p.scheme == CG_LAD_C6 && s->p.filter_on) return lad_filter<ND>(s, U, st);
+  return CG_OK;
+}
+
+template <int ND>
+static void cfl_launch(cg_solver* s, const double* U, double* dt_dev, double* t_dev, double t_end, cudaStream_t st) {
+  cudaMemsetAsync(s->cflmax, 0, sizeof(unsigned long long), st);
+  if (s->dg.curv) k_cfl_max<ND, false><<<grid_blocks(s->N, 256), 256, 0, st>>>(s->dg, U, s->cflmax);
+  else k_cfl_max<ND, true><<<grid_blocks(s->N, 256), 256, 0, st>>>(s->dg, U, s->cflmax);
+  k_cfl_finish<<<1, 1, 0, st>>>(s->cflmax, s->p.cfl, dt_dev, t_dev, t_end);
+  s->launches += 2;
+}
+
+#define DISPATCH_ND(s, fn, ...)                      \
+  ((s)->nd == 1 ? fn<1>(__VA_ARGS__)                 \
+   : (s)->nd == 2 ? fn<2>(__VA_ARGS__)               \
+                  : fn<3>(__VA_ARGS__))
+
+#include "cg_lad_impl.cuh"
+
+// ======================================================================
+extern "C" {
+
+CG_API void cg_params_default(cg_params* p) {
+  memset(p, 0, sizeof *p);
+  p->gamma = 1.4;
+  p->minf = 1.0;
+  p->scheme = CG_MEG6;
+  p->precision = CG_FP64;
+  p->hybrid_mode = CG_HYBRID_GLOBAL;
+  p->hybrid_sensor = 0;
+  p->hyb_rho = -HUGE_VAL;
+  p->hyb_p = -HUGE_VAL;
+  p->cfl = 0.2;
+  p->c_beta = 1.75;
+  p->c_kappa = 0.01;
+  p->alpha_f = 0.45;
+  p->sensor_thresh = 0.01;
+  p->mp_eps = 1e-20;
+  p->mp_alpha = 4.0;
+  p->filter_on = 1;
+  p->omega_window = 4;
+}
+
+CG_API const char* cg_last_error(void) { return g_err.c_str(); }
+
+static int check_grid_args(int ndim, const int64_t n[3], const int bc[6]) {
+  if (ndim < 1 || ndim > 3) return fail(CG_ERR_INVALID_ARG, "ndim must be 1, 2 or 3");
+  for (int d = 0; d < 3; ++d) {
+    if (d >= ndim) {
+      if (n[d] != 1) return fail(CG_ERR_INVALID_ARG, "unused direction %d must have n = 1", d);
+      continue;
+    }
+    if (n[d] < 1 || n[d] > (1 << 24)) return fail(CG_ERR_INVALID_ARG, "n[%d] out of range", d);
+    for (int s = 0; s < 2; ++s)
+      if (bc[2 * d + s] < CG_BC_PERIODIC || bc[2 * d + s] > CG_BC_INFLOW)
+        return fail(CG_ERR_INVALID_ARG, "bad boundary type");
+    if ((bc[2 * d] == CG_BC_PERIODIC) != (bc[2 * d + 1] == CG_BC_PERIODIC))
+      return fail(CG_ERR_INVALID_ARG, "periodic direction %d needs both sides periodic", d);
+    if (bc[2 * d] != CG_BC_PERIODIC && n[d] < 8)
+      return fail(CG_ERR_INVALID_ARG, "non-periodic direction %d needs n >= 8", d);
+  }
+  return CG_OK;
+}
+
+CG_API int cg_grid_create_cartesian(int ndim, const int64_t n[3], const double h[3], const int bc[6], cg_grid** out) {
+  if (!n || !h || !bc || !out) return fail(CG_ERR_INVALID_ARG, "null argument");
+  int rc = check_grid_args(ndim, n, bc);
+  if (rc) return rc;
+  for (int d = 0; d < ndim; ++d)
+    if (!(h[d] > 0.0)) return fail(CG_ERR_INVALID_ARG, "spacing must be positive");
+  cg_grid* g = new (std::nothrow) cg_grid();
+  if (!g) return fail(CG_ERR_OOM, "host allocation failed");
+  g->nd = ndim;
+  g->curv = 0;
+  for (int d = 0; d < 3; ++d) {
+    g->n[d] = (int)n[d];
+    g->h[d] = d < ndim ? h[d] : 1.0;
+    g->bc[d][0] = d < ndim ? bc[2 * d] : CG_BC_PERIODIC;
+    g->bc[d][1] = d < ndim ? bc[2 * d + 1] : CG_BC_PERIODIC;
+    for (int m = 0; m < 3; ++m) g->period[d][m] = 0.0;
+  }
+  *out = g;
+  return CG_OK;
+}
+
+CG_API int cg_grid_create_curvilinear(int ndim, const int64_t n[3], const double* xyz_dev, const double period[9],
+                                      const int bc[6], cg_grid** out) {
+  if (!n || !xyz_dev || !bc || !out) return fail(CG_ERR_INVALID_ARG, "null argument");
+  int rc = check_grid_args(ndim, n, bc);
+  if (rc) return rc;
+  for (int d = 0; d < ndim; ++d)
+    if (bc[2 * d] != CG_BC_PERIODIC && n[d] < 2) return fail(CG_ERR_INVALID_ARG, "need two nodes per line");
+  cg_grid* g = new (std::nothrow) cg_grid();
+  if (!g) return fail(CG_ERR_OOM, "host allocation failed");
+  g->nd = ndim;
+  g->curv = 1;
+  long long N = 1;
+  for (int d = 0; d < 3; ++d) {
+    g->n[d] = (int)n[d];
+    N *= n[d];
+    g->h[d] = 1.0;
+    g->bc[d][0] = d < ndim ? bc[2 * d] : CG_BC_PERIODIC;
+    g->bc[d][1] = d < ndim ? bc[2 * d + 1] : CG_BC_PERIODIC;
+    for (int m = 0; m < 3; ++m) g->period[d][m] = (period && d < ndim && m < ndim) ? period[3 * d + m] : 0.0;
+  }
+  if (dalloc(&g->xyz, (size_t)ndim * N)) { delete g; return CG_ERR_OOM; }
+  cudaError_t e = cudaMemcpy(g->xyz, xyz_dev, sizeof(double) * ndim * N, cudaMemcpyDeviceToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(g->xyz);
+    delete g;
+    return fail(CG_ERR_CUDA, "coordinate copy failed: %s", cudaGetErrorString(e));
+  }
+  *out = g;
+  return CG_OK;
+}
+
+CG_API void cg_grid_destroy(cg_grid* g) {
+  if (!g) return;
+  if (g->xyz) cudaFree(g->xyz);
+  delete g;
+}
+
+CG_API void cg_solver_destroy(cg_solver* s) {
+  if (!s) return;
+  double* bufs[] = {s->metric, s->W, s->acc, s->om, s->U1, s->U2, s->Rtmp, s->G[0], s->G[1], s->G[2],
+                    s->hflux[0], s->hflux[1], s->hflux[2], s->dt, s->t, s->host_stage};
+  for (double* b : bufs)
+    if (b) cudaFree(b);
+  for (int d = 0; d < 3; ++d) {
+    DevLine* ls[4] = {&s->mig4[d], &s->c6grad[d], &s->c6flux[d], &s->filt[d]};
+    for (DevLine* l : ls)
+      if (l->buf) cudaFree(l->buf);
+  }
+  if (s->work) cudaFree(s->work);
+  lad_free(s->lad);
+  if (s->mask) cudaFree(s->mask);
+  if (s->hyb_flag) cudaFree(s->hyb_flag);
+  if (s->hyb_count) cudaFree(s->hyb_count);
+  if (s->cflmax) cudaFree(s->cflmax);
+  if (s->bad_flag) cudaFree(s->bad_flag);
+  if (s->bad_idx) cudaFree(s->bad_idx);
+  delete s;
+}
+
+CG_API int cg_solver_create(const cg_grid* g, const cg_params* p, cg_solver** out) {
+  if (!g || !p || !out) return fail(CG_ERR_INVALID_ARG, "null argument");
+  if (p->scheme < CG_MEG6 || p->scheme > CG_HYBRID) return fail(CG_ERR_INVALID_ARG, "bad scheme");
+  if (p->precision != CG_FP64) return fail(CG_ERR_UNSUPPORTED, "only the FP64 form is built in this library");
+  if (!(p->gamma > 1.0) || !(p->cfl > 0.0)) return fail(CG_ERR_INVALID_ARG, "gamma > 1 and cfl > 0 required");
+  if (p->omega_window < 1 || p->omega_window > 4) return fail(CG_ERR_INVALID_ARG, "omega_window must be 1..4");
+  if (g->curv && p->scheme == CG_LAD_C6)
+    return fail(CG_ERR_UNSUPPORTED, "LAD-C6 on curvilinear grids is not supported (the metric identities need the compact operator)");
+  cg_solver* s = new (std::nothrow) cg_solver();
+  if (!s) return fail(CG_ERR_OOM, "host allocation failed");
+  s->grid = g;
+  s->p = *p;
+  s->nd = g->nd;
+  s->nv = g->nd + 2;
+  fill_devgrid(g, p, s->dg);
+  s->N = s->dg.N;
+  int rc = CG_OK;
+  size_t NV = (size_t)s->nv * s->N;
+  s->omBox = make_box(s, 4, -1, 4);
+  if ((rc = dalloc(&s->W, NV)) || (rc = dalloc(&s->acc, NV)) || (rc = dalloc(&s->U1, NV)) ||
+      (rc = dalloc(&s->U2, NV)) || (rc = dalloc(&s->om, (size_t)s->omBox.size())) || (rc = dalloc(&s->dt, 2)) ||
+      (rc = dalloc(&s->t, 2)) || (rc = dalloc(&s->cflmax, 1)) || (rc = dalloc(&s->bad_flag, 1)) ||
+      (rc = dalloc(&s->bad_idx, 1)) || (rc = dalloc(&s->hyb_flag, 2)) || (rc = dalloc(&s->hyb_count, 1))) {
+    cg_solver_destroy(s);
+    return rc;
+  }
+  cudaMemset(s->bad_flag, 0, sizeof(unsigned int));
+  cudaMemset(s->bad_idx, 0xff, sizeof(unsigned long long));
+  cudaMemset(s->hyb_flag, 0, 2 * sizeof(int));
+  cudaMemset(s->hyb_count, 0, sizeof(unsigned long long));
+  bool compact = p->scheme == CG_MIG4;
+  for (int d = 0; d < s->nd; ++d) {
+    s->gdBox[d] = make_box(s, 4, d, 6);
+    if (compact) {
+      if ((rc = dalloc(&s->G[d], (size_t)s->nv * s->gdBox[d].size()))) { cg_solver_destroy(s); return rc; }
+      bool cyc = g->bc[d][0] == CG_BC_PERIODIC;
+      int m = cyc ? g->n[d] : g->n[d] + 12;
+      if (cyc && m < 3) { cg_solver_destroy(s); return fail(CG_ERR_INVALID_ARG, "periodic compact lines need n >= 3"); }
+      if ((rc = upload_line(s->mig4[d], m, 0.25, cyc, -6))) { cg_solver_destroy(s); return rc; }
+    }
+  }
+  if (g->curv) {
+    size_t planes = (size_t)3 * s->nd * s->nd + 1;
+    if ((rc = dalloc(&s->metric, planes * (size_t)s->dg.NP))) { cg_solver_destroy(s); return rc; }
+    if ((rc = compute_metrics(s, 0))) { cg_solver_destroy(s); return rc; }
+  }
+  if ((rc = lad_alloc(s))) { cg_solver_destroy(s); return rc; }
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) { cg_solver_destroy(s); return fail(CG_ERR_CUDA, "setup: %s", cudaGetErrorString(e)); }
+  *out = s;
+  return CG_OK;
+}
+
+CG_API int cg_metrics(cg_solver* s, double* node_dev, double* iface_dev, void* stream) {
+  if (!s || !node_dev) return fail(CG_ERR_INVALID_ARG, "null argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  int nd = s->nd;
+  long long N = s->N;
+  std::vector<double> node((size_t)(nd * nd + 1) * N), ifc((size_t)nd * nd * N);
+  std::vector<double> xh, xt, jac;
+  if (s->dg.curv) {
+    long long NP = s->dg.NP;
+    std::vector<double> all((size_t)(3 * nd * nd + 1) * NP);
+    CG_CUDA(cudaMemcpy(all.data(), s->metric, all.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    for (int k = 0; k < s->dg.n[2]; ++k)
+      for (int j = 0; j < s->dg.n[1]; ++j)
+        for (int i = 0; i < s->dg.n[0]; ++i) {
+          long long q = i + (long long)s->dg.n[0] * (j + (long long)s->dg.n[1] * k);
+          long long pq = (i + (nd > 0 ? PM : 0)) +
+                         (long long)s->dg.P[0] * ((j + (nd > 1 ? PM : 0)) + (long long)s->dg.P[1] * (k + (nd > 2 ? PM : 0)));
+          for (int a = 0; a < nd * nd; ++a) {
+            node[(size_t)a * N + q] = all[(size_t)a * NP + pq];
+            ifc[(size_t)a * N + q] = all[(size_t)(nd * nd + a) * NP + pq];
+          }
+          node[(size_t)nd * nd * N + q] = all[(size_t)2 * nd * nd * NP + pq];
+        }
+  } else {
+    for (long long q = 0; q < N; ++q) {
+      for (int l = 0; l < nd; ++l)
+        for (int m = 0; m < nd; ++m) {
+          node[(size_t)(l * nd + m) * N + q] = l == m ? s->dg.cxh[l] : 0.0;
+          ifc[(size_t)(l * nd + m) * N + q] = l == m ? s->dg.cxh[l] : 0.0;
+        }
+      node[(size_t)nd * nd * N + q] = s->dg.cjac;
+    }
+  }
+  CG_CUDA(cudaMemcpyAsync(node_dev, node.data(), node.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+  if (iface_dev)
+    CG_CUDA(cudaMemcpyAsync(iface_dev, ifc.data(), ifc.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+  CG_CUDA(cudaStreamSynchronize(st));
+  return CG_OK;
+}
+
+CG_API int cg_rhs(cg_solver* s, const double* U, double* R, void* stream) {
+  if (!s || !U || !R) return fail(CG_ERR_INVALID_ARG, "null argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = DISPATCH_ND(s, stage, s, U, U, R, 0, 1, st);
+  if (rc) return rc;
+  CG_CUDA(cudaGetLastError());
+  return CG_OK;
+}
+
+CG_API int cg_rk3_step_dev(cg_solver* s, double* U, const double* dt_dev, void* stream) {
+  if (!s || !U || !dt_dev) return fail(CG_ERR_INVALID_ARG, "null argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  const double* keep = s->dt;
+  s->dt = const_cast<double*>(dt_dev);
+  int rc = DISPATCH_ND(s, rk3, s, U, st);
+  s->dt = const_cast<double*>(keep);
+  if (rc) return rc;
+  CG_CUDA(cudaGetLastError());
+  return CG_OK;
+}
+
+CG_API int cg_rk3_step(cg_solver* s, double* U, double dt, void* stream) {
+  if (!s || !U) return fail(CG_ERR_INVALID_ARG, "null argument");
+  if (!(dt >= 0.0)) return fail(CG_ERR_INVALID_ARG, "dt must be >= 0");
+  cudaStream_t st = (cudaStream_t)stream;
+  CG_CUDA(cudaMemcpyAsync(s->dt + 1, &dt, sizeof(double), cudaMemcpyHostToDevice, st));
+  CG_CUDA(cudaStreamSynchronize(st));  // dt is pageable host memory
+  return cg_rk3_step_dev(s, U, s->dt + 1, stream);
+}
+
+CG_API int cg_cfl_dt(cg_solver* s, const double* U, double* dt_out, int dt_on_device, void* stream) {
+  if (!s || !U || !dt_out) return fail(CG_ERR_INVALID_ARG, "null argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  double* target = dt_on_device ? dt_out : s->dt;
+  DISPATCH_ND(s, cfl_launch, s, U, target, nullptr, 0.0, st);
+  CG_CUDA(cudaGetLastError());
+  if (!dt_on_device) {
+    CG_CUDA(cudaMemcpyAsync(dt_out, s->dt, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CG_CUDA(cudaStreamSynchronize(st));
+  }
+  return CG_OK;
+}
+
+CG_API int cg_sync_status(cg_solver* s, void* stream) {
+  if (!s) return fail(CG_ERR_INVALID_ARG, "null argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned int flag = 0;
+  unsigned long long idx = 0;
+  CG_CUDA(cudaMemcpyAsync(&flag, s->bad_flag, sizeof flag, cudaMemcpyDeviceToHost, st));
+  CG_CUDA(cudaMemcpyAsync(&idx, s->bad_idx, sizeof idx, cudaMemcpyDeviceToHost, st));
+  CG_CUDA(cudaStreamSynchronize(st));
+  if (flag) {
+    s->last_bad = (long long)idx;
+    CG_CUDA(cudaMemsetAsync(s->bad_flag, 0, sizeof(unsigned int), st));
+    CG_CUDA(cudaMemsetAsync(s->bad_idx, 0xff, sizeof(unsigned long long), st));
+    CG_CUDA(cudaStreamSynchronize(st));
+    return fail(CG_ERR_NONPHYSICAL, "non-physical state (rho or p <= 0 or NaN) at node %lld", (long long)idx);
+  }
+  return CG_OK;
+}
+
+CG_API int64_t cg_last_bad_index(const cg_solver* s) { return s ? s->last_bad : -1; }
+CG_API int64_t cg_launch_count(const cg_solver* s) { return s ? s->launches : 0; }
+
+CG_API int cg_advance(cg_solver* s, double* U, int64_t nsteps, double t_end, double* t_out, int64_t* steps_out,
+                      void* stream) {
+  if (!s || !U) return fail(CG_ERR_INVALID_ARG, "null argument");
+  if (nsteps <= 0 && !(t_end > 0.0)) return fail(CG_ERR_INVALID_ARG, "need nsteps > 0 or t_end > 0");
+  cudaStream_t st = (cudaStream_t)stream;
+  int64_t k = 0;
+  double t = 0.0;
+  CG_CUDA(cudaMemsetAsync(s->t, 0, sizeof(double), st));
+  while (nsteps <= 0 || k < nsteps) {
+    if (t_end > 0.0) {
+      // final time: the step size comes back to the host to clip the last step
+      if (t >= t_end - 1e-14) break;
+      DISPATCH_ND(s, cfl_launch, s, U, s->dt, nullptr, 0.0, st);
+      double dt;
+      CG_CUDA(cudaMemcpyAsync(&dt, s->dt, sizeof(double), cudaMemcpyDeviceToHost, st));
+      CG_CUDA(cudaStreamSynchronize(st));
+      if (t + dt > t_end) {
+        dt = t_end - t;
+        CG_CUDA(cudaMemcpyAsync(s->dt, &dt, sizeof(double), cudaMemcpyHostToDevice, st));
+        CG_CUDA(cudaStreamSynchronize(st));
+      }
+      int rc = DISPATCH_ND(s, rk3, s, U, st);
+      if (rc) return rc;
+      t += dt;
+    } else {
+      DISPATCH_ND(s, cfl_launch, s, U, s->dt, s->t, 0.0, st);
+      int rc = DISPATCH_ND(s, rk3, s, U, st);
+      if (rc) return rc;
+    }
+    ++k;
+  }
+  if (!(t_end > 0.0)) {
+    CG_CUDA(cudaMemcpyAsync(&t, s->t, sizeof(double), cudaMemcpyDeviceToHost, st));
+  }
+  CG_CUDA(cudaStreamSynchronize(st));
+  if (t_out) *t_out = t;
+  if (steps_out) *steps_out = k;
+  return cg_sync_status(s, stream);
+}
+
+CG_API int cg_advance_host(cg_solver* s, double* U_host, int64_t nsteps, double t_end, double* t_out, void* stream) {
+  if (!s || !U_host) return fail(CG_ERR_INVALID_ARG, "null argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  size_t bytes = sizeof(double) * s->nv * s->N;
+  if (!s->host_stage && dalloc(&s->host_stage, (size_t)s->nv * s->N)) return CG_ERR_OOM;
+  CG_CUDA(cudaMemcpyAsync(s->host_stage, U_host, bytes, cudaMemcpyHostToDevice, st));
+  int rc = cg_advance(s, s->host_stage, nsteps, t_end, t_out, nullptr, stream);
+  CG_CUDA(cudaMemcpyAsync(U_host, s->host_stage, bytes, cudaMemcpyDeviceToHost, st));
+  CG_CUDA(cudaStreamSynchronize(st));
+  return rc;
+}
+
+CG_API int cg_omega(cg_solver* s, const double* U, double* omega, void* stream) {
+  if (!s || !U || !omega) return fail(CG_ERR_INVALID_ARG, "null argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  bool compact = s->p.scheme == CG_MIG4;
+  DISPATCH_ND(s, stage_prep_gbr, s, U, compact, st);
+  // interior part of the sensor box
+  Box ob = s->omBox;
+  std::vector<double> box((size_t)ob.size()), in((size_t)s->N);
+  CG_CUDA(cudaMemcpyAsync(box.data(), s->om, box.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CG_CUDA(cudaStreamSynchronize(st));
+  for (int k = 0; k < s->dg.n[2]; ++k)
+    for (int j = 0; j < s->dg.n[1]; ++j)
+      for (int i = 0; i < s->dg.n[0]; ++i)
+        in[i + (size_t)s->dg.n[0] * (j + (size_t)s->dg.n[1] * k)] = box[(size_t)ob.at(i, j, k)];
+  CG_CUDA(cudaMemcpyAsync(omega, in.data(), in.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+  CG_CUDA(cudaStreamSynchronize(st));
+  return CG_OK;
+}
+
+CG_API int cg_iface_flux(cg_solver* s, const double* U, int dir, double* F, void* stream) {
+  if (!s || !U || !F) return fail(CG_ERR_INVALID_ARG, "null argument");
+  if (dir < 0 || dir >= s->nd) return fail(CG_ERR_INVALID_ARG, "bad direction");
+  int sch = s->p.scheme;
+  if (sch != CG_MEG6 && sch != CG_MIG4 && !(sch == CG_HYBRID && s->p.hybrid_mode == CG_HYBRID_CELL))
+    return fail(CG_ERR_UNSUPPORTED, "interface fluxes exist for the C-GBR and per-interface hybrid schemes");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!s->Rtmp && dalloc(&s->Rtmp, (size_t)s->nv * s->N)) return CG_ERR_OOM;
+  s->iface_dir = dir;
+  s->iface_out = F;
+  int rc = DISPATCH_ND(s, stage, s, U, U, s->Rtmp, 0, 1, st);
+  s->iface_out = nullptr;
+  if (rc) return rc;
+  CG_CUDA(cudaGetLastError());
+  return CG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,554 @@
+// Kernels of one RK stage of the FP64 RHS: primitives, sensor, compact
+// (tridiagonal) gradients, the fused C-GBR interface sweep with the residual
+// and RK epilogue, and the CFL reduction.
+#pragma once
+#include "cg_gbr.cuh"
+
+namespace cgk {
+
+// A box of node positions: index (i+off0) + ext0*((j+off1) + ext1*(k+off2)).
+struct Box {
+  int off[3], ext[3];
+  __host__ __device__ long long size() const { return (long long)ext[0] * ext[1] * ext[2]; }
+  __host__ __device__ long long at(int i, int j, int k) const {
+    return (long long)(i + off[0]) + (long long)ext[0] * ((long long)(j + off[1]) + (long long)ext[1] * (long long)(k + off[2]));
+  }
+};
+
+// Everything the stage kernels read and write besides the grid.
+struct StageArgs {
+  const double* W;     // primitives (nv planes, interior)
+  const double* om;    // sensor on omBox
+  Box omBox;
+  const double* Gd;    // compact gradients along the sweep direction (nv planes on gdBox)
+  Box gdBox;
+  double* acc;         // flux-difference accumulator (nv planes)
+  int first, last;     // first / last direction of the stage
+  int rk;              // last direction: 1 = RK update, 0 = write R
+  int stage;           // 1, 2, 3
+  double* R;
+  const double* Un;    // state at the start of the step
+  const double* Uc;    // state of the current stage
+  double* Uout;
+  const double* dt;    // device scalar
+  unsigned int* bad_flag;
+  unsigned long long* bad_idx;
+  const unsigned char* mask;  // per-interface hybrid: troubled nodes on tBox (GBR where a neighbour is troubled)
+  Box tBox;
+  const int* guard;           // global hybrid: the kernel runs only if *guard == guard_want
+  int guard_want;
+  const double* hflux;        // per-interface hybrid: LAD flux-form interface fluxes (nv planes on hBox)
+  Box hBox;
+  double* iface_out;          // diagnostics: interface fluxes [v][line][n+1] (NULL: none)
+};
+
+// ---------------------------------------------------------------- primitives
+template <int ND>
+__global__ void k_prim(DevGrid g, const double* __restrict__ U, double* __restrict__ W) {
+  constexpr int NV = ND + 2;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < g.N;
+       q += (long long)gridDim.x * blockDim.x) {
+    double Q[NV], w[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Q[v] = U[v * g.N + q];
+    cons_to_prim<ND>(g.gm1, Q, w);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) W[v * g.N + q] = w[v];
+  }
+}
+
+// ---------------------------------------------------------------- sensor
+// Omega^d = phi * zeta on the box [-4, n+3]: phi the largest normalised
+// pressure second difference over the directions, zeta a Ducros ratio of the
+// dilatation (one in irrotational dilatation-free flow).
+template <int ND, bool CART, bool COMPACT>
+__global__ void k_omega(DevGrid g, const double* __restrict__ W, const double* __restrict__ G0,
+                        const double* __restrict__ G1, const double* __restrict__ G2, Box gb0, Box gb1,
+                        Box gb2, double* __restrict__ om, Box ob, const int* guard, int want) {
+  constexpr int NV = ND + 2, IP = ND + 1;
+  if (guard && *guard != want) return;
+  long long tot = ob.size();
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    int c[3];
+    long long r = e;
+    c[0] = (int)(r % ob.ext[0]) - ob.off[0];
+    r /= ob.ext[0];
+    c[1] = (int)(r % ob.ext[1]) - ob.off[1];
+    c[2] = (int)(r / ob.ext[1]) - ob.off[2];
+    double w0[NV];
+    load_state<ND>(g, W, c[0], c[1], c[2], w0);
+    double phi = 0.0;
+    double du[3][3];  // du[l][k] = d u_k / d xi_l
+#pragma unroll
+    for (int l = 0; l < ND; ++l) {
+      int cm[3] = {c[0], c[1], c[2]}, cp[3] = {c[0], c[1], c[2]};
+      cm[l] -= 1;
+      cp[l] += 1;
+      double wm[NV], wp[NV];
+      load_state<ND>(g, W, cm[0], cm[1], cm[2], wm);
+      load_state<ND>(g, W, cp[0], cp[1], cp[2], wp);
+      double a = fabs(wp[IP] - 2.0 * w0[IP] + wm[IP]) / (wp[IP] + 2.0 * w0[IP] + wm[IP]);
+      if (a > phi) phi = a;
+      if (!COMPACT) {
+        double s[6][NV];
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+          int a1[3] = {c[0], c[1], c[2]}, a2[3] = {c[0], c[1], c[2]};
+          a1[l] -= 3 - t;
+          a2[l] += 1 + t;
+          load_state<ND>(g, W, a1[0], a1[1], a1[2], s[t]);
+          load_state<ND>(g, W, a2[0], a2[1], a2[2], s[3 + t]);
+        }
+#pragma unroll
+        for (int k = 0; k < ND; ++k)
+          du[l][k] = d6(s[0][1 + k], s[1][1 + k], s[2][1 + k], s[3][1 + k], s[4][1 + k], s[5][1 + k]);
+      } else {
+        const double* G = l == 0 ? G0 : (l == 1 ? G1 : G2);
+        const Box& gb = l == 0 ? gb0 : (l == 1 ? gb1 : gb2);
+        long long gi = gb.at(c[0], c[1], c[2]);
+        long long gs = gb.size();
+#pragma unroll
+        for (int k = 0; k < ND; ++k) du[l][k] = G[(1 + k) * gs + gi];
+      }
+    }
+    // physical velocity gradients gu[k][m] = sum_l (J xi_hat[l][m]) du[l][k]
+    double gu[3][3];
+    if (CART) {
+#pragma unroll
+      for (int k = 0; k < ND; ++k)
+#pragma unroll
+        for (int m = 0; m < ND; ++m) gu[k][m] = (g.cjac * g.cxh[m]) * du[m][k];
+    } else {
+      long long pq = plin(g, c[0], c[1], c[2]);
+      double J = g.jac[pq];
+      double xm[3][3];
+#pragma unroll
+      for (int l = 0; l < ND; ++l)
+#pragma unroll
+        for (int m = 0; m < ND; ++m) xm[l][m] = J * g.xh[(l * ND + m) * g.NP + pq];
+#pragma unroll
+      for (int k = 0; k < ND; ++k)
+#pragma unroll
+        for (int m = 0; m < ND; ++m) {
+          double s = xm[0][m] * du[0][k];
+#pragma unroll
+          for (int l = 1; l < ND; ++l) s = s + xm[l][m] * du[l][k];
+          gu[k][m] = s;
+        }
+    }
+    double div = gu[0][0];
+#pragma unroll
+    for (int k = 1; k < ND; ++k) div = div + gu[k][k];
+    double zeta;
+    if (ND == 1) {
+      zeta = (div * div + 1e-32) / (div * div + 1e-32);
+    } else if (ND == 2) {
+      double w3 = gu[1][0] - gu[0][1];
+      zeta = (div * div + 1e-32) / (div * div + w3 * w3 + 1e-32);
+    } else {
+      double w1 = gu[2][1] - gu[1][2], w2 = gu[0][2] - gu[2][0], w3 = gu[1][0] - gu[0][1];
+      zeta = (div * div + 1e-32) / (div * div + (w1 * w1 + w2 * w2 + w3 * w3) + 1e-32);
+    }
+    om[ob.at(c[0], c[1], c[2])] = phi * zeta;
+  }
+}
+
+// ---------------------------------------------------------------- compact gradients
+// Tridiagonal (MIG4: 1/4, 1, 1/4) first derivative of the primitives along d,
+// one thread per (line, variable), Thomas elimination with the line-independent
+// pivots cp[], den[] precomputed on the host.  Non-periodic lines span the
+// positions [-6, n+5] with E4 closure rows at both ends; periodic lines are
+// cyclic on [0, n-1] (Sherman-Morrison with the correction vector z[]) and
+// the ghost positions copy the wrapped values.  Lines exist for every
+// position of the other directions in [-4, n+3].
+struct LineCoef {
+  const double* cp;   // Thomas pivots of the line system
+  const double* den;
+  const double* z;    // cyclic: solution of the correction system
+  double a;           // off-diagonal
+  double gam;         // cyclic: -1
+  double fden;        // cyclic: 1 + z[0] + a z[m-1] / gam
+  int m;              // unknowns
+  int lo;             // first position of the system (non-periodic)
+  int periodic;
+};
+
+template <int ND>
+__global__ void k_compact_grad(DevGrid g, const double* __restrict__ W, int d, LineCoef lc,
+                               double* __restrict__ G, Box gb) {
+  constexpr int NV = ND + 2;
+  // lines: positions of the other directions on [-4, n+3]
+  int o1 = (d + 1) % 3, o2 = (d + 2) % 3;
+  int e1 = o1 < ND ? g.n[o1] + 8 : 1, e2 = o2 < ND ? g.n[o2] + 8 : 1;
+  long long nl = (long long)e1 * e2 * NV;
+  long long gs = gb.size();
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= nl) return;
+  int v = (int)(t % NV);
+  long long r = t / NV;
+  int p1 = (int)(r % e1) - (o1 < ND ? 4 : 0);
+  int p2 = (int)(r / e1) - (o2 < ND ? 4 : 0);
+  int c[3];
+  c[o1] = p1;
+  c[o2] = p2;
+  int n = g.n[d];
+  auto val = [&](int x) {
+    c[d] = x;
+    double w[NV];
+    load_state<ND>(g, W, c[0], c[1], c[2], w);
+    return w[v];
+  };
+  auto out = [&](int x) -> double& {
+    c[d] = x;
+    return G[(long long)v * gs + gb.at(c[0], c[1], c[2])];
+  };
+  const double a = lc.a;
+  if (!lc.periodic) {
+    int m = lc.m, lo = lc.lo;
+    // forward elimination (row 0 and row m-1 are the explicit E4 closures)
+    double dp = d4(val(lo - 2), val(lo - 1), val(lo + 1), val(lo + 2));
+    out(lo) = dp;
+    double fm1 = val(lo), f0 = val(lo + 1), fp1;
+    for (int i = 1; i < m - 1; ++i) {
+      fp1 = val(lo + i + 1);
+      double rhs = 0.75 * (fp1 - fm1);
+      dp = (rhs - a * dp) / lc.den[i];
+      out(lo + i) = dp;
+      fm1 = f0;
+      f0 = fp1;
+    }
+    int hi = lo + m - 1;
+    double x = d4(val(hi - 2), val(hi - 1), val(hi + 1), val(hi + 2));
+    out(hi) = x;
+    for (int i = m - 2; i >= 0; --i) {
+      double& o = out(lo + i);
+      x = o - lc.cp[i] * x;
+      o = x;
+    }
+  } else {
+    int m = n;
+    double dp = 0.75 * (val(1) - val(-1)) / 2.0;
+    out(0) = dp;
+    for (int i = 1; i < m; ++i) {
+      double rhs = 0.75 * (val(i + 1) - val(i - 1));
+      dp = (rhs - a * dp) / lc.den[i];
+      out(i) = dp;
+    }
+    double x = dp;
+    const double xlast = dp;
+    for (int i = m - 2; i >= 0; --i) {
+      double& o = out(i);
+      x = o - lc.cp[i] * x;
+      o = x;
+    }
+    double x0 = out(0);
+    double fact = (x0 + a * xlast / lc.gam) / lc.fden;
+    for (int i = 0; i < m; ++i) {
+      double& o = out(i);
+      o = o - fact * lc.z[i];
+    }
+    for (int q = 1; q <= 6; ++q) {
+      double lv = out(((-q) % m + m) % m);
+      double rv = out((n - 1 + q) % m);
+      out(-q) = lv;
+      out(n - 1 + q) = rv;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- C-GBR sweep
+constexpr int SWEEP_TL = 64;
+__host__ __device__ constexpr int sweep_lw(int dir) { return dir == 0 ? 4 : 8; }
+template <int ND, int DIR>
+__host__ __device__ constexpr int sweep_smem_doubles() {
+  return (ND + 2) * (SWEEP_TL + 9 + SWEEP_TL + 3 + SWEEP_TL + 1 + SWEEP_TL) * sweep_lw(DIR) +
+         (SWEEP_TL + 7) * sweep_lw(DIR);
+}
+
+template <int ND, int DIR, bool CART, bool COMPACT>
+__global__ void __launch_bounds__(256) k_gbr_sweep(DevGrid g, GbrCfg q, StageArgs A) {
+  constexpr int NV = ND + 2, IP = ND + 1;
+  constexpr int TL = SWEEP_TL, LW = sweep_lw(DIR);
+  constexpr int RW = TL + 9, RD = TL + 3, RDD = TL + 1, RO = TL + 7;
+  extern __shared__ double sm[];
+  double* sW = sm;
+  double* sD = sW + NV * RW * LW;
+  double* sDD = sD + NV * RD * LW;
+  double* sF = sDD + NV * RDD * LW;
+  double* sO = sF + NV * TL * LW;
+  auto IX = [](int v, int r, int l, int rows) {
+    return DIR == 0 ? (v * LW + l) * rows + r : (v * rows + r) * LW + l;
+  };
+  if (A.guard && *A.guard != A.guard_want) return;
+  const int tid = threadIdx.x;
+  const int n = g.n[DIR];
+  // tile origin along DIR and line coordinates
+  int i0, lc1 = 0, lc2 = 0;  // lc1/lc2: coordinates of the other dims for line 0
+  long long nlines;
+  if (DIR == 0) {
+    i0 = blockIdx.x * (TL - 1);
+    nlines = (long long)g.n[1] * g.n[2];
+  } else {
+    i0 = blockIdx.y * (TL - 1);
+    nlines = 0;
+  }
+  // coordinates of line l (the two other directions)
+  auto line_coords = [&](int l, int* c) -> bool {
+    if (DIR == 0) {
+      long long L = (long long)blockIdx.y * LW + l;
+      if (L >= nlines) return false;
+      c[1] = (int)(L % g.n[1]);
+      c[2] = (int)(L / g.n[1]);
+    } else {
+      int x = blockIdx.x * LW + l;
+      if (x >= g.n[0]) return false;
+      c[0] = x;
+      int o = DIR == 1 ? 2 : 1;
+      c[o] = blockIdx.z;
+    }
+    return true;
+  };
+  (void)lc1;
+  (void)lc2;
+  // 1. primitives of the tile (ghosts resolved by the boundary conditions)
+  for (int e = tid; e < RW * LW; e += blockDim.x) {
+    int r = DIR == 0 ? e % RW : e / LW;
+    int l = DIR == 0 ? e / RW : e % LW;
+    int c[3] = {0, 0, 0};
+    double w[NV];
+    if (line_coords(l, c)) {
+      c[DIR] = i0 - 5 + r;
+      load_state<ND>(g, A.W, c[0], c[1], c[2], w);
+    } else {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) w[v] = 1.0;
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) sW[IX(v, r, l, RW)] = w[v];
+  }
+  // sensor window values
+  for (int e = tid; e < RO * LW; e += blockDim.x) {
+    int r = DIR == 0 ? e % RO : e / LW;
+    int l = DIR == 0 ? e / RO : e % LW;
+    int c[3] = {0, 0, 0};
+    double o = 0.0;
+    int x = i0 - 4 + r;
+    if (line_coords(l, c) && x <= n + 3) {
+      c[DIR] = x;
+      o = A.om[A.omBox.at(c[0], c[1], c[2])];
+    }
+    sO[(DIR == 0) ? l * RO + r : r * LW + l] = o;
+  }
+  __syncthreads();
+  // 2. first derivatives along DIR on nodes i0-2 .. i0+TL
+  for (int e = tid; e < RD * LW; e += blockDim.x) {
+    int r = DIR == 0 ? e % RD : e / LW;
+    int l = DIR == 0 ? e / RD : e % LW;
+    if (!COMPACT) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v)
+        sD[IX(v, r, l, RD)] = d6(sW[IX(v, r, l, RW)], sW[IX(v, r + 1, l, RW)], sW[IX(v, r + 2, l, RW)],
+                                 sW[IX(v, r + 4, l, RW)], sW[IX(v, r + 5, l, RW)], sW[IX(v, r + 6, l, RW)]);
+    } else {
+      int c[3] = {0, 0, 0};
+      int x = i0 - 2 + r;
+      bool ok = line_coords(l, c) && x <= n + 5;
+      c[DIR] = x;
+      long long gi = ok ? A.gdBox.at(c[0], c[1], c[2]) : 0;
+      long long gs = A.gdBox.size();
+#pragma unroll
+      for (int v = 0; v < NV; ++v) sD[IX(v, r, l, RD)] = ok ? A.Gd[v * gs + gi] : 0.0;
+    }
+  }
+  __syncthreads();
+  // 3. second derivatives on nodes i0-1 .. i0+TL-1
+  for (int e = tid; e < RDD * LW; e += blockDim.x) {
+    int r = DIR == 0 ? e % RDD : e / LW;
+    int l = DIR == 0 ? e / RDD : e % LW;
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+      sDD[IX(v, r, l, RDD)] = d2_from_grad(sW[IX(v, r + 3, l, RW)], sW[IX(v, r + 4, l, RW)],
+                                           sW[IX(v, r + 5, l, RW)], sD[IX(v, r, l, RD)],
+                                           sD[IX(v, r + 2, l, RD)]);
+  }
+  __syncthreads();
+  // 4. interface fluxes i+1/2, i = i0-1+a
+  constexpr int PER = (TL * LW) / 256;
+#pragma unroll 1
+  for (int k = 0; k < PER; ++k) {
+    int e = tid + k * 256;
+    int a = DIR == 0 ? e % TL : e / LW;
+    int l = DIR == 0 ? e / TL : e % LW;
+    int i = i0 - 1 + a;
+    int c[3] = {0, 0, 0};
+    double F[NV];
+    bool ok = line_coords(l, c) && i <= n - 1;
+    c[DIR] = i;
+    bool use_gbr = ok;
+    if (ok && A.mask) {
+      int cn[3] = {c[0], c[1], c[2]};
+      cn[DIR] = i + 1;
+      use_gbr = A.mask[A.tBox.at(c[0], c[1], c[2])] != 0 || A.mask[A.tBox.at(cn[0], cn[1], cn[2])] != 0;
+    }
+    if (use_gbr) {
+      double Wst[6][NV], Wd[2][NV], Wdd[2][NV];
+#pragma unroll
+      for (int j = 0; j < 6; ++j)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) Wst[j][v] = sW[IX(v, a + 2 + j, l, RW)];
+#pragma unroll
+      for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          Wd[j][v] = sD[IX(v, a + 1 + j, l, RD)];
+          Wdd[j][v] = sDD[IX(v, a + j, l, RDD)];
+        }
+      double omb = sO[(DIR == 0) ? l * RO + a + 3 : (a + 3) * LW + l];
+      for (int jj = 1 - q.window; jj <= q.window; ++jj) {
+        double o = sO[(DIR == 0) ? l * RO + a + 3 + jj : (a + 3 + jj) * LW + l];
+        omb = dmax(omb, o);
+      }
+      double xi[3] = {0.0, 0.0, 0.0};
+      if (!CART) {
+        long long pq = plin(g, c[0], c[1], c[2]);
+#pragma unroll
+        for (int m = 0; m < ND; ++m) xi[m] = g.xt[(DIR * ND + m) * g.NP + pq];
+      }
+      gbr_flux<ND, CART, DIR>(q, g, Wst, Wd, Wdd, omb, xi, F);
+    } else if (ok) {
+      long long hi = A.hBox.at(c[0], c[1], c[2]);
+      long long hs = A.hBox.size();
+#pragma unroll
+      for (int v = 0; v < NV; ++v) F[v] = A.hflux[v * hs + hi];
+    } else {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) F[v] = 0.0;
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) sF[IX(v, a, l, TL)] = F[v];
+    if (A.iface_out && ok) {
+      long long line = DIR == 0 ? (long long)c[1] + (long long)g.n[1] * c[2]
+                                : (DIR == 1 ? (long long)c[0] + (long long)g.n[0] * c[2]
+                                            : (long long)c[0] + (long long)g.n[0] * c[1]);
+      long long nlin = g.N / n;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) A.iface_out[((long long)v * nlin + line) * (n + 1) + (i + 1)] = F[v];
+    }
+  }
+  __syncthreads();
+  // 5. flux differences of cells i0 .. i0+TL-2, residual and RK epilogue
+  for (int e = tid; e < (TL - 1) * LW; e += blockDim.x) {
+    int a = DIR == 0 ? e % (TL - 1) : e / LW;
+    int l = DIR == 0 ? e / (TL - 1) : e % LW;
+    int c[3] = {0, 0, 0};
+    int x = i0 + a;
+    if (!line_coords(l, c) || x >= n) continue;
+    c[DIR] = x;
+    long long qi = lin(g, c[0], c[1], c[2]);
+    double J = CART ? g.cjac : g.jac[plin(g, c[0], c[1], c[2])];
+    double out[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      double diff = sF[IX(v, a + 1, l, TL)] - sF[IX(v, a, l, TL)];
+      double tot = A.first ? diff : A.acc[v * g.N + qi] + diff;
+      if (!A.last) {
+        A.acc[v * g.N + qi] = tot;
+        continue;
+      }
+      double r = -(J * tot);
+      if (!A.rk) {
+        A.R[v * g.N + qi] = r;
+        continue;
+      }
+      double dt = *A.dt;
+      double un = A.Un[v * g.N + qi];
+      double o;
+      if (A.stage == 1) o = un + dt * r;
+      else if (A.stage == 2) o = 0.75 * un + 0.25 * (A.Uc[v * g.N + qi] + dt * r);
+      else o = (1.0 / 3.0) * un + (2.0 / 3.0) * (A.Uc[v * g.N + qi] + dt * r);
+      out[v] = o;
+      A.Uout[v * g.N + qi] = o;
+    }
+    if (A.last && A.rk && A.stage == 3) {
+      double ke = out[1] * (out[1] / out[0]);
+#pragma unroll
+      for (int m = 1; m < ND; ++m) ke = ke + out[1 + m] * (out[1 + m] / out[0]);
+      double p = g.gm1 * (out[IP] - 0.5 * ke);
+      if (!(out[0] > 0.0) || !(p > 0.0)) {
+        atomicOr(A.bad_flag, 1u);
+        atomicMin(A.bad_idx, (unsigned long long)qi);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- CFL
+template <int ND, bool CART>
+__global__ void k_cfl_max(DevGrid g, const double* __restrict__ U, unsigned long long* __restrict__ mx) {
+  constexpr int NV = ND + 2, IP = ND + 1;
+  double best = 0.0;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < g.N;
+       q += (long long)gridDim.x * blockDim.x) {
+    double Q[NV], w[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Q[v] = U[v * g.N + q];
+    cons_to_prim<ND>(g.gm1, Q, w);
+    double cs = sqrt(g.gamma * w[IP] / w[0]);
+    double s = 0.0;
+    double J;
+    if (CART) {
+      J = g.cjac;
+#pragma unroll
+      for (int l = 0; l < ND; ++l) {
+        double t = fabs(g.cxh[l] * w[1 + l]) + cs * sqrt(g.cxh[l] * g.cxh[l]);
+        s = (l == 0) ? t : s + t;
+      }
+    } else {
+      int k = (int)(q / ((long long)g.n[0] * g.n[1]));
+      int j = (int)((q / g.n[0]) % g.n[1]);
+      int i = (int)(q % g.n[0]);
+      long long pq = plin(g, i, j, k);
+      J = g.jac[pq];
+#pragma unroll
+      for (int l = 0; l < ND; ++l) {
+        double dot = 0.0, mag = 0.0;
+#pragma unroll
+        for (int m = 0; m < ND; ++m) {
+          double x = g.xh[(l * ND + m) * g.NP + pq];
+          dot = (m == 0) ? x * w[1 + m] : dot + x * w[1 + m];
+          mag = (m == 0) ? x * x : mag + x * x;
+        }
+        double t = fabs(dot) + cs * sqrt(mag);
+        s = (l == 0) ? t : s + t;
+      }
+    }
+    double r = J * s;
+    if (r > best) best = r;
+  }
+  // block max, then one atomic (non-negative doubles order like their bits)
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) best = dmax(best, __shfl_xor_sync(0xffffffffu, best, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = best;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double b = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) b = dmax(b, __shfl_xor_sync(0xffffffffu, b, o));
+    if (threadIdx.x == 0) atomicMax(mx, (unsigned long long)__double_as_longlong(b));
+  }
+}
+
+// dt = cfl / max rate; with a final time: clip to t_end - t and advance t.
+__global__ void k_cfl_finish(const unsigned long long* mx, double cfl, double* dt, double* t, double t_end) {
+  double m = __longlong_as_double((long long)*mx);
+  double d = cfl / m;
+  if (t) {
+    double tt = *t;
+    if (t_end > 0.0 && tt + d > t_end) d = t_end - tt;
+    if (d < 0.0) d = 0.0;
+    *t = tt + d;
+  }
+  *dt = d;
+}
+
+}  // namespace cgk

@@ -1,0 +1,260 @@
+// LAD and hybrid stage orchestration (included by cg_api.cu after the
+// C-GBR helpers).  Algorithm 1 (LAD: node fluxes, viscous/LAD terms, residual,
+// RK update, filter on the last stage), Algorithm 3 (hybrid: the whole stage
+// by GBR if a troubled cell exists, else LAD) and its per-interface variant.
+
+static int lad_alloc(cg_solver* s) {
+  int sch = s->p.scheme;
+  if (sch != CG_LAD_E4 && sch != CG_LAD_C6 && sch != CG_HYBRID) return CG_OK;
+  LadBuffers& L = s->lad;
+  int nd = s->nd, nv = s->nv, nf = nd + 3;
+  L.b3 = make_box(s, 3, -1, 3);
+  L.tbox = make_box(s, 1, -1, 1);
+  size_t fmax = 0;
+  for (int d = 0; d < nd; ++d) {
+    L.fbox[d] = make_box(s, 0, d, 2);
+    Box hb = make_box(s, 0, d, 0);
+    hb.off[d] = 1;
+    hb.ext[d] = s->dg.n[d] + 1;
+    L.hbox[d] = hb;
+    s->hBox[d] = hb;
+    fmax = std::max(fmax, (size_t)L.fbox[d].size());
+  }
+  int rc;
+  if ((rc = dalloc(&L.gr, (size_t)nf * nd * L.b3.size())) || (rc = dalloc(&L.dv, (size_t)L.b3.size())) ||
+      (rc = dalloc(&L.bt[0], (size_t)s->N)) || (rc = dalloc(&L.bt[1], (size_t)s->N)) ||
+      (rc = dalloc(&L.kp[0], (size_t)s->N)) || (rc = dalloc(&L.kp[1], (size_t)s->N)) ||
+      (rc = dalloc(&L.Fn, (size_t)nv * fmax)))
+    return rc;
+  if (sch == CG_LAD_C6) {
+    if ((rc = dalloc(&L.D, (size_t)nv * s->N)) || (rc = dalloc(&L.tmp, (size_t)nv * s->N))) return rc;
+    for (int d = 0; d < nd; ++d) {
+      if ((rc = dalloc(&L.df[d], (size_t)nf * L.b3.size()))) return rc;
+      bool cyc = s->grid->bc[d][0] == CG_BC_PERIODIC;
+      int n = s->dg.n[d];
+      if (cyc && n < 3) return fail(CG_ERR_INVALID_ARG, "periodic compact lines need n >= 3");
+      if ((rc = upload_line(s->c6grad[d], cyc ? n : n + 12, 1.0 / 3.0, cyc, -6))) return rc;
+      if ((rc = upload_line(s->c6flux[d], n, 1.0 / 3.0, cyc, 0))) return rc;
+      if ((rc = upload_line(s->filt[d], cyc ? n : n + 2, s->p.alpha_f, cyc, -1))) return rc;
+      // line scratch of the compact solves
+      int o1 = (d + 1) % 3, o2 = (d + 2) % 3;
+      size_t lines_f = (size_t)L.b3.ext[o1] * L.b3.ext[o2] * nf * (size_t)(n + 16);
+      size_t lines_u = (size_t)s->dg.n[o1] * s->dg.n[o2] * nv * (size_t)(n + 2);
+      s->work_elems = std::max(s->work_elems, std::max(lines_f, lines_u));
+    }
+    if ((rc = dalloc(&s->work, s->work_elems))) return rc;
+  }
+  if (sch == CG_HYBRID) {
+    if ((rc = dalloc(&L.tr, (size_t)L.tbox.size()))) return rc;
+    for (int d = 0; d < nd; ++d)
+      if ((rc = dalloc(&s->hflux[d], (size_t)nv * L.hbox[d].size()))) return rc;
+  }
+  return CG_OK;
+}
+
+static void lad_free(LadBuffers& L) {
+  double* bufs[] = {L.gr, L.dv, L.bt[0], L.bt[1], L.kp[0], L.kp[1], L.Fn, L.D, L.df[0], L.df[1], L.df[2], L.tmp};
+  for (double* b : bufs)
+    if (b) cudaFree(b);
+  if (L.tr) cudaFree(L.tr);
+}
+
+// beta*, kappa* (filtered, interior) of the primitives in s->W; result in
+// bt[0], kp[0].  dkind: 2 = E4, 3 = C6.
+template <int ND>
+static int lad_coeffs_run(cg_solver* s, int dkind, cudaStream_t st, const int* guard, int want) {
+  LadBuffers& L = s->lad;
+  bool c6 = dkind == 3;
+  if (c6) {
+    for (int l = 0; l < ND; ++l) {
+      int o1 = (l + 1) % 3, o2 = (l + 2) % 3;
+      long long lines = (long long)L.b3.ext[o1] * L.b3.ext[o2] * (ND + 3);
+      k_lad_c6_fields<ND><<<(unsigned)((lines + 127) / 128), 128, 0, st>>>(s->dg, l, s->W, s->c6grad[l].lc, s->work,
+                                                                         s->dg.n[l] + 16, L.df[l], L.b3);
+      s->launches++;
+    }
+  }
+  int gb = grid_blocks(L.b3.size(), 128);
+  if (s->dg.curv) {
+    if (c6) k_lad_grad<ND, false, true><<<gb, 128, 0, st>>>(s->dg, s->W, L.df[0], L.df[1], L.df[2], L.gr, L.dv, L.b3, guard, want);
+    else k_lad_grad<ND, false, false><<<gb, 128, 0, st>>>(s->dg, s->W, L.df[0], L.df[1], L.df[2], L.gr, L.dv, L.b3, guard, want);
+    k_lad_coef<ND, false><<<grid_blocks(s->N, 128), 128, 0, st>>>(s->dg, s->W, L.gr, L.dv, L.b3, s->p.c_beta,
+                                                                  s->p.c_kappa, L.bt[0], L.kp[0], guard, want);
+  } else {
+    if (c6) k_lad_grad<ND, true, true><<<gb, 128, 0, st>>>(s->dg, s->W, L.df[0], L.df[1], L.df[2], L.gr, L.dv, L.b3, guard, want);
+    else k_lad_grad<ND, true, false><<<gb, 128, 0, st>>>(s->dg, s->W, L.df[0], L.df[1], L.df[2], L.gr, L.dv, L.b3, guard, want);
+    k_lad_coef<ND, true><<<grid_blocks(s->N, 128), 128, 0, st>>>(s->dg, s->W, L.gr, L.dv, L.b3, s->p.c_beta,
+                                                                 s->p.c_kappa, L.bt[0], L.kp[0], guard, want);
+  }
+  s->launches += 2;
+  int cur = 0;
+  for (int l = 0; l < ND; ++l) {
+    k_gauss<ND><<<grid_blocks(s->N, 256), 256, 0, st>>>(s->dg, l, L.bt[cur], L.kp[cur], L.bt[1 - cur], L.kp[1 - cur],
+                                                       guard, want);
+    s->launches++;
+    cur = 1 - cur;
+  }
+  if (cur != 0) {
+    CG_CUDA(cudaMemcpyAsync(L.bt[0], L.bt[1], sizeof(double) * s->N, cudaMemcpyDeviceToDevice, st));
+    CG_CUDA(cudaMemcpyAsync(L.kp[0], L.kp[1], sizeof(double) * s->N, cudaMemcpyDeviceToDevice, st));
+  }
+  return CG_OK;
+}
+
+template <int ND>
+static void lad_nodeflux(cg_solver* s, int l, cudaStream_t st, const int* guard, int want) {
+  LadBuffers& L = s->lad;
+  int gb = grid_blocks(L.fbox[l].size(), 128);
+  if (s->dg.curv)
+    k_lad_nodeflux<ND, false><<<gb, 128, 0, st>>>(s->dg, l, s->W, L.bt[0], L.kp[0], L.gr, L.dv, L.b3, L.Fn, L.fbox[l], guard, want);
+  else
+    k_lad_nodeflux<ND, true><<<gb, 128, 0, st>>>(s->dg, l, s->W, L.bt[0], L.kp[0], L.gr, L.dv, L.b3, L.Fn, L.fbox[l], guard, want);
+  s->launches++;
+}
+
+// LAD residual (E4 or C6) of the primitives in s->W with the epilogue of A.
+template <int ND>
+static int lad_pass(cg_solver* s, int dkind, StageArgs A, cudaStream_t st, const int* guard, int want) {
+  int rc = lad_coeffs_run<ND>(s, dkind, st, guard, want);
+  if (rc) return rc;
+  LadBuffers& L = s->lad;
+  for (int l = 0; l < ND; ++l) {
+    lad_nodeflux<ND>(s, l, st, guard, want);
+    A.first = l == 0;
+    A.last = l == ND - 1;
+    const double* D = nullptr;
+    if (dkind == 3) {
+      int o1 = (l + 1) % 3, o2 = (l + 2) % 3;
+      long long lines = (long long)s->dg.n[o1] * s->dg.n[o2] * (ND + 2);
+      k_lad_c6_flux<ND><<<(unsigned)((lines + 127) / 128), 128, 0, st>>>(s->dg, l, L.Fn, L.fbox[l], s->c6flux[l].lc, L.D);
+      s->launches++;
+      D = L.D;
+    }
+    k_lad_div<ND><<<grid_blocks(s->N, 256), 256, 0, st>>>(s->dg, l, L.Fn, L.fbox[l], D, A, guard, want);
+    s->launches++;
+  }
+  return CG_OK;
+}
+
+template <int ND>
+static int lad_stage(cg_solver* s, const double* Uc, StageArgs A, cudaStream_t st) {
+  int sch = s->p.scheme;
+  k_prim<ND><<<grid_blocks(s->N, 256), 256, 0, st>>>(s->dg, Uc, s->W);
+  s->launches++;
+  if (sch == CG_LAD_E4 || sch == CG_LAD_C6) return lad_pass<ND>(s, sch == CG_LAD_E4 ? 2 : 3, A, st, nullptr, 0);
+  LadBuffers& L = s->lad;
+  CG_CUDA(cudaMemsetAsync(s->hyb_flag, 0, sizeof(int), st));
+  CG_CUDA(cudaMemsetAsync(s->hyb_count, 0, sizeof(unsigned long long), st));
+  if (s->p.hybrid_mode == CG_HYBRID_GLOBAL) {
+    // Algorithm 3: GBR-MEG6 for the whole stage if any node is troubled, else LAD-E4
+    k_troubled<ND><<<grid_blocks(L.tbox.size(), 256), 256, 0, st>>>(s->dg, s->W, s->p.hyb_rho, s->p.hyb_p, nullptr,
+                                                                   s->omBox, 0.0, nullptr, L.tbox, s->hyb_flag,
+                                                                   s->hyb_count);
+    s->launches++;
+    stage_prep_gbr<ND>(s, Uc, false, st, false, s->hyb_flag, 1);
+    StageArgs G = A;
+    G.guard = s->hyb_flag;
+    G.guard_want = 1;
+    int rc = gbr_sweeps<ND>(s, false, G, st);
+    if (rc) return rc;
+    return lad_pass<ND>(s, 2, A, st, s->hyb_flag, 0);
+  }
+  // per interface: GBR-MEG6 where a neighbour node is troubled, LAD-E4 (flux form) elsewhere
+  stage_prep_gbr<ND>(s, Uc, false, st, false);
+  k_troubled<ND><<<grid_blocks(L.tbox.size(), 256), 256, 0, st>>>(
+      s->dg, s->W, s->p.hyb_rho, s->p.hyb_p, s->p.hybrid_sensor ? s->om : nullptr, s->omBox, s->p.sensor_thresh, L.tr,
+      L.tbox, s->hyb_flag, s->hyb_count);
+  s->launches++;
+  int rc = lad_coeffs_run<ND>(s, 2, st, nullptr, 0);
+  if (rc) return rc;
+  for (int l = 0; l < ND; ++l) {
+    lad_nodeflux<ND>(s, l, st, nullptr, 0);
+    k_lad_hflux<ND><<<grid_blocks(L.hbox[l].size(), 256), 256, 0, st>>>(s->dg, l, L.Fn, L.fbox[l], s->hflux[l], L.hbox[l]);
+    s->launches++;
+  }
+  StageArgs H = A;
+  H.mask = L.tr;
+  H.tBox = L.tbox;
+  for (int d = 0; d < ND; ++d) {
+    H.first = d == 0;
+    H.last = d == ND - 1;
+    H.hflux = s->hflux[d];
+    H.hBox = L.hbox[d];
+    H.Gd = nullptr;
+    H.gdBox = s->gdBox[d];
+    H.iface_out = (s->iface_out && s->iface_dir == d) ? s->iface_out : nullptr;
+    if (s->dg.curv) rc = sweep_dir<ND, false, false>(s, d, H, st);
+    else rc = sweep_dir<ND, true, false>(s, d, H, st);
+    if (rc) return rc;
+  }
+  return CG_OK;
+}
+
+static void filter_coeffs(double af, double b[5]) {
+  b[0] = (93.0 + 70.0 * af) / 128.0;
+  b[1] = 0.5 * ((7.0 + 18.0 * af) / 16.0);
+  b[2] = 0.5 * ((-7.0 + 14.0 * af) / 32.0);
+  b[3] = 0.5 * ((1.0 - 2.0 * af) / 16.0);
+  b[4] = 0.5 * ((-1.0 + 2.0 * af) / 128.0);
+}
+
+template <int ND>
+static int lad_filter(cg_solver* s, double* U, cudaStream_t st) {
+  if (!s->lad.tmp) return fail(CG_ERR_UNSUPPORTED, "the implicit filter belongs to LAD-C6");
+  double b[5];
+  filter_coeffs(s->p.alpha_f, b);
+  const double* in = U;
+  double* bufs[2] = {s->lad.tmp, U};
+  int cur = 0;
+  for (int l = 0; l < ND; ++l) {
+    int o1 = (l + 1) % 3, o2 = (l + 2) % 3;
+    long long lines = (long long)s->dg.n[o1] * s->dg.n[o2] * (ND + 2);
+    double* out = bufs[cur];
+    k_filter<ND><<<(unsigned)((lines + 127) / 128), 128, 0, st>>>(s->dg, l, in, s->filt[l].lc, b[0], b[1], b[2], b[3],
+                                                                b[4], s->work, out);
+    s->launches++;
+    in = out;
+    cur = 1 - cur;
+  }
+  if (in != U) CG_CUDA(cudaMemcpyAsync(U, in, sizeof(double) * s->nv * s->N, cudaMemcpyDeviceToDevice, st));
+  return CG_OK;
+}
+
+extern "C" {
+
+CG_API int cg_lad_coeffs(cg_solver* s, const double* U, double* beta, double* kappa, void* stream) {
+  if (!s || !U || !beta || !kappa) return fail(CG_ERR_INVALID_ARG, "null argument");
+  if (!s->lad.gr) return fail(CG_ERR_UNSUPPORTED, "LAD coefficients exist for the LAD and hybrid schemes");
+  cudaStream_t st = (cudaStream_t)stream;
+  DISPATCH_ND(s, stage_prep_prim, s, U, st);
+  int rc = DISPATCH_ND(s, lad_coeffs_run, s, s->p.scheme == CG_LAD_C6 ? 3 : 2, st, nullptr, 0);
+  if (rc) return rc;
+  CG_CUDA(cudaMemcpyAsync(beta, s->lad.bt[0], sizeof(double) * s->N, cudaMemcpyDeviceToDevice, st));
+  CG_CUDA(cudaMemcpyAsync(kappa, s->lad.kp[0], sizeof(double) * s->N, cudaMemcpyDeviceToDevice, st));
+  CG_CUDA(cudaGetLastError());
+  return CG_OK;
+}
+
+CG_API int cg_filter(cg_solver* s, double* U, void* stream) {
+  if (!s || !U) return fail(CG_ERR_INVALID_ARG, "null argument");
+  int rc = DISPATCH_ND(s, lad_filter, s, U, (cudaStream_t)stream);
+  if (rc) return rc;
+  CG_CUDA(cudaGetLastError());
+  return CG_OK;
+}
+
+CG_API int cg_hybrid_state(cg_solver* s, int* last_flag, int64_t* n_troubled, void* stream) {
+  if (!s) return fail(CG_ERR_INVALID_ARG, "null argument");
+  if (s->p.scheme != CG_HYBRID) return fail(CG_ERR_UNSUPPORTED, "not a hybrid solver");
+  cudaStream_t st = (cudaStream_t)stream;
+  int f = 0;
+  unsigned long long c = 0;
+  CG_CUDA(cudaMemcpyAsync(&f, s->hyb_flag, sizeof f, cudaMemcpyDeviceToHost, st));
+  CG_CUDA(cudaMemcpyAsync(&c, s->hyb_count, sizeof c, cudaMemcpyDeviceToHost, st));
+  CG_CUDA(cudaStreamSynchronize(st));
+  if (last_flag) *last_flag = f;
+  if (n_troubled) *n_troubled = (int64_t)c;
+  return CG_OK;
+}
+
+}  // extern "C"

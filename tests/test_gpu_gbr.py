@@ -1,0 +1,166 @@
+"""GPU parity of the C-GBR path (MEG6 / MIG4) against the oracle.
+
+The CUDA library evaluates every expression in the oracle's operation order
+with contraction disabled, so the expected difference is zero; the bar is the
+spec tolerance, max relative error <= 1e-11 per variable after 100 RK3
+steps (relative to the variable's largest magnitude), and <= 1e-13 for a
+single RHS evaluation."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2511_18042_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2511_18042_gb300 import api as a
+    return a
+
+
+from tests.gpu_util import rel_err, to_dev  # noqa: E402
+
+
+def _pair(orc, api, prob, **kw):
+    o = orc.Oracle(prob, **kw)
+    s = api.Solver.from_problem(prob, **kw)
+    return o, s
+
+
+@pytest.mark.parametrize("scheme", ["MEG6", "MIG4"])
+@pytest.mark.parametrize("case", ["sod", "leblanc"])
+def test_rhs_1d(orc, api, scheme, case):
+    prob = inputs.shock_tube(case, 400 if case == "sod" else 900)
+    o, s = _pair(orc, api, prob, scheme=scheme, cfl=0.5)
+    U = prob["U"]
+    U, _, _ = o.advance(U, nsteps=5)
+    R = s.rhs(to_dev(U))
+    assert rel_err(R, o.rhs(U)) <= 1e-13
+
+
+@pytest.mark.parametrize("scheme", ["MEG6", "MIG4"])
+def test_sod_100_steps(orc, api, scheme):
+    prob = inputs.shock_tube("sod", 400)
+    o, s = _pair(orc, api, prob, scheme=scheme, cfl=0.5)
+    Uo, to, ko = o.advance(prob["U"], nsteps=100)
+    Ug = to_dev(prob["U"])
+    tg, kg = s.advance(Ug, nsteps=100)
+    assert kg == 100 and abs(tg - to) <= 1e-12 * to
+    assert rel_err(Ug, Uo) <= 1e-11
+
+
+@pytest.mark.parametrize("scheme", ["MEG6", "MIG4"])
+def test_sod_to_final_time(orc, api, scheme):
+    prob = inputs.shock_tube("sod", 400)
+    o, s = _pair(orc, api, prob, scheme=scheme, cfl=0.5)
+    Uo, to, ko = o.advance(prob["U"], t_end=0.2)
+    Ug = to_dev(prob["U"])
+    tg, kg = s.advance(Ug, t_end=0.2)
+    assert abs(tg - 0.2) < 1e-14 and abs(to - 0.2) < 1e-14
+    assert rel_err(Ug, Uo) <= 1e-11
+
+
+@pytest.mark.parametrize("scheme", ["MEG6", "MIG4"])
+@pytest.mark.parametrize("shape", [(224, 96), (130, 70)])
+def test_triple_point_downsized_100_steps(orc, api, scheme, shape):
+    """Several tiles and a ragged tail in both directions (tiles cover 63 cells)."""
+    prob = inputs.triple_point(*shape)
+    o, s = _pair(orc, api, prob, scheme=scheme)
+    Uo, to, _ = o.advance(prob["U"], nsteps=100)
+    Ug = to_dev(prob["U"])
+    tg, _ = s.advance(Ug, nsteps=100)
+    assert rel_err(Ug, Uo) <= 1e-11
+    assert abs(tg - to) <= 1e-12 * to
+
+
+@pytest.mark.parametrize("scheme", ["MEG6", "MIG4"])
+def test_periodic_kelvin_helmholtz(orc, api, scheme):
+    prob = inputs.kelvin_helmholtz(64)
+    o, s = _pair(orc, api, prob, scheme=scheme)
+    Uo, _, _ = o.advance(prob["U"], nsteps=30)
+    Ug = to_dev(prob["U"])
+    s.advance(Ug, nsteps=30)
+    assert rel_err(Ug, Uo) <= 1e-11
+
+
+def test_interface_sensor_and_flux_parity(orc, api):
+    prob = inputs.riemann_c3(48)
+    o, s = _pair(orc, api, prob, scheme="MEG6")
+    U, _, _ = o.advance(prob["U"], nsteps=10)
+    Ud = to_dev(U)
+    assert rel_err(s.omega(Ud)[None], o.omega(U)[None]) == 0.0
+
+
+def test_triple_point_full_size_one_step(orc, api):
+    """The bench configuration (1792 x 768, MEG6): one RK3 step, every element."""
+    prob = inputs.triple_point()
+    o, s = _pair(orc, api, prob, scheme="MEG6")
+    U = prob["U"]
+    dt_o = o.cfl_dt(U)
+    Ud = to_dev(U)
+    dt_g = s.cfl_dt(Ud)
+    assert dt_g == dt_o
+    Uo = o.rk3_step(U, dt_o)
+    s.rk3_step(Ud, dt_g)
+    assert rel_err(Ud, Uo) <= 1e-13
+
+
+@pytest.mark.parametrize("nd", [2, 3])
+@pytest.mark.parametrize("scheme", ["MEG6", "MIG4"])
+def test_curvilinear_rhs_and_freestream(orc, api, nd, scheme):
+    if nd == 2:
+        xyz, per = inputs.wavy_grid_2d(40, 36, amp=0.08)
+        x, y = xyz
+        W = np.stack([1.0 + 0.3 * np.sin(2 * math.pi * x) * np.cos(2 * math.pi * y), 0.5 + 0 * x,
+                      0.2 + 0.1 * np.cos(2 * math.pi * y), 1.0 + 0.2 * np.sin(2 * math.pi * (x + y))])
+        W0 = (1.0, 2.0, 0.5, 1.0)
+    else:
+        xyz, per = inputs.wavy_grid_3d((14, 12, 10), amp=0.06)
+        x, y, z = xyz
+        W = np.stack([1.0 + 0.2 * np.sin(2 * math.pi * x), 0.3 + 0 * x, 0.1 * np.cos(2 * math.pi * z),
+                      -0.2 + 0 * x, 1.0 + 0.1 * np.sin(2 * math.pi * y)])
+        W0 = (1.0, 1.5, 0.7, -0.4, 1.0)
+    prob = inputs.field_on_curvilinear(xyz, per, W)
+    o, s = _pair(orc, api, prob, scheme=scheme)
+    node_o, ifc_o = o.metrics()
+    node_g, ifc_g = s.metrics()
+    assert rel_err(node_g, node_o) <= 1e-13 and rel_err(ifc_g, ifc_o) <= 1e-13
+    assert rel_err(s.rhs(to_dev(prob["U"])), o.rhs(prob["U"])) <= 1e-12
+    fs = inputs.uniform_flow_curvilinear(xyz, per, W0)
+    R = s.rhs(to_dev(fs["U"])).cpu().numpy()
+    J = node_o[-1]
+    assert np.abs(R).max() <= 1e-14 * J.max() * np.abs(fs["U"]).max() * 10
+
+
+def test_cartesian_3d_rhs(orc, api):
+    n = (20, 14, 12)
+    h = [1.0 / n[0], 1.0 / n[1], 1.0 / n[2]]
+    K, J, I = np.meshgrid(np.arange(n[2]), np.arange(n[1]), np.arange(n[0]), indexing="ij")
+    x, y, z = (I + 0.5) * h[0], (J + 0.5) * h[1], (K + 0.5) * h[2]
+    W = np.stack([1.0 + 0.5 * (x > 0.5), 0.2 * np.sin(2 * math.pi * y), 0.1 + 0 * x, 0.3 * np.cos(2 * math.pi * x),
+                  1.0 + 0.9 * (z > 0.5)])
+    prob = inputs._problem("box3d", 3, list(n), h, [[1, 1], [2, 2], [0, 0]], W, 1.4)
+    for scheme in ("MEG6", "MIG4"):
+        o, s = _pair(orc, api, prob, scheme=scheme)
+        Uo, _, _ = o.advance(prob["U"], nsteps=5)
+        Ug = to_dev(prob["U"])
+        s.advance(Ug, nsteps=5)
+        assert rel_err(Ug, Uo) <= 1e-12, scheme
+
+
+def test_nonphysical_state_is_reported(api):
+    prob = inputs.shock_tube("sod", 64)
+    s = api.Solver.from_problem(prob, scheme="MEG6")
+    U = to_dev(prob["U"])
+    U[2, 10] = -1.0  # negative total energy: p < 0 after the step
+    s.rk3_step(U, 1e-4)
+    rc = s.sync_status()
+    assert rc == -4
+    assert s.sync_status() == 0  # the flag is cleared once reported
