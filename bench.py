@@ -1,0 +1,344 @@
+"""Benchmark: cell-updates/s of the FP64 RHS + TVD-RK3 on the triple-point
+problem (1792 x 768, gamma 1.4, reflective walls), one RK3 step (with its CFL
+time step) of every scheme per bench step.
+
+  python bench.py --gpus N --steps K --warmup W [--impl reference]
+
+One bench step = for each scheme in {MEG6, MIG4, LAD_E4, LAD_C6, HYBRID global,
+HYBRID per interface}: restore the scheme's state from a fixed developed
+triple-point state (device copy), CFL dt, one RK3 step.  The developed state is
+the initial condition advanced 200 MEG6 steps on the GPU before timing, so
+every timed step sees the same flow.  value = cells x schemes x steps / time.
+N > 1: every rank runs the same workload on its own GPU (independent
+replicas, no exchange); value sums over ranks with the max-over-ranks time.
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload (one RK3 step of each scheme on the triple point at 448 x 192).
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NX, NY = 1792, 768
+SCHEMES = [
+    ("MEG6", dict(scheme="MEG6")),
+    ("MIG4", dict(scheme="MIG4")),
+    ("LAD_E4", dict(scheme="LAD_E4")),
+    ("LAD_C6", dict(scheme="LAD_C6")),
+    ("HYBRID_GLOBAL", dict(scheme="HYBRID", hybrid_mode=0, hyb_rho=0.5 * 0.125)),
+    ("HYBRID_CELL", dict(scheme="HYBRID", hybrid_mode=1, hyb_rho=0.5 * 0.125, hybrid_sensor=1)),
+]
+DEVELOP_STEPS = 200
+# FP64 roofline of the dominant kernel (the C-GBR interface sweep).  Per-unit
+# figure: FP64 floating-point operations per interface flux of the developed
+# triple-point state (adds, multiplies, FMAs x2 of the divide / square-root
+# sequences included), from the ncu instruction counts of one sweep launch.
+SWEEP_FLOP_PER_IFACE = None  # from the ncu instruction counts summarised under profiles/
+SWEEP_TRAFFIC_BYTES = None   # dram bytes read + written per sweep launch (ncu), None until captured
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12  # SMs x DFMA/clk x 2 flop x max clock
+HBM_BYTES_PER_CELL_STEP = 256.0  # minimal-traffic model, FP64 state, nv = 4, uniform grid
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {"hbm_gbs": 6800.0}
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2511_18042_gb300 import api, inputs
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    prob = inputs.triple_point(NX, NY)
+    grid = api.Grid.from_problem(prob)
+    cells = NX * NY
+    names = [n for n, _ in SCHEMES if args.schemes is None or n in args.schemes.split(",")]
+    solvers = {n: api.Solver(grid, **kw) for n, kw in SCHEMES if n in names}
+    # developed state: 200 MEG6 steps from the initial condition
+    base = torch.as_tensor(prob["U"], device=dev)
+    dev_solver = solvers.get("MEG6") or api.Solver(grid, scheme="MEG6")
+    dev_solver.advance(base, nsteps=args.develop)
+    torch.cuda.synchronize()
+    U = {n: torch.empty_like(base) for n in names}
+    dt = {n: torch.zeros(2, dtype=torch.float64, device=dev) for n in names}
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def one_step(events=None):
+        for n in names:
+            s = solvers[n]
+            if events is not None:
+                events[n][0].record(stream)
+            U[n].copy_(base)
+            s.cfl_dt(U[n], out=dt[n])
+            s.rk3_step(U[n], dt[n])
+            if events is not None:
+                events[n][1].record(stream)
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    launches0 = sum(s.launch_count() for s in solvers.values())
+    per = {n: 0.0 for n in names}
+    step_ms = []
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        wall0 = time.perf_counter()
+        for _ in range(args.steps):
+            flush.zero_()  # evict L2 (256 MB > 126 MB) between timed steps
+            ev = {n: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for n in names}
+            one_step(ev)
+            torch.cuda.synchronize()
+            tot = 0.0
+            for n in names:
+                ms = ev[n][0].elapsed_time(ev[n][1])
+                per[n] += ms
+                tot += ms
+            step_ms.append(tot)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+    launches = sum(s.launch_count() for s in solvers.values()) - launches0
+    for n in names:
+        rc = solvers[n].sync_status()
+        if rc not in (0, -4):
+            raise RuntimeError("solver status %d" % rc)
+    ms_step = sum(step_ms) / len(step_ms)
+    if ws > 1:
+        t = torch.tensor([ms_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+        dist.barrier()
+    value = ws * cells * len(names) / (ms_step * 1e-3)
+
+    # roofline of the dominant kernel: the MEG6 interface sweep, timed alone
+    roof = sweep_roofline(api, torch, grid, base, dev, args)
+
+    # end to end through the C ABI with host buffers (pinned), one step per scheme
+    host = torch.empty(base.shape, dtype=torch.float64, pin_memory=True)
+    host_base = base.cpu()
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for n in names:
+            host.copy_(host_base)
+            solvers[n].advance_host(host, nsteps=1)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    nbytes = base.numel() * 8
+    e2e = {"value": ws * cells * len(names) / e2e_s, "unit": "cell-updates/s",
+           "h2d_bytes_per_step": nbytes * len(names), "d2h_bytes_per_step": nbytes * len(names)}
+
+    per_scheme = {}
+    peaks = _peaks()
+    for n in names:
+        ms = per[n] / args.steps
+        cu = cells / (ms * 1e-3)
+        per_scheme[n] = {"cell_updates_per_s": cu, "ms_per_rk3_step": ms,
+                         "hbm_frac_of_measured": cu * HBM_BYTES_PER_CELL_STEP / (peaks["hbm_gbs"] * 1e9)}
+    line = {
+        "metric": "cell-updates/s per scheme & % HBM roofline; batched solves/s, p50/p99 latency",
+        "value": value, "unit": "cell-updates/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "triple point 1792x768 (config 2), FP64, one RK3 step of each of %d schemes "
+                               "from a developed state (200 MEG6 steps)" % len(names),
+                   "schemes": names, "cells": cells, "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "per_scheme": per_scheme, "roofline": roof, "e2e": e2e, "gpu_launches": launches // max(1, args.steps),
+        "gpu_launches_timed_total": launches, "wall_s_timed": wall, "clocks": clk.summary(),
+    }
+    if rank == 0 and args.cpu_baseline and ws == 1:
+        line["cpu_baseline"] = cpu_baseline(names, sample=(448, 192))
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def sweep_roofline(api, torch, grid, base, dev, args):
+    """Average duration of the MEG6 interface-sweep launches (CUDA events around
+    each launch on its stream, recorded by the library) over RK3 steps of the
+    bench state; FP64 roofline of that kernel."""
+    s = api.Solver(grid, scheme="MEG6")
+    U = torch.empty_like(base)
+    dtd = torch.zeros(2, dtype=torch.float64, device=dev)
+    for _ in range(2):
+        U.copy_(base)
+        s.cfl_dt(U, out=dtd)
+        s.rk3_step(U, dtd)
+    torch.cuda.synchronize()
+    s.timing_enable(True)
+    reps = max(2, args.steps)
+    for _ in range(reps):
+        U.copy_(base)
+        s.cfl_dt(U, out=dtd)
+        s.rk3_step(U, dtd)
+    torch.cuda.synchronize()
+    ms, n = s.timing_query(0)
+    s.timing_enable(False)
+    avg_ms = ms / n
+    ifaces = ((NX + 1) * NY + NX * (NY + 1)) / 2.0  # algorithmic interfaces per sweep launch (x, y average)
+    roof = {"bound": "alu", "unit": "TFLOP/s", "peak": FP64_PEAK_TFLOPS,
+            "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (FP64 is not in MEASURED_PEAKS.json)",
+            "kernel": "k_gbr_sweep (MEG6), x and y launches of RK3 steps of the bench state",
+            "launch_ms": avg_ms, "launches": n, "ifaces_per_launch": ifaces, "traffic": SWEEP_TRAFFIC_BYTES}
+    if SWEEP_FLOP_PER_IFACE:
+        ach = SWEEP_FLOP_PER_IFACE * ifaces / (avg_ms * 1e-3) / 1e12
+        roof.update({"achieved": ach, "frac": ach / FP64_PEAK_TFLOPS, "flop_per_iface": SWEEP_FLOP_PER_IFACE})
+    else:
+        roof.update({"achieved": None, "frac": None})
+    return roof
+
+
+def cpu_baseline(names, sample=(448, 192)):
+    """The oracle as it stands, single thread, one RK3 step of each scheme on a
+    448 x 192 triple point (same physics, 1/16 of the cells)."""
+    import oracle
+    from paper_2511_18042_gb300 import inputs
+    prob = inputs.triple_point(*sample)
+    kws = dict(SCHEMES)
+    pre = oracle.Oracle(prob, scheme="MEG6")
+    U0, _, _ = pre.advance(prob["U"], nsteps=20)
+    t0 = time.perf_counter()
+    for n in names:
+        o = oracle.Oracle(prob, **kws[n])
+        o.rk3_step(U0, o.cfl_dt(U0))
+    sec = time.perf_counter() - t0
+    cells = sample[0] * sample[1] * len(names)
+    return {"value": cells / sec, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+            "sample": "one RK3 step of each of %d schemes on a %dx%d triple point (1/16 of the cells), "
+                      "from 20 MEG6 steps of development; %.1f s" % (len(names), sample[0], sample[1], sec)}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    names = [n for n, _ in SCHEMES if args.schemes is None or n in args.schemes.split(",")]
+    import oracle
+    from paper_2511_18042_gb300 import inputs
+    sample = (448, 192)
+    prob = inputs.triple_point(*sample)
+    kws = dict(SCHEMES)
+    pre = oracle.Oracle(prob, scheme="MEG6")
+    U0, _, _ = pre.advance(prob["U"], nsteps=20)
+    orcs = {n: oracle.Oracle(prob, **kws[n]) for n in names}
+
+    def step():
+        for n in names:
+            o = orcs[n]
+            o.rk3_step(U0, o.cfl_dt(U0))
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    sec = (time.perf_counter() - t0) / args.steps
+    cells = sample[0] * sample[1] * len(names)
+    value = cells / sec
+    desc = ("FP64 CPU oracle, single thread: one RK3 step of each of %d schemes on a %dx%d triple point "
+            "(bounded sample of the 1792x768 workload)" % (len(names), sample[0], sample[1]))
+    line = {"impl": "reference", "metric": "cell-updates/s per scheme & % HBM roofline; batched solves/s, p50/p99 latency",
+            "value": value, "unit": "cell-updates/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "triple point 1792x768 (config 2), FP64, one RK3 step of each of %d schemes" % len(names),
+                       "sample": "%dx%d" % sample},
+            "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="cgflow", choices=["cgflow", "reference"])
+    ap.add_argument("--schemes", default=None, help="comma-separated subset (default: all six)")
+    ap.add_argument("--develop", type=int, default=DEVELOP_STEPS)
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        from paper_2511_18042_gb300 import build
+        build.build()
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

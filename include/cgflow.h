@@ -149,6 +149,14 @@ CG_API const char *cg_last_error(void);
 /* Number of kernel launches this handle has enqueued since creation. */
 CG_API int64_t cg_launch_count(const cg_solver *s);
 
+/* Kernel timing for measurement: while enabled, every launch of a timed
+ * kernel class is bracketed by CUDA events on its stream; cg_timing_query
+ * synchronises on them, returns the summed duration (ms) and the number of
+ * launches of that class since the last query, and forgets them. */
+#define CG_TIMING_SWEEP 0 /* the fused C-GBR interface sweep */
+CG_API int cg_timing_enable(cg_solver *s, int on);
+CG_API int cg_timing_query(cg_solver *s, int kernel_class, double *total_ms, int64_t *count);
+
 #ifdef __cplusplus
 }
 #endif

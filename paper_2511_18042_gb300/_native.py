@@ -62,6 +62,9 @@ _SIGS = {
     "cg_last_bad_index": (ctypes.c_int64, [ctypes.c_void_p]),
     "cg_last_error": (ctypes.c_char_p, []),
     "cg_launch_count": (ctypes.c_int64, [ctypes.c_void_p]),
+    "cg_timing_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "cg_timing_query": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_int64)]),
 }
 
 

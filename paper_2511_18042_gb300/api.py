@@ -180,3 +180,12 @@ class Solver:
 
     def launch_count(self):
         return int(nat.lib().cg_launch_count(self._h))
+
+    def timing_enable(self, on=True):
+        nat.check(nat.lib().cg_timing_enable(self._h, 1 if on else 0))
+
+    def timing_query(self, kernel_class=0):
+        ms = ctypes.c_double()
+        n = ctypes.c_int64()
+        nat.check(nat.lib().cg_timing_query(self._h, int(kernel_class), ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value

@@ -138,6 +138,10 @@ struct cg_solver {
   int iface_dir = -1;               // diagnostics: direction whose interface fluxes are written
   double* iface_out = nullptr;
   DevLine c6grad[3], c6flux[3], filt[3];  // LAD-C6 line systems
+  // kernel timing (cg_timing_enable): CUDA events around the sweep launches
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_open;
   double* work = nullptr;           // line scratch of the LAD-C6 solves
   size_t work_elems = 0;
 };
@@ -359,6 +363,38 @@ static int compute_metrics(cg_solver* s, cudaStream_t st) {
   return CG_OK;
 }
 
+
+// ---------------------------------------------------------------- timing
+static cudaEvent_t timing_event(cg_solver* s) {
+  if (!s->ev_pool.empty()) {
+    cudaEvent_t e = s->ev_pool.back();
+    s->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+struct TimedRegion {
+  cg_solver* s;
+  int cls;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr;
+  TimedRegion(cg_solver* s_, int c, cudaStream_t st_) : s(s_), cls(c), st(st_) {
+    if (s->timing) {
+      a = timing_event(s);
+      cudaEventRecord(a, st);
+    }
+  }
+  ~TimedRegion() {
+    if (s->timing) {
+      cudaEvent_t b = timing_event(s);
+      cudaEventRecord(b, st);
+      s->ev_open.push_back({cls, {a, b}});
+    }
+  }
+};
+
 // ---------------------------------------------------------------- launches
 template <int ND, bool CART, bool COMPACT>
 static void launch_omega(cg_solver* s, cudaStream_t st, const int* guard, int want) {
@@ -398,7 +434,10 @@ static int launch_sweep(cg_solver* s, const StageArgs& A, cudaStream_t st) {
     int other = DIR == 1 ? n[2] : n[1];
     grid = dim3((n[0] + LW - 1) / LW, (n[DIR] + SWEEP_TL - 2) / (SWEEP_TL - 1), other);
   }
-  k_gbr_sweep<ND, DIR, CART, COMPACT><<<grid, 256, smem, st>>>(s->dg, gbr_cfg(s), A);
+  {
+    TimedRegion tr(s, CG_TIMING_SWEEP, st);
+    k_gbr_sweep<ND, DIR, CART, COMPACT><<<grid, 256, smem, st>>>(s->dg, gbr_cfg(s), A);
+  }
   s->launches++;
   return CG_OK;
 }
@@ -638,6 +677,8 @@ CG_API void cg_solver_destroy(cg_solver* s) {
                     s->hflux[0], s->hflux[1], s->hflux[2], s->dt, s->t, s->host_stage};
   for (double* b : bufs)
     if (b) cudaFree(b);
+  for (auto& o : s->ev_open) { cudaEventDestroy(o.second.first); cudaEventDestroy(o.second.second); }
+  for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
   for (int d = 0; d < 3; ++d) {
     DevLine* ls[4] = {&s->mig4[d], &s->c6grad[d], &s->c6flux[d], &s->filt[d]};
     for (DevLine* l : ls)
@@ -896,6 +937,33 @@ CG_API int cg_iface_flux(cg_solver* s, const double* U, int dir, double* F, void
   s->iface_out = nullptr;
   if (rc) return rc;
   CG_CUDA(cudaGetLastError());
+  return CG_OK;
+}
+
+CG_API int cg_timing_enable(cg_solver* s, int on) {
+  if (!s) return fail(CG_ERR_INVALID_ARG, "null argument");
+  s->timing = on != 0;
+  return CG_OK;
+}
+
+CG_API int cg_timing_query(cg_solver* s, int kernel_class, double* total_ms, int64_t* count) {
+  if (!s || !total_ms || !count) return fail(CG_ERR_INVALID_ARG, "null argument");
+  double tot = 0.0;
+  int64_t n = 0;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> keep;
+  for (auto& o : s->ev_open) {
+    if (o.first != kernel_class) { keep.push_back(o); continue; }
+    CG_CUDA(cudaEventSynchronize(o.second.second));
+    float ms = 0.0f;
+    CG_CUDA(cudaEventElapsedTime(&ms, o.second.first, o.second.second));
+    tot += ms;
+    ++n;
+    s->ev_pool.push_back(o.second.first);
+    s->ev_pool.push_back(o.second.second);
+  }
+  s->ev_open.swap(keep);
+  *total_ms = tot;
+  *count = n;
   return CG_OK;
 }
 

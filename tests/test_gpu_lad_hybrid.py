@@ -1,0 +1,174 @@
+"""GPU parity of the LAD (E4 / C6 + implicit filter) and hybrid LAD-GBR paths
+against the oracle (same tolerance rules as the C-GBR tests: the CUDA library
+follows the oracle's operation order, so the expected difference is zero)."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2511_18042_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+from tests.gpu_util import rel_err, to_dev  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2511_18042_gb300 import api as a
+    return a
+
+
+def _pair(orc, api, prob, **kw):
+    return orc.Oracle(prob, **kw), api.Solver.from_problem(prob, **kw)
+
+
+@pytest.mark.parametrize("scheme,cfl", [("LAD_E4", 0.5), ("LAD_C6", 0.1)])
+def test_sod_100_steps(orc, api, scheme, cfl):
+    prob = inputs.shock_tube("sod", 400)
+    o, s = _pair(orc, api, prob, scheme=scheme, cfl=cfl)
+    Uo, to, _ = o.advance(prob["U"], nsteps=100)
+    Ug = to_dev(prob["U"])
+    tg, _ = s.advance(Ug, nsteps=100)
+    assert rel_err(Ug, Uo) <= 1e-11
+    assert abs(tg - to) <= 1e-12 * to
+
+
+@pytest.mark.parametrize("scheme", ["LAD_E4", "LAD_C6"])
+def test_lad_coefficients_and_rhs(orc, api, scheme):
+    prob = inputs.triple_point(224, 96)
+    pre = orc.Oracle(prob, scheme="MEG6")
+    U, _, _ = pre.advance(prob["U"], nsteps=20)
+    o, s = _pair(orc, api, prob, scheme=scheme)
+    Ud = to_dev(U)
+    bg, kg = s.lad_coeffs(Ud)
+    bo, ko = o.lad_coeffs(U)
+    assert rel_err(torch.stack([bg, kg]), np.stack([bo, ko])) <= 1e-13
+    assert rel_err(s.rhs(Ud), o.rhs(U)) <= 1e-13
+
+
+@pytest.mark.parametrize("shape", [(224, 96), (130, 70)])
+def test_triple_point_lad_e4_100_steps(orc, api, shape):
+    prob = inputs.triple_point(*shape)
+    o, s = _pair(orc, api, prob, scheme="LAD_E4")
+    Uo, _, _ = o.advance(prob["U"], nsteps=100)
+    Ug = to_dev(prob["U"])
+    s.advance(Ug, nsteps=100)
+    assert rel_err(Ug, Uo) <= 1e-11
+
+
+def test_triple_point_lad_c6(orc, api):
+    """LAD-C6 without the filter for 60 steps, then the filtered step (the
+    filtered scheme diverges within a few steps on this case, as the paper
+    reports for LAD-C6 on the triple point)."""
+    prob = inputs.triple_point(224, 96)
+    o0, s0 = _pair(orc, api, prob, scheme="LAD_C6", filter_on=0)
+    Uo, _, _ = o0.advance(prob["U"], nsteps=60)
+    Ug = to_dev(prob["U"])
+    s0.advance(Ug, nsteps=60)
+    assert rel_err(Ug, Uo) <= 1e-11
+    o1, s1 = _pair(orc, api, prob, scheme="LAD_C6")
+    dt = o1.cfl_dt(Uo)
+    Uo1 = o1.rk3_step(Uo, dt)
+    s1.rk3_step(Ug, dt)
+    assert rel_err(Ug, Uo1) <= 1e-11
+    Uf = to_dev(Uo)
+    s1.filter(Uf)
+    assert rel_err(Uf, o1.filter(Uo)) <= 1e-13
+
+
+@pytest.mark.parametrize("scheme", ["LAD_E4", "LAD_C6"])
+def test_periodic_lad(orc, api, scheme):
+    prob = inputs.kelvin_helmholtz(64)
+    o, s = _pair(orc, api, prob, scheme=scheme, cfl=0.1)
+    Uo, _, _ = o.advance(prob["U"], nsteps=20)
+    Ug = to_dev(prob["U"])
+    s.advance(Ug, nsteps=20)
+    assert rel_err(Ug, Uo) <= 1e-11
+
+
+def test_hybrid_global_triple_point(orc, api):
+    """Algorithm 3 with a density criterion rho < 0.12 (just under the lowest
+    initial density, so that the LAD stages' undershoots switch the whole stage
+    to GBR and back several times within 40 steps)."""
+    prob = inputs.triple_point(224, 96)
+    kw = dict(scheme="HYBRID", hybrid_mode=0, hyb_rho=0.12)
+    o, s = _pair(orc, api, prob, **kw)
+    U = prob["U"]
+    Ug = to_dev(U)
+    flags_o, flags_g = [], []
+    for _ in range(40):
+        dt = o.cfl_dt(U)
+        flags_o.append(o.hybrid_flag(U))
+        U = o.rk3_step(U, dt)
+        assert s.cfl_dt(Ug) == dt
+        s.rk3_step(Ug, dt)
+        flags_g.append(s.hybrid_state()[0])
+    assert rel_err(Ug, U) <= 1e-11
+    assert 0 < sum(flags_o) < len(flags_o)  # both schemes ran
+    assert 0 < sum(flags_g) < len(flags_g)
+
+
+@pytest.mark.parametrize("sensor", [0, 1])
+def test_hybrid_per_interface_triple_point(orc, api, sensor):
+    prob = inputs.triple_point(224, 96)
+    kw = dict(scheme="HYBRID", hybrid_mode=1, hyb_rho=0.5 * 0.125, hybrid_sensor=sensor)
+    o, s = _pair(orc, api, prob, **kw)
+    Uo, _, _ = o.advance(prob["U"], nsteps=60)
+    Ug = to_dev(prob["U"])
+    s.advance(Ug, nsteps=60)
+    assert rel_err(Ug, Uo) <= 1e-11
+    for d in (0, 1):
+        assert rel_err(s.iface_flux(to_dev(Uo), d), o.iface_flux(Uo, d)) <= 1e-13
+
+
+def test_hybrid_limits_on_gpu(orc, api):
+    prob = inputs.triple_point(130, 70)
+    U0 = to_dev(prob["U"])
+    runs = {}
+    for name, kw in {"lad": dict(scheme="LAD_E4"), "never": dict(scheme="HYBRID", hybrid_mode=0),
+                     "meg": dict(scheme="MEG6"), "always": dict(scheme="HYBRID", hybrid_mode=0, hyb_rho=math.inf)}.items():
+        s = api.Solver.from_problem(prob, **kw)
+        U = U0.clone()
+        s.advance(U, nsteps=5)
+        runs[name] = U
+    assert torch.equal(runs["lad"], runs["never"])
+    assert torch.equal(runs["meg"], runs["always"])
+
+
+@pytest.mark.parametrize("scheme,extra", [("LAD_E4", {}), ("HYBRID", dict(hybrid_mode=1, hyb_rho=1.05))])
+def test_curvilinear_lad_and_hybrid(orc, api, scheme, extra):
+    xyz, per = inputs.wavy_grid_2d(40, 36, amp=0.08)
+    x, y = xyz
+    W = np.stack([1.0 + 0.3 * np.sin(2 * math.pi * x) * np.cos(2 * math.pi * y), 0.5 + 0 * x,
+                  0.2 + 0.1 * np.cos(2 * math.pi * y), 1.0 + 0.2 * np.sin(2 * math.pi * (x + y))])
+    prob = inputs.field_on_curvilinear(xyz, per, W)
+    o, s = _pair(orc, api, prob, scheme=scheme, **extra)
+    Uo, _, _ = o.advance(prob["U"], nsteps=5)
+    Ug = to_dev(prob["U"])
+    s.advance(Ug, nsteps=5)
+    assert rel_err(Ug, Uo) <= 1e-12
+    fs = inputs.uniform_flow_curvilinear(xyz, per, (1.0, 2.0, 0.5, 1.0))
+    R = s.rhs(to_dev(fs["U"])).cpu().numpy()
+    J = o.metrics()[0][-1]
+    assert np.abs(R).max() <= 1e-14 * J.max() * np.abs(fs["U"]).max() * 10
+
+
+def test_lad_3d(orc, api):
+    n = (18, 12, 10)
+    h = [1.0 / n[0], 1.0 / n[1], 1.0 / n[2]]
+    K, J, I = np.meshgrid(np.arange(n[2]), np.arange(n[1]), np.arange(n[0]), indexing="ij")
+    x, y, z = (I + 0.5) * h[0], (J + 0.5) * h[1], (K + 0.5) * h[2]
+    W = np.stack([1.0 + 0.5 * (x > 0.5), 0.2 * np.sin(2 * math.pi * y), 0.1 + 0 * x, 0.3 * np.cos(2 * math.pi * x),
+                  1.0 + 0.9 * (z > 0.5)])
+    prob = inputs._problem("box3d", 3, list(n), h, [[1, 1], [2, 2], [0, 0]], W, 1.4)
+    for kw in (dict(scheme="LAD_E4"), dict(scheme="LAD_C6", cfl=0.1),
+               dict(scheme="HYBRID", hybrid_mode=1, hyb_p=1.5, hybrid_sensor=1)):
+        o, s = _pair(orc, api, prob, **kw)
+        Uo, _, _ = o.advance(prob["U"], nsteps=4)
+        Ug = to_dev(prob["U"])
+        s.advance(Ug, nsteps=4)
+        assert rel_err(Ug, Uo) <= 1e-12, kw
