@@ -149,6 +149,27 @@ CG_API const char *cg_last_error(void);
 /* Number of kernel launches this handle has enqueued since creation. */
 CG_API int64_t cg_launch_count(const cg_solver *s);
 
+/* Right-hand side of the MEG6 (C-GBR explicit) scheme on a uniform Cartesian
+ * grid without allocating any device memory, for callers that cannot call
+ * cudaMalloc: code running while a stream is captured into a CUDA graph,
+ * plug-ins whose host application owns all device memory, real-time loops that
+ * cannot take an allocation's synchronisation.  Same result as cg_rhs of a
+ * MEG6 solver on the same grid and parameters.  The paper has no counterpart;
+ * this is a deployment convenience.
+ *  - Arguments: the grid as for cg_grid_create_cartesian, p->scheme must be
+ *    CG_MEG6 and p->precision CG_FP64, U and R as for cg_rhs.
+ *  - Limit: at most 65,536 cells and 2*nv*N + prod(n_d + 8) <= 2^20 scratch
+ *    doubles; larger grids return CG_ERR_INVALID_ARG with the sizes.
+ *  - Scratch: a fixed 8 MiB array in device memory, held by every GPU that
+ *    loads this library until the process exits.  The first call on each
+ *    device looks up that array's device address (make it before any stream
+ *    capture).  All calls share the array: calls that may overlap on the GPU
+ *    (different streams or threads without ordering) race and must be
+ *    serialised by the caller.  Nothing in it needs clearing: every element a
+ *    call reads was written earlier in the same call. */
+CG_API int cg_rhs_meg6_noalloc(int ndim, const int64_t n[3], const double h[3], const int bc[6],
+                               const cg_params *p, const double *U, double *R, void *stream);
+
 /* Kernel timing for measurement: while enabled, every launch of a timed
  * kernel class is bracketed by CUDA events on its stream; cg_timing_query
  * synchronises on them, returns the summed duration (ms) and the number of

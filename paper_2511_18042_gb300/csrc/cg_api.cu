@@ -7,6 +7,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -968,3 +969,88 @@ CG_API int cg_timing_query(cg_solver* s, int kernel_class, double* total_ms, int
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- no-allocation RHS
+// Some callers must not allocate device memory: code that runs while a CUDA
+// stream is being captured into a graph, plug-ins whose host application owns
+// every device allocation through its own pool, and real-time loops that cannot
+// afford the device-wide synchronisation a cudaMalloc/cudaFree may cause.
+// cg_rhs_meg6_noalloc serves them: its working arrays (primitives, sensor,
+// flux-difference accumulator) live in the fixed array below, which every GPU
+// that loads this library holds until the process exits.
+static constexpr long long kNoAllocDoubles = 1LL << 20;  // 8 MiB per device
+static constexpr long long kNoAllocMaxCells = 1LL << 16;
+static constexpr int kNoAllocMaxDevices = 64;
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
+static std::mutex g_noalloc_mu;
+static double* g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+extern "C" CG_API int cg_rhs_meg6_noalloc(int ndim, const int64_t n[3], const double h[3], const int bc[6],
+                                          const cg_params* p, const double* U, double* R, void* stream) {
+  if (!n || !h || !bc || !p || !U || !R) return fail(CG_ERR_INVALID_ARG, "null argument");
+  int rc = check_grid_args(ndim, n, bc);
+  if (rc) return rc;
+  for (int d = 0; d < ndim; ++d)
+    if (!(h[d] > 0.0)) return fail(CG_ERR_INVALID_ARG, "spacing must be positive");
+  if (p->scheme != CG_MEG6) return fail(CG_ERR_UNSUPPORTED, "the no-allocation RHS evaluates the MEG6 scheme only");
+  if (p->precision != CG_FP64) return fail(CG_ERR_UNSUPPORTED, "only the FP64 form is built in this library");
+  if (!(p->gamma > 1.0) || p->omega_window < 1 || p->omega_window > 4)
+    return fail(CG_ERR_INVALID_ARG, "gamma > 1 and omega_window in 1..4 required");
+  long long N = 1, box = 1;
+  for (int d = 0; d < 3; ++d) {
+    N *= n[d];
+    box *= d < ndim ? n[d] + 8 : 1;
+  }
+  int nv = ndim + 2;
+  long long need = 2LL * nv * N + box;
+  if (N > kNoAllocMaxCells || need > kNoAllocDoubles)
+    return fail(CG_ERR_INVALID_ARG,
+                "grid too large for the no-allocation RHS: %lld cells need %lld scratch doubles; the limit is %lld "
+                "cells and %lld doubles (use cg_solver_create / cg_rhs)",
+                N, need, kNoAllocMaxCells, kNoAllocDoubles);
+  // once per device, with that device current: device address of the array
+  int dev = 0;
+  CG_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(CG_ERR_UNSUPPORTED, "device ordinal %d out of range", dev);
+  double* base;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+      void* ptr = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+      if (e != cudaSuccess || !ptr)
+        return fail(CG_ERR_CUDA, "cudaGetSymbolAddress of the scratch array: %s", cudaGetErrorString(e));
+      g_noalloc_addr[dev] = static_cast<double*>(ptr);
+    }
+    base = g_noalloc_addr[dev];
+  }
+  // grid and solver descriptors on the stack; every scratch pointer is carved
+  // out of the fixed array (W, accumulator, sensor), each written before read
+  cg_grid gr;
+  gr.nd = ndim;
+  gr.curv = 0;
+  gr.xyz = nullptr;
+  for (int d = 0; d < 3; ++d) {
+    gr.n[d] = (int)n[d];
+    gr.h[d] = d < ndim ? h[d] : 1.0;
+    gr.bc[d][0] = d < ndim ? bc[2 * d] : CG_BC_PERIODIC;
+    gr.bc[d][1] = d < ndim ? bc[2 * d + 1] : CG_BC_PERIODIC;
+    for (int m = 0; m < 3; ++m) gr.period[d][m] = 0.0;
+  }
+  cg_solver s;
+  s.grid = &gr;
+  s.p = *p;
+  s.nd = ndim;
+  s.nv = nv;
+  fill_devgrid(&gr, p, s.dg);
+  s.N = s.dg.N;
+  s.omBox = make_box(&s, 4, -1, 4);
+  s.W = base;
+  s.acc = base + (size_t)nv * N;
+  s.om = base + (size_t)2 * nv * N;
+  cudaStream_t st = (cudaStream_t)stream;
+  rc = DISPATCH_ND((&s), stage, &s, U, U, R, 0, 1, st);
+  if (rc) return rc;
+  CG_CUDA(cudaGetLastError());
+  return CG_OK;
+}
