@@ -42,8 +42,8 @@ DEVELOP_STEPS = 200
 # figure: FP64 floating-point operations per interface flux of the developed
 # triple-point state (adds, multiplies, FMAs x2 of the divide / square-root
 # sequences included), from the ncu instruction counts of one sweep launch.
-SWEEP_FLOP_PER_IFACE = None  # from the ncu instruction counts summarised under profiles/
-SWEEP_TRAFFIC_BYTES = None   # dram bytes read + written per sweep launch (ncu), None until captured
+SWEEP_FLOP_PER_IFACE = 632.2  # profiles/sweep_meg6_triple_point_1792x768.md (mean of x and y)
+SWEEP_TRAFFIC_BYTES = 116.4e6  # dram read + write per launch (mean of x and y), same capture
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12  # SMs x DFMA/clk x 2 flop x max clock
 HBM_BYTES_PER_CELL_STEP = 256.0  # minimal-traffic model, FP64 state, nv = 4, uniform grid
 
