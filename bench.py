@@ -37,6 +37,10 @@ SCHEMES = [
     ("HYBRID_GLOBAL", dict(scheme="HYBRID", hybrid_mode=0, hyb_rho=0.5 * 0.125)),
     ("HYBRID_CELL", dict(scheme="HYBRID", hybrid_mode=1, hyb_rho=0.5 * 0.125, hybrid_sensor=1)),
 ]
+MIXED = [
+    ("MEG6_MIXED", dict(scheme="MEG6", precision=1)),
+    ("HYBRID_CELL_MIXED", dict(scheme="HYBRID", hybrid_mode=1, hyb_rho=0.5 * 0.125, hybrid_sensor=1, precision=1)),
+]
 DEVELOP_STEPS = 200
 # FP64 roofline of the dominant kernel (the C-GBR interface sweep).  Per-unit
 # figure: FP64 floating-point operations per interface flux of the developed
@@ -110,6 +114,21 @@ def _dist():
     return ws, rank, local
 
 
+def aggregate_over_ranks(ms_step, units_per_rank, device=None):
+    """Whole-job throughput of independent replicas: every rank processed
+    units_per_rank units per step; the step time is the slowest rank's.
+    Returns (max-over-ranks ms per step, units of all ranks per second)."""
+    import torch
+    import torch.distributed as dist
+    ws = dist.get_world_size() if dist.is_available() and dist.is_initialized() else 1
+    if ws > 1:
+        t = torch.tensor([float(ms_step)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+        dist.barrier()
+    return ms_step, ws * units_per_rank / (ms_step * 1e-3)
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -175,12 +194,13 @@ def run_gpu(args):
         if rc not in (0, -4):
             raise RuntimeError("solver status %d" % rc)
     ms_step = sum(step_ms) / len(step_ms)
-    if ws > 1:
-        t = torch.tensor([ms_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
-        dist.barrier()
-    value = ws * cells * len(names) / (ms_step * 1e-3)
+    ms_step, value = aggregate_over_ranks(ms_step, cells * len(names), dev if ws > 1 else None)
+
+    # the mixed form (FP32 fluxes, FP64 accumulation) of the schemes that have it
+    mixed = {}
+    for n, kw in MIXED:
+        ms = time_mixed(api, torch, grid, base, dev, kw, args)
+        mixed[n] = {"cell_updates_per_s": cells / (ms * 1e-3), "ms_per_rk3_step": ms}
 
     # roofline of the dominant kernel: the MEG6 interface sweep, timed alone
     roof = sweep_roofline(api, torch, grid, base, dev, args)
@@ -216,7 +236,7 @@ def run_gpu(args):
                                "from a developed state (200 MEG6 steps)" % len(names),
                    "schemes": names, "cells": cells, "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
-        "per_scheme": per_scheme, "roofline": roof, "e2e": e2e, "gpu_launches": launches // max(1, args.steps),
+        "per_scheme": per_scheme, "mixed_precision": mixed, "roofline": roof, "e2e": e2e, "gpu_launches": launches // max(1, args.steps),
         "gpu_launches_timed_total": launches, "wall_s_timed": wall, "clocks": clk.summary(),
     }
     if rank == 0 and args.cpu_baseline and ws == 1:
@@ -225,6 +245,30 @@ def run_gpu(args):
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+
+
+def time_mixed(api, torch, grid, base, dev, kw, args):
+    """ms per RK3 step (with CFL) of a mixed-precision solver on the bench state."""
+    s = api.Solver(grid, **kw)
+    U = torch.empty_like(base)
+    dtd = torch.zeros(2, dtype=torch.float64, device=dev)
+    for _ in range(max(3, args.warmup)):
+        U.copy_(base)
+        s.cfl_dt(U, out=dtd)
+        s.rk3_step(U, dtd)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    tot = 0.0
+    for _ in range(max(1, args.steps)):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        U.copy_(base)
+        s.cfl_dt(U, out=dtd)
+        s.rk3_step(U, dtd)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tot += e0.elapsed_time(e1)
+    return tot / max(1, args.steps)
 
 
 def sweep_roofline(api, torch, grid, base, dev, args):

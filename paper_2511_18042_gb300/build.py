@@ -8,11 +8,13 @@ SRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libcgflow.so")
 
-# FP64 parity translation units: no contraction of a*b+c on device or host.
-NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
-              "-fmad=false", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
-              "-Xcompiler", "-fvisibility=hidden"]
-SOURCES = ["cg_api.cu"]
+COMMON = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
+          "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"]
+# FP64 parity unit: no contraction of a*b+c on device or host.  Mixed unit:
+# FP32 flux arithmetic with contraction.
+UNITS = [("cg_api.cu", ["-fmad=false", "-Xcompiler", "-ffp-contract=off"]),
+         ("cg_mixed.cu", ["-fmad=true"])]
+NVCC_FLAGS = COMMON + UNITS[0][1]
 
 
 def _sources_mtime():
@@ -27,8 +29,19 @@ def build(force=False, verbose=False):
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _sources_mtime():
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)
+    objs, procs = [], []
+    for src, flags in UNITS:
+        obj = os.path.join(OUT_DIR, src.replace(".cu", ".o"))
+        cmd = ["nvcc"] + COMMON + flags + ["-c", "-o", obj, os.path.join(SRC, src)]
+        if verbose:
+            print(" ".join(cmd))
+        procs.append(subprocess.Popen(cmd))
+        objs.append(obj)
+    for p in procs:
+        if p.wait() != 0:
+            raise subprocess.CalledProcessError(p.returncode, "nvcc")
     tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = ["nvcc"] + NVCC_FLAGS + ["-shared", "-o", tmp] + [os.path.join(SRC, s) for s in SOURCES]
+    cmd = ["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-shared", "-o", tmp] + objs
     if verbose:
         print(" ".join(cmd))
     subprocess.check_call(cmd)

@@ -15,6 +15,7 @@
 #include "../../include/cgflow.h"
 #include "cg_kernels.cuh"
 #include "cg_lad.cuh"
+#include "cg_lines.cuh"
 #include "cg_metrics.cuh"
 
 using namespace cgk;
@@ -117,7 +118,8 @@ struct cg_solver {
   // stage scratch
   double *W = nullptr, *acc = nullptr, *om = nullptr, *U1 = nullptr, *U2 = nullptr, *Rtmp = nullptr;
   double* G[3] = {nullptr, nullptr, nullptr};
-  Box omBox, gdBox[3];
+  Box omBox;
+  LineBuf gdLB[3];
   DevLine mig4[3];
   // LAD scratch
   LadBuffers lad;
@@ -143,8 +145,6 @@ struct cg_solver {
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_open;
-  double* work = nullptr;           // line scratch of the LAD-C6 solves
-  size_t work_elems = 0;
 };
 
 static void fill_devgrid(const cg_grid* g, const cg_params* p, DevGrid& d) {
@@ -228,6 +228,25 @@ static Box make_box(const cg_solver* s, int grow_all, int dir, int grow_dir) {
     b.ext[k] = s->dg.n[k] + 2 * gr;
   }
   return b;
+}
+
+// Line buffer along d: rows [lo, lo+m) (periodic: the n nodes), lines over
+// the other active directions grown by `grow`.
+static LineBuf make_lines(const cg_solver* s, int d, int lo, int m_nonper, int grow) {
+  LineBuf lb;
+  lb.d = d;
+  lb.n = s->dg.n[d];
+  lb.periodic = s->grid->bc[d][0] == CG_BC_PERIODIC;
+  lb.lo = lb.periodic ? 0 : lo;
+  lb.m = lb.periodic ? lb.n : m_nonper;
+  lb.nl = 1;
+  for (int k = 0; k < 3; ++k) {
+    int gr = (k < s->nd && k != d) ? grow : 0;
+    lb.off[k] = gr;
+    lb.ext[k] = k == d ? 1 : s->dg.n[k] + 2 * gr;
+    if (k != d) lb.nl *= lb.ext[k];
+  }
+  return lb;
 }
 
 template <typename T>
@@ -401,7 +420,7 @@ template <int ND, bool CART, bool COMPACT>
 static void launch_omega(cg_solver* s, cudaStream_t st, const int* guard, int want) {
   long long tot = s->omBox.size();
   k_omega<ND, CART, COMPACT><<<grid_blocks(tot, 128), 128, 0, st>>>(
-      s->dg, s->W, s->G[0], s->G[1], s->G[2], s->gdBox[0], s->gdBox[1], s->gdBox[2], s->om, s->omBox, guard, want);
+      s->dg, s->W, s->G[0], s->G[1], s->G[2], s->gdLB[0], s->gdLB[1], s->gdLB[2], s->om, s->omBox, guard, want);
   s->launches++;
 }
 
@@ -414,6 +433,11 @@ static GbrCfg gbr_cfg(const cg_solver* s) {
   q.alpha = s->p.mp_alpha;
   q.window = s->p.omega_window;
   return q;
+}
+
+namespace cgk {
+int launch_sweep_f32(int nd, int dir, bool cart, const DevGrid& g, const GbrCfg& q, const StageArgs& A, dim3 grid,
+                     cudaStream_t st);
 }
 
 template <int ND, int DIR, bool CART, bool COMPACT>
@@ -437,7 +461,12 @@ static int launch_sweep(cg_solver* s, const StageArgs& A, cudaStream_t st) {
   }
   {
     TimedRegion tr(s, CG_TIMING_SWEEP, st);
-    k_gbr_sweep<ND, DIR, CART, COMPACT><<<grid, 256, smem, st>>>(s->dg, gbr_cfg(s), A);
+    if (s->p.precision == CG_MIXED && !COMPACT) {
+      int e = launch_sweep_f32(ND, DIR, CART, s->dg, gbr_cfg(s), A, grid, st);
+      if (e) return fail(CG_ERR_CUDA, "mixed sweep launch: %s", cudaGetErrorString((cudaError_t)e));
+    } else {
+      k_gbr_sweep<ND, DIR, CART, COMPACT><<<grid, 256, smem, st>>>(s->dg, gbr_cfg(s), A);
+    }
   }
   s->launches++;
   return CG_OK;
@@ -451,6 +480,13 @@ static int sweep_dir(cg_solver* s, int dir, const StageArgs& A, cudaStream_t st)
   return fail(CG_ERR_INVALID_ARG, "bad direction");
 }
 
+// one thread per line column in 32-thread blocks, so the few long recurrences
+// spread over as many SMs as possible
+static void launch_thomas(const ThomasJobs& J, cudaStream_t st) {
+  long long cols = J.start[J.njobs];
+  k_thomas_jobs<<<(unsigned)((cols + 31) / 32), 32, 0, st>>>(J);
+}
+
 // Primitives, sensor (and compact gradients) of the state Uc into W, om, G.
 template <int ND>
 static int stage_prep_gbr(cg_solver* s, const double* Uc, bool compact, cudaStream_t st, bool prim = true,
@@ -460,14 +496,21 @@ static int stage_prep_gbr(cg_solver* s, const double* Uc, bool compact, cudaStre
     s->launches++;
   }
   if (compact) {
+    ThomasJobs J;
+    J.njobs = ND;
+    J.start[0] = 0;
     for (int d = 0; d < ND; ++d) {
-      int e1 = (d + 1) % 3 < ND ? s->dg.n[(d + 1) % 3] + 8 : 1;
-      int e2 = (d + 2) % 3 < ND ? s->dg.n[(d + 2) % 3] + 8 : 1;
-      long long lines = (long long)e1 * e2 * (ND + 2);
-      k_compact_grad<ND><<<(unsigned)((lines + 127) / 128), 128, 0, st>>>(s->dg, s->W, d, s->mig4[d].lc, s->G[d],
-                                                                         s->gdBox[d]);
+      const LineBuf& lb = s->gdLB[d];
+      k_rhs_mig4<ND><<<grid_blocks((long long)lb.m * lb.nl, 256), 256, 0, st>>>(s->dg, s->W, lb, s->G[d]);
       s->launches++;
+      J.lc[d] = s->mig4[d].lc;
+      J.x[d] = s->G[d];
+      J.nl[d] = lb.nl;
+      J.ncomp[d] = ND + 2;
+      J.start[d + 1] = J.start[d] + lb.nl * (ND + 2);
     }
+    launch_thomas(J, st);
+    s->launches++;
   }
   if (s->dg.curv) {
     if (compact) launch_omega<ND, false, true>(s, st, guard, want);
@@ -506,7 +549,7 @@ static int gbr_sweeps(cg_solver* s, bool compact, StageArgs A, cudaStream_t st) 
     A.first = d == 0;
     A.last = d == ND - 1;
     A.Gd = s->G[d];
-    A.gdBox = s->gdBox[d];
+    A.gdLB = s->gdLB[d];
     A.iface_out = (s->iface_out && s->iface_dir == d) ? s->iface_out : nullptr;
     int rc;
     if (s->dg.curv) rc = compact ? sweep_dir<ND, false, true>(s, d, A, st) : sweep_dir<ND, false, false>(s, d, A, st);
@@ -685,7 +728,6 @@ CG_API void cg_solver_destroy(cg_solver* s) {
     for (DevLine* l : ls)
       if (l->buf) cudaFree(l->buf);
   }
-  if (s->work) cudaFree(s->work);
   lad_free(s->lad);
   if (s->mask) cudaFree(s->mask);
   if (s->hyb_flag) cudaFree(s->hyb_flag);
@@ -699,7 +741,9 @@ CG_API void cg_solver_destroy(cg_solver* s) {
 CG_API int cg_solver_create(const cg_grid* g, const cg_params* p, cg_solver** out) {
   if (!g || !p || !out) return fail(CG_ERR_INVALID_ARG, "null argument");
   if (p->scheme < CG_MEG6 || p->scheme > CG_HYBRID) return fail(CG_ERR_INVALID_ARG, "bad scheme");
-  if (p->precision != CG_FP64) return fail(CG_ERR_UNSUPPORTED, "only the FP64 form is built in this library");
+  if (p->precision != CG_FP64 && p->precision != CG_MIXED) return fail(CG_ERR_INVALID_ARG, "bad precision");
+  if (p->precision == CG_MIXED && p->scheme != CG_MEG6 && p->scheme != CG_HYBRID)
+    return fail(CG_ERR_UNSUPPORTED, "the mixed form is built for MEG6 and the hybrid's MEG6 interfaces");
   if (!(p->gamma > 1.0) || !(p->cfl > 0.0)) return fail(CG_ERR_INVALID_ARG, "gamma > 1 and cfl > 0 required");
   if (p->omega_window < 1 || p->omega_window > 4) return fail(CG_ERR_INVALID_ARG, "omega_window must be 1..4");
   if (g->curv && p->scheme == CG_LAD_C6)
@@ -728,9 +772,9 @@ CG_API int cg_solver_create(const cg_grid* g, const cg_params* p, cg_solver** ou
   cudaMemset(s->hyb_count, 0, sizeof(unsigned long long));
   bool compact = p->scheme == CG_MIG4;
   for (int d = 0; d < s->nd; ++d) {
-    s->gdBox[d] = make_box(s, 4, d, 6);
+    s->gdLB[d] = make_lines(s, d, -6, g->n[d] + 12, 4);
     if (compact) {
-      if ((rc = dalloc(&s->G[d], (size_t)s->nv * s->gdBox[d].size()))) { cg_solver_destroy(s); return rc; }
+      if ((rc = dalloc(&s->G[d], (size_t)s->nv * s->gdLB[d].m * s->gdLB[d].nl))) { cg_solver_destroy(s); return rc; }
       bool cyc = g->bc[d][0] == CG_BC_PERIODIC;
       int m = cyc ? g->n[d] : g->n[d] + 12;
       if (cyc && m < 3) { cg_solver_destroy(s); return fail(CG_ERR_INVALID_ARG, "periodic compact lines need n >= 3"); }

@@ -134,6 +134,34 @@ __device__ __forceinline__ long long scalar_src(const DevGrid& g, int c0, int c1
   return lin(g, c[0], c[1], c[2]);
 }
 
+// ---------------------------------------------------------------- line buffers
+// Rows [lo, lo + m) along direction d (periodic: rows 0..n-1, positions wrap);
+// lines over the other directions on the box (off, ext).
+struct LineBuf {
+  int d, lo, m, n, periodic;
+  int off[3], ext[3];  // box of the other directions (entry d unused)
+  long long nl;        // lines
+  __host__ __device__ long long line(const int* c) const {
+    int o1 = (d + 1) % 3, o2 = (d + 2) % 3;
+    return (long long)(c[o1] + off[o1]) + (long long)ext[o1] * (long long)(c[o2] + off[o2]);
+  }
+  __device__ long long at(int comp, int pos, const int* c) const {
+    int row;
+    if (periodic) {
+      row = pos % n;
+      if (row < 0) row += n;
+    } else {
+      row = pos - lo;
+    }
+    return ((long long)comp * m + row) * nl + line(c);
+  }
+  __device__ void coords(long long L, int* c) const {
+    int o1 = (d + 1) % 3, o2 = (d + 2) % 3;
+    c[o1] = (int)(L % ext[o1]) - off[o1];
+    c[o2] = (int)(L / ext[o1]) - off[o2];
+  }
+};
+
 // ---------------------------------------------------------------- state
 // primitive from conserved: rho, u = m / rho, p = (gamma-1)(E - (m.u)/2)
 template <int ND>
@@ -151,50 +179,58 @@ __device__ __forceinline__ void cons_to_prim(double gm1, const double* Q, double
 }
 
 // ---------------------------------------------------------------- stencils
+// T = double: the FP64 parity form; T = float: the mixed form's flux arithmetic.
 // explicit sixth-order central first derivative (MEG6 gradients)
-__device__ __forceinline__ double d6(double m3, double m2, double m1, double p1, double p2, double p3) {
-  return 0.75 * (p1 - m1) - (3.0 / 20.0) * (p2 - m2) + (1.0 / 60.0) * (p3 - m3);
+template <typename T = double>
+__device__ __forceinline__ T d6(T m3, T m2, T m1, T p1, T p2, T p3) {
+  return T(0.75) * (p1 - m1) - T(3.0 / 20.0) * (p2 - m2) + T(1.0 / 60.0) * (p3 - m3);
 }
 // explicit fourth-order central first derivative (E4)
-__device__ __forceinline__ double d4(double m2, double m1, double p1, double p2) {
-  return (2.0 / 3.0) * (p1 - m1) - (1.0 / 12.0) * (p2 - m2);
+template <typename T = double>
+__device__ __forceinline__ T d4(T m2, T m1, T p1, T p2) {
+  return T(2.0 / 3.0) * (p1 - m1) - T(1.0 / 12.0) * (p2 - m2);
 }
 // second derivative from values and first derivatives (gradient-based)
-__device__ __forceinline__ double d2_from_grad(double wm, double w0, double wp, double dm, double dp) {
-  return 2.0 * (wp - 2.0 * w0 + wm) - 0.5 * (dp - dm);
+template <typename T = double>
+__device__ __forceinline__ T d2_from_grad(T wm, T w0, T wp, T dm, T dp) {
+  return T(2.0) * (wp - T(2.0) * w0 + wm) - T(0.5) * (dp - dm);
 }
 
 // ---------------------------------------------------------------- MP5
-__device__ __forceinline__ double dmin(double a, double b) { return a < b ? a : b; }
-__device__ __forceinline__ double dmax(double a, double b) { return a > b ? a : b; }
-__device__ __forceinline__ double minmod2(double a, double b) {
-  if (a > 0.0 && b > 0.0) return dmin(a, b);
-  if (a < 0.0 && b < 0.0) return dmax(a, b);
-  return 0.0;
+template <typename T>
+__device__ __forceinline__ T dmin(T a, T b) { return a < b ? a : b; }
+template <typename T>
+__device__ __forceinline__ T dmax(T a, T b) { return a > b ? a : b; }
+template <typename T>
+__device__ __forceinline__ T minmod2(T a, T b) {
+  if (a > T(0) && b > T(0)) return dmin(a, b);
+  if (a < T(0) && b < T(0)) return dmax(a, b);
+  return T(0);
 }
-__device__ __forceinline__ double minmod4(double a, double b, double c, double d) {
-  if (a > 0.0 && b > 0.0 && c > 0.0 && d > 0.0) return dmin(dmin(a, b), dmin(c, d));
-  if (a < 0.0 && b < 0.0 && c < 0.0 && d < 0.0) return dmax(dmax(a, b), dmax(c, d));
-  return 0.0;
+template <typename T>
+__device__ __forceinline__ T minmod4(T a, T b, T c, T d) {
+  if (a > T(0) && b > T(0) && c > T(0) && d > T(0)) return dmin(dmin(a, b), dmin(c, d));
+  if (a < T(0) && b < T(0) && c < T(0) && d < T(0)) return dmax(dmax(a, b), dmax(c, d));
+  return T(0);
 }
 // Suresh & Huynh (1997) monotonicity-preserving fifth-order interface value
 // from u_{i-2} .. u_{i+2} (left state at i+1/2).
-__device__ __forceinline__ double mp5(double um2, double um1, double u0, double up1, double up2,
-                                      double alpha, double eps) {
-  double ul = (2.0 * um2 - 13.0 * um1 + 47.0 * u0 + 27.0 * up1 - 3.0 * up2) / 60.0;
-  double ump = u0 + minmod2(up1 - u0, alpha * (u0 - um1));
+template <typename T>
+__device__ __forceinline__ T mp5(T um2, T um1, T u0, T up1, T up2, T alpha, T eps) {
+  T ul = (T(2.0) * um2 - T(13.0) * um1 + T(47.0) * u0 + T(27.0) * up1 - T(3.0) * up2) / T(60.0);
+  T ump = u0 + minmod2(up1 - u0, alpha * (u0 - um1));
   if ((ul - u0) * (ul - ump) <= eps) return ul;
-  double dm1 = um2 - 2.0 * um1 + u0;
-  double d0 = um1 - 2.0 * u0 + up1;
-  double dp1 = u0 - 2.0 * up1 + up2;
-  double dm4p = minmod4(4.0 * d0 - dp1, 4.0 * dp1 - d0, d0, dp1);
-  double dm4m = minmod4(4.0 * d0 - dm1, 4.0 * dm1 - d0, d0, dm1);
-  double uul = u0 + alpha * (u0 - um1);
-  double uav = 0.5 * (u0 + up1);
-  double umd = uav - 0.5 * dm4p;
-  double ulc = u0 + 0.5 * (u0 - um1) + (4.0 / 3.0) * dm4m;
-  double umin = dmax(dmin(dmin(u0, up1), umd), dmin(dmin(u0, uul), ulc));
-  double umax = dmin(dmax(dmax(u0, up1), umd), dmax(dmax(u0, uul), ulc));
+  T dm1 = um2 - T(2.0) * um1 + u0;
+  T d0 = um1 - T(2.0) * u0 + up1;
+  T dp1 = u0 - T(2.0) * up1 + up2;
+  T dm4p = minmod4(T(4.0) * d0 - dp1, T(4.0) * dp1 - d0, d0, dp1);
+  T dm4m = minmod4(T(4.0) * d0 - dm1, T(4.0) * dm1 - d0, d0, dm1);
+  T uul = u0 + alpha * (u0 - um1);
+  T uav = T(0.5) * (u0 + up1);
+  T umd = uav - T(0.5) * dm4p;
+  T ulc = u0 + T(0.5) * (u0 - um1) + T(4.0 / 3.0) * dm4m;
+  T umin = dmax(dmin(dmin(u0, up1), umd), dmin(dmin(u0, uul), ulc));
+  T umax = dmin(dmax(dmax(u0, up1), umd), dmax(dmax(u0, uul), ulc));
   return ul + minmod2(umin - ul, umax - ul);
 }
 
@@ -209,9 +245,9 @@ __host__ __device__ constexpr bool frame_nz(bool cart, int nd, int dir, int vec,
 }
 
 // sum_m a[m] * u[m] over the structurally non-zero a[m], in index order
-template <int ND, bool CART, int DIR, int VEC>
-__device__ __forceinline__ double sdot(const double* a, const double* u) {
-  double s = 0.0;
+template <int ND, bool CART, int DIR, int VEC, typename T = double>
+__device__ __forceinline__ T sdot(const T* a, const T* u) {
+  T s = T(0);
   bool first = true;
 #pragma unroll
   for (int m = 0; m < ND; ++m) {

@@ -20,8 +20,8 @@ struct StageArgs {
   const double* W;     // primitives (nv planes, interior)
   const double* om;    // sensor on omBox
   Box omBox;
-  const double* Gd;    // compact gradients along the sweep direction (nv planes on gdBox)
-  Box gdBox;
+  const double* Gd;    // compact gradients along the sweep direction (line buffer gdLB)
+  LineBuf gdLB;
   double* acc;         // flux-difference accumulator (nv planes)
   int first, last;     // first / last direction of the stage
   int rk;              // last direction: 1 = RK update, 0 = write R
@@ -63,8 +63,8 @@ __global__ void k_prim(DevGrid g, const double* __restrict__ U, double* __restri
 // dilatation (one in irrotational dilatation-free flow).
 template <int ND, bool CART, bool COMPACT>
 __global__ void k_omega(DevGrid g, const double* __restrict__ W, const double* __restrict__ G0,
-                        const double* __restrict__ G1, const double* __restrict__ G2, Box gb0, Box gb1,
-                        Box gb2, double* __restrict__ om, Box ob, const int* guard, int want) {
+                        const double* __restrict__ G1, const double* __restrict__ G2, LineBuf gb0,
+                        LineBuf gb1, LineBuf gb2, double* __restrict__ om, Box ob, const int* guard, int want) {
   constexpr int NV = ND + 2, IP = ND + 1;
   if (guard && *guard != want) return;
   long long tot = ob.size();
@@ -105,11 +105,9 @@ __global__ void k_omega(DevGrid g, const double* __restrict__ W, const double* _
           du[l][k] = d6(s[0][1 + k], s[1][1 + k], s[2][1 + k], s[3][1 + k], s[4][1 + k], s[5][1 + k]);
       } else {
         const double* G = l == 0 ? G0 : (l == 1 ? G1 : G2);
-        const Box& gb = l == 0 ? gb0 : (l == 1 ? gb1 : gb2);
-        long long gi = gb.at(c[0], c[1], c[2]);
-        long long gs = gb.size();
+        const LineBuf& gb = l == 0 ? gb0 : (l == 1 ? gb1 : gb2);
 #pragma unroll
-        for (int k = 0; k < ND; ++k) du[l][k] = G[(1 + k) * gs + gi];
+        for (int k = 0; k < ND; ++k) du[l][k] = G[gb.at(1 + k, c[l], c)];
       }
     }
     // physical velocity gradients gu[k][m] = sum_l (J xi_hat[l][m]) du[l][k]
@@ -174,89 +172,6 @@ struct LineCoef {
   int periodic;
 };
 
-template <int ND>
-__global__ void k_compact_grad(DevGrid g, const double* __restrict__ W, int d, LineCoef lc,
-                               double* __restrict__ G, Box gb) {
-  constexpr int NV = ND + 2;
-  // lines: positions of the other directions on [-4, n+3]
-  int o1 = (d + 1) % 3, o2 = (d + 2) % 3;
-  int e1 = o1 < ND ? g.n[o1] + 8 : 1, e2 = o2 < ND ? g.n[o2] + 8 : 1;
-  long long nl = (long long)e1 * e2 * NV;
-  long long gs = gb.size();
-  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= nl) return;
-  int v = (int)(t % NV);
-  long long r = t / NV;
-  int p1 = (int)(r % e1) - (o1 < ND ? 4 : 0);
-  int p2 = (int)(r / e1) - (o2 < ND ? 4 : 0);
-  int c[3];
-  c[o1] = p1;
-  c[o2] = p2;
-  int n = g.n[d];
-  auto val = [&](int x) {
-    c[d] = x;
-    double w[NV];
-    load_state<ND>(g, W, c[0], c[1], c[2], w);
-    return w[v];
-  };
-  auto out = [&](int x) -> double& {
-    c[d] = x;
-    return G[(long long)v * gs + gb.at(c[0], c[1], c[2])];
-  };
-  const double a = lc.a;
-  if (!lc.periodic) {
-    int m = lc.m, lo = lc.lo;
-    // forward elimination (row 0 and row m-1 are the explicit E4 closures)
-    double dp = d4(val(lo - 2), val(lo - 1), val(lo + 1), val(lo + 2));
-    out(lo) = dp;
-    double fm1 = val(lo), f0 = val(lo + 1), fp1;
-    for (int i = 1; i < m - 1; ++i) {
-      fp1 = val(lo + i + 1);
-      double rhs = 0.75 * (fp1 - fm1);
-      dp = (rhs - a * dp) / lc.den[i];
-      out(lo + i) = dp;
-      fm1 = f0;
-      f0 = fp1;
-    }
-    int hi = lo + m - 1;
-    double x = d4(val(hi - 2), val(hi - 1), val(hi + 1), val(hi + 2));
-    out(hi) = x;
-    for (int i = m - 2; i >= 0; --i) {
-      double& o = out(lo + i);
-      x = o - lc.cp[i] * x;
-      o = x;
-    }
-  } else {
-    int m = n;
-    double dp = 0.75 * (val(1) - val(-1)) / 2.0;
-    out(0) = dp;
-    for (int i = 1; i < m; ++i) {
-      double rhs = 0.75 * (val(i + 1) - val(i - 1));
-      dp = (rhs - a * dp) / lc.den[i];
-      out(i) = dp;
-    }
-    double x = dp;
-    const double xlast = dp;
-    for (int i = m - 2; i >= 0; --i) {
-      double& o = out(i);
-      x = o - lc.cp[i] * x;
-      o = x;
-    }
-    double x0 = out(0);
-    double fact = (x0 + a * xlast / lc.gam) / lc.fden;
-    for (int i = 0; i < m; ++i) {
-      double& o = out(i);
-      o = o - fact * lc.z[i];
-    }
-    for (int q = 1; q <= 6; ++q) {
-      double lv = out(((-q) % m + m) % m);
-      double rv = out((n - 1 + q) % m);
-      out(-q) = lv;
-      out(n - 1 + q) = rv;
-    }
-  }
-}
-
 // ---------------------------------------------------------------- C-GBR sweep
 constexpr int SWEEP_TL = 64;
 __host__ __device__ constexpr int sweep_lw(int dir) { return dir == 0 ? 4 : 8; }
@@ -266,17 +181,20 @@ __host__ __device__ constexpr int sweep_smem_doubles() {
          (SWEEP_TL + 7) * sweep_lw(DIR);
 }
 
-template <int ND, int DIR, bool CART, bool COMPACT>
-__global__ void __launch_bounds__(256) k_gbr_sweep(DevGrid g, GbrCfg q, StageArgs A) {
+// T = double: FP64 parity form; T = float: mixed form (FP32 reconstruction and
+// fluxes from FP64 primitives; FP64 flux differences, residual and RK update).
+template <int ND, int DIR, bool CART, bool COMPACT, typename T = double>
+__global__ void __launch_bounds__(256, 2) k_gbr_sweep(DevGrid g, GbrCfg q, StageArgs A) {
   constexpr int NV = ND + 2, IP = ND + 1;
   constexpr int TL = SWEEP_TL, LW = sweep_lw(DIR);
   constexpr int RW = TL + 9, RD = TL + 3, RDD = TL + 1, RO = TL + 7;
-  extern __shared__ double sm[];
-  double* sW = sm;
-  double* sD = sW + NV * RW * LW;
-  double* sDD = sD + NV * RD * LW;
-  double* sF = sDD + NV * RDD * LW;
-  double* sO = sF + NV * TL * LW;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* sm = reinterpret_cast<T*>(smraw);
+  T* sW = sm;
+  T* sD = sW + NV * RW * LW;
+  T* sDD = sD + NV * RD * LW;
+  T* sF = sDD + NV * RDD * LW;
+  T* sO = sF + NV * TL * LW;
   auto IX = [](int v, int r, int l, int rows) {
     return DIR == 0 ? (v * LW + l) * rows + r : (v * rows + r) * LW + l;
   };
@@ -325,7 +243,7 @@ __global__ void __launch_bounds__(256) k_gbr_sweep(DevGrid g, GbrCfg q, StageArg
       for (int v = 0; v < NV; ++v) w[v] = 1.0;
     }
 #pragma unroll
-    for (int v = 0; v < NV; ++v) sW[IX(v, r, l, RW)] = w[v];
+    for (int v = 0; v < NV; ++v) sW[IX(v, r, l, RW)] = T(w[v]);
   }
   // sensor window values
   for (int e = tid; e < RO * LW; e += blockDim.x) {
@@ -338,7 +256,7 @@ __global__ void __launch_bounds__(256) k_gbr_sweep(DevGrid g, GbrCfg q, StageArg
       c[DIR] = x;
       o = A.om[A.omBox.at(c[0], c[1], c[2])];
     }
-    sO[(DIR == 0) ? l * RO + r : r * LW + l] = o;
+    sO[(DIR == 0) ? l * RO + r : r * LW + l] = T(o);
   }
   __syncthreads();
   // 2. first derivatives along DIR on nodes i0-2 .. i0+TL
@@ -354,11 +272,8 @@ __global__ void __launch_bounds__(256) k_gbr_sweep(DevGrid g, GbrCfg q, StageArg
       int c[3] = {0, 0, 0};
       int x = i0 - 2 + r;
       bool ok = line_coords(l, c) && x <= n + 5;
-      c[DIR] = x;
-      long long gi = ok ? A.gdBox.at(c[0], c[1], c[2]) : 0;
-      long long gs = A.gdBox.size();
 #pragma unroll
-      for (int v = 0; v < NV; ++v) sD[IX(v, r, l, RD)] = ok ? A.Gd[v * gs + gi] : 0.0;
+      for (int v = 0; v < NV; ++v) sD[IX(v, r, l, RD)] = ok ? T(A.Gd[A.gdLB.at(v, x, c)]) : T(0);
     }
   }
   __syncthreads();
@@ -382,7 +297,7 @@ __global__ void __launch_bounds__(256) k_gbr_sweep(DevGrid g, GbrCfg q, StageArg
     int l = DIR == 0 ? e / TL : e % LW;
     int i = i0 - 1 + a;
     int c[3] = {0, 0, 0};
-    double F[NV];
+    T F[NV];
     bool ok = line_coords(l, c) && i <= n - 1;
     c[DIR] = i;
     bool use_gbr = ok;
@@ -392,7 +307,7 @@ __global__ void __launch_bounds__(256) k_gbr_sweep(DevGrid g, GbrCfg q, StageArg
       use_gbr = A.mask[A.tBox.at(c[0], c[1], c[2])] != 0 || A.mask[A.tBox.at(cn[0], cn[1], cn[2])] != 0;
     }
     if (use_gbr) {
-      double Wst[6][NV], Wd[2][NV], Wdd[2][NV];
+      T Wst[6][NV], Wd[2][NV], Wdd[2][NV];
 #pragma unroll
       for (int j = 0; j < 6; ++j)
 #pragma unroll
@@ -404,26 +319,26 @@ __global__ void __launch_bounds__(256) k_gbr_sweep(DevGrid g, GbrCfg q, StageArg
           Wd[j][v] = sD[IX(v, a + 1 + j, l, RD)];
           Wdd[j][v] = sDD[IX(v, a + j, l, RDD)];
         }
-      double omb = sO[(DIR == 0) ? l * RO + a + 3 : (a + 3) * LW + l];
+      T omb = sO[(DIR == 0) ? l * RO + a + 3 : (a + 3) * LW + l];
       for (int jj = 1 - q.window; jj <= q.window; ++jj) {
-        double o = sO[(DIR == 0) ? l * RO + a + 3 + jj : (a + 3 + jj) * LW + l];
+        T o = sO[(DIR == 0) ? l * RO + a + 3 + jj : (a + 3 + jj) * LW + l];
         omb = dmax(omb, o);
       }
-      double xi[3] = {0.0, 0.0, 0.0};
+      T xi[3] = {T(0), T(0), T(0)};
       if (!CART) {
         long long pq = plin(g, c[0], c[1], c[2]);
 #pragma unroll
-        for (int m = 0; m < ND; ++m) xi[m] = g.xt[(DIR * ND + m) * g.NP + pq];
+        for (int m = 0; m < ND; ++m) xi[m] = T(g.xt[(DIR * ND + m) * g.NP + pq]);
       }
-      gbr_flux<ND, CART, DIR>(q, g, Wst, Wd, Wdd, omb, xi, F);
+      gbr_flux<ND, CART, DIR, T>(q, g, Wst, Wd, Wdd, omb, xi, F);
     } else if (ok) {
       long long hi = A.hBox.at(c[0], c[1], c[2]);
       long long hs = A.hBox.size();
 #pragma unroll
-      for (int v = 0; v < NV; ++v) F[v] = A.hflux[v * hs + hi];
+      for (int v = 0; v < NV; ++v) F[v] = T(A.hflux[v * hs + hi]);
     } else {
 #pragma unroll
-      for (int v = 0; v < NV; ++v) F[v] = 0.0;
+      for (int v = 0; v < NV; ++v) F[v] = T(0);
     }
 #pragma unroll
     for (int v = 0; v < NV; ++v) sF[IX(v, a, l, TL)] = F[v];
@@ -433,7 +348,7 @@ __global__ void __launch_bounds__(256) k_gbr_sweep(DevGrid g, GbrCfg q, StageArg
                                             : (long long)c[0] + (long long)g.n[0] * c[1]);
       long long nlin = g.N / n;
 #pragma unroll
-      for (int v = 0; v < NV; ++v) A.iface_out[((long long)v * nlin + line) * (n + 1) + (i + 1)] = F[v];
+      for (int v = 0; v < NV; ++v) A.iface_out[((long long)v * nlin + line) * (n + 1) + (i + 1)] = (double)F[v];
     }
   }
   __syncthreads();
@@ -450,7 +365,7 @@ __global__ void __launch_bounds__(256) k_gbr_sweep(DevGrid g, GbrCfg q, StageArg
     double out[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      double diff = sF[IX(v, a + 1, l, TL)] - sF[IX(v, a, l, TL)];
+      double diff = (double)sF[IX(v, a + 1, l, TL)] - (double)sF[IX(v, a, l, TL)];
       double tot = A.first ? diff : A.acc[v * g.N + qi] + diff;
       if (!A.last) {
         A.acc[v * g.N + qi] = tot;
@@ -539,7 +454,7 @@ __global__ void k_cfl_max(DevGrid g, const double* __restrict__ U, unsigned long
 }
 
 // dt = cfl / max rate; with a final time: clip to t_end - t and advance t.
-__global__ void k_cfl_finish(const unsigned long long* mx, double cfl, double* dt, double* t, double t_end) {
+static __global__ void k_cfl_finish(const unsigned long long* mx, double cfl, double* dt, double* t, double t_end) {
   double m = __longlong_as_double((long long)*mx);
   double d = cfl / m;
   if (t) {

@@ -9,16 +9,18 @@
 namespace cgk {
 
 struct LadBuffers {
-  double* gr = nullptr;     // physical gradients of (u_k, T, rho, e): nf*nd planes on b3 ([-3, n+2]^nd)
+  double* fb = nullptr;     // LAD fields (u_k, T, rho, e) on fbx ([-8, n+7]^nd)
+  double* gr = nullptr;     // physical gradients of the fields: nf*nd planes on b3 ([-3, n+2]^nd)
   double* dv = nullptr;     // dilatation on b3
   double* bt[2] = {nullptr, nullptr};  // beta* (ping-pong, interior)
   double* kp[2] = {nullptr, nullptr};  // kappa*
   double* Fn = nullptr;     // node fluxes along one direction: nv planes on fbox (positions [-2, n+1])
-  double* D = nullptr;      // compact flux derivative (nv planes, interior)
-  double* df[3] = {nullptr, nullptr, nullptr};  // C6: computational derivatives of the fields on b3
-  double* tmp = nullptr;    // filter ping-pong state
+  double* D = nullptr;      // C6 flux derivative along one direction (line buffer DLB)
+  double* df[3] = {nullptr, nullptr, nullptr};  // C6 computational derivatives of the fields (line buffers)
+  double* lines = nullptr;  // right-hand sides / solutions of the filter lines
   unsigned char* tr = nullptr;  // hybrid: troubled nodes on tbox ([-1, n]^nd)
-  Box b3, tbox, fbox[3], hbox[3];
+  Box fbx, b3, tbox, fbox[3], hbox[3];
+  LineBuf dfLB[3], DLB[3], filtLB[3];
 };
 
 // fields differentiated by LAD: velocities, T = gamma M^2 p / rho, rho, e = p / (rho (gamma-1))
@@ -33,6 +35,10 @@ __device__ __forceinline__ void lad_fields(const DevGrid& g, const double* w, do
   f[ND + 2] = p / (rho * g.gm1);
 }
 
+// the LAD fields at every node of the box fbx (ghosts by the boundary rule)
+template <int ND>
+__global__ void k_lad_fieldbuf(DevGrid g, const double* __restrict__ W, double* __restrict__ f, Box fbx);
+
 __device__ __forceinline__ void box_coords(const Box& b, long long e, int* c) {
   c[0] = (int)(e % b.ext[0]) - b.off[0];
   long long r = e / b.ext[0];
@@ -43,34 +49,50 @@ __device__ __forceinline__ void box_coords(const Box& b, long long e, int* c) {
 #define BOX_LOOP(b, e) \
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (b).size(); e += (long long)gridDim.x * blockDim.x)
 
-// Physical gradients and dilatation on b3.  E4 computes the computational
-// derivatives in place; C6 reads them from the compact line solves (df).
-template <int ND, bool CART, bool C6>
-__global__ void k_lad_grad(DevGrid g, const double* __restrict__ W, const double* __restrict__ df0,
-                           const double* __restrict__ df1, const double* __restrict__ df2, double* __restrict__ gr,
-                           double* __restrict__ dv, Box b3, const int* guard, int want) {
+template <int ND>
+__global__ void k_lad_fieldbuf(DevGrid g, const double* __restrict__ W, double* __restrict__ f, Box fbx) {
   constexpr int NV = ND + 2, NF = ND + 3;
+  long long fs = fbx.size();
+  BOX_LOOP(fbx, e) {
+    int c[3];
+    box_coords(fbx, e, c);
+    double w[NV], fl[NF];
+    load_state<ND>(g, W, c[0], c[1], c[2], w);
+    lad_fields<ND>(g, w, fl);
+#pragma unroll
+    for (int v = 0; v < NF; ++v) f[v * fs + e] = fl[v];
+  }
+}
+
+// Physical gradients and dilatation on b3.  E4 differences the field buffer;
+// C6 reads the compact derivatives from the line buffers df.
+template <int ND, bool CART, bool C6>
+__global__ void k_lad_grad(DevGrid g, const double* __restrict__ fb, Box fbx, const double* __restrict__ df0,
+                           const double* __restrict__ df1, const double* __restrict__ df2, LineBuf lb0, LineBuf lb1,
+                           LineBuf lb2, double* __restrict__ gr, double* __restrict__ dv, Box b3, const int* guard,
+                           int want) {
+  constexpr int NF = ND + 3;
   if (guard && *guard != want) return;
-  long long bs = b3.size();
+  long long bs = b3.size(), fs = fbx.size();
   BOX_LOOP(b3, e) {
     int c[3];
     box_coords(b3, e, c);
     double d[3][NF];  // d[l][f] = d f / d xi_l
+    long long q = fbx.at(c[0], c[1], c[2]);
 #pragma unroll
     for (int l = 0; l < ND; ++l) {
       if (C6) {
         const double* df = l == 0 ? df0 : (l == 1 ? df1 : df2);
+        const LineBuf& lb = l == 0 ? lb0 : (l == 1 ? lb1 : lb2);
 #pragma unroll
-        for (int f = 0; f < NF; ++f) d[l][f] = df[f * bs + e];
+        for (int f = 0; f < NF; ++f) d[l][f] = df[lb.at(f, c[l], c)];
       } else {
-        double fm2[NF], fm1[NF], fp1[NF], fp2[NF], w[NV];
-        int cc[3] = {c[0], c[1], c[2]};
-        cc[l] = c[l] - 2; load_state<ND>(g, W, cc[0], cc[1], cc[2], w); lad_fields<ND>(g, w, fm2);
-        cc[l] = c[l] - 1; load_state<ND>(g, W, cc[0], cc[1], cc[2], w); lad_fields<ND>(g, w, fm1);
-        cc[l] = c[l] + 1; load_state<ND>(g, W, cc[0], cc[1], cc[2], w); lad_fields<ND>(g, w, fp1);
-        cc[l] = c[l] + 2; load_state<ND>(g, W, cc[0], cc[1], cc[2], w); lad_fields<ND>(g, w, fp2);
+        long long st = l == 0 ? 1 : (l == 1 ? (long long)fbx.ext[0] : (long long)fbx.ext[0] * fbx.ext[1]);
 #pragma unroll
-        for (int f = 0; f < NF; ++f) d[l][f] = d4(fm2[f], fm1[f], fp1[f], fp2[f]);
+        for (int f = 0; f < NF; ++f) {
+          const double* p = fb + f * fs + q;
+          d[l][f] = d4(p[-2 * st], p[-st], p[st], p[2 * st]);
+        }
       }
     }
     double div = 0.0;
@@ -95,11 +117,11 @@ __global__ void k_lad_grad(DevGrid g, const double* __restrict__ W, const double
       for (int f = 0; f < NF; ++f)
 #pragma unroll
         for (int m = 0; m < ND; ++m) {
-          double s = xm[0][m] * d[0][f];
+          double sm = xm[0][m] * d[0][f];
 #pragma unroll
-          for (int l = 1; l < ND; ++l) s = s + xm[l][m] * d[l][f];
-          gr[(f * ND + m) * bs + e] = s;
-          if (f < ND && m == f) div = (f == 0) ? s : div + s;
+          for (int l = 1; l < ND; ++l) sm = sm + xm[l][m] * d[l][f];
+          gr[(f * ND + m) * bs + e] = sm;
+          if (f < ND && m == f) div = (f == 0) ? sm : div + sm;
         }
     }
     dv[e] = div;
@@ -110,12 +132,13 @@ __global__ void k_lad_grad(DevGrid g, const double* __restrict__ W, const double
 // beta* = C_beta rho f_sw |sum_l d4(div)_l Delta_{l,beta}^2|,
 // kappa* = C_kappa (rho c / T) |sum_l d4(e)_l Delta_{l,kappa}|.
 template <int ND, bool CART>
-__global__ void k_lad_coef(DevGrid g, const double* __restrict__ W, const double* __restrict__ gr,
-                           const double* __restrict__ dv, Box b3, double c_beta, double c_kappa,
-                           double* __restrict__ bt, double* __restrict__ kp, const int* guard, int want) {
+__global__ void k_lad_coef(DevGrid g, const double* __restrict__ W, const double* __restrict__ fb, Box fbx,
+                           const double* __restrict__ gr, const double* __restrict__ dv, Box b3, double c_beta,
+                           double c_kappa, double* __restrict__ bt, double* __restrict__ kp, const int* guard,
+                           int want) {
   constexpr int NV = ND + 2, IP = ND + 1;
   if (guard && *guard != want) return;
-  long long bs = b3.size();
+  long long bs = b3.size(), fs = fbx.size();
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < g.N; q += (long long)gridDim.x * blockDim.x) {
     int c[3];
     c[0] = (int)(q % g.n[0]);
@@ -126,7 +149,8 @@ __global__ void k_lad_coef(DevGrid g, const double* __restrict__ W, const double
 #pragma unroll
     for (int v = 0; v < NV; ++v) w[v] = W[v * g.N + q];
     double rho = w[0], p = w[IP];
-    double T = g.gm2 * p / rho;
+    long long fq = fbx.at(c[0], c[1], c[2]);
+    double T = fb[ND * fs + fq];
     double cs = sqrt(g.gamma * p / rho);
     double div = dv[e0];
     double curl2 = 0.0;
@@ -153,16 +177,9 @@ __global__ void k_lad_coef(DevGrid g, const double* __restrict__ W, const double
     for (int l = 0; l < ND; ++l) {
       long long st = l == 0 ? 1 : (l == 1 ? (long long)b3.ext[0] : (long long)b3.ext[0] * b3.ext[1]);
       double d4d = (dv[e0 - 2 * st] + dv[e0 + 2 * st]) - 4.0 * (dv[e0 - st] + dv[e0 + st]) + 6.0 * div;
-      double ev[5];
-#pragma unroll
-      for (int t = -2; t <= 2; ++t) {
-        int cc[3] = {c[0], c[1], c[2]};
-        cc[l] += t;
-        double ww[NV];
-        load_state<ND>(g, W, cc[0], cc[1], cc[2], ww);
-        ev[t + 2] = ww[IP] / (ww[0] * g.gm1);
-      }
-      double d4e = (ev[0] + ev[4]) - 4.0 * (ev[1] + ev[3]) + 6.0 * ev[2];
+      long long fst = l == 0 ? 1 : (l == 1 ? (long long)fbx.ext[0] : (long long)fbx.ext[0] * fbx.ext[1]);
+      const double* ev = fb + (ND + 2) * fs + fq;
+      double d4e = (ev[-2 * fst] + ev[2 * fst]) - 4.0 * (ev[-fst] + ev[fst]) + 6.0 * ev[0];
       double pr, pe;
       if (CART) {
         pr = g.ch[l] * G(ND + 1, l);
@@ -320,7 +337,7 @@ __device__ __forceinline__ void lad_epilogue(const DevGrid& g, const StageArgs& 
 // E4 divergence of the node fluxes along l (explicit) or the compact result D.
 template <int ND>
 __global__ void k_lad_div(DevGrid g, int l, const double* __restrict__ Fn, Box fb, const double* __restrict__ D,
-                          StageArgs A, const int* guard, int want) {
+                          LineBuf DL, StageArgs A, const int* guard, int want) {
   constexpr int NV = ND + 2;
   if (guard && *guard != want) return;
   long long fs = fb.size();
@@ -332,7 +349,7 @@ __global__ void k_lad_div(DevGrid g, int l, const double* __restrict__ Fn, Box f
     double Dv[NV];
     if (D) {
 #pragma unroll
-      for (int v = 0; v < NV; ++v) Dv[v] = D[v * g.N + q];
+      for (int v = 0; v < NV; ++v) Dv[v] = D[DL.at(v, c[l], c)];
     } else {
       long long e = fb.at(c[0], c[1], c[2]);
       long long st = l == 0 ? 1 : (l == 1 ? (long long)fb.ext[0] : (long long)fb.ext[0] * fb.ext[1]);
@@ -343,167 +360,6 @@ __global__ void k_lad_div(DevGrid g, int l, const double* __restrict__ Fn, Box f
       }
     }
     lad_epilogue<ND>(g, A, q, c, Dv);
-  }
-}
-
-// Compact (Thomas) solve of one line: rows [0, m-1] <-> positions lo .. lo+m-1
-// (non-periodic: explicit E4 closure rows 0 and m-1; periodic: cyclic on
-// [0, n-1]).  rhsfn(x) gives the interior right-hand side at position x,
-// e4fn(x) the closure value, out(x) the result slot.
-template <typename RHS, typename E4F, typename OUT>
-__device__ __forceinline__ void thomas_line(const LineCoef& lc, RHS rhsfn, E4F e4fn, OUT out) {
-  const double a = lc.a;
-  int m = lc.m;
-  if (!lc.periodic) {
-    int lo = lc.lo;
-    double dp = e4fn(lo);
-    out(lo) = dp;
-    for (int i = 1; i < m - 1; ++i) {
-      dp = (rhsfn(lo + i) - a * dp) / lc.den[i];
-      out(lo + i) = dp;
-    }
-    double x = e4fn(lo + m - 1);
-    out(lo + m - 1) = x;
-    for (int i = m - 2; i >= 0; --i) {
-      double& o = out(lo + i);
-      x = o - lc.cp[i] * x;
-      o = x;
-    }
-  } else {
-    double dp = rhsfn(0) / 2.0;
-    out(0) = dp;
-    for (int i = 1; i < m; ++i) {
-      dp = (rhsfn(i) - a * dp) / lc.den[i];
-      out(i) = dp;
-    }
-    const double xlast = dp;
-    double x = dp;
-    for (int i = m - 2; i >= 0; --i) {
-      double& o = out(i);
-      x = o - lc.cp[i] * x;
-      o = x;
-    }
-    double fact = (out(0) + a * xlast / lc.gam) / lc.fden;
-    for (int i = 0; i < m; ++i) {
-      double& o = out(i);
-      o = o - fact * lc.z[i];
-    }
-  }
-}
-
-// C6 computational derivatives of the LAD fields along l for lines on b3 in
-// the other directions; the system spans [-6, n+5] (or is cyclic); results
-// at positions [-3, n+2] are kept (df on b3).
-template <int ND>
-__global__ void k_lad_c6_fields(DevGrid g, int l, const double* __restrict__ W, LineCoef lc, double* __restrict__ work,
-                                long long wstride, double* __restrict__ df, Box b3) {
-  constexpr int NV = ND + 2, NF = ND + 3;
-  int o1 = (l + 1) % 3, o2 = (l + 2) % 3;
-  int e1 = b3.ext[o1], e2 = b3.ext[o2];
-  long long nl = (long long)e1 * e2 * NF;
-  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= nl) return;
-  int f = (int)(t % NF);
-  long long r = t / NF;
-  int c[3];
-  c[o1] = (int)(r % e1) - b3.off[o1];
-  c[o2] = (int)(r / e1) - b3.off[o2];
-  int n = g.n[l];
-  double* wk = work + (t / NF) * wstride * NF + (long long)f * wstride;  // scratch line of length n + 16
-  auto fv = [&](int x) {
-    int cc[3] = {c[0], c[1], c[2]};
-    cc[l] = x;
-    double w[NV], fl[NF];
-    load_state<ND>(g, W, cc[0], cc[1], cc[2], w);
-    lad_fields<ND>(g, w, fl);
-    return fl[f];
-  };
-  auto rhs = [&](int x) {
-    return (7.0 / 9.0) * (fv(x + 1) - fv(x - 1)) + (1.0 / 36.0) * (fv(x + 2) - fv(x - 2));
-  };
-  auto e4 = [&](int x) { return d4(fv(x - 2), fv(x - 1), fv(x + 1), fv(x + 2)); };
-  auto out = [&](int x) -> double& { return wk[x + 8]; };
-  thomas_line(lc, rhs, e4, out);
-  long long bs = b3.size();
-  for (int x = -3; x <= n + 2; ++x) {
-    int cc[3] = {c[0], c[1], c[2]};
-    cc[l] = x;
-    double v = lc.periodic ? wk[((x % n) + n) % n + 8] : wk[x + 8];
-    df[f * bs + b3.at(cc[0], cc[1], cc[2])] = v;
-  }
-}
-
-// C6 derivative of the node fluxes along l on interior lines: system on
-// [0, n-1] with E4 closure rows (or cyclic); D gets the interior values.
-template <int ND>
-__global__ void k_lad_c6_flux(DevGrid g, int l, const double* __restrict__ Fn, Box fb, LineCoef lc,
-                              double* __restrict__ D) {
-  constexpr int NV = ND + 2;
-  int o1 = (l + 1) % 3, o2 = (l + 2) % 3;
-  int e1 = g.n[o1], e2 = g.n[o2];
-  long long nl = (long long)e1 * e2 * NV;
-  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= nl) return;
-  int v = (int)(t % NV);
-  long long r = t / NV;
-  int c[3];
-  c[o1] = (int)(r % e1);
-  c[o2] = (int)(r / e1);
-  long long fs = fb.size();
-  auto f = [&](int x) {
-    int cc[3] = {c[0], c[1], c[2]};
-    cc[l] = x;
-    return Fn[v * fs + fb.at(cc[0], cc[1], cc[2])];
-  };
-  auto rhs = [&](int x) { return (7.0 / 9.0) * (f(x + 1) - f(x - 1)) + (1.0 / 36.0) * (f(x + 2) - f(x - 2)); };
-  auto e4 = [&](int x) { return d4(f(x - 2), f(x - 1), f(x + 1), f(x + 2)); };
-  auto out = [&](int x) -> double& {
-    int cc[3] = {c[0], c[1], c[2]};
-    cc[l] = x;
-    return D[v * g.N + (cc[0] + (long long)g.n[0] * (cc[1] + (long long)g.n[1] * cc[2]))];
-  };
-  thomas_line(lc, rhs, e4, out);
-}
-
-// Eighth-order implicit filter of the conserved state along l (LAD-C6, after
-// the last stage): non-periodic system on [-1, n] whose end rows keep the
-// ghost values, periodic cyclic on [0, n-1].  Reads Uin (ghosts by the
-// conserved-variable boundary rule), writes Uout on interior lines.
-template <int ND>
-__global__ void k_filter(DevGrid g, int l, const double* __restrict__ Uin, LineCoef lc, double b0, double b1,
-                         double b2, double b3c, double b4, double* __restrict__ work, double* __restrict__ Uout) {
-  constexpr int NV = ND + 2;
-  int o1 = (l + 1) % 3, o2 = (l + 2) % 3;
-  int e1 = g.n[o1], e2 = g.n[o2];
-  long long nl = (long long)e1 * e2 * NV;
-  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= nl) return;
-  int v = (int)(t % NV);
-  long long r = t / NV;
-  int c[3];
-  c[o1] = (int)(r % e1);
-  c[o2] = (int)(r / e1);
-  int n = g.n[l];
-  auto f = [&](int x) {
-    int cc[3] = {c[0], c[1], c[2]};
-    cc[l] = x;
-    double w[NV];
-    load_state<ND, true>(g, Uin, cc[0], cc[1], cc[2], w);
-    return w[v];
-  };
-  auto rhs = [&](int x) {
-    int y = x;
-    return b0 * f(y) + b1 * (f(y + 1) + f(y - 1)) + b2 * (f(y + 2) + f(y - 2)) + b3c * (f(y + 3) + f(y - 3)) +
-           b4 * (f(y + 4) + f(y - 4));
-  };
-  auto ends = [&](int x) { return x == lc.lo ? f(-1) : f(n); };
-  double* wk = work + t * (long long)(n + 2);
-  auto out = [&](int x) -> double& { return wk[lc.periodic ? x : x - lc.lo]; };
-  thomas_line(lc, rhs, ends, out);
-  for (int x = 0; x < n; ++x) {
-    int cc[3] = {c[0], c[1], c[2]};
-    cc[l] = x;
-    Uout[v * g.N + (cc[0] + (long long)g.n[0] * (cc[1] + (long long)g.n[1] * cc[2]))] = wk[lc.periodic ? x : x + 1];
   }
 }
 

@@ -8,6 +8,7 @@ static int lad_alloc(cg_solver* s) {
   if (sch != CG_LAD_E4 && sch != CG_LAD_C6 && sch != CG_HYBRID) return CG_OK;
   LadBuffers& L = s->lad;
   int nd = s->nd, nv = s->nv, nf = nd + 3;
+  L.fbx = make_box(s, 8, -1, 8);
   L.b3 = make_box(s, 3, -1, 3);
   L.tbox = make_box(s, 1, -1, 1);
   size_t fmax = 0;
@@ -21,28 +22,28 @@ static int lad_alloc(cg_solver* s) {
     fmax = std::max(fmax, (size_t)L.fbox[d].size());
   }
   int rc;
-  if ((rc = dalloc(&L.gr, (size_t)nf * nd * L.b3.size())) || (rc = dalloc(&L.dv, (size_t)L.b3.size())) ||
-      (rc = dalloc(&L.bt[0], (size_t)s->N)) || (rc = dalloc(&L.bt[1], (size_t)s->N)) ||
-      (rc = dalloc(&L.kp[0], (size_t)s->N)) || (rc = dalloc(&L.kp[1], (size_t)s->N)) ||
-      (rc = dalloc(&L.Fn, (size_t)nv * fmax)))
+  if ((rc = dalloc(&L.fb, (size_t)nf * L.fbx.size())) || (rc = dalloc(&L.gr, (size_t)nf * nd * L.b3.size())) ||
+      (rc = dalloc(&L.dv, (size_t)L.b3.size())) || (rc = dalloc(&L.bt[0], (size_t)s->N)) ||
+      (rc = dalloc(&L.bt[1], (size_t)s->N)) || (rc = dalloc(&L.kp[0], (size_t)s->N)) ||
+      (rc = dalloc(&L.kp[1], (size_t)s->N)) || (rc = dalloc(&L.Fn, (size_t)nv * fmax)))
     return rc;
   if (sch == CG_LAD_C6) {
-    if ((rc = dalloc(&L.D, (size_t)nv * s->N)) || (rc = dalloc(&L.tmp, (size_t)nv * s->N))) return rc;
+    size_t dmax = 0, fl = 0;
     for (int d = 0; d < nd; ++d) {
-      if ((rc = dalloc(&L.df[d], (size_t)nf * L.b3.size()))) return rc;
       bool cyc = s->grid->bc[d][0] == CG_BC_PERIODIC;
       int n = s->dg.n[d];
       if (cyc && n < 3) return fail(CG_ERR_INVALID_ARG, "periodic compact lines need n >= 3");
+      L.dfLB[d] = make_lines(s, d, -6, n + 12, 3);
+      L.DLB[d] = make_lines(s, d, 0, n, 0);
+      L.filtLB[d] = make_lines(s, d, -1, n + 2, 0);
+      if ((rc = dalloc(&L.df[d], (size_t)nf * L.dfLB[d].m * L.dfLB[d].nl))) return rc;
+      dmax = std::max(dmax, (size_t)nv * (size_t)L.DLB[d].m * (size_t)L.DLB[d].nl);
+      fl = std::max(fl, (size_t)nv * (size_t)L.filtLB[d].m * (size_t)L.filtLB[d].nl);
       if ((rc = upload_line(s->c6grad[d], cyc ? n : n + 12, 1.0 / 3.0, cyc, -6))) return rc;
       if ((rc = upload_line(s->c6flux[d], n, 1.0 / 3.0, cyc, 0))) return rc;
       if ((rc = upload_line(s->filt[d], cyc ? n : n + 2, s->p.alpha_f, cyc, -1))) return rc;
-      // line scratch of the compact solves
-      int o1 = (d + 1) % 3, o2 = (d + 2) % 3;
-      size_t lines_f = (size_t)L.b3.ext[o1] * L.b3.ext[o2] * nf * (size_t)(n + 16);
-      size_t lines_u = (size_t)s->dg.n[o1] * s->dg.n[o2] * nv * (size_t)(n + 2);
-      s->work_elems = std::max(s->work_elems, std::max(lines_f, lines_u));
     }
-    if ((rc = dalloc(&s->work, s->work_elems))) return rc;
+    if ((rc = dalloc(&L.D, dmax)) || (rc = dalloc(&L.lines, fl))) return rc;
   }
   if (sch == CG_HYBRID) {
     if ((rc = dalloc(&L.tr, (size_t)L.tbox.size()))) return rc;
@@ -53,7 +54,7 @@ static int lad_alloc(cg_solver* s) {
 }
 
 static void lad_free(LadBuffers& L) {
-  double* bufs[] = {L.gr, L.dv, L.bt[0], L.bt[1], L.kp[0], L.kp[1], L.Fn, L.D, L.df[0], L.df[1], L.df[2], L.tmp};
+  double* bufs[] = {L.fb, L.gr, L.dv, L.bt[0], L.bt[1], L.kp[0], L.kp[1], L.Fn, L.D, L.df[0], L.df[1], L.df[2], L.lines};
   for (double* b : bufs)
     if (b) cudaFree(b);
   if (L.tr) cudaFree(L.tr);
@@ -65,25 +66,35 @@ template <int ND>
 static int lad_coeffs_run(cg_solver* s, int dkind, cudaStream_t st, const int* guard, int want) {
   LadBuffers& L = s->lad;
   bool c6 = dkind == 3;
+  k_lad_fieldbuf<ND><<<grid_blocks(L.fbx.size(), 256), 256, 0, st>>>(s->dg, s->W, L.fb, L.fbx);
+  s->launches++;
   if (c6) {
+    ThomasJobs J;
+    J.njobs = ND;
+    J.start[0] = 0;
     for (int l = 0; l < ND; ++l) {
-      int o1 = (l + 1) % 3, o2 = (l + 2) % 3;
-      long long lines = (long long)L.b3.ext[o1] * L.b3.ext[o2] * (ND + 3);
-      k_lad_c6_fields<ND><<<(unsigned)((lines + 127) / 128), 128, 0, st>>>(s->dg, l, s->W, s->c6grad[l].lc, s->work,
-                                                                         s->dg.n[l] + 16, L.df[l], L.b3);
+      const LineBuf& lb = L.dfLB[l];
+      k_rhs_c6<<<grid_blocks((long long)lb.m * lb.nl, 256), 256, 0, st>>>(L.fb, L.fbx, ND + 3, lb, L.df[l]);
       s->launches++;
+      J.lc[l] = s->c6grad[l].lc;
+      J.x[l] = L.df[l];
+      J.nl[l] = lb.nl;
+      J.ncomp[l] = ND + 3;
+      J.start[l + 1] = J.start[l] + lb.nl * (ND + 3);
     }
+    launch_thomas(J, st);
+    s->launches++;
   }
   int gb = grid_blocks(L.b3.size(), 128);
   if (s->dg.curv) {
-    if (c6) k_lad_grad<ND, false, true><<<gb, 128, 0, st>>>(s->dg, s->W, L.df[0], L.df[1], L.df[2], L.gr, L.dv, L.b3, guard, want);
-    else k_lad_grad<ND, false, false><<<gb, 128, 0, st>>>(s->dg, s->W, L.df[0], L.df[1], L.df[2], L.gr, L.dv, L.b3, guard, want);
-    k_lad_coef<ND, false><<<grid_blocks(s->N, 128), 128, 0, st>>>(s->dg, s->W, L.gr, L.dv, L.b3, s->p.c_beta,
+    if (c6) k_lad_grad<ND, false, true><<<gb, 128, 0, st>>>(s->dg, L.fb, L.fbx, L.df[0], L.df[1], L.df[2], L.dfLB[0], L.dfLB[1], L.dfLB[2], L.gr, L.dv, L.b3, guard, want);
+    else k_lad_grad<ND, false, false><<<gb, 128, 0, st>>>(s->dg, L.fb, L.fbx, L.df[0], L.df[1], L.df[2], L.dfLB[0], L.dfLB[1], L.dfLB[2], L.gr, L.dv, L.b3, guard, want);
+    k_lad_coef<ND, false><<<grid_blocks(s->N, 128), 128, 0, st>>>(s->dg, s->W, L.fb, L.fbx, L.gr, L.dv, L.b3, s->p.c_beta,
                                                                   s->p.c_kappa, L.bt[0], L.kp[0], guard, want);
   } else {
-    if (c6) k_lad_grad<ND, true, true><<<gb, 128, 0, st>>>(s->dg, s->W, L.df[0], L.df[1], L.df[2], L.gr, L.dv, L.b3, guard, want);
-    else k_lad_grad<ND, true, false><<<gb, 128, 0, st>>>(s->dg, s->W, L.df[0], L.df[1], L.df[2], L.gr, L.dv, L.b3, guard, want);
-    k_lad_coef<ND, true><<<grid_blocks(s->N, 128), 128, 0, st>>>(s->dg, s->W, L.gr, L.dv, L.b3, s->p.c_beta,
+    if (c6) k_lad_grad<ND, true, true><<<gb, 128, 0, st>>>(s->dg, L.fb, L.fbx, L.df[0], L.df[1], L.df[2], L.dfLB[0], L.dfLB[1], L.dfLB[2], L.gr, L.dv, L.b3, guard, want);
+    else k_lad_grad<ND, true, false><<<gb, 128, 0, st>>>(s->dg, L.fb, L.fbx, L.df[0], L.df[1], L.df[2], L.dfLB[0], L.dfLB[1], L.dfLB[2], L.gr, L.dv, L.b3, guard, want);
+    k_lad_coef<ND, true><<<grid_blocks(s->N, 128), 128, 0, st>>>(s->dg, s->W, L.fb, L.fbx, L.gr, L.dv, L.b3, s->p.c_beta,
                                                                  s->p.c_kappa, L.bt[0], L.kp[0], guard, want);
   }
   s->launches += 2;
@@ -123,14 +134,14 @@ static int lad_pass(cg_solver* s, int dkind, StageArgs A, cudaStream_t st, const
     A.first = l == 0;
     A.last = l == ND - 1;
     const double* D = nullptr;
+    LineBuf DL = L.DLB[l];
     if (dkind == 3) {
-      int o1 = (l + 1) % 3, o2 = (l + 2) % 3;
-      long long lines = (long long)s->dg.n[o1] * s->dg.n[o2] * (ND + 2);
-      k_lad_c6_flux<ND><<<(unsigned)((lines + 127) / 128), 128, 0, st>>>(s->dg, l, L.Fn, L.fbox[l], s->c6flux[l].lc, L.D);
-      s->launches++;
+      k_rhs_c6<<<grid_blocks((long long)DL.m * DL.nl, 256), 256, 0, st>>>(L.Fn, L.fbox[l], ND + 2, DL, L.D);
+      k_thomas<<<(unsigned)((DL.nl * (ND + 2) + 31) / 32), 32, 0, st>>>(s->c6flux[l].lc, L.D, DL.nl, ND + 2);
+      s->launches += 2;
       D = L.D;
     }
-    k_lad_div<ND><<<grid_blocks(s->N, 256), 256, 0, st>>>(s->dg, l, L.Fn, L.fbox[l], D, A, guard, want);
+    k_lad_div<ND><<<grid_blocks(s->N, 256), 256, 0, st>>>(s->dg, l, L.Fn, L.fbox[l], D, DL, A, guard, want);
     s->launches++;
   }
   return CG_OK;
@@ -181,7 +192,7 @@ static int lad_stage(cg_solver* s, const double* Uc, StageArgs A, cudaStream_t s
     H.hflux = s->hflux[d];
     H.hBox = L.hbox[d];
     H.Gd = nullptr;
-    H.gdBox = s->gdBox[d];
+    H.gdLB = s->gdLB[d];
     H.iface_out = (s->iface_out && s->iface_dir == d) ? s->iface_out : nullptr;
     if (s->dg.curv) rc = sweep_dir<ND, false, false>(s, d, H, st);
     else rc = sweep_dir<ND, true, false>(s, d, H, st);
@@ -200,23 +211,17 @@ static void filter_coeffs(double af, double b[5]) {
 
 template <int ND>
 static int lad_filter(cg_solver* s, double* U, cudaStream_t st) {
-  if (!s->lad.tmp) return fail(CG_ERR_UNSUPPORTED, "the implicit filter belongs to LAD-C6");
+  if (!s->lad.lines) return fail(CG_ERR_UNSUPPORTED, "the implicit filter belongs to LAD-C6");
   double b[5];
   filter_coeffs(s->p.alpha_f, b);
-  const double* in = U;
-  double* bufs[2] = {s->lad.tmp, U};
-  int cur = 0;
   for (int l = 0; l < ND; ++l) {
-    int o1 = (l + 1) % 3, o2 = (l + 2) % 3;
-    long long lines = (long long)s->dg.n[o1] * s->dg.n[o2] * (ND + 2);
-    double* out = bufs[cur];
-    k_filter<ND><<<(unsigned)((lines + 127) / 128), 128, 0, st>>>(s->dg, l, in, s->filt[l].lc, b[0], b[1], b[2], b[3],
-                                                                b[4], s->work, out);
-    s->launches++;
-    in = out;
-    cur = 1 - cur;
+    const LineBuf& lb = s->lad.filtLB[l];
+    k_rhs_filter<ND><<<grid_blocks((long long)lb.m * lb.nl, 256), 256, 0, st>>>(s->dg, U, lb, b[0], b[1], b[2], b[3],
+                                                                              b[4], s->lad.lines);
+    k_thomas<<<(unsigned)((lb.nl * (ND + 2) + 31) / 32), 32, 0, st>>>(s->filt[l].lc, s->lad.lines, lb.nl, ND + 2);
+    k_filter_store<ND><<<grid_blocks(s->N, 256), 256, 0, st>>>(s->dg, s->lad.lines, lb, U);
+    s->launches += 3;
   }
-  if (in != U) CG_CUDA(cudaMemcpyAsync(U, in, sizeof(double) * s->nv * s->N, cudaMemcpyDeviceToDevice, st));
   return CG_OK;
 }
 

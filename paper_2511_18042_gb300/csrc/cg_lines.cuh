@@ -1,0 +1,183 @@
+// Batched tridiagonal line solves of the compact schemes and the implicit
+// filter.  A parallel kernel builds every right-hand side into a line-major
+// buffer ([component][row][line], lines contiguous, so a warp of 32 lines
+// reads and writes 32 consecutive values); k_thomas then runs only the
+// recurrence, one thread per (line, component), with the pivots precomputed
+// on the host: dp_i = (r_i - a dp_{i-1}) / den_i, x_i = dp_i - cp_i x_{i+1}
+// (cyclic lines add the Sherman-Morrison correction).  Every row of every line
+// is processed in the order of the sequential elimination, so the result is
+// the one the line's own Thomas elimination gives.
+#pragma once
+#include "cg_kernels.cuh"
+
+namespace cgk {
+
+// Up to three independent families of lines solved by one launch (e.g. the x
+// and y lines of a stage): job j covers columns [start_j, start_j + nl_j * ncomp_j).
+struct ThomasJobs {
+  LineCoef lc[3];
+  double* x[3];
+  long long nl[3];
+  int ncomp[3];
+  long long start[4];
+  int njobs;
+};
+
+__device__ __forceinline__ void thomas_column(const LineCoef& lc, double* __restrict__ x, long long nl, long long t);
+
+// Thomas recurrence over every column (line x component) of x (in place).
+__global__ void k_thomas(LineCoef lc, double* __restrict__ x, long long nl, int ncomp) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= nl * ncomp) return;
+  thomas_column(lc, x, nl, t);
+}
+
+__global__ void k_thomas_jobs(ThomasJobs J) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  int j = 0;
+  while (j + 1 < J.njobs && t >= J.start[j + 1]) ++j;
+  if (t >= J.start[J.njobs]) return;
+  thomas_column(J.lc[j], J.x[j], J.nl[j], t - J.start[j]);
+}
+
+__device__ __forceinline__ void thomas_column(const LineCoef& lc, double* __restrict__ x, long long nl, long long t) {
+  long long comp = t / nl, L = t % nl;
+  double* col = x + comp * lc.m * nl + L;
+  const double a = lc.a;
+  const int m = lc.m;
+  if (!lc.periodic) {
+    double dp = col[0];
+    for (int i = 1; i < m - 1; ++i) {
+      dp = (col[(long long)i * nl] - a * dp) / lc.den[i];
+      col[(long long)i * nl] = dp;
+    }
+    double xv = col[(long long)(m - 1) * nl];
+    for (int i = m - 2; i >= 0; --i) {
+      xv = col[(long long)i * nl] - lc.cp[i] * xv;
+      col[(long long)i * nl] = xv;
+    }
+  } else {
+    double dp = col[0] / 2.0;
+    col[0] = dp;
+    for (int i = 1; i < m; ++i) {
+      dp = (col[(long long)i * nl] - a * dp) / lc.den[i];
+      col[(long long)i * nl] = dp;
+    }
+    const double xlast = dp;
+    double xv = dp;
+    for (int i = m - 2; i >= 0; --i) {
+      xv = col[(long long)i * nl] - lc.cp[i] * xv;
+      col[(long long)i * nl] = xv;
+    }
+    double fact = (xv + a * xlast / lc.gam) / lc.fden;
+    for (int i = 0; i < m; ++i) col[(long long)i * nl] = col[(long long)i * nl] - fact * lc.z[i];
+  }
+}
+
+#define LB_LOOP(lb, e) \
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)(lb).m * (lb).nl; \
+       e += (long long)gridDim.x * blockDim.x)
+
+// MIG4 right-hand sides of the primitives along lb.d: 3/4 (W_{i+1} - W_{i-1}),
+// E4 closure rows at both ends of a non-periodic line.
+template <int ND>
+__global__ void k_rhs_mig4(DevGrid g, const double* __restrict__ W, LineBuf lb, double* __restrict__ r) {
+  constexpr int NV = ND + 2;
+  LB_LOOP(lb, e) {
+    int i = (int)(e / lb.nl);
+    long long L = e % lb.nl;
+    int c[3] = {0, 0, 0};
+    lb.coords(L, c);
+    int pos = lb.periodic ? i : lb.lo + i;
+    bool closure = !lb.periodic && (i == 0 || i == lb.m - 1);
+    double wp1[NV], wm1[NV];
+    int cc[3] = {c[0], c[1], c[2]};
+    cc[lb.d] = pos + 1; load_state<ND>(g, W, cc[0], cc[1], cc[2], wp1);
+    cc[lb.d] = pos - 1; load_state<ND>(g, W, cc[0], cc[1], cc[2], wm1);
+    if (closure) {
+      double wp2[NV], wm2[NV];
+      cc[lb.d] = pos + 2; load_state<ND>(g, W, cc[0], cc[1], cc[2], wp2);
+      cc[lb.d] = pos - 2; load_state<ND>(g, W, cc[0], cc[1], cc[2], wm2);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) r[((long long)v * lb.m + i) * lb.nl + L] = d4(wm2[v], wm1[v], wp1[v], wp2[v]);
+    } else {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) r[((long long)v * lb.m + i) * lb.nl + L] = 0.75 * (wp1[v] - wm1[v]);
+    }
+  }
+}
+
+// C6 right-hand sides of nc components of a field held on box fb (values at
+// positions up to two past the rows): 7/9 (f_{i+1} - f_{i-1}) + 1/36 (f_{i+2} - f_{i-2}),
+// E4 closure rows at both ends of a non-periodic line.  Periodic rows read the
+// field at wrapped positions through the box (fb covers the wrap).
+__global__ void k_rhs_c6(const double* __restrict__ f, Box fb, int nc, LineBuf lb, double* __restrict__ r) {
+  long long fs = fb.size();
+  long long st = lb.d == 0 ? 1 : (lb.d == 1 ? (long long)fb.ext[0] : (long long)fb.ext[0] * fb.ext[1]);
+  LB_LOOP(lb, e) {
+    int i = (int)(e / lb.nl);
+    long long L = e % lb.nl;
+    int c[3] = {0, 0, 0};
+    lb.coords(L, c);
+    c[lb.d] = lb.periodic ? i : lb.lo + i;
+    long long q = fb.at(c[0], c[1], c[2]);
+    bool closure = !lb.periodic && (i == 0 || i == lb.m - 1);
+    for (int v = 0; v < nc; ++v) {
+      const double* p = f + v * fs + q;
+      double rv = closure ? d4(p[-2 * st], p[-st], p[st], p[2 * st])
+                          : (7.0 / 9.0) * (p[st] - p[-st]) + (1.0 / 36.0) * (p[2 * st] - p[-2 * st]);
+      r[((long long)v * lb.m + i) * lb.nl + L] = rv;
+    }
+  }
+}
+
+// Implicit-filter right-hand sides of the conserved state along lb.d:
+// non-periodic rows 0 and m-1 hold the ghost values at -1 and n; rows 1..n
+// hold sum_{m=0}^{4} (a_m/2)(f_{i+m} + f_{i-m}) of positions 0..n-1.
+template <int ND>
+__global__ void k_rhs_filter(DevGrid g, const double* __restrict__ U, LineBuf lb, double b0, double b1, double b2,
+                             double b3, double b4, double* __restrict__ r) {
+  constexpr int NV = ND + 2;
+  LB_LOOP(lb, e) {
+    int i = (int)(e / lb.nl);
+    long long L = e % lb.nl;
+    int c[3] = {0, 0, 0};
+    lb.coords(L, c);
+    int pos = lb.periodic ? i : lb.lo + i;
+    bool closure = !lb.periodic && (i == 0 || i == lb.m - 1);
+    double w[9][NV];
+    int cc[3] = {c[0], c[1], c[2]};
+    if (closure) {
+      cc[lb.d] = pos;
+      load_state<ND, true>(g, U, cc[0], cc[1], cc[2], w[4]);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) r[((long long)v * lb.m + i) * lb.nl + L] = w[4][v];
+      continue;
+    }
+#pragma unroll
+    for (int t = -4; t <= 4; ++t) {
+      cc[lb.d] = pos + t;
+      load_state<ND, true>(g, U, cc[0], cc[1], cc[2], w[t + 4]);
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+      r[((long long)v * lb.m + i) * lb.nl + L] = b0 * w[4][v] + b1 * (w[5][v] + w[3][v]) + b2 * (w[6][v] + w[2][v]) +
+                                                 b3 * (w[7][v] + w[1][v]) + b4 * (w[8][v] + w[0][v]);
+  }
+}
+
+// Filtered line values back into the interior of the state.
+template <int ND>
+__global__ void k_filter_store(DevGrid g, const double* __restrict__ x, LineBuf lb, double* __restrict__ U) {
+  constexpr int NV = ND + 2;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < g.N; q += (long long)gridDim.x * blockDim.x) {
+    int c[3];
+    c[0] = (int)(q % g.n[0]);
+    c[1] = (int)((q / g.n[0]) % g.n[1]);
+    c[2] = (int)(q / ((long long)g.n[0] * g.n[1]));
+#pragma unroll
+    for (int v = 0; v < NV; ++v) U[v * g.N + q] = x[lb.at(v, c[lb.d], c)];
+  }
+}
+
+}  // namespace cgk

@@ -1,0 +1,67 @@
+"""Mixed precision form (FP32 reconstruction and fluxes, FP64 primitive
+recovery and RK accumulation) against the FP64 oracle.  Tolerance: density L1
+(mean absolute difference) <= 1e-5 on shocked 2D cases after 100 RK3 steps,
+and the same on the Sod tube at t = 0.2."""
+import numpy as np
+import pytest
+
+from paper_2511_18042_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+from tests.gpu_util import to_dev  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2511_18042_gb300 import api as a
+    return a
+
+
+def _l1_rho(Ug, Uo):
+    return float(np.abs(Ug[0].cpu().numpy() - Uo[0]).mean())
+
+
+@pytest.mark.parametrize("kw", [dict(scheme="MEG6"),
+                                dict(scheme="HYBRID", hybrid_mode=1, hyb_rho=0.0625, hybrid_sensor=1),
+                                dict(scheme="HYBRID", hybrid_mode=0, hyb_rho=0.12)])
+def test_mixed_triple_point_100_steps(orc, api, kw):
+    prob = inputs.triple_point(224, 96)
+    o = orc.Oracle(prob, **kw)
+    Uo, _, _ = o.advance(prob["U"], nsteps=100)
+    s = api.Solver.from_problem(prob, precision=1, **kw)
+    Ug = to_dev(prob["U"])
+    s.advance(Ug, nsteps=100)
+    err = _l1_rho(Ug, Uo)
+    assert err <= 1e-5, err
+    assert torch.isfinite(Ug).all()
+
+
+def test_mixed_sod(orc, api):
+    prob = inputs.shock_tube("sod", 400)
+    o = orc.Oracle(prob, scheme="MEG6", cfl=0.5)
+    Uo, _, _ = o.advance(prob["U"], t_end=0.2)
+    s = api.Solver.from_problem(prob, scheme="MEG6", precision=1, cfl=0.5)
+    Ug = to_dev(prob["U"])
+    s.advance(Ug, t_end=0.2)
+    assert _l1_rho(Ug, Uo) <= 1e-5
+
+
+def test_mixed_rhs_close_to_fp64(orc, api):
+    prob = inputs.triple_point(224, 96)
+    pre = orc.Oracle(prob, scheme="MEG6")
+    U, _, _ = pre.advance(prob["U"], nsteps=30)
+    s = api.Solver.from_problem(prob, scheme="MEG6", precision=1)
+    R = s.rhs(to_dev(U)).cpu().numpy()
+    Ro = pre.rhs(U)
+    for v in range(4):
+        assert np.abs(R[v] - Ro[v]).max() <= 1e-4 * np.abs(Ro[v]).max()
+
+
+def test_mixed_rejects_unsupported_schemes(api):
+    prob = inputs.triple_point(64, 32)
+    with pytest.raises(Exception):
+        api.Solver.from_problem(prob, scheme="LAD_C6", precision=1)
