@@ -39,6 +39,9 @@ SCHEMES = [
 ]
 MIXED = [
     ("MEG6_MIXED", dict(scheme="MEG6", precision=1)),
+    ("MIG4_MIXED", dict(scheme="MIG4", precision=1)),
+    ("LAD_E4_MIXED", dict(scheme="LAD_E4", precision=1)),
+    ("HYBRID_GLOBAL_MIXED", dict(scheme="HYBRID", hybrid_mode=0, hyb_rho=0.5 * 0.125, precision=1)),
     ("HYBRID_CELL_MIXED", dict(scheme="HYBRID", hybrid_mode=1, hyb_rho=0.5 * 0.125, hybrid_sensor=1, precision=1)),
 ]
 DEVELOP_STEPS = 200
@@ -202,6 +205,10 @@ def run_gpu(args):
         ms = time_mixed(api, torch, grid, base, dev, kw, args)
         mixed[n] = {"cell_updates_per_s": cells / (ms * 1e-3), "ms_per_rk3_step": ms}
 
+    sod = run_sod_latency(api, torch, dev)
+    batched = run_batched(api, torch, dev, args) if args.batched else None
+    serving = run_serving(args) if args.serving else None
+
     # roofline of the dominant kernel: the MEG6 interface sweep, timed alone
     roof = sweep_roofline(api, torch, grid, base, dev, args)
 
@@ -236,7 +243,9 @@ def run_gpu(args):
                                "from a developed state (200 MEG6 steps)" % len(names),
                    "schemes": names, "cells": cells, "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
-        "per_scheme": per_scheme, "mixed_precision": mixed, "roofline": roof, "e2e": e2e, "gpu_launches": launches // max(1, args.steps),
+        "per_scheme": per_scheme, "mixed_precision": mixed, "sod_latency": sod, "batched": batched,
+        "serving": serving,
+        "roofline": roof, "e2e": e2e, "gpu_launches": launches // max(1, args.steps),
         "gpu_launches_timed_total": launches, "wall_s_timed": wall, "clocks": clk.summary(),
     }
     if rank == 0 and args.cpu_baseline and ws == 1:
@@ -245,6 +254,114 @@ def run_gpu(args):
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+
+
+def _hybrid_kw(prob, precision):
+    """Per-instance troubled-cell thresholds of the quadrant problems: half the
+    smallest initial quadrant density and pressure."""
+    st = prob["quad_states"]
+    return dict(scheme="HYBRID", hybrid_mode=1, hybrid_sensor=1, hyb_rho=0.5 * float(st[:, 0].min()),
+                hyb_p=0.5 * float(st[:, 3].min()), precision=precision)
+
+
+def run_sod_latency(api, torch, dev, steps=200):
+    """Sod tube, 400 cells (latency-bound): microseconds per RK3 step (with the
+    device CFL time step) for MEG6 and LAD-C6, launched eagerly and replayed
+    as a one-member CUDA graph."""
+    from paper_2511_18042_gb300 import inputs
+    prob = inputs.shock_tube("sod", 400)
+    out = {}
+    for name, kw in (("MEG6", dict(scheme="MEG6")), ("LAD_C6", dict(scheme="LAD_C6", cfl=0.1))):
+        res = {}
+        for mode in ("eager", "graph"):
+            s = api.Solver.from_problem(prob, **kw)
+            U = torch.as_tensor(prob["U"], device=dev)
+            stream = torch.cuda.Stream()
+            with torch.cuda.stream(stream):
+                if mode == "graph":
+                    batch = api.Batch([s], [U])
+                    step = lambda: batch.step(stream)  # noqa: E731
+                else:
+                    step = lambda: api.multi_step([s], [U], stream=stream)  # noqa: E731
+                for _ in range(3):
+                    step()
+                stream.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(steps):
+                    step()
+                e1.record(stream)
+                stream.synchronize()
+            res[mode + "_us_per_step"] = e0.elapsed_time(e1) * 1e3 / steps
+        out[name] = res
+    return {"workload": "Sod tube 400 cells, %d RK3 steps from the initial state" % steps, **out}
+
+
+def run_batched(api, torch, dev, args, count=256, steps_per_solve=200):
+    """Batched 2D Riemann problems (256 uneven grids, 64^2..512^2, seed 0):
+    per-interface hybrid in the mixed form, all members advanced by one CUDA
+    graph replay per RK3 step, against the per-case FP64 loop on the same grids."""
+    from paper_2511_18042_gb300 import inputs
+    probs = inputs.batched_riemann(count=count, seed=0)
+    cells = sum(p["n"][0] * p["n"][1] for p in probs)
+    solvers = [api.Solver.from_problem(p, **_hybrid_kw(p, 1)) for p in probs]
+    states = [torch.as_tensor(p["U"], device=dev) for p in probs]
+    stream = torch.cuda.Stream()
+    batch = api.Batch(solvers, states)
+    with torch.cuda.stream(stream):
+        for _ in range(3):  # eager, capture, first replay
+            batch.step(stream)
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k = max(2, args.steps)
+        e0.record(stream)
+        for _ in range(k):
+            batch.step(stream)
+        e1.record(stream)
+        stream.synchronize()
+    ms = e0.elapsed_time(e1) / k
+    bad = sum(1 for s in solvers if s.sync_status() != 0)
+    del batch, solvers, states
+    torch.cuda.empty_cache()
+    # per-case FP64: each grid advanced on its own, one after the other
+    ref_solvers = [api.Solver.from_problem(p, **_hybrid_kw(p, 0)) for p in probs]
+    ref_states = [torch.as_tensor(p["U"], device=dev) for p in probs]
+    dts = [torch.zeros(2, dtype=torch.float64, device=dev) for _ in probs]
+    for s, U, d in zip(ref_solvers, ref_states, dts):
+        s.cfl_dt(U, out=d)
+        s.rk3_step(U, d)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s, U, d in zip(ref_solvers, ref_states, dts):
+        s.cfl_dt(U, out=d)
+        s.rk3_step(U, d)
+    torch.cuda.synchronize()
+    ref_ms = (time.perf_counter() - t0) * 1e3
+    del ref_solvers, ref_states
+    torch.cuda.empty_cache()
+    return {"workload": "%d quadrant Riemann problems, N in [64, 512] log-uniform (seed 0), %d cells; "
+                        "per-interface hybrid, FP32 fluxes / FP64 accumulation, one graph replay per RK3 step"
+                        % (count, cells),
+            "ms_per_rk3_step": ms, "cell_updates_per_s": cells / (ms * 1e-3),
+            "solves_per_s": count / (steps_per_solve * ms * 1e-3), "steps_per_solve": steps_per_solve,
+            "nonphysical_members": bad,
+            "per_case_fp64": {"ms_per_rk3_step": ref_ms, "solves_per_s": count / (steps_per_solve * ref_ms * 1e-3),
+                              "how": "each grid stepped alone in FP64 (wall clock, host-issued launches)"}}
+
+
+def run_serving(args, count=24, rates=(2.0, 8.0, 32.0)):
+    """Serving stream (Poisson arrivals of the seeded 60/40 tube/quadrant mix,
+    50..500 RK3 steps each, 100 GB admission budget): p50/p99 latency and
+    solves/s per arrival rate."""
+    from paper_2511_18042_gb300 import serve
+    out = []
+    for lam in rates:
+        reqs = serve.request_mix(count, rate=lam, seed=0)
+        stats, _ = serve.run(reqs, budget_bytes=100 << 30)
+        stats["lambda_per_s"] = lam
+        out.append(stats)
+    return {"scheme": "per-interface hybrid, FP32 fluxes / FP64 accumulation", "requests_per_rate": count,
+            "rates": out}
 
 
 def time_mixed(api, torch, grid, base, dev, kw, args):
@@ -375,6 +492,8 @@ def main():
     ap.add_argument("--schemes", default=None, help="comma-separated subset (default: all six)")
     ap.add_argument("--develop", type=int, default=DEVELOP_STEPS)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-batched", dest="batched", action="store_false")
+    ap.add_argument("--no-serving", dest="serving", action="store_false")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -149,6 +149,22 @@ CG_API const char *cg_last_error(void);
 /* Number of kernel launches this handle has enqueued since creation. */
 CG_API int64_t cg_launch_count(const cg_solver *s);
 
+/* Many independent grids (batched and served workloads).  cg_multi_step
+ * advances each solvers[i] by one RK3 step of its own CFL time step on
+ * states[i]: the members run concurrently on internal streams forked from
+ * `stream` and joined back to it (stream-ordered, capturable in a CUDA graph).
+ * Solvers must be distinct; every member keeps its own results (no
+ * cross-member reduction), so a member's result does not depend on the batch.
+ * cg_batch fixes a member list and its state pointers: the first
+ * cg_batch_step runs eagerly, the second captures one step into a CUDA graph,
+ * later calls replay it (one graph launch per batch step; `stream` must not
+ * be the legacy default stream from the second call on). */
+typedef struct cg_batch cg_batch;
+CG_API int cg_multi_step(cg_solver *const *solvers, double *const *states, int count, void *stream);
+CG_API int cg_batch_create(int count, cg_solver *const *solvers, double *const *states, cg_batch **out);
+CG_API int cg_batch_step(cg_batch *b, void *stream);
+CG_API void cg_batch_destroy(cg_batch *b);
+
 /* Right-hand side of the MEG6 (C-GBR explicit) scheme on a uniform Cartesian
  * grid without allocating any device memory, for callers that cannot call
  * cudaMalloc: code running while a stream is captured into a CUDA graph,

@@ -63,6 +63,12 @@ _SIGS = {
     "cg_last_error": (ctypes.c_char_p, []),
     "cg_launch_count": (ctypes.c_int64, [ctypes.c_void_p]),
     "cg_timing_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "cg_multi_step": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p), ctypes.c_int,
+                                     ctypes.c_void_p]),
+    "cg_batch_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
+                                       ctypes.POINTER(ctypes.c_void_p)]),
+    "cg_batch_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "cg_batch_destroy": (None, [ctypes.c_void_p]),
     "cg_timing_query": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_int64)]),
 }

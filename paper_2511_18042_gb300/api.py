@@ -189,3 +189,37 @@ class Solver:
         n = ctypes.c_int64()
         nat.check(nat.lib().cg_timing_query(self._h, int(kernel_class), ctypes.byref(ms), ctypes.byref(n)))
         return ms.value, n.value
+
+
+def multi_step(solvers, states, stream=None):
+    """One RK3 step (own CFL dt) of every solver on its state, concurrently."""
+    n = len(solvers)
+    hs = (ctypes.c_void_p * n)(*[s._h.value for s in solvers])
+    ps = (ctypes.c_void_p * n)(*[U.data_ptr() for U in states])
+    for s, U in zip(solvers, states):
+        s._check_state(U)
+    nat.check(nat.lib().cg_multi_step(hs, ps, n, _stream(stream)))
+
+
+class Batch:
+    """A fixed set of (solver, state) pairs stepped together; from the second
+    step on, one CUDA graph replay per step (needs a non-default stream)."""
+
+    def __init__(self, solvers, states):
+        self.solvers = list(solvers)
+        self.states = list(states)
+        for s, U in zip(self.solvers, self.states):
+            s._check_state(U)
+        n = len(self.solvers)
+        hs = (ctypes.c_void_p * n)(*[s._h.value for s in self.solvers])
+        ps = (ctypes.c_void_p * n)(*[U.data_ptr() for U in self.states])
+        self._h = ctypes.c_void_p()
+        nat.check(nat.lib().cg_batch_create(n, hs, ps, ctypes.byref(self._h)))
+
+    def step(self, stream):
+        nat.check(nat.lib().cg_batch_step(self._h, _stream(stream)))
+
+    def __del__(self):
+        if getattr(self, "_h", None) and self._h.value:
+            nat.lib().cg_batch_destroy(self._h)
+            self._h = None

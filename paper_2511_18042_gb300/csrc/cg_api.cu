@@ -436,8 +436,8 @@ static GbrCfg gbr_cfg(const cg_solver* s) {
 }
 
 namespace cgk {
-int launch_sweep_f32(int nd, int dir, bool cart, const DevGrid& g, const GbrCfg& q, const StageArgs& A, dim3 grid,
-                     cudaStream_t st);
+int launch_sweep_f32(int nd, int dir, bool cart, bool compact, const DevGrid& g, const GbrCfg& q, const StageArgs& A,
+                     dim3 grid, cudaStream_t st);
 }
 
 template <int ND, int DIR, bool CART, bool COMPACT>
@@ -461,8 +461,8 @@ static int launch_sweep(cg_solver* s, const StageArgs& A, cudaStream_t st) {
   }
   {
     TimedRegion tr(s, CG_TIMING_SWEEP, st);
-    if (s->p.precision == CG_MIXED && !COMPACT) {
-      int e = launch_sweep_f32(ND, DIR, CART, s->dg, gbr_cfg(s), A, grid, st);
+    if (s->p.precision == CG_MIXED) {
+      int e = launch_sweep_f32(ND, DIR, CART, COMPACT, s->dg, gbr_cfg(s), A, grid, st);
       if (e) return fail(CG_ERR_CUDA, "mixed sweep launch: %s", cudaGetErrorString((cudaError_t)e));
     } else {
       k_gbr_sweep<ND, DIR, CART, COMPACT><<<grid, 256, smem, st>>>(s->dg, gbr_cfg(s), A);
@@ -611,6 +611,7 @@ static void cfl_launch(cg_solver* s, const double* U, double* dt_dev, double* t_
                   : fn<3>(__VA_ARGS__))
 
 #include "cg_lad_impl.cuh"
+#include "cg_batch_impl.cuh"
 
 // ======================================================================
 extern "C" {
@@ -742,8 +743,8 @@ CG_API int cg_solver_create(const cg_grid* g, const cg_params* p, cg_solver** ou
   if (!g || !p || !out) return fail(CG_ERR_INVALID_ARG, "null argument");
   if (p->scheme < CG_MEG6 || p->scheme > CG_HYBRID) return fail(CG_ERR_INVALID_ARG, "bad scheme");
   if (p->precision != CG_FP64 && p->precision != CG_MIXED) return fail(CG_ERR_INVALID_ARG, "bad precision");
-  if (p->precision == CG_MIXED && p->scheme != CG_MEG6 && p->scheme != CG_HYBRID)
-    return fail(CG_ERR_UNSUPPORTED, "the mixed form is built for MEG6 and the hybrid's MEG6 interfaces");
+  if (p->precision == CG_MIXED && p->scheme == CG_LAD_C6)
+    return fail(CG_ERR_UNSUPPORTED, "the mixed form is built for MEG6, MIG4, LAD-E4 and the hybrid (not LAD-C6)");
   if (!(p->gamma > 1.0) || !(p->cfl > 0.0)) return fail(CG_ERR_INVALID_ARG, "gamma > 1 and cfl > 0 required");
   if (p->omega_window < 1 || p->omega_window > 4) return fail(CG_ERR_INVALID_ARG, "omega_window must be 1..4");
   if (g->curv && p->scheme == CG_LAD_C6)

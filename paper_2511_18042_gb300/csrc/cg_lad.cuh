@@ -24,20 +24,18 @@ struct LadBuffers {
 };
 
 // fields differentiated by LAD: velocities, T = gamma M^2 p / rho, rho, e = p / (rho (gamma-1))
-template <int ND>
-__device__ __forceinline__ void lad_fields(const DevGrid& g, const double* w, double* f) {
+// (T = double: FP64 parity form; T = float: mixed form, fields, gradients,
+// coefficients and fluxes in FP32 from FP64 primitives)
+template <int ND, typename T = double>
+__device__ __forceinline__ void lad_fields(const DevGrid& g, const T* w, T* f) {
   constexpr int IP = ND + 1;
-  double rho = w[0], p = w[IP];
+  T rho = w[0], p = w[IP];
 #pragma unroll
   for (int k = 0; k < ND; ++k) f[k] = w[1 + k];
-  f[ND] = g.gm2 * p / rho;
+  f[ND] = T(g.gm2) * p / rho;
   f[ND + 1] = rho;
-  f[ND + 2] = p / (rho * g.gm1);
+  f[ND + 2] = p / (rho * T(g.gm1));
 }
-
-// the LAD fields at every node of the box fbx (ghosts by the boundary rule)
-template <int ND>
-__global__ void k_lad_fieldbuf(DevGrid g, const double* __restrict__ W, double* __restrict__ f, Box fbx);
 
 __device__ __forceinline__ void box_coords(const Box& b, long long e, int* c) {
   c[0] = (int)(e % b.ext[0]) - b.off[0];
@@ -49,16 +47,20 @@ __device__ __forceinline__ void box_coords(const Box& b, long long e, int* c) {
 #define BOX_LOOP(b, e) \
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (b).size(); e += (long long)gridDim.x * blockDim.x)
 
-template <int ND>
-__global__ void k_lad_fieldbuf(DevGrid g, const double* __restrict__ W, double* __restrict__ f, Box fbx) {
+// the LAD fields at every node of the box fbx (ghosts by the boundary rule)
+template <int ND, typename T = double>
+__global__ void k_lad_fieldbuf(DevGrid g, const double* __restrict__ W, T* __restrict__ f, Box fbx) {
   constexpr int NV = ND + 2, NF = ND + 3;
   long long fs = fbx.size();
   BOX_LOOP(fbx, e) {
     int c[3];
     box_coords(fbx, e, c);
-    double w[NV], fl[NF];
-    load_state<ND>(g, W, c[0], c[1], c[2], w);
-    lad_fields<ND>(g, w, fl);
+    double wd[NV];
+    T w[NV], fl[NF];
+    load_state<ND>(g, W, c[0], c[1], c[2], wd);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) w[v] = T(wd[v]);
+    lad_fields<ND, T>(g, w, fl);
 #pragma unroll
     for (int v = 0; v < NF; ++v) f[v * fs + e] = fl[v];
   }
@@ -66,10 +68,10 @@ __global__ void k_lad_fieldbuf(DevGrid g, const double* __restrict__ W, double* 
 
 // Physical gradients and dilatation on b3.  E4 differences the field buffer;
 // C6 reads the compact derivatives from the line buffers df.
-template <int ND, bool CART, bool C6>
-__global__ void k_lad_grad(DevGrid g, const double* __restrict__ fb, Box fbx, const double* __restrict__ df0,
+template <int ND, bool CART, bool C6, typename T = double>
+__global__ void k_lad_grad(DevGrid g, const T* __restrict__ fb, Box fbx, const double* __restrict__ df0,
                            const double* __restrict__ df1, const double* __restrict__ df2, LineBuf lb0, LineBuf lb1,
-                           LineBuf lb2, double* __restrict__ gr, double* __restrict__ dv, Box b3, const int* guard,
+                           LineBuf lb2, T* __restrict__ gr, T* __restrict__ dv, Box b3, const int* guard,
                            int want) {
   constexpr int NF = ND + 3;
   if (guard && *guard != want) return;
@@ -77,7 +79,7 @@ __global__ void k_lad_grad(DevGrid g, const double* __restrict__ fb, Box fbx, co
   BOX_LOOP(b3, e) {
     int c[3];
     box_coords(b3, e, c);
-    double d[3][NF];  // d[l][f] = d f / d xi_l
+    T d[3][NF];  // d[l][f] = d f / d xi_l
     long long q = fbx.at(c[0], c[1], c[2]);
 #pragma unroll
     for (int l = 0; l < ND; ++l) {
@@ -85,39 +87,39 @@ __global__ void k_lad_grad(DevGrid g, const double* __restrict__ fb, Box fbx, co
         const double* df = l == 0 ? df0 : (l == 1 ? df1 : df2);
         const LineBuf& lb = l == 0 ? lb0 : (l == 1 ? lb1 : lb2);
 #pragma unroll
-        for (int f = 0; f < NF; ++f) d[l][f] = df[lb.at(f, c[l], c)];
+        for (int f = 0; f < NF; ++f) d[l][f] = T(df[lb.at(f, c[l], c)]);
       } else {
         long long st = l == 0 ? 1 : (l == 1 ? (long long)fbx.ext[0] : (long long)fbx.ext[0] * fbx.ext[1]);
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
-          const double* p = fb + f * fs + q;
+          const T* p = fb + f * fs + q;
           d[l][f] = d4(p[-2 * st], p[-st], p[st], p[2 * st]);
         }
       }
     }
-    double div = 0.0;
+    T div = T(0);
     if (CART) {
 #pragma unroll
       for (int f = 0; f < NF; ++f)
 #pragma unroll
         for (int m = 0; m < ND; ++m) {
-          double v = (g.cjac * g.cxh[m]) * d[m][f];
+          T v = T(g.cjac * g.cxh[m]) * d[m][f];
           gr[(f * ND + m) * bs + e] = v;
           if (f < ND && m == f) div = (f == 0) ? v : div + v;
         }
     } else {
       long long pq = plin(g, c[0], c[1], c[2]);
       double J = g.jac[pq];
-      double xm[3][3];
+      T xm[3][3];
 #pragma unroll
       for (int l = 0; l < ND; ++l)
 #pragma unroll
-        for (int m = 0; m < ND; ++m) xm[l][m] = J * g.xh[(l * ND + m) * g.NP + pq];
+        for (int m = 0; m < ND; ++m) xm[l][m] = T(J * g.xh[(l * ND + m) * g.NP + pq]);
 #pragma unroll
       for (int f = 0; f < NF; ++f)
 #pragma unroll
         for (int m = 0; m < ND; ++m) {
-          double sm = xm[0][m] * d[0][f];
+          T sm = xm[0][m] * d[0][f];
 #pragma unroll
           for (int l = 1; l < ND; ++l) sm = sm + xm[l][m] * d[l][f];
           gr[(f * ND + m) * bs + e] = sm;
@@ -131,11 +133,11 @@ __global__ void k_lad_grad(DevGrid g, const double* __restrict__ fb, Box fbx, co
 // Raw coefficients at interior nodes, Eq. (4)-(6):
 // beta* = C_beta rho f_sw |sum_l d4(div)_l Delta_{l,beta}^2|,
 // kappa* = C_kappa (rho c / T) |sum_l d4(e)_l Delta_{l,kappa}|.
-template <int ND, bool CART>
-__global__ void k_lad_coef(DevGrid g, const double* __restrict__ W, const double* __restrict__ fb, Box fbx,
-                           const double* __restrict__ gr, const double* __restrict__ dv, Box b3, double c_beta,
-                           double c_kappa, double* __restrict__ bt, double* __restrict__ kp, const int* guard,
-                           int want) {
+template <int ND, bool CART, typename T = double>
+__global__ void k_lad_coef(DevGrid g, const double* __restrict__ W, const T* __restrict__ fb, Box fbx,
+                           const T* __restrict__ gr, const T* __restrict__ dv, Box b3, double c_beta_d,
+                           double c_kappa_d, T* __restrict__ bt, T* __restrict__ kp, const int* guard, int want) {
+  const T c_beta = T(c_beta_d), c_kappa = T(c_kappa_d);
   constexpr int NV = ND + 2, IP = ND + 1;
   if (guard && *guard != want) return;
   long long bs = b3.size(), fs = fbx.size();
@@ -145,26 +147,26 @@ __global__ void k_lad_coef(DevGrid g, const double* __restrict__ W, const double
     c[1] = (int)((q / g.n[0]) % g.n[1]);
     c[2] = (int)(q / ((long long)g.n[0] * g.n[1]));
     long long e0 = b3.at(c[0], c[1], c[2]);
-    double w[NV];
+    T w[NV];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) w[v] = W[v * g.N + q];
-    double rho = w[0], p = w[IP];
+    for (int v = 0; v < NV; ++v) w[v] = T(W[v * g.N + q]);
+    T rho = w[0], p = w[IP];
     long long fq = fbx.at(c[0], c[1], c[2]);
-    double T = fb[ND * fs + fq];
-    double cs = sqrt(g.gamma * p / rho);
-    double div = dv[e0];
-    double curl2 = 0.0;
+    T Tt = fb[ND * fs + fq];
+    T cs = sqrt(T(g.gamma) * p / rho);
+    T div = dv[e0];
+    T curl2 = T(0);
     auto G = [&](int f, int m) { return gr[(f * ND + m) * bs + e0]; };
     if (ND == 2) {
-      double w3 = G(1, 0) - G(0, 1);
+      T w3 = G(1, 0) - G(0, 1);
       curl2 = w3 * w3;
     } else if (ND == 3) {
-      double w1 = G(2, 1) - G(1, 2), w2 = G(0, 2) - G(2, 0), w3 = G(1, 0) - G(0, 1);
+      T w1 = G(2, 1) - G(1, 2), w2 = G(0, 2) - G(2, 0), w3 = G(1, 0) - G(0, 1);
       curl2 = w1 * w1 + w2 * w2 + w3 * w3;
     }
-    double heav = div < 0.0 ? 1.0 : 0.0;
-    double fsw = heav * (div * div) / (div * div + curl2 + 1e-32);
-    double gmr = G(ND + 1, 0) * G(ND + 1, 0), gme = G(ND + 2, 0) * G(ND + 2, 0);
+    T heav = div < T(0) ? T(1) : T(0);
+    T fsw = heav * (div * div) / (div * div + curl2 + T(1e-32));
+    T gmr = G(ND + 1, 0) * G(ND + 1, 0), gme = G(ND + 2, 0) * G(ND + 2, 0);
 #pragma unroll
     for (int m = 1; m < ND; ++m) {
       gmr = gmr + G(ND + 1, m) * G(ND + 1, m);
@@ -172,48 +174,48 @@ __global__ void k_lad_coef(DevGrid g, const double* __restrict__ W, const double
     }
     gmr = sqrt(gmr);
     gme = sqrt(gme);
-    double sb = 0.0, sk = 0.0;
+    T sb = T(0), sk = T(0);
 #pragma unroll
     for (int l = 0; l < ND; ++l) {
       long long st = l == 0 ? 1 : (l == 1 ? (long long)b3.ext[0] : (long long)b3.ext[0] * b3.ext[1]);
-      double d4d = (dv[e0 - 2 * st] + dv[e0 + 2 * st]) - 4.0 * (dv[e0 - st] + dv[e0 + st]) + 6.0 * div;
+      T d4d = (dv[e0 - 2 * st] + dv[e0 + 2 * st]) - T(4.0) * (dv[e0 - st] + dv[e0 + st]) + T(6.0) * div;
       long long fst = l == 0 ? 1 : (l == 1 ? (long long)fbx.ext[0] : (long long)fbx.ext[0] * fbx.ext[1]);
-      const double* ev = fb + (ND + 2) * fs + fq;
-      double d4e = (ev[-2 * fst] + ev[2 * fst]) - 4.0 * (ev[-fst] + ev[fst]) + 6.0 * ev[0];
-      double pr, pe;
+      const T* ev = fb + (ND + 2) * fs + fq;
+      T d4e = (ev[-2 * fst] + ev[2 * fst]) - T(4.0) * (ev[-fst] + ev[fst]) + T(6.0) * ev[0];
+      T pr, pe;
       if (CART) {
-        pr = g.ch[l] * G(ND + 1, l);
-        pe = g.ch[l] * G(ND + 2, l);
+        pr = T(g.ch[l]) * G(ND + 1, l);
+        pe = T(g.ch[l]) * G(ND + 2, l);
       } else {
         long long pq = plin(g, c[0], c[1], c[2]);
-        pr = g.dxl[(l * ND + 0) * g.NP + pq] * G(ND + 1, 0);
-        pe = g.dxl[(l * ND + 0) * g.NP + pq] * G(ND + 2, 0);
+        pr = T(g.dxl[(l * ND + 0) * g.NP + pq]) * G(ND + 1, 0);
+        pe = T(g.dxl[(l * ND + 0) * g.NP + pq]) * G(ND + 2, 0);
 #pragma unroll
         for (int m = 1; m < ND; ++m) {
-          double x = g.dxl[(l * ND + m) * g.NP + pq];
+          T x = T(g.dxl[(l * ND + m) * g.NP + pq]);
           pr = pr + x * G(ND + 1, m);
           pe = pe + x * G(ND + 2, m);
         }
       }
-      double Db = fabs(pr) / (gmr + 1e-32);
-      double Dk = fabs(pe) / (gme + 1e-32);
-      double tb = d4d * Db * Db, tk = d4e * Dk;
+      T Db = fabs(pr) / (gmr + T(1e-32));
+      T Dk = fabs(pe) / (gme + T(1e-32));
+      T tb = d4d * Db * Db, tk = d4e * Dk;
       sb = (l == 0) ? tb : sb + tb;
       sk = (l == 0) ? tk : sk + tk;
     }
     bt[q] = c_beta * rho * fsw * fabs(sb);
-    kp[q] = c_kappa * (rho * cs / T) * fabs(sk);
+    kp[q] = c_kappa * (rho * cs / Tt) * fabs(sk);
   }
 }
 
 // truncated-Gaussian overbar along l (nine points, Cook & Cabot), two fields;
 // ghost values: periodic wrap, wall mirror, otherwise the boundary node.
-template <int ND>
-__global__ void k_gauss(DevGrid g, int l, const double* __restrict__ a, const double* __restrict__ b,
-                        double* __restrict__ ao, double* __restrict__ bo, const int* guard, int want) {
+template <int ND, typename T = double>
+__global__ void k_gauss(DevGrid g, int l, const T* __restrict__ a, const T* __restrict__ b, T* __restrict__ ao,
+                        T* __restrict__ bo, const int* guard, int want) {
   if (guard && *guard != want) return;
-  const double A0 = 3565.0 / 10368.0, A1 = 3091.0 / 12960.0, A2 = 1997.0 / 25920.0, A3 = 149.0 / 12960.0,
-               A4 = 107.0 / 103680.0;
+  const T A0 = T(3565.0 / 10368.0), A1 = T(3091.0 / 12960.0), A2 = T(1997.0 / 25920.0), A3 = T(149.0 / 12960.0),
+          A4 = T(107.0 / 103680.0);
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < g.N; q += (long long)gridDim.x * blockDim.x) {
     int c[3];
     c[0] = (int)(q % g.n[0]);
@@ -236,29 +238,31 @@ __global__ void k_gauss(DevGrid g, int l, const double* __restrict__ a, const do
 // Node fluxes along l at positions [-2, n+1] (interior lines):
 // F = F^c(W; xi_hat_l) - [0, xi_hat_l tau, xi_hat_l . phi], tau = beta* div,
 // phi_m = u_m tau + kappa* dT/dx_m.
-template <int ND, bool CART>
-__global__ void k_lad_nodeflux(DevGrid g, int l, const double* __restrict__ W, const double* __restrict__ bt,
-                               const double* __restrict__ kp, const double* __restrict__ gr,
-                               const double* __restrict__ dv, Box b3, double* __restrict__ Fn, Box fb,
-                               const int* guard, int want) {
+template <int ND, bool CART, typename T = double>
+__global__ void k_lad_nodeflux(DevGrid g, int l, const double* __restrict__ W, const T* __restrict__ bt,
+                               const T* __restrict__ kp, const T* __restrict__ gr, const T* __restrict__ dv, Box b3,
+                               T* __restrict__ Fn, Box fb, const int* guard, int want) {
   constexpr int NV = ND + 2, IP = ND + 1;
   if (guard && *guard != want) return;
   long long fs = fb.size(), bs = b3.size();
   BOX_LOOP(fb, e) {
     int c[3];
     box_coords(fb, e, c);
-    double w[NV];
-    load_state<ND>(g, W, c[0], c[1], c[2], w);
-    double xi[3];
+    double wd[NV];
+    load_state<ND>(g, W, c[0], c[1], c[2], wd);
+    T w[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) w[v] = T(wd[v]);
+    T xi[3];
     if (CART) {
 #pragma unroll
-      for (int m = 0; m < ND; ++m) xi[m] = (m == l) ? g.cxh[l] : 0.0;
+      for (int m = 0; m < ND; ++m) xi[m] = (m == l) ? T(g.cxh[l]) : T(0);
     } else {
       long long pq = plin(g, c[0], c[1], c[2]);
 #pragma unroll
-      for (int m = 0; m < ND; ++m) xi[m] = g.xh[(l * ND + m) * g.NP + pq];
+      for (int m = 0; m < ND; ++m) xi[m] = T(g.xh[(l * ND + m) * g.NP + pq]);
     }
-    double U, q2;
+    T U, q2;
     if (CART) U = xi[l] * w[1 + l];
     else {
       U = xi[0] * w[1];
@@ -268,25 +272,25 @@ __global__ void k_lad_nodeflux(DevGrid g, int l, const double* __restrict__ W, c
     q2 = w[1] * w[1];
 #pragma unroll
     for (int m = 1; m < ND; ++m) q2 = q2 + w[1 + m] * w[1 + m];
-    double rho = w[0], p = w[IP];
-    double E = p / g.gm1 + 0.5 * rho * q2;
+    T rho = w[0], p = w[IP];
+    T E = p / T(g.gm1) + T(0.5) * rho * q2;
     long long sq = scalar_src(g, c[0], c[1], c[2]);
     long long be = b3.at(c[0], c[1], c[2]);
-    double tau = bt[sq] * dv[be];
-    double kap = kp[sq];
-    double fe = 0.0;
+    T tau = bt[sq] * dv[be];
+    T kap = kp[sq];
+    T fe = T(0);
     bool first = true;
 #pragma unroll
     for (int m = 0; m < ND; ++m) {
       if (CART && m != l) continue;
-      double phi = w[1 + m] * tau + kap * gr[(ND * ND + m) * bs + be];
+      T phi = w[1 + m] * tau + kap * gr[(ND * ND + m) * bs + be];
       fe = first ? xi[m] * phi : fe + xi[m] * phi;
       first = false;
     }
     Fn[0 * fs + e] = rho * U;
 #pragma unroll
     for (int m = 0; m < ND; ++m) {
-      double fc = (CART && m != l) ? rho * w[1 + m] * U : rho * w[1 + m] * U + xi[m] * p;
+      T fc = (CART && m != l) ? rho * w[1 + m] * U : rho * w[1 + m] * U + xi[m] * p;
       Fn[(1 + m) * fs + e] = (CART && m != l) ? fc : fc - xi[m] * tau;
     }
     Fn[IP * fs + e] = (E + p) * U - fe;
@@ -335,8 +339,8 @@ __device__ __forceinline__ void lad_epilogue(const DevGrid& g, const StageArgs& 
 }
 
 // E4 divergence of the node fluxes along l (explicit) or the compact result D.
-template <int ND>
-__global__ void k_lad_div(DevGrid g, int l, const double* __restrict__ Fn, Box fb, const double* __restrict__ D,
+template <int ND, typename T = double>
+__global__ void k_lad_div(DevGrid g, int l, const T* __restrict__ Fn, Box fb, const double* __restrict__ D,
                           LineBuf DL, StageArgs A, const int* guard, int want) {
   constexpr int NV = ND + 2;
   if (guard && *guard != want) return;
@@ -355,8 +359,8 @@ __global__ void k_lad_div(DevGrid g, int l, const double* __restrict__ Fn, Box f
       long long st = l == 0 ? 1 : (l == 1 ? (long long)fb.ext[0] : (long long)fb.ext[0] * fb.ext[1]);
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        const double* f = Fn + v * fs;
-        Dv[v] = d4(f[e - 2 * st], f[e - st], f[e + st], f[e + 2 * st]);
+        const T* f = Fn + v * fs;
+        Dv[v] = (double)d4(f[e - 2 * st], f[e - st], f[e + st], f[e + 2 * st]);
       }
     }
     lad_epilogue<ND>(g, A, q, c, Dv);
@@ -393,8 +397,8 @@ __global__ void k_troubled(DevGrid g, const double* __restrict__ W, double hr, d
 
 // Per-interface hybrid: LAD flux at interfaces i+1/2 (i in [-1, n-1]) in the
 // conservative E4 flux form h = 7/12 (F_i + F_{i+1}) - 1/12 (F_{i-1} + F_{i+2}).
-template <int ND>
-__global__ void k_lad_hflux(DevGrid g, int l, const double* __restrict__ Fn, Box fb, double* __restrict__ H, Box hb) {
+template <int ND, typename T = double>
+__global__ void k_lad_hflux(DevGrid g, int l, const T* __restrict__ Fn, Box fb, double* __restrict__ H, Box hb) {
   constexpr int NV = ND + 2;
   long long fs = fb.size(), hs = hb.size();
   long long st = l == 0 ? 1 : (l == 1 ? (long long)fb.ext[0] : (long long)fb.ext[0] * fb.ext[1]);
@@ -404,8 +408,8 @@ __global__ void k_lad_hflux(DevGrid g, int l, const double* __restrict__ Fn, Box
     long long q = fb.at(c[0], c[1], c[2]);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      const double* f = Fn + v * fs;
-      H[v * hs + e] = (7.0 / 12.0) * (f[q] + f[q + st]) - (1.0 / 12.0) * (f[q - st] + f[q + 2 * st]);
+      const T* f = Fn + v * fs;
+      H[v * hs + e] = (double)(T(7.0 / 12.0) * (f[q] + f[q + st]) - T(1.0 / 12.0) * (f[q - st] + f[q + 2 * st]));
     }
   }
 }

@@ -62,11 +62,16 @@ static void lad_free(LadBuffers& L) {
 
 // beta*, kappa* (filtered, interior) of the primitives in s->W; result in
 // bt[0], kp[0].  dkind: 2 = E4, 3 = C6.
-template <int ND>
+template <int ND, typename T = double>
 static int lad_coeffs_run(cg_solver* s, int dkind, cudaStream_t st, const int* guard, int want) {
   LadBuffers& L = s->lad;
   bool c6 = dkind == 3;
-  k_lad_fieldbuf<ND><<<grid_blocks(L.fbx.size(), 256), 256, 0, st>>>(s->dg, s->W, L.fb, L.fbx);
+  T* fb = reinterpret_cast<T*>(L.fb);
+  T* gr = reinterpret_cast<T*>(L.gr);
+  T* dv = reinterpret_cast<T*>(L.dv);
+  T* bt[2] = {reinterpret_cast<T*>(L.bt[0]), reinterpret_cast<T*>(L.bt[1])};
+  T* kp[2] = {reinterpret_cast<T*>(L.kp[0]), reinterpret_cast<T*>(L.kp[1])};
+  k_lad_fieldbuf<ND, T><<<grid_blocks(L.fbx.size(), 256), 256, 0, st>>>(s->dg, s->W, fb, L.fbx);
   s->launches++;
   if (c6) {
     ThomasJobs J;
@@ -74,7 +79,7 @@ static int lad_coeffs_run(cg_solver* s, int dkind, cudaStream_t st, const int* g
     J.start[0] = 0;
     for (int l = 0; l < ND; ++l) {
       const LineBuf& lb = L.dfLB[l];
-      k_rhs_c6<<<grid_blocks((long long)lb.m * lb.nl, 256), 256, 0, st>>>(L.fb, L.fbx, ND + 3, lb, L.df[l]);
+      k_rhs_c6<<<grid_blocks((long long)lb.m * lb.nl, 256), 256, 0, st>>>(reinterpret_cast<double*>(fb), L.fbx, ND + 3, lb, L.df[l]);
       s->launches++;
       J.lc[l] = s->c6grad[l].lc;
       J.x[l] = L.df[l];
@@ -87,72 +92,87 @@ static int lad_coeffs_run(cg_solver* s, int dkind, cudaStream_t st, const int* g
   }
   int gb = grid_blocks(L.b3.size(), 128);
   if (s->dg.curv) {
-    if (c6) k_lad_grad<ND, false, true><<<gb, 128, 0, st>>>(s->dg, L.fb, L.fbx, L.df[0], L.df[1], L.df[2], L.dfLB[0], L.dfLB[1], L.dfLB[2], L.gr, L.dv, L.b3, guard, want);
-    else k_lad_grad<ND, false, false><<<gb, 128, 0, st>>>(s->dg, L.fb, L.fbx, L.df[0], L.df[1], L.df[2], L.dfLB[0], L.dfLB[1], L.dfLB[2], L.gr, L.dv, L.b3, guard, want);
-    k_lad_coef<ND, false><<<grid_blocks(s->N, 128), 128, 0, st>>>(s->dg, s->W, L.fb, L.fbx, L.gr, L.dv, L.b3, s->p.c_beta,
-                                                                  s->p.c_kappa, L.bt[0], L.kp[0], guard, want);
+    if (c6) k_lad_grad<ND, false, true, T><<<gb, 128, 0, st>>>(s->dg, fb, L.fbx, L.df[0], L.df[1], L.df[2], L.dfLB[0], L.dfLB[1], L.dfLB[2], gr, dv, L.b3, guard, want);
+    else k_lad_grad<ND, false, false, T><<<gb, 128, 0, st>>>(s->dg, fb, L.fbx, L.df[0], L.df[1], L.df[2], L.dfLB[0], L.dfLB[1], L.dfLB[2], gr, dv, L.b3, guard, want);
+    k_lad_coef<ND, false, T><<<grid_blocks(s->N, 128), 128, 0, st>>>(s->dg, s->W, fb, L.fbx, gr, dv, L.b3, s->p.c_beta,
+                                                                     s->p.c_kappa, bt[0], kp[0], guard, want);
   } else {
-    if (c6) k_lad_grad<ND, true, true><<<gb, 128, 0, st>>>(s->dg, L.fb, L.fbx, L.df[0], L.df[1], L.df[2], L.dfLB[0], L.dfLB[1], L.dfLB[2], L.gr, L.dv, L.b3, guard, want);
-    else k_lad_grad<ND, true, false><<<gb, 128, 0, st>>>(s->dg, L.fb, L.fbx, L.df[0], L.df[1], L.df[2], L.dfLB[0], L.dfLB[1], L.dfLB[2], L.gr, L.dv, L.b3, guard, want);
-    k_lad_coef<ND, true><<<grid_blocks(s->N, 128), 128, 0, st>>>(s->dg, s->W, L.fb, L.fbx, L.gr, L.dv, L.b3, s->p.c_beta,
-                                                                 s->p.c_kappa, L.bt[0], L.kp[0], guard, want);
+    if (c6) k_lad_grad<ND, true, true, T><<<gb, 128, 0, st>>>(s->dg, fb, L.fbx, L.df[0], L.df[1], L.df[2], L.dfLB[0], L.dfLB[1], L.dfLB[2], gr, dv, L.b3, guard, want);
+    else k_lad_grad<ND, true, false, T><<<gb, 128, 0, st>>>(s->dg, fb, L.fbx, L.df[0], L.df[1], L.df[2], L.dfLB[0], L.dfLB[1], L.dfLB[2], gr, dv, L.b3, guard, want);
+    k_lad_coef<ND, true, T><<<grid_blocks(s->N, 128), 128, 0, st>>>(s->dg, s->W, fb, L.fbx, gr, dv, L.b3, s->p.c_beta,
+                                                                    s->p.c_kappa, bt[0], kp[0], guard, want);
   }
   s->launches += 2;
   int cur = 0;
   for (int l = 0; l < ND; ++l) {
-    k_gauss<ND><<<grid_blocks(s->N, 256), 256, 0, st>>>(s->dg, l, L.bt[cur], L.kp[cur], L.bt[1 - cur], L.kp[1 - cur],
-                                                       guard, want);
+    k_gauss<ND, T><<<grid_blocks(s->N, 256), 256, 0, st>>>(s->dg, l, bt[cur], kp[cur], bt[1 - cur], kp[1 - cur],
+                                                          guard, want);
     s->launches++;
     cur = 1 - cur;
   }
   if (cur != 0) {
-    CG_CUDA(cudaMemcpyAsync(L.bt[0], L.bt[1], sizeof(double) * s->N, cudaMemcpyDeviceToDevice, st));
-    CG_CUDA(cudaMemcpyAsync(L.kp[0], L.kp[1], sizeof(double) * s->N, cudaMemcpyDeviceToDevice, st));
+    CG_CUDA(cudaMemcpyAsync(bt[0], bt[1], sizeof(T) * s->N, cudaMemcpyDeviceToDevice, st));
+    CG_CUDA(cudaMemcpyAsync(kp[0], kp[1], sizeof(T) * s->N, cudaMemcpyDeviceToDevice, st));
   }
   return CG_OK;
 }
 
-template <int ND>
+template <int ND, typename T = double>
 static void lad_nodeflux(cg_solver* s, int l, cudaStream_t st, const int* guard, int want) {
   LadBuffers& L = s->lad;
   int gb = grid_blocks(L.fbox[l].size(), 128);
+  const T* bt = reinterpret_cast<const T*>(L.bt[0]);
+  const T* kp = reinterpret_cast<const T*>(L.kp[0]);
+  const T* gr = reinterpret_cast<const T*>(L.gr);
+  const T* dv = reinterpret_cast<const T*>(L.dv);
+  T* Fn = reinterpret_cast<T*>(L.Fn);
   if (s->dg.curv)
-    k_lad_nodeflux<ND, false><<<gb, 128, 0, st>>>(s->dg, l, s->W, L.bt[0], L.kp[0], L.gr, L.dv, L.b3, L.Fn, L.fbox[l], guard, want);
+    k_lad_nodeflux<ND, false, T><<<gb, 128, 0, st>>>(s->dg, l, s->W, bt, kp, gr, dv, L.b3, Fn, L.fbox[l], guard, want);
   else
-    k_lad_nodeflux<ND, true><<<gb, 128, 0, st>>>(s->dg, l, s->W, L.bt[0], L.kp[0], L.gr, L.dv, L.b3, L.Fn, L.fbox[l], guard, want);
+    k_lad_nodeflux<ND, true, T><<<gb, 128, 0, st>>>(s->dg, l, s->W, bt, kp, gr, dv, L.b3, Fn, L.fbox[l], guard, want);
   s->launches++;
 }
 
 // LAD residual (E4 or C6) of the primitives in s->W with the epilogue of A.
-template <int ND>
+template <int ND, typename T = double>
 static int lad_pass(cg_solver* s, int dkind, StageArgs A, cudaStream_t st, const int* guard, int want) {
-  int rc = lad_coeffs_run<ND>(s, dkind, st, guard, want);
+  int rc = lad_coeffs_run<ND, T>(s, dkind, st, guard, want);
   if (rc) return rc;
   LadBuffers& L = s->lad;
   for (int l = 0; l < ND; ++l) {
-    lad_nodeflux<ND>(s, l, st, guard, want);
+    lad_nodeflux<ND, T>(s, l, st, guard, want);
     A.first = l == 0;
     A.last = l == ND - 1;
     const double* D = nullptr;
     LineBuf DL = L.DLB[l];
     if (dkind == 3) {
-      k_rhs_c6<<<grid_blocks((long long)DL.m * DL.nl, 256), 256, 0, st>>>(L.Fn, L.fbox[l], ND + 2, DL, L.D);
+      k_rhs_c6<<<grid_blocks((long long)DL.m * DL.nl, 256), 256, 0, st>>>(reinterpret_cast<const double*>(L.Fn), L.fbox[l], ND + 2, DL, L.D);
       k_thomas<<<(unsigned)((DL.nl * (ND + 2) + 31) / 32), 32, 0, st>>>(s->c6flux[l].lc, L.D, DL.nl, ND + 2);
       s->launches += 2;
       D = L.D;
     }
-    k_lad_div<ND><<<grid_blocks(s->N, 256), 256, 0, st>>>(s->dg, l, L.Fn, L.fbox[l], D, DL, A, guard, want);
+    k_lad_div<ND, T><<<grid_blocks(s->N, 256), 256, 0, st>>>(s->dg, l, reinterpret_cast<const T*>(L.Fn), L.fbox[l], D, DL,
+                                                            A, guard, want);
     s->launches++;
   }
   return CG_OK;
 }
 
+template <int ND, typename T>
+static int lad_stage_t(cg_solver* s, const double* Uc, StageArgs A, cudaStream_t st);
+
 template <int ND>
 static int lad_stage(cg_solver* s, const double* Uc, StageArgs A, cudaStream_t st) {
+  if (s->p.precision == CG_MIXED) return lad_stage_t<ND, float>(s, Uc, A, st);
+  return lad_stage_t<ND, double>(s, Uc, A, st);
+}
+
+template <int ND, typename T>
+static int lad_stage_t(cg_solver* s, const double* Uc, StageArgs A, cudaStream_t st) {
   int sch = s->p.scheme;
   k_prim<ND><<<grid_blocks(s->N, 256), 256, 0, st>>>(s->dg, Uc, s->W);
   s->launches++;
-  if (sch == CG_LAD_E4 || sch == CG_LAD_C6) return lad_pass<ND>(s, sch == CG_LAD_E4 ? 2 : 3, A, st, nullptr, 0);
+  if (sch == CG_LAD_E4 || sch == CG_LAD_C6) return lad_pass<ND, T>(s, sch == CG_LAD_E4 ? 2 : 3, A, st, nullptr, 0);
   LadBuffers& L = s->lad;
   CG_CUDA(cudaMemsetAsync(s->hyb_flag, 0, sizeof(int), st));
   CG_CUDA(cudaMemsetAsync(s->hyb_count, 0, sizeof(unsigned long long), st));
@@ -168,7 +188,7 @@ static int lad_stage(cg_solver* s, const double* Uc, StageArgs A, cudaStream_t s
     G.guard_want = 1;
     int rc = gbr_sweeps<ND>(s, false, G, st);
     if (rc) return rc;
-    return lad_pass<ND>(s, 2, A, st, s->hyb_flag, 0);
+    return lad_pass<ND, T>(s, 2, A, st, s->hyb_flag, 0);
   }
   // per interface: GBR-MEG6 where a neighbour node is troubled, LAD-E4 (flux form) elsewhere
   stage_prep_gbr<ND>(s, Uc, false, st, false);
@@ -176,11 +196,12 @@ static int lad_stage(cg_solver* s, const double* Uc, StageArgs A, cudaStream_t s
       s->dg, s->W, s->p.hyb_rho, s->p.hyb_p, s->p.hybrid_sensor ? s->om : nullptr, s->omBox, s->p.sensor_thresh, L.tr,
       L.tbox, s->hyb_flag, s->hyb_count);
   s->launches++;
-  int rc = lad_coeffs_run<ND>(s, 2, st, nullptr, 0);
+  int rc = lad_coeffs_run<ND, T>(s, 2, st, nullptr, 0);
   if (rc) return rc;
   for (int l = 0; l < ND; ++l) {
-    lad_nodeflux<ND>(s, l, st, nullptr, 0);
-    k_lad_hflux<ND><<<grid_blocks(L.hbox[l].size(), 256), 256, 0, st>>>(s->dg, l, L.Fn, L.fbox[l], s->hflux[l], L.hbox[l]);
+    lad_nodeflux<ND, T>(s, l, st, nullptr, 0);
+    k_lad_hflux<ND, T><<<grid_blocks(L.hbox[l].size(), 256), 256, 0, st>>>(s->dg, l, reinterpret_cast<const T*>(L.Fn),
+                                                                          L.fbox[l], s->hflux[l], L.hbox[l]);
     s->launches++;
   }
   StageArgs H = A;
@@ -230,6 +251,7 @@ extern "C" {
 CG_API int cg_lad_coeffs(cg_solver* s, const double* U, double* beta, double* kappa, void* stream) {
   if (!s || !U || !beta || !kappa) return fail(CG_ERR_INVALID_ARG, "null argument");
   if (!s->lad.gr) return fail(CG_ERR_UNSUPPORTED, "LAD coefficients exist for the LAD and hybrid schemes");
+  if (s->p.precision != CG_FP64) return fail(CG_ERR_UNSUPPORTED, "coefficient diagnostics are FP64 only");
   cudaStream_t st = (cudaStream_t)stream;
   DISPATCH_ND(s, stage_prep_prim, s, U, st);
   int rc = DISPATCH_ND(s, lad_coeffs_run, s, s->p.scheme == CG_LAD_C6 ? 3 : 2, st, nullptr, 0);

@@ -205,3 +205,11 @@ def field_on_curvilinear(xyz, period, W, gamma=1.4, bc=None):
         bc = [[PERIODIC, PERIODIC]] * nd
     return _problem("curvilinear", nd, n, [1.0] * nd, bc, W, gamma,
                     xyz=np.ascontiguousarray(xyz), period=period)
+
+
+def batched_riemann(count=256, seed=0, n_lo=64, n_hi=512):
+    """Batched 2D quadrant Riemann problems: sizes N ~ round(exp(U(ln n_lo, ln n_hi)))
+    (square N x N), quadrant states as in random_quadrants, one seeded stream."""
+    rng = np.random.default_rng(seed)
+    sizes = np.rint(np.exp(rng.uniform(math.log(n_lo), math.log(n_hi), count))).astype(int)
+    return [random_quadrants(rng, int(n)) for n in sizes]

@@ -25,7 +25,7 @@ def _l1_rho(Ug, Uo):
     return float(np.abs(Ug[0].cpu().numpy() - Uo[0]).mean())
 
 
-@pytest.mark.parametrize("kw", [dict(scheme="MEG6"),
+@pytest.mark.parametrize("kw", [dict(scheme="MEG6"), dict(scheme="MIG4"), dict(scheme="LAD_E4"),
                                 dict(scheme="HYBRID", hybrid_mode=1, hyb_rho=0.0625, hybrid_sensor=1),
                                 dict(scheme="HYBRID", hybrid_mode=0, hyb_rho=0.12)])
 def test_mixed_triple_point_100_steps(orc, api, kw):
