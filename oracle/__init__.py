@@ -24,7 +24,7 @@ _SO = os.path.join(_HERE, "_build", "libcgoracle.so")
 
 MEG6, MIG4, LAD_E4, LAD_C6, HYBRID = 0, 1, 2, 3, 4
 HYB_GLOBAL, HYB_CELL = 0, 1
-BC_PERIODIC, BC_EXTRAP, BC_REFLECT, BC_INFLOW = 0, 1, 2, 3
+BC_PERIODIC, BC_EXTRAP, BC_REFLECT, BC_INFLOW, BC_WALL = 0, 1, 2, 3, 4
 SCHEMES = {"MEG6": MEG6, "MIG4": MIG4, "LAD_E4": LAD_E4, "LAD_C6": LAD_C6, "HYBRID": HYBRID}
 
 
@@ -69,6 +69,11 @@ class OrcParams(ctypes.Structure):
         ("omega_window", ctypes.c_int),
         ("positivity_fallback", ctypes.c_int),
         ("filter_on", ctypes.c_int),
+        ("viscous", ctypes.c_int),
+        ("re", ctypes.c_double),
+        ("pr", ctypes.c_double),
+        ("suth", ctypes.c_double),
+        ("twall", ctypes.c_double),
     ]
 
 
@@ -102,6 +107,7 @@ def lib():
         _lib.orc_line_op.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                      ctypes.c_double, P, P]
         _lib.orc_tridiag.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int, P, P]
+        _lib.orc_set_inflow_profile.argtypes = [vp, ctypes.c_int, ctypes.c_int, P]
     return _lib
 
 
@@ -114,13 +120,15 @@ DEFAULTS = dict(gamma=1.4, minf=1.0, scheme="MEG6", hybrid_mode=HYB_GLOBAL, hybr
                 hyb_rho=-math.inf, hyb_p=-math.inf, cfl=0.2, c_beta=1.75, c_kappa=0.01,
                 alpha_f=0.45, sensor_thresh=0.01, mp_eps=1e-20, mp_alpha=4.0,
                 read_mp_printed=0, read_acoustic_mp5=0, omega_window=4,
-                positivity_fallback=1, filter_on=1)
+                positivity_fallback=1, filter_on=1, viscous=0, re=1.0, pr=0.72, suth=0.0,
+                twall=1.0)
 
 
 def make_params(problem, **over):
     """problem: dict with ndim, n, bc (ndim x 2), h or curvilinear info, inflow."""
     d = dict(DEFAULTS)
-    d.update({k: problem[k] for k in ("gamma",) if k in problem})
+    d.update({k: problem[k] for k in ("gamma", "minf", "viscous", "re", "pr", "suth", "twall")
+              if k in problem})
     d.update(over)
     p = OrcParams()
     nd = problem["ndim"]
@@ -142,10 +150,10 @@ def make_params(problem, **over):
     s = d["scheme"]
     p.scheme = SCHEMES[s] if isinstance(s, str) else int(s)
     for k in ("hybrid_mode", "hybrid_sensor", "read_mp_printed", "read_acoustic_mp5",
-              "omega_window", "positivity_fallback", "filter_on"):
+              "omega_window", "positivity_fallback", "filter_on", "viscous"):
         setattr(p, k, int(d[k]))
     for k in ("hyb_rho", "hyb_p", "cfl", "c_beta", "c_kappa", "alpha_f", "sensor_thresh",
-              "mp_eps", "mp_alpha"):
+              "mp_eps", "mp_alpha", "re", "pr", "suth", "twall"):
         setattr(p, k, float(d[k]))
     return p
 
@@ -164,6 +172,10 @@ class Oracle:
         L = lib()
         self._ctx = L.orc_create(ctypes.byref(self.params),
                                  None if self._xyz is None else _ptr(self._xyz))
+        for (d, side), W in problem.get("inflow_profile", {}).items():
+            Wp = np.ascontiguousarray(W, dtype=np.float64)
+            if L.orc_set_inflow_profile(self._ctx, int(d), int(side), _ptr(Wp)) != 0:
+                raise ValueError("inflow profile on a face that is not an inflow face")
 
     def __del__(self):
         if getattr(self, "_ctx", None):

@@ -30,8 +30,15 @@
  * (sympy); RK3 order; periodic conservation; freestream on curvilinear 2D/3D
  * grids; exact metrics of an affine grid; x<->y symmetry of the 2D Riemann
  * configuration 3; hybrid limits; CFL closed form; hand values of beta* and of
- * the sensor.  Parity unpinned: the value of the thermal coefficient kappa*
- * (exercised only through the LAD conservation, freestream and Sod tests).
+ * the sensor.  Viscous terms (tests/test_oracle_viscous.py): discrete decay
+ * rate of periodic and wall-bounded shear waves (E4 and C6 modified
+ * wavenumbers) and their energy source; the isothermal no-slip wall as the
+ * mirror of the doubled periodic channel; fourth-order convergence of the 3D
+ * viscous terms on Cartesian and curvilinear grids and of heat conduction at
+ * rest; a parallel flow fed by its own inflow profile is steady; Sutherland
+ * against tabulated air viscosity.  Parity unpinned: the value of the thermal
+ * coefficient kappa* (exercised only through the LAD conservation, freestream
+ * and Sod tests).
  */
 #include <math.h>
 #include <stdlib.h>
@@ -50,6 +57,7 @@ typedef struct {
     double *jac;      /* J, padded */
     double *xt[3][3]; /* interface metrics \tilde\xi_{l,m} at l-interface i+1/2, stored at node i */
     double *dxl[3][3];/* LAD displacement vector Delta x_l, component m (Eq. 6) */
+    double *prof[3][2]; /* per-node inflow profiles (primitive), or NULL */
 } ctx_t;
 
 /* ------------------------------------------------------------------ */
@@ -132,9 +140,37 @@ static void prim_to_cons(int nd, double gamma, const double *W, double *Q)
 /* mode 0: primitive state, 1: conserved state, 2: scalar field.      */
 /* extrapolation copies the boundary node; a reflective wall mirrors  */
 /* (ghost -q <- node q-1) and negates the wall-normal velocity or      */
-/* momentum; inflow holds the given state; periodic wraps.  A scalar   */
-/* field wraps, mirrors at a wall and copies otherwise.                */
+/* momentum; inflow holds the given state (constant, or the profile of */
+/* the transverse position); periodic wraps.  The isothermal no-slip   */
+/* wall mirrors with every velocity component negated, the pressure    */
+/* kept and the temperature reflected about the wall value,            */
+/* T_ghost = 2 T_w - T_mirror (so u = 0 and T = T_w at the face to      */
+/* second order).  A scalar field wraps, mirrors at either wall and    */
+/* copies otherwise.                                                   */
 /* ------------------------------------------------------------------ */
+static void wall_prim(const ctx_t *c, const double *Wm, double *Wg)
+{
+    int nd = c->nd, ip = nd + 1;
+    double gm2 = c->p.gamma * c->p.minf * c->p.minf;
+    double Tm = gm2 * Wm[ip] / Wm[0];
+    double Tg = 2.0 * c->p.twall - Tm;
+    Wg[ip] = Wm[ip];
+    Wg[0] = gm2 * Wg[ip] / Tg;
+    for (int m = 0; m < nd; ++m) Wg[1 + m] = -Wm[1 + m];
+}
+
+static long profile_index(const ctx_t *c, int d, const int *a)
+{
+    long pi = 0, mul = 1;
+    for (int e = 0; e < c->nd; ++e) {
+        if (e == d) continue;
+        int x = a[e] < 0 ? 0 : (a[e] >= c->n[e] ? c->n[e] - 1 : a[e]);
+        pi += (long)x * mul;
+        mul *= c->n[e];
+    }
+    return pi;
+}
+
 static void fill_ghosts(const ctx_t *c, double *f, int nc, int mode)
 {
     int nd = c->nd;
@@ -147,8 +183,10 @@ static void fill_ghosts(const ctx_t *c, double *f, int nc, int mode)
         }
         b.lo[d] = 0; b.hi[d] = 1; /* iterate lines along d */
         int n = c->n[d];
+        long face = c->N / n;
         for (int side = 0; side < 2; ++side) {
             int bc = c->p.bc[d][side];
+            const double *prof = bc == ORC_BC_INFLOW ? c->prof[d][side] : NULL;
             double fixed[5];
             if (bc == ORC_BC_INFLOW && mode != 2) {
                 if (mode == 0) for (int v = 0; v < c->nv; ++v) fixed[v] = c->p.inflow[d][side][v];
@@ -156,15 +194,35 @@ static void fill_ghosts(const ctx_t *c, double *f, int nc, int mode)
             }
             for (int q = 1; q <= c->g[d]; ++q) {
                 int gi = side == 0 ? -q : n - 1 + q;
-                int src, flip = 0, isfixed = 0;
+                int src, flip = 0, isfixed = 0, wall = 0;
                 if (bc == ORC_BC_PERIODIC) src = imod(gi, n);
                 else if (bc == ORC_BC_REFLECT) { src = side == 0 ? q - 1 : n - q; flip = (mode != 2); }
+                else if (bc == ORC_BC_WALL) { src = side == 0 ? q - 1 : n - q; wall = (mode != 2); }
                 else if (bc == ORC_BC_INFLOW && mode != 2) { src = 0; isfixed = 1; }
                 else src = side == 0 ? 0 : n - 1;
                 FOR_BOX(b, i, j, k) {
                     int a[3] = {i, j, k}, s[3] = {i, j, k};
                     a[d] = gi; s[d] = src;
                     long qa = pidx(c, a[0], a[1], a[2]), qs = pidx(c, s[0], s[1], s[2]);
+                    if (isfixed && prof) {
+                        long pi = profile_index(c, d, a);
+                        double Wf[5], Qf[5];
+                        for (int v = 0; v < c->nv; ++v) Wf[v] = prof[v * face + pi];
+                        if (mode == 1) prim_to_cons(nd, c->p.gamma, Wf, Qf);
+                        for (int v = 0; v < nc; ++v) f[v * c->NP + qa] = mode == 1 ? Qf[v] : Wf[v];
+                        continue;
+                    }
+                    if (wall) {
+                        double Wm[5], Wg[5], Q[5];
+                        for (int v = 0; v < nc; ++v) Q[v] = f[v * c->NP + qs];
+                        if (mode == 1) cons_to_prim(nd, c->p.gamma, Q, Wm);
+                        else for (int v = 0; v < nc; ++v) Wm[v] = Q[v];
+                        wall_prim(c, Wm, Wg);
+                        if (mode == 1) prim_to_cons(nd, c->p.gamma, Wg, Q);
+                        else for (int v = 0; v < nc; ++v) Q[v] = Wg[v];
+                        for (int v = 0; v < nc; ++v) f[v * c->NP + qa] = Q[v];
+                        continue;
+                    }
                     for (int v = 0; v < nc; ++v) {
                         if (isfixed) f[v * c->NP + qa] = fixed[v];
                         else if (flip && v == 1 + d) f[v * c->NP + qa] = -f[v * c->NP + qs];
@@ -744,7 +802,21 @@ typedef struct {
     double *beta, *kappa; /* filtered coefficients, padded (ghosts by the scalar rule) */
 } lad_out;
 
-static void lad_fluxes(const ctx_t *c, const double *Wp, int dkind, lad_out *out)
+/* mode LADF_FULL: F^c - F^v with the artificial coefficients and, when the
+ * case is viscous, the physical ones; LADF_NOPHYS: without the physical
+ * viscosity; LADF_VISC: the physical viscous flux alone, -F^v (beta* and
+ * kappa* are not computed). */
+enum { LADF_FULL = 0, LADF_NOPHYS = 1, LADF_VISC = 2 };
+
+/* Sutherland's law in units of the free-stream viscosity and temperature,
+ * divided by Re: mu_hat(T) = T^{3/2} (1 + S) / (T + S) / Re (Sec. 2.1). */
+static double mu_hat(const ctx_t *c, double T)
+{
+    double S = c->p.suth;
+    return T * sqrt(T) * (1.0 + S) / (T + S) / c->p.re;
+}
+
+static void lad_fluxes(const ctx_t *c, const double *Wp, int dkind, int mode, lad_out *out)
 {
     int nd = c->nd, nv = c->nv, ip = nd + 1;
     double gamma = c->p.gamma;
@@ -791,6 +863,8 @@ static void lad_fluxes(const ctx_t *c, const double *Wp, int dkind, lad_out *out
     /* raw coefficients at interior nodes, Eq. (4)-(6) */
     double *bt = padded(c, 1), *kp = padded(c, 1);
     box_t b0 = box_grow(c, 0);
+    double *tmp = padded(c, 1);
+    if (mode != LADF_VISC) {
     FOR_BOX(b0, i, j, k) {
         long q = pidx(c, i, j, k);
         double rho = Wp[q];
@@ -837,7 +911,6 @@ static void lad_fluxes(const ctx_t *c, const double *Wp, int dkind, lad_out *out
         kp[q] = c->p.c_kappa * (rho * cs[q] / T) * fabs(sk);
     }
     /* truncated-Gaussian overbar, applied along xi, eta, zeta in turn */
-    double *tmp = padded(c, 1);
     double *fld[2] = {bt, kp};
     for (int w = 0; w < 2; ++w) {
         for (int l = 0; l < nd; ++l) {
@@ -854,9 +927,16 @@ static void lad_fluxes(const ctx_t *c, const double *Wp, int dkind, lad_out *out
         }
         fill_ghosts(c, fld[w], 1, 2);
     }
+    }
     /* node fluxes along each direction at positions [-2, n+1] (interior lines):
      * tau = beta* div I (the stress of Eq. 3 with mu = 0: no physical viscosity
-     * in the inviscid cases and C_mu not employed), phi_m = u_m tau + kappa* dT/dx_m */
+     * in the inviscid cases and C_mu not employed), phi_m = u_m tau + kappa* dT/dx_m.
+     * Viscous cases (Eq. 3 with Stokes' hypothesis): tau_mi = mu (du_i/dx_m +
+     * du_m/dx_i) + delta_mi (beta* - 2/3 mu) div, phi_m = sum_i u_i tau_mi +
+     * (kappa* + kappa_hat) dT/dx_m. */
+    int conv = mode != LADF_VISC, art = mode != LADF_VISC;
+    int phys = c->p.viscous && mode != LADF_NOPHYS;
+    double kc = (gamma - 1.0) * c->p.pr * c->p.minf * c->p.minf;
     for (int l = 0; l < nd; ++l) {
         out->Fn[l] = padded(c, nv);
         box_t bl = box_grow(c, 0);
@@ -866,7 +946,37 @@ static void lad_fluxes(const ctx_t *c, const double *Wp, int dkind, lad_out *out
             double W[5], xi[3], Fc[5];
             for (int v = 0; v < nv; ++v) W[v] = Wp[v * c->NP + q];
             for (int m = 0; m < nd; ++m) xi[m] = c->xh[l][m][q];
-            orc_euler_flux(nd, gamma, W, xi, Fc);
+            if (conv) orc_euler_flux(nd, gamma, W, xi, Fc);
+            else for (int v = 0; v < nv; ++v) Fc[v] = 0.0;
+            if (phys) {
+                double T = fs[nd * c->NP + q];
+                double mu = mu_hat(c, T);
+                double kth = mu / kc;
+                double lam = (art ? bt[q] : 0.0) - (2.0 / 3.0) * mu;
+                double kap = (art ? kp[q] : 0.0) + kth;
+                double tau[3][3];
+                for (int m = 0; m < nd; ++m)
+                    for (int a = 0; a < nd; ++a) {
+                        double sm = gr[(a * nd + m) * c->NP + q] + gr[(m * nd + a) * c->NP + q];
+                        tau[m][a] = mu * sm;
+                        if (m == a) tau[m][a] = tau[m][a] + lam * dv[q];
+                    }
+                double fe = 0.0;
+                for (int m = 0; m < nd; ++m) {
+                    double phi = W[1] * tau[m][0];
+                    for (int a = 1; a < nd; ++a) phi = phi + W[1 + a] * tau[m][a];
+                    phi = phi + kap * gr[(nd * nd + m) * c->NP + q];
+                    fe = m == 0 ? xi[m] * phi : fe + xi[m] * phi;
+                }
+                out->Fn[l][q] = Fc[0];
+                for (int a = 0; a < nd; ++a) {
+                    double fv = xi[0] * tau[0][a];
+                    for (int m = 1; m < nd; ++m) fv = fv + xi[m] * tau[m][a];
+                    out->Fn[l][(1 + a) * c->NP + q] = Fc[1 + a] + (-fv);
+                }
+                out->Fn[l][ip * c->NP + q] = Fc[ip] + (-fe);
+                continue;
+            }
             double tau = bt[q] * dv[q];
             double fe = 0.0;
             for (int m = 0; m < nd; ++m) {
@@ -952,10 +1062,23 @@ static long global_troubled(const ctx_t *c, const double *Wp)
     return cnt;
 }
 
+/* Physical viscous terms of the C-GBR and per-interface hybrid stages
+ * (reading: the paper's viscous routines are central differences shared with
+ * the LAD framework, without the alpha-damping interface scheme): node
+ * fluxes -F^v from E4 gradients, acc += E4 derivative along each direction. */
+static void viscous_pass(const ctx_t *c, const double *Wp, double *acc)
+{
+    lad_out lv;
+    lad_fluxes(c, Wp, 2, LADF_VISC, &lv);
+    lad_divergence(c, lv.Fn, 2, acc);
+    free_lad(&lv, c->nd);
+}
+
 /* scheme: the effective scheme of this stage; acc must be zeroed */
 static void rhs_acc(const ctx_t *c, const double *Wp, int scheme, double *acc, double *iface_out, int iface_dir)
 {
     int nd = c->nd, nv = c->nv;
+    if (c->p.viscous && scheme != ORC_LAD_E4 && scheme != ORC_LAD_C6) viscous_pass(c, Wp, acc);
     if (scheme == ORC_MEG6 || scheme == ORC_MIG4) {
         double *Wd[3] = {NULL, NULL, NULL};
         for (int l = 0; l < nd; ++l) {
@@ -974,7 +1097,7 @@ static void rhs_acc(const ctx_t *c, const double *Wp, int scheme, double *acc, d
         for (int l = 0; l < nd; ++l) free(Wd[l]);
     } else if (scheme == ORC_LAD_E4 || scheme == ORC_LAD_C6) {
         lad_out lo;
-        lad_fluxes(c, Wp, scheme == ORC_LAD_E4 ? 2 : 3, &lo);
+        lad_fluxes(c, Wp, scheme == ORC_LAD_E4 ? 2 : 3, LADF_FULL, &lo);
         lad_divergence(c, lo.Fn, scheme == ORC_LAD_E4 ? 2 : 3, acc);
         free_lad(&lo, nd);
     } else { /* per-cell hybrid: GBR-MEG6 flux where a neighbour is troubled, else LAD-E4 in flux form */
@@ -994,7 +1117,7 @@ static void rhs_acc(const ctx_t *c, const double *Wp, int scheme, double *acc, d
             tr[q] = (unsigned char)t;
         }
         lad_out lo;
-        lad_fluxes(c, Wp, 2, &lo);
+        lad_fluxes(c, Wp, 2, LADF_NOPHYS, &lo);
         double *Fi = padded(c, nv);
         unsigned char *mask = (unsigned char *)calloc(c->NP, 1);
         for (int d = 0; d < nd; ++d) {
@@ -1211,7 +1334,7 @@ int orc_lad_coeffs(void *ctx, const double *U, double *beta, double *kappa)
     const ctx_t *c = (const ctx_t *)ctx;
     double *Wp = padded_prims(c, U);
     lad_out lo;
-    lad_fluxes(c, Wp, c->p.scheme == ORC_LAD_C6 ? 3 : 2, &lo);
+    lad_fluxes(c, Wp, c->p.scheme == ORC_LAD_C6 ? 3 : 2, LADF_NOPHYS, &lo);
     box_t b0 = box_grow(c, 0);
     FOR_BOX(b0, i, j, k) {
         beta[iidx(c, i, j, k)] = lo.beta[pidx(c, i, j, k)];
@@ -1449,12 +1572,24 @@ void *orc_create(const orc_params *p, const double *xyz)
     return c;
 }
 
+int orc_set_inflow_profile(void *ctx, int d, int side, const double *W)
+{
+    ctx_t *c = (ctx_t *)ctx;
+    if (d < 0 || d >= c->nd || side < 0 || side > 1 || c->p.bc[d][side] != ORC_BC_INFLOW) return -1;
+    long face = c->N / c->n[d];
+    free(c->prof[d][side]);
+    c->prof[d][side] = (double *)malloc(sizeof(double) * (size_t)(face * c->nv));
+    memcpy(c->prof[d][side], W, sizeof(double) * (size_t)(face * c->nv));
+    return 0;
+}
+
 void orc_destroy(void *ctx)
 {
     ctx_t *c = (ctx_t *)ctx;
     if (!c) return;
     for (int l = 0; l < 3; ++l)
         for (int m = 0; m < 3; ++m) { free(c->xh[l][m]); free(c->xt[l][m]); free(c->dxl[l][m]); }
+    for (int d = 0; d < 3; ++d) { free(c->prof[d][0]); free(c->prof[d][1]); }
     free(c->jac);
     free(c);
 }

@@ -21,7 +21,9 @@
 extern "C" {
 #endif
 
-enum { ORC_BC_PERIODIC = 0, ORC_BC_EXTRAP = 1, ORC_BC_REFLECT = 2, ORC_BC_INFLOW = 3 };
+/* ORC_BC_WALL: no-slip isothermal wall at the boundary face (Sec. 3.3: the
+ * compression ramps); a supersonic outflow is ORC_BC_EXTRAP. */
+enum { ORC_BC_PERIODIC = 0, ORC_BC_EXTRAP = 1, ORC_BC_REFLECT = 2, ORC_BC_INFLOW = 3, ORC_BC_WALL = 4 };
 enum { ORC_MEG6 = 0, ORC_MIG4 = 1, ORC_LAD_E4 = 2, ORC_LAD_C6 = 3, ORC_HYBRID = 4 };
 enum { ORC_HYB_GLOBAL = 0, ORC_HYB_CELL = 1 };
 
@@ -44,6 +46,13 @@ typedef struct {
     int omega_window;         /* interface sensor = max of Omega over nodes i-w+1..i+w (1..4) */
     int positivity_fallback;  /* first-order interface states when rho or p <= 0 */
     int filter_on;            /* LAD-C6: implicit filter after the last RK stage */
+    /* Physical viscosity (Sec. 2.1, Eq. 3): mu_hat = mu(T)/Re with the
+     * Sutherland law mu(T) = T^{3/2} (1 + S)/(T + S) (T, S in units of
+     * T_inf), Stokes' hypothesis, kappa_hat = mu_hat/((gamma-1) Pr M^2). */
+    int viscous;
+    double re, pr;
+    double suth;              /* Sutherland constant S / T_inf */
+    double twall;             /* temperature of ORC_BC_WALL faces (units of T_inf) */
 } orc_params;
 
 /* Context: holds the metrics (computed from the coordinates for curvilinear
@@ -86,6 +95,12 @@ int orc_line_op(int kind, int n, int ng, int periodic, double alpha_f,
 /* Tridiagonal solve with constant off-diagonal a, unit diagonal, cyclic or not
  * (rows 0 and n-1 decoupled when not cyclic).  Used by the pins. */
 void orc_tridiag(int n, double a, int cyclic, const double *rhs, double *x);
+/* Inflow face (d, side) holds a per-node primitive profile instead of the
+ * constant state: W has nv planes over the face's nodes (the other active
+ * directions, lowest first, e.g. j + n1*k for d = 0).  Ghost nodes of the face
+ * at any depth take the profile of their transverse position (clamped to the
+ * face).  Copied; returns 0, or -1 if the face is not an inflow face. */
+int orc_set_inflow_profile(void *ctx, int d, int side, const double *W);
 
 #ifdef __cplusplus
 }

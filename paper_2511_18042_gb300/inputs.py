@@ -213,3 +213,136 @@ def batched_riemann(count=256, seed=0, n_lo=64, n_hi=512):
     rng = np.random.default_rng(seed)
     sizes = np.rint(np.exp(rng.uniform(math.log(n_lo), math.log(n_hi), count))).astype(int)
     return [random_quadrants(rng, int(n)) for n in sizes]
+
+
+# ---------------------------------------------------------------- viscous cases
+PRANDTL = 0.72
+
+
+def _viscous(d, re, minf, suth=0.0, twall=1.0, pr=PRANDTL):
+    d.update(viscous=1, re=float(re), minf=float(minf), suth=float(suth), twall=float(twall), pr=float(pr))
+    return d
+
+
+def shear_wave(n=32, amp=1e-3, minf=0.2, re=100.0, suth=0.0):
+    """2D periodic shear wave u = amp sin(2 pi y), v = 0, rho = 1, p = 1/(gamma M^2)
+    (T = 1) on [0,1]^2: a linear viscous decay at rate nu (2 pi)^2."""
+    gamma = 1.4
+    h = 1.0 / n
+    x = (np.arange(n) + 0.5) * h
+    X, Y = np.meshgrid(x, x)
+    W = np.zeros((4, n, n))
+    W[0] = 1.0
+    W[1] = amp * np.sin(2 * math.pi * Y)
+    W[3] = 1.0 / (gamma * minf * minf)
+    d = _problem("shear_wave", 2, [n, n], [h, h], [[PERIODIC, PERIODIC]] * 2, W, gamma, amp=amp)
+    return _viscous(d, re, minf, suth)
+
+
+def wall_channel(n=32, nx=8, minf=0.5, re=50.0, suth=0.5, twall=1.0, fields=None, bc_y=None):
+    """2D channel [0, nx/n] x [0,1] (x periodic) with isothermal no-slip walls at
+    y = 0 and y = 1 (bc_y overrides).  fields(X, Y) -> (u, v, p, T) primitive
+    profiles; default: u = 1e-3 sin(pi y), v = 0, p = 1/(gamma M^2), T = twall."""
+    gamma = 1.4
+    h = 1.0 / n
+    x = (np.arange(nx) + 0.5) * h
+    y = (np.arange(n) + 0.5) * h
+    X, Y = np.meshgrid(x, y)
+    if fields is None:
+        u, v = 1e-3 * np.sin(math.pi * Y), 0.0 * Y
+        p, T = np.full_like(Y, 1.0 / (gamma * minf * minf)), np.full_like(Y, twall)
+    else:
+        u, v, p, T = fields(X, Y)
+    W = np.stack([gamma * minf * minf * p / T, u, v, p])
+    bc = [[PERIODIC, PERIODIC], bc_y if bc_y is not None else [WALL, WALL]]
+    d = _problem("wall_channel", 2, [nx, n], [h, h], bc, W, gamma)
+    return _viscous(d, re, minf, suth, twall)
+
+
+WALL = 4
+
+
+def compression_ramp(nx=768, ny=192, nz=128, mach=2.9, re_theta=2400.0, angle_deg=24.0, corner=0.4,
+                     Lx=534.6, Ly=161.0, Lz=61.2, delta=20.4, cf=2.2e-3, t_inf_kelvin=108.1,
+                     noise=0.05, seed=0, cfl=0.2):
+    """3D supersonic compression ramp (Sec. 3.3, M = 2.9, 24 degrees), lengths in
+    units of the inflow momentum thickness theta (so Re = Re_theta):
+
+    * body-fitted algebraic grid, uniform in x and z.  The wall y_w(x) is flat
+      up to x_c = corner * Lx, then rises at the ramp angle (corner rounded
+      over four cells).  Wall-normal lines are vertical; node rows sit at
+      eta_j = (j + 1/2) / ny of the tanh stretching
+      y = y_w + Ly (1 + tanh(b (eta - 1)) / tanh(b)), with b chosen so that the
+      first row is at half the viscous length nu_w / u_tau above the wall
+      (a first cell of y+ = 1, the wall face half-way between row 0 and its
+      mirror ghost).  u_tau comes from an assumed skin friction cf with the
+      wall density and Sutherland viscosity;
+    * wall temperature 1.14 times the recovery temperature (recovery factor
+      0.89), Sutherland constant 110.4 K / T_inf, Pr = 0.72;
+    * mean boundary layer of thickness delta: u = min((y_n/delta)^{1/7},
+      y_n u_tau^2 / nu_w) (power law over a linear sublayer), Crocco-Busemann
+      temperature, uniform pressure, flow along the local wall direction, with
+      y_n = y - y_w(x); the initial state is this mean flow;
+    * inflow plane (x = 0): the mean profile plus seeded uniform velocity
+      fluctuations of amplitude noise * 4 u (1 - u) (frozen in time);
+    * boundaries: x inflow profile / supersonic outflow (extrapolation),
+      y isothermal wall / extrapolation, z periodic."""
+    gamma = 1.4
+    suth = 110.4 / t_inf_kelvin
+    t_rec = 1.0 + 0.89 * 0.5 * (gamma - 1.0) * mach * mach
+    t_wall = 1.14 * t_rec
+    mu_w = t_wall ** 1.5 * (1.0 + suth) / (t_wall + suth)
+    rho_w = 1.0 / t_wall
+    u_tau = math.sqrt(0.5 * cf / rho_w)
+    nu_w = mu_w / (re_theta * rho_w)
+    dy1 = nu_w / u_tau
+    eta = (np.arange(ny) + 0.5) / ny
+
+    def row0(b):
+        return Ly * (1.0 + math.tanh(b * (eta[0] - 1.0)) / math.tanh(b))
+
+    lo, hi = 1e-3, 30.0
+    for _ in range(200):  # bisection: row0 decreases as b grows
+        mid = 0.5 * (lo + hi)
+        if row0(mid) > 0.5 * dy1:
+            lo = mid
+        else:
+            hi = mid
+    b = 0.5 * (lo + hi)
+    s = 1.0 + np.tanh(b * (eta - 1.0)) / math.tanh(b)
+    x = np.arange(nx) * (Lx / (nx - 1.0))
+    z = np.arange(nz) * (Lz / nz)
+    xc = corner * Lx
+    w = 4.0 * Lx / (nx - 1.0)
+    ta = math.tan(math.radians(angle_deg))
+    yw = ta * w * np.logaddexp(0.0, (x - xc) / w)
+    yw = yw - yw[0]
+    Z, S, X = np.meshgrid(z, s, x, indexing="ij")
+    YW = np.broadcast_to(yw[None, None, :], X.shape)
+    Y = YW + Ly * S
+    xyz = np.stack([X, Y, Z])
+    yn = Y - YW
+    ubl = np.minimum(np.clip(yn / delta, 0.0, 1.0) ** (1.0 / 7.0), yn * u_tau * u_tau / nu_w)
+    T = t_wall + (t_rec - t_wall) * ubl + (1.0 - t_rec) * ubl * ubl
+    p0 = 1.0 / (gamma * mach * mach)
+    slope = np.gradient(yw, x)
+    cth = 1.0 / np.sqrt(1.0 + slope * slope)
+    sth = slope * cth
+    u = ubl * cth[None, None, :]
+    v = ubl * sth[None, None, :]
+    p = np.full_like(T, p0)
+    W = np.stack([gamma * mach * mach * p / T, u, v, np.zeros_like(u), p])
+    # inflow plane: mean profile at x = 0 plus frozen seeded fluctuations
+    rng = np.random.default_rng(seed)
+    Win = W[:, :, :, 0].copy()
+    amp = noise * 4.0 * ubl[:, :, 0] * (1.0 - ubl[:, :, 0])
+    Win[1:4] += rng.uniform(-1.0, 1.0, size=(3,) + amp.shape) * amp
+    n = [nx, ny, nz]
+    period = [[0.0, 0.0, 0.0], [0.0, 0.0, 0.0], [0.0, 0.0, Lz]]
+    d = _problem("compression_ramp", 3, n, [1.0, 1.0, 1.0],
+                 [[INFLOW, EXTRAP], [WALL, EXTRAP], [PERIODIC, PERIODIC]], W, gamma,
+                 xyz=np.ascontiguousarray(xyz), period=period, cfl=cfl, t_wall=t_wall, dy1=dy1,
+                 stretch=b, suth_kelvin=110.4, t_inf_kelvin=t_inf_kelvin)
+    d["inflow_profile"] = {(0, 0): np.ascontiguousarray(Win.reshape(5, -1))}
+    d["inflow"] = {(0, 0): (1.0, 1.0, 0.0, 0.0, p0)}
+    return _viscous(d, re_theta, mach, suth, t_wall)
