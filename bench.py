@@ -205,7 +205,8 @@ def run_gpu(args):
         ms = time_mixed(api, torch, grid, base, dev, kw, args)
         mixed[n] = {"cell_updates_per_s": cells / (ms * 1e-3), "ms_per_rk3_step": ms}
 
-    sod = run_sod_latency(api, torch, dev)
+    sod = run_sod_latency(api, torch, dev) if args.sod else None
+    ramp = run_ramp(api, torch, dev, args) if args.ramp else None
     batched = run_batched(api, torch, dev, args) if args.batched else None
     serving = run_serving(args) if args.serving else None
 
@@ -243,7 +244,7 @@ def run_gpu(args):
                                "from a developed state (200 MEG6 steps)" % len(names),
                    "schemes": names, "cells": cells, "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
-        "per_scheme": per_scheme, "mixed_precision": mixed, "sod_latency": sod, "batched": batched,
+        "per_scheme": per_scheme, "mixed_precision": mixed, "sod_latency": sod, "compression_ramp": ramp, "batched": batched,
         "serving": serving,
         "roofline": roof, "e2e": e2e, "gpu_launches": launches // max(1, args.steps),
         "gpu_launches_timed_total": launches, "wall_s_timed": wall, "clocks": clk.summary(),
@@ -262,6 +263,51 @@ def _hybrid_kw(prob, precision):
     st = prob["quad_states"]
     return dict(scheme="HYBRID", hybrid_mode=1, hybrid_sensor=1, hyb_rho=0.5 * float(st[:, 0].min()),
                 hyb_p=0.5 * float(st[:, 3].min()), precision=precision)
+
+
+RAMP_SCHEMES = [("LAD_E4", dict(scheme="LAD_E4")), ("MEG6", dict(scheme="MEG6")), ("MIG4", dict(scheme="MIG4")),
+                ("HYBRID_GLOBAL", dict(scheme="HYBRID", hybrid_mode=0, hyb_rho=0.3)),
+                ("HYBRID_CELL", dict(scheme="HYBRID", hybrid_mode=1, hybrid_sensor=1, hyb_rho=0.3))]
+
+
+def run_ramp(api, torch, dev, args):
+    """3D M2.9 compression ramp, 768x192x128 body-fitted (metrics on the
+    device), Sutherland viscosity, isothermal wall, inflow boundary-layer
+    profile with frozen fluctuations: ms per RK3 step (with the device CFL
+    step) per scheme in FP64 and in the mixed form, over args.ramp_steps steps
+    after one warm-up step, events on the launching stream."""
+    from paper_2511_18042_gb300 import inputs
+    prob = inputs.compression_ramp()
+    cells = prob["n"][0] * prob["n"][1] * prob["n"][2]
+    base = torch.as_tensor(prob["U"], device=dev)
+    grid = api.Grid.from_problem(prob)
+    out = {}
+    for prec in (0, 1):
+        for name, kw in RAMP_SCHEMES:
+            s = api.Solver.from_problem(prob, grid=grid, precision=prec, **kw)
+            U = base.clone()
+            dtd = torch.zeros(2, dtype=torch.float64, device=dev)
+            s.cfl_dt(U, out=dtd)
+            s.rk3_step(U, dtd)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(args.ramp_steps):
+                s.cfl_dt(U, out=dtd)
+                s.rk3_step(U, dtd)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.ramp_steps
+            key = name + ("_MIXED" if prec else "")
+            out[key] = {"ms_per_rk3_step": ms, "cell_updates_per_s": cells / (ms * 1e-3),
+                        "status": s.sync_status()}
+            del s, U
+            torch.cuda.empty_cache()
+    ratios = {"MIG4_over_" + k: out["MIG4"]["ms_per_rk3_step"] / out[k]["ms_per_rk3_step"]
+              for k in ("LAD_E4", "HYBRID_GLOBAL", "HYBRID_CELL")}
+    return {"workload": "M2.9 24-degree compression ramp 768x192x128 (%d cells), curvilinear, viscous; "
+                        "%d RK3 steps from the initial boundary layer after one warm-up step" % (cells, args.ramp_steps),
+            "per_scheme": out, "speed_ratios": ratios}
 
 
 def run_sod_latency(api, torch, dev, steps=200):
@@ -494,6 +540,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-batched", dest="batched", action="store_false")
     ap.add_argument("--no-serving", dest="serving", action="store_false")
+    ap.add_argument("--no-sod", dest="sod", action="store_false")
+    ap.add_argument("--no-ramp", dest="ramp", action="store_false")
+    ap.add_argument("--ramp-steps", type=int, default=3)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

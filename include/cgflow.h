@@ -49,7 +49,11 @@ typedef enum {
     CG_ERR_TIMEOUT = -6
 } cg_status;
 
-typedef enum { CG_BC_PERIODIC = 0, CG_BC_EXTRAP = 1, CG_BC_REFLECT = 2, CG_BC_INFLOW = 3 } cg_bc;
+/* CG_BC_WALL: isothermal no-slip wall at the boundary face (the compression
+ * ramps of Sec. 3.3); ghost nodes mirror the interior with every velocity
+ * component negated, the pressure kept and T_ghost = 2 twall - T.  A
+ * supersonic outflow is CG_BC_EXTRAP. */
+typedef enum { CG_BC_PERIODIC = 0, CG_BC_EXTRAP = 1, CG_BC_REFLECT = 2, CG_BC_INFLOW = 3, CG_BC_WALL = 4 } cg_bc;
 typedef enum { CG_MEG6 = 0, CG_MIG4 = 1, CG_LAD_E4 = 2, CG_LAD_C6 = 3, CG_HYBRID = 4 } cg_scheme;
 typedef enum { CG_HYBRID_GLOBAL = 0, CG_HYBRID_CELL = 1 } cg_hybrid_mode;
 typedef enum { CG_FP64 = 0, CG_MIXED = 1 } cg_precision;
@@ -76,11 +80,21 @@ typedef struct {
     int filter_on;        /* LAD-C6: implicit filter after the last RK stage */
     int omega_window;     /* interface sensor window half-width w (1..4): max over nodes i-w+1..i+w */
     double inflow[3][2][5]; /* primitive (rho, u.., p) held on CG_BC_INFLOW faces [dir][side] */
+    /* Physical viscosity (Sec. 2.1, Eq. 3): mu_hat = mu(T) / re with
+     * Sutherland's law mu(T) = T^{3/2} (1 + suth) / (T + suth) (T in units of
+     * T_inf), Stokes' hypothesis, kappa_hat = mu_hat / ((gamma-1) pr minf^2).
+     * LAD schemes add it to their node fluxes; C-GBR and the per-interface
+     * hybrid add an E4 central pass of node viscous fluxes. */
+    int viscous;          /* 0: inviscid */
+    double re, pr;        /* Reynolds number (reference length 1), Prandtl number */
+    double suth;          /* Sutherland constant S / T_inf */
+    double twall;         /* temperature of CG_BC_WALL faces (units of T_inf) */
 } cg_params;
 
 /* Fills the defaults: gamma 1.4, minf 1, MEG6, FP64, CFL 0.2, C_beta 1.75,
  * C_kappa 0.01, alpha_f 0.45, Omega threshold 0.01, MP eps 1e-20, alpha 4,
- * window 4, filter on, no hybrid thresholds. */
+ * window 4, filter on, no hybrid thresholds, inviscid (re 1, pr 0.72,
+ * suth 0, twall 1). */
 CG_API void cg_params_default(cg_params *p);
 
 /* Uniform Cartesian grid, node spacing h[d] (Sec. 2.1 with x = xi h).
@@ -100,6 +114,16 @@ CG_API void cg_grid_destroy(cg_grid *g);
 /* Solver = grid + parameters + scratch.  The grid must outlive the solver. */
 CG_API int cg_solver_create(const cg_grid *g, const cg_params *p, cg_solver **out);
 CG_API void cg_solver_destroy(cg_solver *s);
+
+/* Inflow face (dir, side) holds a per-node primitive profile instead of the
+ * constant params.inflow state (e.g. a boundary layer with frozen
+ * fluctuations).  W_host: host memory, nv planes over the face's nodes (the
+ * other active directions, lowest first: j + n1*k for dir 0), copied to the
+ * device (the call synchronises).  Ghost nodes of the face at every depth
+ * take the profile of their transverse position, clamped to the face.  Call
+ * before stepping (a captured batch graph keeps the profile it saw).
+ * CG_ERR_INVALID_ARG if the face is not a CG_BC_INFLOW face. */
+CG_API int cg_solver_set_inflow_profile(cg_solver *s, int dir, int side, const double *W_host);
 
 /* Metrics on interior nodes: node_dev gets ndim*ndim planes xi_hat[l][m]
  * then one plane J; iface_dev (may be NULL) gets ndim*ndim planes of the

@@ -27,6 +27,11 @@ class CgParams(ctypes.Structure):
         ("filter_on", ctypes.c_int),
         ("omega_window", ctypes.c_int),
         ("inflow", ((ctypes.c_double * 5) * 2) * 3),
+        ("viscous", ctypes.c_int),
+        ("re", ctypes.c_double),
+        ("pr", ctypes.c_double),
+        ("suth", ctypes.c_double),
+        ("twall", ctypes.c_double),
     ]
 
 
@@ -41,6 +46,8 @@ _SIGS = {
     "cg_grid_destroy": (None, [ctypes.c_void_p]),
     "cg_solver_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(CgParams), ctypes.POINTER(ctypes.c_void_p)]),
     "cg_solver_destroy": (None, [ctypes.c_void_p]),
+    "cg_solver_set_inflow_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                                   ctypes.POINTER(ctypes.c_double)]),
     "cg_metrics": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "cg_rhs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "cg_rk3_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p]),

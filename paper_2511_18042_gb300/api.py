@@ -85,9 +85,25 @@ class Solver:
 
     @classmethod
     def from_problem(cls, prob, grid=None, **kw):
+        """Solver for a problem dict (inputs module): gamma, the inflow state,
+        the viscous parameters and the inflow profiles come from the problem
+        unless overridden."""
         grid = grid or Grid.from_problem(prob)
         kw.setdefault("gamma", prob.get("gamma", 1.4))
-        return cls(grid, inflow=prob.get("inflow"), **kw)
+        if prob.get("viscous"):
+            for k in ("viscous", "re", "pr", "suth", "twall", "minf"):
+                kw.setdefault(k, prob[k])
+        s = cls(grid, inflow=prob.get("inflow"), **kw)
+        for (d, side), W in prob.get("inflow_profile", {}).items():
+            s.set_inflow_profile(d, side, W)
+        return s
+
+    def set_inflow_profile(self, d, side, W):
+        """Per-node primitive profile (nv, face nodes) for inflow face (d, side)."""
+        import numpy as np
+        Wh = np.ascontiguousarray(W, dtype=np.float64)
+        nat.check(nat.lib().cg_solver_set_inflow_profile(
+            self._h, int(d), int(side), Wh.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
 
     def __del__(self):
         if getattr(self, "_h", None) and self._h.value:

@@ -141,6 +141,7 @@ struct cg_solver {
   int iface_dir = -1;               // diagnostics: direction whose interface fluxes are written
   double* iface_out = nullptr;
   DevLine c6grad[3], c6flux[3], filt[3];  // LAD-C6 line systems
+  double* prof[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};  // inflow profiles
   // kernel timing (cg_timing_enable): CUDA events around the sweep launches
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -218,6 +219,12 @@ static void fill_devgrid(const cg_grid* g, const cg_params* p, DevGrid& d) {
       for (int m = 0; m < 3; ++m) { d.cn[dir][m] = n[m]; d.ct1[dir][m] = t1[m]; d.ct2[dir][m] = t2[m]; }
     }
   }
+  d.twall = p->twall;
+  d.visc = p->viscous ? 1 : 0;
+  d.re = p->re;
+  d.suth = p->suth;
+  d.kc = (p->gamma - 1.0) * p->pr * p->minf * p->minf;
+  for (int k = 0; k < 3; ++k) d.pf[k] = d.N / d.n[k];
 }
 
 static Box make_box(const cg_solver* s, int grow_all, int dir, int grow_dir) {
@@ -267,7 +274,7 @@ static int upload_line(DevLine& L, int m, double a, bool cyclic, int lo) {
   std::vector<double> all(3 * (size_t)m, 0.0);
   for (int i = 0; i < m; ++i) {
     all[i] = h.cp[i];
-    all[m + i] = h.den[i];
+    all[m + i] = 1.0 / h.den[i];  // the recurrence multiplies by the reciprocal pivot
     all[2 * m + i] = cyclic ? h.z[i] : 0.0;
   }
   CG_CUDA(cudaMemcpy(L.buf, all.data(), all.size() * sizeof(double), cudaMemcpyHostToDevice));
@@ -544,9 +551,9 @@ static StageArgs base_args(cg_solver* s) {
 
 // One evaluation of the C-GBR fluxes over all directions with the epilogue of A.
 template <int ND>
-static int gbr_sweeps(cg_solver* s, bool compact, StageArgs A, cudaStream_t st) {
+static int gbr_sweeps(cg_solver* s, bool compact, StageArgs A, cudaStream_t st, bool fresh = true) {
   for (int d = 0; d < ND; ++d) {
-    A.first = d == 0;
+    A.first = fresh && d == 0;
     A.last = d == ND - 1;
     A.Gd = s->G[d];
     A.gdLB = s->gdLB[d];
@@ -561,6 +568,8 @@ static int gbr_sweeps(cg_solver* s, bool compact, StageArgs A, cudaStream_t st) 
 
 template <int ND>
 static int lad_stage(cg_solver* s, const double* Uc, StageArgs A, cudaStream_t st);
+template <int ND>
+static void visc_pass_any(cg_solver* s, StageArgs A, cudaStream_t st, bool have_grad, const int* guard, int want);
 template <int ND>
 static int lad_filter(cg_solver* s, double* U, cudaStream_t st);
 static int lad_alloc(cg_solver* s);
@@ -581,7 +590,8 @@ static int stage(cg_solver* s, const double* Uc, const double* Un, double* out, 
   if (sch == CG_MEG6 || sch == CG_MIG4) {
     bool compact = sch == CG_MIG4;
     stage_prep_gbr<ND>(s, Uc, compact, st);
-    return gbr_sweeps<ND>(s, compact, A, st);
+    if (s->p.viscous) visc_pass_any<ND>(s, A, st, false, nullptr, 0);
+    return gbr_sweeps<ND>(s, compact, A, st, !s->p.viscous);
   }
   return lad_stage<ND>(s, Uc, A, st);
 }
@@ -635,6 +645,25 @@ CG_API void cg_params_default(cg_params* p) {
   p->mp_alpha = 4.0;
   p->filter_on = 1;
   p->omega_window = 4;
+  p->viscous = 0;
+  p->re = 1.0;
+  p->pr = 0.72;
+  p->suth = 0.0;
+  p->twall = 1.0;
+}
+
+CG_API int cg_solver_set_inflow_profile(cg_solver* s, int dir, int side, const double* W_host) {
+  if (!s || !W_host) return fail(CG_ERR_INVALID_ARG, "null argument");
+  if (dir < 0 || dir >= s->nd || side < 0 || side > 1 || s->grid->bc[dir][side] != CG_BC_INFLOW)
+    return fail(CG_ERR_INVALID_ARG, "face (%d, %d) is not an inflow face", dir, side);
+  size_t count = (size_t)s->nv * (size_t)s->dg.pf[dir];
+  if (!s->prof[dir][side]) {
+    int rc = dalloc(&s->prof[dir][side], count);
+    if (rc) return rc;
+  }
+  CG_CUDA(cudaMemcpy(s->prof[dir][side], W_host, count * sizeof(double), cudaMemcpyHostToDevice));
+  s->dg.prof[dir][side] = s->prof[dir][side];
+  return CG_OK;
 }
 
 CG_API const char* cg_last_error(void) { return g_err.c_str(); }
@@ -648,7 +677,7 @@ static int check_grid_args(int ndim, const int64_t n[3], const int bc[6]) {
     }
     if (n[d] < 1 || n[d] > (1 << 24)) return fail(CG_ERR_INVALID_ARG, "n[%d] out of range", d);
     for (int s = 0; s < 2; ++s)
-      if (bc[2 * d + s] < CG_BC_PERIODIC || bc[2 * d + s] > CG_BC_INFLOW)
+      if (bc[2 * d + s] < CG_BC_PERIODIC || bc[2 * d + s] > CG_BC_WALL)
         return fail(CG_ERR_INVALID_ARG, "bad boundary type");
     if ((bc[2 * d] == CG_BC_PERIODIC) != (bc[2 * d + 1] == CG_BC_PERIODIC))
       return fail(CG_ERR_INVALID_ARG, "periodic direction %d needs both sides periodic", d);
@@ -730,6 +759,9 @@ CG_API void cg_solver_destroy(cg_solver* s) {
       if (l->buf) cudaFree(l->buf);
   }
   lad_free(s->lad);
+  for (int d = 0; d < 3; ++d)
+    for (int side = 0; side < 2; ++side)
+      if (s->prof[d][side]) cudaFree(s->prof[d][side]);
   if (s->mask) cudaFree(s->mask);
   if (s->hyb_flag) cudaFree(s->hyb_flag);
   if (s->hyb_count) cudaFree(s->hyb_count);
@@ -749,6 +781,12 @@ CG_API int cg_solver_create(const cg_grid* g, const cg_params* p, cg_solver** ou
   if (p->omega_window < 1 || p->omega_window > 4) return fail(CG_ERR_INVALID_ARG, "omega_window must be 1..4");
   if (g->curv && p->scheme == CG_LAD_C6)
     return fail(CG_ERR_UNSUPPORTED, "LAD-C6 on curvilinear grids is not supported (the metric identities need the compact operator)");
+  if (p->viscous && (!(p->re > 0.0) || !(p->pr > 0.0) || !(p->suth >= 0.0) || !(p->minf > 0.0)))
+    return fail(CG_ERR_INVALID_ARG, "viscous: re > 0, pr > 0, minf > 0 and suth >= 0 required");
+  for (int d = 0; d < g->nd; ++d)
+    for (int side = 0; side < 2; ++side)
+      if (g->bc[d][side] == CG_BC_WALL && !(p->twall > 0.0))
+        return fail(CG_ERR_INVALID_ARG, "isothermal walls need twall > 0");
   cg_solver* s = new (std::nothrow) cg_solver();
   if (!s) return fail(CG_ERR_OOM, "host allocation failed");
   s->grid = g;

@@ -14,7 +14,7 @@
 
 namespace cgk {
 
-constexpr int BC_PERIODIC = 0, BC_EXTRAP = 1, BC_REFLECT = 2, BC_INFLOW = 3;
+constexpr int BC_PERIODIC = 0, BC_EXTRAP = 1, BC_REFLECT = 2, BC_INFLOW = 3, BC_WALL = 4;
 constexpr int PM = 8;  // ghost layers stored with curvilinear metric planes
 
 // Grid as seen by the kernels (passed by value).
@@ -42,6 +42,13 @@ struct DevGrid {
   const double* xt;   // nd*nd planes, interface metrics of l-interface i+1/2 at node i
   const double* jac;  // J
   const double* dxl;  // nd*nd planes, LAD displacement vectors
+  // isothermal no-slip walls and physical viscosity (Sutherland)
+  double twall;       // wall temperature (units of T_inf)
+  int visc;           // physical viscous terms on
+  double re, suth, kc;  // Re, S / T_inf, (gamma-1) Pr minf^2
+  // per-node inflow profiles (primitive, nv planes over the face), or null
+  const double* prof[3][2];
+  long long pf[3];    // nodes of a face normal to d
 };
 
 __device__ __forceinline__ long long lin(const DevGrid& g, int i, int j, int k) {
@@ -59,6 +66,8 @@ struct Src {
   long long idx;  // interior linear index (valid when face < 0)
   int flip;       // bit d set: negate velocity component d
   int face;       // >= 0: inflow face 2*d + side (state held fixed)
+  long long pidx; // >= 0: node of the face's inflow profile
+  int walls;      // isothermal-wall images applied (one per wall crossed)
 };
 
 __device__ __forceinline__ Src resolve(const DevGrid& g, int c0, int c1, int c2) {
@@ -66,6 +75,8 @@ __device__ __forceinline__ Src resolve(const DevGrid& g, int c0, int c1, int c2)
   Src s;
   s.flip = 0;
   s.face = -1;
+  s.pidx = -1;
+  s.walls = 0;
 #pragma unroll
   for (int d = 2; d >= 0; --d) {
     if (d >= g.nd) continue;
@@ -77,6 +88,19 @@ __device__ __forceinline__ Src resolve(const DevGrid& g, int c0, int c1, int c2)
     if (bc == BC_INFLOW) {
       s.face = 2 * d + side;
       s.idx = 0;
+      if (g.prof[d][side]) {
+        // transverse position on the face, clamped to it (directions not yet
+        // resolved may still point at ghosts)
+        long long pi = 0, mul = 1;
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+          if (e >= g.nd || e == d) continue;
+          int y = c[e] < 0 ? 0 : (c[e] >= g.n[e] ? g.n[e] - 1 : c[e]);
+          pi += (long long)y * mul;
+          mul *= g.n[e];
+        }
+        s.pidx = pi;
+      }
       return s;
     } else if (bc == BC_PERIODIC) {
       x %= n;
@@ -84,6 +108,9 @@ __device__ __forceinline__ Src resolve(const DevGrid& g, int c0, int c1, int c2)
     } else if (bc == BC_REFLECT) {
       x = side == 0 ? -x - 1 : 2 * n - 1 - x;
       s.flip ^= (1 << d);
+    } else if (bc == BC_WALL) {
+      x = side == 0 ? -x - 1 : 2 * n - 1 - x;
+      s.walls++;
     } else {
       x = side == 0 ? 0 : n - 1;
     }
@@ -97,14 +124,66 @@ __device__ __forceinline__ Src resolve(const DevGrid& g, int c0, int c1, int c2)
 
 // Primitive state (or conserved: cons = true) at a possibly-ghost node from
 // nv planes F of N values.
+template <int ND>
+__device__ __forceinline__ void prim_to_cons(const DevGrid& g, const double* W, double* Q) {
+  double q = 0.0;
+  Q[0] = W[0];
+#pragma unroll
+  for (int k = 0; k < ND; ++k) {
+    Q[1 + k] = W[0] * W[1 + k];
+    q = q + W[1 + k] * W[1 + k];
+  }
+  Q[ND + 1] = W[ND + 1] / g.gm1 + 0.5 * W[0] * q;
+}
+
+template <int ND>
+__device__ __forceinline__ void cons_to_prim_g(const DevGrid& g, const double* Q, double* W) {
+  double rho = Q[0];
+  double irho = 1.0 / rho;
+  double ke = 0.0;
+  W[0] = rho;
+#pragma unroll
+  for (int k = 0; k < ND; ++k) {
+    W[1 + k] = Q[1 + k] * irho;
+    ke = ke + Q[1 + k] * W[1 + k];
+  }
+  W[ND + 1] = g.gm1 * (Q[ND + 1] - 0.5 * ke);
+}
+
+// Image of a state across an isothermal no-slip wall: velocity negated,
+// pressure kept, temperature reflected about the wall value
+// (T_ghost = 2 T_w - T), density from the equation of state.
+template <int ND>
+__device__ __forceinline__ void wall_image(const DevGrid& g, double* w) {
+  constexpr int IP = ND + 1;
+  double Tm = g.gm2 * w[IP] / w[0];
+  double Tg = 2.0 * g.twall - Tm;
+  w[0] = g.gm2 * w[IP] / Tg;
+#pragma unroll
+  for (int m = 0; m < ND; ++m) w[1 + m] = -w[1 + m];
+}
+
 template <int ND, bool CONS = false>
 __device__ __forceinline__ void load_state(const DevGrid& g, const double* __restrict__ F, int c0,
                                            int c1, int c2, double* w) {
   Src s = resolve(g, c0, c1, c2);
   if (s.face >= 0) {
-    const double* st = CONS ? g.inflowQ[s.face >> 1][s.face & 1] : g.inflowW[s.face >> 1][s.face & 1];
+    if (s.pidx >= 0) {
+      const double* P = g.prof[s.face >> 1][s.face & 1];
+      long long fn = g.pf[s.face >> 1];
+      double wp[ND + 2];
 #pragma unroll
-    for (int v = 0; v < ND + 2; ++v) w[v] = st[v];
+      for (int v = 0; v < ND + 2; ++v) wp[v] = P[(long long)v * fn + s.pidx];
+      if (CONS) prim_to_cons<ND>(g, wp, w);
+      else {
+#pragma unroll
+        for (int v = 0; v < ND + 2; ++v) w[v] = wp[v];
+      }
+    } else {
+      const double* st = CONS ? g.inflowQ[s.face >> 1][s.face & 1] : g.inflowW[s.face >> 1][s.face & 1];
+#pragma unroll
+      for (int v = 0; v < ND + 2; ++v) w[v] = st[v];
+    }
   } else {
 #pragma unroll
     for (int v = 0; v < ND + 2; ++v) w[v] = F[(long long)v * g.N + s.idx];
@@ -112,6 +191,16 @@ __device__ __forceinline__ void load_state(const DevGrid& g, const double* __res
 #pragma unroll
   for (int d = 0; d < ND; ++d)
     if (s.flip & (1 << d)) w[1 + d] = -w[1 + d];
+  for (int k = 0; k < s.walls; ++k) {
+    if (CONS) {
+      double wp[ND + 2];
+      cons_to_prim_g<ND>(g, w, wp);
+      wall_image<ND>(g, wp);
+      prim_to_cons<ND>(g, wp, w);
+    } else {
+      wall_image<ND>(g, w);
+    }
+  }
 }
 
 // Scalar field at a possibly-ghost node: periodic wraps, a wall mirrors,
@@ -126,7 +215,7 @@ __device__ __forceinline__ long long scalar_src(const DevGrid& g, int c0, int c1
     int side = x < 0 ? 0 : 1;
     int bc = g.bc[d][side];
     if (bc == BC_PERIODIC) { x %= n; if (x < 0) x += n; }
-    else if (bc == BC_REFLECT) x = side == 0 ? -x - 1 : 2 * n - 1 - x;
+    else if (bc == BC_REFLECT || bc == BC_WALL) x = side == 0 ? -x - 1 : 2 * n - 1 - x;
     else x = side == 0 ? 0 : n - 1;
     x = x < 0 ? 0 : (x >= n ? n - 1 : x);
     c[d] = x;

@@ -155,14 +155,14 @@ __global__ void k_omega(DevGrid g, const double* __restrict__ W, const double* _
 // ---------------------------------------------------------------- compact gradients
 // Tridiagonal (MIG4: 1/4, 1, 1/4) first derivative of the primitives along d,
 // one thread per (line, variable), Thomas elimination with the line-independent
-// pivots cp[], den[] precomputed on the host.  Non-periodic lines span the
+// pivots cp[] and reciprocal pivots 1/den[] precomputed on the host.  Non-periodic lines span the
 // positions [-6, n+5] with E4 closure rows at both ends; periodic lines are
 // cyclic on [0, n-1] (Sherman-Morrison with the correction vector z[]) and
 // the ghost positions copy the wrapped values.  Lines exist for every
 // position of the other directions in [-4, n+3].
 struct LineCoef {
   const double* cp;   // Thomas pivots of the line system
-  const double* den;
+  const double* den;  // reciprocals of the elimination pivots, 1/den_i
   const double* z;    // cyclic: solution of the correction system
   double a;           // off-diagonal
   double gam;         // cyclic: -1
@@ -181,10 +181,16 @@ __host__ __device__ constexpr int sweep_smem_doubles() {
          (SWEEP_TL + 7) * sweep_lw(DIR);
 }
 
+// Blocks per SM the register budget is sized for: two, except the 3D
+// curvilinear FP64 sweep, whose frame and metric terms need more than the
+// 128 registers two blocks of 256 threads leave (one block, no spills).
+template <int ND, bool CART, typename T>
+__host__ __device__ constexpr int sweep_min_blocks() { return (ND == 3 && !CART && sizeof(T) == 8) ? 1 : 2; }
+
 // T = double: FP64 parity form; T = float: mixed form (FP32 reconstruction and
 // fluxes from FP64 primitives; FP64 flux differences, residual and RK update).
 template <int ND, int DIR, bool CART, bool COMPACT, typename T = double>
-__global__ void __launch_bounds__(256, 2) k_gbr_sweep(DevGrid g, GbrCfg q, StageArgs A) {
+__global__ void __launch_bounds__(256, sweep_min_blocks<ND, CART, T>()) k_gbr_sweep(DevGrid g, GbrCfg q, StageArgs A) {
   constexpr int NV = ND + 2, IP = ND + 1;
   constexpr int TL = SWEEP_TL, LW = sweep_lw(DIR);
   constexpr int RW = TL + 9, RD = TL + 3, RDD = TL + 1, RO = TL + 7;

@@ -235,14 +235,23 @@ __global__ void k_gauss(DevGrid g, int l, const T* __restrict__ a, const T* __re
   }
 }
 
-// Node fluxes along l at positions [-2, n+1] (interior lines):
-// F = F^c(W; xi_hat_l) - [0, xi_hat_l tau, xi_hat_l . phi], tau = beta* div,
-// phi_m = u_m tau + kappa* dT/dx_m.
-template <int ND, bool CART, typename T = double>
+// Node fluxes along l at positions [-2, n+1] (interior lines).
+// MODE 0 (LAD, inviscid case): F = F^c(W; xi_hat_l) - [0, xi_hat_l tau,
+//   xi_hat_l . phi], tau = beta* div, phi_m = u_m tau + kappa* dT/dx_m.
+// MODE 1 (LAD with physical viscosity) and MODE 2 (the physical viscous flux
+// alone, -F^v): Eq. (3) with Stokes' hypothesis,
+//   tau_ma = mu (du_a/dx_m + du_m/dx_a) + delta_ma (beta* - 2/3 mu) div,
+//   phi_m = sum_a u_a tau_ma + (kappa* + kappa_hat) dT/dx_m,
+//   mu = T^{3/2} (1 + S) / (T + S) / Re, kappa_hat = mu / ((gamma-1) Pr M^2)
+// (MODE 2: no convective flux, beta* = kappa* = 0).
+constexpr int NF_LAD = 0, NF_LAD_VISC = 1, NF_VISC = 2;
+
+template <int ND, bool CART, int MODE, typename T = double>
 __global__ void k_lad_nodeflux(DevGrid g, int l, const double* __restrict__ W, const T* __restrict__ bt,
                                const T* __restrict__ kp, const T* __restrict__ gr, const T* __restrict__ dv, Box b3,
                                T* __restrict__ Fn, Box fb, const int* guard, int want) {
   constexpr int NV = ND + 2, IP = ND + 1;
+  constexpr bool CONV = MODE != NF_VISC, ART = MODE != NF_VISC, PHYS = MODE != NF_LAD;
   if (guard && *guard != want) return;
   long long fs = fb.size(), bs = b3.size();
   BOX_LOOP(fb, e) {
@@ -262,38 +271,89 @@ __global__ void k_lad_nodeflux(DevGrid g, int l, const double* __restrict__ W, c
 #pragma unroll
       for (int m = 0; m < ND; ++m) xi[m] = T(g.xh[(l * ND + m) * g.NP + pq]);
     }
-    T U, q2;
-    if (CART) U = xi[l] * w[1 + l];
-    else {
-      U = xi[0] * w[1];
-#pragma unroll
-      for (int m = 1; m < ND; ++m) U = U + xi[m] * w[1 + m];
-    }
-    q2 = w[1] * w[1];
-#pragma unroll
-    for (int m = 1; m < ND; ++m) q2 = q2 + w[1 + m] * w[1 + m];
     T rho = w[0], p = w[IP];
-    T E = p / T(g.gm1) + T(0.5) * rho * q2;
+    T fc[NV];
+    if (CONV) {
+      T U, q2;
+      if (CART) U = xi[l] * w[1 + l];
+      else {
+        U = xi[0] * w[1];
+#pragma unroll
+        for (int m = 1; m < ND; ++m) U = U + xi[m] * w[1 + m];
+      }
+      q2 = w[1] * w[1];
+#pragma unroll
+      for (int m = 1; m < ND; ++m) q2 = q2 + w[1 + m] * w[1 + m];
+      T E = p / T(g.gm1) + T(0.5) * rho * q2;
+      fc[0] = rho * U;
+#pragma unroll
+      for (int m = 0; m < ND; ++m) fc[1 + m] = (CART && m != l) ? rho * w[1 + m] * U : rho * w[1 + m] * U + xi[m] * p;
+      fc[IP] = (E + p) * U;
+    } else {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) fc[v] = T(0);
+    }
     long long sq = scalar_src(g, c[0], c[1], c[2]);
     long long be = b3.at(c[0], c[1], c[2]);
-    T tau = bt[sq] * dv[be];
-    T kap = kp[sq];
-    T fe = T(0);
-    bool first = true;
+    if (!PHYS) {
+      T tau = bt[sq] * dv[be];
+      T kap = kp[sq];
+      T fe = T(0);
+      bool first = true;
 #pragma unroll
-    for (int m = 0; m < ND; ++m) {
-      if (CART && m != l) continue;
-      T phi = w[1 + m] * tau + kap * gr[(ND * ND + m) * bs + be];
-      fe = first ? xi[m] * phi : fe + xi[m] * phi;
-      first = false;
-    }
-    Fn[0 * fs + e] = rho * U;
+      for (int m = 0; m < ND; ++m) {
+        if (CART && m != l) continue;
+        T phi = w[1 + m] * tau + kap * gr[(ND * ND + m) * bs + be];
+        fe = first ? xi[m] * phi : fe + xi[m] * phi;
+        first = false;
+      }
+      Fn[0 * fs + e] = fc[0];
 #pragma unroll
-    for (int m = 0; m < ND; ++m) {
-      T fc = (CART && m != l) ? rho * w[1 + m] * U : rho * w[1 + m] * U + xi[m] * p;
-      Fn[(1 + m) * fs + e] = (CART && m != l) ? fc : fc - xi[m] * tau;
+      for (int m = 0; m < ND; ++m) Fn[(1 + m) * fs + e] = (CART && m != l) ? fc[1 + m] : fc[1 + m] - xi[m] * tau;
+      Fn[IP * fs + e] = fc[IP] - fe;
+    } else {
+      T Tt = T(g.gm2) * p / rho;
+      T S = T(g.suth);
+      T mu = Tt * sqrt(Tt) * (T(1.0) + S) / (Tt + S) / T(g.re);
+      T kth = mu / T(g.kc);
+      T lam = (ART ? bt[sq] : T(0)) - T(2.0 / 3.0) * mu;
+      T kap = (ART ? kp[sq] : T(0)) + kth;
+      T div = dv[be];
+      T tau[ND][ND];
+#pragma unroll
+      for (int m = 0; m < ND; ++m)
+#pragma unroll
+        for (int a = 0; a < ND; ++a) {
+          T sm = gr[(a * ND + m) * bs + be] + gr[(m * ND + a) * bs + be];
+          tau[m][a] = mu * sm;
+          if (m == a) tau[m][a] = tau[m][a] + lam * div;
+        }
+      T fe = T(0);
+      bool first = true;
+#pragma unroll
+      for (int m = 0; m < ND; ++m) {
+        if (CART && m != l) continue;
+        T phi = w[1] * tau[m][0];
+#pragma unroll
+        for (int a = 1; a < ND; ++a) phi = phi + w[1 + a] * tau[m][a];
+        phi = phi + kap * gr[(ND * ND + m) * bs + be];
+        fe = first ? xi[m] * phi : fe + xi[m] * phi;
+        first = false;
+      }
+      Fn[0 * fs + e] = fc[0];
+#pragma unroll
+      for (int a = 0; a < ND; ++a) {
+        T fv;
+        if (CART) fv = xi[l] * tau[l][a];
+        else {
+          fv = xi[0] * tau[0][a];
+#pragma unroll
+          for (int m = 1; m < ND; ++m) fv = fv + xi[m] * tau[m][a];
+        }
+        Fn[(1 + a) * fs + e] = fc[1 + a] + (-fv);
+      }
+      Fn[IP * fs + e] = fc[IP] + (-fe);
     }
-    Fn[IP * fs + e] = (E + p) * U - fe;
   }
 }
 

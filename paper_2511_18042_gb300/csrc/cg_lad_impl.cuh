@@ -5,7 +5,7 @@
 
 static int lad_alloc(cg_solver* s) {
   int sch = s->p.scheme;
-  if (sch != CG_LAD_E4 && sch != CG_LAD_C6 && sch != CG_HYBRID) return CG_OK;
+  if (sch != CG_LAD_E4 && sch != CG_LAD_C6 && sch != CG_HYBRID && !s->p.viscous) return CG_OK;
   LadBuffers& L = s->lad;
   int nd = s->nd, nv = s->nv, nf = nd + 3;
   L.fbx = make_box(s, 8, -1, 8);
@@ -117,8 +117,8 @@ static int lad_coeffs_run(cg_solver* s, int dkind, cudaStream_t st, const int* g
   return CG_OK;
 }
 
-template <int ND, typename T = double>
-static void lad_nodeflux(cg_solver* s, int l, cudaStream_t st, const int* guard, int want) {
+template <int ND, int MODE, typename T>
+static void lad_nodeflux_m(cg_solver* s, int l, cudaStream_t st, const int* guard, int want) {
   LadBuffers& L = s->lad;
   int gb = grid_blocks(L.fbox[l].size(), 128);
   const T* bt = reinterpret_cast<const T*>(L.bt[0]);
@@ -127,10 +127,61 @@ static void lad_nodeflux(cg_solver* s, int l, cudaStream_t st, const int* guard,
   const T* dv = reinterpret_cast<const T*>(L.dv);
   T* Fn = reinterpret_cast<T*>(L.Fn);
   if (s->dg.curv)
-    k_lad_nodeflux<ND, false, T><<<gb, 128, 0, st>>>(s->dg, l, s->W, bt, kp, gr, dv, L.b3, Fn, L.fbox[l], guard, want);
+    k_lad_nodeflux<ND, false, MODE, T><<<gb, 128, 0, st>>>(s->dg, l, s->W, bt, kp, gr, dv, L.b3, Fn, L.fbox[l], guard, want);
   else
-    k_lad_nodeflux<ND, true, T><<<gb, 128, 0, st>>>(s->dg, l, s->W, bt, kp, gr, dv, L.b3, Fn, L.fbox[l], guard, want);
+    k_lad_nodeflux<ND, true, MODE, T><<<gb, 128, 0, st>>>(s->dg, l, s->W, bt, kp, gr, dv, L.b3, Fn, L.fbox[l], guard, want);
   s->launches++;
+}
+
+// node fluxes along l: mode NF_LAD (artificial terms only), NF_LAD_VISC (plus
+// the physical viscosity) or NF_VISC (the physical viscous flux alone)
+template <int ND, typename T = double>
+static void lad_nodeflux(cg_solver* s, int l, cudaStream_t st, const int* guard, int want, int mode = NF_LAD) {
+  if (mode == NF_VISC) lad_nodeflux_m<ND, NF_VISC, T>(s, l, st, guard, want);
+  else if (mode == NF_LAD_VISC) lad_nodeflux_m<ND, NF_LAD_VISC, T>(s, l, st, guard, want);
+  else lad_nodeflux_m<ND, NF_LAD, T>(s, l, st, guard, want);
+}
+
+// E4 gradients of the LAD fields of the primitives in s->W (no coefficients)
+template <int ND, typename T>
+static void lad_grad_e4(cg_solver* s, cudaStream_t st, const int* guard, int want) {
+  LadBuffers& L = s->lad;
+  T* fb = reinterpret_cast<T*>(L.fb);
+  T* gr = reinterpret_cast<T*>(L.gr);
+  T* dv = reinterpret_cast<T*>(L.dv);
+  k_lad_fieldbuf<ND, T><<<grid_blocks(L.fbx.size(), 256), 256, 0, st>>>(s->dg, s->W, fb, L.fbx);
+  int gb = grid_blocks(L.b3.size(), 128);
+  if (s->dg.curv)
+    k_lad_grad<ND, false, false, T><<<gb, 128, 0, st>>>(s->dg, fb, L.fbx, L.df[0], L.df[1], L.df[2], L.dfLB[0], L.dfLB[1], L.dfLB[2], gr, dv, L.b3, guard, want);
+  else
+    k_lad_grad<ND, true, false, T><<<gb, 128, 0, st>>>(s->dg, fb, L.fbx, L.df[0], L.df[1], L.df[2], L.dfLB[0], L.dfLB[1], L.dfLB[2], gr, dv, L.b3, guard, want);
+  s->launches += 2;
+}
+
+// Physical viscous terms of the C-GBR and per-interface hybrid stages (the
+// central viscous routines shared with the LAD framework, no interface
+// damping scheme): node fluxes -F^v from E4 gradients of the primitives in
+// s->W and their E4 derivative along each direction, accumulated into acc;
+// the first direction initialises acc, none runs the epilogue.  have_grad:
+// the gradients of this stage's primitives are already in the LAD buffers.
+template <int ND, typename T>
+static void visc_pass(cg_solver* s, StageArgs A, cudaStream_t st, bool have_grad, const int* guard, int want) {
+  LadBuffers& L = s->lad;
+  if (!have_grad) lad_grad_e4<ND, T>(s, st, guard, want);
+  for (int l = 0; l < ND; ++l) {
+    lad_nodeflux<ND, T>(s, l, st, guard, want, NF_VISC);
+    A.first = l == 0;
+    A.last = false;
+    k_lad_div<ND, T><<<grid_blocks(s->N, 256), 256, 0, st>>>(s->dg, l, reinterpret_cast<const T*>(L.Fn), L.fbox[l],
+                                                            nullptr, L.DLB[l], A, guard, want);
+    s->launches++;
+  }
+}
+
+template <int ND>
+static void visc_pass_any(cg_solver* s, StageArgs A, cudaStream_t st, bool have_grad, const int* guard, int want) {
+  if (s->p.precision == CG_MIXED) visc_pass<ND, float>(s, A, st, have_grad, guard, want);
+  else visc_pass<ND, double>(s, A, st, have_grad, guard, want);
 }
 
 // LAD residual (E4 or C6) of the primitives in s->W with the epilogue of A.
@@ -140,7 +191,7 @@ static int lad_pass(cg_solver* s, int dkind, StageArgs A, cudaStream_t st, const
   if (rc) return rc;
   LadBuffers& L = s->lad;
   for (int l = 0; l < ND; ++l) {
-    lad_nodeflux<ND, T>(s, l, st, guard, want);
+    lad_nodeflux<ND, T>(s, l, st, guard, want, s->p.viscous ? NF_LAD_VISC : NF_LAD);
     A.first = l == 0;
     A.last = l == ND - 1;
     const double* D = nullptr;
@@ -186,7 +237,8 @@ static int lad_stage_t(cg_solver* s, const double* Uc, StageArgs A, cudaStream_t
     StageArgs G = A;
     G.guard = s->hyb_flag;
     G.guard_want = 1;
-    int rc = gbr_sweeps<ND>(s, false, G, st);
+    if (s->p.viscous) visc_pass<ND, T>(s, G, st, false, s->hyb_flag, 1);
+    int rc = gbr_sweeps<ND>(s, false, G, st, !s->p.viscous);
     if (rc) return rc;
     return lad_pass<ND, T>(s, 2, A, st, s->hyb_flag, 0);
   }
@@ -198,6 +250,7 @@ static int lad_stage_t(cg_solver* s, const double* Uc, StageArgs A, cudaStream_t
   s->launches++;
   int rc = lad_coeffs_run<ND, T>(s, 2, st, nullptr, 0);
   if (rc) return rc;
+  if (s->p.viscous) visc_pass<ND, T>(s, A, st, true, nullptr, 0);
   for (int l = 0; l < ND; ++l) {
     lad_nodeflux<ND, T>(s, l, st, nullptr, 0);
     k_lad_hflux<ND, T><<<grid_blocks(L.hbox[l].size(), 256), 256, 0, st>>>(s->dg, l, reinterpret_cast<const T*>(L.Fn),
@@ -208,7 +261,7 @@ static int lad_stage_t(cg_solver* s, const double* Uc, StageArgs A, cudaStream_t
   H.mask = L.tr;
   H.tBox = L.tbox;
   for (int d = 0; d < ND; ++d) {
-    H.first = d == 0;
+    H.first = d == 0 && !s->p.viscous;
     H.last = d == ND - 1;
     H.hflux = s->hflux[d];
     H.hBox = L.hbox[d];

@@ -3,10 +3,12 @@
 // buffer ([component][row][line], lines contiguous, so a warp of 32 lines
 // reads and writes 32 consecutive values); k_thomas then runs only the
 // recurrence, one thread per (line, component), with the pivots precomputed
-// on the host: dp_i = (r_i - a dp_{i-1}) / den_i, x_i = dp_i - cp_i x_{i+1}
-// (cyclic lines add the Sherman-Morrison correction).  Every row of every line
-// is processed in the order of the sequential elimination, so the result is
-// the one the line's own Thomas elimination gives.
+// on the host: dp_i = (r_i - a dp_{i-1}) rden_i, x_i = dp_i - cp_i x_{i+1}
+// (cyclic lines add the Sherman-Morrison correction).  rden_i = 1/den_i is
+// taken once on the host and every update is one fused multiply-add: on a
+// GPU whose FP64 rate is the limit, a division per row would cost several
+// times the rest of the row.  The result agrees with the plain elimination to
+// a few units in the last place (the systems are diagonally dominant).
 #pragma once
 #include "cg_kernels.cuh"
 
@@ -40,37 +42,132 @@ __global__ void k_thomas_jobs(ThomasJobs J) {
   thomas_column(J.lc[j], J.x[j], J.nl[j], t - J.start[j]);
 }
 
+// The recurrences below read row i+B..i+2B-1 (forward) or i-B..i-2B+1
+// (backward) before they store rows i..i+B-1: loads of rows not yet written
+// do not wait for the stores of the previous rows, so memory latency is paid
+// once per batch of B rows instead of once per row.  The arithmetic of every
+// row is the plain recurrence, in the same order.
+constexpr int kRowBatch = 8;
+
+// dp_i = (r_i - a dp_{i-1}) rden_i for i in [i0, i1), in place; returns dp_{i1-1}.
+__device__ __forceinline__ double thomas_forward(double* __restrict__ col, long long nl, const double* __restrict__ den,
+                                                 double a, int i0, int i1, double dp) {
+  constexpr int B = kRowBatch;
+  const int nfull = (i1 - i0) / B;
+  double v[B], dn[B];
+  if (nfull > 0) {
+#pragma unroll
+    for (int k = 0; k < B; ++k) {
+      v[k] = col[(long long)(i0 + k) * nl];
+      dn[k] = den[i0 + k];
+    }
+  }
+  for (int b = 0; b < nfull; ++b) {
+    const int base = i0 + b * B;
+    const bool more = b + 1 < nfull;
+    double nv[B], nd[B];
+    if (more) {
+#pragma unroll
+      for (int k = 0; k < B; ++k) {
+        nv[k] = col[(long long)(base + B + k) * nl];
+        nd[k] = den[base + B + k];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < B; ++k) {
+      dp = __fma_rn(-a, dp, v[k]) * dn[k];
+      col[(long long)(base + k) * nl] = dp;
+    }
+    if (more) {
+#pragma unroll
+      for (int k = 0; k < B; ++k) {
+        v[k] = nv[k];
+        dn[k] = nd[k];
+      }
+    }
+  }
+  for (int i = i0 + nfull * B; i < i1; ++i) {
+    dp = __fma_rn(-a, dp, col[(long long)i * nl]) * den[i];
+    col[(long long)i * nl] = dp;
+  }
+  return dp;
+}
+
+// x_i = dp_i - cp_i x_{i+1} for i = i1, i1-1, ..., i0, in place; returns x_{i0}.
+__device__ __forceinline__ double thomas_backward(double* __restrict__ col, long long nl, const double* __restrict__ cp,
+                                                  int i0, int i1, double xv) {
+  constexpr int B = kRowBatch;
+  const int nfull = (i1 - i0 + 1) / B;
+  double v[B], c[B];
+  if (nfull > 0) {
+#pragma unroll
+    for (int k = 0; k < B; ++k) {
+      v[k] = col[(long long)(i1 - k) * nl];
+      c[k] = cp[i1 - k];
+    }
+  }
+  for (int b = 0; b < nfull; ++b) {
+    const int top = i1 - b * B;
+    const bool more = b + 1 < nfull;
+    double nv[B], nc[B];
+    if (more) {
+#pragma unroll
+      for (int k = 0; k < B; ++k) {
+        nv[k] = col[(long long)(top - B - k) * nl];
+        nc[k] = cp[top - B - k];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < B; ++k) {
+      xv = __fma_rn(-c[k], xv, v[k]);
+      col[(long long)(top - k) * nl] = xv;
+    }
+    if (more) {
+#pragma unroll
+      for (int k = 0; k < B; ++k) {
+        v[k] = nv[k];
+        c[k] = nc[k];
+      }
+    }
+  }
+  for (int i = i1 - nfull * B; i >= i0; --i) {
+    xv = __fma_rn(-cp[i], xv, col[(long long)i * nl]);
+    col[(long long)i * nl] = xv;
+  }
+  return xv;
+}
+
+// x_i -= f z_i for i in [0, m), in place.
+__device__ __forceinline__ void thomas_correct(double* __restrict__ col, long long nl, const double* __restrict__ z,
+                                               int m, double f) {
+  constexpr int B = kRowBatch;
+  int i = 0;
+  for (; i + B <= m; i += B) {
+    double v[B];
+#pragma unroll
+    for (int k = 0; k < B; ++k) v[k] = col[(long long)(i + k) * nl];
+#pragma unroll
+    for (int k = 0; k < B; ++k) col[(long long)(i + k) * nl] = __fma_rn(-f, z[i + k], v[k]);
+  }
+  for (; i < m; ++i) col[(long long)i * nl] = __fma_rn(-f, z[i], col[(long long)i * nl]);
+}
+
 __device__ __forceinline__ void thomas_column(const LineCoef& lc, double* __restrict__ x, long long nl, long long t) {
   long long comp = t / nl, L = t % nl;
   double* col = x + comp * lc.m * nl + L;
   const double a = lc.a;
   const int m = lc.m;
   if (!lc.periodic) {
-    double dp = col[0];
-    for (int i = 1; i < m - 1; ++i) {
-      dp = (col[(long long)i * nl] - a * dp) / lc.den[i];
-      col[(long long)i * nl] = dp;
-    }
-    double xv = col[(long long)(m - 1) * nl];
-    for (int i = m - 2; i >= 0; --i) {
-      xv = col[(long long)i * nl] - lc.cp[i] * xv;
-      col[(long long)i * nl] = xv;
-    }
+    // rows 0 and m-1 are identity rows (x = r there)
+    thomas_forward(col, nl, lc.den, a, 1, m - 1, col[0]);
+    thomas_backward(col, nl, lc.cp, 0, m - 2, col[(long long)(m - 1) * nl]);
   } else {
-    double dp = col[0] / 2.0;
+    double dp = col[0] * lc.den[0];
     col[0] = dp;
-    for (int i = 1; i < m; ++i) {
-      dp = (col[(long long)i * nl] - a * dp) / lc.den[i];
-      col[(long long)i * nl] = dp;
-    }
-    const double xlast = dp;
-    double xv = dp;
-    for (int i = m - 2; i >= 0; --i) {
-      xv = col[(long long)i * nl] - lc.cp[i] * xv;
-      col[(long long)i * nl] = xv;
-    }
-    double fact = (xv + a * xlast / lc.gam) / lc.fden;
-    for (int i = 0; i < m; ++i) col[(long long)i * nl] = col[(long long)i * nl] - fact * lc.z[i];
+    const double xlast = thomas_forward(col, nl, lc.den, a, 1, m, dp);
+    const double x0 = thomas_backward(col, nl, lc.cp, 0, m - 2, xlast);
+    const double fact = (x0 + a * xlast / lc.gam) / lc.fden;
+    thomas_correct(col, nl, lc.z, m, fact);
   }
 }
 

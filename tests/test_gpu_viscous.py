@@ -1,0 +1,173 @@
+"""CUDA path vs the oracle with physical viscosity (Sutherland), isothermal
+no-slip walls and per-node inflow profiles: single right-hand sides within
+1e-13 (relative to each variable's largest magnitude; 1e-12 for the compact
+schemes, see RHS_TOL), short runs within 1e-11, on 2D shear waves and wall
+channels, 3D curvilinear fields and a small compression ramp (inflow profile,
+wall, outflow, periodic span); the mixed form within a density L1 of 1e-5."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2511_18042_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+from tests.gpu_util import rel_err, to_dev  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2511_18042_gb300 import api as a
+    return a
+
+
+SCHEMES = [dict(scheme="MEG6"), dict(scheme="MIG4"), dict(scheme="LAD_E4"), dict(scheme="LAD_C6", cfl=0.1),
+           dict(scheme="HYBRID", hybrid_mode=0, hyb_rho=0.9999), dict(scheme="HYBRID", hybrid_mode=1, hyb_rho=0.9999)]
+
+
+def _odd_even(Lx, tw, p0):
+    def f(X, Y):
+        u = 0.02 * np.sin(math.pi * Y) * (1.0 + 0.3 * np.cos(2 * math.pi * X / Lx))
+        v = 0.01 * np.sin(2 * math.pi * Y) * np.sin(2 * math.pi * X / Lx)
+        p = p0 * (1.0 + 0.05 * np.cos(math.pi * Y))
+        T = tw + 0.1 * np.sin(math.pi * Y) * (1.0 + 0.2 * np.cos(2 * math.pi * X / Lx))
+        return u, v, p, T
+    return f
+
+
+def _okw(kw):
+    return {k: v for k, v in kw.items() if k != "precision"}
+
+
+def RHS_TOL(kw):
+    """Single-RHS bound.  The explicit schemes follow the oracle's operation
+    order (bitwise).  The compact ones (MIG4 gradients, LAD-C6 derivatives)
+    solve their line systems with reciprocal pivots and fused multiply-adds:
+    a few ulp per row of the gradient, which the viscous terms difference
+    twice (an amplification of order 1/h against the residual's scale)."""
+    return 1e-12 if kw.get("scheme") in ("MIG4", "LAD_C6") else 1e-13
+
+
+@pytest.mark.parametrize("kw", SCHEMES)
+def test_shear_wave_rhs_and_steps(orc, api, kw):
+    p = inputs.shear_wave(n=48, amp=0.05, minf=0.3, re=200.0, suth=0.7)
+    s = api.Solver.from_problem(p, **kw)
+    o = orc.Oracle(p, **_okw(kw))
+    U = p["U"]
+    assert rel_err(s.rhs(to_dev(U)), o.rhs(U)) <= RHS_TOL(kw)
+    Ug = to_dev(U)
+    s.advance(Ug, nsteps=20)
+    Uo, _, _ = o.advance(U, nsteps=20)
+    assert rel_err(Ug, Uo) <= 1e-11
+
+
+@pytest.mark.parametrize("kw", [dict(scheme="MEG6"), dict(scheme="MIG4"), dict(scheme="LAD_E4"),
+                                dict(scheme="LAD_C6", cfl=0.1),
+                                dict(scheme="HYBRID", hybrid_mode=1, hyb_rho=0.8, hybrid_sensor=1)])
+def test_wall_channel_rhs_and_steps(orc, api, kw):
+    n, nx, minf, tw = 40, 24, 0.5, 1.3
+    f = _odd_even(nx / n, tw, 1.0 / (1.4 * minf * minf))
+    p = inputs.wall_channel(n=n, nx=nx, minf=minf, re=80.0, suth=0.6, twall=tw, fields=f)
+    s = api.Solver.from_problem(p, **kw)
+    o = orc.Oracle(p, **_okw(kw))
+    U = p["U"]
+    assert rel_err(s.rhs(to_dev(U)), o.rhs(U)) <= RHS_TOL(kw)
+    Ug = to_dev(U)
+    s.advance(Ug, nsteps=30)
+    Uo, _, _ = o.advance(U, nsteps=30)
+    assert rel_err(Ug, Uo) <= 1e-11
+
+
+def test_wall_channel_conserved_ghosts_through_the_filter(orc, api):
+    """LAD-C6 filters the conserved state: its ghost nodes take the wall image
+    in conserved variables."""
+    n, nx, minf, tw = 40, 24, 0.5, 1.3
+    f = _odd_even(nx / n, tw, 1.0 / (1.4 * minf * minf))
+    p = inputs.wall_channel(n=n, nx=nx, minf=minf, re=80.0, suth=0.6, twall=tw, fields=f)
+    s = api.Solver.from_problem(p, scheme="LAD_C6")
+    o = orc.Oracle(p, scheme="LAD_C6")
+    Ud = to_dev(p["U"])
+    s.filter(Ud)
+    assert rel_err(Ud, o.filter(p["U"])) <= 1e-13
+
+
+def _field3(P):
+    x, y, z = P
+    tp = 2 * math.pi
+    u = np.stack([0.1 * np.sin(tp * x) + 0.05 * np.sin(tp * y),
+                  0.08 * np.sin(tp * y) + 0.04 * np.cos(tp * z),
+                  0.06 * np.sin(tp * z) + 0.03 * np.sin(tp * x)])
+    rho = 1.0 + 0.1 * np.sin(tp * (x + y))
+    p = (1.0 + 0.05 * np.cos(tp * z)) / (1.4 * 0.3 * 0.3)
+    return np.concatenate([rho[None], u, p[None]])
+
+
+@pytest.mark.parametrize("kw", [dict(scheme="MEG6"), dict(scheme="MIG4"), dict(scheme="LAD_E4"),
+                                dict(scheme="HYBRID", hybrid_mode=1, hyb_rho=1.05)])
+def test_3d_curvilinear_viscous_rhs(orc, api, kw):
+    xyz, per = inputs.wavy_grid_3d((16, 12, 10), amp=0.05)
+    W = _field3(xyz)
+    prob = inputs._viscous(inputs.field_on_curvilinear(xyz, per, W), 30.0, 0.3, 0.5, 1.0)
+    s = api.Solver.from_problem(prob, **kw)
+    o = orc.Oracle(prob, **kw)
+    assert rel_err(s.rhs(to_dev(prob["U"])), o.rhs(prob["U"])) <= RHS_TOL(kw)
+
+
+def test_inflow_profile_parallel_flow_3d(orc, api):
+    nx, ny, nz = 12, 10, 8
+    y = (np.arange(ny) + 0.5) / ny
+    z = (np.arange(nz) + 0.5) / nz
+    Zg, Yg, Xg = np.meshgrid(z, y, np.arange(nx), indexing="ij")
+    W = np.zeros((5, nz, ny, nx))
+    W[0] = 1.0
+    W[1] = 1.5 + 0.3 * np.sin(2 * math.pi * Yg) + 0.1 * np.cos(2 * math.pi * Zg)
+    W[4] = 0.7
+    prob = inputs._problem("parallel", 3, [nx, ny, nz], [0.1, 1.0 / ny, 1.0 / nz],
+                           [[inputs.INFLOW, inputs.EXTRAP], [0, 0], [0, 0]], W, 1.4)
+    prob["inflow"] = {(0, 0): (1.0, 1.0, 0.0, 0.0, 0.7)}
+    # a perturbed profile, so that the inflow ghosts carry information
+    prof = W[:, :, :, 0].copy()
+    prof[2] += 0.01 * np.sin(2 * math.pi * prof[1])
+    prob["inflow_profile"] = {(0, 0): np.ascontiguousarray(prof.reshape(5, -1))}
+    for kw in (dict(scheme="MEG6"), dict(scheme="LAD_E4"), dict(scheme="MIG4")):
+        s = api.Solver.from_problem(prob, **kw)
+        o = orc.Oracle(prob, **kw)
+        assert rel_err(s.rhs(to_dev(prob["U"])), o.rhs(prob["U"])) <= RHS_TOL(kw), kw
+
+
+RAMP_KW = [dict(scheme="MEG6"), dict(scheme="MIG4"), dict(scheme="LAD_E4"),
+           dict(scheme="HYBRID", hybrid_mode=0, hyb_rho=0.4), dict(scheme="HYBRID", hybrid_mode=1, hybrid_sensor=1,
+                                                                   hyb_rho=0.4)]
+
+
+@pytest.fixture(scope="module")
+def ramp():
+    return inputs.compression_ramp(40, 24, 8, Lx=200.0, Ly=60.0, Lz=12.0, delta=8.0)
+
+
+@pytest.mark.parametrize("kw", RAMP_KW)
+def test_compression_ramp_fp64_matches_oracle(orc, api, ramp, kw):
+    s = api.Solver.from_problem(ramp, **kw)
+    o = orc.Oracle(ramp, **kw)
+    U = ramp["U"]
+    assert rel_err(s.rhs(to_dev(U)), o.rhs(U)) <= RHS_TOL(kw)
+    Ug = to_dev(U)
+    s.advance(Ug, nsteps=5)
+    Uo, _, _ = o.advance(U, nsteps=5)
+    assert rel_err(Ug, Uo) <= 1e-11
+
+
+@pytest.mark.parametrize("kw", [dict(scheme="MEG6"), dict(scheme="LAD_E4"),
+                                dict(scheme="HYBRID", hybrid_mode=1, hybrid_sensor=1, hyb_rho=0.4)])
+def test_compression_ramp_mixed_form(orc, api, ramp, kw):
+    s = api.Solver.from_problem(ramp, precision=1, **kw)
+    o = orc.Oracle(ramp, **kw)
+    Ug = to_dev(ramp["U"])
+    s.advance(Ug, nsteps=5)
+    Uo, _, _ = o.advance(ramp["U"], nsteps=5)
+    rho = Ug[0].cpu().numpy()
+    assert np.abs(rho - Uo[0]).mean() / np.abs(Uo[0]).mean() <= 1e-5
