@@ -151,6 +151,7 @@ def run_gpu(args):
     dev_solver = solvers.get("MEG6") or api.Solver(grid, scheme="MEG6")
     dev_solver.advance(base, nsteps=args.develop)
     torch.cuda.synchronize()
+    tiles = {n: solvers[n].autotune(base) for n in names}  # tile shapes by measurement (cached per shape)
     U = {n: torch.empty_like(base) for n in names}
     dt = {n: torch.zeros(2, dtype=torch.float64, device=dev) for n in names}
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -234,7 +235,8 @@ def run_gpu(args):
         ms = per[n] / args.steps
         cu = cells / (ms * 1e-3)
         per_scheme[n] = {"cell_updates_per_s": cu, "ms_per_rk3_step": ms,
-                         "hbm_frac_of_measured": cu * HBM_BYTES_PER_CELL_STEP / (peaks["hbm_gbs"] * 1e9)}
+                         "hbm_frac_of_measured": cu * HBM_BYTES_PER_CELL_STEP / (peaks["hbm_gbs"] * 1e9),
+                         "tile_lines": list(tiles[n])}
     line = {
         "metric": "cell-updates/s per scheme & % HBM roofline; batched solves/s, p50/p99 latency",
         "value": value, "unit": "cell-updates/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -354,18 +356,30 @@ def run_batched(api, torch, dev, args, count=256, steps_per_solve=200):
     states = [torch.as_tensor(p["U"], device=dev) for p in probs]
     stream = torch.cuda.Stream()
     batch = api.Batch(solvers, states)
-    with torch.cuda.stream(stream):
-        for _ in range(3):  # eager, capture, first replay
+    k = max(2, args.steps)
+
+    def timed_steps():
+        for _ in range(3):  # eager or recapture, first replays
             batch.step(stream)
         stream.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        k = max(2, args.steps)
         e0.record(stream)
         for _ in range(k):
             batch.step(stream)
         e1.record(stream)
         stream.synchronize()
-    ms = e0.elapsed_time(e1) / k
+        return e0.elapsed_time(e1) / k
+
+    with torch.cuda.stream(stream):
+        ms_default = timed_steps()
+        t0 = time.perf_counter()
+        width = batch.autotune(stream)
+        tune_s = time.perf_counter() - t0
+        ms = timed_steps()
+    shapes = {}
+    for s_ in solvers:
+        key = "x".join(str(v) for v in s_.tile_shape())
+        shapes[key] = shapes.get(key, 0) + 1
     bad = sum(1 for s in solvers if s.sync_status() != 0)
     del batch, solvers, states
     torch.cuda.empty_cache()
@@ -390,6 +404,8 @@ def run_batched(api, torch, dev, args, count=256, steps_per_solve=200):
                         % (count, cells),
             "ms_per_rk3_step": ms, "cell_updates_per_s": cells / (ms * 1e-3),
             "solves_per_s": count / (steps_per_solve * ms * 1e-3), "steps_per_solve": steps_per_solve,
+            "autotune": {"streams": width, "tile_shapes": shapes, "seconds": tune_s,
+                         "ms_per_rk3_step_default": ms_default},
             "nonphysical_members": bad,
             "per_case_fp64": {"ms_per_rk3_step": ref_ms, "solves_per_s": count / (steps_per_solve * ref_ms * 1e-3),
                               "how": "each grid stepped alone in FP64 (wall clock, host-issued launches)"}}
@@ -439,6 +455,7 @@ def sweep_roofline(api, torch, grid, base, dev, args):
     each launch on its stream, recorded by the library) over RK3 steps of the
     bench state; FP64 roofline of that kernel."""
     s = api.Solver(grid, scheme="MEG6")
+    tile = s.autotune(base)
     U = torch.empty_like(base)
     dtd = torch.zeros(2, dtype=torch.float64, device=dev)
     for _ in range(2):
@@ -460,7 +477,8 @@ def sweep_roofline(api, torch, grid, base, dev, args):
     roof = {"bound": "alu", "unit": "TFLOP/s", "peak": FP64_PEAK_TFLOPS,
             "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (FP64 is not in MEASURED_PEAKS.json)",
             "kernel": "k_gbr_sweep (MEG6), x and y launches of RK3 steps of the bench state",
-            "launch_ms": avg_ms, "launches": n, "ifaces_per_launch": ifaces, "traffic": SWEEP_TRAFFIC_BYTES}
+            "launch_ms": avg_ms, "launches": n, "ifaces_per_launch": ifaces, "traffic": SWEEP_TRAFFIC_BYTES,
+            "tile_lines": list(tile)}
     if SWEEP_FLOP_PER_IFACE:
         ach = SWEEP_FLOP_PER_IFACE * ifaces / (avg_ms * 1e-3) / 1e12
         roof.update({"achieved": ach, "frac": ach / FP64_PEAK_TFLOPS, "flop_per_iface": SWEEP_FLOP_PER_IFACE})

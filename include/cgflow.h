@@ -187,7 +187,29 @@ typedef struct cg_batch cg_batch;
 CG_API int cg_multi_step(cg_solver *const *solvers, double *const *states, int count, void *stream);
 CG_API int cg_batch_create(int count, cg_solver *const *solvers, double *const *states, cg_batch **out);
 CG_API int cg_batch_step(cg_batch *b, void *stream);
+/* Autotunes the batch: every member's tile shape (as cg_autotune; equal
+ * shapes share one measurement), then the number of streams the members are
+ * spread over (1, 4, 8, 16 or 32), each timed over two batch steps from a saved
+ * copy of the states that is restored afterwards: the states are unchanged
+ * on return.  Synchronises; not during stream capture; a captured graph is
+ * recaptured at the next cg_batch_step.  *width_out (may be NULL) gets the
+ * chosen number of streams. */
+CG_API int cg_batch_autotune(cg_batch *b, void *stream, int *width_out);
 CG_API void cg_batch_destroy(cg_batch *b);
+
+/* Autotuner of the C-GBR sweep (MEG6, MIG4, hybrid; a no-op for LAD): for
+ * each direction, the number of grid lines a tile of 64 interfaces spans
+ * (4 or 8 along x; 4, 8 or 16 along y and z) is chosen by timing the
+ * right-hand side of the state U with each candidate.  Results are cached
+ * for the process by grid shape, grid kind and scheme; force = 1 re-times.
+ * U is read only.  Synchronises; not during stream capture.  The choice does
+ * not change any result: it only regroups the same per-interface work. */
+CG_API int cg_autotune(cg_solver *s, const double *U, int force, void *stream);
+/* Lines per sweep tile in use, per direction (0 for unused directions). */
+CG_API int cg_tile_shape(const cg_solver *s, int lines_per_tile[3]);
+/* Sets the lines per sweep tile per direction (entries of unused directions
+ * are ignored); CG_ERR_INVALID_ARG for a value that is not a candidate. */
+CG_API int cg_set_tile_shape(cg_solver *s, const int lines_per_tile[3]);
 
 /* Right-hand side of the MEG6 (C-GBR explicit) scheme on a uniform Cartesian
  * grid without allocating any device memory, for callers that cannot call

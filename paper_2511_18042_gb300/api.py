@@ -137,6 +137,22 @@ class Solver:
         nat.check(nat.lib().cg_cfl_dt(self._h, _dptr(U), ctypes.byref(v), 0, _stream(stream)))
         return v.value
 
+    def autotune(self, U, force=False, stream=None):
+        """Choose the sweep tile shape by timing the RHS of U (cached per shape);
+        returns the lines per tile per direction."""
+        self._check_state(U)
+        nat.check(nat.lib().cg_autotune(self._h, _dptr(U), int(bool(force)), _stream(stream)))
+        return self.tile_shape()
+
+    def tile_shape(self):
+        lw = (ctypes.c_int * 3)()
+        nat.check(nat.lib().cg_tile_shape(self._h, lw))
+        return tuple(lw[: self.nd])
+
+    def set_tile_shape(self, shape):
+        lw = (ctypes.c_int * 3)(*(list(shape) + [0] * (3 - len(shape))))
+        nat.check(nat.lib().cg_set_tile_shape(self._h, lw))
+
     def advance(self, U, nsteps=0, t_end=0.0, stream=None):
         self._check_state(U)
         t = ctypes.c_double()
@@ -234,6 +250,13 @@ class Batch:
 
     def step(self, stream):
         nat.check(nat.lib().cg_batch_step(self._h, _stream(stream)))
+
+    def autotune(self, stream=None):
+        """Tile shapes of the members and the stream-pool width (states unchanged);
+        returns the chosen width."""
+        w = ctypes.c_int()
+        nat.check(nat.lib().cg_batch_autotune(self._h, _stream(stream), ctypes.byref(w)))
+        return w.value
 
     def __del__(self):
         if getattr(self, "_h", None) and self._h.value:

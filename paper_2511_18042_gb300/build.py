@@ -10,11 +10,17 @@ LIB = os.path.join(OUT_DIR, "libcgflow.so")
 
 COMMON = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
           "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"]
-# FP64 parity unit: no contraction of a*b+c on device or host.  Mixed unit:
-# FP32 flux arithmetic with contraction.
-UNITS = [("cg_api.cu", ["-fmad=false", "-Xcompiler", "-ffp-contract=off"]),
-         ("cg_mixed.cu", ["-fmad=true"])]
-NVCC_FLAGS = COMMON + UNITS[0][1]
+# FP64 parity units: no contraction of a*b+c on device or host.  Mixed-form
+# sweep units: FP32 flux arithmetic with contraction.  The sweep is compiled
+# once per (arithmetic type, dimension), in parallel.
+FP64 = ["-fmad=false", "-Xcompiler", "-ffp-contract=off"]
+UNITS = [("cg_api.cu", "cg_api.o", FP64)]
+for _nd in (1, 2, 3):
+    UNITS.append(("cg_sweep_inst.cu", "cg_sweep_f64_%d.o" % _nd,
+                  FP64 + ["-DCGK_SWEEP_ND=%d" % _nd, "-DCGK_SWEEP_FP32=0"]))
+    UNITS.append(("cg_sweep_inst.cu", "cg_sweep_f32_%d.o" % _nd,
+                  ["-fmad=true", "-DCGK_SWEEP_ND=%d" % _nd, "-DCGK_SWEEP_FP32=1"]))
+NVCC_FLAGS = COMMON + FP64
 
 
 def _sources_mtime():
@@ -30,8 +36,8 @@ def build(force=False, verbose=False):
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)
     objs, procs = [], []
-    for src, flags in UNITS:
-        obj = os.path.join(OUT_DIR, src.replace(".cu", ".o"))
+    for src, oname, flags in UNITS:
+        obj = os.path.join(OUT_DIR, oname)
         cmd = ["nvcc"] + COMMON + flags + ["-c", "-o", obj, os.path.join(SRC, src)]
         if verbose:
             print(" ".join(cmd))

@@ -3,7 +3,10 @@
 // Host arithmetic that must reproduce the method's rounding (interface frames
 // of Cartesian grids, Thomas pivots) is compiled with contraction disabled.
 #include <algorithm>
+#include <array>
 #include <cmath>
+#include <map>
+#include <tuple>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -17,6 +20,7 @@
 #include "cg_lad.cuh"
 #include "cg_lines.cuh"
 #include "cg_metrics.cuh"
+#include "cg_sweep.h"
 
 using namespace cgk;
 
@@ -141,6 +145,7 @@ struct cg_solver {
   int iface_dir = -1;               // diagnostics: direction whose interface fluxes are written
   double* iface_out = nullptr;
   DevLine c6grad[3], c6flux[3], filt[3];  // LAD-C6 line systems
+  int sweep_lw[3] = {cgk::sweep_lw(0), cgk::sweep_lw(1), cgk::sweep_lw(2)};  // lines per sweep tile (autotuned or default)
   double* prof[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};  // inflow profiles
   // kernel timing (cg_timing_enable): CUDA events around the sweep launches
   bool timing = false;
@@ -426,8 +431,12 @@ struct TimedRegion {
 template <int ND, bool CART, bool COMPACT>
 static void launch_omega(cg_solver* s, cudaStream_t st, const int* guard, int want) {
   long long tot = s->omBox.size();
-  k_omega<ND, CART, COMPACT><<<grid_blocks(tot, 128), 128, 0, st>>>(
-      s->dg, s->W, s->G[0], s->G[1], s->G[2], s->gdLB[0], s->gdLB[1], s->gdLB[2], s->om, s->omBox, guard, want);
+  if (s->p.precision == CG_MIXED)
+    k_omega<ND, CART, COMPACT, float><<<grid_blocks(tot, 128), 128, 0, st>>>(
+        s->dg, s->W, s->G[0], s->G[1], s->G[2], s->gdLB[0], s->gdLB[1], s->gdLB[2], s->om, s->omBox, guard, want);
+  else
+    k_omega<ND, CART, COMPACT, double><<<grid_blocks(tot, 128), 128, 0, st>>>(
+        s->dg, s->W, s->G[0], s->G[1], s->G[2], s->gdLB[0], s->gdLB[1], s->gdLB[2], s->om, s->omBox, guard, want);
   s->launches++;
 }
 
@@ -442,39 +451,13 @@ static GbrCfg gbr_cfg(const cg_solver* s) {
   return q;
 }
 
-namespace cgk {
-int launch_sweep_f32(int nd, int dir, bool cart, bool compact, const DevGrid& g, const GbrCfg& q, const StageArgs& A,
-                     dim3 grid, cudaStream_t st);
-}
-
 template <int ND, int DIR, bool CART, bool COMPACT>
 static int launch_sweep(cg_solver* s, const StageArgs& A, cudaStream_t st) {
-  constexpr int LW = sweep_lw(DIR);
-  size_t smem = sizeof(double) * sweep_smem_doubles<ND, DIR>();
-  static bool attr_set = false;
-  if (!attr_set) {
-    CG_CUDA(cudaFuncSetAttribute(k_gbr_sweep<ND, DIR, CART, COMPACT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem));
-    attr_set = true;
-  }
-  dim3 grid;
-  const int* n = s->dg.n;
-  if (DIR == 0) {
-    long long lines = (long long)n[1] * n[2];
-    grid = dim3((n[0] + SWEEP_TL - 2) / (SWEEP_TL - 1), (unsigned)((lines + LW - 1) / LW), 1);
-  } else {
-    int other = DIR == 1 ? n[2] : n[1];
-    grid = dim3((n[0] + LW - 1) / LW, (n[DIR] + SWEEP_TL - 2) / (SWEEP_TL - 1), other);
-  }
-  {
-    TimedRegion tr(s, CG_TIMING_SWEEP, st);
-    if (s->p.precision == CG_MIXED) {
-      int e = launch_sweep_f32(ND, DIR, CART, COMPACT, s->dg, gbr_cfg(s), A, grid, st);
-      if (e) return fail(CG_ERR_CUDA, "mixed sweep launch: %s", cudaGetErrorString((cudaError_t)e));
-    } else {
-      k_gbr_sweep<ND, DIR, CART, COMPACT><<<grid, 256, smem, st>>>(s->dg, gbr_cfg(s), A);
-    }
-  }
+  TimedRegion tr(s, CG_TIMING_SWEEP, st);
+  int e = launch_sweep_any(s->p.precision == CG_MIXED, ND, DIR, s->sweep_lw[DIR], CART, COMPACT, s->dg, gbr_cfg(s),
+                           A, st);
+  if (e) return fail(CG_ERR_CUDA, "sweep launch (dir %d, %d lines per tile): %s", DIR, s->sweep_lw[DIR],
+                     cudaGetErrorString((cudaError_t)e));
   s->launches++;
   return CG_OK;
 }
@@ -621,6 +604,90 @@ static void cfl_launch(cg_solver* s, const double* U, double* dt_dev, double* t_
                   : fn<3>(__VA_ARGS__))
 
 #include "cg_lad_impl.cuh"
+
+// ---------------------------------------------------------------- autotuner
+// Lines per sweep tile, chosen per direction by timing the right-hand side of
+// the caller's state with each candidate (one direction at a time, the others
+// at their current choice).  Results are kept for the process, keyed by the
+// grid's shape and kind and the scheme, so equal-sized grids (a batch) are
+// timed once.
+namespace {
+using TuneKey = std::tuple<int, int, int, int, int, int, int, int, int>;
+std::mutex g_tune_mu;
+std::map<TuneKey, std::array<int, 3>> g_tune;
+
+TuneKey tune_key(const cg_solver* s) {
+  return TuneKey(s->nd, s->dg.n[0], s->dg.n[1], s->dg.n[2], s->p.scheme, s->p.precision, s->dg.curv,
+                 s->p.hybrid_mode, s->p.viscous);
+}
+}  // namespace
+
+static bool uses_sweep(const cg_solver* s) {
+  return s->p.scheme == CG_MEG6 || s->p.scheme == CG_MIG4 || s->p.scheme == CG_HYBRID;
+}
+
+// ms of one right-hand side of U with the current tile choices (median of reps)
+static int time_rhs(cg_solver* s, const double* U, double* R, cudaStream_t st, int reps, float* ms) {
+  cudaEvent_t a, b;
+  CG_CUDA(cudaEventCreate(&a));
+  CG_CUDA(cudaEventCreate(&b));
+  std::vector<float> t;
+  int rc = DISPATCH_ND(s, stage, s, U, U, R, 0, 1, st);  // warm-up (first launch of a shape)
+  for (int r = 0; r < reps && rc == CG_OK; ++r) {
+    cudaEventRecord(a, st);
+    rc = DISPATCH_ND(s, stage, s, U, U, R, 0, 1, st);
+    cudaEventRecord(b, st);
+    cudaError_t e = cudaEventSynchronize(b);
+    float x = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&x, a, b);
+    if (e != cudaSuccess && rc == CG_OK) rc = fail(CG_ERR_CUDA, "autotune timing: %s", cudaGetErrorString(e));
+    t.push_back(x);
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (rc) return rc;
+  std::sort(t.begin(), t.end());
+  *ms = t[t.size() / 2];
+  return CG_OK;
+}
+
+static int autotune_solver(cg_solver* s, const double* U, bool force, cudaStream_t st) {
+  if (!uses_sweep(s)) return CG_OK;
+  TuneKey key = tune_key(s);
+  if (!force) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      for (int d = 0; d < 3; ++d) s->sweep_lw[d] = it->second[d];
+      return CG_OK;
+    }
+  }
+  double* R = nullptr;
+  int rc = dalloc(&R, (size_t)s->nv * s->N);
+  if (rc) return rc;
+  for (int d = 0; d < s->nd && rc == CG_OK; ++d) {
+    const int* cands = d == 0 ? kSweepLwCands0 : kSweepLwCands1;
+    int nc = d == 0 ? (int)(sizeof kSweepLwCands0 / sizeof(int)) : (int)(sizeof kSweepLwCands1 / sizeof(int));
+    int best = s->sweep_lw[d];
+    float best_ms = 1e30f;
+    for (int k = 0; k < nc && rc == CG_OK; ++k) {
+      s->sweep_lw[d] = cands[k];
+      float ms = 0.f;
+      rc = time_rhs(s, U, R, st, 3, &ms);
+      if (rc == CG_OK && ms < best_ms) {
+        best_ms = ms;
+        best = cands[k];
+      }
+    }
+    s->sweep_lw[d] = best;
+  }
+  cudaFree(R);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[key] = {s->sweep_lw[0], s->sweep_lw[1], s->sweep_lw[2]};
+  return CG_OK;
+}
+
 #include "cg_batch_impl.cuh"
 
 // ======================================================================
@@ -878,6 +945,36 @@ CG_API int cg_rhs(cg_solver* s, const double* U, double* R, void* stream) {
   int rc = DISPATCH_ND(s, stage, s, U, U, R, 0, 1, st);
   if (rc) return rc;
   CG_CUDA(cudaGetLastError());
+  return CG_OK;
+}
+
+CG_API int cg_autotune(cg_solver* s, const double* U, int force, void* stream) {
+  if (!s || !U) return fail(CG_ERR_INVALID_ARG, "null argument");
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  CG_CUDA(cudaStreamIsCapturing((cudaStream_t)stream, &cs));
+  if (cs != cudaStreamCaptureStatusNone) return fail(CG_ERR_INVALID_ARG, "cg_autotune times kernels: not during capture");
+  int rc = autotune_solver(s, U, force != 0, (cudaStream_t)stream);
+  if (rc) return rc;
+  CG_CUDA(cudaGetLastError());
+  return CG_OK;
+}
+
+CG_API int cg_tile_shape(const cg_solver* s, int lines_per_tile[3]) {
+  if (!s || !lines_per_tile) return fail(CG_ERR_INVALID_ARG, "null argument");
+  for (int d = 0; d < 3; ++d) lines_per_tile[d] = d < s->nd ? s->sweep_lw[d] : 0;
+  return CG_OK;
+}
+
+CG_API int cg_set_tile_shape(cg_solver* s, const int lines_per_tile[3]) {
+  if (!s || !lines_per_tile) return fail(CG_ERR_INVALID_ARG, "null argument");
+  for (int d = 0; d < s->nd; ++d) {
+    const int* cands = d == 0 ? kSweepLwCands0 : kSweepLwCands1;
+    int nc = d == 0 ? (int)(sizeof kSweepLwCands0 / sizeof(int)) : (int)(sizeof kSweepLwCands1 / sizeof(int));
+    bool ok = false;
+    for (int k = 0; k < nc; ++k) ok = ok || cands[k] == lines_per_tile[d];
+    if (!ok) return fail(CG_ERR_INVALID_ARG, "%d lines per tile is not a candidate along direction %d", lines_per_tile[d], d);
+  }
+  for (int d = 0; d < s->nd; ++d) s->sweep_lw[d] = lines_per_tile[d];
   return CG_OK;
 }
 

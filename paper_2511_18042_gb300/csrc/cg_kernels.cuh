@@ -61,7 +61,9 @@ __global__ void k_prim(DevGrid g, const double* __restrict__ U, double* __restri
 // Omega^d = phi * zeta on the box [-4, n+3]: phi the largest normalised
 // pressure second difference over the directions, zeta a Ducros ratio of the
 // dilatation (one in irrotational dilatation-free flow).
-template <int ND, bool CART, bool COMPACT>
+// T = double: FP64 parity form; T = float: the mixed form's FP32 sensor
+// (FP64 primitives and gradients read, converted once).
+template <int ND, bool CART, bool COMPACT, typename T = double>
 __global__ void k_omega(DevGrid g, const double* __restrict__ W, const double* __restrict__ G0,
                         const double* __restrict__ G1, const double* __restrict__ G2, LineBuf gb0,
                         LineBuf gb1, LineBuf gb2, double* __restrict__ om, Box ob, const int* guard, int want) {
@@ -76,10 +78,11 @@ __global__ void k_omega(DevGrid g, const double* __restrict__ W, const double* _
     r /= ob.ext[0];
     c[1] = (int)(r % ob.ext[1]) - ob.off[1];
     c[2] = (int)(r / ob.ext[1]) - ob.off[2];
-    double w0[NV];
-    load_state<ND>(g, W, c[0], c[1], c[2], w0);
-    double phi = 0.0;
-    double du[3][3];  // du[l][k] = d u_k / d xi_l
+    double w0d[NV];
+    load_state<ND>(g, W, c[0], c[1], c[2], w0d);
+    const T p0 = T(w0d[IP]);
+    T phi = T(0);
+    T du[3][3];  // du[l][k] = d u_k / d xi_l
 #pragma unroll
     for (int l = 0; l < ND; ++l) {
       int cm[3] = {c[0], c[1], c[2]}, cp[3] = {c[0], c[1], c[2]};
@@ -88,7 +91,8 @@ __global__ void k_omega(DevGrid g, const double* __restrict__ W, const double* _
       double wm[NV], wp[NV];
       load_state<ND>(g, W, cm[0], cm[1], cm[2], wm);
       load_state<ND>(g, W, cp[0], cp[1], cp[2], wp);
-      double a = fabs(wp[IP] - 2.0 * w0[IP] + wm[IP]) / (wp[IP] + 2.0 * w0[IP] + wm[IP]);
+      const T pm = T(wm[IP]), pp = T(wp[IP]);
+      T a = fabs(pp - T(2.0) * p0 + pm) / (pp + T(2.0) * p0 + pm);
       if (a > phi) phi = a;
       if (!COMPACT) {
         double s[6][NV];
@@ -102,53 +106,55 @@ __global__ void k_omega(DevGrid g, const double* __restrict__ W, const double* _
         }
 #pragma unroll
         for (int k = 0; k < ND; ++k)
-          du[l][k] = d6(s[0][1 + k], s[1][1 + k], s[2][1 + k], s[3][1 + k], s[4][1 + k], s[5][1 + k]);
+          du[l][k] = d6<T>(T(s[0][1 + k]), T(s[1][1 + k]), T(s[2][1 + k]), T(s[3][1 + k]), T(s[4][1 + k]),
+                           T(s[5][1 + k]));
       } else {
         const double* G = l == 0 ? G0 : (l == 1 ? G1 : G2);
         const LineBuf& gb = l == 0 ? gb0 : (l == 1 ? gb1 : gb2);
 #pragma unroll
-        for (int k = 0; k < ND; ++k) du[l][k] = G[gb.at(1 + k, c[l], c)];
+        for (int k = 0; k < ND; ++k) du[l][k] = T(G[gb.at(1 + k, c[l], c)]);
       }
     }
     // physical velocity gradients gu[k][m] = sum_l (J xi_hat[l][m]) du[l][k]
-    double gu[3][3];
+    T gu[3][3];
     if (CART) {
 #pragma unroll
       for (int k = 0; k < ND; ++k)
 #pragma unroll
-        for (int m = 0; m < ND; ++m) gu[k][m] = (g.cjac * g.cxh[m]) * du[m][k];
+        for (int m = 0; m < ND; ++m) gu[k][m] = T(g.cjac * g.cxh[m]) * du[m][k];
     } else {
       long long pq = plin(g, c[0], c[1], c[2]);
       double J = g.jac[pq];
-      double xm[3][3];
+      T xm[3][3];
 #pragma unroll
       for (int l = 0; l < ND; ++l)
 #pragma unroll
-        for (int m = 0; m < ND; ++m) xm[l][m] = J * g.xh[(l * ND + m) * g.NP + pq];
+        for (int m = 0; m < ND; ++m) xm[l][m] = T(J * g.xh[(l * ND + m) * g.NP + pq]);
 #pragma unroll
       for (int k = 0; k < ND; ++k)
 #pragma unroll
         for (int m = 0; m < ND; ++m) {
-          double s = xm[0][m] * du[0][k];
+          T s = xm[0][m] * du[0][k];
 #pragma unroll
           for (int l = 1; l < ND; ++l) s = s + xm[l][m] * du[l][k];
           gu[k][m] = s;
         }
     }
-    double div = gu[0][0];
+    T div = gu[0][0];
 #pragma unroll
     for (int k = 1; k < ND; ++k) div = div + gu[k][k];
-    double zeta;
+    const T eps = T(1e-32);
+    T zeta;
     if (ND == 1) {
-      zeta = (div * div + 1e-32) / (div * div + 1e-32);
+      zeta = (div * div + eps) / (div * div + eps);
     } else if (ND == 2) {
-      double w3 = gu[1][0] - gu[0][1];
-      zeta = (div * div + 1e-32) / (div * div + w3 * w3 + 1e-32);
+      T w3 = gu[1][0] - gu[0][1];
+      zeta = (div * div + eps) / (div * div + w3 * w3 + eps);
     } else {
-      double w1 = gu[2][1] - gu[1][2], w2 = gu[0][2] - gu[2][0], w3 = gu[1][0] - gu[0][1];
-      zeta = (div * div + 1e-32) / (div * div + (w1 * w1 + w2 * w2 + w3 * w3) + 1e-32);
+      T w1 = gu[2][1] - gu[1][2], w2 = gu[0][2] - gu[2][0], w3 = gu[1][0] - gu[0][1];
+      zeta = (div * div + eps) / (div * div + (w1 * w1 + w2 * w2 + w3 * w3) + eps);
     }
-    om[ob.at(c[0], c[1], c[2])] = phi * zeta;
+    om[ob.at(c[0], c[1], c[2])] = double(phi * zeta);
   }
 }
 
@@ -174,11 +180,12 @@ struct LineCoef {
 
 // ---------------------------------------------------------------- C-GBR sweep
 constexpr int SWEEP_TL = 64;
+// lines per tile: the default, and the candidates an autotuner may choose from
+// (LW * SWEEP_TL must be a multiple of the 256 threads of a block)
 __host__ __device__ constexpr int sweep_lw(int dir) { return dir == 0 ? 4 : 8; }
-template <int ND, int DIR>
+template <int ND, int LW>
 __host__ __device__ constexpr int sweep_smem_doubles() {
-  return (ND + 2) * (SWEEP_TL + 9 + SWEEP_TL + 3 + SWEEP_TL + 1 + SWEEP_TL) * sweep_lw(DIR) +
-         (SWEEP_TL + 7) * sweep_lw(DIR);
+  return (ND + 2) * (SWEEP_TL + 9 + SWEEP_TL + 3 + SWEEP_TL + 1 + SWEEP_TL) * LW + (SWEEP_TL + 7) * LW;
 }
 
 // Blocks per SM the register budget is sized for: two, except the 3D
@@ -189,10 +196,11 @@ __host__ __device__ constexpr int sweep_min_blocks() { return (ND == 3 && !CART 
 
 // T = double: FP64 parity form; T = float: mixed form (FP32 reconstruction and
 // fluxes from FP64 primitives; FP64 flux differences, residual and RK update).
-template <int ND, int DIR, bool CART, bool COMPACT, typename T = double>
+template <int ND, int DIR, bool CART, bool COMPACT, typename T, int LW>
 __global__ void __launch_bounds__(256, sweep_min_blocks<ND, CART, T>()) k_gbr_sweep(DevGrid g, GbrCfg q, StageArgs A) {
+  static_assert((SWEEP_TL * LW) % 256 == 0, "a tile must hold a multiple of the block's threads");
   constexpr int NV = ND + 2, IP = ND + 1;
-  constexpr int TL = SWEEP_TL, LW = sweep_lw(DIR);
+  constexpr int TL = SWEEP_TL;
   constexpr int RW = TL + 9, RD = TL + 3, RDD = TL + 1, RO = TL + 7;
   extern __shared__ __align__(16) unsigned char smraw[];
   T* sm = reinterpret_cast<T*>(smraw);

@@ -1,0 +1,40 @@
+// Launchers of the C-GBR interface sweep, one translation unit per
+// (arithmetic type, dimension) so that the many instantiations (direction x
+// grid kind x gradient kind x lines per tile) compile in parallel.  The FP64
+// units are compiled without FMA contraction (the oracle's operation order),
+// the FP32 ones (the mixed form) with it.
+#pragma once
+#include "cg_kernels.cuh"
+
+namespace cgk {
+
+// Lines per tile an autotuner may choose for a sweep along dir.
+constexpr int kSweepLwCands0[] = {4, 8};       // dir 0 (lines along x, contiguous)
+constexpr int kSweepLwCands1[] = {4, 8, 16};   // dir 1, 2 (tile rows contiguous along x)
+
+// Each returns a cudaError_t value (0 on success); cudaErrorInvalidValue for a
+// combination that is not instantiated.
+#define CGK_SWEEP_DECL(name)                                                                              \
+  int name(int dir, int lw, bool cart, bool compact, const DevGrid& g, const GbrCfg& q, const StageArgs& A, \
+           cudaStream_t st);
+CGK_SWEEP_DECL(launch_sweep_f64_1)
+CGK_SWEEP_DECL(launch_sweep_f64_2)
+CGK_SWEEP_DECL(launch_sweep_f64_3)
+CGK_SWEEP_DECL(launch_sweep_f32_1)
+CGK_SWEEP_DECL(launch_sweep_f32_2)
+CGK_SWEEP_DECL(launch_sweep_f32_3)
+#undef CGK_SWEEP_DECL
+
+inline int launch_sweep_any(bool fp32, int nd, int dir, int lw, bool cart, bool compact, const DevGrid& g,
+                            const GbrCfg& q, const StageArgs& A, cudaStream_t st) {
+  if (fp32) {
+    if (nd == 1) return launch_sweep_f32_1(dir, lw, cart, compact, g, q, A, st);
+    if (nd == 2) return launch_sweep_f32_2(dir, lw, cart, compact, g, q, A, st);
+    return launch_sweep_f32_3(dir, lw, cart, compact, g, q, A, st);
+  }
+  if (nd == 1) return launch_sweep_f64_1(dir, lw, cart, compact, g, q, A, st);
+  if (nd == 2) return launch_sweep_f64_2(dir, lw, cart, compact, g, q, A, st);
+  return launch_sweep_f64_3(dir, lw, cart, compact, g, q, A, st);
+}
+
+}  // namespace cgk

@@ -1,0 +1,85 @@
+// Instantiations and launchers of the C-GBR interface sweep for one arithmetic
+// type and dimension, selected at compile time by CGK_SWEEP_FP32 (0: FP64
+// parity form, 1: mixed form) and CGK_SWEEP_ND (1, 2 or 3).
+#include "cg_sweep.h"
+
+#if !defined(CGK_SWEEP_ND) || !defined(CGK_SWEEP_FP32)
+#error "compile with -DCGK_SWEEP_ND=<1|2|3> -DCGK_SWEEP_FP32=<0|1>"
+#endif
+
+namespace cgk {
+
+namespace {
+
+#if CGK_SWEEP_FP32
+using ST = float;
+#else
+using ST = double;
+#endif
+constexpr int SND = CGK_SWEEP_ND;
+
+// grid of tiles: along DIR, tiles of SWEEP_TL interfaces overlapping by one
+// node; across, groups of LW lines
+template <int DIR, int LW>
+dim3 sweep_grid(const DevGrid& g) {
+  const int* n = g.n;
+  if (DIR == 0) {
+    long long lines = (long long)n[1] * n[2];
+    return dim3((n[0] + SWEEP_TL - 2) / (SWEEP_TL - 1), (unsigned)((lines + LW - 1) / LW), 1);
+  }
+  int other = DIR == 1 ? n[2] : n[1];
+  return dim3((n[0] + LW - 1) / LW, (n[DIR] + SWEEP_TL - 2) / (SWEEP_TL - 1), other);
+}
+
+template <int DIR, bool CART, bool COMPACT, int LW>
+int launch_one(const DevGrid& g, const GbrCfg& q, const StageArgs& A, cudaStream_t st) {
+  size_t smem = sizeof(ST) * sweep_smem_doubles<SND, LW>();
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_gbr_sweep<SND, DIR, CART, COMPACT, ST, LW>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return (int)e;
+    attr_set = true;
+  }
+  k_gbr_sweep<SND, DIR, CART, COMPACT, ST, LW><<<sweep_grid<DIR, LW>(g), 256, smem, st>>>(g, q, A);
+  return (int)cudaGetLastError();
+}
+
+template <int DIR, int LW>
+int launch_kind(bool cart, bool compact, const DevGrid& g, const GbrCfg& q, const StageArgs& A, cudaStream_t st) {
+  if (cart) return compact ? launch_one<DIR, true, true, LW>(g, q, A, st) : launch_one<DIR, true, false, LW>(g, q, A, st);
+  return compact ? launch_one<DIR, false, true, LW>(g, q, A, st) : launch_one<DIR, false, false, LW>(g, q, A, st);
+}
+
+template <int DIR>
+int launch_dir(int lw, bool cart, bool compact, const DevGrid& g, const GbrCfg& q, const StageArgs& A,
+               cudaStream_t st) {
+  if (lw == 4) return launch_kind<DIR, 4>(cart, compact, g, q, A, st);
+  if (lw == 8) return launch_kind<DIR, 8>(cart, compact, g, q, A, st);
+  if (DIR > 0 && lw == 16) return launch_kind<DIR, 16>(cart, compact, g, q, A, st);
+  return (int)cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+#define CGK_CAT3_(a, b, c) a##b##c
+#define CGK_CAT3(a, b, c) CGK_CAT3_(a, b, c)
+#if CGK_SWEEP_FP32
+#define CGK_SWEEP_NAME CGK_CAT3(launch_sweep_f32_, CGK_SWEEP_ND, )
+#else
+#define CGK_SWEEP_NAME CGK_CAT3(launch_sweep_f64_, CGK_SWEEP_ND, )
+#endif
+
+int CGK_SWEEP_NAME(int dir, int lw, bool cart, bool compact, const DevGrid& g, const GbrCfg& q, const StageArgs& A,
+                   cudaStream_t st) {
+  if (dir == 0) return launch_dir<0>(lw, cart, compact, g, q, A, st);
+#if CGK_SWEEP_ND >= 2
+  if (dir == 1) return launch_dir<1>(lw, cart, compact, g, q, A, st);
+#endif
+#if CGK_SWEEP_ND >= 3
+  if (dir == 2) return launch_dir<2>(lw, cart, compact, g, q, A, st);
+#endif
+  return (int)cudaErrorInvalidValue;
+}
+
+}  // namespace cgk
