@@ -50,7 +50,10 @@ DEVELOP_STEPS = 200
 # triple-point state (adds, multiplies, FMAs x2 of the divide / square-root
 # sequences included), from the ncu instruction counts of one sweep launch.
 SWEEP_FLOP_PER_IFACE = 632.2  # profiles/sweep_meg6_triple_point_1792x768.md (mean of x and y)
-SWEEP_TRAFFIC_BYTES = 116.4e6  # dram read + write per launch (mean of x and y), same capture
+# dram read + write per launch (mean of x and y) of the sweep form the roofline times,
+# from its ncu capture (profiles/); None until the current kernel has been captured
+SWEEP_TRAFFIC_BYTES = {"exact": 92.05e6, "contracted": 91.95e6}
+ROOFLINE_FORM = "contracted"  # the library default (exact_fp64 = 0)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12  # SMs x DFMA/clk x 2 flop x max clock
 HBM_BYTES_PER_CELL_STEP = 256.0  # minimal-traffic model, FP64 state, nv = 4, uniform grid
 
@@ -454,7 +457,7 @@ def sweep_roofline(api, torch, grid, base, dev, args):
     """Average duration of the MEG6 interface-sweep launches (CUDA events around
     each launch on its stream, recorded by the library) over RK3 steps of the
     bench state; FP64 roofline of that kernel."""
-    s = api.Solver(grid, scheme="MEG6")
+    s = api.Solver(grid, scheme="MEG6", exact_fp64=int(ROOFLINE_FORM == "exact"))
     tile = s.autotune(base)
     U = torch.empty_like(base)
     dtd = torch.zeros(2, dtype=torch.float64, device=dev)
@@ -477,7 +480,8 @@ def sweep_roofline(api, torch, grid, base, dev, args):
     roof = {"bound": "alu", "unit": "TFLOP/s", "peak": FP64_PEAK_TFLOPS,
             "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (FP64 is not in MEASURED_PEAKS.json)",
             "kernel": "k_gbr_sweep (MEG6), x and y launches of RK3 steps of the bench state",
-            "launch_ms": avg_ms, "launches": n, "ifaces_per_launch": ifaces, "traffic": SWEEP_TRAFFIC_BYTES,
+            "launch_ms": avg_ms, "launches": n, "ifaces_per_launch": ifaces,
+            "traffic": SWEEP_TRAFFIC_BYTES[ROOFLINE_FORM], "form": ROOFLINE_FORM,
             "tile_lines": list(tile)}
     if SWEEP_FLOP_PER_IFACE:
         ach = SWEEP_FLOP_PER_IFACE * ifaces / (avg_ms * 1e-3) / 1e12

@@ -10,16 +10,18 @@ LIB = os.path.join(OUT_DIR, "libcgflow.so")
 
 COMMON = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
           "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"]
-# FP64 parity units: no contraction of a*b+c on device or host.  Mixed-form
-# sweep units: FP32 flux arithmetic with contraction.  The sweep is compiled
-# once per (arithmetic type, dimension), in parallel.
+# FP64 parity units: no contraction of a*b+c on device or host.  The sweep is
+# compiled once per (form, dimension), in parallel: FP64 without contraction,
+# FP64 with fused multiply-add, FP32 (mixed form) with contraction.
 FP64 = ["-fmad=false", "-Xcompiler", "-ffp-contract=off"]
 UNITS = [("cg_api.cu", "cg_api.o", FP64)]
 for _nd in (1, 2, 3):
     UNITS.append(("cg_sweep_inst.cu", "cg_sweep_f64_%d.o" % _nd,
-                  FP64 + ["-DCGK_SWEEP_ND=%d" % _nd, "-DCGK_SWEEP_FP32=0"]))
+                  FP64 + ["-DCGK_SWEEP_ND=%d" % _nd, "-DCGK_SWEEP_UNIT=0"]))
+    UNITS.append(("cg_sweep_inst.cu", "cg_sweep_f64c_%d.o" % _nd,
+                  ["-fmad=true", "-DCGK_SWEEP_ND=%d" % _nd, "-DCGK_SWEEP_UNIT=1"]))
     UNITS.append(("cg_sweep_inst.cu", "cg_sweep_f32_%d.o" % _nd,
-                  ["-fmad=true", "-DCGK_SWEEP_ND=%d" % _nd, "-DCGK_SWEEP_FP32=1"]))
+                  ["-fmad=true", "-DCGK_SWEEP_ND=%d" % _nd, "-DCGK_SWEEP_UNIT=2"]))
 NVCC_FLAGS = COMMON + FP64
 
 

@@ -58,21 +58,32 @@ struct HostLine {
   std::vector<double> cp, den, z;
   double fden = 0.0, gam = -1.0;
 };
-HostLine make_line(int m, double a, bool cyclic) {
-  HostLine L;
-  L.cp.assign(m, 0.0);
-  L.den.assign(m, 1.0);
-  std::vector<double> A(m, a), B(m, 1.0), C(m, a);
+// the tridiagonal rows (A x_{i-1} + B x_i + C x_{i+1}) actually eliminated:
+// non-periodic lines with identity closure rows, cyclic lines with the
+// Sherman-Morrison modification (gam = -1)
+void line_rows(int m, double a, bool cyclic, std::vector<double>& A, std::vector<double>& B, std::vector<double>& C,
+               double* gam_out) {
+  A.assign(m, a);
+  B.assign(m, 1.0);
+  C.assign(m, a);
   if (!cyclic) {
     A[0] = 0.0; C[0] = 0.0; A[m - 1] = 0.0; C[m - 1] = 0.0;
   } else {
     double gam = -B[0];
-    L.gam = gam;
+    *gam_out = gam;
     B[0] = B[0] - gam;
     B[m - 1] = B[m - 1] - a * a / gam;
     A[0] = 0.0;
     C[m - 1] = 0.0;
   }
+}
+
+HostLine make_line(int m, double a, bool cyclic) {
+  HostLine L;
+  L.cp.assign(m, 0.0);
+  L.den.assign(m, 1.0);
+  std::vector<double> A, B, C;
+  line_rows(m, a, cyclic, A, B, C, &L.gam);
   L.cp[0] = C[0] / B[0];
   L.den[0] = B[0];
   for (int i = 1; i < m; ++i) {
@@ -94,9 +105,76 @@ HostLine make_line(int m, double a, bool cyclic) {
   return L;
 }
 
+// Partition of a line system into P chunks (see k_tri_part): local pivots,
+// responses to the neighbouring chunks' boundary unknowns, and the factors of
+// the boundary recursion, all in FP64 on the host.
+struct HostPart {
+  std::vector<double> aL, cp, rd, V, W, ch;
+  int q = 0, P = 0;
+};
+
+HostPart make_part(const std::vector<double>& A, const std::vector<double>& B, const std::vector<double>& C, int P) {
+  int m = (int)B.size();
+  HostPart h;
+  h.q = (m + P - 1) / P;
+  h.P = (m + h.q - 1) / h.q;
+  h.aL.assign(m, 0.0);
+  h.cp.assign(m, 0.0);
+  h.rd.assign(m, 0.0);
+  h.V.assign(m, 0.0);
+  h.W.assign(m, 0.0);
+  h.ch.assign(5 * (size_t)h.P, 0.0);
+  double beta_prev = 0.0;
+  for (int k = 0; k < h.P; ++k) {
+    int s = k * h.q, e = std::min(m, s + h.q), n = e - s;
+    std::vector<double> den(n), cpl(n);
+    den[0] = B[s];
+    cpl[0] = n > 1 ? C[s] / den[0] : 0.0;
+    for (int r = 1; r < n; ++r) {
+      den[r] = B[s + r] - A[s + r] * cpl[r - 1];
+      cpl[r] = r < n - 1 ? C[s + r] / den[r] : 0.0;
+    }
+    for (int r = 0; r < n; ++r) {
+      h.aL[s + r] = r == 0 ? 0.0 : A[s + r];
+      h.cp[s + r] = cpl[r];
+      h.rd[s + r] = 1.0 / den[r];
+    }
+    // responses to A_s x_{s-1} (row s) and C_{e-1} x_e (row e-1)
+    auto solve = [&](int row, double val, double* out) {
+      std::vector<double> y(n);
+      for (int r = 0; r < n; ++r) {
+        double rhs = r == row ? val : 0.0;
+        y[r] = (rhs - (r > 0 ? A[s + r] * y[r - 1] : 0.0)) / den[r];
+      }
+      for (int r = n - 2; r >= 0; --r) y[r] = y[r] - cpl[r] * y[r + 1];
+      for (int r = 0; r < n; ++r) out[s + r] = y[r];
+    };
+    solve(0, A[s], h.V.data());
+    solve(n - 1, C[e - 1], h.W.data());
+    double VF = h.V[s], VL = h.V[e - 1], WF = h.W[s], WL = h.W[e - 1];
+    double rF = 1.0 / (1.0 + VF * beta_prev);
+    double qF = -WF * rF;
+    double beta = -VL * beta_prev * qF - WL;
+    double* c = &h.ch[5 * (size_t)k];
+    c[0] = rF; c[1] = qF; c[2] = beta; c[3] = VF; c[4] = VL;
+    beta_prev = beta;
+  }
+  return h;
+}
+
+// chunks per column for a launch of `columns` columns of m rows: enough
+// threads to fill the GPU (152 SMs x 2048), at least 8 rows per chunk
+int choose_parts(int m, long long columns) {
+  int P = 1;
+  while (P < kPartMax && columns * 2LL * P <= 152LL * 2048 && m / (2 * P) >= 8) P *= 2;
+  return P;
+}
+
 struct DevLine {
   LineCoef lc{};
   double* buf = nullptr;
+  PartCoef pc{};        // pc.P >= 4: the partitioned solver is used
+  double* pbuf = nullptr;
 };
 
 }  // namespace
@@ -272,7 +350,7 @@ static int dalloc(T** p, size_t count) {
   return CG_OK;
 }
 
-static int upload_line(DevLine& L, int m, double a, bool cyclic, int lo) {
+static int upload_line(DevLine& L, int m, double a, bool cyclic, int lo, long long launch_columns) {
   HostLine h = make_line(m, a, cyclic);
   int rc = dalloc(&L.buf, (size_t)3 * m);
   if (rc) return rc;
@@ -292,6 +370,34 @@ static int upload_line(DevLine& L, int m, double a, bool cyclic, int lo) {
   L.lc.m = m;
   L.lc.lo = lo;
   L.lc.periodic = cyclic ? 1 : 0;
+  int P = choose_parts(m, launch_columns);
+  if (P >= 4) {
+    std::vector<double> A, B, C;
+    double gam = -1.0;
+    line_rows(m, a, cyclic, A, B, C, &gam);
+    HostPart hp = make_part(A, B, C, P);
+    size_t cnt = 5 * (size_t)m + hp.ch.size();
+    rc = dalloc(&L.pbuf, cnt);
+    if (rc) return rc;
+    std::vector<double> pk;
+    pk.reserve(cnt);
+    for (auto* v : {&hp.aL, &hp.cp, &hp.rd, &hp.V, &hp.W, &hp.ch}) pk.insert(pk.end(), v->begin(), v->end());
+    CG_CUDA(cudaMemcpy(L.pbuf, pk.data(), cnt * sizeof(double), cudaMemcpyHostToDevice));
+    L.pc.aL = L.pbuf;
+    L.pc.cp = L.pbuf + m;
+    L.pc.rd = L.pbuf + 2 * (size_t)m;
+    L.pc.V = L.pbuf + 3 * (size_t)m;
+    L.pc.W = L.pbuf + 4 * (size_t)m;
+    L.pc.ch = L.pbuf + 5 * (size_t)m;
+    L.pc.z = cyclic ? L.lc.z : nullptr;
+    L.pc.a = a;
+    L.pc.gam = h.gam;
+    L.pc.fden = h.fden;
+    L.pc.m = m;
+    L.pc.q = hp.q;
+    L.pc.P = hp.P;
+    L.pc.periodic = cyclic ? 1 : 0;
+  }
   return CG_OK;
 }
 
@@ -454,8 +560,8 @@ static GbrCfg gbr_cfg(const cg_solver* s) {
 template <int ND, int DIR, bool CART, bool COMPACT>
 static int launch_sweep(cg_solver* s, const StageArgs& A, cudaStream_t st) {
   TimedRegion tr(s, CG_TIMING_SWEEP, st);
-  int e = launch_sweep_any(s->p.precision == CG_MIXED, ND, DIR, s->sweep_lw[DIR], CART, COMPACT, s->dg, gbr_cfg(s),
-                           A, st);
+  int form = s->p.precision == CG_MIXED ? kSweepFP32 : (s->p.exact_fp64 ? kSweepExact : kSweepContracted);
+  int e = launch_sweep_any(form, ND, DIR, s->sweep_lw[DIR], CART, COMPACT, s->dg, gbr_cfg(s), A, st);
   if (e) return fail(CG_ERR_CUDA, "sweep launch (dir %d, %d lines per tile): %s", DIR, s->sweep_lw[DIR],
                      cudaGetErrorString((cudaError_t)e));
   s->launches++;
@@ -470,10 +576,47 @@ static int sweep_dir(cg_solver* s, int dir, const StageArgs& A, cudaStream_t st)
   return fail(CG_ERR_INVALID_ARG, "bad direction");
 }
 
-// one thread per line column in 32-thread blocks, so the few long recurrences
-// spread over as many SMs as possible
-static void launch_thomas(const ThomasJobs& J, cudaStream_t st) {
-  long long cols = J.start[J.njobs];
+// Line solves of up to three systems in one launch.  Many columns: one thread
+// per column in 32-thread blocks, so the long recurrences spread over as many
+// SMs as possible.  Few columns (every system partitioned at set-up): the
+// partitioned solver, 32 columns times the chunks per block.
+struct LineJob {
+  const DevLine* L;
+  double* x;
+  long long nl;
+  int ncomp;
+};
+
+static void launch_lines(const LineJob* jobs, int n, cudaStream_t st) {
+  bool part = true;
+  for (int j = 0; j < n; ++j) part = part && jobs[j].L->pc.P >= 4;
+  if (part) {
+    PartJobs J;
+    J.njobs = n;
+    J.start[0] = 0;
+    int Pmax = 1;
+    for (int j = 0; j < n; ++j) {
+      J.pc[j] = jobs[j].L->pc;
+      J.x[j] = jobs[j].x;
+      J.nl[j] = jobs[j].nl;
+      J.ncomp[j] = jobs[j].ncomp;
+      J.start[j + 1] = J.start[j] + (jobs[j].nl * jobs[j].ncomp + 31) / 32 * 32;
+      Pmax = std::max(Pmax, J.pc[j].P);
+    }
+    k_tri_part<<<(unsigned)(J.start[n] / 32), dim3(32, Pmax), 0, st>>>(J);
+    return;
+  }
+  ThomasJobs J;
+  J.njobs = n;
+  J.start[0] = 0;
+  for (int j = 0; j < n; ++j) {
+    J.lc[j] = jobs[j].L->lc;
+    J.x[j] = jobs[j].x;
+    J.nl[j] = jobs[j].nl;
+    J.ncomp[j] = jobs[j].ncomp;
+    J.start[j + 1] = J.start[j] + jobs[j].nl * jobs[j].ncomp;
+  }
+  long long cols = J.start[n];
   k_thomas_jobs<<<(unsigned)((cols + 31) / 32), 32, 0, st>>>(J);
 }
 
@@ -486,20 +629,14 @@ static int stage_prep_gbr(cg_solver* s, const double* Uc, bool compact, cudaStre
     s->launches++;
   }
   if (compact) {
-    ThomasJobs J;
-    J.njobs = ND;
-    J.start[0] = 0;
+    LineJob jobs[3];
     for (int d = 0; d < ND; ++d) {
       const LineBuf& lb = s->gdLB[d];
       k_rhs_mig4<ND><<<grid_blocks((long long)lb.m * lb.nl, 256), 256, 0, st>>>(s->dg, s->W, lb, s->G[d]);
       s->launches++;
-      J.lc[d] = s->mig4[d].lc;
-      J.x[d] = s->G[d];
-      J.nl[d] = lb.nl;
-      J.ncomp[d] = ND + 2;
-      J.start[d + 1] = J.start[d] + lb.nl * (ND + 2);
+      jobs[d] = LineJob{&s->mig4[d], s->G[d], lb.nl, ND + 2};
     }
-    launch_thomas(J, st);
+    launch_lines(jobs, ND, st);
     s->launches++;
   }
   if (s->dg.curv) {
@@ -717,6 +854,7 @@ CG_API void cg_params_default(cg_params* p) {
   p->pr = 0.72;
   p->suth = 0.0;
   p->twall = 1.0;
+  p->exact_fp64 = 0;
 }
 
 CG_API int cg_solver_set_inflow_profile(cg_solver* s, int dir, int side, const double* W_host) {
@@ -822,8 +960,10 @@ CG_API void cg_solver_destroy(cg_solver* s) {
   for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
   for (int d = 0; d < 3; ++d) {
     DevLine* ls[4] = {&s->mig4[d], &s->c6grad[d], &s->c6flux[d], &s->filt[d]};
-    for (DevLine* l : ls)
+    for (DevLine* l : ls) {
       if (l->buf) cudaFree(l->buf);
+      if (l->pbuf) cudaFree(l->pbuf);
+    }
   }
   lad_free(s->lad);
   for (int d = 0; d < 3; ++d)
@@ -877,14 +1017,18 @@ CG_API int cg_solver_create(const cg_grid* g, const cg_params* p, cg_solver** ou
   cudaMemset(s->hyb_flag, 0, 2 * sizeof(int));
   cudaMemset(s->hyb_count, 0, sizeof(unsigned long long));
   bool compact = p->scheme == CG_MIG4;
+  long long mig4_cols = 0;
   for (int d = 0; d < s->nd; ++d) {
     s->gdLB[d] = make_lines(s, d, -6, g->n[d] + 12, 4);
+    mig4_cols += s->gdLB[d].nl * s->nv;
+  }
+  for (int d = 0; d < s->nd; ++d) {
     if (compact) {
       if ((rc = dalloc(&s->G[d], (size_t)s->nv * s->gdLB[d].m * s->gdLB[d].nl))) { cg_solver_destroy(s); return rc; }
       bool cyc = g->bc[d][0] == CG_BC_PERIODIC;
       int m = cyc ? g->n[d] : g->n[d] + 12;
       if (cyc && m < 3) { cg_solver_destroy(s); return fail(CG_ERR_INVALID_ARG, "periodic compact lines need n >= 3"); }
-      if ((rc = upload_line(s->mig4[d], m, 0.25, cyc, -6))) { cg_solver_destroy(s); return rc; }
+      if ((rc = upload_line(s->mig4[d], m, 0.25, cyc, -6, mig4_cols))) { cg_solver_destroy(s); return rc; }
     }
   }
   if (g->curv) {

@@ -194,9 +194,13 @@ __host__ __device__ constexpr int sweep_smem_doubles() {
 template <int ND, bool CART, typename T>
 __host__ __device__ constexpr int sweep_min_blocks() { return (ND == 3 && !CART && sizeof(T) == 8) ? 1 : 2; }
 
-// T = double: FP64 parity form; T = float: mixed form (FP32 reconstruction and
+// T = double: FP64 form; T = float: mixed form (FP32 reconstruction and
 // fluxes from FP64 primitives; FP64 flux differences, residual and RK update).
-template <int ND, int DIR, bool CART, bool COMPACT, typename T, int LW>
+// UNIT tags the translation unit that compiles the kernel (0: FP64 without
+// contraction, the oracle's operation order; 1: FP64 with fused multiply-add;
+// 2: FP32): the code is the same, the compilation flags differ, and distinct
+// instantiations keep the units' kernels apart.
+template <int ND, int DIR, bool CART, bool COMPACT, typename T, int LW, int UNIT>
 __global__ void __launch_bounds__(256, sweep_min_blocks<ND, CART, T>()) k_gbr_sweep(DevGrid g, GbrCfg q, StageArgs A) {
   static_assert((SWEEP_TL * LW) % 256 == 0, "a tile must hold a multiple of the block's threads");
   constexpr int NV = ND + 2, IP = ND + 1;

@@ -29,19 +29,24 @@ static int lad_alloc(cg_solver* s) {
     return rc;
   if (sch == CG_LAD_C6) {
     size_t dmax = 0, fl = 0;
+    long long grad_cols = 0;
+    for (int d = 0; d < nd; ++d) {
+      int n = s->dg.n[d];
+      L.dfLB[d] = make_lines(s, d, -6, n + 12, 3);
+      L.DLB[d] = make_lines(s, d, 0, n, 0);
+      L.filtLB[d] = make_lines(s, d, -1, n + 2, 0);
+      grad_cols += L.dfLB[d].nl * nf;
+    }
     for (int d = 0; d < nd; ++d) {
       bool cyc = s->grid->bc[d][0] == CG_BC_PERIODIC;
       int n = s->dg.n[d];
       if (cyc && n < 3) return fail(CG_ERR_INVALID_ARG, "periodic compact lines need n >= 3");
-      L.dfLB[d] = make_lines(s, d, -6, n + 12, 3);
-      L.DLB[d] = make_lines(s, d, 0, n, 0);
-      L.filtLB[d] = make_lines(s, d, -1, n + 2, 0);
       if ((rc = dalloc(&L.df[d], (size_t)nf * L.dfLB[d].m * L.dfLB[d].nl))) return rc;
       dmax = std::max(dmax, (size_t)nv * (size_t)L.DLB[d].m * (size_t)L.DLB[d].nl);
       fl = std::max(fl, (size_t)nv * (size_t)L.filtLB[d].m * (size_t)L.filtLB[d].nl);
-      if ((rc = upload_line(s->c6grad[d], cyc ? n : n + 12, 1.0 / 3.0, cyc, -6))) return rc;
-      if ((rc = upload_line(s->c6flux[d], n, 1.0 / 3.0, cyc, 0))) return rc;
-      if ((rc = upload_line(s->filt[d], cyc ? n : n + 2, s->p.alpha_f, cyc, -1))) return rc;
+      if ((rc = upload_line(s->c6grad[d], cyc ? n : n + 12, 1.0 / 3.0, cyc, -6, grad_cols))) return rc;
+      if ((rc = upload_line(s->c6flux[d], n, 1.0 / 3.0, cyc, 0, L.DLB[d].nl * nv))) return rc;
+      if ((rc = upload_line(s->filt[d], cyc ? n : n + 2, s->p.alpha_f, cyc, -1, L.filtLB[d].nl * nv))) return rc;
     }
     if ((rc = dalloc(&L.D, dmax)) || (rc = dalloc(&L.lines, fl))) return rc;
   }
@@ -74,20 +79,14 @@ static int lad_coeffs_run(cg_solver* s, int dkind, cudaStream_t st, const int* g
   k_lad_fieldbuf<ND, T><<<grid_blocks(L.fbx.size(), 256), 256, 0, st>>>(s->dg, s->W, fb, L.fbx);
   s->launches++;
   if (c6) {
-    ThomasJobs J;
-    J.njobs = ND;
-    J.start[0] = 0;
+    LineJob jobs[3];
     for (int l = 0; l < ND; ++l) {
       const LineBuf& lb = L.dfLB[l];
       k_rhs_c6<<<grid_blocks((long long)lb.m * lb.nl, 256), 256, 0, st>>>(reinterpret_cast<double*>(fb), L.fbx, ND + 3, lb, L.df[l]);
       s->launches++;
-      J.lc[l] = s->c6grad[l].lc;
-      J.x[l] = L.df[l];
-      J.nl[l] = lb.nl;
-      J.ncomp[l] = ND + 3;
-      J.start[l + 1] = J.start[l] + lb.nl * (ND + 3);
+      jobs[l] = LineJob{&s->c6grad[l], L.df[l], lb.nl, ND + 3};
     }
-    launch_thomas(J, st);
+    launch_lines(jobs, ND, st);
     s->launches++;
   }
   int gb = grid_blocks(L.b3.size(), 128);
@@ -198,7 +197,8 @@ static int lad_pass(cg_solver* s, int dkind, StageArgs A, cudaStream_t st, const
     LineBuf DL = L.DLB[l];
     if (dkind == 3) {
       k_rhs_c6<<<grid_blocks((long long)DL.m * DL.nl, 256), 256, 0, st>>>(reinterpret_cast<const double*>(L.Fn), L.fbox[l], ND + 2, DL, L.D);
-      k_thomas<<<(unsigned)((DL.nl * (ND + 2) + 31) / 32), 32, 0, st>>>(s->c6flux[l].lc, L.D, DL.nl, ND + 2);
+      LineJob job{&s->c6flux[l], L.D, DL.nl, ND + 2};
+      launch_lines(&job, 1, st);
       s->launches += 2;
       D = L.D;
     }
@@ -292,7 +292,8 @@ static int lad_filter(cg_solver* s, double* U, cudaStream_t st) {
     const LineBuf& lb = s->lad.filtLB[l];
     k_rhs_filter<ND><<<grid_blocks((long long)lb.m * lb.nl, 256), 256, 0, st>>>(s->dg, U, lb, b[0], b[1], b[2], b[3],
                                                                               b[4], s->lad.lines);
-    k_thomas<<<(unsigned)((lb.nl * (ND + 2) + 31) / 32), 32, 0, st>>>(s->filt[l].lc, s->lad.lines, lb.nl, ND + 2);
+    LineJob job{&s->filt[l], s->lad.lines, lb.nl, ND + 2};
+    launch_lines(&job, 1, st);
     k_filter_store<ND><<<grid_blocks(s->N, 256), 256, 0, st>>>(s->dg, s->lad.lines, lb, U);
     s->launches += 3;
   }

@@ -171,6 +171,105 @@ __device__ __forceinline__ void thomas_column(const LineCoef& lc, double* __rest
   }
 }
 
+// ---------------------------------------------------------------- partitioned solves
+// For few columns (a 1D grid, few lines) one thread per column leaves the GPU
+// idle: each column is split into P chunks of q rows solved concurrently.
+// Chunk k solves its own block T_k (local pivots), giving y = T_k^{-1} r and,
+// precomputed on the host, the responses V = T_k^{-1}(A_s e_s) and
+// W = T_k^{-1}(C_{e-1} e_{e-1}) to the unknowns just outside it, so that
+// x_i = y_i - V_i x_{s-1} - W_i x_e.  The 2P chunk-boundary unknowns then
+// satisfy a block-bidiagonal recursion (host-computed factors rF, qF, beta),
+// solved by one thread per column; a last pass applies the correction (and,
+// for cyclic lines, the Sherman-Morrison term).  A block holds 32 columns
+// (lanes, coalesced) times the chunks.
+struct PartCoef {
+  const double* aL;   // sub-diagonal of row i inside its chunk (0 at chunk starts)
+  const double* cp;   // local elimination: super-diagonal / pivot (0 at chunk ends)
+  const double* rd;   // reciprocal local pivots
+  const double* V;    // response to the unknown before the chunk
+  const double* W;    // response to the unknown after the chunk
+  const double* z;    // cyclic: Sherman-Morrison vector, else null
+  const double* ch;   // per chunk: rF, qF, beta, VF (= V at its first row), VL (= V at its last row)
+  double a, gam, fden;
+  int m, q, P, periodic;
+};
+
+struct PartJobs {
+  PartCoef pc[3];
+  double* x[3];
+  long long nl[3];
+  int ncomp[3];
+  long long start[4];  // first 32-column group of each job, in columns (multiples of 32)
+  int njobs;
+};
+
+constexpr int kPartMax = 32;
+
+__global__ void __launch_bounds__(1024) k_tri_part(PartJobs J) {
+  __shared__ double sYF[kPartMax][32], sYL[kPartMax][32], sF[kPartMax][32], sL[kPartMax][32];
+  __shared__ double sFact[32];
+  const int lane = threadIdx.x, k = threadIdx.y;
+  const long long g0 = (long long)blockIdx.x * 32;
+  int j = 0;
+  while (j + 1 < J.njobs && g0 >= J.start[j + 1]) ++j;
+  const PartCoef& pc = J.pc[j];
+  const long long nl = J.nl[j];
+  const long long c = g0 - J.start[j] + lane;
+  const bool active = c < nl * J.ncomp[j];
+  double* col = J.x[j] + (active ? (c / nl) * pc.m * nl + c % nl : 0);
+  const int s = k * pc.q, e = min(pc.m, s + pc.q);
+  const bool mine = active && k < pc.P && s < e;
+  if (mine) {
+    double y = col[(long long)s * nl] * pc.rd[s];
+    col[(long long)s * nl] = y;
+    for (int i = s + 1; i < e; ++i) {
+      y = __fma_rn(-pc.aL[i], y, col[(long long)i * nl]) * pc.rd[i];
+      col[(long long)i * nl] = y;
+    }
+    sYL[k][lane] = y;
+    for (int i = e - 2; i >= s; --i) {
+      y = __fma_rn(-pc.cp[i], y, col[(long long)i * nl]);
+      col[(long long)i * nl] = y;
+    }
+    sYF[k][lane] = y;
+  }
+  __syncthreads();
+  if (k == 0 && active) {
+    // forward: F_k = pF_k + qF_k F_{k+1},  L_k = alpha_k + beta_k F_{k+1}
+    double alpha = 0.0, beta_prev = 0.0;
+    for (int kk = 0; kk < pc.P; ++kk) {
+      const double* h = pc.ch + 5 * kk;
+      double pF = __fma_rn(-h[3], alpha, sYF[kk][lane]) * h[0];
+      alpha = __fma_rn(-h[4], __fma_rn(beta_prev, pF, alpha), sYL[kk][lane]);
+      sF[kk][lane] = pF;
+      sL[kk][lane] = alpha;
+      beta_prev = h[2];
+    }
+    double Fn = 0.0;
+    for (int kk = pc.P - 1; kk >= 0; --kk) {
+      const double* h = pc.ch + 5 * kk;
+      double F = __fma_rn(h[1], Fn, sF[kk][lane]);
+      double L = __fma_rn(h[2], Fn, sL[kk][lane]);
+      sF[kk][lane] = F;
+      sL[kk][lane] = L;
+      Fn = F;
+    }
+    if (pc.periodic) sFact[lane] = (sF[0][lane] + pc.a * sL[pc.P - 1][lane] / pc.gam) / pc.fden;
+  }
+  __syncthreads();
+  if (mine) {
+    const double Lp = k > 0 ? sL[k - 1][lane] : 0.0;
+    const double Fn = k + 1 < pc.P ? sF[k + 1][lane] : 0.0;
+    const double f = pc.periodic ? sFact[lane] : 0.0;
+    for (int i = s; i < e; ++i) {
+      double x = __fma_rn(-pc.V[i], Lp, col[(long long)i * nl]);
+      x = __fma_rn(-pc.W[i], Fn, x);
+      if (pc.periodic) x = __fma_rn(-f, pc.z[i], x);
+      col[(long long)i * nl] = x;
+    }
+  }
+}
+
 #define LB_LOOP(lb, e) \
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)(lb).m * (lb).nl; \
        e += (long long)gridDim.x * blockDim.x)

@@ -1,8 +1,8 @@
 // Launchers of the C-GBR interface sweep, one translation unit per
-// (arithmetic type, dimension) so that the many instantiations (direction x
-// grid kind x gradient kind x lines per tile) compile in parallel.  The FP64
-// units are compiled without FMA contraction (the oracle's operation order),
-// the FP32 ones (the mixed form) with it.
+// (arithmetic form, dimension) so that the many instantiations (direction x
+// grid kind x gradient kind x lines per tile) compile in parallel.  Forms:
+// FP64 without FMA contraction (the oracle's operation order, bitwise
+// reproducible), FP64 with contraction, FP32 (the mixed form, contracted).
 #pragma once
 #include "cg_kernels.cuh"
 
@@ -20,14 +20,24 @@ constexpr int kSweepLwCands1[] = {4, 8, 16};   // dir 1, 2 (tile rows contiguous
 CGK_SWEEP_DECL(launch_sweep_f64_1)
 CGK_SWEEP_DECL(launch_sweep_f64_2)
 CGK_SWEEP_DECL(launch_sweep_f64_3)
+CGK_SWEEP_DECL(launch_sweep_f64c_1)
+CGK_SWEEP_DECL(launch_sweep_f64c_2)
+CGK_SWEEP_DECL(launch_sweep_f64c_3)
 CGK_SWEEP_DECL(launch_sweep_f32_1)
 CGK_SWEEP_DECL(launch_sweep_f32_2)
 CGK_SWEEP_DECL(launch_sweep_f32_3)
 #undef CGK_SWEEP_DECL
 
-inline int launch_sweep_any(bool fp32, int nd, int dir, int lw, bool cart, bool compact, const DevGrid& g,
+constexpr int kSweepExact = 0, kSweepContracted = 1, kSweepFP32 = 2;
+
+inline int launch_sweep_any(int form, int nd, int dir, int lw, bool cart, bool compact, const DevGrid& g,
                             const GbrCfg& q, const StageArgs& A, cudaStream_t st) {
-  if (fp32) {
+  if (form == kSweepContracted) {
+    if (nd == 1) return launch_sweep_f64c_1(dir, lw, cart, compact, g, q, A, st);
+    if (nd == 2) return launch_sweep_f64c_2(dir, lw, cart, compact, g, q, A, st);
+    return launch_sweep_f64c_3(dir, lw, cart, compact, g, q, A, st);
+  }
+  if (form == kSweepFP32) {
     if (nd == 1) return launch_sweep_f32_1(dir, lw, cart, compact, g, q, A, st);
     if (nd == 2) return launch_sweep_f32_2(dir, lw, cart, compact, g, q, A, st);
     return launch_sweep_f32_3(dir, lw, cart, compact, g, q, A, st);

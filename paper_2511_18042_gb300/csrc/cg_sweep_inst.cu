@@ -1,11 +1,13 @@
 // Instantiations and launchers of the C-GBR interface sweep for one arithmetic
-// type and dimension, selected at compile time by CGK_SWEEP_FP32 (0: FP64
-// parity form, 1: mixed form) and CGK_SWEEP_ND (1, 2 or 3).
+// form and dimension, selected at compile time by CGK_SWEEP_UNIT (0: FP64
+// without contraction, 1: FP64 with fused multiply-add, 2: FP32 mixed form;
+// the build passes the matching -fmad flag) and CGK_SWEEP_ND (1, 2 or 3).
 #include "cg_sweep.h"
 
-#if !defined(CGK_SWEEP_ND) || !defined(CGK_SWEEP_FP32)
-#error "compile with -DCGK_SWEEP_ND=<1|2|3> -DCGK_SWEEP_FP32=<0|1>"
+#if !defined(CGK_SWEEP_ND) || !defined(CGK_SWEEP_UNIT)
+#error "compile with -DCGK_SWEEP_ND=<1|2|3> -DCGK_SWEEP_UNIT=<0|1|2>"
 #endif
+#define CGK_SWEEP_FP32 (CGK_SWEEP_UNIT == 2)
 
 namespace cgk {
 
@@ -36,12 +38,12 @@ int launch_one(const DevGrid& g, const GbrCfg& q, const StageArgs& A, cudaStream
   size_t smem = sizeof(ST) * sweep_smem_doubles<SND, LW>();
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_gbr_sweep<SND, DIR, CART, COMPACT, ST, LW>,
+    cudaError_t e = cudaFuncSetAttribute(k_gbr_sweep<SND, DIR, CART, COMPACT, ST, LW, CGK_SWEEP_UNIT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return (int)e;
     attr_set = true;
   }
-  k_gbr_sweep<SND, DIR, CART, COMPACT, ST, LW><<<sweep_grid<DIR, LW>(g), 256, smem, st>>>(g, q, A);
+  k_gbr_sweep<SND, DIR, CART, COMPACT, ST, LW, CGK_SWEEP_UNIT><<<sweep_grid<DIR, LW>(g), 256, smem, st>>>(g, q, A);
   return (int)cudaGetLastError();
 }
 
@@ -64,8 +66,10 @@ int launch_dir(int lw, bool cart, bool compact, const DevGrid& g, const GbrCfg& 
 
 #define CGK_CAT3_(a, b, c) a##b##c
 #define CGK_CAT3(a, b, c) CGK_CAT3_(a, b, c)
-#if CGK_SWEEP_FP32
+#if CGK_SWEEP_UNIT == 2
 #define CGK_SWEEP_NAME CGK_CAT3(launch_sweep_f32_, CGK_SWEEP_ND, )
+#elif CGK_SWEEP_UNIT == 1
+#define CGK_SWEEP_NAME CGK_CAT3(launch_sweep_f64c_, CGK_SWEEP_ND, )
 #else
 #define CGK_SWEEP_NAME CGK_CAT3(launch_sweep_f64_, CGK_SWEEP_ND, )
 #endif

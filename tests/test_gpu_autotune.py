@@ -1,7 +1,9 @@
 """Autotuner of the sweep tile shape and of the batch stream-pool width: every
-candidate tile shape gives the same right-hand side bit for bit (it only
-regroups the same per-interface work), the tuner picks a candidate and caches
-it per grid shape, and tuning a batch leaves its states unchanged."""
+candidate tile shape gives the same right-hand side (it only regroups the same
+per-interface work): bit for bit in the exact FP64 form; to rounding where the
+compiler fuses multiply-adds (contracted FP64, FP32), since fusion is decided
+per instantiation.  The tuner picks a candidate and caches it per grid shape,
+and tuning a batch leaves its states unchanged."""
 import itertools
 
 import pytest
@@ -11,7 +13,7 @@ from paper_2511_18042_gb300 import inputs
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-from tests.gpu_util import to_dev  # noqa: E402
+from tests.gpu_util import rel_err, to_dev  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -34,10 +36,21 @@ def _cases():
     W[1], W[2], W[3] = 0.3, -0.2, 0.1
     W[4] = 1.0 + 0.05 * np.cos(6.28 * xyz[1])
     c3 = inputs.field_on_curvilinear(xyz, per, W)
-    return [("tp_meg6", tp, dict(scheme="MEG6")), ("tp_mig4", tp, dict(scheme="MIG4")),
+    return [("tp_meg6_exact", tp, dict(scheme="MEG6", exact_fp64=1)), ("tp_meg6", tp, dict(scheme="MEG6")),
+            ("tp_mig4_exact", tp, dict(scheme="MIG4", exact_fp64=1)),
             ("tp_meg6_mixed", tp, dict(scheme="MEG6", precision=1)),
-            ("tp_hybrid_cell", tp, dict(scheme="HYBRID", hybrid_mode=1, hyb_rho=0.2, hybrid_sensor=1)),
-            ("curv3d_meg6", c3, dict(scheme="MEG6")), ("curv3d_mig4_mixed", c3, dict(scheme="MIG4", precision=1))]
+            ("tp_hybrid_cell_exact", tp, dict(scheme="HYBRID", hybrid_mode=1, hyb_rho=0.2, hybrid_sensor=1,
+                                               exact_fp64=1)),
+            ("curv3d_meg6_exact", c3, dict(scheme="MEG6", exact_fp64=1)), ("curv3d_meg6", c3, dict(scheme="MEG6")),
+            ("curv3d_mig4_mixed", c3, dict(scheme="MIG4", precision=1))]
+
+
+def _same(a, b, kw):
+    if kw.get("exact_fp64"):
+        return torch.equal(a, b)
+    if kw.get("precision"):  # FP32: the mixed form's own metric, relative L1 per variable
+        return all(float((a[v] - b[v]).abs().mean() / b[v].abs().mean()) <= 1e-5 for v in range(a.shape[0]))
+    return rel_err(a, b.cpu().numpy()) <= 1e-13
 
 
 @pytest.mark.parametrize("name,prob,kw", _cases(), ids=[c[0] for c in _cases()])
@@ -49,10 +62,10 @@ def test_every_tile_shape_gives_the_same_rhs(api, name, prob, kw):
     shapes = list(itertools.product(*[CANDS[d] for d in range(nd)]))
     for shape in shapes:
         s.set_tile_shape(shape)
-        assert torch.equal(s.rhs(U), ref), shape
+        assert _same(s.rhs(U), ref, kw), shape
     tuned = s.autotune(U, force=True)
     assert all(tuned[d] in CANDS[d] for d in range(nd))
-    assert torch.equal(s.rhs(U), ref)
+    assert _same(s.rhs(U), ref, kw)
     # a second solver of the same shape takes the cached choice
     s2 = api.Solver.from_problem(prob, **kw)
     assert s2.autotune(U) == tuned
@@ -85,6 +98,8 @@ def test_batch_autotune_keeps_states_and_results(api):
             batch.step(stream)
     stream.synchronize()
     alone = [api.Solver.from_problem(p, **kw) for p in probs]
+    for a, m in zip(alone, solvers):  # same tile shapes: the contracted forms round per instantiation
+        a.set_tile_shape(m.tile_shape())
     Ua = [to_dev(p["U"]) for p in probs]
     for s, U in zip(alone, Ua):
         s.advance(U, nsteps=5)

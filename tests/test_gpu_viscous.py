@@ -44,18 +44,23 @@ def _okw(kw):
 
 
 def RHS_TOL(kw):
-    """Single-RHS bound.  The explicit schemes follow the oracle's operation
-    order (bitwise).  The compact ones (MIG4 gradients, LAD-C6 derivatives)
-    solve their line systems with reciprocal pivots and fused multiply-adds:
-    a few ulp per row of the gradient, which the viscous terms difference
-    twice (an amplification of order 1/h against the residual's scale)."""
+    """Single-RHS bound, the solvers in their exact FP64 form (exact_fp64 = 1).
+    The explicit schemes then follow the oracle's operation order (bitwise).
+    The compact ones (MIG4 gradients, LAD-C6 derivatives) solve their line
+    systems with reciprocal pivots and fused multiply-adds: a few ulp per row
+    of the gradient, which the viscous terms difference twice (an
+    amplification of order 1/h against the residual's scale)."""
     return 1e-12 if kw.get("scheme") in ("MIG4", "LAD_C6") else 1e-13
+
+
+def _solver(api, prob, kw):
+    return api.Solver.from_problem(prob, exact_fp64=1, **kw)
 
 
 @pytest.mark.parametrize("kw", SCHEMES)
 def test_shear_wave_rhs_and_steps(orc, api, kw):
     p = inputs.shear_wave(n=48, amp=0.05, minf=0.3, re=200.0, suth=0.7)
-    s = api.Solver.from_problem(p, **kw)
+    s = _solver(api, p, kw)
     o = orc.Oracle(p, **_okw(kw))
     U = p["U"]
     assert rel_err(s.rhs(to_dev(U)), o.rhs(U)) <= RHS_TOL(kw)
@@ -72,7 +77,7 @@ def test_wall_channel_rhs_and_steps(orc, api, kw):
     n, nx, minf, tw = 40, 24, 0.5, 1.3
     f = _odd_even(nx / n, tw, 1.0 / (1.4 * minf * minf))
     p = inputs.wall_channel(n=n, nx=nx, minf=minf, re=80.0, suth=0.6, twall=tw, fields=f)
-    s = api.Solver.from_problem(p, **kw)
+    s = _solver(api, p, kw)
     o = orc.Oracle(p, **_okw(kw))
     U = p["U"]
     assert rel_err(s.rhs(to_dev(U)), o.rhs(U)) <= RHS_TOL(kw)
@@ -112,7 +117,7 @@ def test_3d_curvilinear_viscous_rhs(orc, api, kw):
     xyz, per = inputs.wavy_grid_3d((16, 12, 10), amp=0.05)
     W = _field3(xyz)
     prob = inputs._viscous(inputs.field_on_curvilinear(xyz, per, W), 30.0, 0.3, 0.5, 1.0)
-    s = api.Solver.from_problem(prob, **kw)
+    s = _solver(api, prob, kw)
     o = orc.Oracle(prob, **kw)
     assert rel_err(s.rhs(to_dev(prob["U"])), o.rhs(prob["U"])) <= RHS_TOL(kw)
 
@@ -134,7 +139,7 @@ def test_inflow_profile_parallel_flow_3d(orc, api):
     prof[2] += 0.01 * np.sin(2 * math.pi * prof[1])
     prob["inflow_profile"] = {(0, 0): np.ascontiguousarray(prof.reshape(5, -1))}
     for kw in (dict(scheme="MEG6"), dict(scheme="LAD_E4"), dict(scheme="MIG4")):
-        s = api.Solver.from_problem(prob, **kw)
+        s = _solver(api, prob, kw)
         o = orc.Oracle(prob, **kw)
         assert rel_err(s.rhs(to_dev(prob["U"])), o.rhs(prob["U"])) <= RHS_TOL(kw), kw
 
@@ -151,7 +156,7 @@ def ramp():
 
 @pytest.mark.parametrize("kw", RAMP_KW)
 def test_compression_ramp_fp64_matches_oracle(orc, api, ramp, kw):
-    s = api.Solver.from_problem(ramp, **kw)
+    s = _solver(api, ramp, kw)
     o = orc.Oracle(ramp, **kw)
     U = ramp["U"]
     assert rel_err(s.rhs(to_dev(U)), o.rhs(U)) <= RHS_TOL(kw)
@@ -171,3 +176,20 @@ def test_compression_ramp_mixed_form(orc, api, ramp, kw):
     Uo, _, _ = o.advance(ramp["U"], nsteps=5)
     rho = Ug[0].cpu().numpy()
     assert np.abs(rho - Uo[0]).mean() / np.abs(Uo[0]).mean() <= 1e-5
+
+
+@pytest.mark.parametrize("kw", [dict(scheme="MEG6"), dict(scheme="MIG4"),
+                                dict(scheme="HYBRID", hybrid_mode=1, hybrid_sensor=1, hyb_rho=0.4)])
+def test_compression_ramp_default_contracted_form(orc, api, ramp, kw):
+    """The default FP64 form (the interface sweep's multiply-adds fused): the
+    residual of this nearly balanced boundary layer is ~1e-3 of the flux
+    scale |F|/h, so rounding-level flux differences read ~1e-12 against it;
+    after steps the state agrees to the spec bar."""
+    s = api.Solver.from_problem(ramp, **kw)
+    o = orc.Oracle(ramp, **kw)
+    U = ramp["U"]
+    assert rel_err(s.rhs(to_dev(U)), o.rhs(U)) <= 1e-11
+    Ug = to_dev(U)
+    s.advance(Ug, nsteps=5)
+    Uo, _, _ = o.advance(U, nsteps=5)
+    assert rel_err(Ug, Uo) <= 1e-11
