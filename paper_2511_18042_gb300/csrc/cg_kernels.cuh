@@ -78,11 +78,41 @@ __global__ void k_omega(DevGrid g, const double* __restrict__ W, const double* _
     r /= ob.ext[0];
     c[1] = (int)(r % ob.ext[1]) - ob.off[1];
     c[2] = (int)(r / ob.ext[1]) - ob.off[2];
+    T phi = T(0);
+    T du[3][3];  // du[l][k] = d u_k / d xi_l
+    // nodes whose whole stencil is interior read the planes directly (the
+    // same values the boundary mapping would give), and only the components
+    // used: pressure at the neighbours, velocities on the gradient stencil
+    bool inner = true;
+#pragma unroll
+    for (int d = 0; d < ND; ++d) inner = inner && c[d] >= 3 && c[d] < g.n[d] - 3;
+    if (inner) {
+      const long long q = lin(g, c[0], c[1], c[2]);
+      const T p0 = T(W[IP * g.N + q]);
+#pragma unroll
+      for (int l = 0; l < ND; ++l) {
+        const long long st = l == 0 ? 1 : (l == 1 ? (long long)g.n[0] : (long long)g.n[0] * g.n[1]);
+        const double* P = W + IP * g.N + q;
+        const T pm = T(P[-st]), pp = T(P[st]);
+        T a = fabs(pp - T(2.0) * p0 + pm) / (pp + T(2.0) * p0 + pm);
+        if (a > phi) phi = a;
+        if (!COMPACT) {
+#pragma unroll
+          for (int k = 0; k < ND; ++k) {
+            const double* V = W + (1 + k) * g.N + q;
+            du[l][k] = d6<T>(T(V[-3 * st]), T(V[-2 * st]), T(V[-st]), T(V[st]), T(V[2 * st]), T(V[3 * st]));
+          }
+        } else {
+          const double* G = l == 0 ? G0 : (l == 1 ? G1 : G2);
+          const LineBuf& gb = l == 0 ? gb0 : (l == 1 ? gb1 : gb2);
+#pragma unroll
+          for (int k = 0; k < ND; ++k) du[l][k] = T(G[gb.at(1 + k, c[l], c)]);
+        }
+      }
+    } else {
     double w0d[NV];
     load_state<ND>(g, W, c[0], c[1], c[2], w0d);
     const T p0 = T(w0d[IP]);
-    T phi = T(0);
-    T du[3][3];  // du[l][k] = d u_k / d xi_l
 #pragma unroll
     for (int l = 0; l < ND; ++l) {
       int cm[3] = {c[0], c[1], c[2]}, cp[3] = {c[0], c[1], c[2]};
@@ -114,6 +144,7 @@ __global__ void k_omega(DevGrid g, const double* __restrict__ W, const double* _
 #pragma unroll
         for (int k = 0; k < ND; ++k) du[l][k] = T(G[gb.at(1 + k, c[l], c)]);
       }
+    }
     }
     // physical velocity gradients gu[k][m] = sum_l (J xi_hat[l][m]) du[l][k]
     T gu[3][3];
