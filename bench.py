@@ -53,7 +53,7 @@ SWEEP_FLOP_PER_IFACE = 632.2  # profiles/sweep_meg6_triple_point_1792x768.md (me
 # dram read + write per launch (mean of x and y) of the sweep form the roofline times,
 # from its ncu capture (profiles/); None until the current kernel has been captured
 SWEEP_TRAFFIC_BYTES = {"exact": 92.05e6, "contracted": 91.95e6}
-ROOFLINE_FORM = "contracted"  # the library default (exact_fp64 = 0)
+ROOFLINE_FORM = "exact"  # the library default (fma_sweep = 0)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12  # SMs x DFMA/clk x 2 flop x max clock
 HBM_BYTES_PER_CELL_STEP = 256.0  # minimal-traffic model, FP64 state, nv = 4, uniform grid
 
@@ -133,6 +133,14 @@ def aggregate_over_ranks(ms_step, units_per_rank, device=None):
         ms_step = float(t.item())
         dist.barrier()
     return ms_step, ws * units_per_rank / (ms_step * 1e-3)
+
+
+def bench_config(names, ws):
+    """The workload of the JSON line, shared by both arms."""
+    return {"workload": "triple point 1792x768, FP64, one RK3 step of each of %d schemes "
+                        "from a developed state (200 MEG6 steps)" % len(names),
+            "schemes": names, "cells": NX * NY, "l2": "flushed between timed steps (256 MB write)",
+            "parallelism": "replicas" if ws > 1 else "single GPU"}
 
 
 def run_gpu(args):
@@ -245,10 +253,7 @@ def run_gpu(args):
         "value": value, "unit": "cell-updates/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": "triple point 1792x768 (config 2), FP64, one RK3 step of each of %d schemes "
-                               "from a developed state (200 MEG6 steps)" % len(names),
-                   "schemes": names, "cells": cells, "l2": "flushed between timed steps (256 MB write)",
-                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "config": bench_config(names, ws),
         "per_scheme": per_scheme, "mixed_precision": mixed, "sod_latency": sod, "compression_ramp": ramp, "batched": batched,
         "serving": serving,
         "roofline": roof, "e2e": e2e, "gpu_launches": launches // max(1, args.steps),
@@ -453,11 +458,11 @@ def time_mixed(api, torch, grid, base, dev, kw, args):
     return tot / max(1, args.steps)
 
 
-def sweep_roofline(api, torch, grid, base, dev, args):
+def _sweep_ms(api, torch, grid, base, dev, args, form):
     """Average duration of the MEG6 interface-sweep launches (CUDA events around
     each launch on its stream, recorded by the library) over RK3 steps of the
-    bench state; FP64 roofline of that kernel."""
-    s = api.Solver(grid, scheme="MEG6", exact_fp64=int(ROOFLINE_FORM == "exact"))
+    bench state, for the exact or the FMA form; returns (ms, launches, tile)."""
+    s = api.Solver(grid, scheme="MEG6", fma_sweep=int(form == "contracted"))
     tile = s.autotune(base)
     U = torch.empty_like(base)
     dtd = torch.zeros(2, dtype=torch.float64, device=dev)
@@ -475,19 +480,27 @@ def sweep_roofline(api, torch, grid, base, dev, args):
     torch.cuda.synchronize()
     ms, n = s.timing_query(0)
     s.timing_enable(False)
-    avg_ms = ms / n
+    return ms / n, n, tile
+
+
+def sweep_roofline(api, torch, grid, base, dev, args):
+    """FP64 roofline of the dominant kernel, the MEG6 interface sweep, in the
+    library's default (exact) form; the opt-in FMA form beside it."""
     ifaces = ((NX + 1) * NY + NX * (NY + 1)) / 2.0  # algorithmic interfaces per sweep launch (x, y average)
+    avg_ms, n, tile = _sweep_ms(api, torch, grid, base, dev, args, ROOFLINE_FORM)
     roof = {"bound": "alu", "unit": "TFLOP/s", "peak": FP64_PEAK_TFLOPS,
             "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (FP64 is not in MEASURED_PEAKS.json)",
             "kernel": "k_gbr_sweep (MEG6), x and y launches of RK3 steps of the bench state",
             "launch_ms": avg_ms, "launches": n, "ifaces_per_launch": ifaces,
             "traffic": SWEEP_TRAFFIC_BYTES[ROOFLINE_FORM], "form": ROOFLINE_FORM,
             "tile_lines": list(tile)}
-    if SWEEP_FLOP_PER_IFACE:
-        ach = SWEEP_FLOP_PER_IFACE * ifaces / (avg_ms * 1e-3) / 1e12
-        roof.update({"achieved": ach, "frac": ach / FP64_PEAK_TFLOPS, "flop_per_iface": SWEEP_FLOP_PER_IFACE})
-    else:
-        roof.update({"achieved": None, "frac": None})
+    ach = SWEEP_FLOP_PER_IFACE * ifaces / (avg_ms * 1e-3) / 1e12
+    roof.update({"achieved": ach, "frac": ach / FP64_PEAK_TFLOPS, "flop_per_iface": SWEEP_FLOP_PER_IFACE})
+    fms, fn, ftile = _sweep_ms(api, torch, grid, base, dev, args, "contracted")
+    fach = SWEEP_FLOP_PER_IFACE * ifaces / (fms * 1e-3) / 1e12
+    roof["fma_sweep"] = {"launch_ms": fms, "launches": fn, "tile_lines": list(ftile), "achieved": fach,
+                         "frac": fach / FP64_PEAK_TFLOPS, "traffic": SWEEP_TRAFFIC_BYTES["contracted"],
+                         "note": "opt-in FMA form (fma_sweep = 1): not bitwise; see profiles"}
     return roof
 
 
@@ -544,8 +557,7 @@ def run_reference(args):
             "value": value, "unit": "cell-updates/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "triple point 1792x768 (config 2), FP64, one RK3 step of each of %d schemes" % len(names),
-                       "sample": "%dx%d" % sample},
+            "config": dict(bench_config(names, ws), sample="%dx%d triple point from its initial state" % sample),
             "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": 1, "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)

@@ -89,17 +89,20 @@ typedef struct {
     double re, pr;        /* Reynolds number (reference length 1), Prandtl number */
     double suth;          /* Sutherland constant S / T_inf */
     double twall;         /* temperature of CG_BC_WALL faces (units of T_inf) */
-    /* FP64 C-GBR interface sweep: 1 evaluates every expression in the
-     * oracle's operation order without contracting a*b+c (bitwise
-     * reproducible); 0 lets the compiler fuse multiply-adds there (fewer FP64
-     * instructions; agrees to rounding).  Other kernels are always exact. */
-    int exact_fp64;
+    /* FP64 C-GBR interface sweep.  0 (default): every expression in the
+     * oracle's operation order, no a*b+c contracted (bitwise reproducible).
+     * 1: multiply-adds fused (16 % fewer FP64 instructions in the sweep);
+     * results agree to rounding, except where a value sits at a threshold of
+     * the selection (Eq. 8) and the branch flips: on the 1792x768 triple point
+     * the per-interface hybrid then differs by ~1e-11 after one step.  Other
+     * kernels are always exact. */
+    int fma_sweep;
 } cg_params;
 
 /* Fills the defaults: gamma 1.4, minf 1, MEG6, FP64, CFL 0.2, C_beta 1.75,
  * C_kappa 0.01, alpha_f 0.45, Omega threshold 0.01, MP eps 1e-20, alpha 4,
  * window 4, filter on, no hybrid thresholds, inviscid (re 1, pr 0.72,
- * suth 0, twall 1), contracted FP64 sweep (exact_fp64 0). */
+ * suth 0, twall 1), exact FP64 sweep (fma_sweep 0). */
 CG_API void cg_params_default(cg_params *p);
 
 /* Uniform Cartesian grid, node spacing h[d] (Sec. 2.1 with x = xi h).

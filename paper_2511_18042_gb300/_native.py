@@ -32,7 +32,7 @@ class CgParams(ctypes.Structure):
         ("pr", ctypes.c_double),
         ("suth", ctypes.c_double),
         ("twall", ctypes.c_double),
-        ("exact_fp64", ctypes.c_int),
+        ("fma_sweep", ctypes.c_int),
     ]
 
 

@@ -560,7 +560,7 @@ static GbrCfg gbr_cfg(const cg_solver* s) {
 template <int ND, int DIR, bool CART, bool COMPACT>
 static int launch_sweep(cg_solver* s, const StageArgs& A, cudaStream_t st) {
   TimedRegion tr(s, CG_TIMING_SWEEP, st);
-  int form = s->p.precision == CG_MIXED ? kSweepFP32 : (s->p.exact_fp64 ? kSweepExact : kSweepContracted);
+  int form = s->p.precision == CG_MIXED ? kSweepFP32 : (s->p.fma_sweep ? kSweepContracted : kSweepExact);
   int e = launch_sweep_any(form, ND, DIR, s->sweep_lw[DIR], CART, COMPACT, s->dg, gbr_cfg(s), A, st);
   if (e) return fail(CG_ERR_CUDA, "sweep launch (dir %d, %d lines per tile): %s", DIR, s->sweep_lw[DIR],
                      cudaGetErrorString((cudaError_t)e));
@@ -854,7 +854,7 @@ CG_API void cg_params_default(cg_params* p) {
   p->pr = 0.72;
   p->suth = 0.0;
   p->twall = 1.0;
-  p->exact_fp64 = 0;
+  p->fma_sweep = 0;
 }
 
 CG_API int cg_solver_set_inflow_profile(cg_solver* s, int dir, int side, const double* W_host) {

@@ -2,9 +2,9 @@
 
 The bar is the benchmark spec's tolerance, max relative error <= 1e-11 per variable
 after 100 RK3 steps (relative to the variable's largest magnitude), and
-<= 1e-13 for a single RHS evaluation.  With exact_fp64 = 1 the interface sweep
+<= 1e-13 for a single RHS evaluation.  The interface sweep (default form)
 evaluates every expression in the oracle's operation order without
-contraction, and MEG6 reproduces the oracle bit for bit."""
+contraction, and MEG6 and the hybrids reproduce the oracle bit for bit."""
 import math
 
 import numpy as np
@@ -168,10 +168,10 @@ def test_nonphysical_state_is_reported(api):
 
 @pytest.mark.parametrize("kw", [dict(scheme="MEG6"), dict(scheme="HYBRID", hybrid_mode=1, hyb_rho=0.3, hybrid_sensor=1),
                                 dict(scheme="HYBRID", hybrid_mode=0, hyb_rho=0.12)])
-def test_exact_fp64_is_bitwise(orc, api, kw):
+def test_exact_form_is_bitwise(orc, api, kw):
     prob = inputs.triple_point(130, 70)
     o = orc.Oracle(prob, **kw)
-    s = api.Solver.from_problem(prob, exact_fp64=1, **kw)
+    s = api.Solver.from_problem(prob, **kw)
     Uo, to, _ = o.advance(prob["U"], nsteps=20)
     Ug = to_dev(prob["U"])
     tg, _ = s.advance(Ug, nsteps=20)

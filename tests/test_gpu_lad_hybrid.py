@@ -97,7 +97,7 @@ def test_hybrid_global_triple_point(orc, api):
     prob = inputs.triple_point(224, 96)
     kw = dict(scheme="HYBRID", hybrid_mode=0, hyb_rho=0.12)
     o = orc.Oracle(prob, **kw)
-    s = api.Solver.from_problem(prob, exact_fp64=1, **kw)  # bitwise: equal dt and decisions every step
+    s = api.Solver.from_problem(prob, **kw)  # exact form, bitwise: equal dt and decisions every step
     U = prob["U"]
     Ug = to_dev(U)
     flags_o, flags_g = [], []

@@ -44,7 +44,7 @@ def _okw(kw):
 
 
 def RHS_TOL(kw):
-    """Single-RHS bound, the solvers in their exact FP64 form (exact_fp64 = 1).
+    """Single-RHS bound, the solvers in their exact FP64 form (the default).
     The explicit schemes then follow the oracle's operation order (bitwise).
     The compact ones (MIG4 gradients, LAD-C6 derivatives) solve their line
     systems with reciprocal pivots and fused multiply-adds: a few ulp per row
@@ -54,7 +54,7 @@ def RHS_TOL(kw):
 
 
 def _solver(api, prob, kw):
-    return api.Solver.from_problem(prob, exact_fp64=1, **kw)
+    return api.Solver.from_problem(prob, **kw)
 
 
 @pytest.mark.parametrize("kw", SCHEMES)
@@ -180,12 +180,12 @@ def test_compression_ramp_mixed_form(orc, api, ramp, kw):
 
 @pytest.mark.parametrize("kw", [dict(scheme="MEG6"), dict(scheme="MIG4"),
                                 dict(scheme="HYBRID", hybrid_mode=1, hybrid_sensor=1, hyb_rho=0.4)])
-def test_compression_ramp_default_contracted_form(orc, api, ramp, kw):
-    """The default FP64 form (the interface sweep's multiply-adds fused): the
+def test_compression_ramp_fma_form(orc, api, ramp, kw):
+    """The opt-in FMA form (the interface sweep's multiply-adds fused): the
     residual of this nearly balanced boundary layer is ~1e-3 of the flux
     scale |F|/h, so rounding-level flux differences read ~1e-12 against it;
     after steps the state agrees to the spec bar."""
-    s = api.Solver.from_problem(ramp, **kw)
+    s = api.Solver.from_problem(ramp, fma_sweep=1, **kw)
     o = orc.Oracle(ramp, **kw)
     U = ramp["U"]
     assert rel_err(s.rhs(to_dev(U)), o.rhs(U)) <= 1e-11
