@@ -729,8 +729,14 @@ static int rk3(cg_solver* s, double* U, cudaStream_t st) {
 template <int ND>
 static void cfl_launch(cg_solver* s, const double* U, double* dt_dev, double* t_dev, double t_end, cudaStream_t st) {
   cudaMemsetAsync(s->cflmax, 0, sizeof(unsigned long long), st);
-  if (s->dg.curv) k_cfl_max<ND, false><<<grid_blocks(s->N, 256), 256, 0, st>>>(s->dg, U, s->cflmax);
-  else k_cfl_max<ND, true><<<grid_blocks(s->N, 256), 256, 0, st>>>(s->dg, U, s->cflmax);
+  const bool mixed = s->p.precision == CG_MIXED;
+  if (s->dg.curv) {
+    if (mixed) k_cfl_max<ND, false, float><<<grid_blocks(s->N, 256), 256, 0, st>>>(s->dg, U, s->cflmax);
+    else k_cfl_max<ND, false, double><<<grid_blocks(s->N, 256), 256, 0, st>>>(s->dg, U, s->cflmax);
+  } else {
+    if (mixed) k_cfl_max<ND, true, float><<<grid_blocks(s->N, 256), 256, 0, st>>>(s->dg, U, s->cflmax);
+    else k_cfl_max<ND, true, double><<<grid_blocks(s->N, 256), 256, 0, st>>>(s->dg, U, s->cflmax);
+  }
   k_cfl_finish<<<1, 1, 0, st>>>(s->cflmax, s->p.cfl, dt_dev, t_dev, t_end);
   s->launches += 2;
 }

@@ -448,7 +448,9 @@ __global__ void __launch_bounds__(256, sweep_min_blocks<ND, CART, T>()) k_gbr_sw
 }
 
 // ---------------------------------------------------------------- CFL
-template <int ND, bool CART>
+// T = double: the exact FP64 rate.  T = float (mixed form): the primitives
+// (pressure recovery) in FP64, the sound speed and the spectral radii in FP32.
+template <int ND, bool CART, typename T = double>
 __global__ void k_cfl_max(DevGrid g, const double* __restrict__ U, unsigned long long* __restrict__ mx) {
   constexpr int NV = ND + 2, IP = ND + 1;
   double best = 0.0;
@@ -458,14 +460,14 @@ __global__ void k_cfl_max(DevGrid g, const double* __restrict__ U, unsigned long
 #pragma unroll
     for (int v = 0; v < NV; ++v) Q[v] = U[v * g.N + q];
     cons_to_prim<ND>(g.gm1, Q, w);
-    double cs = sqrt(g.gamma * w[IP] / w[0]);
-    double s = 0.0;
-    double J;
+    T cs = sqrt(T(g.gamma) * T(w[IP]) / T(w[0]));
+    T s = T(0);
+    T J;
     if (CART) {
-      J = g.cjac;
+      J = T(g.cjac);
 #pragma unroll
       for (int l = 0; l < ND; ++l) {
-        double t = fabs(g.cxh[l] * w[1 + l]) + cs * sqrt(g.cxh[l] * g.cxh[l]);
+        T t = fabs(T(g.cxh[l]) * T(w[1 + l])) + cs * sqrt(T(g.cxh[l]) * T(g.cxh[l]));
         s = (l == 0) ? t : s + t;
       }
     } else {
@@ -473,21 +475,21 @@ __global__ void k_cfl_max(DevGrid g, const double* __restrict__ U, unsigned long
       int j = (int)((q / g.n[0]) % g.n[1]);
       int i = (int)(q % g.n[0]);
       long long pq = plin(g, i, j, k);
-      J = g.jac[pq];
+      J = T(g.jac[pq]);
 #pragma unroll
       for (int l = 0; l < ND; ++l) {
-        double dot = 0.0, mag = 0.0;
+        T dot = T(0), mag = T(0);
 #pragma unroll
         for (int m = 0; m < ND; ++m) {
-          double x = g.xh[(l * ND + m) * g.NP + pq];
-          dot = (m == 0) ? x * w[1 + m] : dot + x * w[1 + m];
+          T x = T(g.xh[(l * ND + m) * g.NP + pq]);
+          dot = (m == 0) ? x * T(w[1 + m]) : dot + x * T(w[1 + m]);
           mag = (m == 0) ? x * x : mag + x * x;
         }
-        double t = fabs(dot) + cs * sqrt(mag);
+        T t = fabs(dot) + cs * sqrt(mag);
         s = (l == 0) ? t : s + t;
       }
     }
-    double r = J * s;
+    double r = double(J * s);
     if (r > best) best = r;
   }
   // block max, then one atomic (non-negative doubles order like their bits)

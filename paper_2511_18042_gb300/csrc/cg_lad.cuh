@@ -222,11 +222,17 @@ __global__ void k_gauss(DevGrid g, int l, const T* __restrict__ a, const T* __re
     c[1] = (int)((q / g.n[0]) % g.n[1]);
     c[2] = (int)(q / ((long long)g.n[0] * g.n[1]));
     long long s[9];
+    if (c[l] >= 4 && c[l] < g.n[l] - 4) {  // interior stencil: the nodes themselves
+      const long long st = l == 0 ? 1 : (l == 1 ? (long long)g.n[0] : (long long)g.n[0] * g.n[1]);
 #pragma unroll
-    for (int t = -4; t <= 4; ++t) {
-      int cc[3] = {c[0], c[1], c[2]};
-      cc[l] += t;
-      s[t + 4] = scalar_src(g, cc[0], cc[1], cc[2]);
+      for (int t = -4; t <= 4; ++t) s[t + 4] = q + t * st;
+    } else {
+#pragma unroll
+      for (int t = -4; t <= 4; ++t) {
+        int cc[3] = {c[0], c[1], c[2]};
+        cc[l] += t;
+        s[t + 4] = scalar_src(g, cc[0], cc[1], cc[2]);
+      }
     }
     ao[q] = A0 * a[s[4]] + A1 * (a[s[3]] + a[s[5]]) + A2 * (a[s[2]] + a[s[6]]) + A3 * (a[s[1]] + a[s[7]]) +
             A4 * (a[s[0]] + a[s[8]]);
@@ -359,7 +365,9 @@ __global__ void k_lad_nodeflux(DevGrid g, int l, const double* __restrict__ W, c
 
 // Stage epilogue shared by the LAD divergence kernels: tot = acc + D (or D),
 // then store acc, R = -J tot, or the RK combination.
-template <int ND>
+// FUSED (mixed form): the FP64 accumulation and RK combination with explicit
+// fused multiply-adds; otherwise the oracle's operation order.
+template <int ND, bool FUSED = false>
 __device__ __forceinline__ void lad_epilogue(const DevGrid& g, const StageArgs& A, long long qi, const int* c,
                                              const double* Dv) {
   constexpr int NV = ND + 2, IP = ND + 1;
@@ -380,7 +388,11 @@ __device__ __forceinline__ void lad_epilogue(const DevGrid& g, const StageArgs& 
     double dt = *A.dt;
     double un = A.Un[v * g.N + qi];
     double o;
-    if (A.stage == 1) o = un + dt * r;
+    if (FUSED) {
+      if (A.stage == 1) o = __fma_rn(dt, r, un);
+      else if (A.stage == 2) o = __fma_rn(0.75, un, 0.25 * __fma_rn(dt, r, A.Uc[v * g.N + qi]));
+      else o = __fma_rn(1.0 / 3.0, un, (2.0 / 3.0) * __fma_rn(dt, r, A.Uc[v * g.N + qi]));
+    } else if (A.stage == 1) o = un + dt * r;
     else if (A.stage == 2) o = 0.75 * un + 0.25 * (A.Uc[v * g.N + qi] + dt * r);
     else o = (1.0 / 3.0) * un + (2.0 / 3.0) * (A.Uc[v * g.N + qi] + dt * r);
     out[v] = o;
@@ -423,7 +435,7 @@ __global__ void k_lad_div(DevGrid g, int l, const T* __restrict__ Fn, Box fb, co
         Dv[v] = (double)d4(f[e - 2 * st], f[e - st], f[e + st], f[e + 2 * st]);
       }
     }
-    lad_epilogue<ND>(g, A, q, c, Dv);
+    lad_epilogue<ND, sizeof(T) == 4>(g, A, q, c, Dv);
   }
 }
 
