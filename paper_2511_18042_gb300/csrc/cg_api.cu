@@ -539,7 +539,8 @@ static void launch_omega(cg_solver* s, cudaStream_t st, const int* guard, int wa
   long long tot = s->omBox.size();
   if (s->p.precision == CG_MIXED)
     k_omega<ND, CART, COMPACT, float><<<grid_blocks(tot, 128), 128, 0, st>>>(
-        s->dg, s->W, s->G[0], s->G[1], s->G[2], s->gdLB[0], s->gdLB[1], s->gdLB[2], s->om, s->omBox, guard, want);
+        s->dg, reinterpret_cast<const float*>(s->W), s->G[0], s->G[1], s->G[2], s->gdLB[0], s->gdLB[1], s->gdLB[2],
+        s->om, s->omBox, guard, want);
   else
     k_omega<ND, CART, COMPACT, double><<<grid_blocks(tot, 128), 128, 0, st>>>(
         s->dg, s->W, s->G[0], s->G[1], s->G[2], s->gdLB[0], s->gdLB[1], s->gdLB[2], s->om, s->omBox, guard, want);
@@ -620,19 +621,33 @@ static void launch_lines(const LineJob* jobs, int n, cudaStream_t st) {
   k_thomas_jobs<<<(unsigned)((cols + 31) / 32), 32, 0, st>>>(J);
 }
 
+// Primitives of Uc into W: FP64 storage, or FP32 for the mixed form (the
+// recovery itself is FP64 in both).
+template <int ND>
+static void launch_prim(cg_solver* s, const double* Uc, cudaStream_t st) {
+  if (s->p.precision == CG_MIXED)
+    k_prim<ND, float><<<grid_blocks(s->N, 256), 256, 0, st>>>(s->dg, Uc, reinterpret_cast<float*>(s->W));
+  else
+    k_prim<ND, double><<<grid_blocks(s->N, 256), 256, 0, st>>>(s->dg, Uc, s->W);
+  s->launches++;
+}
+
 // Primitives, sensor (and compact gradients) of the state Uc into W, om, G.
 template <int ND>
 static int stage_prep_gbr(cg_solver* s, const double* Uc, bool compact, cudaStream_t st, bool prim = true,
                           const int* guard = nullptr, int want = 0) {
   if (prim) {
-    k_prim<ND><<<grid_blocks(s->N, 256), 256, 0, st>>>(s->dg, Uc, s->W);
-    s->launches++;
+    launch_prim<ND>(s, Uc, st);
   }
   if (compact) {
     LineJob jobs[3];
     for (int d = 0; d < ND; ++d) {
       const LineBuf& lb = s->gdLB[d];
-      k_rhs_mig4<ND><<<grid_blocks((long long)lb.m * lb.nl, 256), 256, 0, st>>>(s->dg, s->W, lb, s->G[d]);
+      if (s->p.precision == CG_MIXED)
+        k_rhs_mig4<ND, float><<<grid_blocks((long long)lb.m * lb.nl, 256), 256, 0, st>>>(
+            s->dg, reinterpret_cast<const float*>(s->W), lb, s->G[d]);
+      else
+        k_rhs_mig4<ND, double><<<grid_blocks((long long)lb.m * lb.nl, 256), 256, 0, st>>>(s->dg, s->W, lb, s->G[d]);
       s->launches++;
       jobs[d] = LineJob{&s->mig4[d], s->G[d], lb.nl, ND + 2};
     }
@@ -651,8 +666,7 @@ static int stage_prep_gbr(cg_solver* s, const double* Uc, bool compact, cudaStre
 
 template <int ND>
 static int stage_prep_prim(cg_solver* s, const double* Uc, cudaStream_t st) {
-  k_prim<ND><<<grid_blocks(s->N, 256), 256, 0, st>>>(s->dg, Uc, s->W);
-  s->launches++;
+  launch_prim<ND>(s, Uc, st);
   return CG_OK;
 }
 
@@ -660,6 +674,7 @@ static StageArgs base_args(cg_solver* s) {
   StageArgs A;
   memset(&A, 0, sizeof A);
   A.W = s->W;
+  A.Wf = reinterpret_cast<const float*>(s->W);
   A.om = s->om;
   A.omBox = s->omBox;
   A.acc = s->acc;

@@ -153,19 +153,23 @@ __device__ __forceinline__ void cons_to_prim_g(const DevGrid& g, const double* Q
 // Image of a state across an isothermal no-slip wall: velocity negated,
 // pressure kept, temperature reflected about the wall value
 // (T_ghost = 2 T_w - T), density from the equation of state.
-template <int ND>
-__device__ __forceinline__ void wall_image(const DevGrid& g, double* w) {
+template <int ND, typename T = double>
+__device__ __forceinline__ void wall_image(const DevGrid& g, T* w) {
   constexpr int IP = ND + 1;
-  double Tm = g.gm2 * w[IP] / w[0];
-  double Tg = 2.0 * g.twall - Tm;
-  w[0] = g.gm2 * w[IP] / Tg;
+  T Tm = T(g.gm2) * w[IP] / w[0];
+  T Tg = T(2.0) * T(g.twall) - Tm;
+  w[0] = T(g.gm2) * w[IP] / Tg;
 #pragma unroll
   for (int m = 0; m < ND; ++m) w[1 + m] = -w[1 + m];
 }
 
-template <int ND, bool CONS = false>
-__device__ __forceinline__ void load_state(const DevGrid& g, const double* __restrict__ F, int c0,
-                                           int c1, int c2, double* w) {
+// TW: the type the planes are stored in (double; float for the mixed form's
+// primitives); TO: the type the state is returned (and its ghost images
+// formed) in.  The conserved form (CONS) is FP64 only.
+template <int ND, bool CONS = false, typename TW = double, typename TO = double>
+__device__ __forceinline__ void load_state(const DevGrid& g, const TW* __restrict__ F, int c0,
+                                           int c1, int c2, TO* w) {
+  static_assert(!CONS || sizeof(TO) == 8, "conserved ghosts are FP64");
   Src s = resolve(g, c0, c1, c2);
   if (s.face >= 0) {
     if (s.pidx >= 0) {
@@ -174,19 +178,19 @@ __device__ __forceinline__ void load_state(const DevGrid& g, const double* __res
       double wp[ND + 2];
 #pragma unroll
       for (int v = 0; v < ND + 2; ++v) wp[v] = P[(long long)v * fn + s.pidx];
-      if (CONS) prim_to_cons<ND>(g, wp, w);
+      if (CONS) prim_to_cons<ND>(g, wp, reinterpret_cast<double*>(w));
       else {
 #pragma unroll
-        for (int v = 0; v < ND + 2; ++v) w[v] = wp[v];
+        for (int v = 0; v < ND + 2; ++v) w[v] = TO(wp[v]);
       }
     } else {
       const double* st = CONS ? g.inflowQ[s.face >> 1][s.face & 1] : g.inflowW[s.face >> 1][s.face & 1];
 #pragma unroll
-      for (int v = 0; v < ND + 2; ++v) w[v] = st[v];
+      for (int v = 0; v < ND + 2; ++v) w[v] = TO(st[v]);
     }
   } else {
 #pragma unroll
-    for (int v = 0; v < ND + 2; ++v) w[v] = F[(long long)v * g.N + s.idx];
+    for (int v = 0; v < ND + 2; ++v) w[v] = TO(F[(long long)v * g.N + s.idx]);
   }
 #pragma unroll
   for (int d = 0; d < ND; ++d)
@@ -194,11 +198,11 @@ __device__ __forceinline__ void load_state(const DevGrid& g, const double* __res
   for (int k = 0; k < s.walls; ++k) {
     if (CONS) {
       double wp[ND + 2];
-      cons_to_prim_g<ND>(g, w, wp);
+      cons_to_prim_g<ND>(g, reinterpret_cast<const double*>(w), wp);
       wall_image<ND>(g, wp);
-      prim_to_cons<ND>(g, wp, w);
+      prim_to_cons<ND>(g, wp, reinterpret_cast<double*>(w));
     } else {
-      wall_image<ND>(g, w);
+      wall_image<ND, TO>(g, w);
     }
   }
 }

@@ -40,11 +40,14 @@ struct StageArgs {
   const double* hflux;        // per-interface hybrid: LAD flux-form interface fluxes (nv planes on hBox)
   Box hBox;
   double* iface_out;          // diagnostics: interface fluxes [v][line][n+1] (NULL: none)
+  const float* Wf;            // mixed form: the primitives stored in FP32
 };
 
 // ---------------------------------------------------------------- primitives
-template <int ND>
-__global__ void k_prim(DevGrid g, const double* __restrict__ U, double* __restrict__ W) {
+// Primitives recovered in FP64 (p = (gamma-1)(E - rho|u|^2/2)); stored as TW
+// (float for the mixed form's FP32 consumers).
+template <int ND, typename TW = double>
+__global__ void k_prim(DevGrid g, const double* __restrict__ U, TW* __restrict__ W) {
   constexpr int NV = ND + 2;
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < g.N;
        q += (long long)gridDim.x * blockDim.x) {
@@ -53,7 +56,7 @@ __global__ void k_prim(DevGrid g, const double* __restrict__ U, double* __restri
     for (int v = 0; v < NV; ++v) Q[v] = U[v * g.N + q];
     cons_to_prim<ND>(g.gm1, Q, w);
 #pragma unroll
-    for (int v = 0; v < NV; ++v) W[v * g.N + q] = w[v];
+    for (int v = 0; v < NV; ++v) W[v * g.N + q] = TW(w[v]);
   }
 }
 
@@ -64,7 +67,7 @@ __global__ void k_prim(DevGrid g, const double* __restrict__ U, double* __restri
 // T = double: FP64 parity form; T = float: the mixed form's FP32 sensor
 // (FP64 primitives and gradients read, converted once).
 template <int ND, bool CART, bool COMPACT, typename T = double>
-__global__ void k_omega(DevGrid g, const double* __restrict__ W, const double* __restrict__ G0,
+__global__ void k_omega(DevGrid g, const T* __restrict__ W, const double* __restrict__ G0,
                         const double* __restrict__ G1, const double* __restrict__ G2, LineBuf gb0,
                         LineBuf gb1, LineBuf gb2, double* __restrict__ om, Box ob, const int* guard, int want) {
   constexpr int NV = ND + 2, IP = ND + 1;
@@ -92,14 +95,14 @@ __global__ void k_omega(DevGrid g, const double* __restrict__ W, const double* _
 #pragma unroll
       for (int l = 0; l < ND; ++l) {
         const long long st = l == 0 ? 1 : (l == 1 ? (long long)g.n[0] : (long long)g.n[0] * g.n[1]);
-        const double* P = W + IP * g.N + q;
+        const T* P = W + IP * g.N + q;
         const T pm = T(P[-st]), pp = T(P[st]);
         T a = fabs(pp - T(2.0) * p0 + pm) / (pp + T(2.0) * p0 + pm);
         if (a > phi) phi = a;
         if (!COMPACT) {
 #pragma unroll
           for (int k = 0; k < ND; ++k) {
-            const double* V = W + (1 + k) * g.N + q;
+            const T* V = W + (1 + k) * g.N + q;
             du[l][k] = d6<T>(T(V[-3 * st]), T(V[-2 * st]), T(V[-st]), T(V[st]), T(V[2 * st]), T(V[3 * st]));
           }
         } else {
@@ -111,7 +114,7 @@ __global__ void k_omega(DevGrid g, const double* __restrict__ W, const double* _
       }
     } else {
     double w0d[NV];
-    load_state<ND>(g, W, c[0], c[1], c[2], w0d);
+    load_state<ND, false, T, double>(g, W, c[0], c[1], c[2], w0d);
     const T p0 = T(w0d[IP]);
 #pragma unroll
     for (int l = 0; l < ND; ++l) {
@@ -119,8 +122,8 @@ __global__ void k_omega(DevGrid g, const double* __restrict__ W, const double* _
       cm[l] -= 1;
       cp[l] += 1;
       double wm[NV], wp[NV];
-      load_state<ND>(g, W, cm[0], cm[1], cm[2], wm);
-      load_state<ND>(g, W, cp[0], cp[1], cp[2], wp);
+      load_state<ND, false, T, double>(g, W, cm[0], cm[1], cm[2], wm);
+      load_state<ND, false, T, double>(g, W, cp[0], cp[1], cp[2], wp);
       const T pm = T(wm[IP]), pp = T(wp[IP]);
       T a = fabs(pp - T(2.0) * p0 + pm) / (pp + T(2.0) * p0 + pm);
       if (a > phi) phi = a;
@@ -131,8 +134,8 @@ __global__ void k_omega(DevGrid g, const double* __restrict__ W, const double* _
           int a1[3] = {c[0], c[1], c[2]}, a2[3] = {c[0], c[1], c[2]};
           a1[l] -= 3 - t;
           a2[l] += 1 + t;
-          load_state<ND>(g, W, a1[0], a1[1], a1[2], s[t]);
-          load_state<ND>(g, W, a2[0], a2[1], a2[2], s[3 + t]);
+          load_state<ND, false, T, double>(g, W, a1[0], a1[1], a1[2], s[t]);
+          load_state<ND, false, T, double>(g, W, a2[0], a2[1], a2[2], s[3 + t]);
         }
 #pragma unroll
         for (int k = 0; k < ND; ++k)
@@ -235,6 +238,7 @@ template <int ND, int DIR, bool CART, bool COMPACT, typename T, int LW, int UNIT
 __global__ void __launch_bounds__(256, sweep_min_blocks<ND, CART, T>()) k_gbr_sweep(DevGrid g, GbrCfg q, StageArgs A) {
   static_assert((SWEEP_TL * LW) % 256 == 0, "a tile must hold a multiple of the block's threads");
   constexpr int NV = ND + 2, IP = ND + 1;
+  constexpr bool MIX = sizeof(T) == 4;
   constexpr int TL = SWEEP_TL;
   constexpr int RW = TL + 9, RD = TL + 3, RDD = TL + 1, RO = TL + 7;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -283,16 +287,17 @@ __global__ void __launch_bounds__(256, sweep_min_blocks<ND, CART, T>()) k_gbr_sw
     int r = DIR == 0 ? e % RW : e / LW;
     int l = DIR == 0 ? e / RW : e % LW;
     int c[3] = {0, 0, 0};
-    double w[NV];
+    T w[NV];
     if (line_coords(l, c)) {
       c[DIR] = i0 - 5 + r;
-      load_state<ND>(g, A.W, c[0], c[1], c[2], w);
+      if (MIX) load_state<ND, false, float, T>(g, A.Wf, c[0], c[1], c[2], w);
+      else load_state<ND, false, double, T>(g, A.W, c[0], c[1], c[2], w);
     } else {
 #pragma unroll
-      for (int v = 0; v < NV; ++v) w[v] = 1.0;
+      for (int v = 0; v < NV; ++v) w[v] = T(1);
     }
 #pragma unroll
-    for (int v = 0; v < NV; ++v) sW[IX(v, r, l, RW)] = T(w[v]);
+    for (int v = 0; v < NV; ++v) sW[IX(v, r, l, RW)] = w[v];
   }
   // sensor window values
   for (int e = tid; e < RO * LW; e += blockDim.x) {
@@ -414,7 +419,9 @@ __global__ void __launch_bounds__(256, sweep_min_blocks<ND, CART, T>()) k_gbr_sw
     double out[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      double diff = (double)sF[IX(v, a + 1, l, TL)] - (double)sF[IX(v, a, l, TL)];
+      // mixed form: the FP32 fluxes differenced in FP32, accumulated in FP64
+      double diff = MIX ? (double)(sF[IX(v, a + 1, l, TL)] - sF[IX(v, a, l, TL)])
+                        : (double)sF[IX(v, a + 1, l, TL)] - (double)sF[IX(v, a, l, TL)];
       double tot = A.first ? diff : A.acc[v * g.N + qi] + diff;
       if (!A.last) {
         A.acc[v * g.N + qi] = tot;
@@ -435,11 +442,20 @@ __global__ void __launch_bounds__(256, sweep_min_blocks<ND, CART, T>()) k_gbr_sw
       A.Uout[v * g.N + qi] = o;
     }
     if (A.last && A.rk && A.stage == 3) {
-      double ke = out[1] * (out[1] / out[0]);
+      bool bad;
+      if (MIX) {  // sign of rho p / (gamma-1) = rho E - |m|^2 / 2, no division
+        double m2 = out[1] * out[1];
 #pragma unroll
-      for (int m = 1; m < ND; ++m) ke = ke + out[1 + m] * (out[1 + m] / out[0]);
-      double p = g.gm1 * (out[IP] - 0.5 * ke);
-      if (!(out[0] > 0.0) || !(p > 0.0)) {
+        for (int m = 1; m < ND; ++m) m2 = m2 + out[1 + m] * out[1 + m];
+        bad = !(out[0] > 0.0) || !(out[0] * out[IP] - 0.5 * m2 > 0.0);
+      } else {
+        double ke = out[1] * (out[1] / out[0]);
+#pragma unroll
+        for (int m = 1; m < ND; ++m) ke = ke + out[1 + m] * (out[1 + m] / out[0]);
+        double p = g.gm1 * (out[IP] - 0.5 * ke);
+        bad = !(out[0] > 0.0) || !(p > 0.0);
+      }
+      if (bad) {
         atomicOr(A.bad_flag, 1u);
         atomicMin(A.bad_idx, (unsigned long long)qi);
       }

@@ -49,17 +49,14 @@ __device__ __forceinline__ void box_coords(const Box& b, long long e, int* c) {
 
 // the LAD fields at every node of the box fbx (ghosts by the boundary rule)
 template <int ND, typename T = double>
-__global__ void k_lad_fieldbuf(DevGrid g, const double* __restrict__ W, T* __restrict__ f, Box fbx) {
+__global__ void k_lad_fieldbuf(DevGrid g, const T* __restrict__ W, T* __restrict__ f, Box fbx) {
   constexpr int NV = ND + 2, NF = ND + 3;
   long long fs = fbx.size();
   BOX_LOOP(fbx, e) {
     int c[3];
     box_coords(fbx, e, c);
-    double wd[NV];
     T w[NV], fl[NF];
-    load_state<ND>(g, W, c[0], c[1], c[2], wd);
-#pragma unroll
-    for (int v = 0; v < NV; ++v) w[v] = T(wd[v]);
+    load_state<ND, false, T, T>(g, W, c[0], c[1], c[2], w);
     lad_fields<ND, T>(g, w, fl);
 #pragma unroll
     for (int v = 0; v < NF; ++v) f[v * fs + e] = fl[v];
@@ -134,7 +131,7 @@ __global__ void k_lad_grad(DevGrid g, const T* __restrict__ fb, Box fbx, const d
 // beta* = C_beta rho f_sw |sum_l d4(div)_l Delta_{l,beta}^2|,
 // kappa* = C_kappa (rho c / T) |sum_l d4(e)_l Delta_{l,kappa}|.
 template <int ND, bool CART, typename T = double>
-__global__ void k_lad_coef(DevGrid g, const double* __restrict__ W, const T* __restrict__ fb, Box fbx,
+__global__ void k_lad_coef(DevGrid g, const T* __restrict__ W, const T* __restrict__ fb, Box fbx,
                            const T* __restrict__ gr, const T* __restrict__ dv, Box b3, double c_beta_d,
                            double c_kappa_d, T* __restrict__ bt, T* __restrict__ kp, const int* guard, int want) {
   const T c_beta = T(c_beta_d), c_kappa = T(c_kappa_d);
@@ -253,7 +250,7 @@ __global__ void k_gauss(DevGrid g, int l, const T* __restrict__ a, const T* __re
 constexpr int NF_LAD = 0, NF_LAD_VISC = 1, NF_VISC = 2;
 
 template <int ND, bool CART, int MODE, typename T = double>
-__global__ void k_lad_nodeflux(DevGrid g, int l, const double* __restrict__ W, const T* __restrict__ bt,
+__global__ void k_lad_nodeflux(DevGrid g, int l, const T* __restrict__ W, const T* __restrict__ bt,
                                const T* __restrict__ kp, const T* __restrict__ gr, const T* __restrict__ dv, Box b3,
                                T* __restrict__ Fn, Box fb, const int* guard, int want) {
   constexpr int NV = ND + 2, IP = ND + 1;
@@ -263,11 +260,8 @@ __global__ void k_lad_nodeflux(DevGrid g, int l, const double* __restrict__ W, c
   BOX_LOOP(fb, e) {
     int c[3];
     box_coords(fb, e, c);
-    double wd[NV];
-    load_state<ND>(g, W, c[0], c[1], c[2], wd);
     T w[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) w[v] = T(wd[v]);
+    load_state<ND, false, T, T>(g, W, c[0], c[1], c[2], w);
     T xi[3];
     if (CART) {
 #pragma unroll
@@ -442,8 +436,8 @@ __global__ void k_lad_div(DevGrid g, int l, const T* __restrict__ Fn, Box fb, co
 // Hybrid: troubled nodes on tbox ([-1, n]^nd): rho < hyb_rho or p < hyb_p, or
 // (with the sensor) Omega > threshold; counts troubled interior nodes and
 // sets flag[0] = 1 if any (the global decision of Algorithm 3).
-template <int ND>
-__global__ void k_troubled(DevGrid g, const double* __restrict__ W, double hr, double hp, const double* __restrict__ om,
+template <int ND, typename TW = double>
+__global__ void k_troubled(DevGrid g, const TW* __restrict__ W, double hr, double hp, const double* __restrict__ om,
                            Box ob, double thr, unsigned char* __restrict__ tr, Box tb, int* flag,
                            unsigned long long* count) {
   constexpr int NV = ND + 2, IP = ND + 1;
@@ -452,7 +446,7 @@ __global__ void k_troubled(DevGrid g, const double* __restrict__ W, double hr, d
     int c[3];
     box_coords(tb, e, c);
     double w[NV];
-    load_state<ND>(g, W, c[0], c[1], c[2], w);
+    load_state<ND, false, TW, double>(g, W, c[0], c[1], c[2], w);
     bool t = w[0] < hr || w[IP] < hp;
     if (om && om[ob.at(c[0], c[1], c[2])] > thr) t = true;
     if (tr) tr[e] = t ? 1 : 0;

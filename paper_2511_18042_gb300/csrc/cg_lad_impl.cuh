@@ -76,7 +76,7 @@ static int lad_coeffs_run(cg_solver* s, int dkind, cudaStream_t st, const int* g
   T* dv = reinterpret_cast<T*>(L.dv);
   T* bt[2] = {reinterpret_cast<T*>(L.bt[0]), reinterpret_cast<T*>(L.bt[1])};
   T* kp[2] = {reinterpret_cast<T*>(L.kp[0]), reinterpret_cast<T*>(L.kp[1])};
-  k_lad_fieldbuf<ND, T><<<grid_blocks(L.fbx.size(), 256), 256, 0, st>>>(s->dg, s->W, fb, L.fbx);
+  k_lad_fieldbuf<ND, T><<<grid_blocks(L.fbx.size(), 256), 256, 0, st>>>(s->dg, reinterpret_cast<const T*>(s->W), fb, L.fbx);
   s->launches++;
   if (c6) {
     LineJob jobs[3];
@@ -93,12 +93,12 @@ static int lad_coeffs_run(cg_solver* s, int dkind, cudaStream_t st, const int* g
   if (s->dg.curv) {
     if (c6) k_lad_grad<ND, false, true, T><<<gb, 128, 0, st>>>(s->dg, fb, L.fbx, L.df[0], L.df[1], L.df[2], L.dfLB[0], L.dfLB[1], L.dfLB[2], gr, dv, L.b3, guard, want);
     else k_lad_grad<ND, false, false, T><<<gb, 128, 0, st>>>(s->dg, fb, L.fbx, L.df[0], L.df[1], L.df[2], L.dfLB[0], L.dfLB[1], L.dfLB[2], gr, dv, L.b3, guard, want);
-    k_lad_coef<ND, false, T><<<grid_blocks(s->N, 128), 128, 0, st>>>(s->dg, s->W, fb, L.fbx, gr, dv, L.b3, s->p.c_beta,
+    k_lad_coef<ND, false, T><<<grid_blocks(s->N, 128), 128, 0, st>>>(s->dg, reinterpret_cast<const T*>(s->W), fb, L.fbx, gr, dv, L.b3, s->p.c_beta,
                                                                      s->p.c_kappa, bt[0], kp[0], guard, want);
   } else {
     if (c6) k_lad_grad<ND, true, true, T><<<gb, 128, 0, st>>>(s->dg, fb, L.fbx, L.df[0], L.df[1], L.df[2], L.dfLB[0], L.dfLB[1], L.dfLB[2], gr, dv, L.b3, guard, want);
     else k_lad_grad<ND, true, false, T><<<gb, 128, 0, st>>>(s->dg, fb, L.fbx, L.df[0], L.df[1], L.df[2], L.dfLB[0], L.dfLB[1], L.dfLB[2], gr, dv, L.b3, guard, want);
-    k_lad_coef<ND, true, T><<<grid_blocks(s->N, 128), 128, 0, st>>>(s->dg, s->W, fb, L.fbx, gr, dv, L.b3, s->p.c_beta,
+    k_lad_coef<ND, true, T><<<grid_blocks(s->N, 128), 128, 0, st>>>(s->dg, reinterpret_cast<const T*>(s->W), fb, L.fbx, gr, dv, L.b3, s->p.c_beta,
                                                                     s->p.c_kappa, bt[0], kp[0], guard, want);
   }
   s->launches += 2;
@@ -126,9 +126,9 @@ static void lad_nodeflux_m(cg_solver* s, int l, cudaStream_t st, const int* guar
   const T* dv = reinterpret_cast<const T*>(L.dv);
   T* Fn = reinterpret_cast<T*>(L.Fn);
   if (s->dg.curv)
-    k_lad_nodeflux<ND, false, MODE, T><<<gb, 128, 0, st>>>(s->dg, l, s->W, bt, kp, gr, dv, L.b3, Fn, L.fbox[l], guard, want);
+    k_lad_nodeflux<ND, false, MODE, T><<<gb, 128, 0, st>>>(s->dg, l, reinterpret_cast<const T*>(s->W), bt, kp, gr, dv, L.b3, Fn, L.fbox[l], guard, want);
   else
-    k_lad_nodeflux<ND, true, MODE, T><<<gb, 128, 0, st>>>(s->dg, l, s->W, bt, kp, gr, dv, L.b3, Fn, L.fbox[l], guard, want);
+    k_lad_nodeflux<ND, true, MODE, T><<<gb, 128, 0, st>>>(s->dg, l, reinterpret_cast<const T*>(s->W), bt, kp, gr, dv, L.b3, Fn, L.fbox[l], guard, want);
   s->launches++;
 }
 
@@ -148,7 +148,7 @@ static void lad_grad_e4(cg_solver* s, cudaStream_t st, const int* guard, int wan
   T* fb = reinterpret_cast<T*>(L.fb);
   T* gr = reinterpret_cast<T*>(L.gr);
   T* dv = reinterpret_cast<T*>(L.dv);
-  k_lad_fieldbuf<ND, T><<<grid_blocks(L.fbx.size(), 256), 256, 0, st>>>(s->dg, s->W, fb, L.fbx);
+  k_lad_fieldbuf<ND, T><<<grid_blocks(L.fbx.size(), 256), 256, 0, st>>>(s->dg, reinterpret_cast<const T*>(s->W), fb, L.fbx);
   int gb = grid_blocks(L.b3.size(), 128);
   if (s->dg.curv)
     k_lad_grad<ND, false, false, T><<<gb, 128, 0, st>>>(s->dg, fb, L.fbx, L.df[0], L.df[1], L.df[2], L.dfLB[0], L.dfLB[1], L.dfLB[2], gr, dv, L.b3, guard, want);
@@ -221,7 +221,7 @@ static int lad_stage(cg_solver* s, const double* Uc, StageArgs A, cudaStream_t s
 template <int ND, typename T>
 static int lad_stage_t(cg_solver* s, const double* Uc, StageArgs A, cudaStream_t st) {
   int sch = s->p.scheme;
-  k_prim<ND><<<grid_blocks(s->N, 256), 256, 0, st>>>(s->dg, Uc, s->W);
+  k_prim<ND, T><<<grid_blocks(s->N, 256), 256, 0, st>>>(s->dg, Uc, reinterpret_cast<T*>(s->W));
   s->launches++;
   if (sch == CG_LAD_E4 || sch == CG_LAD_C6) return lad_pass<ND, T>(s, sch == CG_LAD_E4 ? 2 : 3, A, st, nullptr, 0);
   LadBuffers& L = s->lad;
@@ -229,7 +229,7 @@ static int lad_stage_t(cg_solver* s, const double* Uc, StageArgs A, cudaStream_t
   CG_CUDA(cudaMemsetAsync(s->hyb_count, 0, sizeof(unsigned long long), st));
   if (s->p.hybrid_mode == CG_HYBRID_GLOBAL) {
     // Algorithm 3: GBR-MEG6 for the whole stage if any node is troubled, else LAD-E4
-    k_troubled<ND><<<grid_blocks(L.tbox.size(), 256), 256, 0, st>>>(s->dg, s->W, s->p.hyb_rho, s->p.hyb_p, nullptr,
+    k_troubled<ND, T><<<grid_blocks(L.tbox.size(), 256), 256, 0, st>>>(s->dg, reinterpret_cast<const T*>(s->W), s->p.hyb_rho, s->p.hyb_p, nullptr,
                                                                    s->omBox, 0.0, nullptr, L.tbox, s->hyb_flag,
                                                                    s->hyb_count);
     s->launches++;
@@ -244,8 +244,8 @@ static int lad_stage_t(cg_solver* s, const double* Uc, StageArgs A, cudaStream_t
   }
   // per interface: GBR-MEG6 where a neighbour node is troubled, LAD-E4 (flux form) elsewhere
   stage_prep_gbr<ND>(s, Uc, false, st, false);
-  k_troubled<ND><<<grid_blocks(L.tbox.size(), 256), 256, 0, st>>>(
-      s->dg, s->W, s->p.hyb_rho, s->p.hyb_p, s->p.hybrid_sensor ? s->om : nullptr, s->omBox, s->p.sensor_thresh, L.tr,
+  k_troubled<ND, T><<<grid_blocks(L.tbox.size(), 256), 256, 0, st>>>(
+      s->dg, reinterpret_cast<const T*>(s->W), s->p.hyb_rho, s->p.hyb_p, s->p.hybrid_sensor ? s->om : nullptr, s->omBox, s->p.sensor_thresh, L.tr,
       L.tbox, s->hyb_flag, s->hyb_count);
   s->launches++;
   int rc = lad_coeffs_run<ND, T>(s, 2, st, nullptr, 0);

@@ -276,8 +276,8 @@ __global__ void __launch_bounds__(1024) k_tri_part(PartJobs J) {
 
 // MIG4 right-hand sides of the primitives along lb.d: 3/4 (W_{i+1} - W_{i-1}),
 // E4 closure rows at both ends of a non-periodic line.
-template <int ND>
-__global__ void k_rhs_mig4(DevGrid g, const double* __restrict__ W, LineBuf lb, double* __restrict__ r) {
+template <int ND, typename TW = double>
+__global__ void k_rhs_mig4(DevGrid g, const TW* __restrict__ W, LineBuf lb, double* __restrict__ r) {
   constexpr int NV = ND + 2;
   LB_LOOP(lb, e) {
     int i = (int)(e / lb.nl);
@@ -288,12 +288,12 @@ __global__ void k_rhs_mig4(DevGrid g, const double* __restrict__ W, LineBuf lb, 
     bool closure = !lb.periodic && (i == 0 || i == lb.m - 1);
     double wp1[NV], wm1[NV];
     int cc[3] = {c[0], c[1], c[2]};
-    cc[lb.d] = pos + 1; load_state<ND>(g, W, cc[0], cc[1], cc[2], wp1);
-    cc[lb.d] = pos - 1; load_state<ND>(g, W, cc[0], cc[1], cc[2], wm1);
+    cc[lb.d] = pos + 1; load_state<ND, false, TW, double>(g, W, cc[0], cc[1], cc[2], wp1);
+    cc[lb.d] = pos - 1; load_state<ND, false, TW, double>(g, W, cc[0], cc[1], cc[2], wm1);
     if (closure) {
       double wp2[NV], wm2[NV];
-      cc[lb.d] = pos + 2; load_state<ND>(g, W, cc[0], cc[1], cc[2], wp2);
-      cc[lb.d] = pos - 2; load_state<ND>(g, W, cc[0], cc[1], cc[2], wm2);
+      cc[lb.d] = pos + 2; load_state<ND, false, TW, double>(g, W, cc[0], cc[1], cc[2], wp2);
+      cc[lb.d] = pos - 2; load_state<ND, false, TW, double>(g, W, cc[0], cc[1], cc[2], wm2);
 #pragma unroll
       for (int v = 0; v < NV; ++v) r[((long long)v * lb.m + i) * lb.nl + L] = d4(wm2[v], wm1[v], wp1[v], wp2[v]);
     } else {

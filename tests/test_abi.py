@@ -48,3 +48,52 @@ def test_defaults_and_argument_errors_without_gpu():
     assert L.cg_grid_create_cartesian(1, n2, h, bad, ctypes.byref(g)) == -1  # half-periodic
     assert L.cg_grid_create_cartesian(1, n2, h, bc, ctypes.byref(g)) == 0
     L.cg_grid_destroy(g)
+
+
+def test_solver_parameter_validation_without_gpu():
+    """cg_solver_create rejects bad parameters on the host, before any device work."""
+    from paper_2511_18042_gb300 import _native as nat
+    L = nat.lib()
+    p = nat.CgParams()
+    L.cg_params_default(ctypes.byref(p))
+    assert p.viscous == 0 and p.pr == 0.72 and p.twall == 1.0 and p.fma_sweep == 0 and p.precision == 0
+    n = (ctypes.c_int64 * 3)(16, 1, 1)
+    h = (ctypes.c_double * 3)(0.1, 1.0, 1.0)
+    g = ctypes.c_void_p()
+    wall = (ctypes.c_int * 6)(4, 1, 0, 0, 0, 0)  # isothermal wall, extrapolation
+    assert L.cg_grid_create_cartesian(1, n, h, wall, ctypes.byref(g)) == 0
+    s = ctypes.c_void_p()
+
+    def create(**kw):
+        q = nat.CgParams()
+        L.cg_params_default(ctypes.byref(q))
+        for k, v in kw.items():
+            setattr(q, k, v)
+        return L.cg_solver_create(g, ctypes.byref(q), ctypes.byref(s))
+
+    assert create(scheme=7) == -1
+    assert create(precision=3) == -1
+    assert create(scheme=3, precision=1) == -5  # no mixed form of LAD-C6
+    assert b"LAD-C6" in L.cg_last_error()
+    assert create(omega_window=5) == -1
+    assert create(cfl=0.0) == -1
+    assert create(viscous=1, re=0.0) == -1
+    assert b"re > 0" in L.cg_last_error()
+    assert create(viscous=1, re=100.0, suth=-1.0) == -1
+    assert create(twall=0.0) == -1  # the grid has an isothermal wall
+    assert b"twall" in L.cg_last_error()
+    L.cg_grid_destroy(g)
+    bad = (ctypes.c_int * 6)(5, 1, 0, 0, 0, 0)  # no boundary type 5
+    assert L.cg_grid_create_cartesian(1, n, h, bad, ctypes.byref(g)) == -1
+
+
+def test_empty_and_oversized_grids_rejected_without_gpu():
+    from paper_2511_18042_gb300 import _native as nat
+    L = nat.lib()
+    h = (ctypes.c_double * 3)(0.1, 0.1, 1.0)
+    per = (ctypes.c_int * 6)(0, 0, 0, 0, 0, 0)
+    g = ctypes.c_void_p()
+    assert L.cg_grid_create_cartesian(2, (ctypes.c_int64 * 3)(0, 16, 1), h, per, ctypes.byref(g)) == -1  # empty
+    assert L.cg_grid_create_cartesian(2, (ctypes.c_int64 * 3)(1 << 25, 16, 1), h, per, ctypes.byref(g)) == -1
+    assert L.cg_grid_create_cartesian(2, (ctypes.c_int64 * 3)(16, 1, 1), h, per, ctypes.byref(g)) == 0  # one periodic line
+    L.cg_grid_destroy(g)

@@ -177,3 +177,33 @@ def test_exact_form_is_bitwise(orc, api, kw):
     tg, _ = s.advance(Ug, nsteps=20)
     assert tg == to
     assert rel_err(Ug, Uo) == 0.0
+
+
+@pytest.mark.parametrize("scheme", ["MEG6", "LAD_E4", "HYBRID"])
+def test_single_periodic_line_2d_equals_1d(api, scheme):
+    """Degenerate direction: a 2D grid one node high (periodic in y) carrying
+    a 1D Sod state gives the 1D right-hand side in its x-momentum, mass and
+    energy, and zero y-momentum."""
+    tube = inputs.shock_tube("sod", 200)
+    n = tube["n"][0]
+    W1 = np.stack([tube["U"][0], tube["U"][1] / tube["U"][0], (1.4 - 1) * (tube["U"][2] - 0.5 * tube["U"][1] ** 2 / tube["U"][0])])
+    W2 = np.zeros((4, 1, n))
+    W2[0, 0], W2[1, 0], W2[3, 0] = W1[0], W1[1], W1[2]
+    p2 = inputs._problem("line", 2, [n, 1], [tube["h"][0], 1.0], [tube["bc"][0], [0, 0]], W2, 1.4)
+    p2["inflow"] = {(0, 0): (1.0, 0.0, 0.0, 1.0)}
+    s1 = api.Solver.from_problem(tube, scheme=scheme)
+    s2 = api.Solver.from_problem(p2, scheme=scheme)
+    R1 = s1.rhs(to_dev(tube["U"])).cpu().numpy()
+    R2 = s2.rhs(to_dev(p2["U"])).cpu().numpy()[:, 0, :]
+    for a, b in ((0, 0), (1, 1), (2, 3)):
+        assert np.abs(R2[b] - R1[a]).max() <= 1e-12 * np.abs(R1[a]).max(), (a, b)
+    assert np.abs(R2[2]).max() <= 1e-12 * np.abs(R1[1]).max()
+
+
+def test_single_periodic_line_rejected_by_compact_schemes(api):
+    tube = inputs.shock_tube("sod", 64)
+    p2 = inputs._problem("line", 2, [64, 1], [tube["h"][0], 1.0], [tube["bc"][0], [0, 0]],
+                         np.ones((4, 1, 64)), 1.4)
+    from paper_2511_18042_gb300._native import CgError
+    with pytest.raises(CgError):
+        api.Solver.from_problem(p2, scheme="MIG4")  # a cyclic compact system needs 3 unknowns
