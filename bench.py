@@ -407,6 +407,24 @@ def run_batched(api, torch, dev, args, count=256, steps_per_solve=200):
     ref_ms = (time.perf_counter() - t0) * 1e3
     del ref_solvers, ref_states
     torch.cuda.empty_cache()
+    # accuracy of the batched mixed form against the FP64 form, member by member
+    sub = probs[:16]
+    mix = [api.Solver.from_problem(p, **_hybrid_kw(p, 1)) for p in sub]
+    fp = [api.Solver.from_problem(p, **_hybrid_kw(p, 0)) for p in sub]
+    Um = [torch.as_tensor(p["U"], device=dev) for p in sub]
+    Uf = [torch.as_tensor(p["U"], device=dev) for p in sub]
+    acc_steps = 20
+    with torch.cuda.stream(stream):
+        b2 = api.Batch(mix, Um)
+        for _ in range(acc_steps):
+            b2.step(stream)
+        stream.synchronize()
+    for s_, U_ in zip(fp, Uf):
+        s_.advance(U_, nsteps=acc_steps)
+    torch.cuda.synchronize()
+    l1 = max(float((a[0] - b[0]).abs().mean() / b[0].abs().mean()) for a, b in zip(Um, Uf))
+    del b2, mix, fp, Um, Uf
+    torch.cuda.empty_cache()
     return {"workload": "%d quadrant Riemann problems, N in [64, 512] log-uniform (seed 0), %d cells; "
                         "per-interface hybrid, FP32 fluxes / FP64 accumulation, one graph replay per RK3 step"
                         % (count, cells),
@@ -415,6 +433,7 @@ def run_batched(api, torch, dev, args, count=256, steps_per_solve=200):
             "autotune": {"streams": width, "tile_shapes": shapes, "seconds": tune_s,
                          "ms_per_rk3_step_default": ms_default},
             "nonphysical_members": bad,
+            "accuracy_vs_fp64": {"members": len(sub), "steps": acc_steps, "density_l1_rel_max": l1},
             "per_case_fp64": {"ms_per_rk3_step": ref_ms, "solves_per_s": count / (steps_per_solve * ref_ms * 1e-3),
                               "how": "each grid stepped alone in FP64 (wall clock, host-issued launches)"}}
 
