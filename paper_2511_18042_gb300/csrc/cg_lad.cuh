@@ -249,17 +249,15 @@ __global__ void k_gauss(DevGrid g, int l, const T* __restrict__ a, const T* __re
 // (MODE 2: no convective flux, beta* = kappa* = 0).
 constexpr int NF_LAD = 0, NF_LAD_VISC = 1, NF_VISC = 2;
 
-template <int ND, bool CART, int MODE, typename T = double>
-__global__ void k_lad_nodeflux(DevGrid g, int l, const T* __restrict__ W, const T* __restrict__ bt,
-                               const T* __restrict__ kp, const T* __restrict__ gr, const T* __restrict__ dv, Box b3,
-                               T* __restrict__ Fn, Box fb, const int* guard, int want) {
+// node flux along l at node c (the body of k_lad_nodeflux; F: nv values)
+template <int ND, bool CART, int MODE, typename T>
+__device__ __forceinline__ void nodeflux_at(const DevGrid& g, int l, const T* __restrict__ W, const T* __restrict__ bt,
+                                            const T* __restrict__ kp, const T* __restrict__ gr,
+                                            const T* __restrict__ dv, const Box& b3, const int* c, T* F) {
   constexpr int NV = ND + 2, IP = ND + 1;
   constexpr bool CONV = MODE != NF_VISC, ART = MODE != NF_VISC, PHYS = MODE != NF_LAD;
-  if (guard && *guard != want) return;
-  long long fs = fb.size(), bs = b3.size();
-  BOX_LOOP(fb, e) {
-    int c[3];
-    box_coords(fb, e, c);
+  const long long bs = b3.size();
+  {
     T w[NV];
     load_state<ND, false, T, T>(g, W, c[0], c[1], c[2], w);
     T xi[3];
@@ -307,10 +305,10 @@ __global__ void k_lad_nodeflux(DevGrid g, int l, const T* __restrict__ W, const 
         fe = first ? xi[m] * phi : fe + xi[m] * phi;
         first = false;
       }
-      Fn[0 * fs + e] = fc[0];
+      F[0] = fc[0];
 #pragma unroll
-      for (int m = 0; m < ND; ++m) Fn[(1 + m) * fs + e] = (CART && m != l) ? fc[1 + m] : fc[1 + m] - xi[m] * tau;
-      Fn[IP * fs + e] = fc[IP] - fe;
+      for (int m = 0; m < ND; ++m) F[1 + m] = (CART && m != l) ? fc[1 + m] : fc[1 + m] - xi[m] * tau;
+      F[IP] = fc[IP] - fe;
     } else {
       T Tt = T(g.gm2) * p / rho;
       T S = T(g.suth);
@@ -340,7 +338,7 @@ __global__ void k_lad_nodeflux(DevGrid g, int l, const T* __restrict__ W, const 
         fe = first ? xi[m] * phi : fe + xi[m] * phi;
         first = false;
       }
-      Fn[0 * fs + e] = fc[0];
+      F[0] = fc[0];
 #pragma unroll
       for (int a = 0; a < ND; ++a) {
         T fv;
@@ -350,10 +348,27 @@ __global__ void k_lad_nodeflux(DevGrid g, int l, const T* __restrict__ W, const 
 #pragma unroll
           for (int m = 1; m < ND; ++m) fv = fv + xi[m] * tau[m][a];
         }
-        Fn[(1 + a) * fs + e] = fc[1 + a] + (-fv);
+        F[1 + a] = fc[1 + a] + (-fv);
       }
-      Fn[IP * fs + e] = fc[IP] + (-fe);
+      F[IP] = fc[IP] + (-fe);
     }
+  }
+}
+
+template <int ND, bool CART, int MODE, typename T = double>
+__global__ void k_lad_nodeflux(DevGrid g, int l, const T* __restrict__ W, const T* __restrict__ bt,
+                               const T* __restrict__ kp, const T* __restrict__ gr, const T* __restrict__ dv, Box b3,
+                               T* __restrict__ Fn, Box fb, const int* guard, int want) {
+  constexpr int NV = ND + 2;
+  if (guard && *guard != want) return;
+  long long fs = fb.size();
+  BOX_LOOP(fb, e) {
+    int c[3];
+    box_coords(fb, e, c);
+    T F[NV];
+    nodeflux_at<ND, CART, MODE, T>(g, l, W, bt, kp, gr, dv, b3, c, F);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Fn[v * fs + e] = F[v];
   }
 }
 
@@ -393,11 +408,20 @@ __device__ __forceinline__ void lad_epilogue(const DevGrid& g, const StageArgs& 
     A.Uout[v * g.N + qi] = o;
   }
   if (A.last && A.rk && A.stage == 3) {
-    double ke = out[1] * (out[1] / out[0]);
+    bool bad;
+    if (FUSED) {  // sign of rho p / (gamma-1) = rho E - |m|^2 / 2, no division
+      double m2 = out[1] * out[1];
 #pragma unroll
-    for (int m = 1; m < ND; ++m) ke = ke + out[1 + m] * (out[1 + m] / out[0]);
-    double p = g.gm1 * (out[IP] - 0.5 * ke);
-    if (!(out[0] > 0.0) || !(p > 0.0)) {
+      for (int m = 1; m < ND; ++m) m2 = __fma_rn(out[1 + m], out[1 + m], m2);
+      bad = !(out[0] > 0.0) || !(__fma_rn(out[0], out[IP], -0.5 * m2) > 0.0);
+    } else {
+      double ke = out[1] * (out[1] / out[0]);
+#pragma unroll
+      for (int m = 1; m < ND; ++m) ke = ke + out[1 + m] * (out[1 + m] / out[0]);
+      double p = g.gm1 * (out[IP] - 0.5 * ke);
+      bad = !(out[0] > 0.0) || !(p > 0.0);
+    }
+    if (bad) {
       atomicOr(A.bad_flag, 1u);
       atomicMin(A.bad_idx, (unsigned long long)qi);
     }
@@ -430,6 +454,60 @@ __global__ void k_lad_div(DevGrid g, int l, const T* __restrict__ Fn, Box fb, co
       }
     }
     lad_epilogue<ND, sizeof(T) == 4>(g, A, q, c, Dv);
+  }
+}
+
+// Node fluxes and their E4 divergence along l in one pass: a block computes
+// the fluxes of FD_TL + 4 consecutive nodes (the tile and the stencil's two on
+// each side) on FD_LW lines into shared memory, then differences them and runs
+// the stage epilogue (as k_lad_node_flux + k_lad_div, without the global
+// round trip of the fluxes).  Lines are blockIdx.x, tiles along l blockIdx.y.
+constexpr int FD_TL = 64, FD_LW = 4;
+
+template <int ND, bool CART, int MODE, typename T>
+__global__ void __launch_bounds__(256) k_lad_fluxdiv(DevGrid g, int l, const T* __restrict__ W,
+                                                     const T* __restrict__ bt, const T* __restrict__ kp,
+                                                     const T* __restrict__ gr, const T* __restrict__ dv, Box b3,
+                                                     StageArgs A, const int* guard, int want) {
+  constexpr int NV = ND + 2, TL = FD_TL, LW = FD_LW, RW = TL + 4;
+  __shared__ T sF[NV][RW * LW];
+  if (guard && *guard != want) return;
+  const int n = g.n[l];
+  const int i0 = blockIdx.y * TL;
+  const int o1 = l == 0 ? 1 : 0, o2 = l == 2 ? 1 : 2;  // the other two directions
+  const long long n1 = g.n[o1], lines = g.N / n;
+  auto line_coords = [&](int ln, int* c) -> bool {
+    long long L = (long long)blockIdx.x * LW + ln;
+    if (L >= lines) return false;
+    c[o1] = (int)(L % n1);
+    c[o2] = (int)(L / n1);
+    return true;
+  };
+  // element e of a tile: along l fastest when l = 0 (contiguous in x), else lines fastest
+  for (int e = threadIdx.x; e < RW * LW; e += blockDim.x) {
+    int r = l == 0 ? e % RW : e / LW, ln = l == 0 ? e / RW : e % LW;
+    int c[3] = {0, 0, 0};
+    int x = i0 - 2 + r;
+    if (!line_coords(ln, c) || x > n + 1) continue;
+    c[l] = x;
+    T F[NV];
+    nodeflux_at<ND, CART, MODE, T>(g, l, W, bt, kp, gr, dv, b3, c, F);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) sF[v][r * LW + ln] = F[v];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < TL * LW; e += blockDim.x) {
+    int a = l == 0 ? e % TL : e / LW, ln = l == 0 ? e / TL : e % LW;
+    int c[3] = {0, 0, 0};
+    int x = i0 + a;
+    if (!line_coords(ln, c) || x >= n) continue;
+    c[l] = x;
+    double Dv[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+      Dv[v] = (double)d4(sF[v][a * LW + ln], sF[v][(a + 1) * LW + ln], sF[v][(a + 3) * LW + ln],
+                         sF[v][(a + 4) * LW + ln]);
+    lad_epilogue<ND, sizeof(T) == 4>(g, A, lin(g, c[0], c[1], c[2]), c, Dv);
   }
 }
 
