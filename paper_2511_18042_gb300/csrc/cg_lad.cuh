@@ -457,60 +457,6 @@ __global__ void k_lad_div(DevGrid g, int l, const T* __restrict__ Fn, Box fb, co
   }
 }
 
-// Node fluxes and their E4 divergence along l in one pass: a block computes
-// the fluxes of FD_TL + 4 consecutive nodes (the tile and the stencil's two on
-// each side) on FD_LW lines into shared memory, then differences them and runs
-// the stage epilogue (as k_lad_node_flux + k_lad_div, without the global
-// round trip of the fluxes).  Lines are blockIdx.x, tiles along l blockIdx.y.
-constexpr int FD_TL = 64, FD_LW = 4;
-
-template <int ND, bool CART, int MODE, typename T>
-__global__ void __launch_bounds__(256) k_lad_fluxdiv(DevGrid g, int l, const T* __restrict__ W,
-                                                     const T* __restrict__ bt, const T* __restrict__ kp,
-                                                     const T* __restrict__ gr, const T* __restrict__ dv, Box b3,
-                                                     StageArgs A, const int* guard, int want) {
-  constexpr int NV = ND + 2, TL = FD_TL, LW = FD_LW, RW = TL + 4;
-  __shared__ T sF[NV][RW * LW];
-  if (guard && *guard != want) return;
-  const int n = g.n[l];
-  const int i0 = blockIdx.y * TL;
-  const int o1 = l == 0 ? 1 : 0, o2 = l == 2 ? 1 : 2;  // the other two directions
-  const long long n1 = g.n[o1], lines = g.N / n;
-  auto line_coords = [&](int ln, int* c) -> bool {
-    long long L = (long long)blockIdx.x * LW + ln;
-    if (L >= lines) return false;
-    c[o1] = (int)(L % n1);
-    c[o2] = (int)(L / n1);
-    return true;
-  };
-  // element e of a tile: along l fastest when l = 0 (contiguous in x), else lines fastest
-  for (int e = threadIdx.x; e < RW * LW; e += blockDim.x) {
-    int r = l == 0 ? e % RW : e / LW, ln = l == 0 ? e / RW : e % LW;
-    int c[3] = {0, 0, 0};
-    int x = i0 - 2 + r;
-    if (!line_coords(ln, c) || x > n + 1) continue;
-    c[l] = x;
-    T F[NV];
-    nodeflux_at<ND, CART, MODE, T>(g, l, W, bt, kp, gr, dv, b3, c, F);
-#pragma unroll
-    for (int v = 0; v < NV; ++v) sF[v][r * LW + ln] = F[v];
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < TL * LW; e += blockDim.x) {
-    int a = l == 0 ? e % TL : e / LW, ln = l == 0 ? e / TL : e % LW;
-    int c[3] = {0, 0, 0};
-    int x = i0 + a;
-    if (!line_coords(ln, c) || x >= n) continue;
-    c[l] = x;
-    double Dv[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v)
-      Dv[v] = (double)d4(sF[v][a * LW + ln], sF[v][(a + 1) * LW + ln], sF[v][(a + 3) * LW + ln],
-                         sF[v][(a + 4) * LW + ln]);
-    lad_epilogue<ND, sizeof(T) == 4>(g, A, lin(g, c[0], c[1], c[2]), c, Dv);
-  }
-}
-
 // Hybrid: troubled nodes on tbox ([-1, n]^nd): rho < hyb_rho or p < hyb_p, or
 // (with the sensor) Omega > threshold; counts troubled interior nodes and
 // sets flag[0] = 1 if any (the global decision of Algorithm 3).

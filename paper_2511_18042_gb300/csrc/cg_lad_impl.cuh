@@ -141,30 +141,6 @@ static void lad_nodeflux(cg_solver* s, int l, cudaStream_t st, const int* guard,
   else lad_nodeflux_m<ND, NF_LAD, T>(s, l, st, guard, want);
 }
 
-// Node fluxes and E4 divergence along l in one launch (k_lad_fluxdiv), mode as
-// lad_nodeflux, epilogue flags in A.
-template <int ND, int MODE, typename T>
-static void lad_fluxdiv_m(cg_solver* s, int l, const StageArgs& A, cudaStream_t st, const int* guard, int want) {
-  LadBuffers& L = s->lad;
-  long long lines = s->N / s->dg.n[l];
-  dim3 grid((unsigned)((lines + FD_LW - 1) / FD_LW), (unsigned)((s->dg.n[l] + FD_TL - 1) / FD_TL));
-  const T* W = reinterpret_cast<const T*>(s->W);
-  const T* bt = reinterpret_cast<const T*>(L.bt[0]);
-  const T* kp = reinterpret_cast<const T*>(L.kp[0]);
-  const T* gr = reinterpret_cast<const T*>(L.gr);
-  const T* dv = reinterpret_cast<const T*>(L.dv);
-  if (s->dg.curv) k_lad_fluxdiv<ND, false, MODE, T><<<grid, 256, 0, st>>>(s->dg, l, W, bt, kp, gr, dv, L.b3, A, guard, want);
-  else k_lad_fluxdiv<ND, true, MODE, T><<<grid, 256, 0, st>>>(s->dg, l, W, bt, kp, gr, dv, L.b3, A, guard, want);
-  s->launches++;
-}
-
-template <int ND, typename T>
-static void lad_fluxdiv(cg_solver* s, int l, const StageArgs& A, cudaStream_t st, const int* guard, int want, int mode) {
-  if (mode == NF_VISC) lad_fluxdiv_m<ND, NF_VISC, T>(s, l, A, st, guard, want);
-  else if (mode == NF_LAD_VISC) lad_fluxdiv_m<ND, NF_LAD_VISC, T>(s, l, A, st, guard, want);
-  else lad_fluxdiv_m<ND, NF_LAD, T>(s, l, A, st, guard, want);
-}
-
 // E4 gradients of the LAD fields of the primitives in s->W (no coefficients)
 template <int ND, typename T>
 static void lad_grad_e4(cg_solver* s, cudaStream_t st, const int* guard, int want) {
@@ -190,12 +166,14 @@ static void lad_grad_e4(cg_solver* s, cudaStream_t st, const int* guard, int wan
 template <int ND, typename T>
 static void visc_pass(cg_solver* s, StageArgs A, cudaStream_t st, bool have_grad, const int* guard, int want) {
   LadBuffers& L = s->lad;
-  (void)L;
   if (!have_grad) lad_grad_e4<ND, T>(s, st, guard, want);
   for (int l = 0; l < ND; ++l) {
+    lad_nodeflux<ND, T>(s, l, st, guard, want, NF_VISC);
     A.first = l == 0;
     A.last = false;
-    lad_fluxdiv<ND, T>(s, l, A, st, guard, want, NF_VISC);
+    k_lad_div<ND, T><<<grid_blocks(s->N, 256), 256, 0, st>>>(s->dg, l, reinterpret_cast<const T*>(L.Fn), L.fbox[l],
+                                                            nullptr, L.DLB[l], A, guard, want);
+    s->launches++;
   }
 }
 
@@ -214,10 +192,6 @@ static int lad_pass(cg_solver* s, int dkind, StageArgs A, cudaStream_t st, const
   for (int l = 0; l < ND; ++l) {
     A.first = l == 0;
     A.last = l == ND - 1;
-    if (dkind == 2) {  // E4: fluxes and divergence in one pass
-      lad_fluxdiv<ND, T>(s, l, A, st, guard, want, s->p.viscous ? NF_LAD_VISC : NF_LAD);
-      continue;
-    }
     lad_nodeflux<ND, T>(s, l, st, guard, want, s->p.viscous ? NF_LAD_VISC : NF_LAD);
     const double* D = nullptr;
     LineBuf DL = L.DLB[l];
