@@ -175,7 +175,25 @@ struct DevLine {
   double* buf = nullptr;
   PartCoef pc{};        // pc.P >= 4: the partitioned solver is used
   double* pbuf = nullptr;
+  // FP32 mirrors of the same factors (the mixed form's gradient solves)
+  LineCoefT<float> lcf{};
+  float* fbuf = nullptr;
+  PartCoefT<float> pcf{};
+  float* fpbuf = nullptr;
 };
+
+template <typename T>
+static const LineCoefT<T>& line_coef(const DevLine& L);
+template <>
+const LineCoefT<double>& line_coef<double>(const DevLine& L) { return L.lc; }
+template <>
+const LineCoefT<float>& line_coef<float>(const DevLine& L) { return L.lcf; }
+template <typename T>
+static const PartCoefT<T>& part_coef(const DevLine& L);
+template <>
+const PartCoefT<double>& part_coef<double>(const DevLine& L) { return L.pc; }
+template <>
+const PartCoefT<float>& part_coef<float>(const DevLine& L) { return L.pcf; }
 
 }  // namespace
 
@@ -397,6 +415,23 @@ static int upload_line(DevLine& L, int m, double a, bool cyclic, int lo, long lo
     L.pc.q = hp.q;
     L.pc.P = hp.P;
     L.pc.periodic = cyclic ? 1 : 0;
+    std::vector<float> pf(pk.begin(), pk.end());
+    rc = dalloc(&L.fpbuf, cnt);
+    if (rc) return rc;
+    CG_CUDA(cudaMemcpy(L.fpbuf, pf.data(), cnt * sizeof(float), cudaMemcpyHostToDevice));
+    L.pcf = PartCoefT<float>{L.fpbuf, L.fpbuf + m, L.fpbuf + 2 * (size_t)m, L.fpbuf + 3 * (size_t)m,
+                             L.fpbuf + 4 * (size_t)m, nullptr, L.fpbuf + 5 * (size_t)m, (float)a, (float)h.gam,
+                             (float)h.fden, m, hp.q, hp.P, cyclic ? 1 : 0};
+  }
+  // FP32 mirror of the Thomas factors (and of z, which the partitioned form shares)
+  {
+    std::vector<float> af(all.begin(), all.end());
+    rc = dalloc(&L.fbuf, af.size());
+    if (rc) return rc;
+    CG_CUDA(cudaMemcpy(L.fbuf, af.data(), af.size() * sizeof(float), cudaMemcpyHostToDevice));
+    L.lcf = LineCoefT<float>{L.fbuf, L.fbuf + m, L.fbuf + 2 * (size_t)m, (float)a, (float)h.gam, (float)h.fden,
+                             m, lo, cyclic ? 1 : 0};
+    if (L.pcf.P) L.pcf.z = cyclic ? L.lcf.z : nullptr;
   }
   return CG_OK;
 }
@@ -539,8 +574,9 @@ static void launch_omega(cg_solver* s, cudaStream_t st, const int* guard, int wa
   long long tot = s->omBox.size();
   if (s->p.precision == CG_MIXED)
     k_omega<ND, CART, COMPACT, float><<<grid_blocks(tot, 128), 128, 0, st>>>(
-        s->dg, reinterpret_cast<const float*>(s->W), s->G[0], s->G[1], s->G[2], s->gdLB[0], s->gdLB[1], s->gdLB[2],
-        s->om, s->omBox, guard, want);
+        s->dg, reinterpret_cast<const float*>(s->W), reinterpret_cast<const float*>(s->G[0]),
+        reinterpret_cast<const float*>(s->G[1]), reinterpret_cast<const float*>(s->G[2]), s->gdLB[0], s->gdLB[1],
+        s->gdLB[2], s->om, s->omBox, guard, want);
   else
     k_omega<ND, CART, COMPACT, double><<<grid_blocks(tot, 128), 128, 0, st>>>(
         s->dg, s->W, s->G[0], s->G[1], s->G[2], s->gdLB[0], s->gdLB[1], s->gdLB[2], s->om, s->omBox, guard, want);
@@ -581,44 +617,46 @@ static int sweep_dir(cg_solver* s, int dir, const StageArgs& A, cudaStream_t st)
 // per column in 32-thread blocks, so the long recurrences spread over as many
 // SMs as possible.  Few columns (every system partitioned at set-up): the
 // partitioned solver, 32 columns times the chunks per block.
+template <typename T = double>
 struct LineJob {
   const DevLine* L;
-  double* x;
+  T* x;
   long long nl;
   int ncomp;
 };
 
-static void launch_lines(const LineJob* jobs, int n, cudaStream_t st) {
+template <typename T>
+static void launch_lines(const LineJob<T>* jobs, int n, cudaStream_t st) {
   bool part = true;
   for (int j = 0; j < n; ++j) part = part && jobs[j].L->pc.P >= 4;
   if (part) {
-    PartJobs J;
+    PartJobsT<T> J;
     J.njobs = n;
     J.start[0] = 0;
     int Pmax = 1;
     for (int j = 0; j < n; ++j) {
-      J.pc[j] = jobs[j].L->pc;
+      J.pc[j] = part_coef<T>(*jobs[j].L);
       J.x[j] = jobs[j].x;
       J.nl[j] = jobs[j].nl;
       J.ncomp[j] = jobs[j].ncomp;
       J.start[j + 1] = J.start[j] + (jobs[j].nl * jobs[j].ncomp + 31) / 32 * 32;
       Pmax = std::max(Pmax, J.pc[j].P);
     }
-    k_tri_part<<<(unsigned)(J.start[n] / 32), dim3(32, Pmax), 0, st>>>(J);
+    k_tri_part<T><<<(unsigned)(J.start[n] / 32), dim3(32, Pmax), 0, st>>>(J);
     return;
   }
-  ThomasJobs J;
+  ThomasJobsT<T> J;
   J.njobs = n;
   J.start[0] = 0;
   for (int j = 0; j < n; ++j) {
-    J.lc[j] = jobs[j].L->lc;
+    J.lc[j] = line_coef<T>(*jobs[j].L);
     J.x[j] = jobs[j].x;
     J.nl[j] = jobs[j].nl;
     J.ncomp[j] = jobs[j].ncomp;
     J.start[j + 1] = J.start[j] + jobs[j].nl * jobs[j].ncomp;
   }
   long long cols = J.start[n];
-  k_thomas_jobs<<<(unsigned)((cols + 31) / 32), 32, 0, st>>>(J);
+  k_thomas_jobs<T><<<(unsigned)((cols + 31) / 32), 32, 0, st>>>(J);
 }
 
 // Primitives of Uc into W: FP64 storage, or FP32 for the mixed form (the
@@ -640,18 +678,28 @@ static int stage_prep_gbr(cg_solver* s, const double* Uc, bool compact, cudaStre
     launch_prim<ND>(s, Uc, st);
   }
   if (compact) {
-    LineJob jobs[3];
-    for (int d = 0; d < ND; ++d) {
-      const LineBuf& lb = s->gdLB[d];
-      if (s->p.precision == CG_MIXED)
-        k_rhs_mig4<ND, float><<<grid_blocks((long long)lb.m * lb.nl, 256), 256, 0, st>>>(
-            s->dg, reinterpret_cast<const float*>(s->W), lb, s->G[d]);
-      else
-        k_rhs_mig4<ND, double><<<grid_blocks((long long)lb.m * lb.nl, 256), 256, 0, st>>>(s->dg, s->W, lb, s->G[d]);
-      s->launches++;
-      jobs[d] = LineJob{&s->mig4[d], s->G[d], lb.nl, ND + 2};
+    if (s->p.precision == CG_MIXED) {  // the mixed form's gradients: FP32 right-hand sides and solves
+      LineJob<float> jobs[3];
+      for (int d = 0; d < ND; ++d) {
+        const LineBuf& lb = s->gdLB[d];
+        float* G = reinterpret_cast<float*>(s->G[d]);
+        k_rhs_mig4<ND, float, float><<<grid_blocks((long long)lb.m * lb.nl, 256), 256, 0, st>>>(
+            s->dg, reinterpret_cast<const float*>(s->W), lb, G);
+        s->launches++;
+        jobs[d] = LineJob<float>{&s->mig4[d], G, lb.nl, ND + 2};
+      }
+      launch_lines(jobs, ND, st);
+    } else {
+      LineJob<double> jobs[3];
+      for (int d = 0; d < ND; ++d) {
+        const LineBuf& lb = s->gdLB[d];
+        k_rhs_mig4<ND, double, double><<<grid_blocks((long long)lb.m * lb.nl, 256), 256, 0, st>>>(s->dg, s->W, lb,
+                                                                                                 s->G[d]);
+        s->launches++;
+        jobs[d] = LineJob<double>{&s->mig4[d], s->G[d], lb.nl, ND + 2};
+      }
+      launch_lines(jobs, ND, st);
     }
-    launch_lines(jobs, ND, st);
     s->launches++;
   }
   if (s->dg.curv) {
@@ -691,6 +739,7 @@ static int gbr_sweeps(cg_solver* s, bool compact, StageArgs A, cudaStream_t st, 
     A.first = fresh && d == 0;
     A.last = d == ND - 1;
     A.Gd = s->G[d];
+    A.Gdf = reinterpret_cast<const float*>(s->G[d]);
     A.gdLB = s->gdLB[d];
     A.iface_out = (s->iface_out && s->iface_dir == d) ? s->iface_out : nullptr;
     int rc;
@@ -984,6 +1033,8 @@ CG_API void cg_solver_destroy(cg_solver* s) {
     for (DevLine* l : ls) {
       if (l->buf) cudaFree(l->buf);
       if (l->pbuf) cudaFree(l->pbuf);
+      if (l->fbuf) cudaFree(l->fbuf);
+      if (l->fpbuf) cudaFree(l->fpbuf);
     }
   }
   lad_free(s->lad);

@@ -271,6 +271,10 @@ __device__ __forceinline__ void cons_to_prim(double gm1, const double* Q, double
   W[ND + 1] = gm1 * (Q[ND + 1] - 0.5 * ke);
 }
 
+// fused multiply-add in the arithmetic type
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
 // ---------------------------------------------------------------- stencils
 // T = double: the FP64 parity form; T = float: the mixed form's flux arithmetic.
 // explicit sixth-order central first derivative (MEG6 gradients)

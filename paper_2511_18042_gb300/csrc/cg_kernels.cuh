@@ -41,6 +41,7 @@ struct StageArgs {
   Box hBox;
   double* iface_out;          // diagnostics: interface fluxes [v][line][n+1] (NULL: none)
   const float* Wf;            // mixed form: the primitives stored in FP32
+  const float* Gdf;           // mixed form: the compact gradients in FP32
 };
 
 // ---------------------------------------------------------------- primitives
@@ -67,8 +68,8 @@ __global__ void k_prim(DevGrid g, const double* __restrict__ U, TW* __restrict__
 // T = double: FP64 parity form; T = float: the mixed form's FP32 sensor
 // (FP64 primitives and gradients read, converted once).
 template <int ND, bool CART, bool COMPACT, typename T = double>
-__global__ void k_omega(DevGrid g, const T* __restrict__ W, const double* __restrict__ G0,
-                        const double* __restrict__ G1, const double* __restrict__ G2, LineBuf gb0,
+__global__ void k_omega(DevGrid g, const T* __restrict__ W, const T* __restrict__ G0,
+                        const T* __restrict__ G1, const T* __restrict__ G2, LineBuf gb0,
                         LineBuf gb1, LineBuf gb2, double* __restrict__ om, Box ob, const int* guard, int want) {
   constexpr int NV = ND + 2, IP = ND + 1;
   if (guard && *guard != want) return;
@@ -106,7 +107,7 @@ __global__ void k_omega(DevGrid g, const T* __restrict__ W, const double* __rest
             du[l][k] = d6<T>(T(V[-3 * st]), T(V[-2 * st]), T(V[-st]), T(V[st]), T(V[2 * st]), T(V[3 * st]));
           }
         } else {
-          const double* G = l == 0 ? G0 : (l == 1 ? G1 : G2);
+          const T* G = l == 0 ? G0 : (l == 1 ? G1 : G2);
           const LineBuf& gb = l == 0 ? gb0 : (l == 1 ? gb1 : gb2);
 #pragma unroll
           for (int k = 0; k < ND; ++k) du[l][k] = T(G[gb.at(1 + k, c[l], c)]);
@@ -142,7 +143,7 @@ __global__ void k_omega(DevGrid g, const T* __restrict__ W, const double* __rest
           du[l][k] = d6<T>(T(s[0][1 + k]), T(s[1][1 + k]), T(s[2][1 + k]), T(s[3][1 + k]), T(s[4][1 + k]),
                            T(s[5][1 + k]));
       } else {
-        const double* G = l == 0 ? G0 : (l == 1 ? G1 : G2);
+        const T* G = l == 0 ? G0 : (l == 1 ? G1 : G2);
         const LineBuf& gb = l == 0 ? gb0 : (l == 1 ? gb1 : gb2);
 #pragma unroll
         for (int k = 0; k < ND; ++k) du[l][k] = T(G[gb.at(1 + k, c[l], c)]);
@@ -200,17 +201,19 @@ __global__ void k_omega(DevGrid g, const T* __restrict__ W, const double* __rest
 // cyclic on [0, n-1] (Sherman-Morrison with the correction vector z[]) and
 // the ghost positions copy the wrapped values.  Lines exist for every
 // position of the other directions in [-4, n+3].
-struct LineCoef {
-  const double* cp;   // Thomas pivots of the line system
-  const double* den;  // reciprocals of the elimination pivots, 1/den_i
-  const double* z;    // cyclic: solution of the correction system
-  double a;           // off-diagonal
-  double gam;         // cyclic: -1
-  double fden;        // cyclic: 1 + z[0] + a z[m-1] / gam
-  int m;              // unknowns
-  int lo;             // first position of the system (non-periodic)
+template <typename T>
+struct LineCoefT {
+  const T* cp;   // Thomas pivots of the line system
+  const T* den;  // reciprocals of the elimination pivots, 1/den_i
+  const T* z;    // cyclic: solution of the correction system
+  T a;           // off-diagonal
+  T gam;         // cyclic: -1
+  T fden;        // cyclic: 1 + z[0] + a z[m-1] / gam
+  int m;         // unknowns
+  int lo;        // first position of the system (non-periodic)
   int periodic;
 };
+using LineCoef = LineCoefT<double>;
 
 // ---------------------------------------------------------------- C-GBR sweep
 constexpr int SWEEP_TL = 64;
@@ -327,7 +330,8 @@ __global__ void __launch_bounds__(256, sweep_min_blocks<ND, CART, T>()) k_gbr_sw
       int x = i0 - 2 + r;
       bool ok = line_coords(l, c) && x <= n + 5;
 #pragma unroll
-      for (int v = 0; v < NV; ++v) sD[IX(v, r, l, RD)] = ok ? T(A.Gd[A.gdLB.at(v, x, c)]) : T(0);
+      for (int v = 0; v < NV; ++v)
+        sD[IX(v, r, l, RD)] = ok ? (MIX ? T(A.Gdf[A.gdLB.at(v, x, c)]) : T(A.Gd[A.gdLB.at(v, x, c)])) : T(0);
     }
   }
   __syncthreads();

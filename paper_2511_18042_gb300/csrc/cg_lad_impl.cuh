@@ -79,12 +79,12 @@ static int lad_coeffs_run(cg_solver* s, int dkind, cudaStream_t st, const int* g
   k_lad_fieldbuf<ND, T><<<grid_blocks(L.fbx.size(), 256), 256, 0, st>>>(s->dg, reinterpret_cast<const T*>(s->W), fb, L.fbx);
   s->launches++;
   if (c6) {
-    LineJob jobs[3];
+    LineJob<double> jobs[3];
     for (int l = 0; l < ND; ++l) {
       const LineBuf& lb = L.dfLB[l];
       k_rhs_c6<<<grid_blocks((long long)lb.m * lb.nl, 256), 256, 0, st>>>(reinterpret_cast<double*>(fb), L.fbx, ND + 3, lb, L.df[l]);
       s->launches++;
-      jobs[l] = LineJob{&s->c6grad[l], L.df[l], lb.nl, ND + 3};
+      jobs[l] = LineJob<double>{&s->c6grad[l], L.df[l], lb.nl, ND + 3};
     }
     launch_lines(jobs, ND, st);
     s->launches++;
@@ -197,7 +197,7 @@ static int lad_pass(cg_solver* s, int dkind, StageArgs A, cudaStream_t st, const
     LineBuf DL = L.DLB[l];
     if (dkind == 3) {
       k_rhs_c6<<<grid_blocks((long long)DL.m * DL.nl, 256), 256, 0, st>>>(reinterpret_cast<const double*>(L.Fn), L.fbox[l], ND + 2, DL, L.D);
-      LineJob job{&s->c6flux[l], L.D, DL.nl, ND + 2};
+      LineJob<double> job{&s->c6flux[l], L.D, DL.nl, ND + 2};
       launch_lines(&job, 1, st);
       s->launches += 2;
       D = L.D;
@@ -292,7 +292,7 @@ static int lad_filter(cg_solver* s, double* U, cudaStream_t st) {
     const LineBuf& lb = s->lad.filtLB[l];
     k_rhs_filter<ND><<<grid_blocks((long long)lb.m * lb.nl, 256), 256, 0, st>>>(s->dg, U, lb, b[0], b[1], b[2], b[3],
                                                                               b[4], s->lad.lines);
-    LineJob job{&s->filt[l], s->lad.lines, lb.nl, ND + 2};
+    LineJob<double> job{&s->filt[l], s->lad.lines, lb.nl, ND + 2};
     launch_lines(&job, 1, st);
     k_filter_store<ND><<<grid_blocks(s->N, 256), 256, 0, st>>>(s->dg, s->lad.lines, lb, U);
     s->launches += 3;

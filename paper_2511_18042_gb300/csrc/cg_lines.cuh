@@ -1,7 +1,7 @@
 // Batched tridiagonal line solves of the compact schemes and the implicit
 // filter.  A parallel kernel builds every right-hand side into a line-major
 // buffer ([component][row][line], lines contiguous, so a warp of 32 lines
-// reads and writes 32 consecutive values); k_thomas then runs only the
+// reads and writes 32 consecutive values); k_thomas_jobs then runs only the
 // recurrence, one thread per (line, component), with the pivots precomputed
 // on the host: dp_i = (r_i - a dp_{i-1}) rden_i, x_i = dp_i - cp_i x_{i+1}
 // (cyclic lines add the Sherman-Morrison correction).  rden_i = 1/den_i is
@@ -16,30 +16,29 @@ namespace cgk {
 
 // Up to three independent families of lines solved by one launch (e.g. the x
 // and y lines of a stage): job j covers columns [start_j, start_j + nl_j * ncomp_j).
-struct ThomasJobs {
-  LineCoef lc[3];
-  double* x[3];
+// T = double: the FP64 solves; T = float: the mixed form's FP32 gradient solves
+// (coefficients mirrored in FP32).
+template <typename T>
+struct ThomasJobsT {
+  LineCoefT<T> lc[3];
+  T* x[3];
   long long nl[3];
   int ncomp[3];
   long long start[4];
   int njobs;
 };
 
-__device__ __forceinline__ void thomas_column(const LineCoef& lc, double* __restrict__ x, long long nl, long long t);
+template <typename T>
+__device__ __forceinline__ void thomas_column(const LineCoefT<T>& lc, T* __restrict__ x, long long nl, long long t);
 
 // Thomas recurrence over every column (line x component) of x (in place).
-__global__ void k_thomas(LineCoef lc, double* __restrict__ x, long long nl, int ncomp) {
-  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= nl * ncomp) return;
-  thomas_column(lc, x, nl, t);
-}
-
-__global__ void k_thomas_jobs(ThomasJobs J) {
+template <typename T>
+__global__ void k_thomas_jobs(ThomasJobsT<T> J) {
   long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   int j = 0;
   while (j + 1 < J.njobs && t >= J.start[j + 1]) ++j;
   if (t >= J.start[J.njobs]) return;
-  thomas_column(J.lc[j], J.x[j], J.nl[j], t - J.start[j]);
+  thomas_column<T>(J.lc[j], J.x[j], J.nl[j], t - J.start[j]);
 }
 
 // The recurrences below read row i+B..i+2B-1 (forward) or i-B..i-2B+1
@@ -50,11 +49,12 @@ __global__ void k_thomas_jobs(ThomasJobs J) {
 constexpr int kRowBatch = 8;
 
 // dp_i = (r_i - a dp_{i-1}) rden_i for i in [i0, i1), in place; returns dp_{i1-1}.
-__device__ __forceinline__ double thomas_forward(double* __restrict__ col, long long nl, const double* __restrict__ den,
-                                                 double a, int i0, int i1, double dp) {
+template <typename T>
+__device__ __forceinline__ T thomas_forward(T* __restrict__ col, long long nl, const T* __restrict__ den,
+                                            T a, int i0, int i1, T dp) {
   constexpr int B = kRowBatch;
   const int nfull = (i1 - i0) / B;
-  double v[B], dn[B];
+  T v[B], dn[B];
   if (nfull > 0) {
 #pragma unroll
     for (int k = 0; k < B; ++k) {
@@ -65,7 +65,7 @@ __device__ __forceinline__ double thomas_forward(double* __restrict__ col, long 
   for (int b = 0; b < nfull; ++b) {
     const int base = i0 + b * B;
     const bool more = b + 1 < nfull;
-    double nv[B], nd[B];
+    T nv[B], nd[B];
     if (more) {
 #pragma unroll
       for (int k = 0; k < B; ++k) {
@@ -75,7 +75,7 @@ __device__ __forceinline__ double thomas_forward(double* __restrict__ col, long 
     }
 #pragma unroll
     for (int k = 0; k < B; ++k) {
-      dp = __fma_rn(-a, dp, v[k]) * dn[k];
+      dp = fma_t(-a, dp, v[k]) * dn[k];
       col[(long long)(base + k) * nl] = dp;
     }
     if (more) {
@@ -87,18 +87,19 @@ __device__ __forceinline__ double thomas_forward(double* __restrict__ col, long 
     }
   }
   for (int i = i0 + nfull * B; i < i1; ++i) {
-    dp = __fma_rn(-a, dp, col[(long long)i * nl]) * den[i];
+    dp = fma_t(-a, dp, col[(long long)i * nl]) * den[i];
     col[(long long)i * nl] = dp;
   }
   return dp;
 }
 
 // x_i = dp_i - cp_i x_{i+1} for i = i1, i1-1, ..., i0, in place; returns x_{i0}.
-__device__ __forceinline__ double thomas_backward(double* __restrict__ col, long long nl, const double* __restrict__ cp,
-                                                  int i0, int i1, double xv) {
+template <typename T>
+__device__ __forceinline__ T thomas_backward(T* __restrict__ col, long long nl, const T* __restrict__ cp,
+                                             int i0, int i1, T xv) {
   constexpr int B = kRowBatch;
   const int nfull = (i1 - i0 + 1) / B;
-  double v[B], c[B];
+  T v[B], c[B];
   if (nfull > 0) {
 #pragma unroll
     for (int k = 0; k < B; ++k) {
@@ -109,7 +110,7 @@ __device__ __forceinline__ double thomas_backward(double* __restrict__ col, long
   for (int b = 0; b < nfull; ++b) {
     const int top = i1 - b * B;
     const bool more = b + 1 < nfull;
-    double nv[B], nc[B];
+    T nv[B], nc[B];
     if (more) {
 #pragma unroll
       for (int k = 0; k < B; ++k) {
@@ -119,7 +120,7 @@ __device__ __forceinline__ double thomas_backward(double* __restrict__ col, long
     }
 #pragma unroll
     for (int k = 0; k < B; ++k) {
-      xv = __fma_rn(-c[k], xv, v[k]);
+      xv = fma_t(-c[k], xv, v[k]);
       col[(long long)(top - k) * nl] = xv;
     }
     if (more) {
@@ -131,42 +132,44 @@ __device__ __forceinline__ double thomas_backward(double* __restrict__ col, long
     }
   }
   for (int i = i1 - nfull * B; i >= i0; --i) {
-    xv = __fma_rn(-cp[i], xv, col[(long long)i * nl]);
+    xv = fma_t(-cp[i], xv, col[(long long)i * nl]);
     col[(long long)i * nl] = xv;
   }
   return xv;
 }
 
 // x_i -= f z_i for i in [0, m), in place.
-__device__ __forceinline__ void thomas_correct(double* __restrict__ col, long long nl, const double* __restrict__ z,
-                                               int m, double f) {
+template <typename T>
+__device__ __forceinline__ void thomas_correct(T* __restrict__ col, long long nl, const T* __restrict__ z,
+                                               int m, T f) {
   constexpr int B = kRowBatch;
   int i = 0;
   for (; i + B <= m; i += B) {
-    double v[B];
+    T v[B];
 #pragma unroll
     for (int k = 0; k < B; ++k) v[k] = col[(long long)(i + k) * nl];
 #pragma unroll
-    for (int k = 0; k < B; ++k) col[(long long)(i + k) * nl] = __fma_rn(-f, z[i + k], v[k]);
+    for (int k = 0; k < B; ++k) col[(long long)(i + k) * nl] = fma_t(-f, z[i + k], v[k]);
   }
-  for (; i < m; ++i) col[(long long)i * nl] = __fma_rn(-f, z[i], col[(long long)i * nl]);
+  for (; i < m; ++i) col[(long long)i * nl] = fma_t(-f, z[i], col[(long long)i * nl]);
 }
 
-__device__ __forceinline__ void thomas_column(const LineCoef& lc, double* __restrict__ x, long long nl, long long t) {
+template <typename T>
+__device__ __forceinline__ void thomas_column(const LineCoefT<T>& lc, T* __restrict__ x, long long nl, long long t) {
   long long comp = t / nl, L = t % nl;
-  double* col = x + comp * lc.m * nl + L;
-  const double a = lc.a;
+  T* col = x + comp * lc.m * nl + L;
+  const T a = lc.a;
   const int m = lc.m;
   if (!lc.periodic) {
     // rows 0 and m-1 are identity rows (x = r there)
     thomas_forward(col, nl, lc.den, a, 1, m - 1, col[0]);
     thomas_backward(col, nl, lc.cp, 0, m - 2, col[(long long)(m - 1) * nl]);
   } else {
-    double dp = col[0] * lc.den[0];
+    T dp = col[0] * lc.den[0];
     col[0] = dp;
-    const double xlast = thomas_forward(col, nl, lc.den, a, 1, m, dp);
-    const double x0 = thomas_backward(col, nl, lc.cp, 0, m - 2, xlast);
-    const double fact = (x0 + a * xlast / lc.gam) / lc.fden;
+    const T xlast = thomas_forward(col, nl, lc.den, a, 1, m, dp);
+    const T x0 = thomas_backward(col, nl, lc.cp, 0, m - 2, xlast);
+    const T fact = (x0 + a * xlast / lc.gam) / lc.fden;
     thomas_correct(col, nl, lc.z, m, fact);
   }
 }
@@ -182,21 +185,24 @@ __device__ __forceinline__ void thomas_column(const LineCoef& lc, double* __rest
 // solved by one thread per column; a last pass applies the correction (and,
 // for cyclic lines, the Sherman-Morrison term).  A block holds 32 columns
 // (lanes, coalesced) times the chunks.
-struct PartCoef {
-  const double* aL;   // sub-diagonal of row i inside its chunk (0 at chunk starts)
-  const double* cp;   // local elimination: super-diagonal / pivot (0 at chunk ends)
-  const double* rd;   // reciprocal local pivots
-  const double* V;    // response to the unknown before the chunk
-  const double* W;    // response to the unknown after the chunk
-  const double* z;    // cyclic: Sherman-Morrison vector, else null
-  const double* ch;   // per chunk: rF, qF, beta, VF (= V at its first row), VL (= V at its last row)
-  double a, gam, fden;
+template <typename T>
+struct PartCoefT {
+  const T* aL;   // sub-diagonal of row i inside its chunk (0 at chunk starts)
+  const T* cp;   // local elimination: super-diagonal / pivot (0 at chunk ends)
+  const T* rd;   // reciprocal local pivots
+  const T* V;    // response to the unknown before the chunk
+  const T* W;    // response to the unknown after the chunk
+  const T* z;    // cyclic: Sherman-Morrison vector, else null
+  const T* ch;   // per chunk: rF, qF, beta, VF (= V at its first row), VL (= V at its last row)
+  T a, gam, fden;
   int m, q, P, periodic;
 };
+using PartCoef = PartCoefT<double>;
 
-struct PartJobs {
-  PartCoef pc[3];
-  double* x[3];
+template <typename T>
+struct PartJobsT {
+  PartCoefT<T> pc[3];
+  T* x[3];
   long long nl[3];
   int ncomp[3];
   long long start[4];  // first 32-column group of each job, in columns (multiples of 32)
@@ -205,30 +211,31 @@ struct PartJobs {
 
 constexpr int kPartMax = 32;
 
-__global__ void __launch_bounds__(1024) k_tri_part(PartJobs J) {
-  __shared__ double sYF[kPartMax][32], sYL[kPartMax][32], sF[kPartMax][32], sL[kPartMax][32];
-  __shared__ double sFact[32];
+template <typename T>
+__global__ void __launch_bounds__(1024) k_tri_part(PartJobsT<T> J) {
+  __shared__ T sYF[kPartMax][32], sYL[kPartMax][32], sF[kPartMax][32], sL[kPartMax][32];
+  __shared__ T sFact[32];
   const int lane = threadIdx.x, k = threadIdx.y;
   const long long g0 = (long long)blockIdx.x * 32;
   int j = 0;
   while (j + 1 < J.njobs && g0 >= J.start[j + 1]) ++j;
-  const PartCoef& pc = J.pc[j];
+  const PartCoefT<T>& pc = J.pc[j];
   const long long nl = J.nl[j];
   const long long c = g0 - J.start[j] + lane;
   const bool active = c < nl * J.ncomp[j];
-  double* col = J.x[j] + (active ? (c / nl) * pc.m * nl + c % nl : 0);
+  T* col = J.x[j] + (active ? (c / nl) * pc.m * nl + c % nl : 0);
   const int s = k * pc.q, e = min(pc.m, s + pc.q);
   const bool mine = active && k < pc.P && s < e;
   if (mine) {
-    double y = col[(long long)s * nl] * pc.rd[s];
+    T y = col[(long long)s * nl] * pc.rd[s];
     col[(long long)s * nl] = y;
     for (int i = s + 1; i < e; ++i) {
-      y = __fma_rn(-pc.aL[i], y, col[(long long)i * nl]) * pc.rd[i];
+      y = fma_t(-pc.aL[i], y, col[(long long)i * nl]) * pc.rd[i];
       col[(long long)i * nl] = y;
     }
     sYL[k][lane] = y;
     for (int i = e - 2; i >= s; --i) {
-      y = __fma_rn(-pc.cp[i], y, col[(long long)i * nl]);
+      y = fma_t(-pc.cp[i], y, col[(long long)i * nl]);
       col[(long long)i * nl] = y;
     }
     sYF[k][lane] = y;
@@ -236,20 +243,20 @@ __global__ void __launch_bounds__(1024) k_tri_part(PartJobs J) {
   __syncthreads();
   if (k == 0 && active) {
     // forward: F_k = pF_k + qF_k F_{k+1},  L_k = alpha_k + beta_k F_{k+1}
-    double alpha = 0.0, beta_prev = 0.0;
+    T alpha = T(0), beta_prev = T(0);
     for (int kk = 0; kk < pc.P; ++kk) {
-      const double* h = pc.ch + 5 * kk;
-      double pF = __fma_rn(-h[3], alpha, sYF[kk][lane]) * h[0];
-      alpha = __fma_rn(-h[4], __fma_rn(beta_prev, pF, alpha), sYL[kk][lane]);
+      const T* h = pc.ch + 5 * kk;
+      T pF = fma_t(-h[3], alpha, sYF[kk][lane]) * h[0];
+      alpha = fma_t(-h[4], fma_t(beta_prev, pF, alpha), sYL[kk][lane]);
       sF[kk][lane] = pF;
       sL[kk][lane] = alpha;
       beta_prev = h[2];
     }
-    double Fn = 0.0;
+    T Fn = T(0);
     for (int kk = pc.P - 1; kk >= 0; --kk) {
-      const double* h = pc.ch + 5 * kk;
-      double F = __fma_rn(h[1], Fn, sF[kk][lane]);
-      double L = __fma_rn(h[2], Fn, sL[kk][lane]);
+      const T* h = pc.ch + 5 * kk;
+      T F = fma_t(h[1], Fn, sF[kk][lane]);
+      T L = fma_t(h[2], Fn, sL[kk][lane]);
       sF[kk][lane] = F;
       sL[kk][lane] = L;
       Fn = F;
@@ -258,13 +265,13 @@ __global__ void __launch_bounds__(1024) k_tri_part(PartJobs J) {
   }
   __syncthreads();
   if (mine) {
-    const double Lp = k > 0 ? sL[k - 1][lane] : 0.0;
-    const double Fn = k + 1 < pc.P ? sF[k + 1][lane] : 0.0;
-    const double f = pc.periodic ? sFact[lane] : 0.0;
+    const T Lp = k > 0 ? sL[k - 1][lane] : T(0);
+    const T Fn = k + 1 < pc.P ? sF[k + 1][lane] : T(0);
+    const T f = pc.periodic ? sFact[lane] : T(0);
     for (int i = s; i < e; ++i) {
-      double x = __fma_rn(-pc.V[i], Lp, col[(long long)i * nl]);
-      x = __fma_rn(-pc.W[i], Fn, x);
-      if (pc.periodic) x = __fma_rn(-f, pc.z[i], x);
+      T x = fma_t(-pc.V[i], Lp, col[(long long)i * nl]);
+      x = fma_t(-pc.W[i], Fn, x);
+      if (pc.periodic) x = fma_t(-f, pc.z[i], x);
       col[(long long)i * nl] = x;
     }
   }
@@ -276,8 +283,8 @@ __global__ void __launch_bounds__(1024) k_tri_part(PartJobs J) {
 
 // MIG4 right-hand sides of the primitives along lb.d: 3/4 (W_{i+1} - W_{i-1}),
 // E4 closure rows at both ends of a non-periodic line.
-template <int ND, typename TW = double>
-__global__ void k_rhs_mig4(DevGrid g, const TW* __restrict__ W, LineBuf lb, double* __restrict__ r) {
+template <int ND, typename TW = double, typename TR = double>
+__global__ void k_rhs_mig4(DevGrid g, const TW* __restrict__ W, LineBuf lb, TR* __restrict__ r) {
   constexpr int NV = ND + 2;
   LB_LOOP(lb, e) {
     int i = (int)(e / lb.nl);
@@ -286,19 +293,19 @@ __global__ void k_rhs_mig4(DevGrid g, const TW* __restrict__ W, LineBuf lb, doub
     lb.coords(L, c);
     int pos = lb.periodic ? i : lb.lo + i;
     bool closure = !lb.periodic && (i == 0 || i == lb.m - 1);
-    double wp1[NV], wm1[NV];
+    TR wp1[NV], wm1[NV];
     int cc[3] = {c[0], c[1], c[2]};
-    cc[lb.d] = pos + 1; load_state<ND, false, TW, double>(g, W, cc[0], cc[1], cc[2], wp1);
-    cc[lb.d] = pos - 1; load_state<ND, false, TW, double>(g, W, cc[0], cc[1], cc[2], wm1);
+    cc[lb.d] = pos + 1; load_state<ND, false, TW, TR>(g, W, cc[0], cc[1], cc[2], wp1);
+    cc[lb.d] = pos - 1; load_state<ND, false, TW, TR>(g, W, cc[0], cc[1], cc[2], wm1);
     if (closure) {
-      double wp2[NV], wm2[NV];
-      cc[lb.d] = pos + 2; load_state<ND, false, TW, double>(g, W, cc[0], cc[1], cc[2], wp2);
-      cc[lb.d] = pos - 2; load_state<ND, false, TW, double>(g, W, cc[0], cc[1], cc[2], wm2);
+      TR wp2[NV], wm2[NV];
+      cc[lb.d] = pos + 2; load_state<ND, false, TW, TR>(g, W, cc[0], cc[1], cc[2], wp2);
+      cc[lb.d] = pos - 2; load_state<ND, false, TW, TR>(g, W, cc[0], cc[1], cc[2], wm2);
 #pragma unroll
       for (int v = 0; v < NV; ++v) r[((long long)v * lb.m + i) * lb.nl + L] = d4(wm2[v], wm1[v], wp1[v], wp2[v]);
     } else {
 #pragma unroll
-      for (int v = 0; v < NV; ++v) r[((long long)v * lb.m + i) * lb.nl + L] = 0.75 * (wp1[v] - wm1[v]);
+      for (int v = 0; v < NV; ++v) r[((long long)v * lb.m + i) * lb.nl + L] = TR(0.75) * (wp1[v] - wm1[v]);
     }
   }
 }
