@@ -41,6 +41,7 @@ MIXED = [
     ("MEG6_MIXED", dict(scheme="MEG6", precision=1)),
     ("MIG4_MIXED", dict(scheme="MIG4", precision=1)),
     ("LAD_E4_MIXED", dict(scheme="LAD_E4", precision=1)),
+    ("LAD_C6_MIXED", dict(scheme="LAD_C6", precision=1)),
     ("HYBRID_GLOBAL_MIXED", dict(scheme="HYBRID", hybrid_mode=0, hyb_rho=0.5 * 0.125, precision=1)),
     ("HYBRID_CELL_MIXED", dict(scheme="HYBRID", hybrid_mode=1, hyb_rho=0.5 * 0.125, hybrid_sensor=1, precision=1)),
 ]

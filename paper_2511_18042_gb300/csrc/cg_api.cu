@@ -1054,8 +1054,6 @@ CG_API int cg_solver_create(const cg_grid* g, const cg_params* p, cg_solver** ou
   if (!g || !p || !out) return fail(CG_ERR_INVALID_ARG, "null argument");
   if (p->scheme < CG_MEG6 || p->scheme > CG_HYBRID) return fail(CG_ERR_INVALID_ARG, "bad scheme");
   if (p->precision != CG_FP64 && p->precision != CG_MIXED) return fail(CG_ERR_INVALID_ARG, "bad precision");
-  if (p->precision == CG_MIXED && p->scheme == CG_LAD_C6)
-    return fail(CG_ERR_UNSUPPORTED, "the mixed form is built for MEG6, MIG4, LAD-E4 and the hybrid (not LAD-C6)");
   if (!(p->gamma > 1.0) || !(p->cfl > 0.0)) return fail(CG_ERR_INVALID_ARG, "gamma > 1 and cfl > 0 required");
   if (p->omega_window < 1 || p->omega_window > 4) return fail(CG_ERR_INVALID_ARG, "omega_window must be 1..4");
   if (g->curv && p->scheme == CG_LAD_C6)

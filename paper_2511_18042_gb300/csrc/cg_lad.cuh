@@ -66,8 +66,8 @@ __global__ void k_lad_fieldbuf(DevGrid g, const T* __restrict__ W, T* __restrict
 // Physical gradients and dilatation on b3.  E4 differences the field buffer;
 // C6 reads the compact derivatives from the line buffers df.
 template <int ND, bool CART, bool C6, typename T = double>
-__global__ void k_lad_grad(DevGrid g, const T* __restrict__ fb, Box fbx, const double* __restrict__ df0,
-                           const double* __restrict__ df1, const double* __restrict__ df2, LineBuf lb0, LineBuf lb1,
+__global__ void k_lad_grad(DevGrid g, const T* __restrict__ fb, Box fbx, const T* __restrict__ df0,
+                           const T* __restrict__ df1, const T* __restrict__ df2, LineBuf lb0, LineBuf lb1,
                            LineBuf lb2, T* __restrict__ gr, T* __restrict__ dv, Box b3, const int* guard,
                            int want) {
   constexpr int NF = ND + 3;
@@ -81,7 +81,7 @@ __global__ void k_lad_grad(DevGrid g, const T* __restrict__ fb, Box fbx, const d
 #pragma unroll
     for (int l = 0; l < ND; ++l) {
       if (C6) {
-        const double* df = l == 0 ? df0 : (l == 1 ? df1 : df2);
+        const T* df = l == 0 ? df0 : (l == 1 ? df1 : df2);
         const LineBuf& lb = l == 0 ? lb0 : (l == 1 ? lb1 : lb2);
 #pragma unroll
         for (int f = 0; f < NF; ++f) d[l][f] = T(df[lb.at(f, c[l], c)]);
@@ -430,7 +430,7 @@ __device__ __forceinline__ void lad_epilogue(const DevGrid& g, const StageArgs& 
 
 // E4 divergence of the node fluxes along l (explicit) or the compact result D.
 template <int ND, typename T = double>
-__global__ void k_lad_div(DevGrid g, int l, const T* __restrict__ Fn, Box fb, const double* __restrict__ D,
+__global__ void k_lad_div(DevGrid g, int l, const T* __restrict__ Fn, Box fb, const T* __restrict__ D,
                           LineBuf DL, StageArgs A, const int* guard, int want) {
   constexpr int NV = ND + 2;
   if (guard && *guard != want) return;
@@ -443,7 +443,7 @@ __global__ void k_lad_div(DevGrid g, int l, const T* __restrict__ Fn, Box fb, co
     double Dv[NV];
     if (D) {
 #pragma unroll
-      for (int v = 0; v < NV; ++v) Dv[v] = D[DL.at(v, c[l], c)];
+      for (int v = 0; v < NV; ++v) Dv[v] = (double)D[DL.at(v, c[l], c)];
     } else {
       long long e = fb.at(c[0], c[1], c[2]);
       long long st = l == 0 ? 1 : (l == 1 ? (long long)fb.ext[0] : (long long)fb.ext[0] * fb.ext[1]);

@@ -78,26 +78,27 @@ static int lad_coeffs_run(cg_solver* s, int dkind, cudaStream_t st, const int* g
   T* kp[2] = {reinterpret_cast<T*>(L.kp[0]), reinterpret_cast<T*>(L.kp[1])};
   k_lad_fieldbuf<ND, T><<<grid_blocks(L.fbx.size(), 256), 256, 0, st>>>(s->dg, reinterpret_cast<const T*>(s->W), fb, L.fbx);
   s->launches++;
+  T* df[3] = {reinterpret_cast<T*>(L.df[0]), reinterpret_cast<T*>(L.df[1]), reinterpret_cast<T*>(L.df[2])};
   if (c6) {
-    LineJob<double> jobs[3];
+    LineJob<T> jobs[3];
     for (int l = 0; l < ND; ++l) {
       const LineBuf& lb = L.dfLB[l];
-      k_rhs_c6<<<grid_blocks((long long)lb.m * lb.nl, 256), 256, 0, st>>>(reinterpret_cast<double*>(fb), L.fbx, ND + 3, lb, L.df[l]);
+      k_rhs_c6<T><<<grid_blocks((long long)lb.m * lb.nl, 256), 256, 0, st>>>(fb, L.fbx, ND + 3, lb, df[l]);
       s->launches++;
-      jobs[l] = LineJob<double>{&s->c6grad[l], L.df[l], lb.nl, ND + 3};
+      jobs[l] = LineJob<T>{&s->c6grad[l], df[l], lb.nl, ND + 3};
     }
     launch_lines(jobs, ND, st);
     s->launches++;
   }
   int gb = grid_blocks(L.b3.size(), 128);
   if (s->dg.curv) {
-    if (c6) k_lad_grad<ND, false, true, T><<<gb, 128, 0, st>>>(s->dg, fb, L.fbx, L.df[0], L.df[1], L.df[2], L.dfLB[0], L.dfLB[1], L.dfLB[2], gr, dv, L.b3, guard, want);
-    else k_lad_grad<ND, false, false, T><<<gb, 128, 0, st>>>(s->dg, fb, L.fbx, L.df[0], L.df[1], L.df[2], L.dfLB[0], L.dfLB[1], L.dfLB[2], gr, dv, L.b3, guard, want);
+    if (c6) k_lad_grad<ND, false, true, T><<<gb, 128, 0, st>>>(s->dg, fb, L.fbx, df[0], df[1], df[2], L.dfLB[0], L.dfLB[1], L.dfLB[2], gr, dv, L.b3, guard, want);
+    else k_lad_grad<ND, false, false, T><<<gb, 128, 0, st>>>(s->dg, fb, L.fbx, df[0], df[1], df[2], L.dfLB[0], L.dfLB[1], L.dfLB[2], gr, dv, L.b3, guard, want);
     k_lad_coef<ND, false, T><<<grid_blocks(s->N, 128), 128, 0, st>>>(s->dg, reinterpret_cast<const T*>(s->W), fb, L.fbx, gr, dv, L.b3, s->p.c_beta,
                                                                      s->p.c_kappa, bt[0], kp[0], guard, want);
   } else {
-    if (c6) k_lad_grad<ND, true, true, T><<<gb, 128, 0, st>>>(s->dg, fb, L.fbx, L.df[0], L.df[1], L.df[2], L.dfLB[0], L.dfLB[1], L.dfLB[2], gr, dv, L.b3, guard, want);
-    else k_lad_grad<ND, true, false, T><<<gb, 128, 0, st>>>(s->dg, fb, L.fbx, L.df[0], L.df[1], L.df[2], L.dfLB[0], L.dfLB[1], L.dfLB[2], gr, dv, L.b3, guard, want);
+    if (c6) k_lad_grad<ND, true, true, T><<<gb, 128, 0, st>>>(s->dg, fb, L.fbx, df[0], df[1], df[2], L.dfLB[0], L.dfLB[1], L.dfLB[2], gr, dv, L.b3, guard, want);
+    else k_lad_grad<ND, true, false, T><<<gb, 128, 0, st>>>(s->dg, fb, L.fbx, df[0], df[1], df[2], L.dfLB[0], L.dfLB[1], L.dfLB[2], gr, dv, L.b3, guard, want);
     k_lad_coef<ND, true, T><<<grid_blocks(s->N, 128), 128, 0, st>>>(s->dg, reinterpret_cast<const T*>(s->W), fb, L.fbx, gr, dv, L.b3, s->p.c_beta,
                                                                     s->p.c_kappa, bt[0], kp[0], guard, want);
   }
@@ -151,9 +152,9 @@ static void lad_grad_e4(cg_solver* s, cudaStream_t st, const int* guard, int wan
   k_lad_fieldbuf<ND, T><<<grid_blocks(L.fbx.size(), 256), 256, 0, st>>>(s->dg, reinterpret_cast<const T*>(s->W), fb, L.fbx);
   int gb = grid_blocks(L.b3.size(), 128);
   if (s->dg.curv)
-    k_lad_grad<ND, false, false, T><<<gb, 128, 0, st>>>(s->dg, fb, L.fbx, L.df[0], L.df[1], L.df[2], L.dfLB[0], L.dfLB[1], L.dfLB[2], gr, dv, L.b3, guard, want);
+    k_lad_grad<ND, false, false, T><<<gb, 128, 0, st>>>(s->dg, fb, L.fbx, nullptr, nullptr, nullptr, L.dfLB[0], L.dfLB[1], L.dfLB[2], gr, dv, L.b3, guard, want);
   else
-    k_lad_grad<ND, true, false, T><<<gb, 128, 0, st>>>(s->dg, fb, L.fbx, L.df[0], L.df[1], L.df[2], L.dfLB[0], L.dfLB[1], L.dfLB[2], gr, dv, L.b3, guard, want);
+    k_lad_grad<ND, true, false, T><<<gb, 128, 0, st>>>(s->dg, fb, L.fbx, nullptr, nullptr, nullptr, L.dfLB[0], L.dfLB[1], L.dfLB[2], gr, dv, L.b3, guard, want);
   s->launches += 2;
 }
 
@@ -193,14 +194,15 @@ static int lad_pass(cg_solver* s, int dkind, StageArgs A, cudaStream_t st, const
     A.first = l == 0;
     A.last = l == ND - 1;
     lad_nodeflux<ND, T>(s, l, st, guard, want, s->p.viscous ? NF_LAD_VISC : NF_LAD);
-    const double* D = nullptr;
+    const T* D = nullptr;
     LineBuf DL = L.DLB[l];
     if (dkind == 3) {
-      k_rhs_c6<<<grid_blocks((long long)DL.m * DL.nl, 256), 256, 0, st>>>(reinterpret_cast<const double*>(L.Fn), L.fbox[l], ND + 2, DL, L.D);
-      LineJob<double> job{&s->c6flux[l], L.D, DL.nl, ND + 2};
+      T* Dw = reinterpret_cast<T*>(L.D);
+      k_rhs_c6<T><<<grid_blocks((long long)DL.m * DL.nl, 256), 256, 0, st>>>(reinterpret_cast<const T*>(L.Fn), L.fbox[l], ND + 2, DL, Dw);
+      LineJob<T> job{&s->c6flux[l], Dw, DL.nl, ND + 2};
       launch_lines(&job, 1, st);
       s->launches += 2;
-      D = L.D;
+      D = Dw;
     }
     k_lad_div<ND, T><<<grid_blocks(s->N, 256), 256, 0, st>>>(s->dg, l, reinterpret_cast<const T*>(L.Fn), L.fbox[l], D, DL,
                                                             A, guard, want);

@@ -314,7 +314,8 @@ __global__ void k_rhs_mig4(DevGrid g, const TW* __restrict__ W, LineBuf lb, TR* 
 // positions up to two past the rows): 7/9 (f_{i+1} - f_{i-1}) + 1/36 (f_{i+2} - f_{i-2}),
 // E4 closure rows at both ends of a non-periodic line.  Periodic rows read the
 // field at wrapped positions through the box (fb covers the wrap).
-__global__ void k_rhs_c6(const double* __restrict__ f, Box fb, int nc, LineBuf lb, double* __restrict__ r) {
+template <typename T = double>
+__global__ void k_rhs_c6(const T* __restrict__ f, Box fb, int nc, LineBuf lb, T* __restrict__ r) {
   long long fs = fb.size();
   long long st = lb.d == 0 ? 1 : (lb.d == 1 ? (long long)fb.ext[0] : (long long)fb.ext[0] * fb.ext[1]);
   LB_LOOP(lb, e) {
@@ -326,9 +327,9 @@ __global__ void k_rhs_c6(const double* __restrict__ f, Box fb, int nc, LineBuf l
     long long q = fb.at(c[0], c[1], c[2]);
     bool closure = !lb.periodic && (i == 0 || i == lb.m - 1);
     for (int v = 0; v < nc; ++v) {
-      const double* p = f + v * fs + q;
-      double rv = closure ? d4(p[-2 * st], p[-st], p[st], p[2 * st])
-                          : (7.0 / 9.0) * (p[st] - p[-st]) + (1.0 / 36.0) * (p[2 * st] - p[-2 * st]);
+      const T* p = f + v * fs + q;
+      T rv = closure ? d4(p[-2 * st], p[-st], p[st], p[2 * st])
+                     : T(7.0 / 9.0) * (p[st] - p[-st]) + T(1.0 / 36.0) * (p[2 * st] - p[-2 * st]);
       r[((long long)v * lb.m + i) * lb.nl + L] = rv;
     }
   }

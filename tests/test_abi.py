@@ -73,8 +73,6 @@ def test_solver_parameter_validation_without_gpu():
 
     assert create(scheme=7) == -1
     assert create(precision=3) == -1
-    assert create(scheme=3, precision=1) == -5  # no mixed form of LAD-C6
-    assert b"LAD-C6" in L.cg_last_error()
     assert create(omega_window=5) == -1
     assert create(cfl=0.0) == -1
     assert create(viscous=1, re=0.0) == -1

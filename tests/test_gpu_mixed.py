@@ -61,7 +61,24 @@ def test_mixed_rhs_close_to_fp64(orc, api):
         assert np.abs(R[v] - Ro[v]).max() <= 1e-4 * np.abs(Ro[v]).max()
 
 
-def test_mixed_rejects_unsupported_schemes(api):
-    prob = inputs.triple_point(64, 32)
-    with pytest.raises(Exception):
-        api.Solver.from_problem(prob, scheme="LAD_C6", precision=1)
+def test_mixed_lad_c6_sod(orc, api):
+    """LAD-C6 in the mixed form: FP32 compact derivatives of the fields and the
+    fluxes, FP64 implicit filter of the state."""
+    prob = inputs.shock_tube("sod", 400)
+    o = orc.Oracle(prob, scheme="LAD_C6", cfl=0.1)
+    Uo, _, _ = o.advance(prob["U"], t_end=0.2)
+    s = api.Solver.from_problem(prob, scheme="LAD_C6", precision=1, cfl=0.1)
+    Ug = to_dev(prob["U"])
+    s.advance(Ug, t_end=0.2)
+    assert _l1_rho(Ug, Uo) <= 1e-5
+
+
+def test_mixed_lad_c6_periodic_2d(orc, api):
+    prob = inputs.kelvin_helmholtz(64)
+    o = orc.Oracle(prob, scheme="LAD_C6", cfl=0.1)
+    Uo, _, _ = o.advance(prob["U"], nsteps=50)
+    s = api.Solver.from_problem(prob, scheme="LAD_C6", precision=1, cfl=0.1)
+    Ug = to_dev(prob["U"])
+    s.advance(Ug, nsteps=50)
+    assert _l1_rho(Ug, Uo) <= 1e-5
+    assert torch.isfinite(Ug).all()
