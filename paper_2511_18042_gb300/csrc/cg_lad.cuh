@@ -127,6 +127,15 @@ __global__ void k_lad_grad(DevGrid g, const T* __restrict__ fb, Box fbx, const T
   }
 }
 
+// Euclidean norm of an FP32 gradient (ND components), overflow- and
+// underflow-safe through the CUDA library's hypot forms.
+template <int ND>
+__device__ __forceinline__ float grad_norm(float a, float b, float c) {
+  if constexpr (ND == 1) return fabsf(a);
+  else if constexpr (ND == 2) return hypotf(a, b);
+  else return norm3df(a, b, c);
+}
+
 // Raw coefficients at interior nodes, Eq. (4)-(6):
 // beta* = C_beta rho f_sw |sum_l d4(div)_l Delta_{l,beta}^2|,
 // kappa* = C_kappa (rho c / T) |sum_l d4(e)_l Delta_{l,kappa}|.
@@ -163,14 +172,24 @@ __global__ void k_lad_coef(DevGrid g, const T* __restrict__ W, const T* __restri
     }
     T heav = div < T(0) ? T(1) : T(0);
     T fsw = heav * (div * div) / (div * div + curl2 + T(1e-32));
-    T gmr = G(ND + 1, 0) * G(ND + 1, 0), gme = G(ND + 2, 0) * G(ND + 2, 0);
+    T gmr, gme;
+    if constexpr (sizeof(T) == 4) {
+      // |grad rho| and |grad e| without squaring: in FP32 a square under
+      // ~1e-38 flushes, and |x . grad| / (0 + 1e-32) would then inflate the
+      // length scales Delta_beta, Delta_kappa far beyond the grid spacing
+      gmr = grad_norm<ND>(G(ND + 1, 0), G(ND + 1, ND > 1 ? 1 : 0), G(ND + 1, ND > 2 ? 2 : 0));
+      gme = grad_norm<ND>(G(ND + 2, 0), G(ND + 2, ND > 1 ? 1 : 0), G(ND + 2, ND > 2 ? 2 : 0));
+    } else {
+      gmr = G(ND + 1, 0) * G(ND + 1, 0);
+      gme = G(ND + 2, 0) * G(ND + 2, 0);
 #pragma unroll
-    for (int m = 1; m < ND; ++m) {
-      gmr = gmr + G(ND + 1, m) * G(ND + 1, m);
-      gme = gme + G(ND + 2, m) * G(ND + 2, m);
+      for (int m = 1; m < ND; ++m) {
+        gmr = gmr + G(ND + 1, m) * G(ND + 1, m);
+        gme = gme + G(ND + 2, m) * G(ND + 2, m);
+      }
+      gmr = sqrt(gmr);
+      gme = sqrt(gme);
     }
-    gmr = sqrt(gmr);
-    gme = sqrt(gme);
     T sb = T(0), sk = T(0);
 #pragma unroll
     for (int l = 0; l < ND; ++l) {
