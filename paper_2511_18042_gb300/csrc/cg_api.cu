@@ -659,6 +659,41 @@ static void launch_lines(const LineJob<T>* jobs, int n, cudaStream_t st) {
   k_thomas_jobs<T><<<(unsigned)((cols + 31) / 32), 32, 0, st>>>(J);
 }
 
+// Right-hand sides of the compact line systems: x lines staged through shared
+// memory (k_rhs_xtile), the others by the per-row kernels.
+template <int ND, typename T>
+static void launch_rhs_c6(const T* f, Box fb, int nc, const LineBuf& lb, T* r, cudaStream_t st) {
+  if (use_xtile(lb)) {
+    using Tl = XTileC6<T, ND + 3>;
+    k_rhs_xtile<T, ND + 3, 2, Tl><<<xtile_grid(lb), XT_THREADS, 0, st>>>(lb, Tl{f, fb, fb.size(), nc}, r);
+  } else {
+    k_rhs_c6<T><<<grid_blocks((long long)lb.m * lb.nl, 256), 256, 0, st>>>(f, fb, nc, lb, r);
+  }
+}
+
+template <int ND, typename TW, typename TR>
+static void launch_rhs_mig4(const DevGrid& g, const TW* W, const LineBuf& lb, TR* r, cudaStream_t st) {
+  if (use_xtile(lb)) {
+    using Tl = XTileMig4<ND, TW, TR>;
+    k_rhs_xtile<TR, ND + 2, 1, Tl><<<xtile_grid(lb), XT_THREADS, 0, st>>>(lb, Tl{g, W, ND + 2}, r);
+  } else {
+    k_rhs_mig4<ND, TW, TR><<<grid_blocks((long long)lb.m * lb.nl, 256), 256, 0, st>>>(g, W, lb, r);
+  }
+}
+
+template <int ND>
+static void launch_rhs_filter(const DevGrid& g, const double* U, const LineBuf& lb, const double b[5], double* r,
+                              cudaStream_t st) {
+  if (use_xtile(lb)) {
+    using Tl = XTileFilter<ND>;
+    k_rhs_xtile<double, ND + 2, 4, Tl><<<xtile_grid(lb), XT_THREADS, 0, st>>>(
+        lb, Tl{g, U, b[0], b[1], b[2], b[3], b[4], ND + 2}, r);
+  } else {
+    k_rhs_filter<ND><<<grid_blocks((long long)lb.m * lb.nl, 256), 256, 0, st>>>(g, U, lb, b[0], b[1], b[2], b[3],
+                                                                              b[4], r);
+  }
+}
+
 // Primitives of Uc into W: FP64 storage, or FP32 for the mixed form (the
 // recovery itself is FP64 in both).
 template <int ND>
@@ -683,8 +718,7 @@ static int stage_prep_gbr(cg_solver* s, const double* Uc, bool compact, cudaStre
       for (int d = 0; d < ND; ++d) {
         const LineBuf& lb = s->gdLB[d];
         float* G = reinterpret_cast<float*>(s->G[d]);
-        k_rhs_mig4<ND, float, float><<<grid_blocks((long long)lb.m * lb.nl, 256), 256, 0, st>>>(
-            s->dg, reinterpret_cast<const float*>(s->W), lb, G);
+        launch_rhs_mig4<ND, float, float>(s->dg, reinterpret_cast<const float*>(s->W), lb, G, st);
         s->launches++;
         jobs[d] = LineJob<float>{&s->mig4[d], G, lb.nl, ND + 2};
       }
@@ -693,8 +727,7 @@ static int stage_prep_gbr(cg_solver* s, const double* Uc, bool compact, cudaStre
       LineJob<double> jobs[3];
       for (int d = 0; d < ND; ++d) {
         const LineBuf& lb = s->gdLB[d];
-        k_rhs_mig4<ND, double, double><<<grid_blocks((long long)lb.m * lb.nl, 256), 256, 0, st>>>(s->dg, s->W, lb,
-                                                                                                 s->G[d]);
+        launch_rhs_mig4<ND, double, double>(s->dg, s->W, lb, s->G[d], st);
         s->launches++;
         jobs[d] = LineJob<double>{&s->mig4[d], s->G[d], lb.nl, ND + 2};
       }

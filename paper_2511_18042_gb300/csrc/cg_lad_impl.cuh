@@ -83,7 +83,7 @@ static int lad_coeffs_run(cg_solver* s, int dkind, cudaStream_t st, const int* g
     LineJob<T> jobs[3];
     for (int l = 0; l < ND; ++l) {
       const LineBuf& lb = L.dfLB[l];
-      k_rhs_c6<T><<<grid_blocks((long long)lb.m * lb.nl, 256), 256, 0, st>>>(fb, L.fbx, ND + 3, lb, df[l]);
+      launch_rhs_c6<ND, T>(fb, L.fbx, ND + 3, lb, df[l], st);
       s->launches++;
       jobs[l] = LineJob<T>{&s->c6grad[l], df[l], lb.nl, ND + 3};
     }
@@ -198,7 +198,7 @@ static int lad_pass(cg_solver* s, int dkind, StageArgs A, cudaStream_t st, const
     LineBuf DL = L.DLB[l];
     if (dkind == 3) {
       T* Dw = reinterpret_cast<T*>(L.D);
-      k_rhs_c6<T><<<grid_blocks((long long)DL.m * DL.nl, 256), 256, 0, st>>>(reinterpret_cast<const T*>(L.Fn), L.fbox[l], ND + 2, DL, Dw);
+      launch_rhs_c6<ND, T>(reinterpret_cast<const T*>(L.Fn), L.fbox[l], ND + 2, DL, Dw, st);
       LineJob<T> job{&s->c6flux[l], Dw, DL.nl, ND + 2};
       launch_lines(&job, 1, st);
       s->launches += 2;
@@ -292,8 +292,7 @@ static int lad_filter(cg_solver* s, double* U, cudaStream_t st) {
   filter_coeffs(s->p.alpha_f, b);
   for (int l = 0; l < ND; ++l) {
     const LineBuf& lb = s->lad.filtLB[l];
-    k_rhs_filter<ND><<<grid_blocks((long long)lb.m * lb.nl, 256), 256, 0, st>>>(s->dg, U, lb, b[0], b[1], b[2], b[3],
-                                                                              b[4], s->lad.lines);
+    launch_rhs_filter<ND>(s->dg, U, lb, b, s->lad.lines, st);
     LineJob<double> job{&s->filt[l], s->lad.lines, lb.nl, ND + 2};
     launch_lines(&job, 1, st);
     k_filter_store<ND><<<grid_blocks(s->N, 256), 256, 0, st>>>(s->dg, s->lad.lines, lb, U);

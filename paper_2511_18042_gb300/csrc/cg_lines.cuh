@@ -209,6 +209,84 @@ struct PartJobsT {
   int njobs;
 };
 
+// Partitioned forward elimination inside one chunk: y_i = (r_i - aL_i y_{i-1})
+// rd_i for i in [i0, i1), y_{i0-1} = 0 (aL is 0 at the chunk start), in place;
+// returns y_{i1-1}.  Batched like thomas_forward.
+template <typename T>
+__device__ __forceinline__ T part_forward(T* __restrict__ col, long long nl, const T* __restrict__ aL,
+                                          const T* __restrict__ rd, int i0, int i1) {
+  constexpr int B = kRowBatch;
+  const int nfull = (i1 - i0) / B;
+  T y = T(0);
+  T v[B], al[B], dn[B];
+  if (nfull > 0) {
+#pragma unroll
+    for (int k = 0; k < B; ++k) {
+      v[k] = col[(long long)(i0 + k) * nl];
+      al[k] = aL[i0 + k];
+      dn[k] = rd[i0 + k];
+    }
+  }
+  for (int b = 0; b < nfull; ++b) {
+    const int base = i0 + b * B;
+    const bool more = b + 1 < nfull;
+    T nv[B], na[B], nd[B];
+    if (more) {
+#pragma unroll
+      for (int k = 0; k < B; ++k) {
+        nv[k] = col[(long long)(base + B + k) * nl];
+        na[k] = aL[base + B + k];
+        nd[k] = rd[base + B + k];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < B; ++k) {
+      y = fma_t(-al[k], y, v[k]) * dn[k];
+      col[(long long)(base + k) * nl] = y;
+    }
+    if (more) {
+#pragma unroll
+      for (int k = 0; k < B; ++k) {
+        v[k] = nv[k];
+        al[k] = na[k];
+        dn[k] = nd[k];
+      }
+    }
+  }
+  for (int i = i0 + nfull * B; i < i1; ++i) {
+    y = fma_t(-aL[i], y, col[(long long)i * nl]) * rd[i];
+    col[(long long)i * nl] = y;
+  }
+  return y;
+}
+
+// Partitioned update inside one chunk: x_i = y_i - V_i L_prev - W_i F_next
+// (- f z_i on a cyclic line) for i in [i0, i1), in place, B rows per batch.
+template <typename T>
+__device__ __forceinline__ void part_update(T* __restrict__ col, long long nl, const PartCoefT<T>& pc, int i0,
+                                            int i1, T Lp, T Fn, T f) {
+  constexpr int B = kRowBatch;
+  int i = i0;
+  for (; i + B <= i1; i += B) {
+    T v[B];
+#pragma unroll
+    for (int k = 0; k < B; ++k) v[k] = col[(long long)(i + k) * nl];
+#pragma unroll
+    for (int k = 0; k < B; ++k) {
+      T x = fma_t(-pc.V[i + k], Lp, v[k]);
+      x = fma_t(-pc.W[i + k], Fn, x);
+      if (pc.periodic) x = fma_t(-f, pc.z[i + k], x);
+      col[(long long)(i + k) * nl] = x;
+    }
+  }
+  for (; i < i1; ++i) {
+    T x = fma_t(-pc.V[i], Lp, col[(long long)i * nl]);
+    x = fma_t(-pc.W[i], Fn, x);
+    if (pc.periodic) x = fma_t(-f, pc.z[i], x);
+    col[(long long)i * nl] = x;
+  }
+}
+
 constexpr int kPartMax = 32;
 
 template <typename T>
@@ -227,17 +305,9 @@ __global__ void __launch_bounds__(1024) k_tri_part(PartJobsT<T> J) {
   const int s = k * pc.q, e = min(pc.m, s + pc.q);
   const bool mine = active && k < pc.P && s < e;
   if (mine) {
-    T y = col[(long long)s * nl] * pc.rd[s];
-    col[(long long)s * nl] = y;
-    for (int i = s + 1; i < e; ++i) {
-      y = fma_t(-pc.aL[i], y, col[(long long)i * nl]) * pc.rd[i];
-      col[(long long)i * nl] = y;
-    }
+    T y = part_forward<T>(col, nl, pc.aL, pc.rd, s, e);
     sYL[k][lane] = y;
-    for (int i = e - 2; i >= s; --i) {
-      y = fma_t(-pc.cp[i], y, col[(long long)i * nl]);
-      col[(long long)i * nl] = y;
-    }
+    y = thomas_backward<T>(col, nl, pc.cp, s, e - 2, y);
     sYF[k][lane] = y;
   }
   __syncthreads();
@@ -268,12 +338,7 @@ __global__ void __launch_bounds__(1024) k_tri_part(PartJobsT<T> J) {
     const T Lp = k > 0 ? sL[k - 1][lane] : T(0);
     const T Fn = k + 1 < pc.P ? sF[k + 1][lane] : T(0);
     const T f = pc.periodic ? sFact[lane] : T(0);
-    for (int i = s; i < e; ++i) {
-      T x = fma_t(-pc.V[i], Lp, col[(long long)i * nl]);
-      x = fma_t(-pc.W[i], Fn, x);
-      if (pc.periodic) x = fma_t(-f, pc.z[i], x);
-      col[(long long)i * nl] = x;
-    }
+    part_update<T>(col, nl, pc, s, e, Lp, Fn, f);
   }
 }
 
@@ -368,6 +433,115 @@ __global__ void k_rhs_filter(DevGrid g, const double* __restrict__ U, LineBuf lb
       r[((long long)v * lb.m + i) * lb.nl + L] = b0 * w[4][v] + b1 * (w[5][v] + w[3][v]) + b2 * (w[6][v] + w[2][v]) +
                                                  b3 * (w[7][v] + w[1][v]) + b4 * (w[8][v] + w[0][v]);
   }
+}
+
+// ---------------------------------------------------------------- x-line right-hand sides
+// Along x (d = 0) the kernels above give consecutive threads consecutive
+// lines, i.e. rows of the grid nx apart: every stencil load touches its own
+// 32-byte sector.  k_rhs_xtile stages a tile of XT_L lines x XT_R rows through
+// shared memory instead: the stencil window of each line (the tile's rows plus
+// the reach of their stencils) is read along x, coalesced and once, and the
+// right-hand sides are written line-fastest, coalesced in the line buffer.
+// Each Tile type supplies the loads (ghosts resolved as in the kernels above)
+// and the row formula, the same expression as its per-row kernel.
+constexpr int XT_L = 16, XT_R = 32, XT_THREADS = 256;
+
+// H: reach of the interior rows' stencil, Tile::HC: reach of the closure rows.
+template <typename T, int NC, int H, class Tile>
+__global__ void __launch_bounds__(XT_THREADS) k_rhs_xtile(LineBuf lb, Tile tl, T* __restrict__ r) {
+  constexpr int HM = H > Tile::HC ? H : Tile::HC;
+  constexpr int W = XT_R + 2 * HM + 1;  // +1: spreads lines over banks
+  __shared__ T sw[NC][XT_L][W];
+  const long long L0 = (long long)blockIdx.x * XT_L;
+  const int i0 = blockIdx.y * XT_R;
+  const int i1 = min(lb.m, i0 + XT_R);
+  const int nlin = (int)min((long long)XT_L, lb.nl - L0);
+  // window of positions the tile's rows read
+  int ws = 0x7fffffff, we = -0x7fffffff;
+  for (int i = i0; i < i1; ++i) {
+    const bool closure = !lb.periodic && (i == 0 || i == lb.m - 1);
+    const int pos = lb.periodic ? i : lb.lo + i;
+    const int h = closure ? Tile::HC : H;
+    ws = min(ws, pos - h);
+    we = max(we, pos + h);
+  }
+  const int wn = we - ws + 1;
+  for (int e = threadIdx.x; e < nlin * wn; e += XT_THREADS) {
+    const int l = e / wn, p = e - l * wn;
+    int c[3] = {0, 0, 0};
+    lb.coords(L0 + l, c);
+    c[0] = ws + p;
+    T w[NC];
+    tl.load(c, w);
+#pragma unroll
+    for (int v = 0; v < NC; ++v) sw[v][l][p] = w[v];
+  }
+  __syncthreads();
+  const int l = threadIdx.x % XT_L;
+  if (l >= nlin) return;
+  for (int i = i0 + threadIdx.x / XT_L; i < i1; i += XT_THREADS / XT_L) {
+    const bool closure = !lb.periodic && (i == 0 || i == lb.m - 1);
+    const int p = (lb.periodic ? i : lb.lo + i) - ws;
+#pragma unroll
+    for (int v = 0; v < NC; ++v)
+      if (v < tl.nc) r[((long long)v * lb.m + i) * lb.nl + L0 + l] = tl.row(&sw[v][l][0], p, closure);
+  }
+}
+
+// Implicit filter of the conserved state (the formula of k_rhs_filter).
+template <int ND>
+struct XTileFilter {
+  DevGrid g;
+  const double* U;
+  double b0, b1, b2, b3, b4;
+  int nc;
+  static constexpr int HC = 0;
+  __device__ void load(const int* c, double* w) const { load_state<ND, true>(g, U, c[0], c[1], c[2], w); }
+  __device__ double row(const double* w, int p, bool closure) const {
+    if (closure) return w[p];
+    return b0 * w[p] + b1 * (w[p + 1] + w[p - 1]) + b2 * (w[p + 2] + w[p - 2]) + b3 * (w[p + 3] + w[p - 3]) +
+           b4 * (w[p + 4] + w[p - 4]);
+  }
+};
+
+// MIG4 gradients of the primitives (the formula of k_rhs_mig4).
+template <int ND, typename TW, typename TR>
+struct XTileMig4 {
+  DevGrid g;
+  const TW* W;
+  int nc;
+  static constexpr int HC = 2;
+  __device__ void load(const int* c, TR* w) const { load_state<ND, false, TW, TR>(g, W, c[0], c[1], c[2], w); }
+  __device__ TR row(const TR* w, int p, bool closure) const {
+    if (closure) return d4(w[p - 2], w[p - 1], w[p + 1], w[p + 2]);
+    return TR(0.75) * (w[p + 1] - w[p - 1]);
+  }
+};
+
+// C6 derivatives of nc components held on a box (the formula of k_rhs_c6).
+template <typename T, int NC>
+struct XTileC6 {
+  const T* f;
+  Box fb;
+  long long fs;
+  int nc;
+  static constexpr int HC = 2;
+  __device__ void load(const int* c, T* w) const {
+    const long long q = fb.at(c[0], c[1], c[2]);
+#pragma unroll
+    for (int v = 0; v < NC; ++v) w[v] = v < nc ? f[v * fs + q] : T(0);
+  }
+  __device__ T row(const T* w, int p, bool closure) const {
+    if (closure) return d4(w[p - 2], w[p - 1], w[p + 1], w[p + 2]);
+    return T(7.0 / 9.0) * (w[p + 1] - w[p - 1]) + T(1.0 / 36.0) * (w[p + 2] - w[p - 2]);
+  }
+};
+
+// Use the staged form for x lines when a tile's lines are all there to share it.
+__host__ __forceinline__ bool use_xtile(const LineBuf& lb) { return lb.d == 0 && lb.nl >= XT_L; }
+
+__host__ __forceinline__ dim3 xtile_grid(const LineBuf& lb) {
+  return dim3((unsigned)((lb.nl + XT_L - 1) / XT_L), (unsigned)((lb.m + XT_R - 1) / XT_R));
 }
 
 // Filtered line values back into the interior of the state.
