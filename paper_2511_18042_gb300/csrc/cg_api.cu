@@ -659,13 +659,13 @@ static void launch_lines(const LineJob<T>* jobs, int n, cudaStream_t st) {
   k_thomas_jobs<T><<<(unsigned)((cols + 31) / 32), 32, 0, st>>>(J);
 }
 
-// Right-hand sides of the compact line systems: x lines staged through shared
-// memory (k_rhs_xtile), the others by the per-row kernels.
+// Right-hand sides of the compact line systems: staged through shared memory
+// (k_rhs_tile), or by the per-row kernels when there are too few lines.
 template <int ND, typename T>
 static void launch_rhs_c6(const T* f, Box fb, int nc, const LineBuf& lb, T* r, cudaStream_t st) {
-  if (use_xtile(lb)) {
+  if (use_tile(lb)) {
     using Tl = XTileC6<T, ND + 3>;
-    k_rhs_xtile<T, ND + 3, 2, Tl><<<xtile_grid(lb), XT_THREADS, 0, st>>>(lb, Tl{f, fb, fb.size(), nc}, r);
+    k_rhs_tile<T, ND + 3, 2, Tl><<<tile_grid(lb), XT_THREADS, 0, st>>>(lb, Tl{f, fb, fb.size(), nc}, r);
   } else {
     k_rhs_c6<T><<<grid_blocks((long long)lb.m * lb.nl, 256), 256, 0, st>>>(f, fb, nc, lb, r);
   }
@@ -673,9 +673,9 @@ static void launch_rhs_c6(const T* f, Box fb, int nc, const LineBuf& lb, T* r, c
 
 template <int ND, typename TW, typename TR>
 static void launch_rhs_mig4(const DevGrid& g, const TW* W, const LineBuf& lb, TR* r, cudaStream_t st) {
-  if (use_xtile(lb)) {
+  if (use_tile(lb)) {
     using Tl = XTileMig4<ND, TW, TR>;
-    k_rhs_xtile<TR, ND + 2, 1, Tl><<<xtile_grid(lb), XT_THREADS, 0, st>>>(lb, Tl{g, W, ND + 2}, r);
+    k_rhs_tile<TR, ND + 2, 1, Tl><<<tile_grid(lb), XT_THREADS, 0, st>>>(lb, Tl{g, W, ND + 2}, r);
   } else {
     k_rhs_mig4<ND, TW, TR><<<grid_blocks((long long)lb.m * lb.nl, 256), 256, 0, st>>>(g, W, lb, r);
   }
@@ -684,9 +684,9 @@ static void launch_rhs_mig4(const DevGrid& g, const TW* W, const LineBuf& lb, TR
 template <int ND>
 static void launch_rhs_filter(const DevGrid& g, const double* U, const LineBuf& lb, const double b[5], double* r,
                               cudaStream_t st) {
-  if (use_xtile(lb)) {
+  if (use_tile(lb)) {
     using Tl = XTileFilter<ND>;
-    k_rhs_xtile<double, ND + 2, 4, Tl><<<xtile_grid(lb), XT_THREADS, 0, st>>>(
+    k_rhs_tile<double, ND + 2, 4, Tl><<<tile_grid(lb), XT_THREADS, 0, st>>>(
         lb, Tl{g, U, b[0], b[1], b[2], b[3], b[4], ND + 2}, r);
   } else {
     k_rhs_filter<ND><<<grid_blocks((long long)lb.m * lb.nl, 256), 256, 0, st>>>(g, U, lb, b[0], b[1], b[2], b[3],

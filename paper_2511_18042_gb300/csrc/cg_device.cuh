@@ -234,8 +234,9 @@ struct LineBuf {
   int d, lo, m, n, periodic;
   int off[3], ext[3];  // box of the other directions (entry d unused)
   long long nl;        // lines
+  // lines ordered with the lower other direction fastest (x where it is one)
   __host__ __device__ long long line(const int* c) const {
-    int o1 = (d + 1) % 3, o2 = (d + 2) % 3;
+    int o1 = d == 0 ? 1 : 0, o2 = d == 2 ? 1 : 2;
     return (long long)(c[o1] + off[o1]) + (long long)ext[o1] * (long long)(c[o2] + off[o2]);
   }
   __device__ long long at(int comp, int pos, const int* c) const {
@@ -249,7 +250,7 @@ struct LineBuf {
     return ((long long)comp * m + row) * nl + line(c);
   }
   __device__ void coords(long long L, int* c) const {
-    int o1 = (d + 1) % 3, o2 = (d + 2) % 3;
+    int o1 = d == 0 ? 1 : 0, o2 = d == 2 ? 1 : 2;
     c[o1] = (int)(L % ext[o1]) - off[o1];
     c[o2] = (int)(L / ext[o1]) - off[o2];
   }

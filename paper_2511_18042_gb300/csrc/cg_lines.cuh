@@ -94,10 +94,9 @@ __device__ __forceinline__ T thomas_forward(T* __restrict__ col, long long nl, c
 }
 
 // x_i = dp_i - cp_i x_{i+1} for i = i1, i1-1, ..., i0, in place; returns x_{i0}.
-template <typename T>
+template <typename T, int B = kRowBatch>
 __device__ __forceinline__ T thomas_backward(T* __restrict__ col, long long nl, const T* __restrict__ cp,
                                              int i0, int i1, T xv) {
-  constexpr int B = kRowBatch;
   const int nfull = (i1 - i0 + 1) / B;
   T v[B], c[B];
   if (nfull > 0) {
@@ -211,46 +210,34 @@ struct PartJobsT {
 
 // Partitioned forward elimination inside one chunk: y_i = (r_i - aL_i y_{i-1})
 // rd_i for i in [i0, i1), y_{i0-1} = 0 (aL is 0 at the chunk start), in place;
-// returns y_{i1-1}.  Batched like thomas_forward.
-template <typename T>
+// returns y_{i1-1}.  Batched like thomas_forward (the column values only: the
+// coefficients are shared by the block's columns and stay in cache).
+template <typename T, int B>
 __device__ __forceinline__ T part_forward(T* __restrict__ col, long long nl, const T* __restrict__ aL,
                                           const T* __restrict__ rd, int i0, int i1) {
-  constexpr int B = kRowBatch;
   const int nfull = (i1 - i0) / B;
   T y = T(0);
-  T v[B], al[B], dn[B];
+  T v[B];
   if (nfull > 0) {
 #pragma unroll
-    for (int k = 0; k < B; ++k) {
-      v[k] = col[(long long)(i0 + k) * nl];
-      al[k] = aL[i0 + k];
-      dn[k] = rd[i0 + k];
-    }
+    for (int k = 0; k < B; ++k) v[k] = col[(long long)(i0 + k) * nl];
   }
   for (int b = 0; b < nfull; ++b) {
     const int base = i0 + b * B;
     const bool more = b + 1 < nfull;
-    T nv[B], na[B], nd[B];
+    T nv[B];
     if (more) {
 #pragma unroll
-      for (int k = 0; k < B; ++k) {
-        nv[k] = col[(long long)(base + B + k) * nl];
-        na[k] = aL[base + B + k];
-        nd[k] = rd[base + B + k];
-      }
+      for (int k = 0; k < B; ++k) nv[k] = col[(long long)(base + B + k) * nl];
     }
 #pragma unroll
     for (int k = 0; k < B; ++k) {
-      y = fma_t(-al[k], y, v[k]) * dn[k];
+      y = fma_t(-aL[base + k], y, v[k]) * rd[base + k];
       col[(long long)(base + k) * nl] = y;
     }
     if (more) {
 #pragma unroll
-      for (int k = 0; k < B; ++k) {
-        v[k] = nv[k];
-        al[k] = na[k];
-        dn[k] = nd[k];
-      }
+      for (int k = 0; k < B; ++k) v[k] = nv[k];
     }
   }
   for (int i = i0 + nfull * B; i < i1; ++i) {
@@ -262,10 +249,9 @@ __device__ __forceinline__ T part_forward(T* __restrict__ col, long long nl, con
 
 // Partitioned update inside one chunk: x_i = y_i - V_i L_prev - W_i F_next
 // (- f z_i on a cyclic line) for i in [i0, i1), in place, B rows per batch.
-template <typename T>
+template <typename T, int B>
 __device__ __forceinline__ void part_update(T* __restrict__ col, long long nl, const PartCoefT<T>& pc, int i0,
                                             int i1, T Lp, T Fn, T f) {
-  constexpr int B = kRowBatch;
   int i = i0;
   for (; i + B <= i1; i += B) {
     T v[B];
@@ -293,6 +279,8 @@ template <typename T>
 __global__ void __launch_bounds__(1024) k_tri_part(PartJobsT<T> J) {
   __shared__ T sYF[kPartMax][32], sYL[kPartMax][32], sF[kPartMax][32], sL[kPartMax][32];
   __shared__ T sFact[32];
+  // rows per batch: up to 1024 threads leave 64 registers a thread
+  constexpr int PB = 4;
   const int lane = threadIdx.x, k = threadIdx.y;
   const long long g0 = (long long)blockIdx.x * 32;
   int j = 0;
@@ -305,9 +293,9 @@ __global__ void __launch_bounds__(1024) k_tri_part(PartJobsT<T> J) {
   const int s = k * pc.q, e = min(pc.m, s + pc.q);
   const bool mine = active && k < pc.P && s < e;
   if (mine) {
-    T y = part_forward<T>(col, nl, pc.aL, pc.rd, s, e);
+    T y = part_forward<T, PB>(col, nl, pc.aL, pc.rd, s, e);
     sYL[k][lane] = y;
-    y = thomas_backward<T>(col, nl, pc.cp, s, e - 2, y);
+    y = thomas_backward<T, PB>(col, nl, pc.cp, s, e - 2, y);
     sYF[k][lane] = y;
   }
   __syncthreads();
@@ -338,7 +326,7 @@ __global__ void __launch_bounds__(1024) k_tri_part(PartJobsT<T> J) {
     const T Lp = k > 0 ? sL[k - 1][lane] : T(0);
     const T Fn = k + 1 < pc.P ? sF[k + 1][lane] : T(0);
     const T f = pc.periodic ? sFact[lane] : T(0);
-    part_update<T>(col, nl, pc, s, e, Lp, Fn, f);
+    part_update<T, PB>(col, nl, pc, s, e, Lp, Fn, f);
   }
 }
 
@@ -435,20 +423,22 @@ __global__ void k_rhs_filter(DevGrid g, const double* __restrict__ U, LineBuf lb
   }
 }
 
-// ---------------------------------------------------------------- x-line right-hand sides
-// Along x (d = 0) the kernels above give consecutive threads consecutive
-// lines, i.e. rows of the grid nx apart: every stencil load touches its own
-// 32-byte sector.  k_rhs_xtile stages a tile of XT_L lines x XT_R rows through
-// shared memory instead: the stencil window of each line (the tile's rows plus
-// the reach of their stencils) is read along x, coalesced and once, and the
-// right-hand sides are written line-fastest, coalesced in the line buffer.
-// Each Tile type supplies the loads (ghosts resolved as in the kernels above)
-// and the row formula, the same expression as its per-row kernel.
+// ---------------------------------------------------------------- staged right-hand sides
+// The kernels above load every stencil point of every row from memory, and
+// along x (d = 0) consecutive threads take consecutive lines, i.e. grid rows
+// nx apart, so that each load touches its own 32-byte sector.  k_rhs_tile
+// stages a tile of XT_L lines x XT_R rows through shared memory instead: the
+// stencil window of each line (the tile's rows plus the reach of their
+// stencils) is read once, coalesced (along x for x lines, across the lines,
+// which run along x, otherwise), and the right-hand sides are written
+// line-fastest, coalesced in the line buffer.  Each Tile type supplies the
+// loads (ghosts resolved as in the kernels above) and the row formula, the
+// same expression as its per-row kernel.
 constexpr int XT_L = 16, XT_R = 32, XT_THREADS = 256;
 
 // H: reach of the interior rows' stencil, Tile::HC: reach of the closure rows.
 template <typename T, int NC, int H, class Tile>
-__global__ void __launch_bounds__(XT_THREADS) k_rhs_xtile(LineBuf lb, Tile tl, T* __restrict__ r) {
+__global__ void __launch_bounds__(XT_THREADS) k_rhs_tile(LineBuf lb, Tile tl, T* __restrict__ r) {
   constexpr int HM = H > Tile::HC ? H : Tile::HC;
   constexpr int W = XT_R + 2 * HM + 1;  // +1: spreads lines over banks
   __shared__ T sw[NC][XT_L][W];
@@ -466,11 +456,13 @@ __global__ void __launch_bounds__(XT_THREADS) k_rhs_xtile(LineBuf lb, Tile tl, T
     we = max(we, pos + h);
   }
   const int wn = we - ws + 1;
+  const bool along = lb.d == 0;  // window positions contiguous in memory
   for (int e = threadIdx.x; e < nlin * wn; e += XT_THREADS) {
-    const int l = e / wn, p = e - l * wn;
+    const int l = along ? e / wn : e % nlin;
+    const int p = along ? e - l * wn : e / nlin;
     int c[3] = {0, 0, 0};
     lb.coords(L0 + l, c);
-    c[0] = ws + p;
+    c[lb.d] = ws + p;
     T w[NC];
     tl.load(c, w);
 #pragma unroll
@@ -537,10 +529,10 @@ struct XTileC6 {
   }
 };
 
-// Use the staged form for x lines when a tile's lines are all there to share it.
-__host__ __forceinline__ bool use_xtile(const LineBuf& lb) { return lb.d == 0 && lb.nl >= XT_L; }
+// The staged form when a tile's lines are all there to share it.
+__host__ __forceinline__ bool use_tile(const LineBuf& lb) { return lb.nl >= XT_L; }
 
-__host__ __forceinline__ dim3 xtile_grid(const LineBuf& lb) {
+__host__ __forceinline__ dim3 tile_grid(const LineBuf& lb) {
   return dim3((unsigned)((lb.nl + XT_L - 1) / XT_L), (unsigned)((lb.m + XT_R - 1) / XT_R));
 }
 
