@@ -170,54 +170,63 @@ __global__ void k_lad_coef(DevGrid g, const T* __restrict__ W, const T* __restri
       T w1 = G(2, 1) - G(1, 2), w2 = G(0, 2) - G(2, 0), w3 = G(1, 0) - G(0, 1);
       curl2 = w1 * w1 + w2 * w2 + w3 * w3;
     }
-    T heav = div < T(0) ? T(1) : T(0);
-    T fsw = heav * (div * div) / (div * div + curl2 + T(1e-32));
-    T gmr, gme;
+    // The switch of Eq. (4) is zero where the flow expands (div >= 0): there
+    // beta* is +0 whatever its other factors, so the switch's ratio, |grad rho|
+    // and the spacings Delta_beta (divisions and a square root, on the FP64
+    // pipe) are formed only where div < 0, each as in the full product.
+    const bool comp = div < T(0);
+    T fsw = T(0), gmr = T(0), gme;
+    if (comp) fsw = (div * div) / (div * div + curl2 + T(1e-32));
     if constexpr (sizeof(T) == 4) {
       // |grad rho| and |grad e| without squaring: in FP32 a square under
       // ~1e-38 flushes, and |x . grad| / (0 + 1e-32) would then inflate the
       // length scales Delta_beta, Delta_kappa far beyond the grid spacing
-      gmr = grad_norm<ND>(G(ND + 1, 0), G(ND + 1, ND > 1 ? 1 : 0), G(ND + 1, ND > 2 ? 2 : 0));
+      if (comp) gmr = grad_norm<ND>(G(ND + 1, 0), G(ND + 1, ND > 1 ? 1 : 0), G(ND + 1, ND > 2 ? 2 : 0));
       gme = grad_norm<ND>(G(ND + 2, 0), G(ND + 2, ND > 1 ? 1 : 0), G(ND + 2, ND > 2 ? 2 : 0));
     } else {
-      gmr = G(ND + 1, 0) * G(ND + 1, 0);
       gme = G(ND + 2, 0) * G(ND + 2, 0);
 #pragma unroll
-      for (int m = 1; m < ND; ++m) {
-        gmr = gmr + G(ND + 1, m) * G(ND + 1, m);
-        gme = gme + G(ND + 2, m) * G(ND + 2, m);
-      }
-      gmr = sqrt(gmr);
+      for (int m = 1; m < ND; ++m) gme = gme + G(ND + 2, m) * G(ND + 2, m);
       gme = sqrt(gme);
+      if (comp) {
+        gmr = G(ND + 1, 0) * G(ND + 1, 0);
+#pragma unroll
+        for (int m = 1; m < ND; ++m) gmr = gmr + G(ND + 1, m) * G(ND + 1, m);
+        gmr = sqrt(gmr);
+      }
     }
     T sb = T(0), sk = T(0);
 #pragma unroll
     for (int l = 0; l < ND; ++l) {
       long long st = l == 0 ? 1 : (l == 1 ? (long long)b3.ext[0] : (long long)b3.ext[0] * b3.ext[1]);
-      T d4d = (dv[e0 - 2 * st] + dv[e0 + 2 * st]) - T(4.0) * (dv[e0 - st] + dv[e0 + st]) + T(6.0) * div;
       long long fst = l == 0 ? 1 : (l == 1 ? (long long)fbx.ext[0] : (long long)fbx.ext[0] * fbx.ext[1]);
       const T* ev = fb + (ND + 2) * fs + fq;
       T d4e = (ev[-2 * fst] + ev[2 * fst]) - T(4.0) * (ev[-fst] + ev[fst]) + T(6.0) * ev[0];
-      T pr, pe;
+      // projections x_l . grad of rho (pr) and e (pe), x_l = dx/dxi_l
+      T pr = T(0), pe;
       if (CART) {
-        pr = T(g.ch[l]) * G(ND + 1, l);
+        if (comp) pr = T(g.ch[l]) * G(ND + 1, l);
         pe = T(g.ch[l]) * G(ND + 2, l);
       } else {
         long long pq = plin(g, c[0], c[1], c[2]);
-        pr = T(g.dxl[(l * ND + 0) * g.NP + pq]) * G(ND + 1, 0);
         pe = T(g.dxl[(l * ND + 0) * g.NP + pq]) * G(ND + 2, 0);
 #pragma unroll
-        for (int m = 1; m < ND; ++m) {
-          T x = T(g.dxl[(l * ND + m) * g.NP + pq]);
-          pr = pr + x * G(ND + 1, m);
-          pe = pe + x * G(ND + 2, m);
+        for (int m = 1; m < ND; ++m) pe = pe + T(g.dxl[(l * ND + m) * g.NP + pq]) * G(ND + 2, m);
+        if (comp) {
+          pr = T(g.dxl[(l * ND + 0) * g.NP + pq]) * G(ND + 1, 0);
+#pragma unroll
+          for (int m = 1; m < ND; ++m) pr = pr + T(g.dxl[(l * ND + m) * g.NP + pq]) * G(ND + 1, m);
         }
       }
-      T Db = fabs(pr) / (gmr + T(1e-32));
       T Dk = fabs(pe) / (gme + T(1e-32));
-      T tb = d4d * Db * Db, tk = d4e * Dk;
-      sb = (l == 0) ? tb : sb + tb;
+      T tk = d4e * Dk;
       sk = (l == 0) ? tk : sk + tk;
+      if (comp) {
+        T d4d = (dv[e0 - 2 * st] + dv[e0 + 2 * st]) - T(4.0) * (dv[e0 - st] + dv[e0 + st]) + T(6.0) * div;
+        T Db = fabs(pr) / (gmr + T(1e-32));
+        T tb = d4d * Db * Db;
+        sb = (l == 0) ? tb : sb + tb;
+      }
     }
     bt[q] = c_beta * rho * fsw * fabs(sb);
     kp[q] = c_kappa * (rho * cs / Tt) * fabs(sk);
