@@ -225,11 +225,17 @@ __host__ __device__ constexpr int sweep_smem_doubles() {
   return (ND + 2) * (SWEEP_TL + 9 + SWEEP_TL + 3 + SWEEP_TL + 1 + SWEEP_TL) * LW + (SWEEP_TL + 7) * LW;
 }
 
-// Blocks per SM the register budget is sized for: two, except the 3D
-// curvilinear FP64 sweep, whose frame and metric terms need more than the
-// 128 registers two blocks of 256 threads leave (one block, no spills).
+// Blocks per SM the register budget is sized for: two, except
+// * the 3D curvilinear FP64 sweep, whose frame and metric terms need more than
+//   the 128 registers two blocks of 256 threads leave (one block, no spills);
+// * the 1D/2D FP32 sweep, which is latency-bound at two blocks (16 warps an
+//   SM): four blocks (64 registers; up to 40 bytes a thread spill, to L1) took
+//   the triple point's mixed MEG6 step from 1.24 to 1.02 ms.  Its 3D form
+//   spills up to 156 bytes there and keeps two.
 template <int ND, bool CART, typename T>
-__host__ __device__ constexpr int sweep_min_blocks() { return (ND == 3 && !CART && sizeof(T) == 8) ? 1 : 2; }
+__host__ __device__ constexpr int sweep_min_blocks() {
+  return sizeof(T) == 8 ? ((ND == 3 && !CART) ? 1 : 2) : (ND <= 2 ? 4 : 2);
+}
 
 // T = double: FP64 form; T = float: mixed form (FP32 reconstruction and
 // fluxes from FP64 primitives; FP64 flux differences, residual and RK update).
