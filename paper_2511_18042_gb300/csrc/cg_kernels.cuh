@@ -52,12 +52,20 @@ __global__ void k_prim(DevGrid g, const double* __restrict__ U, TW* __restrict__
   constexpr int NV = ND + 2;
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < g.N;
        q += (long long)gridDim.x * blockDim.x) {
-    double Q[NV], w[NV];
+    double Q[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) Q[v] = U[v * g.N + q];
-    cons_to_prim<ND>(g.gm1, Q, w);
+    if constexpr (sizeof(TW) == 4) {
+      float w[NV];
+      cons_to_prim_mixed<ND>(g.gm1, Q, w);
 #pragma unroll
-    for (int v = 0; v < NV; ++v) W[v * g.N + q] = TW(w[v]);
+      for (int v = 0; v < NV; ++v) W[v * g.N + q] = w[v];
+    } else {
+      double w[NV];
+      cons_to_prim<ND>(g.gm1, Q, w);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) W[v * g.N + q] = w[v];
+    }
   }
 }
 
@@ -482,10 +490,15 @@ __global__ void k_cfl_max(DevGrid g, const double* __restrict__ U, unsigned long
   double best = 0.0;
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < g.N;
        q += (long long)gridDim.x * blockDim.x) {
-    double Q[NV], w[NV];
+    double Q[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) Q[v] = U[v * g.N + q];
-    cons_to_prim<ND>(g.gm1, Q, w);
+    T w[NV];
+    if constexpr (sizeof(T) == 4) {
+      cons_to_prim_mixed<ND>(g.gm1, Q, w);
+    } else {
+      cons_to_prim<ND>(g.gm1, Q, w);
+    }
     T cs = sqrt(T(g.gamma) * T(w[IP]) / T(w[0]));
     T s = T(0);
     T J;
