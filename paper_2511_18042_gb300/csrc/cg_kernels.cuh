@@ -233,16 +233,17 @@ __host__ __device__ constexpr int sweep_smem_doubles() {
   return (ND + 2) * (SWEEP_TL + 9 + SWEEP_TL + 3 + SWEEP_TL + 1 + SWEEP_TL) * LW + (SWEEP_TL + 7) * LW;
 }
 
-// Blocks per SM the register budget is sized for: two, except
-// * the 3D curvilinear FP64 sweep, whose frame and metric terms need more than
-//   the 128 registers two blocks of 256 threads leave (one block, no spills);
-// * the 1D/2D FP32 sweep, which is latency-bound at two blocks (16 warps an
-//   SM): four blocks (64 registers; up to 40 bytes a thread spill, to L1) took
-//   the triple point's mixed MEG6 step from 1.24 to 1.02 ms.  Its 3D form
-//   spills up to 156 bytes there and keeps two.
+// Blocks per SM the register budget is sized for (256 threads a block):
+// * FP64: two (128 registers).  The 3D curvilinear sweep, with its frame and
+//   metric terms, spills about 300 bytes a thread there, to L1; at one block
+//   (8 warps an SM) it did not spill but ran 9-12 % slower on the 3D ramp.
+// * 1D/2D FP32: four (64 registers; up to 40 bytes a thread spill).  The
+//   kernel is latency-bound at two blocks, 16 warps an SM: four took the
+//   triple point's mixed MEG6 step from 1.24 to 1.02 ms.
+// * 3D FP32: two (it spills up to 156 bytes at four).
 template <int ND, bool CART, typename T>
 __host__ __device__ constexpr int sweep_min_blocks() {
-  return sizeof(T) == 8 ? ((ND == 3 && !CART) ? 1 : 2) : (ND <= 2 ? 4 : 2);
+  return sizeof(T) == 8 ? 2 : (ND <= 2 ? 4 : 2);
 }
 
 // T = double: FP64 form; T = float: mixed form (FP32 reconstruction and
