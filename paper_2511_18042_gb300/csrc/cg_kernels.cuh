@@ -240,10 +240,11 @@ __host__ __device__ constexpr int sweep_smem_doubles() {
 // * 1D/2D FP32: four (64 registers; up to 40 bytes a thread spill).  The
 //   kernel is latency-bound at two blocks, 16 warps an SM: four took the
 //   triple point's mixed MEG6 step from 1.24 to 1.02 ms.
-// * 3D FP32: two (it spills up to 156 bytes at four).
+// * 3D FP32: three (85 registers; up to 112 bytes a thread spill): on the 3D
+//   ramp 10-15 % faster than two.
 template <int ND, bool CART, typename T>
 __host__ __device__ constexpr int sweep_min_blocks() {
-  return sizeof(T) == 8 ? 2 : (ND <= 2 ? 4 : 2);
+  return sizeof(T) == 8 ? 2 : (ND <= 2 ? 4 : 3);
 }
 
 // T = double: FP64 form; T = float: mixed form (FP32 reconstruction and
