@@ -44,14 +44,28 @@ struct StageArgs {
   const float* Gdf;           // mixed form: the compact gradients in FP32
 };
 
+// ---------------------------------------------------------------- block coordinates
+// Each stage kernel is a body over the coordinates of its block plus a thin
+// __global__ wrapper that passes the hardware ones.  The batched stage
+// (cg_batch_stage.cu) runs the same bodies with a member's share of one
+// persistent grid instead.
+struct VBlock {
+  unsigned x, y, z;     // block index
+  unsigned gx, gy, gz;  // grid size in blocks
+};
+
+__device__ __forceinline__ VBlock hw_block() {
+  return VBlock{blockIdx.x, blockIdx.y, blockIdx.z, gridDim.x, gridDim.y, gridDim.z};
+}
+
 // ---------------------------------------------------------------- primitives
 // Primitives recovered in FP64 (p = (gamma-1)(E - rho|u|^2/2)); stored as TW
 // (float for the mixed form's FP32 consumers).
 template <int ND, typename TW = double>
-__global__ void k_prim(DevGrid g, const double* __restrict__ U, TW* __restrict__ W) {
+__device__ __forceinline__ void k_prim_body(const VBlock& vb, DevGrid g, const double* __restrict__ U, TW* __restrict__ W) {
   constexpr int NV = ND + 2;
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < g.N;
-       q += (long long)gridDim.x * blockDim.x) {
+  for (long long q = vb.x * (long long)blockDim.x + threadIdx.x; q < g.N;
+       q += (long long)vb.gx * blockDim.x) {
     double Q[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) Q[v] = U[v * g.N + q];
@@ -69,6 +83,11 @@ __global__ void k_prim(DevGrid g, const double* __restrict__ U, TW* __restrict__
   }
 }
 
+template <int ND, typename TW = double>
+__global__ void k_prim(DevGrid g, const double* __restrict__ U, TW* __restrict__ W) {
+  k_prim_body<ND, TW>(hw_block(), g, U, W);
+}
+
 // ---------------------------------------------------------------- sensor
 // Omega^d = phi * zeta on the box [-4, n+3]: phi the largest normalised
 // pressure second difference over the directions, zeta a Ducros ratio of the
@@ -76,14 +95,14 @@ __global__ void k_prim(DevGrid g, const double* __restrict__ U, TW* __restrict__
 // T = double: FP64 parity form; T = float: the mixed form's FP32 sensor
 // (FP64 primitives and gradients read, converted once).
 template <int ND, bool CART, bool COMPACT, typename T = double>
-__global__ void k_omega(DevGrid g, const T* __restrict__ W, const T* __restrict__ G0,
+__device__ __forceinline__ void k_omega_body(const VBlock& vb, DevGrid g, const T* __restrict__ W, const T* __restrict__ G0,
                         const T* __restrict__ G1, const T* __restrict__ G2, LineBuf gb0,
                         LineBuf gb1, LineBuf gb2, double* __restrict__ om, Box ob, const int* guard, int want) {
   constexpr int NV = ND + 2, IP = ND + 1;
   if (guard && *guard != want) return;
   long long tot = ob.size();
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
-       e += (long long)gridDim.x * blockDim.x) {
+  for (long long e = vb.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)vb.gx * blockDim.x) {
     int c[3];
     long long r = e;
     c[0] = (int)(r % ob.ext[0]) - ob.off[0];
@@ -201,6 +220,13 @@ __global__ void k_omega(DevGrid g, const T* __restrict__ W, const T* __restrict_
   }
 }
 
+template <int ND, bool CART, bool COMPACT, typename T = double>
+__global__ void k_omega(DevGrid g, const T* __restrict__ W, const T* __restrict__ G0,
+                        const T* __restrict__ G1, const T* __restrict__ G2, LineBuf gb0,
+                        LineBuf gb1, LineBuf gb2, double* __restrict__ om, Box ob, const int* guard, int want) {
+  k_omega_body<ND, CART, COMPACT, T>(hw_block(), g, W, G0, G1, G2, gb0, gb1, gb2, om, ob, guard, want);
+}
+
 // ---------------------------------------------------------------- compact gradients
 // Tridiagonal (MIG4: 1/4, 1, 1/4) first derivative of the primitives along d,
 // one thread per (line, variable), Thomas elimination with the line-independent
@@ -254,7 +280,7 @@ __host__ __device__ constexpr int sweep_min_blocks() {
 // 2: FP32): the code is the same, the compilation flags differ, and distinct
 // instantiations keep the units' kernels apart.
 template <int ND, int DIR, bool CART, bool COMPACT, typename T, int LW, int UNIT>
-__global__ void __launch_bounds__(256, sweep_min_blocks<ND, CART, T>()) k_gbr_sweep(DevGrid g, GbrCfg q, StageArgs A) {
+__device__ __forceinline__ void k_gbr_sweep_body(const VBlock& vb, DevGrid g, GbrCfg q, StageArgs A) {
   static_assert((SWEEP_TL * LW) % 256 == 0, "a tile must hold a multiple of the block's threads");
   constexpr int NV = ND + 2, IP = ND + 1;
   constexpr bool MIX = sizeof(T) == 4;
@@ -277,25 +303,25 @@ __global__ void __launch_bounds__(256, sweep_min_blocks<ND, CART, T>()) k_gbr_sw
   int i0, lc1 = 0, lc2 = 0;  // lc1/lc2: coordinates of the other dims for line 0
   long long nlines;
   if (DIR == 0) {
-    i0 = blockIdx.x * (TL - 1);
+    i0 = vb.x * (TL - 1);
     nlines = (long long)g.n[1] * g.n[2];
   } else {
-    i0 = blockIdx.y * (TL - 1);
+    i0 = vb.y * (TL - 1);
     nlines = 0;
   }
   // coordinates of line l (the two other directions)
   auto line_coords = [&](int l, int* c) -> bool {
     if (DIR == 0) {
-      long long L = (long long)blockIdx.y * LW + l;
+      long long L = (long long)vb.y * LW + l;
       if (L >= nlines) return false;
       c[1] = (int)(L % g.n[1]);
       c[2] = (int)(L / g.n[1]);
     } else {
-      int x = blockIdx.x * LW + l;
+      int x = vb.x * LW + l;
       if (x >= g.n[0]) return false;
       c[0] = x;
       int o = DIR == 1 ? 2 : 1;
-      c[o] = blockIdx.z;
+      c[o] = vb.z;
     }
     return true;
   };
@@ -483,15 +509,20 @@ __global__ void __launch_bounds__(256, sweep_min_blocks<ND, CART, T>()) k_gbr_sw
   }
 }
 
+template <int ND, int DIR, bool CART, bool COMPACT, typename T, int LW, int UNIT>
+__global__ void __launch_bounds__(256, sweep_min_blocks<ND, CART, T>()) k_gbr_sweep(DevGrid g, GbrCfg q, StageArgs A) {
+  k_gbr_sweep_body<ND, DIR, CART, COMPACT, T, LW, UNIT>(hw_block(), g, q, A);
+}
+
 // ---------------------------------------------------------------- CFL
 // T = double: the exact FP64 rate.  T = float (mixed form): the primitives
 // (pressure recovery) in FP64, the sound speed and the spectral radii in FP32.
 template <int ND, bool CART, typename T = double>
-__global__ void k_cfl_max(DevGrid g, const double* __restrict__ U, unsigned long long* __restrict__ mx) {
+__device__ __forceinline__ void k_cfl_max_body(const VBlock& vb, DevGrid g, const double* __restrict__ U, unsigned long long* __restrict__ mx) {
   constexpr int NV = ND + 2, IP = ND + 1;
   double best = 0.0;
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < g.N;
-       q += (long long)gridDim.x * blockDim.x) {
+  for (long long q = vb.x * (long long)blockDim.x + threadIdx.x; q < g.N;
+       q += (long long)vb.gx * blockDim.x) {
     double Q[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) Q[v] = U[v * g.N + q];
@@ -545,8 +576,13 @@ __global__ void k_cfl_max(DevGrid g, const double* __restrict__ U, unsigned long
   }
 }
 
+template <int ND, bool CART, typename T = double>
+__global__ void k_cfl_max(DevGrid g, const double* __restrict__ U, unsigned long long* __restrict__ mx) {
+  k_cfl_max_body<ND, CART, T>(hw_block(), g, U, mx);
+}
+
 // dt = cfl / max rate; with a final time: clip to t_end - t and advance t.
-static __global__ void k_cfl_finish(const unsigned long long* mx, double cfl, double* dt, double* t, double t_end) {
+static __device__ __forceinline__ void k_cfl_finish_body(const VBlock& vb, const unsigned long long* mx, double cfl, double* dt, double* t, double t_end) {
   double m = __longlong_as_double((long long)*mx);
   double d = cfl / m;
   if (t) {
@@ -556,6 +592,10 @@ static __global__ void k_cfl_finish(const unsigned long long* mx, double cfl, do
     *t = tt + d;
   }
   *dt = d;
+}
+
+static __global__ void k_cfl_finish(const unsigned long long* mx, double cfl, double* dt, double* t, double t_end) {
+  k_cfl_finish_body(hw_block(), mx, cfl, dt, t, t_end);
 }
 
 }  // namespace cgk

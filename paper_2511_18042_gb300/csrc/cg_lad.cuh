@@ -44,12 +44,13 @@ __device__ __forceinline__ void box_coords(const Box& b, long long e, int* c) {
   c[2] = (int)(r / b.ext[1]) - b.off[2];
 }
 
+// grid-stride loop over a box (in a kernel body: vb is the block's coordinates)
 #define BOX_LOOP(b, e) \
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (b).size(); e += (long long)gridDim.x * blockDim.x)
+  for (long long e = vb.x * (long long)blockDim.x + threadIdx.x; e < (b).size(); e += (long long)vb.gx * blockDim.x)
 
 // the LAD fields at every node of the box fbx (ghosts by the boundary rule)
 template <int ND, typename T = double>
-__global__ void k_lad_fieldbuf(DevGrid g, const T* __restrict__ W, T* __restrict__ f, Box fbx) {
+__device__ __forceinline__ void k_lad_fieldbuf_body(const VBlock& vb, DevGrid g, const T* __restrict__ W, T* __restrict__ f, Box fbx) {
   constexpr int NV = ND + 2, NF = ND + 3;
   long long fs = fbx.size();
   BOX_LOOP(fbx, e) {
@@ -63,10 +64,15 @@ __global__ void k_lad_fieldbuf(DevGrid g, const T* __restrict__ W, T* __restrict
   }
 }
 
+template <int ND, typename T = double>
+__global__ void k_lad_fieldbuf(DevGrid g, const T* __restrict__ W, T* __restrict__ f, Box fbx) {
+  k_lad_fieldbuf_body<ND, T>(hw_block(), g, W, f, fbx);
+}
+
 // Physical gradients and dilatation on b3.  E4 differences the field buffer;
 // C6 reads the compact derivatives from the line buffers df.
 template <int ND, bool CART, bool C6, typename T = double>
-__global__ void k_lad_grad(DevGrid g, const T* __restrict__ fb, Box fbx, const T* __restrict__ df0,
+__device__ __forceinline__ void k_lad_grad_body(const VBlock& vb, DevGrid g, const T* __restrict__ fb, Box fbx, const T* __restrict__ df0,
                            const T* __restrict__ df1, const T* __restrict__ df2, LineBuf lb0, LineBuf lb1,
                            LineBuf lb2, T* __restrict__ gr, T* __restrict__ dv, Box b3, const int* guard,
                            int want) {
@@ -127,6 +133,14 @@ __global__ void k_lad_grad(DevGrid g, const T* __restrict__ fb, Box fbx, const T
   }
 }
 
+template <int ND, bool CART, bool C6, typename T = double>
+__global__ void k_lad_grad(DevGrid g, const T* __restrict__ fb, Box fbx, const T* __restrict__ df0,
+                           const T* __restrict__ df1, const T* __restrict__ df2, LineBuf lb0, LineBuf lb1,
+                           LineBuf lb2, T* __restrict__ gr, T* __restrict__ dv, Box b3, const int* guard,
+                           int want) {
+  k_lad_grad_body<ND, CART, C6, T>(hw_block(), g, fb, fbx, df0, df1, df2, lb0, lb1, lb2, gr, dv, b3, guard, want);
+}
+
 // Euclidean norm of an FP32 gradient (ND components), overflow- and
 // underflow-safe through the CUDA library's hypot forms.
 template <int ND>
@@ -140,14 +154,14 @@ __device__ __forceinline__ float grad_norm(float a, float b, float c) {
 // beta* = C_beta rho f_sw |sum_l d4(div)_l Delta_{l,beta}^2|,
 // kappa* = C_kappa (rho c / T) |sum_l d4(e)_l Delta_{l,kappa}|.
 template <int ND, bool CART, typename T = double>
-__global__ void k_lad_coef(DevGrid g, const T* __restrict__ W, const T* __restrict__ fb, Box fbx,
+__device__ __forceinline__ void k_lad_coef_body(const VBlock& vb, DevGrid g, const T* __restrict__ W, const T* __restrict__ fb, Box fbx,
                            const T* __restrict__ gr, const T* __restrict__ dv, Box b3, double c_beta_d,
                            double c_kappa_d, T* __restrict__ bt, T* __restrict__ kp, const int* guard, int want) {
   const T c_beta = T(c_beta_d), c_kappa = T(c_kappa_d);
   constexpr int NV = ND + 2, IP = ND + 1;
   if (guard && *guard != want) return;
   long long bs = b3.size(), fs = fbx.size();
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < g.N; q += (long long)gridDim.x * blockDim.x) {
+  for (long long q = vb.x * (long long)blockDim.x + threadIdx.x; q < g.N; q += (long long)vb.gx * blockDim.x) {
     int c[3];
     c[0] = (int)(q % g.n[0]);
     c[1] = (int)((q / g.n[0]) % g.n[1]);
@@ -233,15 +247,22 @@ __global__ void k_lad_coef(DevGrid g, const T* __restrict__ W, const T* __restri
   }
 }
 
+template <int ND, bool CART, typename T = double>
+__global__ void k_lad_coef(DevGrid g, const T* __restrict__ W, const T* __restrict__ fb, Box fbx,
+                           const T* __restrict__ gr, const T* __restrict__ dv, Box b3, double c_beta_d,
+                           double c_kappa_d, T* __restrict__ bt, T* __restrict__ kp, const int* guard, int want) {
+  k_lad_coef_body<ND, CART, T>(hw_block(), g, W, fb, fbx, gr, dv, b3, c_beta_d, c_kappa_d, bt, kp, guard, want);
+}
+
 // truncated-Gaussian overbar along l (nine points, Cook & Cabot), two fields;
 // ghost values: periodic wrap, wall mirror, otherwise the boundary node.
 template <int ND, typename T = double>
-__global__ void k_gauss(DevGrid g, int l, const T* __restrict__ a, const T* __restrict__ b, T* __restrict__ ao,
+__device__ __forceinline__ void k_gauss_body(const VBlock& vb, DevGrid g, int l, const T* __restrict__ a, const T* __restrict__ b, T* __restrict__ ao,
                         T* __restrict__ bo, const int* guard, int want) {
   if (guard && *guard != want) return;
   const T A0 = T(3565.0 / 10368.0), A1 = T(3091.0 / 12960.0), A2 = T(1997.0 / 25920.0), A3 = T(149.0 / 12960.0),
           A4 = T(107.0 / 103680.0);
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < g.N; q += (long long)gridDim.x * blockDim.x) {
+  for (long long q = vb.x * (long long)blockDim.x + threadIdx.x; q < g.N; q += (long long)vb.gx * blockDim.x) {
     int c[3];
     c[0] = (int)(q % g.n[0]);
     c[1] = (int)((q / g.n[0]) % g.n[1]);
@@ -264,6 +285,12 @@ __global__ void k_gauss(DevGrid g, int l, const T* __restrict__ a, const T* __re
     bo[q] = A0 * b[s[4]] + A1 * (b[s[3]] + b[s[5]]) + A2 * (b[s[2]] + b[s[6]]) + A3 * (b[s[1]] + b[s[7]]) +
             A4 * (b[s[0]] + b[s[8]]);
   }
+}
+
+template <int ND, typename T = double>
+__global__ void k_gauss(DevGrid g, int l, const T* __restrict__ a, const T* __restrict__ b, T* __restrict__ ao,
+                        T* __restrict__ bo, const int* guard, int want) {
+  k_gauss_body<ND, T>(hw_block(), g, l, a, b, ao, bo, guard, want);
 }
 
 // Node fluxes along l at positions [-2, n+1] (interior lines).
@@ -384,7 +411,7 @@ __device__ __forceinline__ void nodeflux_at(const DevGrid& g, int l, const T* __
 }
 
 template <int ND, bool CART, int MODE, typename T = double>
-__global__ void k_lad_nodeflux(DevGrid g, int l, const T* __restrict__ W, const T* __restrict__ bt,
+__device__ __forceinline__ void k_lad_nodeflux_body(const VBlock& vb, DevGrid g, int l, const T* __restrict__ W, const T* __restrict__ bt,
                                const T* __restrict__ kp, const T* __restrict__ gr, const T* __restrict__ dv, Box b3,
                                T* __restrict__ Fn, Box fb, const int* guard, int want) {
   constexpr int NV = ND + 2;
@@ -398,6 +425,13 @@ __global__ void k_lad_nodeflux(DevGrid g, int l, const T* __restrict__ W, const 
 #pragma unroll
     for (int v = 0; v < NV; ++v) Fn[v * fs + e] = F[v];
   }
+}
+
+template <int ND, bool CART, int MODE, typename T = double>
+__global__ void k_lad_nodeflux(DevGrid g, int l, const T* __restrict__ W, const T* __restrict__ bt,
+                               const T* __restrict__ kp, const T* __restrict__ gr, const T* __restrict__ dv, Box b3,
+                               T* __restrict__ Fn, Box fb, const int* guard, int want) {
+  k_lad_nodeflux_body<ND, CART, MODE, T>(hw_block(), g, l, W, bt, kp, gr, dv, b3, Fn, fb, guard, want);
 }
 
 // Stage epilogue shared by the LAD divergence kernels: tot = acc + D (or D),
@@ -489,7 +523,7 @@ __global__ void k_lad_div(DevGrid g, int l, const T* __restrict__ Fn, Box fb, co
 // (with the sensor) Omega > threshold; counts troubled interior nodes and
 // sets flag[0] = 1 if any (the global decision of Algorithm 3).
 template <int ND, typename TW = double>
-__global__ void k_troubled(DevGrid g, const TW* __restrict__ W, double hr, double hp, const double* __restrict__ om,
+__device__ __forceinline__ void k_troubled_body(const VBlock& vb, DevGrid g, const TW* __restrict__ W, double hr, double hp, const double* __restrict__ om,
                            Box ob, double thr, unsigned char* __restrict__ tr, Box tb, int* flag,
                            unsigned long long* count) {
   constexpr int NV = ND + 2, IP = ND + 1;
@@ -513,10 +547,17 @@ __global__ void k_troubled(DevGrid g, const TW* __restrict__ W, double hr, doubl
   }
 }
 
+template <int ND, typename TW = double>
+__global__ void k_troubled(DevGrid g, const TW* __restrict__ W, double hr, double hp, const double* __restrict__ om,
+                           Box ob, double thr, unsigned char* __restrict__ tr, Box tb, int* flag,
+                           unsigned long long* count) {
+  k_troubled_body<ND, TW>(hw_block(), g, W, hr, hp, om, ob, thr, tr, tb, flag, count);
+}
+
 // Per-interface hybrid: LAD flux at interfaces i+1/2 (i in [-1, n-1]) in the
 // conservative E4 flux form h = 7/12 (F_i + F_{i+1}) - 1/12 (F_{i-1} + F_{i+2}).
 template <int ND, typename T = double>
-__global__ void k_lad_hflux(DevGrid g, int l, const T* __restrict__ Fn, Box fb, double* __restrict__ H, Box hb) {
+__device__ __forceinline__ void k_lad_hflux_body(const VBlock& vb, DevGrid g, int l, const T* __restrict__ Fn, Box fb, double* __restrict__ H, Box hb) {
   constexpr int NV = ND + 2;
   long long fs = fb.size(), hs = hb.size();
   long long st = l == 0 ? 1 : (l == 1 ? (long long)fb.ext[0] : (long long)fb.ext[0] * fb.ext[1]);
@@ -530,6 +571,11 @@ __global__ void k_lad_hflux(DevGrid g, int l, const T* __restrict__ Fn, Box fb, 
       H[v * hs + e] = (double)(T(7.0 / 12.0) * (f[q] + f[q + st]) - T(1.0 / 12.0) * (f[q - st] + f[q + 2 * st]));
     }
   }
+}
+
+template <int ND, typename T = double>
+__global__ void k_lad_hflux(DevGrid g, int l, const T* __restrict__ Fn, Box fb, double* __restrict__ H, Box hb) {
+  k_lad_hflux_body<ND, T>(hw_block(), g, l, Fn, fb, H, hb);
 }
 
 }  // namespace cgk
