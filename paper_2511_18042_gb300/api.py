@@ -258,6 +258,13 @@ class Batch:
         nat.check(nat.lib().cg_batch_autotune(self._h, _stream(stream), ctypes.byref(w)))
         return w.value
 
+    def path(self):
+        """("table", launches per step) on the work-table path, ("streams", None)
+        on the stream pool."""
+        p, n = ctypes.c_int(), ctypes.c_int()
+        nat.check(nat.lib().cg_batch_path(self._h, ctypes.byref(p), ctypes.byref(n)))
+        return ("table", n.value) if p.value == 1 else ("streams", None)
+
     def __del__(self):
         if getattr(self, "_h", None) and self._h.value:
             nat.lib().cg_batch_destroy(self._h)

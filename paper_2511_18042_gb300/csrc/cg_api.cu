@@ -18,6 +18,7 @@
 #include "../../include/cgflow.h"
 #include "cg_kernels.cuh"
 #include "cg_lad.cuh"
+#include "cg_batch_jobs.cuh"
 #include "cg_lines.cuh"
 #include "cg_metrics.cuh"
 #include "cg_sweep.h"

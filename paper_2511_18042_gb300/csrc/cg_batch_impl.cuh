@@ -60,6 +60,282 @@ int multi_step(cg_solver* const* solvers, double* const* states, int count, cuda
   return CG_OK;
 }
 
+// ---------------------------------------------------------------- work-table path
+// A batch of 2D Cartesian per-interface hybrids (inviscid, one tile shape)
+// advances phase by phase: each launch runs one phase of the RK stage for
+// every member (cg_batch_jobs.cuh), 15 launches for the first stage of a step
+// and 13 for the others, whatever the number of members.  The job arrays and
+// block offsets are built once on the host and kept in one device buffer.
+
+// one phase: device job array, block offsets (nm + 1) and total blocks
+struct TKind {
+  const void* jobs = nullptr;
+  const long long* off = nullptr;
+  long long total = 0;
+};
+
+struct BatchTable {
+  int state = 0;  // 0: not built, 1: built, -1: the batch does not qualify
+  int mixed = 0;
+  int lw[2] = {0, 0};
+  int nm = 0;
+  void* dmem = nullptr;
+  TKind zero1, zero23, cfl, fin, prim[3], omega, field, troubled, grad, coef, gauss[2], nodeflux[2], hflux[2];
+  TKind sweep[3][2];
+};
+
+static bool table_member_ok(const cg_solver* s, const cg_solver* s0, bool same_tiles = true) {
+  return s->nd == 2 && !s->dg.curv && s->p.scheme == CG_HYBRID && s->p.hybrid_mode == CG_HYBRID_CELL &&
+         !s->p.viscous && !s->iface_out && s->p.precision == s0->p.precision &&
+         (!same_tiles || (s->sweep_lw[0] == s0->sweep_lw[0] && s->sweep_lw[1] == s0->sweep_lw[1])) && s->lad.fb &&
+         s->lad.tr && s->hflux[0] && s->hflux[1];
+}
+
+// host staging of the job arrays and offsets, copied to the device at once
+struct TableBlob {
+  std::vector<char> bytes;
+  struct Rec { TKind* k; size_t jobs_at, off_at; long long total; };
+  std::vector<Rec> recs;
+  template <class Job>
+  void add(TKind* k, const std::vector<Job>& jobs, const std::vector<long long>& off) {
+    auto put = [&](const void* p, size_t n) {
+      size_t at = (bytes.size() + 255) / 256 * 256;
+      bytes.resize(at + n);
+      memcpy(bytes.data() + at, p, n);
+      return at;
+    };
+    Rec r{k, put(jobs.data(), sizeof(Job) * jobs.size()), put(off.data(), sizeof(long long) * off.size()), off.back()};
+    recs.push_back(r);
+  }
+};
+
+static long long table_blocks(long long work) { return work < 1 ? 1 : (work + BATCH_THREADS - 1) / BATCH_THREADS; }
+
+template <typename T>
+static int table_build_t(BatchTable& tb, cg_solver* const* sv, double* const* states, int nm) {
+  TableBlob blob;
+  auto offsets = [&](auto nblk) {
+    std::vector<long long> off(nm + 1, 0);
+    for (int m = 0; m < nm; ++m) off[m + 1] = off[m] + nblk(m);
+    return off;
+  };
+  auto one = [](int) { return 1LL; };
+  std::vector<JobZero> z1(nm), z23(nm);
+  std::vector<JobFinish> fin(nm);
+  std::vector<JobCfl<T>> cfl(nm);
+  for (int m = 0; m < nm; ++m) {
+    cg_solver* s = sv[m];
+    z1[m] = JobZero{s->cflmax, s->hyb_flag, s->hyb_count};
+    z23[m] = JobZero{nullptr, s->hyb_flag, s->hyb_count};
+    fin[m] = JobFinish{s->cflmax, s->p.cfl, s->dt};
+    cfl[m] = JobCfl<T>{s->dg, states[m], s->cflmax, (unsigned)table_blocks(s->N)};
+  }
+  blob.add(&tb.zero1, z1, offsets(one));
+  blob.add(&tb.zero23, z23, offsets(one));
+  blob.add(&tb.fin, fin, offsets(one));
+  blob.add(&tb.cfl, cfl, offsets([&](int m) { return (long long)cfl[m].nb; }));
+  for (int k = 0; k < 3; ++k) {
+    std::vector<JobPrim<T>> pr(nm);
+    for (int m = 0; m < nm; ++m) {
+      cg_solver* s = sv[m];
+      const double* Uc = k == 0 ? states[m] : (k == 1 ? s->U1 : s->U2);
+      pr[m] = JobPrim<T>{s->dg, Uc, reinterpret_cast<T*>(s->W), (unsigned)table_blocks(s->N)};
+    }
+    blob.add(&tb.prim[k], pr, offsets([&](int m) { return (long long)pr[m].nb; }));
+  }
+  std::vector<JobOmega<T>> om(nm);
+  std::vector<JobField<T>> fd(nm);
+  std::vector<JobTroubled<T>> tr(nm);
+  std::vector<JobGrad<T>> gr(nm);
+  std::vector<JobCoef<T>> co(nm);
+  std::vector<JobGauss<T>> ga[2] = {std::vector<JobGauss<T>>(nm), std::vector<JobGauss<T>>(nm)};
+  std::vector<JobNodeflux<T>> nf[2] = {std::vector<JobNodeflux<T>>(nm), std::vector<JobNodeflux<T>>(nm)};
+  std::vector<JobHflux<T>> hf[2] = {std::vector<JobHflux<T>>(nm), std::vector<JobHflux<T>>(nm)};
+  for (int m = 0; m < nm; ++m) {
+    cg_solver* s = sv[m];
+    LadBuffers& L = s->lad;
+    const T* W = reinterpret_cast<const T*>(s->W);
+    T* fb = reinterpret_cast<T*>(L.fb);
+    T* g = reinterpret_cast<T*>(L.gr);
+    T* dv = reinterpret_cast<T*>(L.dv);
+    T* bt[2] = {reinterpret_cast<T*>(L.bt[0]), reinterpret_cast<T*>(L.bt[1])};
+    T* kp[2] = {reinterpret_cast<T*>(L.kp[0]), reinterpret_cast<T*>(L.kp[1])};
+    JobOmega<T> o;
+    o.g = s->dg;
+    o.W = W;
+    for (int d = 0; d < 3; ++d) {
+      o.G[d] = reinterpret_cast<const T*>(s->G[d]);
+      o.gb[d] = s->gdLB[d];
+    }
+    o.om = s->om;
+    o.ob = s->omBox;
+    o.nb = (unsigned)table_blocks(s->omBox.size());
+    om[m] = o;
+    fd[m] = JobField<T>{s->dg, W, fb, L.fbx, (unsigned)table_blocks(L.fbx.size())};
+    tr[m] = JobTroubled<T>{s->dg, W, s->p.hyb_rho, s->p.hyb_p, s->p.hybrid_sensor ? s->om : nullptr, s->omBox,
+                           s->p.sensor_thresh, L.tr, L.tbox, s->hyb_flag, s->hyb_count,
+                           (unsigned)table_blocks(L.tbox.size())};
+    JobGrad<T> j;
+    j.g = s->dg;
+    j.fb = fb;
+    j.fbx = L.fbx;
+    for (int d = 0; d < 3; ++d) j.lb[d] = L.dfLB[d];
+    j.gr = g;
+    j.dv = dv;
+    j.b3 = L.b3;
+    j.nb = (unsigned)table_blocks(L.b3.size());
+    gr[m] = j;
+    co[m] = JobCoef<T>{s->dg, W, fb, L.fbx, g, dv, L.b3, s->p.c_beta, s->p.c_kappa, bt[0], kp[0],
+                       (unsigned)table_blocks(s->N)};
+    // the overbar along x then y: bt/kp 0 -> 1 -> 0
+    ga[0][m] = JobGauss<T>{s->dg, 0, bt[0], kp[0], bt[1], kp[1], (unsigned)table_blocks(s->N)};
+    ga[1][m] = JobGauss<T>{s->dg, 1, bt[1], kp[1], bt[0], kp[0], (unsigned)table_blocks(s->N)};
+    for (int l = 0; l < 2; ++l) {
+      nf[l][m] = JobNodeflux<T>{s->dg, l, W, bt[0], kp[0], g, dv, L.b3, reinterpret_cast<T*>(L.Fn), L.fbox[l],
+                                (unsigned)table_blocks(L.fbox[l].size())};
+      hf[l][m] = JobHflux<T>{s->dg, l, reinterpret_cast<const T*>(L.Fn), L.fbox[l], s->hflux[l], L.hbox[l],
+                             (unsigned)table_blocks(L.hbox[l].size())};
+    }
+  }
+  blob.add(&tb.omega, om, offsets([&](int m) { return (long long)om[m].nb; }));
+  blob.add(&tb.field, fd, offsets([&](int m) { return (long long)fd[m].nb; }));
+  blob.add(&tb.troubled, tr, offsets([&](int m) { return (long long)tr[m].nb; }));
+  blob.add(&tb.grad, gr, offsets([&](int m) { return (long long)gr[m].nb; }));
+  blob.add(&tb.coef, co, offsets([&](int m) { return (long long)co[m].nb; }));
+  for (int l = 0; l < 2; ++l) {
+    blob.add(&tb.gauss[l], ga[l], offsets([&](int m) { return (long long)ga[l][m].nb; }));
+    blob.add(&tb.nodeflux[l], nf[l], offsets([&](int m) { return (long long)nf[l][m].nb; }));
+    blob.add(&tb.hflux[l], hf[l], offsets([&](int m) { return (long long)hf[l][m].nb; }));
+  }
+  // sweeps: the stage arguments of the per-interface hybrid stage
+  for (int k = 0; k < 3; ++k)
+    for (int d = 0; d < 2; ++d) {
+      std::vector<SweepJob> sj(nm);
+      for (int m = 0; m < nm; ++m) {
+        cg_solver* s = sv[m];
+        double* U = states[m];
+        const double* Uc = k == 0 ? U : (k == 1 ? s->U1 : s->U2);
+        double* out = k == 0 ? s->U1 : (k == 1 ? s->U2 : U);
+        StageArgs A = base_args(s);
+        A.rk = 1;
+        A.stage = k + 1;
+        A.R = out;
+        A.Un = U;
+        A.Uc = Uc;
+        A.Uout = out;
+        A.mask = s->lad.tr;
+        A.tBox = s->lad.tbox;
+        A.first = d == 0;
+        A.last = d == 1;
+        A.hflux = s->hflux[d];
+        A.hBox = s->lad.hbox[d];
+        A.Gd = nullptr;
+        A.gdLB = s->gdLB[d];
+        A.iface_out = nullptr;
+        dim3 gd = sweep_grid_dims(d, s->sweep_lw[d], s->dg);
+        sj[m] = SweepJob{s->dg, gbr_cfg(s), A, gd.x, gd.y, gd.z};
+      }
+      blob.add(&tb.sweep[k][d], sj, offsets([&](int m) { return (long long)sj[m].gx * sj[m].gy * sj[m].gz; }));
+    }
+  void* dm = nullptr;
+  int rc = dalloc((char**)&dm, blob.bytes.size());
+  if (rc) return rc;
+  CG_CUDA(cudaMemcpy(dm, blob.bytes.data(), blob.bytes.size(), cudaMemcpyHostToDevice));
+  for (auto& r : blob.recs) {
+    r.k->jobs = (const char*)dm + r.jobs_at;
+    r.k->off = reinterpret_cast<const long long*>((const char*)dm + r.off_at);
+    r.k->total = r.total;
+  }
+  tb.dmem = dm;
+  return CG_OK;
+}
+
+static void table_free(BatchTable& tb) {
+  if (tb.dmem) cudaFree(tb.dmem);
+  tb = BatchTable();
+}
+
+// Builds the table if the batch qualifies (state 1), else marks it (-1).
+static int table_build(BatchTable& tb, const std::vector<cg_solver*>& sv, const std::vector<double*>& states) {
+  table_free(tb);
+  const int nm = (int)sv.size();
+  for (int m = 0; m < nm; ++m)
+    if (!table_member_ok(sv[m], sv[0])) {
+      tb.state = -1;
+      return CG_OK;
+    }
+  tb.nm = nm;
+  tb.mixed = sv[0]->p.precision == CG_MIXED;
+  tb.lw[0] = sv[0]->sweep_lw[0];
+  tb.lw[1] = sv[0]->sweep_lw[1];
+  int rc = tb.mixed ? table_build_t<float>(tb, sv.data(), states.data(), nm)
+                    : table_build_t<double>(tb, sv.data(), states.data(), nm);
+  if (rc) {
+    table_free(tb);
+    return rc;
+  }
+  tb.state = 1;
+  return CG_OK;
+}
+
+template <class Job>
+static int table_launch(const TKind& k, int nm, cudaStream_t st) {
+  k_batched<Job><<<(unsigned)k.total, BATCH_THREADS, 0, st>>>(static_cast<const Job*>(k.jobs), k.off, nm);
+  return CG_OK;
+}
+
+template <class J1, class J2>
+static int table_launch2(const TKind& a, const TKind& b, int nm, cudaStream_t st) {
+  k_batched2<J1, J2><<<(unsigned)(a.total + b.total), BATCH_THREADS, 0, st>>>(
+      static_cast<const J1*>(a.jobs), a.off, static_cast<const J2*>(b.jobs), b.off, nm);
+  return CG_OK;
+}
+
+// One RK3 step (with each member's CFL dt) of every member.
+template <typename T>
+static int table_step_t(const BatchTable& tb, cudaStream_t st) {
+  const int nm = tb.nm;
+  auto sweep = [&](int k, int d) -> int {
+    const TKind& K = tb.sweep[k][d];
+    const SweepJob* J = static_cast<const SweepJob*>(K.jobs);
+    int e = tb.mixed ? launch_sweep_batched_f32_2(d, tb.lw[d], J, K.off, nm, K.total, st)
+                     : launch_sweep_batched_f64_2(d, tb.lw[d], J, K.off, nm, K.total, st);
+    if (e) return fail(CG_ERR_CUDA, "batched sweep (dir %d): %s", d, cudaGetErrorString((cudaError_t)e));
+    return CG_OK;
+  };
+  for (int k = 0; k < 3; ++k) {
+    if (k == 0) {
+      table_launch<JobZero>(tb.zero1, nm, st);
+      table_launch<JobCfl<T>>(tb.cfl, nm, st);
+      table_launch<JobFinish>(tb.fin, nm, st);
+    } else {
+      table_launch<JobZero>(tb.zero23, nm, st);
+    }
+    table_launch<JobPrim<T>>(tb.prim[k], nm, st);
+    table_launch2<JobOmega<T>, JobField<T>>(tb.omega, tb.field, nm, st);
+    table_launch2<JobTroubled<T>, JobGrad<T>>(tb.troubled, tb.grad, nm, st);
+    table_launch<JobCoef<T>>(tb.coef, nm, st);
+    table_launch<JobGauss<T>>(tb.gauss[0], nm, st);
+    table_launch<JobGauss<T>>(tb.gauss[1], nm, st);
+    for (int l = 0; l < 2; ++l) {
+      table_launch<JobNodeflux<T>>(tb.nodeflux[l], nm, st);
+      table_launch<JobHflux<T>>(tb.hflux[l], nm, st);
+    }
+    int rc;
+    if ((rc = sweep(k, 0))) return rc;
+    if ((rc = sweep(k, 1))) return rc;
+  }
+  CG_CUDA(cudaGetLastError());
+  return CG_OK;
+}
+
+static int table_step(const BatchTable& tb, cudaStream_t st) {
+  return tb.mixed ? table_step_t<float>(tb, st) : table_step_t<double>(tb, st);
+}
+
+// launches of one table step
+static int table_launches(const BatchTable&) { return 3 * 13 + 2; }
+
 }  // namespace
 
 struct cg_batch {
@@ -69,6 +345,8 @@ struct cg_batch {
   cudaGraph_t graph = nullptr;
   int warm = 0;
   int width = kPoolStreams;  // streams the members are spread over
+  BatchTable table;          // work-table path (qualifying batches)
+  int use_table = 1;         // 0: the stream pool even where the table qualifies
 };
 
 extern "C" {
@@ -98,13 +376,23 @@ CG_API int cg_batch_create(int count, cg_solver* const* solvers, double* const* 
   return CG_OK;
 }
 
+// one eager step of the batch by its current path
+static int batch_once(cg_batch* b, cudaStream_t st) {
+  if (b->use_table && b->table.state == 1) return table_step(b->table, st);
+  return multi_step(b->solvers.data(), b->states.data(), (int)b->solvers.size(), st, b->width);
+}
+
 CG_API int cg_batch_step(cg_batch* b, void* stream) {
   if (!b) return fail(CG_ERR_INVALID_ARG, "null batch");
   cudaStream_t st = (cudaStream_t)stream;
-  int count = (int)b->solvers.size();
   if (!b->warm) {
-    // first step runs eagerly: one-time kernel attributes and stream pool set-up
-    int rc = multi_step(b->solvers.data(), b->states.data(), count, st, b->width);
+    // first step runs eagerly: the work table, one-time kernel attributes and
+    // the stream pool are set up here
+    if (b->table.state == 0) {
+      int rc = table_build(b->table, b->solvers, b->states);
+      if (rc) return rc;
+    }
+    int rc = batch_once(b, st);
     if (rc) return rc;
     b->warm = 1;
     return CG_OK;
@@ -113,7 +401,7 @@ CG_API int cg_batch_step(cg_batch* b, void* stream) {
     // capture one batch step; later calls replay it
     if (st == nullptr) return fail(CG_ERR_INVALID_ARG, "graph replay needs a non-default stream");
     CG_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    int rc = multi_step(b->solvers.data(), b->states.data(), count, st, b->width);
+    int rc = batch_once(b, st);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(st, &g);
     if (rc) {
@@ -131,8 +419,9 @@ CG_API int cg_batch_step(cg_batch* b, void* stream) {
 // Autotunes every member's tile shape (equal shapes share one measurement),
 // then the pool width: each candidate width times two batch steps from a
 // saved copy of the states, which are restored afterwards (the call leaves
-// the members' states as it found them).  A captured graph is dropped and
-// recaptured at the next step.
+// the members' states as it found them).  A batch that qualifies for the work
+// table also times the table with each common tile shape and keeps whichever
+// path is faster.  A captured graph is dropped and recaptured at the next step.
 CG_API int cg_batch_autotune(cg_batch* b, void* stream, int* width_out) {
   if (!b) return fail(CG_ERR_INVALID_ARG, "null batch");
   cudaStream_t st = (cudaStream_t)stream;
@@ -184,6 +473,53 @@ CG_API int cg_batch_autotune(cg_batch* b, void* stream, int* width_out) {
       if ((rc = copy_states(false))) break;
     }
   }
+  // the work table, where the batch qualifies: one tile shape for all members,
+  // each candidate timed the same way; it replaces the stream pool if faster
+  bool table_ok = rc == CG_OK && e0 && e1;
+  for (int i = 0; table_ok && i < count; ++i) table_ok = table_member_ok(b->solvers[i], b->solvers[0], false);
+  b->use_table = 0;
+  if (table_ok) {
+    std::vector<std::array<int, 3>> keep(count);
+    for (int i = 0; i < count; ++i)
+      keep[i] = {b->solvers[i]->sweep_lw[0], b->solvers[i]->sweep_lw[1], b->solvers[i]->sweep_lw[2]};
+    int tbest[2] = {0, 0};
+    float tbest_ms = 1e30f;
+    for (int lx : kSweepLwCands0)
+      for (int ly : kSweepLwCands1) {
+        for (cg_solver* s : b->solvers) {
+          s->sweep_lw[0] = lx;
+          s->sweep_lw[1] = ly;
+        }
+        if ((rc = table_build(b->table, b->solvers, b->states)) || b->table.state != 1) break;
+        if ((rc = table_step(b->table, st))) break;  // warm-up
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < 2 && rc == CG_OK; ++r) rc = table_step(b->table, st);
+        cudaEventRecord(e1, st);
+        float ms = 0.f;
+        if (rc || cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+          if (!rc) rc = fail(CG_ERR_CUDA, "batch autotune timing failed");
+          break;
+        }
+        if (ms < tbest_ms) {
+          tbest_ms = ms;
+          tbest[0] = lx;
+          tbest[1] = ly;
+        }
+        if ((rc = copy_states(false))) break;
+      }
+    if (rc == CG_OK && tbest[0] && tbest_ms < best_ms) {
+      for (cg_solver* s : b->solvers) {
+        s->sweep_lw[0] = tbest[0];
+        s->sweep_lw[1] = tbest[1];
+      }
+      rc = table_build(b->table, b->solvers, b->states);
+      b->use_table = 1;
+    } else {
+      for (int i = 0; i < count; ++i)
+        for (int d = 0; d < 3; ++d) b->solvers[i]->sweep_lw[d] = keep[i][d];
+      table_free(b->table);
+    }
+  }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   int rc2 = copy_states(false);
@@ -193,6 +529,7 @@ CG_API int cg_batch_autotune(cg_batch* b, void* stream, int* width_out) {
   if (rc2) return rc2;
   if (e != cudaSuccess) return fail(CG_ERR_CUDA, "batch autotune: %s", cudaGetErrorString(e));
   b->width = best;
+  if (!b->use_table) b->table.state = -1;  // stays on the stream pool
   if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
   if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
   if (width_out) *width_out = best;
@@ -203,7 +540,16 @@ CG_API void cg_batch_destroy(cg_batch* b) {
   if (!b) return;
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
+  table_free(b->table);
   delete b;
+}
+
+CG_API int cg_batch_path(const cg_batch* b, int* path_out, int* launches_out) {
+  if (!b || !path_out) return fail(CG_ERR_INVALID_ARG, "null argument");
+  const bool table = b->use_table && b->table.state == 1;
+  *path_out = table ? 1 : 0;
+  if (launches_out) *launches_out = table ? table_launches(b->table) : -1;  // -1: per member, counted by the members
+  return CG_OK;
 }
 
 }  // extern "C"

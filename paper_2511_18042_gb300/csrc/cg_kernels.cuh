@@ -62,7 +62,7 @@ __device__ __forceinline__ VBlock hw_block() {
 // Primitives recovered in FP64 (p = (gamma-1)(E - rho|u|^2/2)); stored as TW
 // (float for the mixed form's FP32 consumers).
 template <int ND, typename TW = double>
-__device__ __forceinline__ void k_prim_body(const VBlock& vb, DevGrid g, const double* __restrict__ U, TW* __restrict__ W) {
+__device__ __forceinline__ void k_prim_body(const VBlock& vb, const DevGrid& g, const double* __restrict__ U, TW* __restrict__ W) {
   constexpr int NV = ND + 2;
   for (long long q = vb.x * (long long)blockDim.x + threadIdx.x; q < g.N;
        q += (long long)vb.gx * blockDim.x) {
@@ -95,7 +95,7 @@ __global__ void k_prim(DevGrid g, const double* __restrict__ U, TW* __restrict__
 // T = double: FP64 parity form; T = float: the mixed form's FP32 sensor
 // (FP64 primitives and gradients read, converted once).
 template <int ND, bool CART, bool COMPACT, typename T = double>
-__device__ __forceinline__ void k_omega_body(const VBlock& vb, DevGrid g, const T* __restrict__ W, const T* __restrict__ G0,
+__device__ __forceinline__ void k_omega_body(const VBlock& vb, const DevGrid& g, const T* __restrict__ W, const T* __restrict__ G0,
                         const T* __restrict__ G1, const T* __restrict__ G2, LineBuf gb0,
                         LineBuf gb1, LineBuf gb2, double* __restrict__ om, Box ob, const int* guard, int want) {
   constexpr int NV = ND + 2, IP = ND + 1;
@@ -280,7 +280,7 @@ __host__ __device__ constexpr int sweep_min_blocks() {
 // 2: FP32): the code is the same, the compilation flags differ, and distinct
 // instantiations keep the units' kernels apart.
 template <int ND, int DIR, bool CART, bool COMPACT, typename T, int LW, int UNIT>
-__device__ __forceinline__ void k_gbr_sweep_body(const VBlock& vb, DevGrid g, GbrCfg q, StageArgs A) {
+__device__ __forceinline__ void k_gbr_sweep_body(const VBlock& vb, const DevGrid& g, const GbrCfg& q, const StageArgs& A) {
   static_assert((SWEEP_TL * LW) % 256 == 0, "a tile must hold a multiple of the block's threads");
   constexpr int NV = ND + 2, IP = ND + 1;
   constexpr bool MIX = sizeof(T) == 4;
@@ -518,7 +518,7 @@ __global__ void __launch_bounds__(256, sweep_min_blocks<ND, CART, T>()) k_gbr_sw
 // T = double: the exact FP64 rate.  T = float (mixed form): the primitives
 // (pressure recovery) in FP64, the sound speed and the spectral radii in FP32.
 template <int ND, bool CART, typename T = double>
-__device__ __forceinline__ void k_cfl_max_body(const VBlock& vb, DevGrid g, const double* __restrict__ U, unsigned long long* __restrict__ mx) {
+__device__ __forceinline__ void k_cfl_max_body(const VBlock& vb, const DevGrid& g, const double* __restrict__ U, unsigned long long* __restrict__ mx) {
   constexpr int NV = ND + 2, IP = ND + 1;
   double best = 0.0;
   for (long long q = vb.x * (long long)blockDim.x + threadIdx.x; q < g.N;

@@ -50,7 +50,7 @@ __device__ __forceinline__ void box_coords(const Box& b, long long e, int* c) {
 
 // the LAD fields at every node of the box fbx (ghosts by the boundary rule)
 template <int ND, typename T = double>
-__device__ __forceinline__ void k_lad_fieldbuf_body(const VBlock& vb, DevGrid g, const T* __restrict__ W, T* __restrict__ f, Box fbx) {
+__device__ __forceinline__ void k_lad_fieldbuf_body(const VBlock& vb, const DevGrid& g, const T* __restrict__ W, T* __restrict__ f, Box fbx) {
   constexpr int NV = ND + 2, NF = ND + 3;
   long long fs = fbx.size();
   BOX_LOOP(fbx, e) {
@@ -72,7 +72,7 @@ __global__ void k_lad_fieldbuf(DevGrid g, const T* __restrict__ W, T* __restrict
 // Physical gradients and dilatation on b3.  E4 differences the field buffer;
 // C6 reads the compact derivatives from the line buffers df.
 template <int ND, bool CART, bool C6, typename T = double>
-__device__ __forceinline__ void k_lad_grad_body(const VBlock& vb, DevGrid g, const T* __restrict__ fb, Box fbx, const T* __restrict__ df0,
+__device__ __forceinline__ void k_lad_grad_body(const VBlock& vb, const DevGrid& g, const T* __restrict__ fb, Box fbx, const T* __restrict__ df0,
                            const T* __restrict__ df1, const T* __restrict__ df2, LineBuf lb0, LineBuf lb1,
                            LineBuf lb2, T* __restrict__ gr, T* __restrict__ dv, Box b3, const int* guard,
                            int want) {
@@ -154,7 +154,7 @@ __device__ __forceinline__ float grad_norm(float a, float b, float c) {
 // beta* = C_beta rho f_sw |sum_l d4(div)_l Delta_{l,beta}^2|,
 // kappa* = C_kappa (rho c / T) |sum_l d4(e)_l Delta_{l,kappa}|.
 template <int ND, bool CART, typename T = double>
-__device__ __forceinline__ void k_lad_coef_body(const VBlock& vb, DevGrid g, const T* __restrict__ W, const T* __restrict__ fb, Box fbx,
+__device__ __forceinline__ void k_lad_coef_body(const VBlock& vb, const DevGrid& g, const T* __restrict__ W, const T* __restrict__ fb, Box fbx,
                            const T* __restrict__ gr, const T* __restrict__ dv, Box b3, double c_beta_d,
                            double c_kappa_d, T* __restrict__ bt, T* __restrict__ kp, const int* guard, int want) {
   const T c_beta = T(c_beta_d), c_kappa = T(c_kappa_d);
@@ -257,7 +257,7 @@ __global__ void k_lad_coef(DevGrid g, const T* __restrict__ W, const T* __restri
 // truncated-Gaussian overbar along l (nine points, Cook & Cabot), two fields;
 // ghost values: periodic wrap, wall mirror, otherwise the boundary node.
 template <int ND, typename T = double>
-__device__ __forceinline__ void k_gauss_body(const VBlock& vb, DevGrid g, int l, const T* __restrict__ a, const T* __restrict__ b, T* __restrict__ ao,
+__device__ __forceinline__ void k_gauss_body(const VBlock& vb, const DevGrid& g, int l, const T* __restrict__ a, const T* __restrict__ b, T* __restrict__ ao,
                         T* __restrict__ bo, const int* guard, int want) {
   if (guard && *guard != want) return;
   const T A0 = T(3565.0 / 10368.0), A1 = T(3091.0 / 12960.0), A2 = T(1997.0 / 25920.0), A3 = T(149.0 / 12960.0),
@@ -411,7 +411,7 @@ __device__ __forceinline__ void nodeflux_at(const DevGrid& g, int l, const T* __
 }
 
 template <int ND, bool CART, int MODE, typename T = double>
-__device__ __forceinline__ void k_lad_nodeflux_body(const VBlock& vb, DevGrid g, int l, const T* __restrict__ W, const T* __restrict__ bt,
+__device__ __forceinline__ void k_lad_nodeflux_body(const VBlock& vb, const DevGrid& g, int l, const T* __restrict__ W, const T* __restrict__ bt,
                                const T* __restrict__ kp, const T* __restrict__ gr, const T* __restrict__ dv, Box b3,
                                T* __restrict__ Fn, Box fb, const int* guard, int want) {
   constexpr int NV = ND + 2;
@@ -523,7 +523,7 @@ __global__ void k_lad_div(DevGrid g, int l, const T* __restrict__ Fn, Box fb, co
 // (with the sensor) Omega > threshold; counts troubled interior nodes and
 // sets flag[0] = 1 if any (the global decision of Algorithm 3).
 template <int ND, typename TW = double>
-__device__ __forceinline__ void k_troubled_body(const VBlock& vb, DevGrid g, const TW* __restrict__ W, double hr, double hp, const double* __restrict__ om,
+__device__ __forceinline__ void k_troubled_body(const VBlock& vb, const DevGrid& g, const TW* __restrict__ W, double hr, double hp, const double* __restrict__ om,
                            Box ob, double thr, unsigned char* __restrict__ tr, Box tb, int* flag,
                            unsigned long long* count) {
   constexpr int NV = ND + 2, IP = ND + 1;
@@ -557,7 +557,7 @@ __global__ void k_troubled(DevGrid g, const TW* __restrict__ W, double hr, doubl
 // Per-interface hybrid: LAD flux at interfaces i+1/2 (i in [-1, n-1]) in the
 // conservative E4 flux form h = 7/12 (F_i + F_{i+1}) - 1/12 (F_{i-1} + F_{i+2}).
 template <int ND, typename T = double>
-__device__ __forceinline__ void k_lad_hflux_body(const VBlock& vb, DevGrid g, int l, const T* __restrict__ Fn, Box fb, double* __restrict__ H, Box hb) {
+__device__ __forceinline__ void k_lad_hflux_body(const VBlock& vb, const DevGrid& g, int l, const T* __restrict__ Fn, Box fb, double* __restrict__ H, Box hb) {
   constexpr int NV = ND + 2;
   long long fs = fb.size(), hs = hb.size();
   long long st = l == 0 ? 1 : (l == 1 ? (long long)fb.ext[0] : (long long)fb.ext[0] * fb.ext[1]);

@@ -30,6 +30,37 @@ CGK_SWEEP_DECL(launch_sweep_f32_3)
 
 constexpr int kSweepExact = 0, kSweepContracted = 1, kSweepFP32 = 2;
 
+// Tile grid of a sweep along dir with lw lines per tile: along dir, tiles of
+// SWEEP_TL interfaces overlapping by one node; across, groups of lw lines.
+inline dim3 sweep_grid_dims(int dir, int lw, const DevGrid& g) {
+  const int* n = g.n;
+  if (dir == 0) {
+    long long lines = (long long)n[1] * n[2];
+    return dim3((n[0] + SWEEP_TL - 2) / (SWEEP_TL - 1), (unsigned)((lines + lw - 1) / lw), 1);
+  }
+  int other = dir == 1 ? n[2] : n[1];
+  return dim3((n[0] + lw - 1) / lw, (n[dir] + SWEEP_TL - 2) / (SWEEP_TL - 1), other);
+}
+
+// ---------------------------------------------------------------- batched sweeps
+// One grid of a batched sweep (2D, Cartesian): its arguments and its tile
+// grid, which takes blocks [off_m, off_m + gx gy gz) of the one launch.
+struct SweepJob {
+  DevGrid g;
+  GbrCfg q;
+  StageArgs A;
+  unsigned gx, gy, gz;
+};
+
+// Sweep along dir of every grid of a batch in one launch: jobs[nm] and
+// off[nm + 1] (off[nm] = total blocks) in device memory.  Returns a
+// cudaError_t value; cudaErrorInvalidValue for a form or shape that is not
+// instantiated (2D Cartesian, exact FP64 or FP32, non-compact gradients).
+int launch_sweep_batched_f64_2(int dir, int lw, const SweepJob* jobs, const long long* off, int nm,
+                               long long total, cudaStream_t st);
+int launch_sweep_batched_f32_2(int dir, int lw, const SweepJob* jobs, const long long* off, int nm,
+                               long long total, cudaStream_t st);
+
 inline int launch_sweep_any(int form, int nd, int dir, int lw, bool cart, bool compact, const DevGrid& g,
                             const GbrCfg& q, const StageArgs& A, cudaStream_t st) {
   if (form == kSweepContracted) {

@@ -24,13 +24,7 @@ constexpr int SND = CGK_SWEEP_ND;
 // node; across, groups of LW lines
 template <int DIR, int LW>
 dim3 sweep_grid(const DevGrid& g) {
-  const int* n = g.n;
-  if (DIR == 0) {
-    long long lines = (long long)n[1] * n[2];
-    return dim3((n[0] + SWEEP_TL - 2) / (SWEEP_TL - 1), (unsigned)((lines + LW - 1) / LW), 1);
-  }
-  int other = DIR == 1 ? n[2] : n[1];
-  return dim3((n[0] + LW - 1) / LW, (n[DIR] + SWEEP_TL - 2) / (SWEEP_TL - 1), other);
+  return sweep_grid_dims(DIR, LW, g);
 }
 
 template <int DIR, bool CART, bool COMPACT, int LW>
@@ -62,7 +56,66 @@ int launch_dir(int lw, bool cart, bool compact, const DevGrid& g, const GbrCfg& 
   return (int)cudaErrorInvalidValue;
 }
 
+#if CGK_SWEEP_ND == 2 && CGK_SWEEP_UNIT != 1
+// Batched sweep: block b of the launch belongs to the grid m with
+// off[m] <= b < off[m + 1] and is that grid's tile (b - off[m]).
+template <int DIR, int LW>
+__global__ void __launch_bounds__(256, sweep_min_blocks<SND, true, ST>())
+    k_gbr_sweep_batched(const SweepJob* __restrict__ jobs, const long long* __restrict__ off, int nm) {
+  const long long b = blockIdx.x;
+  int lo = 0, hi = nm;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (off[mid] <= b) lo = mid;
+    else hi = mid;
+  }
+  const SweepJob& J = jobs[lo];
+  const long long r = b - off[lo];
+  const VBlock vb{(unsigned)(r % J.gx), (unsigned)((r / J.gx) % J.gy), (unsigned)(r / ((long long)J.gx * J.gy)),
+                  J.gx, J.gy, J.gz};
+  k_gbr_sweep_body<SND, DIR, true, false, ST, LW, CGK_SWEEP_UNIT>(vb, J.g, J.q, J.A);
+}
+
+template <int DIR, int LW>
+int launch_batched_one(const SweepJob* jobs, const long long* off, int nm, long long total, cudaStream_t st) {
+  size_t smem = sizeof(ST) * sweep_smem_doubles<SND, LW>();
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_gbr_sweep_batched<DIR, LW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return (int)e;
+    attr_set = true;
+  }
+  if (total < 1 || total > 0x7fffffffLL) return (int)cudaErrorInvalidValue;
+  k_gbr_sweep_batched<DIR, LW><<<(unsigned)total, 256, smem, st>>>(jobs, off, nm);
+  return (int)cudaGetLastError();
+}
+
+int launch_batched(int dir, int lw, const SweepJob* jobs, const long long* off, int nm, long long total,
+                   cudaStream_t st) {
+  if (dir == 0 && lw == 4) return launch_batched_one<0, 4>(jobs, off, nm, total, st);
+  if (dir == 0 && lw == 8) return launch_batched_one<0, 8>(jobs, off, nm, total, st);
+  if (dir == 1 && lw == 4) return launch_batched_one<1, 4>(jobs, off, nm, total, st);
+  if (dir == 1 && lw == 8) return launch_batched_one<1, 8>(jobs, off, nm, total, st);
+  if (dir == 1 && lw == 16) return launch_batched_one<1, 16>(jobs, off, nm, total, st);
+  return (int)cudaErrorInvalidValue;
+}
+#endif
+
 }  // namespace
+
+#if CGK_SWEEP_ND == 2 && CGK_SWEEP_UNIT == 0
+int launch_sweep_batched_f64_2(int dir, int lw, const SweepJob* jobs, const long long* off, int nm,
+                               long long total, cudaStream_t st) {
+  return launch_batched(dir, lw, jobs, off, nm, total, st);
+}
+#endif
+#if CGK_SWEEP_ND == 2 && CGK_SWEEP_UNIT == 2
+int launch_sweep_batched_f32_2(int dir, int lw, const SweepJob* jobs, const long long* off, int nm,
+                               long long total, cudaStream_t st) {
+  return launch_batched(dir, lw, jobs, off, nm, total, st);
+}
+#endif
 
 #define CGK_CAT3_(a, b, c) a##b##c
 #define CGK_CAT3(a, b, c) CGK_CAT3_(a, b, c)

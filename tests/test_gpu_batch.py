@@ -42,6 +42,40 @@ def test_batch_equals_members_alone(api, kw):
     torch.cuda.synchronize()
     for a, b in zip(Ua, Ub):
         assert torch.equal(a, b)
+    # 2D Cartesian per-interface hybrids step through the work table
+    want = "table" if kw.get("hybrid_mode") == 1 else "streams"
+    assert batch.path()[0] == want
+
+
+def test_work_table_after_autotune(api):
+    """The autotuner may move a qualifying batch to one common tile shape;
+    members then match members alone with that shape, and the table's launch
+    count does not grow with the member count."""
+    kw = dict(scheme="HYBRID", hybrid_mode=1, hyb_rho=0.3, hybrid_sensor=1, precision=1)
+    probs = inputs.batched_riemann(count=24, seed=7, n_lo=20, n_hi=130)
+    solvers = [api.Solver.from_problem(p, **kw) for p in probs]
+    Ub = [to_dev(p["U"]) for p in probs]
+    stream = torch.cuda.Stream()
+    batch = api.Batch(solvers, Ub)
+    batch.autotune(stream)
+    with torch.cuda.stream(stream):
+        for _ in range(4):
+            batch.step(stream)
+    stream.synchronize()
+    path, launches = batch.path()
+    alone = []
+    for p, s in zip(probs, solvers):
+        a = api.Solver.from_problem(p, **kw)
+        a.set_tile_shape(s.tile_shape())
+        U = to_dev(p["U"])
+        a.advance(U, nsteps=4)
+        alone.append(U)
+    torch.cuda.synchronize()
+    for a, b in zip(alone, Ub):
+        assert torch.isfinite(b).all()
+        assert rel_err(b, a) <= 1e-6
+    if path == "table":
+        assert launches == 41
 
 
 def test_multi_step_member_matches_oracle(orc, api):
