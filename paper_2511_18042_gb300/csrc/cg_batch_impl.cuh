@@ -67,10 +67,12 @@ int multi_step(cg_solver* const* solvers, double* const* states, int count, cuda
 // and 13 for the others, whatever the number of members.  The job arrays and
 // block offsets are built once on the host and kept in one device buffer.
 
-// one phase: device job array, block offsets (nm + 1) and total blocks
+// one phase: device job array, block offsets (nm + 1), the member of every
+// block, and the total blocks
 struct TKind {
   const void* jobs = nullptr;
   const long long* off = nullptr;
+  const int* mem = nullptr;
   long long total = 0;
 };
 
@@ -94,7 +96,7 @@ static bool table_member_ok(const cg_solver* s, const cg_solver* s0, bool same_t
 // host staging of the job arrays and offsets, copied to the device at once
 struct TableBlob {
   std::vector<char> bytes;
-  struct Rec { TKind* k; size_t jobs_at, off_at; long long total; };
+  struct Rec { TKind* k; size_t jobs_at, off_at, mem_at; long long total; };
   std::vector<Rec> recs;
   template <class Job>
   void add(TKind* k, const std::vector<Job>& jobs, const std::vector<long long>& off) {
@@ -104,7 +106,11 @@ struct TableBlob {
       memcpy(bytes.data() + at, p, n);
       return at;
     };
-    Rec r{k, put(jobs.data(), sizeof(Job) * jobs.size()), put(off.data(), sizeof(long long) * off.size()), off.back()};
+    std::vector<int> mem((size_t)off.back());
+    for (size_t m = 0; m + 1 < off.size(); ++m)
+      for (long long b = off[m]; b < off[m + 1]; ++b) mem[(size_t)b] = (int)m;
+    Rec r{k, put(jobs.data(), sizeof(Job) * jobs.size()), put(off.data(), sizeof(long long) * off.size()),
+          put(mem.data(), sizeof(int) * mem.size()), off.back()};
     recs.push_back(r);
   }
 };
@@ -244,6 +250,7 @@ static int table_build_t(BatchTable& tb, cg_solver* const* sv, double* const* st
   for (auto& r : blob.recs) {
     r.k->jobs = (const char*)dm + r.jobs_at;
     r.k->off = reinterpret_cast<const long long*>((const char*)dm + r.off_at);
+    r.k->mem = reinterpret_cast<const int*>((const char*)dm + r.mem_at);
     r.k->total = r.total;
   }
   tb.dmem = dm;
@@ -279,16 +286,14 @@ static int table_build(BatchTable& tb, const std::vector<cg_solver*>& sv, const 
 }
 
 template <class Job>
-static int table_launch(const TKind& k, int nm, cudaStream_t st) {
-  k_batched<Job><<<(unsigned)k.total, BATCH_THREADS, 0, st>>>(static_cast<const Job*>(k.jobs), k.off, nm);
-  return CG_OK;
+static void table_launch(const TKind& k, int, cudaStream_t st) {
+  k_batched<Job><<<(unsigned)k.total, BATCH_THREADS, 0, st>>>(static_cast<const Job*>(k.jobs), k.off, k.mem);
 }
 
 template <class J1, class J2>
-static int table_launch2(const TKind& a, const TKind& b, int nm, cudaStream_t st) {
+static void table_launch2(const TKind& a, const TKind& b, int, cudaStream_t st) {
   k_batched2<J1, J2><<<(unsigned)(a.total + b.total), BATCH_THREADS, 0, st>>>(
-      static_cast<const J1*>(a.jobs), a.off, static_cast<const J2*>(b.jobs), b.off, nm);
-  return CG_OK;
+      static_cast<const J1*>(a.jobs), a.off, a.mem, a.total, static_cast<const J2*>(b.jobs), b.off, b.mem);
 }
 
 // One RK3 step (with each member's CFL dt) of every member.
@@ -298,8 +303,8 @@ static int table_step_t(const BatchTable& tb, cudaStream_t st) {
   auto sweep = [&](int k, int d) -> int {
     const TKind& K = tb.sweep[k][d];
     const SweepJob* J = static_cast<const SweepJob*>(K.jobs);
-    int e = tb.mixed ? launch_sweep_batched_f32_2(d, tb.lw[d], J, K.off, nm, K.total, st)
-                     : launch_sweep_batched_f64_2(d, tb.lw[d], J, K.off, nm, K.total, st);
+    int e = tb.mixed ? launch_sweep_batched_f32_2(d, tb.lw[d], J, K.off, K.mem, K.total, st)
+                     : launch_sweep_batched_f64_2(d, tb.lw[d], J, K.off, K.mem, K.total, st);
     if (e) return fail(CG_ERR_CUDA, "batched sweep (dir %d): %s", d, cudaGetErrorString((cudaError_t)e));
     return CG_OK;
   };
@@ -417,9 +422,10 @@ CG_API int cg_batch_step(cg_batch* b, void* stream) {
 }
 
 // Autotunes every member's tile shape (equal shapes share one measurement),
-// then the pool width: each candidate width times two batch steps from a
-// saved copy of the states, which are restored afterwards (the call leaves
-// the members' states as it found them).  A batch that qualifies for the work
+// then the pool width: each candidate width times two batch steps (replays of
+// a captured step where the stream allows) from a saved copy of the states,
+// which are restored afterwards (the call leaves the members' states as it
+// found them).  A batch that qualifies for the work
 // table also times the table with each common tile shape and keeps whichever
 // path is faster.  A captured graph is dropped and recaptured at the next step.
 CG_API int cg_batch_autotune(cg_batch* b, void* stream, int* width_out) {
@@ -455,17 +461,50 @@ CG_API int cg_batch_autotune(cg_batch* b, void* stream, int* width_out) {
   int best = b->width;
   float best_ms = 1e30f;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
+  // device time of two batch steps of fn: one eager step first (kernel
+  // attributes, stream pool), then, on a stream that can be captured, two
+  // replays of a captured step after one warm-up replay, as cg_batch_step runs
+  // them from its third call on; on the legacy stream, two eager steps
+  auto time_steps = [&](auto&& fn, float* ms) -> int {
+    int r = fn();
+    if (r) return r;
+    if (st != nullptr) {
+      cudaGraph_t g = nullptr;
+      cudaGraphExec_t x = nullptr;
+      CG_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+      r = fn();
+      cudaError_t e = cudaStreamEndCapture(st, &g);
+      if (r) {
+        if (g) cudaGraphDestroy(g);
+        return r;
+      }
+      if (e != cudaSuccess) return fail(CG_ERR_CUDA, "batch autotune capture: %s", cudaGetErrorString(e));
+      e = cudaGraphInstantiate(&x, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return fail(CG_ERR_CUDA, "batch autotune graph: %s", cudaGetErrorString(e));
+      e = cudaGraphLaunch(x, st);
+      if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+      for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaGraphLaunch(x, st);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      cudaGraphExecDestroy(x);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+      if (e != cudaSuccess) return fail(CG_ERR_CUDA, "batch autotune timing: %s", cudaGetErrorString(e));
+      return CG_OK;
+    }
+    CG_CUDA(cudaEventRecord(e0, st));
+    for (int k = 0; k < 2 && r == CG_OK; ++k) r = fn();
+    if (r) return r;
+    CG_CUDA(cudaEventRecord(e1, st));
+    CG_CUDA(cudaEventSynchronize(e1));
+    CG_CUDA(cudaEventElapsedTime(ms, e0, e1));
+    return CG_OK;
+  };
   if ((rc = copy_states(true)) == CG_OK && cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) {
     for (int w : cands) {
-      if ((rc = multi_step(b->solvers.data(), b->states.data(), count, st, w))) break;  // warm-up
-      cudaEventRecord(e0, st);
-      for (int r = 0; r < 2 && rc == CG_OK; ++r) rc = multi_step(b->solvers.data(), b->states.data(), count, st, w);
-      cudaEventRecord(e1, st);
       float ms = 0.f;
-      if (rc || cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
-        if (!rc) rc = fail(CG_ERR_CUDA, "batch autotune timing failed");
-        break;
-      }
+      rc = time_steps([&]() { return multi_step(b->solvers.data(), b->states.data(), count, st, w); }, &ms);
+      if (rc) break;
       if (ms < best_ms) {
         best_ms = ms;
         best = w;
@@ -491,15 +530,8 @@ CG_API int cg_batch_autotune(cg_batch* b, void* stream, int* width_out) {
           s->sweep_lw[1] = ly;
         }
         if ((rc = table_build(b->table, b->solvers, b->states)) || b->table.state != 1) break;
-        if ((rc = table_step(b->table, st))) break;  // warm-up
-        cudaEventRecord(e0, st);
-        for (int r = 0; r < 2 && rc == CG_OK; ++r) rc = table_step(b->table, st);
-        cudaEventRecord(e1, st);
         float ms = 0.f;
-        if (rc || cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
-          if (!rc) rc = fail(CG_ERR_CUDA, "batch autotune timing failed");
-          break;
-        }
+        if ((rc = time_steps([&]() { return table_step(b->table, st); }, &ms))) break;
         if (ms < tbest_ms) {
           tbest_ms = ms;
           tbest[0] = lx;

@@ -1,9 +1,10 @@
 // Work-table launches of a batch of 2D Cartesian grids: one launch runs one
 // phase of an RK stage for every grid of the batch.  Block b of the launch
-// belongs to the grid m with off[m] <= b < off[m + 1] (off[nm] = the total)
-// and runs that grid's block (b - off[m]) of the phase's kernel body, with
-// the grid's own arguments (a job).  The bodies are those of the per-grid
-// kernels, so a batched phase computes what the per-grid launches compute.
+// belongs to the grid m = mem[b] (off[m] <= b < off[m + 1], off[nm] = the
+// total) and runs that grid's block (b - off[m]) of the phase's kernel body,
+// with the grid's own arguments (a job).  The bodies are those of the
+// per-grid kernels, so a batched phase computes what the per-grid launches
+// compute.
 #pragma once
 #include "cg_lad.cuh"
 
@@ -11,39 +12,31 @@ namespace cgk {
 
 constexpr int BATCH_THREADS = 256;
 
-__device__ __forceinline__ int batch_member(const long long* __restrict__ off, int nm, long long b) {
-  int lo = 0, hi = nm;
-  while (hi - lo > 1) {
-    const int mid = (lo + hi) >> 1;
-    if (off[mid] <= b) lo = mid;
-    else hi = mid;
-  }
-  return lo;
-}
-
 // grid-stride bodies: nb virtual blocks along x
 __device__ __forceinline__ VBlock vblock_1d(unsigned b, unsigned nb) { return VBlock{b, 0u, 0u, nb, 1u, 1u}; }
 
 template <class Job>
 __global__ void __launch_bounds__(BATCH_THREADS) k_batched(const Job* __restrict__ jobs,
-                                                          const long long* __restrict__ off, int nm) {
+                                                          const long long* __restrict__ off,
+                                                          const int* __restrict__ mem) {
   const long long b = blockIdx.x;
-  const int m = batch_member(off, nm, b);
+  const int m = mem[b];
   jobs[m].run((unsigned)(b - off[m]));
 }
 
-// two independent phases in one launch: blocks [0, o1[nm]) run J1, the rest J2
+// two independent phases in one launch: blocks [0, t1) run J1, the rest J2
 template <class J1, class J2>
 __global__ void __launch_bounds__(BATCH_THREADS) k_batched2(const J1* __restrict__ j1, const long long* __restrict__ o1,
+                                                           const int* __restrict__ m1, long long t1,
                                                            const J2* __restrict__ j2, const long long* __restrict__ o2,
-                                                           int nm) {
-  const long long b = blockIdx.x, t1 = o1[nm];
+                                                           const int* __restrict__ m2) {
+  const long long b = blockIdx.x;
   if (b < t1) {
-    const int m = batch_member(o1, nm, b);
+    const int m = m1[b];
     j1[m].run((unsigned)(b - o1[m]));
   } else {
     const long long r = b - t1;
-    const int m = batch_member(o2, nm, r);
+    const int m = m2[r];
     j2[m].run((unsigned)(r - o2[m]));
   }
 }

@@ -52,13 +52,14 @@ struct SweepJob {
   unsigned gx, gy, gz;
 };
 
-// Sweep along dir of every grid of a batch in one launch: jobs[nm] and
-// off[nm + 1] (off[nm] = total blocks) in device memory.  Returns a
-// cudaError_t value; cudaErrorInvalidValue for a form or shape that is not
-// instantiated (2D Cartesian, exact FP64 or FP32, non-compact gradients).
-int launch_sweep_batched_f64_2(int dir, int lw, const SweepJob* jobs, const long long* off, int nm,
+// Sweep along dir of every grid of a batch in one launch: jobs[nm], off[nm + 1]
+// (off[nm] = total blocks) and mem[total] (the grid of every block) in device
+// memory.  Returns a cudaError_t value; cudaErrorInvalidValue for a form or
+// shape that is not instantiated (2D Cartesian, exact FP64 or FP32,
+// non-compact gradients).
+int launch_sweep_batched_f64_2(int dir, int lw, const SweepJob* jobs, const long long* off, const int* mem,
                                long long total, cudaStream_t st);
-int launch_sweep_batched_f32_2(int dir, int lw, const SweepJob* jobs, const long long* off, int nm,
+int launch_sweep_batched_f32_2(int dir, int lw, const SweepJob* jobs, const long long* off, const int* mem,
                                long long total, cudaStream_t st);
 
 inline int launch_sweep_any(int form, int nd, int dir, int lw, bool cart, bool compact, const DevGrid& g,

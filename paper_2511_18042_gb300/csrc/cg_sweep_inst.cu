@@ -57,27 +57,23 @@ int launch_dir(int lw, bool cart, bool compact, const DevGrid& g, const GbrCfg& 
 }
 
 #if CGK_SWEEP_ND == 2 && CGK_SWEEP_UNIT != 1
-// Batched sweep: block b of the launch belongs to the grid m with
-// off[m] <= b < off[m + 1] and is that grid's tile (b - off[m]).
+// Batched sweep: block b of the launch belongs to the grid m = mem[b]
+// (off[m] <= b < off[m + 1]) and is that grid's tile (b - off[m]).
 template <int DIR, int LW>
 __global__ void __launch_bounds__(256, sweep_min_blocks<SND, true, ST>())
-    k_gbr_sweep_batched(const SweepJob* __restrict__ jobs, const long long* __restrict__ off, int nm) {
+    k_gbr_sweep_batched(const SweepJob* __restrict__ jobs, const long long* __restrict__ off,
+                        const int* __restrict__ mem) {
   const long long b = blockIdx.x;
-  int lo = 0, hi = nm;
-  while (hi - lo > 1) {
-    const int mid = (lo + hi) >> 1;
-    if (off[mid] <= b) lo = mid;
-    else hi = mid;
-  }
-  const SweepJob& J = jobs[lo];
-  const long long r = b - off[lo];
+  const int m = mem[b];
+  const SweepJob& J = jobs[m];
+  const long long r = b - off[m];
   const VBlock vb{(unsigned)(r % J.gx), (unsigned)((r / J.gx) % J.gy), (unsigned)(r / ((long long)J.gx * J.gy)),
                   J.gx, J.gy, J.gz};
   k_gbr_sweep_body<SND, DIR, true, false, ST, LW, CGK_SWEEP_UNIT>(vb, J.g, J.q, J.A);
 }
 
 template <int DIR, int LW>
-int launch_batched_one(const SweepJob* jobs, const long long* off, int nm, long long total, cudaStream_t st) {
+int launch_batched_one(const SweepJob* jobs, const long long* off, const int* mem, long long total, cudaStream_t st) {
   size_t smem = sizeof(ST) * sweep_smem_doubles<SND, LW>();
   static bool attr_set = false;
   if (!attr_set) {
@@ -87,17 +83,17 @@ int launch_batched_one(const SweepJob* jobs, const long long* off, int nm, long 
     attr_set = true;
   }
   if (total < 1 || total > 0x7fffffffLL) return (int)cudaErrorInvalidValue;
-  k_gbr_sweep_batched<DIR, LW><<<(unsigned)total, 256, smem, st>>>(jobs, off, nm);
+  k_gbr_sweep_batched<DIR, LW><<<(unsigned)total, 256, smem, st>>>(jobs, off, mem);
   return (int)cudaGetLastError();
 }
 
-int launch_batched(int dir, int lw, const SweepJob* jobs, const long long* off, int nm, long long total,
+int launch_batched(int dir, int lw, const SweepJob* jobs, const long long* off, const int* mem, long long total,
                    cudaStream_t st) {
-  if (dir == 0 && lw == 4) return launch_batched_one<0, 4>(jobs, off, nm, total, st);
-  if (dir == 0 && lw == 8) return launch_batched_one<0, 8>(jobs, off, nm, total, st);
-  if (dir == 1 && lw == 4) return launch_batched_one<1, 4>(jobs, off, nm, total, st);
-  if (dir == 1 && lw == 8) return launch_batched_one<1, 8>(jobs, off, nm, total, st);
-  if (dir == 1 && lw == 16) return launch_batched_one<1, 16>(jobs, off, nm, total, st);
+  if (dir == 0 && lw == 4) return launch_batched_one<0, 4>(jobs, off, mem, total, st);
+  if (dir == 0 && lw == 8) return launch_batched_one<0, 8>(jobs, off, mem, total, st);
+  if (dir == 1 && lw == 4) return launch_batched_one<1, 4>(jobs, off, mem, total, st);
+  if (dir == 1 && lw == 8) return launch_batched_one<1, 8>(jobs, off, mem, total, st);
+  if (dir == 1 && lw == 16) return launch_batched_one<1, 16>(jobs, off, mem, total, st);
   return (int)cudaErrorInvalidValue;
 }
 #endif
@@ -105,15 +101,15 @@ int launch_batched(int dir, int lw, const SweepJob* jobs, const long long* off, 
 }  // namespace
 
 #if CGK_SWEEP_ND == 2 && CGK_SWEEP_UNIT == 0
-int launch_sweep_batched_f64_2(int dir, int lw, const SweepJob* jobs, const long long* off, int nm,
+int launch_sweep_batched_f64_2(int dir, int lw, const SweepJob* jobs, const long long* off, const int* mem,
                                long long total, cudaStream_t st) {
-  return launch_batched(dir, lw, jobs, off, nm, total, st);
+  return launch_batched(dir, lw, jobs, off, mem, total, st);
 }
 #endif
 #if CGK_SWEEP_ND == 2 && CGK_SWEEP_UNIT == 2
-int launch_sweep_batched_f32_2(int dir, int lw, const SweepJob* jobs, const long long* off, int nm,
+int launch_sweep_batched_f32_2(int dir, int lw, const SweepJob* jobs, const long long* off, const int* mem,
                                long long total, cudaStream_t st) {
-  return launch_batched(dir, lw, jobs, off, nm, total, st);
+  return launch_batched(dir, lw, jobs, off, mem, total, st);
 }
 #endif
 
