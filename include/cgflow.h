@@ -194,10 +194,12 @@ CG_API int64_t cg_launch_count(const cg_solver *s);
  * Work table: a batch whose members are all 2D
  * Cartesian inviscid per-interface hybrids (CG_HYBRID, CG_HYBRID_CELL) of one
  * precision and one sweep tile shape steps phase by phase instead: each
- * launch runs one phase of an RK stage for every member through a table of
- * per-member jobs and block offsets built at the first cg_batch_step (41
- * launches per RK3 step, whatever the member count).  Each member computes
- * what it computes alone.  The table holds the members' buffer addresses:
+ * launch runs one phase of an RK stage for every member of a group through a
+ * table of per-member jobs and block offsets built at the first
+ * cg_batch_step (41 launches per RK3 step and group, whatever the member
+ * count; groups of members, 1 unless the autotuner chose more, run
+ * concurrently on internal streams).  Each member computes what it computes
+ * alone.  The table holds the members' buffer addresses:
  * members and states must outlive the batch, as for the stream path. */
 typedef struct cg_batch cg_batch;
 CG_API int cg_multi_step(cg_solver *const *solvers, double *const *states, int count, void *stream);
@@ -210,11 +212,12 @@ CG_API int cg_batch_step(cg_batch *b, void *stream);
  * on return.  Synchronises; not during stream capture; a captured graph is
  * recaptured at the next cg_batch_step.  *width_out (may be NULL) gets the
  * chosen number of streams.  A batch that qualifies for the work table also
- * times the table with each common tile shape and keeps the faster path. */
+ * times the table with each common tile shape, then with 2, 4 and 8 member
+ * groups, and keeps the faster path. */
 CG_API int cg_batch_autotune(cg_batch *b, void *stream, int *width_out);
 /* The path the batch steps by: *path_out = 1 for the work table, 0 for the
  * stream pool; *launches_out (may be NULL) = kernel launches of one table
- * step, or -1 for the stream pool (each member counts its own).  Before the
+ * step (41 per group), or -1 for the stream pool (each member counts its own).  Before the
  * first cg_batch_step the table is not built yet and the path reads 0. */
 CG_API int cg_batch_path(const cg_batch *b, int *path_out, int *launches_out);
 CG_API void cg_batch_destroy(cg_batch *b);

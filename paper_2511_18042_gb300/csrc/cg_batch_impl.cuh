@@ -341,6 +341,69 @@ static int table_step(const BatchTable& tb, cudaStream_t st) {
 // launches of one table step
 static int table_launches(const BatchTable&) { return 3 * 13 + 2; }
 
+// The members split into groups (largest first, dealt round robin), one table
+// per group; the groups run concurrently on the stream pool, so that phases
+// of different groups (FP64-bound recovery, FP32 sweeps, memory-bound
+// stencils) overlap on the device.
+struct TableSet {
+  int state = 0;  // 0: not built, 1: built, -1: the batch does not qualify
+  std::vector<BatchTable> t;
+};
+
+static void tables_free(TableSet& ts) {
+  for (auto& t : ts.t) table_free(t);
+  ts.t.clear();
+  ts.state = 0;
+}
+
+static int tables_build(TableSet& ts, const std::vector<cg_solver*>& sv, const std::vector<double*>& states,
+                        int groups) {
+  tables_free(ts);
+  const int nm = (int)sv.size();
+  for (int m = 0; m < nm; ++m)
+    if (!table_member_ok(sv[m], sv[0])) {
+      ts.state = -1;
+      return CG_OK;
+    }
+  groups = std::max(1, std::min(groups, std::min(nm, kMaxPoolStreams)));
+  std::vector<int> order(nm);
+  for (int m = 0; m < nm; ++m) order[m] = m;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return sv[a]->N > sv[b]->N; });
+  std::vector<std::vector<cg_solver*>> gs(groups);
+  std::vector<std::vector<double*>> gu(groups);
+  for (int i = 0; i < nm; ++i) {
+    gs[i % groups].push_back(sv[order[i]]);
+    gu[i % groups].push_back(states[order[i]]);
+  }
+  ts.t.resize(groups);
+  for (int g = 0; g < groups; ++g) {
+    int rc = table_build(ts.t[g], gs[g], gu[g]);
+    if (rc || ts.t[g].state != 1) {
+      tables_free(ts);
+      if (rc) return rc;
+      ts.state = -1;
+      return CG_OK;
+    }
+  }
+  ts.state = 1;
+  return CG_OK;
+}
+
+static int tables_step(const TableSet& ts, cudaStream_t st) {
+  const int ng = (int)ts.t.size();
+  if (ng == 1) return table_step(ts.t[0], st);
+  int rc = pool_ready();
+  if (rc) return rc;
+  CG_CUDA(cudaEventRecord(g_pool.fork, st));
+  for (int g = 0; g < ng; ++g) {
+    CG_CUDA(cudaStreamWaitEvent(g_pool.s[g], g_pool.fork, 0));
+    if ((rc = table_step(ts.t[g], g_pool.s[g]))) return rc;
+    CG_CUDA(cudaEventRecord(g_pool.join[g], g_pool.s[g]));
+    CG_CUDA(cudaStreamWaitEvent(st, g_pool.join[g], 0));
+  }
+  return CG_OK;
+}
+
 }  // namespace
 
 struct cg_batch {
@@ -350,7 +413,8 @@ struct cg_batch {
   cudaGraph_t graph = nullptr;
   int warm = 0;
   int width = kPoolStreams;  // streams the members are spread over
-  BatchTable table;          // work-table path (qualifying batches)
+  TableSet tables;           // work-table path (qualifying batches)
+  int groups = 1;            // member groups of the work table, run concurrently
   int use_table = 1;         // 0: the stream pool even where the table qualifies
 };
 
@@ -383,7 +447,7 @@ CG_API int cg_batch_create(int count, cg_solver* const* solvers, double* const* 
 
 // one eager step of the batch by its current path
 static int batch_once(cg_batch* b, cudaStream_t st) {
-  if (b->use_table && b->table.state == 1) return table_step(b->table, st);
+  if (b->use_table && b->tables.state == 1) return tables_step(b->tables, st);
   return multi_step(b->solvers.data(), b->states.data(), (int)b->solvers.size(), st, b->width);
 }
 
@@ -393,8 +457,8 @@ CG_API int cg_batch_step(cg_batch* b, void* stream) {
   if (!b->warm) {
     // first step runs eagerly: the work table, one-time kernel attributes and
     // the stream pool are set up here
-    if (b->table.state == 0) {
-      int rc = table_build(b->table, b->solvers, b->states);
+    if (b->tables.state == 0) {
+      int rc = tables_build(b->tables, b->solvers, b->states, b->groups);
       if (rc) return rc;
     }
     int rc = batch_once(b, st);
@@ -521,35 +585,44 @@ CG_API int cg_batch_autotune(cg_batch* b, void* stream, int* width_out) {
     std::vector<std::array<int, 3>> keep(count);
     for (int i = 0; i < count; ++i)
       keep[i] = {b->solvers[i]->sweep_lw[0], b->solvers[i]->sweep_lw[1], b->solvers[i]->sweep_lw[2]};
-    int tbest[2] = {0, 0};
+    int tbest[3] = {0, 0, 1};  // lines per x tile, per y tile, groups
     float tbest_ms = 1e30f;
-    for (int lx : kSweepLwCands0)
-      for (int ly : kSweepLwCands1) {
-        for (cg_solver* s : b->solvers) {
-          s->sweep_lw[0] = lx;
-          s->sweep_lw[1] = ly;
-        }
-        if ((rc = table_build(b->table, b->solvers, b->states)) || b->table.state != 1) break;
-        float ms = 0.f;
-        if ((rc = time_steps([&]() { return table_step(b->table, st); }, &ms))) break;
-        if (ms < tbest_ms) {
-          tbest_ms = ms;
-          tbest[0] = lx;
-          tbest[1] = ly;
-        }
-        if ((rc = copy_states(false))) break;
+    auto try_table = [&](int lx, int ly, int ng) -> int {
+      for (cg_solver* s : b->solvers) {
+        s->sweep_lw[0] = lx;
+        s->sweep_lw[1] = ly;
       }
+      int r = tables_build(b->tables, b->solvers, b->states, ng);
+      if (r || b->tables.state != 1) return r;
+      float ms = 0.f;
+      if ((r = time_steps([&]() { return tables_step(b->tables, st); }, &ms))) return r;
+      if (ms < tbest_ms) {
+        tbest_ms = ms;
+        tbest[0] = lx;
+        tbest[1] = ly;
+        tbest[2] = ng;
+      }
+      return copy_states(false);
+    };
+    // the tile shape with one group, then the number of groups with that shape
+    for (int lx : kSweepLwCands0)
+      for (int ly : kSweepLwCands1)
+        if (rc == CG_OK) rc = try_table(lx, ly, 1);
+    const int lx = tbest[0], ly = tbest[1];
+    for (int ng : {2, 4, 8})
+      if (rc == CG_OK && lx && ng <= count) rc = try_table(lx, ly, ng);
     if (rc == CG_OK && tbest[0] && tbest_ms < best_ms) {
       for (cg_solver* s : b->solvers) {
         s->sweep_lw[0] = tbest[0];
         s->sweep_lw[1] = tbest[1];
       }
-      rc = table_build(b->table, b->solvers, b->states);
+      b->groups = tbest[2];
+      rc = tables_build(b->tables, b->solvers, b->states, b->groups);
       b->use_table = 1;
     } else {
       for (int i = 0; i < count; ++i)
         for (int d = 0; d < 3; ++d) b->solvers[i]->sweep_lw[d] = keep[i][d];
-      table_free(b->table);
+      tables_free(b->tables);
     }
   }
   if (e0) cudaEventDestroy(e0);
@@ -561,7 +634,7 @@ CG_API int cg_batch_autotune(cg_batch* b, void* stream, int* width_out) {
   if (rc2) return rc2;
   if (e != cudaSuccess) return fail(CG_ERR_CUDA, "batch autotune: %s", cudaGetErrorString(e));
   b->width = best;
-  if (!b->use_table) b->table.state = -1;  // stays on the stream pool
+  if (!b->use_table) b->tables.state = -1;  // stays on the stream pool
   if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
   if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
   if (width_out) *width_out = best;
@@ -572,15 +645,18 @@ CG_API void cg_batch_destroy(cg_batch* b) {
   if (!b) return;
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
-  table_free(b->table);
+  tables_free(b->tables);
   delete b;
 }
 
 CG_API int cg_batch_path(const cg_batch* b, int* path_out, int* launches_out) {
   if (!b || !path_out) return fail(CG_ERR_INVALID_ARG, "null argument");
-  const bool table = b->use_table && b->table.state == 1;
+  const bool table = b->use_table && b->tables.state == 1;
   *path_out = table ? 1 : 0;
-  if (launches_out) *launches_out = table ? table_launches(b->table) : -1;  // -1: per member, counted by the members
+  int n = 0;
+  if (table)
+    for (const BatchTable& t : b->tables.t) n += table_launches(t);
+  if (launches_out) *launches_out = table ? n : -1;  // -1: per member, counted by the members
   return CG_OK;
 }
 
