@@ -115,7 +115,13 @@ struct TableBlob {
   }
 };
 
-static long long table_blocks(long long work) { return work < 1 ? 1 : (work + BATCH_THREADS - 1) / BATCH_THREADS; }
+// virtual blocks of a grid-stride body: each thread takes up to kTableItems
+// items, so that a block's set-up (member lookup, job fields) is shared
+constexpr int kTableItems = 4;
+static long long table_blocks(long long work) {
+  const long long per = (long long)BATCH_THREADS * kTableItems;
+  return work < 1 ? 1 : (work + per - 1) / per;
+}
 
 template <typename T>
 static int table_build_t(BatchTable& tb, cg_solver* const* sv, double* const* states, int nm) {
