@@ -117,7 +117,7 @@ struct TableBlob {
 
 // virtual blocks of a grid-stride body: each thread takes up to kTableItems
 // items, so that a block's set-up (member lookup, job fields) is shared
-constexpr int kTableItems = 4;
+constexpr int kTableItems = 16;
 static long long table_blocks(long long work) {
   const long long per = (long long)BATCH_THREADS * kTableItems;
   return work < 1 ? 1 : (work + per - 1) / per;
