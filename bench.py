@@ -389,6 +389,7 @@ def run_batched(api, torch, dev, args, count=256, steps_per_solve=200):
     for s_ in solvers:
         key = "x".join(str(v) for v in s_.tile_shape())
         shapes[key] = shapes.get(key, 0) + 1
+    path, path_launches = batch.path()
     bad = sum(1 for s in solvers if s.sync_status() != 0)
     del batch, solvers, states
     torch.cuda.empty_cache()
@@ -431,8 +432,12 @@ def run_batched(api, torch, dev, args, count=256, steps_per_solve=200):
                         % (count, cells),
             "ms_per_rk3_step": ms, "cell_updates_per_s": cells / (ms * 1e-3),
             "solves_per_s": count / (steps_per_solve * ms * 1e-3), "steps_per_solve": steps_per_solve,
-            "autotune": {"streams": width, "tile_shapes": shapes, "seconds": tune_s,
-                         "ms_per_rk3_step_default": ms_default},
+            "autotune": {"path": path, "launches_per_step": path_launches,
+                         "streams": width, "tile_shapes": shapes, "seconds": tune_s,
+                         "ms_per_rk3_step_default": ms_default,
+                         "note": "path: 'table' = one launch per phase of an RK stage for every member "
+                                 "(41 per step and member group); 'streams' = per-member launches on "
+                                 "the stream pool; default = the work table, untuned"},
             "nonphysical_members": bad,
             "accuracy_vs_fp64": {"members": len(sub), "steps": acc_steps, "density_l1_rel_max": l1},
             "per_case_fp64": {"ms_per_rk3_step": ref_ms, "solves_per_s": count / (steps_per_solve * ref_ms * 1e-3),

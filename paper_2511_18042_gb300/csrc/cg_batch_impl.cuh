@@ -2,9 +2,11 @@
 // cg_multi_step forks the caller's stream into a pool of internal streams,
 // runs each member's CFL time step and RK3 step on one of them (members are
 // independent: each solver owns its scratch), and joins back.  cg_batch
-// captures one such call into a CUDA graph and replays it, so a step of a
-// whole batch of uneven grids costs one graph launch on the host;
-// cg_batch_autotune picks the members' tile shapes and the pool width.
+// captures one step into a CUDA graph and replays it, so a step of a whole
+// batch of uneven grids costs one graph launch on the host.  A batch of 2D
+// Cartesian per-interface hybrids steps through a work table instead (one
+// launch per phase for every member, below); cg_batch_autotune picks the tile
+// shapes, the pool width, the number of table groups and the faster path.
 
 namespace {
 
