@@ -141,29 +141,29 @@ __device__ __forceinline__ void k_omega_body(const VBlock& vb, const DevGrid& g,
         }
       }
     } else {
-    double w0d[NV];
-    load_state<ND, false, T, double>(g, W, c[0], c[1], c[2], w0d);
+    T w0d[NV];
+    load_state<ND, false, T, T>(g, W, c[0], c[1], c[2], w0d);
     const T p0 = T(w0d[IP]);
 #pragma unroll
     for (int l = 0; l < ND; ++l) {
       int cm[3] = {c[0], c[1], c[2]}, cp[3] = {c[0], c[1], c[2]};
       cm[l] -= 1;
       cp[l] += 1;
-      double wm[NV], wp[NV];
-      load_state<ND, false, T, double>(g, W, cm[0], cm[1], cm[2], wm);
-      load_state<ND, false, T, double>(g, W, cp[0], cp[1], cp[2], wp);
+      T wm[NV], wp[NV];
+      load_state<ND, false, T, T>(g, W, cm[0], cm[1], cm[2], wm);
+      load_state<ND, false, T, T>(g, W, cp[0], cp[1], cp[2], wp);
       const T pm = T(wm[IP]), pp = T(wp[IP]);
       T a = fabs(pp - T(2.0) * p0 + pm) / (pp + T(2.0) * p0 + pm);
       if (a > phi) phi = a;
       if (!COMPACT) {
-        double s[6][NV];
+        T s[6][NV];
 #pragma unroll
         for (int t = 0; t < 3; ++t) {
           int a1[3] = {c[0], c[1], c[2]}, a2[3] = {c[0], c[1], c[2]};
           a1[l] -= 3 - t;
           a2[l] += 1 + t;
-          load_state<ND, false, T, double>(g, W, a1[0], a1[1], a1[2], s[t]);
-          load_state<ND, false, T, double>(g, W, a2[0], a2[1], a2[2], s[3 + t]);
+          load_state<ND, false, T, T>(g, W, a1[0], a1[1], a1[2], s[t]);
+          load_state<ND, false, T, T>(g, W, a2[0], a2[1], a2[2], s[3 + t]);
         }
 #pragma unroll
         for (int k = 0; k < ND; ++k)
@@ -186,12 +186,14 @@ __device__ __forceinline__ void k_omega_body(const VBlock& vb, const DevGrid& g,
         for (int m = 0; m < ND; ++m) gu[k][m] = T(g.cjac * g.cxh[m]) * du[m][k];
     } else {
       long long pq = plin(g, c[0], c[1], c[2]);
-      double J = g.jac[pq];
+      // J xi_hat: in the mixed form each factor is rounded to FP32 and the
+      // product taken there (FP32 arithmetic, two conversions, no FP64 multiply)
+      const T J = T(g.jac[pq]);
       T xm[3][3];
 #pragma unroll
       for (int l = 0; l < ND; ++l)
 #pragma unroll
-        for (int m = 0; m < ND; ++m) xm[l][m] = T(J * g.xh[(l * ND + m) * g.NP + pq]);
+        for (int m = 0; m < ND; ++m) xm[l][m] = J * T(g.xh[(l * ND + m) * g.NP + pq]);
 #pragma unroll
       for (int k = 0; k < ND; ++k)
 #pragma unroll
