@@ -185,7 +185,8 @@ struct JobNodeflux {
   Box fb;
   unsigned nb;
   __device__ void run(unsigned b) const {
-    k_lad_nodeflux_body<2, true, NF_LAD, T>(vblock_1d(b, nb), g, l, W, bt, kp, gr, dv, b3, Fn, fb, nullptr, 0);
+    k_lad_nodeflux_body<2, true, NF_LAD, T>(vblock_1d(b, nb), g, l, W, bt, kp, gr, dv, b3, nullptr, Box{}, Fn, fb,
+                                            nullptr, 0);
   }
 };
 

@@ -18,6 +18,8 @@ struct LadBuffers {
   double* D = nullptr;      // C6 flux derivative along one direction (line buffer DLB)
   double* df[3] = {nullptr, nullptr, nullptr};  // C6 computational derivatives of the fields (line buffers)
   double* lines = nullptr;  // right-hand sides / solutions of the filter lines
+  double* vco = nullptr;    // physical viscosity: mu, lambda, kappa at the nodes of vbx (3 planes)
+  Box vbx;                  // [-2, n+1]^nd: every node a node flux is taken at
   unsigned char* tr = nullptr;  // hybrid: troubled nodes on tbox ([-1, n]^nd)
   Box fbx, b3, tbox, fbox[3], hbox[3];
   LineBuf dfLB[3], DLB[3], filtLB[3];
@@ -308,7 +310,8 @@ constexpr int NF_LAD = 0, NF_LAD_VISC = 1, NF_VISC = 2;
 template <int ND, bool CART, int MODE, typename T>
 __device__ __forceinline__ void nodeflux_at(const DevGrid& g, int l, const T* __restrict__ W, const T* __restrict__ bt,
                                             const T* __restrict__ kp, const T* __restrict__ gr,
-                                            const T* __restrict__ dv, const Box& b3, const int* c, T* F) {
+                                            const T* __restrict__ dv, const Box& b3, const T* __restrict__ vco,
+                                            const Box& vbx, const int* c, T* F) {
   constexpr int NV = ND + 2, IP = ND + 1;
   constexpr bool CONV = MODE != NF_VISC, ART = MODE != NF_VISC, PHYS = MODE != NF_LAD;
   const long long bs = b3.size();
@@ -365,12 +368,12 @@ __device__ __forceinline__ void nodeflux_at(const DevGrid& g, int l, const T* __
       for (int m = 0; m < ND; ++m) F[1 + m] = (CART && m != l) ? fc[1 + m] : fc[1 + m] - xi[m] * tau;
       F[IP] = fc[IP] - fe;
     } else {
-      T Tt = T(g.gm2) * p / rho;
-      T S = T(g.suth);
-      T mu = Tt * sqrt(Tt) * (T(1.0) + S) / (Tt + S) / T(g.re);
-      T kth = mu / T(g.kc);
-      T lam = (ART ? bt[sq] : T(0)) - T(2.0 / 3.0) * mu;
-      T kap = (ART ? kp[sq] : T(0)) + kth;
+      // mu, lambda = beta* - 2/3 mu and kappa* + mu / ((gamma-1) Pr M^2) of
+      // the node, formed once per stage by k_lad_viscoef
+      const long long vq = vbx.at(c[0], c[1], c[2]), vs = vbx.size();
+      T mu = vco[vq];
+      T lam = vco[vs + vq];
+      T kap = vco[2 * vs + vq];
       T div = dv[be];
       T tau[ND][ND];
 #pragma unroll
@@ -413,7 +416,8 @@ __device__ __forceinline__ void nodeflux_at(const DevGrid& g, int l, const T* __
 template <int ND, bool CART, int MODE, typename T = double>
 __device__ __forceinline__ void k_lad_nodeflux_body(const VBlock& vb, const DevGrid& g, int l, const T* __restrict__ W, const T* __restrict__ bt,
                                const T* __restrict__ kp, const T* __restrict__ gr, const T* __restrict__ dv, Box b3,
-                               T* __restrict__ Fn, Box fb, const int* guard, int want) {
+                               const T* __restrict__ vco, Box vbx, T* __restrict__ Fn, Box fb, const int* guard,
+                               int want) {
   constexpr int NV = ND + 2;
   if (guard && *guard != want) return;
   long long fs = fb.size();
@@ -421,7 +425,7 @@ __device__ __forceinline__ void k_lad_nodeflux_body(const VBlock& vb, const DevG
     int c[3];
     box_coords(fb, e, c);
     T F[NV];
-    nodeflux_at<ND, CART, MODE, T>(g, l, W, bt, kp, gr, dv, b3, c, F);
+    nodeflux_at<ND, CART, MODE, T>(g, l, W, bt, kp, gr, dv, b3, vco, vbx, c, F);
 #pragma unroll
     for (int v = 0; v < NV; ++v) Fn[v * fs + e] = F[v];
   }
@@ -430,8 +434,46 @@ __device__ __forceinline__ void k_lad_nodeflux_body(const VBlock& vb, const DevG
 template <int ND, bool CART, int MODE, typename T = double>
 __global__ void k_lad_nodeflux(DevGrid g, int l, const T* __restrict__ W, const T* __restrict__ bt,
                                const T* __restrict__ kp, const T* __restrict__ gr, const T* __restrict__ dv, Box b3,
-                               T* __restrict__ Fn, Box fb, const int* guard, int want) {
-  k_lad_nodeflux_body<ND, CART, MODE, T>(hw_block(), g, l, W, bt, kp, gr, dv, b3, Fn, fb, guard, want);
+                               const T* __restrict__ vco, Box vbx, T* __restrict__ Fn, Box fb, const int* guard,
+                               int want) {
+  k_lad_nodeflux_body<ND, CART, MODE, T>(hw_block(), g, l, W, bt, kp, gr, dv, b3, vco, vbx, Fn, fb, guard, want);
+}
+
+// Physical viscosity of Eq. (3) with Sutherland's law at every node of vbx,
+// for the node fluxes of all directions: mu, lambda = beta* - 2/3 mu (beta*
+// added when ART, the LAD scheme with physical viscosity) and the
+// conductivity kappa* + mu / ((gamma-1) Pr M^2), each formed as the node
+// fluxes formed them.
+template <int ND, bool ART, typename T = double>
+__device__ __forceinline__ void k_lad_viscoef_body(const VBlock& vb, const DevGrid& g, const T* __restrict__ W,
+                                                   const T* __restrict__ bt, const T* __restrict__ kp,
+                                                   T* __restrict__ vco, Box vbx, const int* guard, int want) {
+  constexpr int NV = ND + 2, IP = ND + 1;
+  if (guard && *guard != want) return;
+  const long long vs = vbx.size();
+  BOX_LOOP(vbx, e) {
+    int c[3];
+    box_coords(vbx, e, c);
+    T w[NV];
+    load_state<ND, false, T, T>(g, W, c[0], c[1], c[2], w);
+    T rho = w[0], p = w[IP];
+    long long sq = scalar_src(g, c[0], c[1], c[2]);
+    T Tt = T(g.gm2) * p / rho;
+    T S = T(g.suth);
+    T mu = Tt * sqrt(Tt) * (T(1.0) + S) / (Tt + S) / T(g.re);
+    T kth = mu / T(g.kc);
+    T lam = (ART ? bt[sq] : T(0)) - T(2.0 / 3.0) * mu;
+    T kap = (ART ? kp[sq] : T(0)) + kth;
+    vco[e] = mu;
+    vco[vs + e] = lam;
+    vco[2 * vs + e] = kap;
+  }
+}
+
+template <int ND, bool ART, typename T = double>
+__global__ void k_lad_viscoef(DevGrid g, const T* __restrict__ W, const T* __restrict__ bt, const T* __restrict__ kp,
+                              T* __restrict__ vco, Box vbx, const int* guard, int want) {
+  k_lad_viscoef_body<ND, ART, T>(hw_block(), g, W, bt, kp, vco, vbx, guard, want);
 }
 
 // Stage epilogue shared by the LAD divergence kernels: tot = acc + D (or D),

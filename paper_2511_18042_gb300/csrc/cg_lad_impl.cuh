@@ -27,6 +27,10 @@ static int lad_alloc(cg_solver* s) {
       (rc = dalloc(&L.bt[1], (size_t)s->N)) || (rc = dalloc(&L.kp[0], (size_t)s->N)) ||
       (rc = dalloc(&L.kp[1], (size_t)s->N)) || (rc = dalloc(&L.Fn, (size_t)nv * fmax)))
     return rc;
+  if (s->p.viscous) {
+    L.vbx = make_box(s, 2, -1, 2);
+    if ((rc = dalloc(&L.vco, (size_t)3 * L.vbx.size()))) return rc;
+  }
   if (sch == CG_LAD_C6) {
     size_t dmax = 0, fl = 0;
     long long grad_cols = 0;
@@ -59,7 +63,8 @@ static int lad_alloc(cg_solver* s) {
 }
 
 static void lad_free(LadBuffers& L) {
-  double* bufs[] = {L.fb, L.gr, L.dv, L.bt[0], L.bt[1], L.kp[0], L.kp[1], L.Fn, L.D, L.df[0], L.df[1], L.df[2], L.lines};
+  double* bufs[] = {L.fb, L.gr, L.dv, L.bt[0], L.bt[1], L.kp[0], L.kp[1], L.Fn, L.D, L.df[0], L.df[1], L.df[2], L.lines,
+                    L.vco};
   for (double* b : bufs)
     if (b) cudaFree(b);
   if (L.tr) cudaFree(L.tr);
@@ -126,10 +131,26 @@ static void lad_nodeflux_m(cg_solver* s, int l, cudaStream_t st, const int* guar
   const T* gr = reinterpret_cast<const T*>(L.gr);
   const T* dv = reinterpret_cast<const T*>(L.dv);
   T* Fn = reinterpret_cast<T*>(L.Fn);
+  const T* vco = reinterpret_cast<const T*>(L.vco);
   if (s->dg.curv)
-    k_lad_nodeflux<ND, false, MODE, T><<<gb, 128, 0, st>>>(s->dg, l, reinterpret_cast<const T*>(s->W), bt, kp, gr, dv, L.b3, Fn, L.fbox[l], guard, want);
+    k_lad_nodeflux<ND, false, MODE, T><<<gb, 128, 0, st>>>(s->dg, l, reinterpret_cast<const T*>(s->W), bt, kp, gr, dv, L.b3, vco, L.vbx, Fn, L.fbox[l], guard, want);
   else
-    k_lad_nodeflux<ND, true, MODE, T><<<gb, 128, 0, st>>>(s->dg, l, reinterpret_cast<const T*>(s->W), bt, kp, gr, dv, L.b3, Fn, L.fbox[l], guard, want);
+    k_lad_nodeflux<ND, true, MODE, T><<<gb, 128, 0, st>>>(s->dg, l, reinterpret_cast<const T*>(s->W), bt, kp, gr, dv, L.b3, vco, L.vbx, Fn, L.fbox[l], guard, want);
+  s->launches++;
+}
+
+// mu, lambda, kappa of the physical viscosity at the nodes of every node flux
+// (art: with the LAD coefficients beta*, kappa* of bt[0], kp[0])
+template <int ND, typename T>
+static void lad_viscoef(cg_solver* s, cudaStream_t st, const int* guard, int want, bool art) {
+  LadBuffers& L = s->lad;
+  const T* W = reinterpret_cast<const T*>(s->W);
+  const T* bt = reinterpret_cast<const T*>(L.bt[0]);
+  const T* kp = reinterpret_cast<const T*>(L.kp[0]);
+  T* vco = reinterpret_cast<T*>(L.vco);
+  int gb = grid_blocks(L.vbx.size(), 256);
+  if (art) k_lad_viscoef<ND, true, T><<<gb, 256, 0, st>>>(s->dg, W, bt, kp, vco, L.vbx, guard, want);
+  else k_lad_viscoef<ND, false, T><<<gb, 256, 0, st>>>(s->dg, W, bt, kp, vco, L.vbx, guard, want);
   s->launches++;
 }
 
@@ -168,6 +189,7 @@ template <int ND, typename T>
 static void visc_pass(cg_solver* s, StageArgs A, cudaStream_t st, bool have_grad, const int* guard, int want) {
   LadBuffers& L = s->lad;
   if (!have_grad) lad_grad_e4<ND, T>(s, st, guard, want);
+  lad_viscoef<ND, T>(s, st, guard, want, false);
   for (int l = 0; l < ND; ++l) {
     lad_nodeflux<ND, T>(s, l, st, guard, want, NF_VISC);
     A.first = l == 0;
@@ -190,6 +212,7 @@ static int lad_pass(cg_solver* s, int dkind, StageArgs A, cudaStream_t st, const
   int rc = lad_coeffs_run<ND, T>(s, dkind, st, guard, want);
   if (rc) return rc;
   LadBuffers& L = s->lad;
+  if (s->p.viscous) lad_viscoef<ND, T>(s, st, guard, want, true);
   for (int l = 0; l < ND; ++l) {
     A.first = l == 0;
     A.last = l == ND - 1;
