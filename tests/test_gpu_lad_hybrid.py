@@ -173,3 +173,24 @@ def test_lad_3d(orc, api):
         Ug = to_dev(prob["U"])
         s.advance(Ug, nsteps=4)
         assert rel_err(Ug, Uo) <= 1e-12, kw
+
+
+@pytest.mark.parametrize("kw", [dict(scheme="LAD_E4"), dict(scheme="LAD_C6", cfl=0.1), dict(scheme="MIG4"),
+                                dict(scheme="HYBRID", hybrid_mode=1, hyb_p=1.5, hybrid_sensor=1)])
+def test_3d_mixed_form(orc, api, kw):
+    """The mixed form in 3D (compact lines along x, y and z, in FP32 for MIG4 and
+    LAD-C6): density L1 against the FP64 oracle after 4 steps <= 1e-5 of its mean."""
+    n = (18, 12, 10)
+    h = [1.0 / n[0], 1.0 / n[1], 1.0 / n[2]]
+    K, J, I = np.meshgrid(np.arange(n[2]), np.arange(n[1]), np.arange(n[0]), indexing="ij")
+    x, y, z = (I + 0.5) * h[0], (J + 0.5) * h[1], (K + 0.5) * h[2]
+    W = np.stack([1.0 + 0.5 * (x > 0.5), 0.2 * np.sin(2 * math.pi * y), 0.1 + 0 * x, 0.3 * np.cos(2 * math.pi * x),
+                  1.0 + 0.9 * (z > 0.5)])
+    prob = inputs._problem("box3d", 3, list(n), h, [[1, 1], [2, 2], [0, 0]], W, 1.4)
+    o = orc.Oracle(prob, **kw)
+    s = api.Solver.from_problem(prob, precision=1, **kw)
+    Uo, _, _ = o.advance(prob["U"], nsteps=4)
+    Ug = to_dev(prob["U"])
+    s.advance(Ug, nsteps=4)
+    rho = Ug[0].cpu().numpy()
+    assert np.abs(rho - Uo[0]).mean() / np.abs(Uo[0]).mean() <= 1e-5, kw

@@ -166,7 +166,7 @@ def test_compression_ramp_fp64_matches_oracle(orc, api, ramp, kw):
     assert rel_err(Ug, Uo) <= 1e-11
 
 
-@pytest.mark.parametrize("kw", [dict(scheme="MEG6"), dict(scheme="LAD_E4"),
+@pytest.mark.parametrize("kw", [dict(scheme="MEG6"), dict(scheme="MIG4"), dict(scheme="LAD_E4"),
                                 dict(scheme="HYBRID", hybrid_mode=1, hybrid_sensor=1, hyb_rho=0.4)])
 def test_compression_ramp_mixed_form(orc, api, ramp, kw):
     s = api.Solver.from_problem(ramp, precision=1, **kw)
