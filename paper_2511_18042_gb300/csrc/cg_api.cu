@@ -327,6 +327,22 @@ static void fill_devgrid(const cg_grid* g, const cg_params* p, DevGrid& d) {
   d.suth = p->suth;
   d.kc = (p->gamma - 1.0) * p->pr * p->minf * p->minf;
   for (int k = 0; k < 3; ++k) d.pf[k] = d.N / d.n[k];
+  d.f_gamma = (float)d.gamma;
+  d.f_gm1 = (float)d.gm1;
+  d.f_gm2 = (float)d.gm2;
+  d.f_cjac = (float)d.cjac;
+  for (int k = 0; k < 3; ++k) {
+    d.f_cxh[k] = (float)d.cxh[k];
+    d.f_ch[k] = (float)d.ch[k];
+    d.f_cg2[k] = (float)d.cg2[k];
+    d.f_cg[k] = (float)d.cg[k];
+    d.f_cig2[k] = (float)d.cig2[k];
+    for (int m = 0; m < 3; ++m) {
+      d.f_cn[k][m] = (float)d.cn[k][m];
+      d.f_ct1[k][m] = (float)d.ct1[k][m];
+      d.f_ct2[k][m] = (float)d.ct2[k][m];
+    }
+  }
 }
 
 static Box make_box(const cg_solver* s, int grow_all, int dir, int grow_dir) {
@@ -592,6 +608,11 @@ static GbrCfg gbr_cfg(const cg_solver* s) {
   q.eps = s->p.mp_eps;
   q.alpha = s->p.mp_alpha;
   q.window = s->p.omega_window;
+  q.f_gamma = (float)q.gamma;
+  q.f_gm1 = (float)q.gm1;
+  q.f_thr = (float)q.thr;
+  q.f_eps = (float)q.eps;
+  q.f_alpha = (float)q.alpha;
   return q;
 }
 

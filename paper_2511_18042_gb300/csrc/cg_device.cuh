@@ -49,7 +49,21 @@ struct DevGrid {
   // per-node inflow profiles (primitive, nv planes over the face), or null
   const double* prof[3][2];
   long long pf[3];    // nodes of a face normal to d
+  // FP32 copies of the constants the mixed form's kernels use, rounded once on
+  // the host: a conversion in the kernel would run on the FP64 pipe
+  float f_gamma, f_gm1, f_gm2;
+  float f_cxh[3], f_cjac, f_ch[3];
+  float f_cg2[3], f_cg[3], f_cig2[3];
+  float f_cn[3][3], f_ct1[3][3], f_ct2[3][3];
 };
+
+// A grid constant in the arithmetic type T: the FP64 value, or its FP32 copy
+// (the same float the conversion would give).
+template <typename T>
+__device__ __forceinline__ T gconst(double d, float f) {
+  if constexpr (sizeof(T) == 4) return f;
+  else return d;
+}
 
 __device__ __forceinline__ long long lin(const DevGrid& g, int i, int j, int k) {
   return (long long)i + (long long)g.n[0] * ((long long)j + (long long)g.n[1] * (long long)k);

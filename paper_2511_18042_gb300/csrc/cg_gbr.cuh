@@ -9,6 +9,7 @@ namespace cgk {
 struct GbrCfg {
   double gamma, gm1, thr, eps, alpha;
   int window;  // interface sensor window half-width
+  float f_gamma, f_gm1, f_thr, f_eps, f_alpha;  // FP32 copies for the mixed form
 };
 
 // interface frame: unit normal, tangents, averaged state and its sound speed
@@ -143,18 +144,19 @@ __device__ __forceinline__ void gbr_flux(const GbrCfg& q, const DevGrid& g, cons
                                          const T* xi, T* F) {
   constexpr int NV = ND + 2, IP = ND + 1;
   const T c12 = T(1.0 / 12.0);
-  const T gamma = T(q.gamma), gm1 = T(q.gm1), alpha = T(q.alpha), eps = T(q.eps), thr = T(q.thr);
+  const T gamma = gconst<T>(q.gamma, q.f_gamma), gm1 = gconst<T>(q.gm1, q.f_gm1),
+          alpha = gconst<T>(q.alpha, q.f_alpha), eps = gconst<T>(q.eps, q.f_eps), thr = gconst<T>(q.thr, q.f_thr);
   Frame<ND, T> fr;
   T g2, gg, ig2;
   if (CART) {
-    g2 = T(g.cg2[DIR]);
-    gg = T(g.cg[DIR]);
-    ig2 = T(g.cig2[DIR]);
+    g2 = gconst<T>(g.cg2[DIR], g.f_cg2[DIR]);
+    gg = gconst<T>(g.cg[DIR], g.f_cg[DIR]);
+    ig2 = gconst<T>(g.cig2[DIR], g.f_cig2[DIR]);
 #pragma unroll
     for (int m = 0; m < ND; ++m) {
-      fr.n[m] = T(g.cn[DIR][m]);
-      fr.t1[m] = T(g.ct1[DIR][m]);
-      fr.t2[m] = T(g.ct2[DIR][m]);
+      fr.n[m] = gconst<T>(g.cn[DIR][m], g.f_cn[DIR][m]);
+      fr.t1[m] = gconst<T>(g.ct1[DIR][m], g.f_ct1[DIR][m]);
+      fr.t2[m] = gconst<T>(g.ct2[DIR][m], g.f_ct2[DIR][m]);
     }
   } else {
     g2 = xi[0] * xi[0];
@@ -226,7 +228,7 @@ __device__ __forceinline__ void gbr_flux(const GbrCfg& q, const DevGrid& g, cons
   T xl[3];
   if (CART) {
 #pragma unroll
-    for (int m = 0; m < ND; ++m) xl[m] = (m == DIR) ? T(g.cxh[DIR]) : T(0);
+    for (int m = 0; m < ND; ++m) xl[m] = (m == DIR) ? gconst<T>(g.cxh[DIR], g.f_cxh[DIR]) : T(0);
   } else {
 #pragma unroll
     for (int m = 0; m < ND; ++m) xl[m] = xi[m];

@@ -534,14 +534,15 @@ __device__ __forceinline__ void k_cfl_max_body(const VBlock& vb, const DevGrid& 
     } else {
       cons_to_prim<ND>(g.gm1, Q, w);
     }
-    T cs = sqrt(T(g.gamma) * T(w[IP]) / T(w[0]));
+    T cs = sqrt(gconst<T>(g.gamma, g.f_gamma) * T(w[IP]) / T(w[0]));
     T s = T(0);
     T J;
     if (CART) {
-      J = T(g.cjac);
+      J = gconst<T>(g.cjac, g.f_cjac);
 #pragma unroll
       for (int l = 0; l < ND; ++l) {
-        T t = fabs(T(g.cxh[l]) * T(w[1 + l])) + cs * sqrt(T(g.cxh[l]) * T(g.cxh[l]));
+        const T xh = gconst<T>(g.cxh[l], g.f_cxh[l]);
+        T t = fabs(xh * T(w[1 + l])) + cs * sqrt(xh * xh);
         s = (l == 0) ? t : s + t;
       }
     } else {

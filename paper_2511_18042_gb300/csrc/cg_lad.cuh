@@ -34,9 +34,9 @@ __device__ __forceinline__ void lad_fields(const DevGrid& g, const T* w, T* f) {
   T rho = w[0], p = w[IP];
 #pragma unroll
   for (int k = 0; k < ND; ++k) f[k] = w[1 + k];
-  f[ND] = T(g.gm2) * p / rho;
+  f[ND] = gconst<T>(g.gm2, g.f_gm2) * p / rho;
   f[ND + 1] = rho;
-  f[ND + 2] = p / (rho * T(g.gm1));
+  f[ND + 2] = p / (rho * gconst<T>(g.gm1, g.f_gm1));
 }
 
 __device__ __forceinline__ void box_coords(const Box& b, long long e, int* c) {
@@ -175,7 +175,7 @@ __device__ __forceinline__ void k_lad_coef_body(const VBlock& vb, const DevGrid&
     T rho = w[0], p = w[IP];
     long long fq = fbx.at(c[0], c[1], c[2]);
     T Tt = fb[ND * fs + fq];
-    T cs = sqrt(T(g.gamma) * p / rho);
+    T cs = sqrt(gconst<T>(g.gamma, g.f_gamma) * p / rho);
     T div = dv[e0];
     T curl2 = T(0);
     auto G = [&](int f, int m) { return gr[(f * ND + m) * bs + e0]; };
@@ -221,8 +221,8 @@ __device__ __forceinline__ void k_lad_coef_body(const VBlock& vb, const DevGrid&
       // projections x_l . grad of rho (pr) and e (pe), x_l = dx/dxi_l
       T pr = T(0), pe;
       if (CART) {
-        if (comp) pr = T(g.ch[l]) * G(ND + 1, l);
-        pe = T(g.ch[l]) * G(ND + 2, l);
+        if (comp) pr = gconst<T>(g.ch[l], g.f_ch[l]) * G(ND + 1, l);
+        pe = gconst<T>(g.ch[l], g.f_ch[l]) * G(ND + 2, l);
       } else {
         long long pq = plin(g, c[0], c[1], c[2]);
         pe = T(g.dxl[(l * ND + 0) * g.NP + pq]) * G(ND + 2, 0);
@@ -321,7 +321,7 @@ __device__ __forceinline__ void nodeflux_at(const DevGrid& g, int l, const T* __
     T xi[3];
     if (CART) {
 #pragma unroll
-      for (int m = 0; m < ND; ++m) xi[m] = (m == l) ? T(g.cxh[l]) : T(0);
+      for (int m = 0; m < ND; ++m) xi[m] = (m == l) ? gconst<T>(g.cxh[l], g.f_cxh[l]) : T(0);
     } else {
       long long pq = plin(g, c[0], c[1], c[2]);
 #pragma unroll
@@ -340,7 +340,7 @@ __device__ __forceinline__ void nodeflux_at(const DevGrid& g, int l, const T* __
       q2 = w[1] * w[1];
 #pragma unroll
       for (int m = 1; m < ND; ++m) q2 = q2 + w[1 + m] * w[1 + m];
-      T E = p / T(g.gm1) + T(0.5) * rho * q2;
+      T E = p / gconst<T>(g.gm1, g.f_gm1) + T(0.5) * rho * q2;
       fc[0] = rho * U;
 #pragma unroll
       for (int m = 0; m < ND; ++m) fc[1 + m] = (CART && m != l) ? rho * w[1 + m] * U : rho * w[1 + m] * U + xi[m] * p;
