@@ -2,6 +2,7 @@
 // (tridiagonal) gradients, the fused C-GBR interface sweep with the residual
 // and RK epilogue, and the CFL reduction.
 #pragma once
+#include <type_traits>
 #include "cg_gbr.cuh"
 
 namespace cgk {
@@ -465,17 +466,20 @@ __device__ __forceinline__ void k_gbr_sweep_body(const VBlock& vb, const DevGrid
     long long qi = lin(g, c[0], c[1], c[2]);
     double J = CART ? g.cjac : g.jac[plin(g, c[0], c[1], c[2])];
     double out[NV];
+    // mixed form: the FP32 fluxes differenced and summed over the directions in
+    // FP32 (acc read as float), the stage total carried into the FP64 update
+    using TA = typename std::conditional<MIX, float, double>::type;
+    TA* acc = reinterpret_cast<TA*>(A.acc);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      // mixed form: the FP32 fluxes differenced in FP32, accumulated in FP64
-      double diff = MIX ? (double)(sF[IX(v, a + 1, l, TL)] - sF[IX(v, a, l, TL)])
-                        : (double)sF[IX(v, a + 1, l, TL)] - (double)sF[IX(v, a, l, TL)];
-      double tot = A.first ? diff : A.acc[v * g.N + qi] + diff;
+      TA diff = MIX ? TA(sF[IX(v, a + 1, l, TL)] - sF[IX(v, a, l, TL)])
+                    : TA((double)sF[IX(v, a + 1, l, TL)] - (double)sF[IX(v, a, l, TL)]);
+      TA tot = A.first ? diff : acc[v * g.N + qi] + diff;
       if (!A.last) {
-        A.acc[v * g.N + qi] = tot;
+        acc[v * g.N + qi] = tot;
         continue;
       }
-      double r = -(J * tot);
+      double r = -(J * double(tot));
       if (!A.rk) {
         A.R[v * g.N + qi] = r;
         continue;

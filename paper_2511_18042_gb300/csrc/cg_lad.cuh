@@ -4,6 +4,7 @@
 // E4 / C6 divergence; the eighth-order implicit filter of LAD-C6; the
 // troubled-node flags of the hybrid (Sec. 5).
 #pragma once
+#include <type_traits>
 #include "cg_kernels.cuh"
 
 namespace cgk {
@@ -480,20 +481,26 @@ __global__ void k_lad_viscoef(DevGrid g, const T* __restrict__ W, const T* __res
 // then store acc, R = -J tot, or the RK combination.
 // FUSED (mixed form): the FP64 accumulation and RK combination with explicit
 // fused multiply-adds; otherwise the oracle's operation order.
-template <int ND, bool FUSED = false>
+// FUSED (the mixed form) also sums the directions' flux differences in FP32:
+// acc then holds FP32 values (the buffer read as float), and only the stage
+// total enters the FP64 residual and update.
+template <int ND, bool FUSED = false, typename TD = double>
 __device__ __forceinline__ void lad_epilogue(const DevGrid& g, const StageArgs& A, long long qi, const int* c,
-                                             const double* Dv) {
+                                             const TD* Dv) {
   constexpr int NV = ND + 2, IP = ND + 1;
+  static_assert(FUSED || sizeof(TD) == 8, "the FP64 form accumulates in FP64");
+  using TA = typename std::conditional<FUSED, float, double>::type;
+  TA* acc = reinterpret_cast<TA*>(A.acc);
   double J = g.curv ? g.jac[plin(g, c[0], c[1], c[2])] : g.cjac;
   double out[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
-    double tot = A.first ? Dv[v] : A.acc[v * g.N + qi] + Dv[v];
+    TA tot = A.first ? TA(Dv[v]) : acc[v * g.N + qi] + TA(Dv[v]);
     if (!A.last) {
-      A.acc[v * g.N + qi] = tot;
+      acc[v * g.N + qi] = tot;
       continue;
     }
-    double r = -(J * tot);
+    double r = -(J * double(tot));
     if (!A.rk) {
       A.R[v * g.N + qi] = r;
       continue;
@@ -544,20 +551,20 @@ __global__ void k_lad_div(DevGrid g, int l, const T* __restrict__ Fn, Box fb, co
     c[0] = (int)(q % g.n[0]);
     c[1] = (int)((q / g.n[0]) % g.n[1]);
     c[2] = (int)(q / ((long long)g.n[0] * g.n[1]));
-    double Dv[NV];
+    T Dv[NV];
     if (D) {
 #pragma unroll
-      for (int v = 0; v < NV; ++v) Dv[v] = (double)D[DL.at(v, c[l], c)];
+      for (int v = 0; v < NV; ++v) Dv[v] = D[DL.at(v, c[l], c)];
     } else {
       long long e = fb.at(c[0], c[1], c[2]);
       long long st = l == 0 ? 1 : (l == 1 ? (long long)fb.ext[0] : (long long)fb.ext[0] * fb.ext[1]);
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         const T* f = Fn + v * fs;
-        Dv[v] = (double)d4(f[e - 2 * st], f[e - st], f[e + st], f[e + 2 * st]);
+        Dv[v] = d4(f[e - 2 * st], f[e - st], f[e + st], f[e + 2 * st]);
       }
     }
-    lad_epilogue<ND, sizeof(T) == 4>(g, A, q, c, Dv);
+    lad_epilogue<ND, sizeof(T) == 4, T>(g, A, q, c, Dv);
   }
 }
 
