@@ -526,7 +526,10 @@ __global__ void __launch_bounds__(256, sweep_min_blocks<ND, CART, T>()) k_gbr_sw
 template <int ND, bool CART, typename T = double>
 __device__ __forceinline__ void k_cfl_max_body(const VBlock& vb, const DevGrid& g, const double* __restrict__ U, unsigned long long* __restrict__ mx) {
   constexpr int NV = ND + 2, IP = ND + 1;
-  double best = 0.0;
+  // the running maximum in T: the largest float converted once equals the
+  // largest of the converted floats (conversion keeps order), so the FP32 form
+  // compares in FP32 and the FP64 form is unchanged
+  T best = T(0);
   for (long long q = vb.x * (long long)blockDim.x + threadIdx.x; q < g.N;
        q += (long long)vb.gx * blockDim.x) {
     double Q[NV];
@@ -568,13 +571,14 @@ __device__ __forceinline__ void k_cfl_max_body(const VBlock& vb, const DevGrid& 
         s = (l == 0) ? t : s + t;
       }
     }
-    double r = double(J * s);
+    T r = J * s;
     if (r > best) best = r;
   }
   // block max, then one atomic (non-negative doubles order like their bits)
   __shared__ double red[32];
   for (int o = 16; o > 0; o >>= 1) best = dmax(best, __shfl_xor_sync(0xffffffffu, best, o));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = best;
+  const double bestd = double(best);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = bestd;
   __syncthreads();
   if (threadIdx.x < 32) {
     double b = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
