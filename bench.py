@@ -81,7 +81,7 @@ class ClockSampler:
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -93,7 +93,7 @@ class ClockSampler:
         for line in self.proc.stdout:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) >= 9:
-                self.rows.append(parts)
+                self.rows.append((time.time(), parts))
 
     def __exit__(self, *a):
         if self.proc:
@@ -103,15 +103,24 @@ class ClockSampler:
             except Exception:
                 self.proc.kill()
 
+    def mark(self, start):
+        """Wall-clock bounds of the timed region (samples outside it are dropped)."""
+        if start:
+            self.t0 = time.time()
+        else:
+            self.t1 = time.time()
+
     def summary(self):
-        if not self.rows:
+        t0, t1 = getattr(self, "t0", None), getattr(self, "t1", None)
+        rows = [r for t, r in self.rows if t0 is None or (t0 - 0.15 <= t <= (t1 or t) + 0.15)]
+        if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(self.rows)}
+                "reasons": reasons, "samples": len(rows)}
 
 
 def _dist():
@@ -180,6 +189,9 @@ def run_gpu(args):
             if events is not None:
                 events[n][1].record(stream)
 
+    # the clock sampler starts before the warm-up (nvidia-smi takes a moment to
+    # start); only its samples inside the timed region are kept
+    clk = ClockSampler(local).__enter__()
     for _ in range(args.warmup):
         one_step()
     torch.cuda.synchronize()
@@ -189,7 +201,8 @@ def run_gpu(args):
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
+    try:
+        clk.mark(True)
         wall0 = time.perf_counter()
         for _ in range(args.steps):
             flush.zero_()  # evict L2 (256 MB > 126 MB) between timed steps
@@ -204,6 +217,9 @@ def run_gpu(args):
             step_ms.append(tot)
         torch.cuda.synchronize()
         wall = time.perf_counter() - wall0
+        clk.mark(False)
+    finally:
+        clk.__exit__(None, None, None)
     launches = sum(s.launch_count() for s in solvers.values()) - launches0
     for n in names:
         rc = solvers[n].sync_status()
@@ -595,7 +611,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="cgflow", choices=["cgflow", "reference"])
     ap.add_argument("--schemes", default=None, help="comma-separated subset (default: all six)")
