@@ -1,6 +1,6 @@
 """GPU parity of the C-GBR path (MEG6 / MIG4) against the oracle.
 
-The bar is the benchmark spec's tolerance, max relative error <= 1e-11 per variable
+The bar is the parity tolerance, max relative error <= 1e-11 per variable
 after 100 RK3 steps (relative to the variable's largest magnitude), and
 <= 1e-13 for a single RHS evaluation.  The interface sweep (default form)
 evaluates every expression in the oracle's operation order without

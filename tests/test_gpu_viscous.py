@@ -184,7 +184,7 @@ def test_compression_ramp_fma_form(orc, api, ramp, kw):
     """The opt-in FMA form (the interface sweep's multiply-adds fused): the
     residual of this nearly balanced boundary layer is ~1e-3 of the flux
     scale |F|/h, so rounding-level flux differences read ~1e-12 against it;
-    after steps the state agrees to the spec bar."""
+    after steps the state agrees to the 1e-11 parity bar."""
     s = api.Solver.from_problem(ramp, fma_sweep=1, **kw)
     o = orc.Oracle(ramp, **kw)
     U = ramp["U"]
