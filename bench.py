@@ -232,7 +232,9 @@ def run_gpu(args):
     mixed = {}
     for n, kw in MIXED:
         ms, tile = time_mixed(api, torch, grid, base, dev, kw, args)
-        mixed[n] = {"cell_updates_per_s": cells / (ms * 1e-3), "ms_per_rk3_step": ms, "tile_lines": list(tile)}
+        cu = cells / (ms * 1e-3)
+        mixed[n] = {"cell_updates_per_s": cu, "ms_per_rk3_step": ms, "tile_lines": list(tile),
+                    "hbm_frac_of_measured": cu * HBM_BYTES_PER_CELL_STEP / (_peaks()["hbm_gbs"] * 1e9)}
 
     sod = run_sod_latency(api, torch, dev) if args.sod else None
     ramp = run_ramp(api, torch, dev, args) if args.ramp else None
