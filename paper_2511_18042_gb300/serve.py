@@ -10,12 +10,6 @@ once and its result is read back to the host; new requests join at the next
 tick.  Latency = result on the host minus arrival.  The scheme is the
 per-interface hybrid LAD-GBR in the mixed form (FP32 fluxes, FP64
 accumulation) unless told otherwise.
-
-A tick lasts as long as its largest member's step.  A member whose step costs
-a small fraction of that (a short tube beside a 1024^2 grid) takes up to
-MAX_SUBSTEPS steps in the same tick (its own CFL step each time), so that it
-is not held to the pace of the largest member; its results are those of the
-same number of steps taken one per tick.
 """
 import math
 import time
@@ -85,17 +79,6 @@ def bytes_estimate(prob):
     return 8 * nv * cells * 40
 
 
-MAX_SUBSTEPS = 8  # steps a cheap member may take in one tick
-SUBSTEP_RATIO = 4  # a member takes k steps when its step costs under 1/(k * SUBSTEP_RATIO) of the largest
-
-
-def substeps(cells, cells_max, left):
-    """Steps a member of `cells` cells takes in a tick whose largest member has
-    cells_max cells (per-step cost taken proportional to the cells)."""
-    k = cells_max // max(1, SUBSTEP_RATIO * cells)
-    return int(max(1, min(MAX_SUBSTEPS, k, left)))
-
-
 def run(requests, budget_bytes=100 << 30, precision=1, device="cuda", max_active=None):
     """Serve the requests; returns (stats dict, requests with results)."""
     dev = torch.device(device)
@@ -128,19 +111,15 @@ def run(requests, budget_bytes=100 << 30, precision=1, device="cuda", max_active
                 time.sleep(min(wait, 0.05))
             continue
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        cmax = max(r.cells for r in active)
-        k = {r.rid: substeps(r.cells, cmax, r.left) for r in active}
         e0.record(stream)
-        for j in range(max(k.values())):
-            part = [r for r in active if k[r.rid] > j]
-            api.multi_step([r.solver for r in part], [r.state for r in part], stream=stream)
+        api.multi_step([r.solver for r in active], [r.state for r in active], stream=stream)
         e1.record(stream)
         e1.synchronize()
         gpu_ms += e0.elapsed_time(e1)
         ticks += 1
         still = []
         for r in active:
-            r.left -= k[r.rid]
+            r.left -= 1
             if r.left == 0:
                 r.result = r.state.cpu().numpy()
                 r.done_at = time.perf_counter() - t0
