@@ -53,7 +53,7 @@ DEVELOP_STEPS = 200
 SWEEP_FLOP_PER_IFACE = 632.2  # profiles/sweep_meg6_triple_point_1792x768.md (mean of x and y)
 # dram read + write per launch (mean of x and y) of the sweep form the roofline times,
 # from its ncu capture (profiles/); None until the current kernel has been captured
-SWEEP_TRAFFIC_BYTES = {"exact": 91.90e6, "contracted": 139.8e6}
+SWEEP_TRAFFIC_BYTES = {"exact": 92.0e6, "contracted": 140.2e6}
 ROOFLINE_FORM = "exact"  # the library default (fma_sweep = 0)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12  # SMs x DFMA/clk x 2 flop x max clock
 HBM_BYTES_PER_CELL_STEP = 256.0  # minimal-traffic model, FP64 state, nv = 4, uniform grid
