@@ -147,25 +147,22 @@ __device__ __forceinline__ void k_omega_body(const VBlock& vb, const DevGrid& g,
     const T p0 = T(w0d[IP]);
 #pragma unroll
     for (int l = 0; l < ND; ++l) {
-      int cm[3] = {c[0], c[1], c[2]}, cp[3] = {c[0], c[1], c[2]};
-      cm[l] -= 1;
-      cp[l] += 1;
-      T wm[NV], wp[NV];
-      load_state<ND, false, T, T>(g, W, cm[0], cm[1], cm[2], wm);
-      load_state<ND, false, T, T>(g, W, cp[0], cp[1], cp[2], wp);
-      const T pm = T(wm[IP]), pp = T(wp[IP]);
+      // neighbours c-3..c-1, c+1..c+3 along l (c-1, c+1 only with compact
+      // gradients) from one load site: the boundary resolution is inlined once
+      // per direction instead of once per neighbour, which kept the 3D kernel's
+      // code out of the instruction cache
+      T s[6][NV];
+      const int t0 = COMPACT ? 2 : 0, t1 = COMPACT ? 4 : 6;
+#pragma unroll 1
+      for (int t = t0; t < t1; ++t) {
+        int a[3] = {c[0], c[1], c[2]};
+        a[l] += t < 3 ? t - 3 : t - 2;
+        load_state<ND, false, T, T>(g, W, a[0], a[1], a[2], s[t]);
+      }
+      const T pm = T(s[2][IP]), pp = T(s[3][IP]);
       T a = fabs(pp - T(2.0) * p0 + pm) / (pp + T(2.0) * p0 + pm);
       if (a > phi) phi = a;
       if (!COMPACT) {
-        T s[6][NV];
-#pragma unroll
-        for (int t = 0; t < 3; ++t) {
-          int a1[3] = {c[0], c[1], c[2]}, a2[3] = {c[0], c[1], c[2]};
-          a1[l] -= 3 - t;
-          a2[l] += 1 + t;
-          load_state<ND, false, T, T>(g, W, a1[0], a1[1], a1[2], s[t]);
-          load_state<ND, false, T, T>(g, W, a2[0], a2[1], a2[2], s[3 + t]);
-        }
 #pragma unroll
         for (int k = 0; k < ND; ++k)
           du[l][k] = d6<T>(T(s[0][1 + k]), T(s[1][1 + k]), T(s[2][1 + k]), T(s[3][1 + k]), T(s[4][1 + k]),
