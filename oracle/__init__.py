@@ -8,8 +8,8 @@ The arithmetic lives in ``cg_oracle.c`` (plain C, FP64, compiled with
 ``-ffp-contract=off``); this module builds it with gcc and wraps it with ctypes.
 ``riemann_exact`` holds the textbook exact Riemann solver used as a pin.
 
-Functions without an independent pin are listed as "parity unpinned" in
-``cg_oracle.c``'s header comment and in the design notes.
+A function without an independent pin would be listed as "parity unpinned" in
+``cg_oracle.c``'s header comment and in the design notes; every function has one.
 """
 import ctypes
 import math

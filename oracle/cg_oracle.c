@@ -29,16 +29,14 @@
  * of the Gaussian and implicit filters; design order from the stencils
  * (sympy); RK3 order; periodic conservation; freestream on curvilinear 2D/3D
  * grids; exact metrics of an affine grid; x<->y symmetry of the 2D Riemann
- * configuration 3; hybrid limits; CFL closed form; hand values of beta* and of
- * the sensor.  Viscous terms (tests/test_oracle_viscous.py): discrete decay
+ * configuration 3; hybrid limits; CFL closed form; hand values of beta*, of
+ * kappa* and of the sensor.  Viscous terms (tests/test_oracle_viscous.py): discrete decay
  * rate of periodic and wall-bounded shear waves (E4 and C6 modified
  * wavenumbers) and their energy source; the isothermal no-slip wall as the
  * mirror of the doubled periodic channel; fourth-order convergence of the 3D
  * viscous terms on Cartesian and curvilinear grids and of heat conduction at
  * rest; a parallel flow fed by its own inflow profile is steady; Sutherland
- * against tabulated air viscosity.  Parity unpinned: the value of the thermal
- * coefficient kappa* (exercised only through the LAD conservation, freestream
- * and Sod tests).
+ * against tabulated air viscosity.
  */
 #include <math.h>
 #include <stdlib.h>

@@ -485,7 +485,30 @@ def test_lad_bulk_coefficient_hand_value(orc):
     beta, _ = orc.Oracle(prob, scheme="LAD_E4").lad_coeffs(prob["U"])
     want = 1.75 * 120.0 * h ** 6 * (1.0 + 0.1 * x)
     sl = slice(10, n - 10)
-    assert np.allclose(beta[sl], want[sl], rtol=1e-7)
+    assert np.allclose(beta[sl], want[sl], rtol=1e-7, atol=0.0)
+
+
+def test_lad_conductivity_hand_value(orc):
+    """kappa* for rho = 1, u = 0, e = 2.5 + x^4/10 (1D, E4): the five-point fourth
+    difference of the quartic is 24 h^4 / 10; Delta_kappa = |h de/dx| / |de/dx| = h;
+    rho c / T = 1 / sqrt(gamma p) (T = gamma p / rho at M = 1); so the raw
+    coefficient is C_kappa 2.4 h^5 / sqrt(gamma p(x)), then the truncated-Gaussian
+    overbar of Cook & Cabot (nine points) along x."""
+    n = 64
+    h = 1.0 / n
+    gamma = 1.4
+    x = 0.5 + (np.arange(n) + 0.5) * h
+    e = 2.5 + 0.1 * x ** 4
+    p = (gamma - 1.0) * e
+    W = np.stack([np.ones(n), np.zeros(n), p])
+    prob = inputs._problem("lad", 1, [n], [h], [[1, 1]], W, gamma)
+    _, kappa = orc.Oracle(prob, scheme="LAD_E4").lad_coeffs(prob["U"])
+    raw = 0.01 * 2.4 * h ** 5 / np.sqrt(gamma * p)
+    wts = [3565.0 / 10368.0, 3091.0 / 12960.0, 1997.0 / 25920.0, 149.0 / 12960.0, 107.0 / 103680.0]
+    assert abs(wts[0] + 2.0 * sum(wts[1:]) - 1.0) < 1e-15
+    sl = np.arange(12, n - 12)
+    want = wts[0] * raw[sl] + sum(wts[t] * (raw[sl - t] + raw[sl + t]) for t in range(1, 5))
+    assert np.allclose(kappa[sl], want, rtol=1e-6, atol=0.0)
 
 
 def test_sensor_hand_values(orc):
