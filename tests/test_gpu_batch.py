@@ -101,3 +101,29 @@ def test_multi_step_member_matches_oracle(orc, api):
         o = orc.Oracle(p, scheme="MEG6")
         Uo, _, _ = o.advance(p["U"], nsteps=10)
         assert rel_err(U, Uo) <= 1e-11
+
+
+def test_full_batch_sampled_members(api):
+    """The batched workload at full size, as the benchmark runs it: 256 quadrant
+    problems (64^2..512^2, seed 0), per-interface hybrid in the mixed form,
+    autotuned batch (work table or stream pool), graph replays; eight sampled
+    members match the same members advanced alone with their tuned tile shapes."""
+    from bench import _hybrid_kw
+    probs = inputs.batched_riemann(count=256, seed=0)
+    solvers = [api.Solver.from_problem(p, **_hybrid_kw(p, 1)) for p in probs]
+    Ub = [to_dev(p["U"]) for p in probs]
+    stream = torch.cuda.Stream()
+    batch = api.Batch(solvers, Ub)
+    with torch.cuda.stream(stream):
+        batch.autotune(stream)
+        for _ in range(4):  # eager, capture, replays
+            batch.step(stream)
+    stream.synchronize()
+    rng = np.random.default_rng(1)
+    for m in sorted(rng.choice(len(probs), size=8, replace=False)):
+        a = api.Solver.from_problem(probs[m], **_hybrid_kw(probs[m], 1))
+        a.set_tile_shape(solvers[m].tile_shape())
+        U = to_dev(probs[m]["U"])
+        a.advance(U, nsteps=4)
+        torch.cuda.synchronize()
+        same_member(U, Ub[m], dict(precision=1))
