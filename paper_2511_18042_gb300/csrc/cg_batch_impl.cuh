@@ -207,7 +207,8 @@ static int table_build_t(BatchTable& tb, cg_solver* const* sv, double* const* st
     for (int l = 0; l < 2; ++l) {
       nf[l][m] = JobNodeflux<T>{s->dg, l, W, bt[0], kp[0], g, dv, L.b3, reinterpret_cast<T*>(L.Fn), L.fbox[l],
                                 (unsigned)table_blocks(L.fbox[l].size())};
-      hf[l][m] = JobHflux<T>{s->dg, l, reinterpret_cast<const T*>(L.Fn), L.fbox[l], s->hflux[l], L.hbox[l],
+      hf[l][m] = JobHflux<T>{s->dg, l, reinterpret_cast<const T*>(L.Fn), L.fbox[l],
+                             reinterpret_cast<T*>(s->hflux[l]), L.hbox[l],
                              (unsigned)table_blocks(L.hbox[l].size())};
     }
   }

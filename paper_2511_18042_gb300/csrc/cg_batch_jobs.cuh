@@ -196,7 +196,7 @@ struct JobHflux {
   int l;
   const T* Fn;
   Box fb;
-  double* H;
+  T* H;
   Box hb;
   unsigned nb;
   __device__ void run(unsigned b) const { k_lad_hflux_body<2, T>(vblock_1d(b, nb), g, l, Fn, fb, H, hb); }

@@ -38,7 +38,8 @@ struct StageArgs {
   Box tBox;
   const int* guard;           // global hybrid: the kernel runs only if *guard == guard_want
   int guard_want;
-  const double* hflux;        // per-interface hybrid: LAD flux-form interface fluxes (nv planes on hBox)
+  const void* hflux;          // per-interface hybrid: LAD flux-form interface fluxes (nv planes on hBox,
+                              // in the sweep's arithmetic type)
   Box hBox;
   double* iface_out;          // diagnostics: interface fluxes [v][line][n+1] (NULL: none)
   const float* Wf;            // mixed form: the primitives stored in FP32
@@ -435,7 +436,7 @@ __device__ __forceinline__ void k_gbr_sweep_body(const VBlock& vb, const DevGrid
       long long hi = A.hBox.at(c[0], c[1], c[2]);
       long long hs = A.hBox.size();
 #pragma unroll
-      for (int v = 0; v < NV; ++v) F[v] = T(A.hflux[v * hs + hi]);
+      for (int v = 0; v < NV; ++v) F[v] = static_cast<const T*>(A.hflux)[v * hs + hi];
     } else {
 #pragma unroll
       for (int v = 0; v < NV; ++v) F[v] = T(0);

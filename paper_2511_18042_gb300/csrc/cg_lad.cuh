@@ -606,7 +606,7 @@ __global__ void k_troubled(DevGrid g, const TW* __restrict__ W, double hr, doubl
 // Per-interface hybrid: LAD flux at interfaces i+1/2 (i in [-1, n-1]) in the
 // conservative E4 flux form h = 7/12 (F_i + F_{i+1}) - 1/12 (F_{i-1} + F_{i+2}).
 template <int ND, typename T = double>
-__device__ __forceinline__ void k_lad_hflux_body(const VBlock& vb, const DevGrid& g, int l, const T* __restrict__ Fn, Box fb, double* __restrict__ H, Box hb) {
+__device__ __forceinline__ void k_lad_hflux_body(const VBlock& vb, const DevGrid& g, int l, const T* __restrict__ Fn, Box fb, T* __restrict__ H, Box hb) {
   constexpr int NV = ND + 2;
   long long fs = fb.size(), hs = hb.size();
   long long st = l == 0 ? 1 : (l == 1 ? (long long)fb.ext[0] : (long long)fb.ext[0] * fb.ext[1]);
@@ -617,13 +617,13 @@ __device__ __forceinline__ void k_lad_hflux_body(const VBlock& vb, const DevGrid
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       const T* f = Fn + v * fs;
-      H[v * hs + e] = (double)(T(7.0 / 12.0) * (f[q] + f[q + st]) - T(1.0 / 12.0) * (f[q - st] + f[q + 2 * st]));
+      H[v * hs + e] = T(7.0 / 12.0) * (f[q] + f[q + st]) - T(1.0 / 12.0) * (f[q - st] + f[q + 2 * st]);
     }
   }
 }
 
 template <int ND, typename T = double>
-__global__ void k_lad_hflux(DevGrid g, int l, const T* __restrict__ Fn, Box fb, double* __restrict__ H, Box hb) {
+__global__ void k_lad_hflux(DevGrid g, int l, const T* __restrict__ Fn, Box fb, T* __restrict__ H, Box hb) {
   k_lad_hflux_body<ND, T>(hw_block(), g, l, Fn, fb, H, hb);
 }
 

@@ -56,8 +56,13 @@ static int lad_alloc(cg_solver* s) {
   }
   if (sch == CG_HYBRID) {
     if ((rc = dalloc(&L.tr, (size_t)L.tbox.size()))) return rc;
-    for (int d = 0; d < nd; ++d)
-      if ((rc = dalloc(&s->hflux[d], (size_t)nv * L.hbox[d].size()))) return rc;
+    // interface fluxes in the arithmetic type of the LAD pass and the sweep
+    // (FP32 in the mixed form, stored in half as many doubles)
+    for (int d = 0; d < nd; ++d) {
+      size_t cnt = (size_t)nv * L.hbox[d].size();
+      if (s->p.precision == CG_MIXED) cnt = (cnt + 1) / 2;
+      if ((rc = dalloc(&s->hflux[d], cnt))) return rc;
+    }
   }
   return CG_OK;
 }
@@ -279,7 +284,7 @@ static int lad_stage_t(cg_solver* s, const double* Uc, StageArgs A, cudaStream_t
   for (int l = 0; l < ND; ++l) {
     lad_nodeflux<ND, T>(s, l, st, nullptr, 0);
     k_lad_hflux<ND, T><<<grid_blocks(L.hbox[l].size(), 256), 256, 0, st>>>(s->dg, l, reinterpret_cast<const T*>(L.Fn),
-                                                                          L.fbox[l], s->hflux[l], L.hbox[l]);
+                                                                          L.fbox[l], reinterpret_cast<T*>(s->hflux[l]), L.hbox[l]);
     s->launches++;
   }
   StageArgs H = A;
