@@ -165,6 +165,9 @@ CG_API int cg_advance_host(cg_solver *s, double *U_host, int64_t nsteps, double 
                            double *t_out, void *stream);
 
 /* Diagnostics. */
+/* Discontinuity sensor Omega^d (the switch of the wave-appropriate selection,
+ * Eq. 8) of state U at the n0*n1*n2 nodes, written to omega in FP64; the mixed
+ * form computes and keeps it in FP32 and widens it on return.  Synchronises. */
 CG_API int cg_omega(cg_solver *s, const double *U, double *omega, void *stream);
 CG_API int cg_lad_coeffs(cg_solver *s, const double *U, double *beta, double *kappa, void *stream);
 CG_API int cg_filter(cg_solver *s, double *U, void *stream);

@@ -593,7 +593,7 @@ static void launch_omega(cg_solver* s, cudaStream_t st, const int* guard, int wa
     k_omega<ND, CART, COMPACT, float><<<grid_blocks(tot, 128), 128, 0, st>>>(
         s->dg, reinterpret_cast<const float*>(s->W), reinterpret_cast<const float*>(s->G[0]),
         reinterpret_cast<const float*>(s->G[1]), reinterpret_cast<const float*>(s->G[2]), s->gdLB[0], s->gdLB[1],
-        s->gdLB[2], s->om, s->omBox, guard, want);
+        s->gdLB[2], reinterpret_cast<float*>(s->om), s->omBox, guard, want);
   else
     k_omega<ND, CART, COMPACT, double><<<grid_blocks(tot, 128), 128, 0, st>>>(
         s->dg, s->W, s->G[0], s->G[1], s->G[2], s->gdLB[0], s->gdLB[1], s->gdLB[2], s->om, s->omBox, guard, want);
@@ -1362,8 +1362,15 @@ CG_API int cg_omega(cg_solver* s, const double* U, double* omega, void* stream) 
   // interior part of the sensor box
   Box ob = s->omBox;
   std::vector<double> box((size_t)ob.size()), in((size_t)s->N);
-  CG_CUDA(cudaMemcpyAsync(box.data(), s->om, box.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
-  CG_CUDA(cudaStreamSynchronize(st));
+  if (s->p.precision == CG_MIXED) {  // the mixed form keeps the sensor in FP32
+    std::vector<float> boxf(box.size());
+    CG_CUDA(cudaMemcpyAsync(boxf.data(), s->om, boxf.size() * sizeof(float), cudaMemcpyDeviceToHost, st));
+    CG_CUDA(cudaStreamSynchronize(st));
+    for (size_t i = 0; i < box.size(); ++i) box[i] = boxf[i];
+  } else {
+    CG_CUDA(cudaMemcpyAsync(box.data(), s->om, box.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CG_CUDA(cudaStreamSynchronize(st));
+  }
   for (int k = 0; k < s->dg.n[2]; ++k)
     for (int j = 0; j < s->dg.n[1]; ++j)
       for (int i = 0; i < s->dg.n[0]; ++i)

@@ -181,12 +181,12 @@ static int table_build_t(BatchTable& tb, cg_solver* const* sv, double* const* st
       o.G[d] = reinterpret_cast<const T*>(s->G[d]);
       o.gb[d] = s->gdLB[d];
     }
-    o.om = s->om;
+    o.om = reinterpret_cast<T*>(s->om);
     o.ob = s->omBox;
     o.nb = (unsigned)table_blocks(s->omBox.size());
     om[m] = o;
     fd[m] = JobField<T>{s->dg, W, fb, L.fbx, (unsigned)table_blocks(L.fbx.size())};
-    tr[m] = JobTroubled<T>{s->dg, W, s->p.hyb_rho, s->p.hyb_p, s->p.hybrid_sensor ? s->om : nullptr, s->omBox,
+    tr[m] = JobTroubled<T>{s->dg, W, s->p.hyb_rho, s->p.hyb_p, s->p.hybrid_sensor ? reinterpret_cast<const T*>(s->om) : nullptr, s->omBox,
                            s->p.sensor_thresh, L.tr, L.tbox, s->hyb_flag, s->hyb_count,
                            (unsigned)table_blocks(L.tbox.size())};
     JobGrad<T> j;

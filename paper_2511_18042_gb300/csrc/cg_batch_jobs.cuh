@@ -88,7 +88,7 @@ struct JobOmega {
   const T* W;
   const T* G[3];
   LineBuf gb[3];
-  double* om;
+  T* om;
   Box ob;
   unsigned nb;
   __device__ void run(unsigned b) const {
@@ -112,7 +112,7 @@ struct JobTroubled {
   DevGrid g;
   const T* W;
   double hr, hp;
-  const double* om;
+  const T* om;
   Box ob;
   double thr;
   unsigned char* tr;

@@ -19,7 +19,7 @@ struct Box {
 // Everything the stage kernels read and write besides the grid.
 struct StageArgs {
   const double* W;     // primitives (nv planes, interior)
-  const double* om;    // sensor on omBox
+  const void* om;      // sensor on omBox, in the stage's arithmetic type
   Box omBox;
   const double* Gd;    // compact gradients along the sweep direction (line buffer gdLB)
   LineBuf gdLB;
@@ -99,7 +99,7 @@ __global__ void k_prim(DevGrid g, const double* __restrict__ U, TW* __restrict__
 template <int ND, bool CART, bool COMPACT, typename T = double>
 __device__ __forceinline__ void k_omega_body(const VBlock& vb, const DevGrid& g, const T* __restrict__ W, const T* __restrict__ G0,
                         const T* __restrict__ G1, const T* __restrict__ G2, LineBuf gb0,
-                        LineBuf gb1, LineBuf gb2, double* __restrict__ om, Box ob, const int* guard, int want) {
+                        LineBuf gb1, LineBuf gb2, T* __restrict__ om, Box ob, const int* guard, int want) {
   constexpr int NV = ND + 2, IP = ND + 1;
   if (guard && *guard != want) return;
   long long tot = ob.size();
@@ -217,14 +217,14 @@ __device__ __forceinline__ void k_omega_body(const VBlock& vb, const DevGrid& g,
       T w1 = gu[2][1] - gu[1][2], w2 = gu[0][2] - gu[2][0], w3 = gu[1][0] - gu[0][1];
       zeta = (div * div + eps) / (div * div + (w1 * w1 + w2 * w2 + w3 * w3) + eps);
     }
-    om[ob.at(c[0], c[1], c[2])] = double(phi * zeta);
+    om[ob.at(c[0], c[1], c[2])] = phi * zeta;
   }
 }
 
 template <int ND, bool CART, bool COMPACT, typename T = double>
 __global__ void k_omega(DevGrid g, const T* __restrict__ W, const T* __restrict__ G0,
                         const T* __restrict__ G1, const T* __restrict__ G2, LineBuf gb0,
-                        LineBuf gb1, LineBuf gb2, double* __restrict__ om, Box ob, const int* guard, int want) {
+                        LineBuf gb1, LineBuf gb2, T* __restrict__ om, Box ob, const int* guard, int want) {
   k_omega_body<ND, CART, COMPACT, T>(hw_block(), g, W, G0, G1, G2, gb0, gb1, gb2, om, ob, guard, want);
 }
 
@@ -350,13 +350,13 @@ __device__ __forceinline__ void k_gbr_sweep_body(const VBlock& vb, const DevGrid
     int r = DIR == 0 ? e % RO : e / LW;
     int l = DIR == 0 ? e / RO : e % LW;
     int c[3] = {0, 0, 0};
-    double o = 0.0;
+    T o = T(0);
     int x = i0 - 4 + r;
     if (line_coords(l, c) && x <= n + 3) {
       c[DIR] = x;
-      o = A.om[A.omBox.at(c[0], c[1], c[2])];
+      o = static_cast<const T*>(A.om)[A.omBox.at(c[0], c[1], c[2])];
     }
-    sO[(DIR == 0) ? l * RO + r : r * LW + l] = T(o);
+    sO[(DIR == 0) ? l * RO + r : r * LW + l] = o;
   }
   __syncthreads();
   // 2. first derivatives along DIR on nodes i0-2 .. i0+TL

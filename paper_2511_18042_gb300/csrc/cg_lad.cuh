@@ -572,7 +572,7 @@ __global__ void k_lad_div(DevGrid g, int l, const T* __restrict__ Fn, Box fb, co
 // (with the sensor) Omega > threshold; counts troubled interior nodes and
 // sets flag[0] = 1 if any (the global decision of Algorithm 3).
 template <int ND, typename TW = double>
-__device__ __forceinline__ void k_troubled_body(const VBlock& vb, const DevGrid& g, const TW* __restrict__ W, double hr, double hp, const double* __restrict__ om,
+__device__ __forceinline__ void k_troubled_body(const VBlock& vb, const DevGrid& g, const TW* __restrict__ W, double hr, double hp, const TW* __restrict__ om,
                            Box ob, double thr, unsigned char* __restrict__ tr, Box tb, int* flag,
                            unsigned long long* count) {
   constexpr int NV = ND + 2, IP = ND + 1;
@@ -583,7 +583,7 @@ __device__ __forceinline__ void k_troubled_body(const VBlock& vb, const DevGrid&
     double w[NV];
     load_state<ND, false, TW, double>(g, W, c[0], c[1], c[2], w);
     bool t = w[0] < hr || w[IP] < hp;
-    if (om && om[ob.at(c[0], c[1], c[2])] > thr) t = true;
+    if (om && double(om[ob.at(c[0], c[1], c[2])]) > thr) t = true;
     if (tr) tr[e] = t ? 1 : 0;
     bool interior = true;
 #pragma unroll
@@ -597,7 +597,7 @@ __device__ __forceinline__ void k_troubled_body(const VBlock& vb, const DevGrid&
 }
 
 template <int ND, typename TW = double>
-__global__ void k_troubled(DevGrid g, const TW* __restrict__ W, double hr, double hp, const double* __restrict__ om,
+__global__ void k_troubled(DevGrid g, const TW* __restrict__ W, double hr, double hp, const TW* __restrict__ om,
                            Box ob, double thr, unsigned char* __restrict__ tr, Box tb, int* flag,
                            unsigned long long* count) {
   k_troubled_body<ND, TW>(hw_block(), g, W, hr, hp, om, ob, thr, tr, tb, flag, count);

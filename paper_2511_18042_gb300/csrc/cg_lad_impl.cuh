@@ -275,7 +275,7 @@ static int lad_stage_t(cg_solver* s, const double* Uc, StageArgs A, cudaStream_t
   // per interface: GBR-MEG6 where a neighbour node is troubled, LAD-E4 (flux form) elsewhere
   stage_prep_gbr<ND>(s, Uc, false, st, false);
   k_troubled<ND, T><<<grid_blocks(L.tbox.size(), 256), 256, 0, st>>>(
-      s->dg, reinterpret_cast<const T*>(s->W), s->p.hyb_rho, s->p.hyb_p, s->p.hybrid_sensor ? s->om : nullptr, s->omBox, s->p.sensor_thresh, L.tr,
+      s->dg, reinterpret_cast<const T*>(s->W), s->p.hyb_rho, s->p.hyb_p, s->p.hybrid_sensor ? reinterpret_cast<const T*>(s->om) : nullptr, s->omBox, s->p.sensor_thresh, L.tr,
       L.tbox, s->hyb_flag, s->hyb_count);
   s->launches++;
   int rc = lad_coeffs_run<ND, T>(s, 2, st, nullptr, 0);

@@ -63,6 +63,21 @@ def test_mixed_rhs_close_to_fp64(orc, api):
         assert np.abs(R[v] - Ro[v]).max() <= 1e-4 * np.abs(Ro[v]).max()
 
 
+def test_mixed_sensor_close_to_fp64(orc, api):
+    """The mixed form keeps the discontinuity sensor of Eq. (8) in FP32. Read back through
+    the diagnostics call it stays within FP32 rounding of the oracle's sensor
+    (values up to ~0.4 here) on a shocked state."""
+    prob = inputs.riemann_c3(48)
+    o = orc.Oracle(prob, scheme="MEG6")
+    U, _, _ = o.advance(prob["U"], nsteps=10)
+    om_o = o.omega(U)
+    assert om_o.max() > 0.2
+    s = api.Solver.from_problem(prob, scheme="MEG6", precision=1)
+    om = s.omega(to_dev(U)).cpu().numpy()
+    d = np.abs(om - om_o)
+    assert d.max() <= 1e-2 and d.mean() <= 1e-4, (d.max(), d.mean())
+
+
 @pytest.mark.parametrize("scheme", ["LAD_C6", "LAD_E4"])
 def test_mixed_lad_sod(orc, api, scheme):
     """LAD in the mixed form on the Sod tube (N = 400, long quiet region ahead of
