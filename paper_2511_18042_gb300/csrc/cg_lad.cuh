@@ -314,7 +314,7 @@ __device__ __forceinline__ void nodeflux_at(const DevGrid& g, int l, const T* __
                                             const T* __restrict__ dv, const Box& b3, const T* __restrict__ vco,
                                             const Box& vbx, const int* c, T* F) {
   constexpr int NV = ND + 2, IP = ND + 1;
-  constexpr bool CONV = MODE != NF_VISC, ART = MODE != NF_VISC, PHYS = MODE != NF_LAD;
+  constexpr bool CONV = MODE != NF_VISC, PHYS = MODE != NF_LAD;
   const long long bs = b3.size();
   {
     T w[NV];
