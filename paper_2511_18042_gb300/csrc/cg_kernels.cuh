@@ -328,67 +328,89 @@ __device__ __forceinline__ void k_gbr_sweep_body(const VBlock& vb, const DevGrid
   };
   (void)lc1;
   (void)lc2;
-  // 1. primitives of the tile (ghosts resolved by the boundary conditions)
-  for (int e = tid; e < RW * LW; e += blockDim.x) {
-    int r = DIR == 0 ? e % RW : e / LW;
-    int l = DIR == 0 ? e / RW : e % LW;
-    int c[3] = {0, 0, 0};
-    T w[NV];
-    if (line_coords(l, c)) {
-      c[DIR] = i0 - 5 + r;
-      if (MIX) load_state<ND, false, float, T>(g, A.Wf, c[0], c[1], c[2], w);
-      else load_state<ND, false, double, T>(g, A.W, c[0], c[1], c[2], w);
-    } else {
-#pragma unroll
-      for (int v = 0; v < NV; ++v) w[v] = T(1);
-    }
-#pragma unroll
-    for (int v = 0; v < NV; ++v) sW[IX(v, r, l, RW)] = w[v];
-  }
-  // sensor window values
-  for (int e = tid; e < RO * LW; e += blockDim.x) {
-    int r = DIR == 0 ? e % RO : e / LW;
-    int l = DIR == 0 ? e / RO : e % LW;
-    int c[3] = {0, 0, 0};
-    T o = T(0);
-    int x = i0 - 4 + r;
-    if (line_coords(l, c) && x <= n + 3) {
-      c[DIR] = x;
-      o = static_cast<const T*>(A.om)[A.omBox.at(c[0], c[1], c[2])];
-    }
-    sO[(DIR == 0) ? l * RO + r : r * LW + l] = o;
-  }
-  __syncthreads();
-  // 2. first derivatives along DIR on nodes i0-2 .. i0+TL
-  for (int e = tid; e < RD * LW; e += blockDim.x) {
-    int r = DIR == 0 ? e % RD : e / LW;
-    int l = DIR == 0 ? e / RD : e % LW;
-    if (!COMPACT) {
-#pragma unroll
-      for (int v = 0; v < NV; ++v)
-        sD[IX(v, r, l, RD)] = d6(sW[IX(v, r, l, RW)], sW[IX(v, r + 1, l, RW)], sW[IX(v, r + 2, l, RW)],
-                                 sW[IX(v, r + 4, l, RW)], sW[IX(v, r + 5, l, RW)], sW[IX(v, r + 6, l, RW)]);
-    } else {
+  // Per-interface hybrid: a tile none of whose interfaces takes the GBR flux
+  // (no troubled node on either side of any of them) skips steps 1-3, whose
+  // staged primitives, derivatives and sensor values only the GBR fluxes read.
+  bool stage_tile = true;
+  if (A.mask) {
+    int any = 0;
+#pragma unroll 1
+    for (int e = tid; e < TL * LW; e += blockDim.x) {
+      int a = DIR == 0 ? e % TL : e / LW;
+      int l = DIR == 0 ? e / TL : e % LW;
+      int i = i0 - 1 + a;
       int c[3] = {0, 0, 0};
-      int x = i0 - 2 + r;
-      bool ok = line_coords(l, c) && x <= n + 5;
+      if (!line_coords(l, c) || i > n - 1) continue;
+      c[DIR] = i;
+      int cn[3] = {c[0], c[1], c[2]};
+      cn[DIR] = i + 1;
+      if (A.mask[A.tBox.at(c[0], c[1], c[2])] != 0 || A.mask[A.tBox.at(cn[0], cn[1], cn[2])] != 0) any = 1;
+    }
+    stage_tile = __syncthreads_or(any) != 0;
+  }
+  if (stage_tile) {
+    // 1. primitives of the tile (ghosts resolved by the boundary conditions)
+    for (int e = tid; e < RW * LW; e += blockDim.x) {
+      int r = DIR == 0 ? e % RW : e / LW;
+      int l = DIR == 0 ? e / RW : e % LW;
+      int c[3] = {0, 0, 0};
+      T w[NV];
+      if (line_coords(l, c)) {
+        c[DIR] = i0 - 5 + r;
+        if (MIX) load_state<ND, false, float, T>(g, A.Wf, c[0], c[1], c[2], w);
+        else load_state<ND, false, double, T>(g, A.W, c[0], c[1], c[2], w);
+      } else {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) w[v] = T(1);
+      }
+#pragma unroll
+      for (int v = 0; v < NV; ++v) sW[IX(v, r, l, RW)] = w[v];
+    }
+    // sensor window values
+    for (int e = tid; e < RO * LW; e += blockDim.x) {
+      int r = DIR == 0 ? e % RO : e / LW;
+      int l = DIR == 0 ? e / RO : e % LW;
+      int c[3] = {0, 0, 0};
+      T o = T(0);
+      int x = i0 - 4 + r;
+      if (line_coords(l, c) && x <= n + 3) {
+        c[DIR] = x;
+        o = static_cast<const T*>(A.om)[A.omBox.at(c[0], c[1], c[2])];
+      }
+      sO[(DIR == 0) ? l * RO + r : r * LW + l] = o;
+    }
+    __syncthreads();
+    // 2. first derivatives along DIR on nodes i0-2 .. i0+TL
+    for (int e = tid; e < RD * LW; e += blockDim.x) {
+      int r = DIR == 0 ? e % RD : e / LW;
+      int l = DIR == 0 ? e / RD : e % LW;
+      if (!COMPACT) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+          sD[IX(v, r, l, RD)] = d6(sW[IX(v, r, l, RW)], sW[IX(v, r + 1, l, RW)], sW[IX(v, r + 2, l, RW)],
+                                   sW[IX(v, r + 4, l, RW)], sW[IX(v, r + 5, l, RW)], sW[IX(v, r + 6, l, RW)]);
+      } else {
+        int c[3] = {0, 0, 0};
+        int x = i0 - 2 + r;
+        bool ok = line_coords(l, c) && x <= n + 5;
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+          sD[IX(v, r, l, RD)] = ok ? (MIX ? T(A.Gdf[A.gdLB.at(v, x, c)]) : T(A.Gd[A.gdLB.at(v, x, c)])) : T(0);
+      }
+    }
+    __syncthreads();
+    // 3. second derivatives on nodes i0-1 .. i0+TL-1
+    for (int e = tid; e < RDD * LW; e += blockDim.x) {
+      int r = DIR == 0 ? e % RDD : e / LW;
+      int l = DIR == 0 ? e / RDD : e % LW;
 #pragma unroll
       for (int v = 0; v < NV; ++v)
-        sD[IX(v, r, l, RD)] = ok ? (MIX ? T(A.Gdf[A.gdLB.at(v, x, c)]) : T(A.Gd[A.gdLB.at(v, x, c)])) : T(0);
+        sDD[IX(v, r, l, RDD)] = d2_from_grad(sW[IX(v, r + 3, l, RW)], sW[IX(v, r + 4, l, RW)],
+                                             sW[IX(v, r + 5, l, RW)], sD[IX(v, r, l, RD)],
+                                             sD[IX(v, r + 2, l, RD)]);
     }
+    __syncthreads();
   }
-  __syncthreads();
-  // 3. second derivatives on nodes i0-1 .. i0+TL-1
-  for (int e = tid; e < RDD * LW; e += blockDim.x) {
-    int r = DIR == 0 ? e % RDD : e / LW;
-    int l = DIR == 0 ? e / RDD : e % LW;
-#pragma unroll
-    for (int v = 0; v < NV; ++v)
-      sDD[IX(v, r, l, RDD)] = d2_from_grad(sW[IX(v, r + 3, l, RW)], sW[IX(v, r + 4, l, RW)],
-                                           sW[IX(v, r + 5, l, RW)], sD[IX(v, r, l, RD)],
-                                           sD[IX(v, r + 2, l, RD)]);
-  }
-  __syncthreads();
   // 4. interface fluxes i+1/2, i = i0-1+a
   constexpr int PER = (TL * LW) / 256;
 #pragma unroll 1
