@@ -138,6 +138,20 @@ def test_hybrid_limits_on_gpu(orc, api):
         runs[name] = U
     assert torch.equal(runs["lad"], runs["never"])
     assert torch.equal(runs["meg"], runs["always"])
+    # per interface, every node troubled: every sweep tile is staged and every
+    # interface takes the GBR flux, as in MEG6
+    s = api.Solver.from_problem(prob, scheme="HYBRID", hybrid_mode=1, hyb_rho=math.inf)
+    U = U0.clone()
+    s.advance(U, nsteps=5)
+    assert torch.equal(U, runs["meg"])
+    # per interface, no node troubled: every tile skips its staging and every
+    # interface takes the LAD-E4 flux-form flux
+    kw = dict(scheme="HYBRID", hybrid_mode=1)
+    o, s = _pair(orc, api, prob, **kw)
+    U = U0.clone()
+    s.advance(U, nsteps=5)
+    Uo, _, _ = o.advance(prob["U"], nsteps=5)
+    assert rel_err(U, Uo) <= 1e-11
 
 
 @pytest.mark.parametrize("scheme,extra", [("LAD_E4", {}), ("HYBRID", dict(hybrid_mode=1, hyb_rho=1.05))])
