@@ -1,6 +1,7 @@
-"""Multi-rank bench aggregation on CPU (gloo, world_size 2): each rank runs its
-own replica; the job's step time is the slowest rank's and the value sums the
-units of all ranks."""
+"""Bench host logic on CPU. Multi-rank aggregation (gloo, world_size 2): each
+rank runs its own replica; the job's step time is the slowest rank's and the
+value sums the units of all ranks. The clock record: samples inside the timed
+region, their median SM clock and the throttle reasons seen there."""
 import os
 import socket
 
@@ -50,3 +51,35 @@ def test_aggregate_single_rank():
     import bench
     ms, value = bench.aggregate_over_ranks(20.0, 500.0)
     assert ms == 20.0 and abs(value - 500.0 / 20e-3) < 1e-9
+
+
+# ---------------------------------------------------------------- clock record
+def _row(sm, mx, hw="Not Active", hwt="Not Active", swt="Not Active", pcap="Not Active"):
+    return ["0", str(sm), str(mx), "900.0", "0x0", hw, hwt, swt, pcap]
+
+
+def test_clock_summary_window_median_and_reasons():
+    """The clock record keeps the samples inside the timed region (0.15 s of
+    slack each side), reports their median SM clock, the maximum clock and
+    every throttle reason seen active there."""
+    import bench
+    c = bench.ClockSampler(0)
+    c.rows = [(9.0, _row(900, 2070, hw="Active")),     # before the region: dropped
+              (10.0, _row(2070, 2070)),
+              (10.1, _row(1980, 2070, pcap="Active")),
+              (10.2, _row(2055, 2070)),
+              (10.45, _row(600, 2070, hwt="Active"))]   # after the region: dropped
+    c.t0, c.t1 = 10.0, 10.25
+    s = c.summary()
+    assert s["samples"] == 3
+    assert s["sm_mhz"] == 2055.0 and s["sm_max_mhz"] == 2070.0
+    assert s["reasons"] == ["sw_power_cap"]
+    c.t1 = 10.35  # the late sample now falls inside the slack
+    assert c.summary()["reasons"] == ["hw_thermal_slowdown", "sw_power_cap"]
+
+
+def test_clock_summary_unsampled():
+    import bench
+    c = bench.ClockSampler(0)
+    c.t0, c.t1 = 1.0, 2.0
+    assert c.summary() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
