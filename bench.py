@@ -46,6 +46,7 @@ MIXED = [
     ("HYBRID_CELL_MIXED", dict(scheme="HYBRID", hybrid_mode=1, hyb_rho=0.5 * 0.125, hybrid_sensor=1, precision=1)),
 ]
 DEVELOP_STEPS = 200
+METRIC = "cell-updates/s per scheme & % HBM roofline; batched solves/s, p50/p99 latency"
 # FP64 roofline of the dominant kernel (the C-GBR interface sweep).  Per-unit
 # figure: FP64 floating-point operations per interface flux of the developed
 # triple-point state (adds, multiplies, FMAs x2 of the divide / square-root
@@ -268,7 +269,7 @@ def run_gpu(args):
                          "hbm_frac_of_measured": cu * HBM_BYTES_PER_CELL_STEP / (peaks["hbm_gbs"] * 1e9),
                          "tile_lines": list(tiles[n])}
     line = {
-        "metric": "cell-updates/s per scheme & % HBM roofline; batched solves/s, p50/p99 latency",
+        "metric": METRIC,
         "value": value, "unit": "cell-updates/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
@@ -600,7 +601,7 @@ def run_reference(args):
     value = cells / sec
     desc = ("FP64 CPU oracle, single thread: one RK3 step of each of %d schemes on a %dx%d triple point "
             "(bounded sample of the 1792x768 workload)" % (len(names), sample[0], sample[1]))
-    line = {"impl": "reference", "metric": "cell-updates/s per scheme & % HBM roofline; batched solves/s, p50/p99 latency",
+    line = {"impl": "reference", "metric": METRIC,
             "value": value, "unit": "cell-updates/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",

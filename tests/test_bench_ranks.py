@@ -1,7 +1,8 @@
 """Bench host logic on CPU. Multi-rank aggregation (gloo, world_size 2): each
 rank runs its own replica; the job's step time is the slowest rank's and the
 value sums the units of all ranks. The clock record: samples inside the timed
-region, their median SM clock and the throttle reasons seen there."""
+region, their median SM clock and the throttle reasons seen there. The
+reference arm's JSON line (the CPU oracle, timed on a short run)."""
 import os
 import socket
 
@@ -83,3 +84,28 @@ def test_clock_summary_unsampled():
     c = bench.ClockSampler(0)
     c.t0, c.t1 = 1.0, 2.0
     assert c.summary() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+
+
+# ---------------------------------------------------------------- reference arm
+def test_reference_arm_json_line():
+    """`--impl reference` times the CPU oracle and prints one JSON line with
+    the GPU arm's metric, unit and workload, a cpu_baseline of the oracle and
+    an e2e record without host-device traffic (a short run of two schemes)."""
+    import json
+    import subprocess
+    import sys
+    import bench
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0",
+                          "--schemes", "MEG6,LAD_E4"], cwd=root, capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == "cell-updates/s"
+    assert d["higher_is_better"] is True and d["n_gpus"] == 1 and d["steps"] == 1
+    assert d["value"] > 0 and abs(d["ms_per_step"] - 448 * 192 * 2 / d["value"] * 1e3) <= 1e-6 * d["ms_per_step"]
+    assert d["config"]["workload"] == bench.bench_config(["MEG6", "LAD_E4"], 1)["workload"]
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == d["value"] and cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
