@@ -102,6 +102,7 @@ def lib():
         _lib.orc_iface_flux.argtypes = [vp, P, ctypes.c_int, P]
         _lib.orc_hllc.argtypes = [ctypes.c_int, ctypes.c_double, P, P, P, P]
         _lib.orc_euler_flux.argtypes = [ctypes.c_int, ctypes.c_double, P, P, P]
+        _lib.orc_char_transform.argtypes = [ctypes.c_int, ctypes.c_double, P, P, P, ctypes.c_int, P, P]
         _lib.orc_mp5.restype = ctypes.c_double
         _lib.orc_mp5.argtypes = [ctypes.c_double] * 7
         _lib.orc_line_op.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -278,6 +279,18 @@ def euler_flux(W, xi, gamma=1.4):
     F = np.empty(nd + 2)
     lib().orc_euler_flux(nd, gamma, _ptr(Wa), _ptr(x), _ptr(F))
     return F
+
+
+def char_transform(W_i, W_i1, xi, w, inverse=False, gamma=1.4):
+    """Characteristic variables L w (or primitive R w with inverse=True) in the
+    frame of the interface between nodes with primitive states W_i, W_i1."""
+    nd = len(xi)
+    a, b = (np.ascontiguousarray(v, dtype=np.float64) for v in (W_i, W_i1))
+    x = np.ascontiguousarray(xi, dtype=np.float64)
+    wi = np.ascontiguousarray(w, dtype=np.float64)
+    out = np.empty(nd + 2)
+    lib().orc_char_transform(nd, gamma, _ptr(a), _ptr(b), _ptr(x), int(bool(inverse)), _ptr(wi), _ptr(out))
+    return out
 
 
 def mp5(um2, um1, u0, up1, up2, alpha=4.0, eps=1e-20):

@@ -30,7 +30,13 @@
  * (sympy); RK3 order; periodic conservation; freestream on curvilinear 2D/3D
  * grids; exact metrics of an affine grid; x<->y symmetry of the 2D Riemann
  * configuration 3; hybrid limits; CFL closed form; hand values of beta*, of
- * kappa* and of the sensor.  Viscous terms (tests/test_oracle_viscous.py): discrete decay
+ * kappa* and of the sensor.  C-GBR details (tests/test_oracle_gbr_pins.py):
+ * the central states of the entropy and shear waves (Eq. 7-8) make their
+ * semi-discrete operator skew-symmetric (energy conserved, the upwind
+ * acoustic states dissipate); the characteristic frame diagonalises the
+ * primitive Jacobian at the arithmetic mean state; a reflective wall is the
+ * mirror plane of the doubled periodic domain; the per-interface hybrid
+ * marks exactly the interfaces beside a troubled node.  Viscous terms (tests/test_oracle_viscous.py): discrete decay
  * rate of periodic and wall-bounded shear waves (E4 and C6 modified
  * wavenumbers) and their energy source; the isothermal no-slip wall as the
  * mirror of the doubled periodic channel; fourth-order convergence of the 3D
@@ -631,6 +637,40 @@ static void from_char(int nd, const charframe *fr, const double *cv, double *w)
     }
 }
 
+/* interface frame (Sec. 2.3): unit normal n = xi/|xi| of the interface
+ * metrics, its tangents, and the sound speed and density of the arithmetic
+ * mean of the primitive states at nodes i and i+1 (reading: mean state) */
+static void char_frame(int nd, double gamma, const double *Wi, const double *Wi1,
+                       const double *xi, charframe *fr)
+{
+    int ip = nd + 1;
+    double g2 = 0.0;
+    for (int m = 0; m < nd; ++m) g2 += xi[m] * xi[m];
+    double ig = 1.0 / sqrt(g2);
+    for (int m = 0; m < nd; ++m) fr->n[m] = xi[m] * ig;
+    tangents(nd, fr->n, fr->t1, fr->t2);
+    fr->rb = 0.5 * (Wi[0] + Wi1[0]);
+    double pb = 0.5 * (Wi[ip] + Wi1[ip]);
+    fr->cb = sqrt(gamma * pb / fr->rb);
+    double ic = 1.0 / fr->cb;
+    fr->ic2 = ic * ic;
+    fr->ha = 0.5 * fr->ic2;
+    fr->hb = 0.5 * fr->rb * ic;
+    fr->cr = fr->cb / fr->rb;
+}
+
+/* The characteristic transform of the interface between nodes with primitive
+ * states Wi and Wi1 (exposed for the pins): inverse = 0 gives cv = L w, the
+ * characteristic variables of primitive w; inverse = 1 gives w = R cv. */
+void orc_char_transform(int nd, double gamma, const double *Wi, const double *Wi1,
+                        const double *xi, int inverse, const double *in, double *out)
+{
+    charframe fr;
+    char_frame(nd, gamma, Wi, Wi1, xi, &fr);
+    if (inverse) from_char(nd, &fr, in, out);
+    else to_char(nd, &fr, in, out);
+}
+
 /* Wst[j] = W_{i-2+j} (j = 0..5), Wd[j] = W'_{i-1+j} (j = 0..3), om = interface sensor */
 static void gbr_flux(const gbr_cfg *q, const double Wst[6][5], const double Wd[4][5],
                      double om, const double *xi, double *F)
@@ -644,21 +684,8 @@ static void gbr_flux(const gbr_cfg *q, const double Wst[6][5], const double Wd[4
         W2[0][v] = 2.0 * (Wst[3][v] - 2.0 * Wst[2][v] + Wst[1][v]) - 0.5 * (Wd[2][v] - Wd[0][v]);
         W2[1][v] = 2.0 * (Wst[4][v] - 2.0 * Wst[3][v] + Wst[2][v]) - 0.5 * (Wd[3][v] - Wd[1][v]);
     }
-    /* interface frame from the interface metrics and the arithmetic mean state */
     charframe fr;
-    double g2 = 0.0;
-    for (int m = 0; m < nd; ++m) g2 += xi[m] * xi[m];
-    double ig = 1.0 / sqrt(g2);
-    for (int m = 0; m < nd; ++m) fr.n[m] = xi[m] * ig;
-    tangents(nd, fr.n, fr.t1, fr.t2);
-    fr.rb = 0.5 * (Wst[2][0] + Wst[3][0]);
-    double pb = 0.5 * (Wst[2][ip] + Wst[3][ip]);
-    fr.cb = sqrt(q->gamma * pb / fr.rb);
-    double ic = 1.0 / fr.cb;
-    fr.ic2 = ic * ic;
-    fr.ha = 0.5 * fr.ic2;
-    fr.hb = 0.5 * fr.rb * ic;
-    fr.cr = fr.cb / fr.rb;
+    char_frame(nd, q->gamma, Wst[2], Wst[3], xi, &fr);
 
     double C[6][5], Cd[2][5], Cdd[2][5];
     for (int j = 0; j < 6; ++j) to_char(nd, &fr, Wst[j], C[j]);

@@ -84,6 +84,11 @@ int orc_iface_flux(void *ctx, const double *U, int d, double *F);
 void orc_hllc(int ndim, double gamma, const double *WL, const double *WR,
               const double *xi, double *F);
 void orc_euler_flux(int ndim, double gamma, const double *W, const double *xi, double *F);
+/* Characteristic transform at the interface between nodes with primitive
+ * states Wi, Wi1 and interface metrics xi (Sec. 2.3): inverse = 0: out = L in
+ * (primitive -> characteristic); inverse = 1: out = R in. */
+void orc_char_transform(int nd, double gamma, const double *Wi, const double *Wi1,
+                        const double *xi, int inverse, const double *in, double *out);
 double orc_mp5(double um2, double um1, double u0, double up1, double up2,
                double alpha, double eps);
 /* Derivative / filter operators on one line of n values with ng ghost values
