@@ -48,16 +48,45 @@ MIXED = [
 DEVELOP_STEPS = 200
 METRIC = "cell-updates/s per scheme & % HBM roofline; batched solves/s, p50/p99 latency"
 # FP64 roofline of the dominant kernel (the C-GBR interface sweep).  Per-unit
-# figure: FP64 floating-point operations per interface flux of the developed
-# triple-point state (adds, multiplies, FMAs x2 of the divide / square-root
-# sequences included), from the ncu instruction counts of one sweep launch.
-SWEEP_FLOP_PER_IFACE = 632.2  # profiles/sweep_meg6_triple_point_1792x768.md (mean of x and y)
+# figure: the algorithmic FP64 operations per interface of one sweep launch
+# (gradients along the sweep, reconstruction with MP5, HLLC, flux difference,
+# residual and RK stage update; add, mul, div and sqrt one each), counted by
+# the flop-counting build of the oracle on the developed triple-point state:
+# profiles/flops_triple_point_1792x768.md (oracle/count_flops.py).
+SWEEP_FLOP_PER_IFACE = 524.8
 # dram read + write per launch (mean of x and y) of the sweep form the roofline times,
 # from its ncu capture (profiles/); None until the current kernel has been captured
 SWEEP_TRAFFIC_BYTES = {"exact": 92.0e6, "contracted": 140.2e6}
 ROOFLINE_FORM = "exact"  # the library default (fma_sweep = 0)
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12  # SMs x DFMA/clk x 2 flop x max clock
+FP64_PEAK_DERIVED_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12  # SMs x DFMA/clk x 2 flop x max clock (context only)
 HBM_BYTES_PER_CELL_STEP = 256.0  # minimal-traffic model, FP64 state, nv = 4, uniform grid
+
+
+def measure_fma_peaks(local):
+    """Measured FP64 and FP32 FMA throughput of this GPU (the FMA-chain probe,
+    libcgprobe.so; one FMA = 2 flop), with the SM clock sampled meanwhile."""
+    import ctypes
+    from paper_2511_18042_gb300 import build
+    L = ctypes.CDLL(build.PROBE)
+    L.cgp_fma_peak.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                               ctypes.POINTER(ctypes.c_int)]
+    out = {}
+    clk = ClockSampler(local).__enter__()
+    time.sleep(0.3)
+    clk.mark(True)
+    try:
+        for name, fp64 in (("fp64", 1), ("fp32", 0)):
+            f, ms, sms = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+            rc = L.cgp_fma_peak(fp64, ctypes.byref(f), ctypes.byref(ms), ctypes.byref(sms))
+            if rc != 0:
+                raise RuntimeError("FMA probe failed (%d)" % rc)
+            out[name + "_tflops"] = f.value / 1e12
+            out["sms"] = sms.value
+    finally:
+        clk.mark(False)
+        clk.__exit__(None, None, None)
+    out["clocks"] = clk.summary()
+    return out
 
 
 def _peaks():
@@ -210,24 +239,25 @@ def run_gpu(args):
             ev = {n: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for n in names}
             one_step(ev)
             torch.cuda.synchronize()
-            tot = 0.0
             for n in names:
-                ms = ev[n][0].elapsed_time(ev[n][1])
-                per[n] += ms
-                tot += ms
-            step_ms.append(tot)
+                per[n] += ev[n][0].elapsed_time(ev[n][1])
+            step_ms.append({n: ev[n][0].elapsed_time(ev[n][1]) for n in names})
         torch.cuda.synchronize()
         wall = time.perf_counter() - wall0
         clk.mark(False)
     finally:
         clk.__exit__(None, None, None)
     launches = sum(s.launch_count() for s in solvers.values()) - launches0
+    # a scheme whose timed steps produced rho <= 0, p <= 0 or NaN is excluded from value
+    status = {}
     for n in names:
         rc = solvers[n].sync_status()
         if rc not in (0, -4):
             raise RuntimeError("solver status %d" % rc)
-    ms_step = sum(step_ms) / len(step_ms)
-    ms_step, value = aggregate_over_ranks(ms_step, cells * len(names), dev if ws > 1 else None)
+        status[n] = "ok" if rc == 0 else "nonphysical"
+    ok = [n for n in names if status[n] == "ok"]
+    ms_step = sum(sum(st[n] for n in ok) for st in step_ms) / len(step_ms)
+    ms_step, value = aggregate_over_ranks(ms_step, cells * len(ok), dev if ws > 1 else None)
 
     # the mixed form (FP32 fluxes, FP64 accumulation) of the schemes that have it
     mixed = {}
@@ -242,8 +272,9 @@ def run_gpu(args):
     batched = run_batched(api, torch, dev, args) if args.batched else None
     serving = run_serving(args) if args.serving else None
 
-    # roofline of the dominant kernel: the MEG6 interface sweep, timed alone
-    roof = sweep_roofline(api, torch, grid, base, dev, args)
+    # roofline of the dominant kernel: the MEG6 interface sweep, timed alone,
+    # against the measured FP64 FMA throughput
+    roof = sweep_roofline(api, torch, grid, base, dev, args, measure_fma_peaks(local))
 
     # end to end through the C ABI with host buffers (pinned), one step per scheme
     host = torch.empty(base.shape, dtype=torch.float64, pin_memory=True)
@@ -252,20 +283,20 @@ def run_gpu(args):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        for n in names:
+        for n in ok:
             host.copy_(host_base)
             solvers[n].advance_host(host, nsteps=1)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     nbytes = base.numel() * 8
-    e2e = {"value": ws * cells * len(names) / e2e_s, "unit": "cell-updates/s",
-           "h2d_bytes_per_step": nbytes * len(names), "d2h_bytes_per_step": nbytes * len(names)}
+    e2e = {"value": ws * cells * len(ok) / e2e_s, "unit": "cell-updates/s",
+           "h2d_bytes_per_step": nbytes * len(ok), "d2h_bytes_per_step": nbytes * len(ok)}
 
     per_scheme = {}
     peaks = _peaks()
     for n in names:
         ms = per[n] / args.steps
         cu = cells / (ms * 1e-3)
-        per_scheme[n] = {"cell_updates_per_s": cu, "ms_per_rk3_step": ms,
+        per_scheme[n] = {"cell_updates_per_s": cu, "ms_per_rk3_step": ms, "status": status[n],
                          "hbm_frac_of_measured": cu * HBM_BYTES_PER_CELL_STEP / (peaks["hbm_gbs"] * 1e9),
                          "tile_lines": list(tiles[n])}
     line = {
@@ -273,7 +304,8 @@ def run_gpu(args):
         "value": value, "unit": "cell-updates/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": bench_config(names, ws),
+        "config": dict(bench_config(names, ws), counted=ok,
+                       excluded_nonphysical=[n for n in names if status[n] != "ok"]),
         "per_scheme": per_scheme, "mixed_precision": mixed, "sod_latency": sod, "compression_ramp": ramp, "batched": batched,
         "serving": serving,
         "roofline": roof, "e2e": e2e, "gpu_launches": launches // max(1, args.steps),
@@ -289,10 +321,11 @@ def run_gpu(args):
 
 def _hybrid_kw(prob, precision):
     """Per-instance troubled-cell thresholds of the quadrant problems: half the
-    smallest initial quadrant density and pressure."""
+    smallest initial quadrant density and pressure; a one-node buffer around
+    troubled nodes."""
     st = prob["quad_states"]
     return dict(scheme="HYBRID", hybrid_mode=1, hybrid_sensor=1, hyb_rho=0.5 * float(st[:, 0].min()),
-                hyb_p=0.5 * float(st[:, 3].min()), precision=precision)
+                hyb_p=0.5 * float(st[:, 3].min()), hybrid_buffer=1, precision=precision)
 
 
 RAMP_SCHEMES = [("LAD_E4", dict(scheme="LAD_E4")), ("MEG6", dict(scheme="MEG6")), ("MIG4", dict(scheme="MIG4")),
@@ -373,10 +406,14 @@ def run_sod_latency(api, torch, dev, steps=200):
     return {"workload": "Sod tube 400 cells, %d RK3 steps from the initial state" % steps, **out}
 
 
-def run_batched(api, torch, dev, args, count=256, steps_per_solve=200):
+def run_batched(api, torch, dev, args, count=256, steps_per_solve=200, ref_steps=20, acc_members=16):
     """Batched 2D Riemann problems (256 uneven grids, 64^2..512^2, seed 0):
     per-interface hybrid in the mixed form, all members advanced by one CUDA
-    graph replay per RK3 step, against the per-case FP64 loop on the same grids."""
+    graph replay per RK3 step: the batch is autotuned, then all 256 solves run
+    their full 200 RK3 steps from the initial states, timed with events.
+    Members whose state went non-physical are reported and not counted as
+    solves.  Beside it: the per-case FP64 loop (each grid stepped alone,
+    host-issued) over ref_steps steps, scaled to 200."""
     from paper_2511_18042_gb300 import inputs
     probs = inputs.batched_riemann(count=count, seed=0)
     cells = sum(p["n"][0] * p["n"][1] for p in probs)
@@ -384,32 +421,43 @@ def run_batched(api, torch, dev, args, count=256, steps_per_solve=200):
     states = [torch.as_tensor(p["U"], device=dev) for p in probs]
     stream = torch.cuda.Stream()
     batch = api.Batch(solvers, states)
-    k = max(2, args.steps)
 
-    def timed_steps():
-        for _ in range(3):  # eager or recapture, first replays
-            batch.step(stream)
-        stream.synchronize()
+    def timed(k):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(k):
             batch.step(stream)
         e1.record(stream)
         stream.synchronize()
-        return e0.elapsed_time(e1) / k
+        return e0.elapsed_time(e1)
 
     with torch.cuda.stream(stream):
-        ms_default = timed_steps()
+        for _ in range(3):  # eager, capture, first replay
+            batch.step(stream)
+        stream.synchronize()
+        ms_default = timed(10) / 10
         t0 = time.perf_counter()
         width = batch.autotune(stream)
         tune_s = time.perf_counter() - t0
-        ms = timed_steps()
+        for _ in range(3):  # recapture after tuning
+            batch.step(stream)
+        stream.synchronize()
+        for s_ in solvers:
+            s_.sync_status(stream)
+        # the full solves: every member from its initial state, 200 RK3 steps
+        for U_, p in zip(states, probs):
+            U_.copy_(torch.as_tensor(p["U"]))
+        stream.synchronize()
+        total_ms = timed(steps_per_solve)
+    status = [s_.sync_status(stream) for s_ in solvers]
+    bad = [i for i, rc in enumerate(status) if rc != 0]
+    good = count - len(bad)
     shapes = {}
     for s_ in solvers:
         key = "x".join(str(v) for v in s_.tile_shape())
         shapes[key] = shapes.get(key, 0) + 1
     path, path_launches = batch.path()
-    bad = sum(1 for s in solvers if s.sync_status() != 0)
+    mixed_final = [states[i].clone() for i in range(acc_members)]
     del batch, solvers, states
     torch.cuda.empty_cache()
     # per-case FP64: each grid advanced on its own, one after the other
@@ -421,52 +469,58 @@ def run_batched(api, torch, dev, args, count=256, steps_per_solve=200):
         s.rk3_step(U, d)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for s, U, d in zip(ref_solvers, ref_states, dts):
-        s.cfl_dt(U, out=d)
-        s.rk3_step(U, d)
+    for _ in range(ref_steps):
+        for s, U, d in zip(ref_solvers, ref_states, dts):
+            s.cfl_dt(U, out=d)
+            s.rk3_step(U, d)
     torch.cuda.synchronize()
-    ref_ms = (time.perf_counter() - t0) * 1e3
+    ref_ms = (time.perf_counter() - t0) * 1e3 / ref_steps
     del ref_solvers, ref_states
     torch.cuda.empty_cache()
-    # accuracy of the batched mixed form against the FP64 form, member by member
-    sub = probs[:16]
-    mix = [api.Solver.from_problem(p, **_hybrid_kw(p, 1)) for p in sub]
-    fp = [api.Solver.from_problem(p, **_hybrid_kw(p, 0)) for p in sub]
-    Um = [torch.as_tensor(p["U"], device=dev) for p in sub]
-    Uf = [torch.as_tensor(p["U"], device=dev) for p in sub]
-    acc_steps = 20
-    with torch.cuda.stream(stream):
-        b2 = api.Batch(mix, Um)
-        for _ in range(acc_steps):
-            b2.step(stream)
-        stream.synchronize()
-    for s_, U_ in zip(fp, Uf):
-        s_.advance(U_, nsteps=acc_steps)
-    torch.cuda.synchronize()
-    l1 = max(float((a[0] - b[0]).abs().mean() / b[0].abs().mean()) for a, b in zip(Um, Uf))
-    del b2, mix, fp, Um, Uf
-    torch.cuda.empty_cache()
+    # accuracy of the batched mixed form after the full 200 steps against the
+    # FP64 form of the same members stepped alone
+    l1 = []
+    for i in range(acc_members):
+        if i in bad:
+            continue
+        s_ = api.Solver.from_problem(probs[i], **_hybrid_kw(probs[i], 0))
+        U_ = torch.as_tensor(probs[i]["U"], device=dev)
+        s_.advance(U_, nsteps=steps_per_solve)
+        a = mixed_final[i][0]
+        l1.append(float((a - U_[0]).abs().mean() / U_[0].abs().mean()))
+    ms = total_ms / steps_per_solve
     return {"workload": "%d quadrant Riemann problems, N in [64, 512] log-uniform (seed 0), %d cells; "
-                        "per-interface hybrid, FP32 fluxes / FP64 accumulation, one graph replay per RK3 step"
-                        % (count, cells),
-            "ms_per_rk3_step": ms, "cell_updates_per_s": cells / (ms * 1e-3),
-            "solves_per_s": count / (steps_per_solve * ms * 1e-3), "steps_per_solve": steps_per_solve,
+                        "per-interface hybrid (one-node buffer), FP32 fluxes / FP64 accumulation, "
+                        "one graph replay per RK3 step, %d steps per solve" % (count, cells, steps_per_solve),
+            "ms_per_rk3_step": ms,
+            "cell_updates_per_s": sum(p["n"][0] * p["n"][1] for i, p in enumerate(probs) if i not in bad) / (ms * 1e-3),
+            "seconds_for_all_solves": total_ms * 1e-3,
+            "solves_per_s": good / (total_ms * 1e-3), "steps_per_solve": steps_per_solve,
+            "members_ok": good, "nonphysical_members": len(bad),
+            "nonphysical": [{"member": i, "n": probs[i]["n"][0],
+                             "why": "C-GBR (MEG6 alone too) drains the four-state junction cell "
+                                    "within 0.45 cell-crossing times at any resolution"
+                             if i == 249 else "unexplained"} for i in bad],
             "autotune": {"path": path, "launches_per_step": path_launches,
                          "streams": width, "tile_shapes": shapes, "seconds": tune_s,
                          "ms_per_rk3_step_default": ms_default,
                          "note": "path: 'table' = one launch per phase of an RK stage for every member "
                                  "(41 per step and member group); 'streams' = per-member launches on "
                                  "the stream pool; default = the work table, untuned"},
-            "nonphysical_members": bad,
-            "accuracy_vs_fp64": {"members": len(sub), "steps": acc_steps, "density_l1_rel_max": l1},
-            "per_case_fp64": {"ms_per_rk3_step": ref_ms, "solves_per_s": count / (steps_per_solve * ref_ms * 1e-3),
-                              "how": "each grid stepped alone in FP64 (wall clock, host-issued launches)"}}
+            "accuracy_vs_fp64": {"members": len(l1), "steps": steps_per_solve,
+                                 "density_l1_rel_max": max(l1) if l1 else None},
+            "per_case_fp64": {"ms_per_rk3_step": ref_ms,
+                              "solves_per_s": count / (steps_per_solve * ref_ms * 1e-3),
+                              "how": "each grid stepped alone in FP64 (wall clock, host-issued launches), "
+                                     "%d steps timed, scaled to %d" % (ref_steps, steps_per_solve)}}
 
 
-def run_serving(args, count=24, rates=(2.0, 8.0, 32.0)):
+def run_serving(args, count=200, rates=(8.0, 16.0, 32.0, 64.0)):
     """Serving stream (Poisson arrivals of the seeded 60/40 tube/quadrant mix,
-    50..500 RK3 steps each, 100 GB admission budget): p50/p99 latency and
-    solves/s per arrival rate."""
+    50..500 RK3 steps each, 100 GB admission budget): p50/p99 latency,
+    solves/s and GPU busy fraction per arrival rate; the saturation rate is
+    the first one whose median latency exceeds twice the lowest rate's (the
+    queue, not the solves, sets the latency from there on)."""
     from paper_2511_18042_gb300 import serve
     out = []
     for lam in rates:
@@ -474,8 +528,10 @@ def run_serving(args, count=24, rates=(2.0, 8.0, 32.0)):
         stats, _ = serve.run(reqs, budget_bytes=100 << 30)
         stats["lambda_per_s"] = lam
         out.append(stats)
-    return {"scheme": "per-interface hybrid, FP32 fluxes / FP64 accumulation", "requests_per_rate": count,
-            "rates": out}
+    sat = next((o["lambda_per_s"] for o in out if o["p50_latency_s"] > 2.0 * out[0]["p50_latency_s"]), None)
+    return {"scheme": "per-interface hybrid (one-node buffer), FP32 fluxes / FP64 accumulation",
+            "requests_per_rate": count, "rates": out, "saturation_lambda_per_s": sat,
+            "saturated_solves_per_s": max(o["solves_per_s"] for o in out)}
 
 
 def time_mixed(api, torch, grid, base, dev, kw, args):
@@ -531,23 +587,30 @@ def _sweep_ms(api, torch, grid, base, dev, args, form):
     return ms / n, n, tile
 
 
-def sweep_roofline(api, torch, grid, base, dev, args):
+def sweep_roofline(api, torch, grid, base, dev, args, peaks):
     """FP64 roofline of the dominant kernel, the MEG6 interface sweep, in the
-    library's default (exact) form; the opt-in FMA form beside it."""
+    library's default (exact) form: algorithmic flop per interface (oracle
+    count) x interfaces per launch / measured launch time, against the
+    measured FP64 FMA peak; the opt-in FMA form beside it."""
     ifaces = ((NX + 1) * NY + NX * (NY + 1)) / 2.0  # algorithmic interfaces per sweep launch (x, y average)
+    peak = peaks["fp64_tflops"]
     avg_ms, n, tile = _sweep_ms(api, torch, grid, base, dev, args, ROOFLINE_FORM)
-    roof = {"bound": "alu", "unit": "TFLOP/s", "peak": FP64_PEAK_TFLOPS,
-            "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (FP64 is not in MEASURED_PEAKS.json)",
+    roof = {"bound": "alu", "unit": "TFLOP/s", "peak": peak,
+            "peak_source": "measured: FP64 FMA-chain probe on this GPU (%d SMs, SM clock median %s MHz); "
+                           "derived 2 DFMA/clk/SM x 2.07 GHz = %.3f" % (peaks["sms"], peaks["clocks"].get("sm_mhz"),
+                                                                       FP64_PEAK_DERIVED_TFLOPS),
             "kernel": "k_gbr_sweep (MEG6), x and y launches of RK3 steps of the bench state",
             "launch_ms": avg_ms, "launches": n, "ifaces_per_launch": ifaces,
             "traffic": SWEEP_TRAFFIC_BYTES[ROOFLINE_FORM], "form": ROOFLINE_FORM,
             "tile_lines": list(tile)}
     ach = SWEEP_FLOP_PER_IFACE * ifaces / (avg_ms * 1e-3) / 1e12
-    roof.update({"achieved": ach, "frac": ach / FP64_PEAK_TFLOPS, "flop_per_iface": SWEEP_FLOP_PER_IFACE})
+    roof.update({"achieved": ach, "frac": ach / peak, "algorithmic_flop_per_iface": SWEEP_FLOP_PER_IFACE,
+                 "flop_source": "oracle operation count (profiles/flops_triple_point_1792x768.md)",
+                 "peak_measured": {k: v for k, v in peaks.items() if k != "clocks"}})
     fms, fn, ftile = _sweep_ms(api, torch, grid, base, dev, args, "contracted")
     fach = SWEEP_FLOP_PER_IFACE * ifaces / (fms * 1e-3) / 1e12
     roof["fma_sweep"] = {"launch_ms": fms, "launches": fn, "tile_lines": list(ftile), "achieved": fach,
-                         "frac": fach / FP64_PEAK_TFLOPS, "traffic": SWEEP_TRAFFIC_BYTES["contracted"],
+                         "frac": fach / peak, "traffic": SWEEP_TRAFFIC_BYTES["contracted"],
                          "note": "opt-in FMA form (fma_sweep = 1): not bitwise; see profiles"}
     return roof
 
@@ -624,7 +687,7 @@ def main():
     ap.add_argument("--no-serving", dest="serving", action="store_false")
     ap.add_argument("--no-sod", dest="sod", action="store_false")
     ap.add_argument("--no-ramp", dest="ramp", action="store_false")
-    ap.add_argument("--ramp-steps", type=int, default=3)
+    ap.add_argument("--ramp-steps", type=int, default=20)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -97,12 +97,18 @@ typedef struct {
      * the per-interface hybrid then differs by ~1e-11 after one step.  Other
      * kernels are always exact. */
     int fma_sweep;
+    /* Per-interface hybrid: a troubled node also marks every node within
+     * hybrid_buffer nodes of it in each direction (0..2; 0, the default, marks
+     * the node alone).  A buffer of 1 keeps the C-GBR flux on the LAD-E4 side
+     * of a troubled region, where LAD-E4 alone (no artificial shear viscosity)
+     * lets an expanding vortex sheet drain the density to zero. */
+    int hybrid_buffer;
 } cg_params;
 
 /* Fills the defaults: gamma 1.4, minf 1, MEG6, FP64, CFL 0.2, C_beta 1.75,
  * C_kappa 0.01, alpha_f 0.45, Omega threshold 0.01, MP eps 1e-20, alpha 4,
  * window 4, filter on, no hybrid thresholds, inviscid (re 1, pr 0.72,
- * suth 0, twall 1), exact FP64 sweep (fma_sweep 0). */
+ * suth 0, twall 1), exact FP64 sweep (fma_sweep 0), no hybrid buffer. */
 CG_API void cg_params_default(cg_params *p);
 
 /* Uniform Cartesian grid, node spacing h[d] (Sec. 2.1 with x = xi h).
@@ -183,6 +189,12 @@ CG_API int64_t cg_last_bad_index(const cg_solver *s);
 CG_API const char *cg_last_error(void);
 /* Number of kernel launches this handle has enqueued since creation. */
 CG_API int64_t cg_launch_count(const cg_solver *s);
+/* Bytes of device memory the solver holds: its scratch allocated by
+ * cg_solver_create plus buffers allocated later on first use (inflow
+ * profiles, the host-staging state of cg_advance_host, the scratch of
+ * cg_iface_flux); the caller's state arrays are not included.  -1 for NULL.
+ * Memory-budget admission (the serving loop) counts with it. */
+CG_API int64_t cg_solver_device_bytes(const cg_solver *s);
 
 /* Many independent grids (batched and served workloads).  cg_multi_step
  * advances each solvers[i] by one RK3 step of its own CFL time step on
@@ -247,7 +259,10 @@ CG_API int cg_set_tile_shape(cg_solver *s, const int lines_per_tile[3]);
  * MEG6 solver on the same grid and parameters.  The paper has no counterpart;
  * this is a deployment convenience.
  *  - Arguments: the grid as for cg_grid_create_cartesian, p->scheme must be
- *    CG_MEG6 and p->precision CG_FP64, U and R as for cg_rhs.
+ *    CG_MEG6, p->precision CG_FP64 and p->viscous 0 (inviscid only: the
+ *    viscous pass needs the solver's scratch); otherwise CG_ERR_UNSUPPORTED.
+ *    Every other parameter is checked as by cg_solver_create
+ *    (CG_ERR_INVALID_ARG).  U and R as for cg_rhs.
  *  - Limit: at most 65,536 cells and 2*nv*N + prod(n_d + 8) <= 2^20 scratch
  *    doubles; larger grids return CG_ERR_INVALID_ARG with the sizes.
  *  - Scratch: a fixed 8 MiB array in device memory, held by every GPU that

@@ -34,7 +34,7 @@ def build(force=False):
         return _SO
     os.makedirs(os.path.dirname(_SO), exist_ok=True)
     tmp = _SO + ".tmp%d" % os.getpid()
-    cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+    cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared",
            "-o", tmp, _SRC, "-lm"]
     subprocess.check_call(cmd)
     os.replace(tmp, _SO)
@@ -74,6 +74,7 @@ class OrcParams(ctypes.Structure):
         ("pr", ctypes.c_double),
         ("suth", ctypes.c_double),
         ("twall", ctypes.c_double),
+        ("hybrid_buffer", ctypes.c_int),
     ]
 
 
@@ -109,6 +110,8 @@ def lib():
                                      ctypes.c_double, P, P]
         _lib.orc_tridiag.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int, P, P]
         _lib.orc_set_inflow_profile.argtypes = [vp, ctypes.c_int, ctypes.c_int, P]
+        _lib.orc_set_threads.restype = ctypes.c_int
+        _lib.orc_set_threads.argtypes = [ctypes.c_int]
     return _lib
 
 
@@ -122,7 +125,7 @@ DEFAULTS = dict(gamma=1.4, minf=1.0, scheme="MEG6", hybrid_mode=HYB_GLOBAL, hybr
                 alpha_f=0.45, sensor_thresh=0.01, mp_eps=1e-20, mp_alpha=4.0,
                 read_mp_printed=0, read_acoustic_mp5=0, omega_window=4,
                 positivity_fallback=1, filter_on=1, viscous=0, re=1.0, pr=0.72, suth=0.0,
-                twall=1.0)
+                twall=1.0, hybrid_buffer=0)
 
 
 def make_params(problem, **over):
@@ -151,7 +154,7 @@ def make_params(problem, **over):
     s = d["scheme"]
     p.scheme = SCHEMES[s] if isinstance(s, str) else int(s)
     for k in ("hybrid_mode", "hybrid_sensor", "read_mp_printed", "read_acoustic_mp5",
-              "omega_window", "positivity_fallback", "filter_on", "viscous"):
+              "omega_window", "positivity_fallback", "filter_on", "viscous", "hybrid_buffer"):
         setattr(p, k, int(d[k]))
     for k in ("hyb_rho", "hyb_p", "cfl", "c_beta", "c_kappa", "alpha_f", "sensor_thresh",
               "mp_eps", "mp_alpha", "re", "pr", "suth", "twall"):
@@ -260,6 +263,12 @@ class Oracle:
             t += dt
             k += 1
         return U, t, k
+
+
+def set_threads(n=0):
+    """Threads of the oracle's grid loops (0: unchanged); returns the count in
+    use.  Results are the same for any count."""
+    return int(lib().orc_set_threads(int(n)))
 
 
 def hllc(W_L, W_R, xi, gamma=1.4):

@@ -36,7 +36,8 @@
  * acoustic states dissipate); the characteristic frame diagonalises the
  * primitive Jacobian at the arithmetic mean state; a reflective wall is the
  * mirror plane of the doubled periodic domain; the per-interface hybrid
- * marks exactly the interfaces beside a troubled node.  Viscous terms (tests/test_oracle_viscous.py): discrete decay
+ * marks exactly the interfaces beside a troubled node (and, with a buffer
+ * of B nodes, those beside a node within B of one).  Viscous terms (tests/test_oracle_viscous.py): discrete decay
  * rate of periodic and wall-bounded shear waves (E4 and C6 modified
  * wavenumbers) and their energy source; the isothermal no-slip wall as the
  * mirror of the doubled periodic channel; fourth-order convergence of the 3D
@@ -47,7 +48,16 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include "cg_oracle.h"
+
+/* Marks the step of the method a function performs, for the flop-counting
+ * build of this file (oracle/flopcount.cpp); nothing in this build. */
+#ifndef ORC_REGION
+#define ORC_REGION(name)
+#endif
 
 #define GH 8   /* ghost layers of the padded state */
 #define GC 14  /* ghost layers of the extended coordinate box */
@@ -100,6 +110,18 @@ static box_t box_grow(const ctx_t *c, int grow)
     for (int k = (b).lo[2]; k < (b).hi[2]; ++k)      \
         for (int j = (b).lo[1]; j < (b).hi[1]; ++j)  \
             for (int i = (b).lo[0]; i < (b).hi[0]; ++i)
+
+/* The same loop shared among OpenMP threads, for bodies that write only
+ * their own node (or line) and read nothing another iteration writes: every
+ * value is computed by the same arithmetic whatever the thread count, and no
+ * floating-point sum runs across iterations, so results do not depend on it. */
+#ifdef _OPENMP
+#define FOR_BOX_PAR(b, i, j, k)                      \
+    _Pragma("omp parallel for collapse(3) schedule(static)") \
+    FOR_BOX(b, i, j, k)
+#else
+#define FOR_BOX_PAR(b, i, j, k) FOR_BOX(b, i, j, k)
+#endif
 
 static double *padded(const ctx_t *c, int nc)
 {
@@ -177,6 +199,7 @@ static long profile_index(const ctx_t *c, int d, const int *a)
 
 static void fill_ghosts(const ctx_t *c, double *f, int nc, int mode)
 {
+    ORC_REGION(ghost);
     int nd = c->nd;
     for (int d = 0; d < nd; ++d) {
         box_t b;
@@ -204,7 +227,7 @@ static void fill_ghosts(const ctx_t *c, double *f, int nc, int mode)
                 else if (bc == ORC_BC_WALL) { src = side == 0 ? q - 1 : n - q; wall = (mode != 2); }
                 else if (bc == ORC_BC_INFLOW && mode != 2) { src = 0; isfixed = 1; }
                 else src = side == 0 ? 0 : n - 1;
-                FOR_BOX(b, i, j, k) {
+                FOR_BOX_PAR(b, i, j, k) {
                     int a[3] = {i, j, k}, s[3] = {i, j, k};
                     a[d] = gi; s[d] = src;
                     long qa = pidx(c, a[0], a[1], a[2]), qs = pidx(c, s[0], s[1], s[2]);
@@ -241,9 +264,10 @@ static void fill_ghosts(const ctx_t *c, double *f, int nc, int mode)
 /* primitives on the padded box from the interior conserved state */
 static double *padded_prims(const ctx_t *c, const double *U)
 {
+    ORC_REGION(prim);
     double *Wp = padded(c, c->nv);
     box_t b = box_grow(c, 0);
-    FOR_BOX(b, i, j, k) {
+    FOR_BOX_PAR(b, i, j, k) {
         double Q[5], W[5];
         long qi = iidx(c, i, j, k), qp = pidx(c, i, j, k);
         for (int v = 0; v < c->nv; ++v) Q[v] = U[v * c->N + qi];
@@ -429,12 +453,13 @@ int orc_line_op(int kind, int n, int ng, int periodic, double alpha_f,
 /* ------------------------------------------------------------------ */
 static void grad_field(const ctx_t *c, const double *f, int nc, int d, int kind, double *out)
 {
+    ORC_REGION(grad);
     int n = c->n[d], g = c->g[d];
     int periodic = c->p.bc[d][0] == ORC_BC_PERIODIC;
     long s = pstride(c, d);
     box_t b = box_grow(c, GH);
     b.lo[d] = 0; b.hi[d] = 1;
-    FOR_BOX(b, i, j, k) {
+    FOR_BOX_PAR(b, i, j, k) {
         long q0 = pidx(c, i, j, k);
         for (int v = 0; v < nc; ++v) {
             const double *fl = f + v * c->NP + q0;
@@ -455,6 +480,7 @@ static void grad_field(const ctx_t *c, const double *f, int nc, int d, int kind,
 /* ------------------------------------------------------------------ */
 void orc_euler_flux(int nd, double gamma, const double *W, const double *xi, double *F)
 {
+    ORC_REGION(node_flux);
     int ip = nd + 1;
     double rho = W[0], p = W[ip], U = 0.0, q = 0.0;
     for (int m = 0; m < nd; ++m) {
@@ -474,6 +500,7 @@ void orc_euler_flux(int nd, double gamma, const double *W, const double *xi, dou
 void orc_hllc(int nd, double gamma, const double *WL, const double *WR,
               const double *xi, double *F)
 {
+    ORC_REGION(hllc);
     int ip = nd + 1;
     double g2 = 0.0;
     for (int m = 0; m < nd; ++m) g2 += xi[m] * xi[m];
@@ -545,6 +572,7 @@ static double minmod4(double a, double b, double c, double d)
 }
 double orc_mp5(double um2, double um1, double u0, double up1, double up2, double alpha, double eps)
 {
+    ORC_REGION(mp5);
     /* fifth-order upwind-biased interpolation */
     double ul = (2.0 * um2 - 13.0 * um1 + 47.0 * u0 + 27.0 * up1 - 3.0 * up2) / 60.0;
     double ump = u0 + minmod2(up1 - u0, alpha * (u0 - um1));
@@ -675,6 +703,7 @@ void orc_char_transform(int nd, double gamma, const double *Wi, const double *Wi
 static void gbr_flux(const gbr_cfg *q, const double Wst[6][5], const double Wd[4][5],
                      double om, const double *xi, double *F)
 {
+    ORC_REGION(reconstruct);
     int nd = q->nd, nv = q->nv, ip = nv - 1;
     const double c12 = 1.0 / 12.0;
     /* second derivatives from values and first derivatives (Chamarthi):
@@ -741,9 +770,10 @@ static void gbr_flux(const gbr_cfg *q, const double Wst[6][5], const double Wd[4
 /* ------------------------------------------------------------------ */
 static void omega_field(const ctx_t *c, const double *Wp, double *const Wd[3], double *om)
 {
+    ORC_REGION(sensor);
     int nd = c->nd, ip = nd + 1;
     box_t b = box_grow(c, 4);
-    FOR_BOX(b, i, j, k) {
+    FOR_BOX_PAR(b, i, j, k) {
         long q = pidx(c, i, j, k);
         const double *p = Wp + ip * c->NP;
         double phi = 0.0;
@@ -797,7 +827,7 @@ static void gbr_dir_fluxes(const ctx_t *c, const double *Wp, double *const Wd[3]
     gbr_cfg cfg = make_gbr_cfg(c);
     box_t b = box_grow(c, 0);
     b.lo[d] = 0; b.hi[d] = 1;
-    FOR_BOX(b, i0, j0, k0) {
+    FOR_BOX_PAR(b, i0, j0, k0) {
         long q0 = pidx(c, i0, j0, k0);
         for (int i = -1; i <= n - 1; ++i) {
             long q = q0 + i * s;
@@ -843,6 +873,7 @@ static double mu_hat(const ctx_t *c, double T)
 
 static void lad_fluxes(const ctx_t *c, const double *Wp, int dkind, int mode, lad_out *out)
 {
+    ORC_REGION(lad_fluxes);
     int nd = c->nd, nv = c->nv, ip = nd + 1;
     double gamma = c->p.gamma;
     double gm2 = gamma * c->p.minf * c->p.minf;
@@ -851,7 +882,7 @@ static void lad_fluxes(const ctx_t *c, const double *Wp, int dkind, int mode, la
     double *fs = padded(c, nf);
     double *cs = padded(c, 1);
     box_t all = box_grow(c, GH);
-    FOR_BOX(all, i, j, k) {
+    FOR_BOX_PAR(all, i, j, k) {
         long q = pidx(c, i, j, k);
         double rho = Wp[q], p = Wp[ip * c->NP + q];
         for (int kk = 0; kk < nd; ++kk) fs[kk * c->NP + q] = Wp[(1 + kk) * c->NP + q];
@@ -870,7 +901,7 @@ static void lad_fluxes(const ctx_t *c, const double *Wp, int dkind, int mode, la
     double *gr = padded(c, nf * nd);     /* gr[(f*nd + m)] = d f / d x_m */
     double *dv = padded(c, 1);
     box_t b3 = box_grow(c, 3);
-    FOR_BOX(b3, i, j, k) {
+    FOR_BOX_PAR(b3, i, j, k) {
         long q = pidx(c, i, j, k);
         for (int f = 0; f < nf; ++f)
             for (int m = 0; m < nd; ++m) {
@@ -890,7 +921,7 @@ static void lad_fluxes(const ctx_t *c, const double *Wp, int dkind, int mode, la
     box_t b0 = box_grow(c, 0);
     double *tmp = padded(c, 1);
     if (mode != LADF_VISC) {
-    FOR_BOX(b0, i, j, k) {
+    FOR_BOX_PAR(b0, i, j, k) {
         long q = pidx(c, i, j, k);
         double rho = Wp[q];
         double T = fs[nd * c->NP + q];
@@ -941,11 +972,11 @@ static void lad_fluxes(const ctx_t *c, const double *Wp, int dkind, int mode, la
         for (int l = 0; l < nd; ++l) {
             fill_ghosts(c, fld[w], 1, 2);
             long s = pstride(c, l);
-            FOR_BOX(b0, i, j, k) {
+            FOR_BOX_PAR(b0, i, j, k) {
                 long q = pidx(c, i, j, k);
                 tmp[q] = op_gauss(fld[w] + q, s);
             }
-            FOR_BOX(b0, i, j, k) {
+            FOR_BOX_PAR(b0, i, j, k) {
                 long q = pidx(c, i, j, k);
                 fld[w][q] = tmp[q];
             }
@@ -966,7 +997,7 @@ static void lad_fluxes(const ctx_t *c, const double *Wp, int dkind, int mode, la
         out->Fn[l] = padded(c, nv);
         box_t bl = box_grow(c, 0);
         bl.lo[l] = -2; bl.hi[l] = c->n[l] + 2;
-        FOR_BOX(bl, i, j, k) {
+        FOR_BOX_PAR(bl, i, j, k) {
             long q = pidx(c, i, j, k);
             double W[5], xi[3], Fc[5];
             for (int v = 0; v < nv; ++v) W[v] = Wp[v * c->NP + q];
@@ -977,8 +1008,8 @@ static void lad_fluxes(const ctx_t *c, const double *Wp, int dkind, int mode, la
                 double T = fs[nd * c->NP + q];
                 double mu = mu_hat(c, T);
                 double kth = mu / kc;
-                double lam = (art ? bt[q] : 0.0) - (2.0 / 3.0) * mu;
-                double kap = (art ? kp[q] : 0.0) + kth;
+                double lam = (art ? bt[q] : (double)0.0) - (2.0 / 3.0) * mu;
+                double kap = (art ? kp[q] : (double)0.0) + kth;
                 double tau[3][3];
                 for (int m = 0; m < nd; ++m)
                     for (int a = 0; a < nd; ++a) {
@@ -1023,6 +1054,7 @@ static void lad_fluxes(const ctx_t *c, const double *Wp, int dkind, int mode, la
  * with E4 closure rows; periodic: cyclic) */
 static void lad_divergence(const ctx_t *c, double *const Fn[3], int dkind, double *acc)
 {
+    ORC_REGION(lad_div);
     int nd = c->nd, nv = c->nv;
     double *tmp = padded(c, nv);
     for (int l = 0; l < nd; ++l) {
@@ -1031,7 +1063,7 @@ static void lad_divergence(const ctx_t *c, double *const Fn[3], int dkind, doubl
         long s = pstride(c, l);
         box_t b = box_grow(c, 0);
         b.lo[l] = 0; b.hi[l] = 1;
-        FOR_BOX(b, i0, j0, k0) {
+        FOR_BOX_PAR(b, i0, j0, k0) {
             long q0 = pidx(c, i0, j0, k0);
             for (int v = 0; v < nv; ++v) {
                 const double *f = Fn[l] + v * c->NP + q0;
@@ -1041,7 +1073,7 @@ static void lad_divergence(const ctx_t *c, double *const Fn[3], int dkind, doubl
             }
         }
         box_t b0 = box_grow(c, 0);
-        FOR_BOX(b0, i, j, k) {
+        FOR_BOX_PAR(b0, i, j, k) {
             long q = pidx(c, i, j, k), qi = iidx(c, i, j, k);
             for (int v = 0; v < nv; ++v) acc[v * c->N + qi] += tmp[v * c->NP + q];
         }
@@ -1062,9 +1094,10 @@ static void free_lad(lad_out *o, int nd)
 /* acc += F_{i+1/2} - F_{i-1/2} along d */
 static void add_iface_diff(const ctx_t *c, const double *Fi, int d, double *acc)
 {
+    ORC_REGION(flux_diff);
     long s = pstride(c, d);
     box_t b0 = box_grow(c, 0);
-    FOR_BOX(b0, i, j, k) {
+    FOR_BOX_PAR(b0, i, j, k) {
         long q = pidx(c, i, j, k), qi = iidx(c, i, j, k);
         for (int v = 0; v < c->nv; ++v)
             acc[v * c->N + qi] += Fi[v * c->NP + q] - Fi[v * c->NP + q - s];
@@ -1102,6 +1135,7 @@ static void viscous_pass(const ctx_t *c, const double *Wp, double *acc)
 /* scheme: the effective scheme of this stage; acc must be zeroed */
 static void rhs_acc(const ctx_t *c, const double *Wp, int scheme, double *acc, double *iface_out, int iface_dir)
 {
+    ORC_REGION(hybrid_mix);
     int nd = c->nd, nv = c->nv;
     if (c->p.viscous && scheme != ORC_LAD_E4 && scheme != ORC_LAD_C6) viscous_pass(c, Wp, acc);
     if (scheme == ORC_MEG6 || scheme == ORC_MIG4) {
@@ -1133,14 +1167,28 @@ static void rhs_acc(const ctx_t *c, const double *Wp, int scheme, double *acc, d
         }
         double *om = padded(c, 1);
         omega_field(c, Wp, Wd, om);
+        /* troubled nodes on [-1-B, n+B], then the buffer: a node is marked
+         * if any node within B of it (in every direction) is troubled */
+        int B = c->p.hybrid_buffer;
+        unsigned char *t0 = (unsigned char *)calloc(c->NP, 1);
         unsigned char *tr = (unsigned char *)calloc(c->NP, 1);
-        box_t b1 = box_grow(c, 1);
-        FOR_BOX(b1, i, j, k) {
+        box_t bb = box_grow(c, 1 + B);
+        FOR_BOX_PAR(bb, i, j, k) {
             long q = pidx(c, i, j, k);
             int t = is_troubled(c, Wp[q], Wp[(nd + 1) * c->NP + q]);
             if (c->p.hybrid_sensor && om[q] > c->p.sensor_thresh) t = 1;
-            tr[q] = (unsigned char)t;
+            t0[q] = (unsigned char)t;
         }
+        box_t b1 = box_grow(c, 1);
+        FOR_BOX_PAR(b1, i, j, k) {
+            int t = 0;
+            for (int dk = nd > 2 ? -B : 0; dk <= (nd > 2 ? B : 0); ++dk)
+                for (int dj = nd > 1 ? -B : 0; dj <= (nd > 1 ? B : 0); ++dj)
+                    for (int di = -B; di <= B; ++di)
+                        t |= t0[pidx(c, i + di, j + dj, k + dk)];
+            tr[pidx(c, i, j, k)] = (unsigned char)t;
+        }
+        free(t0);
         lad_out lo;
         lad_fluxes(c, Wp, 2, LADF_NOPHYS, &lo);
         double *Fi = padded(c, nv);
@@ -1149,12 +1197,12 @@ static void rhs_acc(const ctx_t *c, const double *Wp, int scheme, double *acc, d
             long s = pstride(c, d);
             box_t b = box_grow(c, 0);
             b.lo[d] = -1;
-            FOR_BOX(b, i, j, k) {
+            FOR_BOX_PAR(b, i, j, k) {
                 long q = pidx(c, i, j, k);
                 mask[q] = (unsigned char)(tr[q] || tr[q + s]);
             }
             gbr_dir_fluxes(c, Wp, Wd, om, d, mask, Fi);
-            FOR_BOX(b, i, j, k) {
+            FOR_BOX_PAR(b, i, j, k) {
                 long q = pidx(c, i, j, k);
                 if (mask[q]) continue;
                 for (int v = 0; v < nv; ++v) {
@@ -1183,12 +1231,13 @@ static int stage_scheme(const ctx_t *c, const double *Wp)
 
 static void rhs_internal(const ctx_t *c, const double *U, double *R)
 {
+    ORC_REGION(residual);
     int nv = c->nv;
     double *Wp = padded_prims(c, U);
     double *acc = (double *)calloc((size_t)c->N * nv, sizeof(double));
     rhs_acc(c, Wp, stage_scheme(c, Wp), acc, NULL, 0);
     box_t b0 = box_grow(c, 0);
-    FOR_BOX(b0, i, j, k) {
+    FOR_BOX_PAR(b0, i, j, k) {
         long q = pidx(c, i, j, k), qi = iidx(c, i, j, k);
         for (int v = 0; v < nv; ++v) R[v * c->N + qi] = -(c->jac[q] * acc[v * c->N + qi]);
     }
@@ -1235,10 +1284,11 @@ int orc_iface_flux(void *ctx, const double *U, int d, double *F)
 /* ------------------------------------------------------------------ */
 static void filter_state(const ctx_t *c, double *U)
 {
+    ORC_REGION(filter);
     int nd = c->nd, nv = c->nv;
     double *Qp = padded(c, nv);
     box_t b0 = box_grow(c, 0);
-    FOR_BOX(b0, i, j, k) {
+    FOR_BOX_PAR(b0, i, j, k) {
         long q = pidx(c, i, j, k), qi = iidx(c, i, j, k);
         for (int v = 0; v < nv; ++v) Qp[v * c->NP + q] = U[v * c->N + qi];
     }
@@ -1250,17 +1300,17 @@ static void filter_state(const ctx_t *c, double *U)
         long s = pstride(c, d);
         box_t b = box_grow(c, 0);
         b.lo[d] = 0; b.hi[d] = 1;
-        FOR_BOX(b, i0, j0, k0) {
+        FOR_BOX_PAR(b, i0, j0, k0) {
             long q0 = pidx(c, i0, j0, k0);
             for (int v = 0; v < nv; ++v)
                 filter_line(n, periodic, c->p.alpha_f, Qp + v * c->NP + q0, s, out + v * c->NP + q0);
         }
-        FOR_BOX(b0, i, j, k) {
+        FOR_BOX_PAR(b0, i, j, k) {
             long q = pidx(c, i, j, k);
             for (int v = 0; v < nv; ++v) Qp[v * c->NP + q] = out[v * c->NP + q];
         }
     }
-    FOR_BOX(b0, i, j, k) {
+    FOR_BOX_PAR(b0, i, j, k) {
         long q = pidx(c, i, j, k), qi = iidx(c, i, j, k);
         for (int v = 0; v < nv; ++v) U[v * c->N + qi] = Qp[v * c->NP + q];
     }
@@ -1278,6 +1328,7 @@ int orc_filter(void *ctx, double *U)
 /* ------------------------------------------------------------------ */
 int orc_rk3_step(void *ctx, double *U, double dt)
 {
+    ORC_REGION(rk3);
     const ctx_t *c = (const ctx_t *)ctx;
     long M = c->N * c->nv;
     double *Un = (double *)malloc(sizeof(double) * M), *R = (double *)malloc(sizeof(double) * M);
@@ -1299,6 +1350,7 @@ int orc_rk3_step(void *ctx, double *U, double dt)
 /* ------------------------------------------------------------------ */
 double orc_cfl_dt(void *ctx, const double *U)
 {
+    ORC_REGION(cfl);
     const ctx_t *c = (const ctx_t *)ctx;
     int nd = c->nd, nv = c->nv;
     double mx = 0.0;
@@ -1438,6 +1490,7 @@ static double *eop(const ebox_t *e, const double *f, int d, int op, int six)
 
 static void metrics_curvilinear(ctx_t *c, const double *xyz)
 {
+    ORC_REGION(metrics);
     int nd = c->nd;
     int six = (c->p.scheme == ORC_MEG6 || c->p.scheme == ORC_MIG4);
     ebox_t e;
@@ -1585,9 +1638,9 @@ void *orc_create(const orc_params *p, const double *xyz)
         for (long q = 0; q < c->NP; ++q) {
             for (int l = 0; l < c->nd; ++l)
                 for (int m = 0; m < c->nd; ++m) {
-                    c->xh[l][m][q] = l == m ? diag[l] : 0.0;
-                    c->xt[l][m][q] = l == m ? diag[l] : 0.0;
-                    c->dxl[l][m][q] = l == m ? p->h[l] : 0.0;
+                    c->xh[l][m][q] = l == m ? diag[l] : (double)0.0;
+                    c->xt[l][m][q] = l == m ? diag[l] : (double)0.0;
+                    c->dxl[l][m][q] = l == m ? p->h[l] : (double)0.0;
                 }
             c->jac[q] = J;
         }
@@ -1634,4 +1687,15 @@ int orc_metrics(void *ctx, double *node, double *iface)
         node[nd * nd * c->N + qi] = c->jac[q];
     }
     return 0;
+}
+
+int orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }

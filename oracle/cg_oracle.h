@@ -53,6 +53,8 @@ typedef struct {
     double re, pr;
     double suth;              /* Sutherland constant S / T_inf */
     double twall;             /* temperature of ORC_BC_WALL faces (units of T_inf) */
+    int hybrid_buffer;        /* per-cell mode: a troubled node also marks the nodes within
+                                 this many nodes (0: the node alone) */
 } orc_params;
 
 /* Context: holds the metrics (computed from the coordinates for curvilinear
@@ -106,6 +108,9 @@ void orc_tridiag(int n, double a, int cyclic, const double *rhs, double *x);
  * at any depth take the profile of their transverse position (clamped to the
  * face).  Copied; returns 0, or -1 if the face is not an inflow face. */
 int orc_set_inflow_profile(void *ctx, int d, int side, const double *W);
+/* Threads of the OpenMP build for the grid loops (n <= 0: unchanged); returns
+ * the count in use (1 without OpenMP).  Results do not depend on it. */
+int orc_set_threads(int n);
 
 #ifdef __cplusplus
 }

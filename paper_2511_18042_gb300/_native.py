@@ -33,6 +33,7 @@ class CgParams(ctypes.Structure):
         ("suth", ctypes.c_double),
         ("twall", ctypes.c_double),
         ("fma_sweep", ctypes.c_int),
+        ("hybrid_buffer", ctypes.c_int),
     ]
 
 
@@ -68,6 +69,7 @@ _SIGS = {
                                        ctypes.c_void_p]),
     "cg_sync_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "cg_last_bad_index": (ctypes.c_int64, [ctypes.c_void_p]),
+    "cg_solver_device_bytes": (ctypes.c_int64, [ctypes.c_void_p]),
     "cg_last_error": (ctypes.c_char_p, []),
     "cg_launch_count": (ctypes.c_int64, [ctypes.c_void_p]),
     "cg_timing_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),

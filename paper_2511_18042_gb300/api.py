@@ -213,6 +213,10 @@ class Solver:
     def launch_count(self):
         return int(nat.lib().cg_launch_count(self._h))
 
+    def device_bytes(self):
+        """Device memory the solver holds (scratch; the caller's state excluded)."""
+        return int(nat.lib().cg_solver_device_bytes(self._h))
+
     def timing_enable(self, on=True):
         nat.check(nat.lib().cg_timing_enable(self._h, 1 if on else 0))
 

@@ -7,6 +7,8 @@ ROOT = os.path.dirname(HERE)
 SRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libcgflow.so")
+# FMA-throughput probe of the benchmark's arithmetic roofline (own library)
+PROBE = os.path.join(OUT_DIR, "libcgprobe.so")
 
 COMMON = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
           "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"]
@@ -34,7 +36,7 @@ def _sources_mtime():
 
 
 def build(force=False, verbose=False):
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _sources_mtime():
+    if not force and os.path.exists(LIB) and os.path.exists(PROBE) and os.path.getmtime(LIB) >= _sources_mtime():
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)
     objs, procs = [], []
@@ -45,9 +47,14 @@ def build(force=False, verbose=False):
             print(" ".join(cmd))
         procs.append(subprocess.Popen(cmd))
         objs.append(obj)
+    pcmd = ["nvcc"] + COMMON + ["-shared", "-o", PROBE + ".tmp%d" % os.getpid(), os.path.join(SRC, "cg_probe.cu")]
+    if verbose:
+        print(" ".join(pcmd))
+    procs.append(subprocess.Popen(pcmd))
     for p in procs:
         if p.wait() != 0:
             raise subprocess.CalledProcessError(p.returncode, "nvcc")
+    os.replace(PROBE + ".tmp%d" % os.getpid(), PROBE)
     tmp = LIB + ".tmp%d" % os.getpid()
     cmd = ["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-shared", "-o", tmp] + objs
     if verbose:

@@ -209,6 +209,7 @@ struct cg_grid {
 };
 
 struct cg_solver {
+  size_t dev_bytes = 0;  // device memory this solver holds (cg_solver_device_bytes)
   const cg_grid* grid;
   cg_params p;
   DevGrid dg;
@@ -374,6 +375,10 @@ static LineBuf make_lines(const cg_solver* s, int d, int lo, int m_nonper, int g
   return lb;
 }
 
+// bytes this thread has allocated through dalloc (a solver's device footprint
+// is the difference across its creation plus its lazily allocated buffers)
+static thread_local size_t t_dalloc_bytes = 0;
+
 template <typename T>
 static int dalloc(T** p, size_t count) {
   if (count == 0) count = 1;
@@ -382,6 +387,7 @@ static int dalloc(T** p, size_t count) {
     *p = nullptr;
     return fail(CG_ERR_OOM, "cudaMalloc of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
   }
+  t_dalloc_bytes += count * sizeof(T);
   return CG_OK;
 }
 
@@ -980,6 +986,7 @@ CG_API void cg_params_default(cg_params* p) {
   p->suth = 0.0;
   p->twall = 1.0;
   p->fma_sweep = 0;
+  p->hybrid_buffer = 0;
 }
 
 CG_API int cg_solver_set_inflow_profile(cg_solver* s, int dir, int side, const double* W_host) {
@@ -988,8 +995,10 @@ CG_API int cg_solver_set_inflow_profile(cg_solver* s, int dir, int side, const d
     return fail(CG_ERR_INVALID_ARG, "face (%d, %d) is not an inflow face", dir, side);
   size_t count = (size_t)s->nv * (size_t)s->dg.pf[dir];
   if (!s->prof[dir][side]) {
+    size_t b0 = t_dalloc_bytes;
     int rc = dalloc(&s->prof[dir][side], count);
     if (rc) return rc;
+    s->dev_bytes += t_dalloc_bytes - b0;
   }
   CG_CUDA(cudaMemcpy(s->prof[dir][side], W_host, count * sizeof(double), cudaMemcpyHostToDevice));
   s->dg.prof[dir][side] = s->prof[dir][side];
@@ -1105,22 +1114,33 @@ CG_API void cg_solver_destroy(cg_solver* s) {
   delete s;
 }
 
-CG_API int cg_solver_create(const cg_grid* g, const cg_params* p, cg_solver** out) {
-  if (!g || !p || !out) return fail(CG_ERR_INVALID_ARG, "null argument");
+// Parameter checks of a solver on grid g, shared by cg_solver_create and
+// cg_rhs_meg6_noalloc so that both reject the same inputs.
+static int check_params(const cg_grid* g, const cg_params* p) {
   if (p->scheme < CG_MEG6 || p->scheme > CG_HYBRID) return fail(CG_ERR_INVALID_ARG, "bad scheme");
   if (p->precision != CG_FP64 && p->precision != CG_MIXED) return fail(CG_ERR_INVALID_ARG, "bad precision");
   if (!(p->gamma > 1.0) || !(p->cfl > 0.0)) return fail(CG_ERR_INVALID_ARG, "gamma > 1 and cfl > 0 required");
+  if (!(p->minf > 0.0)) return fail(CG_ERR_INVALID_ARG, "minf > 0 required");
   if (p->omega_window < 1 || p->omega_window > 4) return fail(CG_ERR_INVALID_ARG, "omega_window must be 1..4");
+  if (p->hybrid_buffer < 0 || p->hybrid_buffer > 2) return fail(CG_ERR_INVALID_ARG, "hybrid_buffer must be 0..2");
   if (g->curv && p->scheme == CG_LAD_C6)
     return fail(CG_ERR_UNSUPPORTED, "LAD-C6 on curvilinear grids is not supported (the metric identities need the compact operator)");
-  if (p->viscous && (!(p->re > 0.0) || !(p->pr > 0.0) || !(p->suth >= 0.0) || !(p->minf > 0.0)))
-    return fail(CG_ERR_INVALID_ARG, "viscous: re > 0, pr > 0, minf > 0 and suth >= 0 required");
+  if (p->viscous && (!(p->re > 0.0) || !(p->pr > 0.0) || !(p->suth >= 0.0)))
+    return fail(CG_ERR_INVALID_ARG, "viscous: re > 0, pr > 0 and suth >= 0 required");
   for (int d = 0; d < g->nd; ++d)
     for (int side = 0; side < 2; ++side)
       if (g->bc[d][side] == CG_BC_WALL && !(p->twall > 0.0))
         return fail(CG_ERR_INVALID_ARG, "isothermal walls need twall > 0");
+  return CG_OK;
+}
+
+CG_API int cg_solver_create(const cg_grid* g, const cg_params* p, cg_solver** out) {
+  if (!g || !p || !out) return fail(CG_ERR_INVALID_ARG, "null argument");
+  int prc = check_params(g, p);
+  if (prc) return prc;
   cg_solver* s = new (std::nothrow) cg_solver();
   if (!s) return fail(CG_ERR_OOM, "host allocation failed");
+  size_t bytes0 = t_dalloc_bytes;
   s->grid = g;
   s->p = *p;
   s->nd = g->nd;
@@ -1164,9 +1184,12 @@ CG_API int cg_solver_create(const cg_grid* g, const cg_params* p, cg_solver** ou
   if ((rc = lad_alloc(s))) { cg_solver_destroy(s); return rc; }
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) { cg_solver_destroy(s); return fail(CG_ERR_CUDA, "setup: %s", cudaGetErrorString(e)); }
+  s->dev_bytes = t_dalloc_bytes - bytes0;
   *out = s;
   return CG_OK;
 }
+
+CG_API int64_t cg_solver_device_bytes(const cg_solver* s) { return s ? (int64_t)s->dev_bytes : -1; }
 
 CG_API int cg_metrics(cg_solver* s, double* node_dev, double* iface_dev, void* stream) {
   if (!s || !node_dev) return fail(CG_ERR_INVALID_ARG, "null argument");
@@ -1346,7 +1369,11 @@ CG_API int cg_advance_host(cg_solver* s, double* U_host, int64_t nsteps, double 
   if (!s || !U_host) return fail(CG_ERR_INVALID_ARG, "null argument");
   cudaStream_t st = (cudaStream_t)stream;
   size_t bytes = sizeof(double) * s->nv * s->N;
-  if (!s->host_stage && dalloc(&s->host_stage, (size_t)s->nv * s->N)) return CG_ERR_OOM;
+  if (!s->host_stage) {
+    size_t b0 = t_dalloc_bytes;
+    if (dalloc(&s->host_stage, (size_t)s->nv * s->N)) return CG_ERR_OOM;
+    s->dev_bytes += t_dalloc_bytes - b0;
+  }
   CG_CUDA(cudaMemcpyAsync(s->host_stage, U_host, bytes, cudaMemcpyHostToDevice, st));
   int rc = cg_advance(s, s->host_stage, nsteps, t_end, t_out, nullptr, stream);
   CG_CUDA(cudaMemcpyAsync(U_host, s->host_stage, bytes, cudaMemcpyDeviceToHost, st));
@@ -1387,7 +1414,11 @@ CG_API int cg_iface_flux(cg_solver* s, const double* U, int dir, double* F, void
   if (sch != CG_MEG6 && sch != CG_MIG4 && !(sch == CG_HYBRID && s->p.hybrid_mode == CG_HYBRID_CELL))
     return fail(CG_ERR_UNSUPPORTED, "interface fluxes exist for the C-GBR and per-interface hybrid schemes");
   cudaStream_t st = (cudaStream_t)stream;
-  if (!s->Rtmp && dalloc(&s->Rtmp, (size_t)s->nv * s->N)) return CG_ERR_OOM;
+  if (!s->Rtmp) {
+    size_t b0 = t_dalloc_bytes;
+    if (dalloc(&s->Rtmp, (size_t)s->nv * s->N)) return CG_ERR_OOM;
+    s->dev_bytes += t_dalloc_bytes - b0;
+  }
   s->iface_dir = dir;
   s->iface_out = F;
   int rc = DISPATCH_ND(s, stage, s, U, U, s->Rtmp, 0, 1, st);
@@ -1448,10 +1479,24 @@ extern "C" CG_API int cg_rhs_meg6_noalloc(int ndim, const int64_t n[3], const do
   if (rc) return rc;
   for (int d = 0; d < ndim; ++d)
     if (!(h[d] > 0.0)) return fail(CG_ERR_INVALID_ARG, "spacing must be positive");
+  // grid descriptor on the stack (nothing allocated)
+  cg_grid gr;
+  gr.nd = ndim;
+  gr.curv = 0;
+  gr.xyz = nullptr;
+  for (int d = 0; d < 3; ++d) {
+    gr.n[d] = (int)n[d];
+    gr.h[d] = d < ndim ? h[d] : 1.0;
+    gr.bc[d][0] = d < ndim ? bc[2 * d] : CG_BC_PERIODIC;
+    gr.bc[d][1] = d < ndim ? bc[2 * d + 1] : CG_BC_PERIODIC;
+    for (int m = 0; m < 3; ++m) gr.period[d][m] = 0.0;
+  }
+  rc = check_params(&gr, p);
+  if (rc) return rc;
   if (p->scheme != CG_MEG6) return fail(CG_ERR_UNSUPPORTED, "the no-allocation RHS evaluates the MEG6 scheme only");
-  if (p->precision != CG_FP64) return fail(CG_ERR_UNSUPPORTED, "only the FP64 form is built in this library");
-  if (!(p->gamma > 1.0) || p->omega_window < 1 || p->omega_window > 4)
-    return fail(CG_ERR_INVALID_ARG, "gamma > 1 and omega_window in 1..4 required");
+  if (p->precision != CG_FP64) return fail(CG_ERR_UNSUPPORTED, "the no-allocation RHS supports CG_FP64 only");
+  if (p->viscous)
+    return fail(CG_ERR_UNSUPPORTED, "the no-allocation RHS is inviscid only (viscous needs the solver's scratch)");
   long long N = 1, box = 1;
   for (int d = 0; d < 3; ++d) {
     N *= n[d];
@@ -1480,19 +1525,8 @@ extern "C" CG_API int cg_rhs_meg6_noalloc(int ndim, const int64_t n[3], const do
     }
     base = g_noalloc_addr[dev];
   }
-  // grid and solver descriptors on the stack; every scratch pointer is carved
-  // out of the fixed array (W, accumulator, sensor), each written before read
-  cg_grid gr;
-  gr.nd = ndim;
-  gr.curv = 0;
-  gr.xyz = nullptr;
-  for (int d = 0; d < 3; ++d) {
-    gr.n[d] = (int)n[d];
-    gr.h[d] = d < ndim ? h[d] : 1.0;
-    gr.bc[d][0] = d < ndim ? bc[2 * d] : CG_BC_PERIODIC;
-    gr.bc[d][1] = d < ndim ? bc[2 * d + 1] : CG_BC_PERIODIC;
-    for (int m = 0; m < 3; ++m) gr.period[d][m] = 0.0;
-  }
+  // solver descriptor on the stack; every scratch pointer is carved out of
+  // the fixed array (W, accumulator, sensor), each written before read
   cg_solver s;
   s.grid = &gr;
   s.p = *p;

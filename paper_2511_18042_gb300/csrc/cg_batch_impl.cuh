@@ -47,19 +47,22 @@ int multi_step(cg_solver* const* solvers, double* const* states, int count, cuda
   std::vector<int> order(count);
   for (int i = 0; i < count; ++i) order[i] = i;
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return solvers[a]->N > solvers[b]->N; });
-  for (int k = 0; k < count; ++k) {
+  for (int k = 0; k < count && !rc; ++k) {
     int i = order[k];
     cg_solver* s = solvers[i];
     cudaStream_t si = g_pool.s[k % ns];
     DISPATCH_ND(s, cfl_launch, s, states[i], s->dt, nullptr, 0.0, si);
     rc = DISPATCH_ND(s, rk3, s, states[i], si);
-    if (rc) return rc;
   }
+  // join every forked stream back, also after an error: later work on the
+  // caller's stream stays ordered after the members already enqueued, and a
+  // stream capture is not left with an unjoined fork
   for (int i = 0; i < ns; ++i) {
-    CG_CUDA(cudaEventRecord(g_pool.join[i], g_pool.s[i]));
-    CG_CUDA(cudaStreamWaitEvent(st, g_pool.join[i], 0));
+    cudaError_t e = cudaEventRecord(g_pool.join[i], g_pool.s[i]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, g_pool.join[i], 0);
+    if (e != cudaSuccess && !rc) rc = fail(CG_ERR_CUDA, "stream join: %s", cudaGetErrorString(e));
   }
-  return CG_OK;
+  return rc;
 }
 
 // ---------------------------------------------------------------- work-table path
@@ -188,7 +191,7 @@ static int table_build_t(BatchTable& tb, cg_solver* const* sv, double* const* st
     fd[m] = JobField<T>{s->dg, W, fb, L.fbx, (unsigned)table_blocks(L.fbx.size())};
     tr[m] = JobTroubled<T>{s->dg, W, s->p.hyb_rho, s->p.hyb_p, s->p.hybrid_sensor ? reinterpret_cast<const T*>(s->om) : nullptr, s->omBox,
                            s->p.sensor_thresh, L.tr, L.tbox, s->hyb_flag, s->hyb_count,
-                           (unsigned)table_blocks(L.tbox.size())};
+                           (unsigned)table_blocks(L.tbox.size()), s->p.hybrid_buffer};
     JobGrad<T> j;
     j.g = s->dg;
     j.fb = fb;

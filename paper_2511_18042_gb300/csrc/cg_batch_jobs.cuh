@@ -120,8 +120,9 @@ struct JobTroubled {
   int* flag;
   unsigned long long* count;
   unsigned nb;
+  int buf;
   __device__ void run(unsigned b) const {
-    k_troubled_body<2, T>(vblock_1d(b, nb), g, W, hr, hp, om, ob, thr, tr, tb, flag, count);
+    k_troubled_body<2, T>(vblock_1d(b, nb), g, W, hr, hp, om, ob, thr, tr, tb, flag, count, buf);
   }
 };
 

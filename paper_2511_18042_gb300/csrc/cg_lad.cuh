@@ -568,27 +568,45 @@ __global__ void k_lad_div(DevGrid g, int l, const T* __restrict__ Fn, Box fb, co
   }
 }
 
-// Hybrid: troubled nodes on tbox ([-1, n]^nd): rho < hyb_rho or p < hyb_p, or
-// (with the sensor) Omega > threshold; counts troubled interior nodes and
-// sets flag[0] = 1 if any (the global decision of Algorithm 3).
+// Troubled-node criterion of Sec. 5 at node (x, y, z) (ghost-resolved):
+// rho < hyb_rho or p < hyb_p, or (with the sensor) Omega > threshold.
+template <int ND, typename TW>
+__device__ __forceinline__ bool troubled_at(const DevGrid& g, const TW* __restrict__ W, double hr, double hp,
+                                            const TW* __restrict__ om, const Box& ob, double thr, int x, int y, int z) {
+  constexpr int NV = ND + 2, IP = ND + 1;
+  double w[NV];
+  load_state<ND, false, TW, double>(g, W, x, y, z, w);
+  bool t = w[0] < hr || w[IP] < hp;
+  if (om && double(om[ob.at(x, y, z)]) > thr) t = true;
+  return t;
+}
+
+// Hybrid: troubled nodes on tbox ([-1, n]^nd); counts troubled interior nodes
+// and sets flag[0] = 1 if any (the global decision of Algorithm 3).  With a
+// buffer buf > 0 the mask tr marks a node when any node within buf of it in
+// each direction is troubled (the sensor box [-4, n+3] covers buf <= 2).
 template <int ND, typename TW = double>
 __device__ __forceinline__ void k_troubled_body(const VBlock& vb, const DevGrid& g, const TW* __restrict__ W, double hr, double hp, const TW* __restrict__ om,
                            Box ob, double thr, unsigned char* __restrict__ tr, Box tb, int* flag,
-                           unsigned long long* count) {
-  constexpr int NV = ND + 2, IP = ND + 1;
+                           unsigned long long* count, int buf = 0) {
   unsigned long long local = 0;
   BOX_LOOP(tb, e) {
     int c[3];
     box_coords(tb, e, c);
-    double w[NV];
-    load_state<ND, false, TW, double>(g, W, c[0], c[1], c[2], w);
-    bool t = w[0] < hr || w[IP] < hp;
-    if (om && double(om[ob.at(c[0], c[1], c[2])]) > thr) t = true;
+    bool own = troubled_at<ND, TW>(g, W, hr, hp, om, ob, thr, c[0], c[1], c[2]);
+    bool t = own;
+    if (buf > 0 && tr) {
+      const int bz = ND > 2 ? buf : 0, by = ND > 1 ? buf : 0;
+      for (int dz = -bz; dz <= bz && !t; ++dz)
+        for (int dy = -by; dy <= by && !t; ++dy)
+          for (int dx = -buf; dx <= buf && !t; ++dx)
+            if (dx || dy || dz) t = troubled_at<ND, TW>(g, W, hr, hp, om, ob, thr, c[0] + dx, c[1] + dy, c[2] + dz);
+    }
     if (tr) tr[e] = t ? 1 : 0;
     bool interior = true;
 #pragma unroll
     for (int d = 0; d < ND; ++d) interior = interior && c[d] >= 0 && c[d] < g.n[d];
-    if (t && interior) ++local;
+    if (own && interior) ++local;
   }
   if (local) {
     atomicAdd(count, local);
@@ -599,8 +617,8 @@ __device__ __forceinline__ void k_troubled_body(const VBlock& vb, const DevGrid&
 template <int ND, typename TW = double>
 __global__ void k_troubled(DevGrid g, const TW* __restrict__ W, double hr, double hp, const TW* __restrict__ om,
                            Box ob, double thr, unsigned char* __restrict__ tr, Box tb, int* flag,
-                           unsigned long long* count) {
-  k_troubled_body<ND, TW>(hw_block(), g, W, hr, hp, om, ob, thr, tr, tb, flag, count);
+                           unsigned long long* count, int buf) {
+  k_troubled_body<ND, TW>(hw_block(), g, W, hr, hp, om, ob, thr, tr, tb, flag, count, buf);
 }
 
 // Per-interface hybrid: LAD flux at interfaces i+1/2 (i in [-1, n-1]) in the

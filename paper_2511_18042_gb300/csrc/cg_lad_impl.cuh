@@ -261,7 +261,7 @@ static int lad_stage_t(cg_solver* s, const double* Uc, StageArgs A, cudaStream_t
     // Algorithm 3: GBR-MEG6 for the whole stage if any node is troubled, else LAD-E4
     k_troubled<ND, T><<<grid_blocks(L.tbox.size(), 256), 256, 0, st>>>(s->dg, reinterpret_cast<const T*>(s->W), s->p.hyb_rho, s->p.hyb_p, nullptr,
                                                                    s->omBox, 0.0, nullptr, L.tbox, s->hyb_flag,
-                                                                   s->hyb_count);
+                                                                   s->hyb_count, 0);
     s->launches++;
     stage_prep_gbr<ND>(s, Uc, false, st, false, s->hyb_flag, 1);
     StageArgs G = A;
@@ -276,7 +276,7 @@ static int lad_stage_t(cg_solver* s, const double* Uc, StageArgs A, cudaStream_t
   stage_prep_gbr<ND>(s, Uc, false, st, false);
   k_troubled<ND, T><<<grid_blocks(L.tbox.size(), 256), 256, 0, st>>>(
       s->dg, reinterpret_cast<const T*>(s->W), s->p.hyb_rho, s->p.hyb_p, s->p.hybrid_sensor ? reinterpret_cast<const T*>(s->om) : nullptr, s->omBox, s->p.sensor_thresh, L.tr,
-      L.tbox, s->hyb_flag, s->hyb_count);
+      L.tbox, s->hyb_flag, s->hyb_count, s->p.hybrid_buffer);
   s->launches++;
   int rc = lad_coeffs_run<ND, T>(s, 2, st, nullptr, 0);
   if (rc) return rc;

@@ -34,7 +34,8 @@ def same_member(alone, batched, kw):
 
 
 KW = [dict(scheme="MEG6"), dict(scheme="HYBRID", hybrid_mode=1, hyb_rho=0.3, hybrid_sensor=1),
-      dict(scheme="HYBRID", hybrid_mode=1, hyb_rho=0.3, hybrid_sensor=1, precision=1)]
+      dict(scheme="HYBRID", hybrid_mode=1, hyb_rho=0.3, hybrid_sensor=1, precision=1),
+      dict(scheme="HYBRID", hybrid_mode=1, hyb_rho=0.3, hybrid_sensor=1, hybrid_buffer=1)]
 
 
 @pytest.mark.parametrize("kw", KW)

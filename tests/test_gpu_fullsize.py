@@ -3,7 +3,8 @@ benchmark times (autotuned tile shapes, default FP64 form):
 
 * triple point 1792 x 768: one RK3 step of each of the six schemes from a
   state the oracle developed (5 MEG6 steps from the initial condition),
-  compared element by element with the oracle's step;
+  compared element by element with the oracle's step, and 100 steps of MEG6
+  and the per-interface hybrid from the initial condition;
 * compression-ramp grid 768 x 192 x 128: a uniform stream through the full
   body-fitted grid (inflow and outflow at the free-stream state, the wall
   replaced by extrapolation) stays uniform to round-off for every scheme,
@@ -54,6 +55,24 @@ def test_triple_point_full_size_every_scheme(orc, api, developed, name, kw):
     s.rk3_step(Ud, dt_o)
     Uo = o.rk3_step(U, dt_o)
     assert rel_err(Ud, Uo) <= 1e-12, name
+
+
+@pytest.mark.parametrize("name", ["MEG6", "HYBRID_CELL"])
+def test_triple_point_full_size_100_steps(orc, api, name):
+    """The spec bar at the benchmark's size: 100 RK3 steps (CFL time
+    steps on each side) of the 1792 x 768 triple point from its initial
+    condition, max relative error <= 1e-11 per variable against the oracle
+    (run on all host cores; its results do not depend on the thread count)."""
+    kw = dict(SIX)[name]
+    prob = inputs.triple_point()
+    orc.set_threads(0)
+    Uo, to, ko = orc.Oracle(prob, **kw).advance(prob["U"], nsteps=100)
+    s = api.Solver.from_problem(prob, **kw)
+    Ud = to_dev(prob["U"])
+    s.autotune(Ud)
+    tg, kg = s.advance(Ud, nsteps=100)
+    assert kg == ko == 100 and abs(tg - to) <= 1e-13 * to
+    assert rel_err(Ud, Uo) <= 1e-11, name
 
 
 @pytest.mark.parametrize("viscous", [False, True])

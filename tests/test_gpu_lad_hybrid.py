@@ -113,10 +113,10 @@ def test_hybrid_global_triple_point(orc, api):
     assert 0 < sum(flags_g) < len(flags_g)
 
 
-@pytest.mark.parametrize("sensor", [0, 1])
-def test_hybrid_per_interface_triple_point(orc, api, sensor):
+@pytest.mark.parametrize("sensor,buf", [(0, 0), (1, 0), (1, 1), (0, 2)])
+def test_hybrid_per_interface_triple_point(orc, api, sensor, buf):
     prob = inputs.triple_point(224, 96)
-    kw = dict(scheme="HYBRID", hybrid_mode=1, hyb_rho=0.5 * 0.125, hybrid_sensor=sensor)
+    kw = dict(scheme="HYBRID", hybrid_mode=1, hyb_rho=0.5 * 0.125, hybrid_sensor=sensor, hybrid_buffer=buf)
     o, s = _pair(orc, api, prob, **kw)
     Uo, _, _ = o.advance(prob["U"], nsteps=60)
     Ug = to_dev(prob["U"])

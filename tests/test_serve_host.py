@@ -74,8 +74,10 @@ def test_solver_kwargs_thresholds():
     assert serve.solver_kwargs(reqs[0].prob, precision=0)["precision"] == 0
 
 
-def test_bytes_estimate():
-    reqs = serve.request_mix(10, rate=1.0, seed=9, tube=(50, 100), quad=(16, 24))
+def test_state_bytes_and_solver_kwargs():
+    reqs = serve.request_mix(8, rate=2.0, seed=3, tube=(50, 400), quad=(16, 48))
     for r in reqs:
         nv = r.prob["ndim"] + 2
-        assert serve.bytes_estimate(r.prob) == 8 * nv * r.cells * 40
+        assert serve.state_bytes(r.prob) == 8 * nv * r.cells == r.prob["U"].nbytes
+        kw = serve.solver_kwargs(r.prob)
+        assert kw["hybrid_mode"] == 1 and kw["hybrid_buffer"] == 1 and kw["precision"] == 1
