@@ -56,7 +56,7 @@ METRIC = "cell-updates/s per scheme & % HBM roofline; batched solves/s, p50/p99 
 SWEEP_FLOP_PER_IFACE = 524.8
 # dram read + write per launch (mean of x and y) of the sweep form the roofline times,
 # from its ncu capture (profiles/); None until the current kernel has been captured
-SWEEP_TRAFFIC_BYTES = {"exact": 92.0e6, "contracted": 140.2e6}
+SWEEP_TRAFFIC_BYTES = {"exact": 117.7e6, "contracted": 140.2e6}
 ROOFLINE_FORM = "exact"  # the library default (fma_sweep = 0)
 FP64_PEAK_DERIVED_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12  # SMs x DFMA/clk x 2 flop x max clock (context only)
 HBM_BYTES_PER_CELL_STEP = 256.0  # minimal-traffic model, FP64 state, nv = 4, uniform grid
@@ -196,7 +196,8 @@ def run_gpu(args):
     grid = api.Grid.from_problem(prob)
     cells = NX * NY
     names = [n for n, _ in SCHEMES if args.schemes is None or n in args.schemes.split(",")]
-    solvers = {n: api.Solver(grid, **kw) for n, kw in SCHEMES if n in names}
+    prec = {"precision": 1} if args.precision == "mixed" else {}
+    solvers = {n: api.Solver(grid, **kw, **prec) for n, kw in SCHEMES if n in names}
     # developed state: 200 MEG6 steps from the initial condition
     base = torch.as_tensor(prob["U"], device=dev)
     dev_solver = solvers.get("MEG6") or api.Solver(grid, scheme="MEG6")
@@ -231,6 +232,8 @@ def run_gpu(args):
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
+    if args.profile_timed:
+        torch.cuda.cudart().cudaProfilerStart()
     try:
         clk.mark(True)
         wall0 = time.perf_counter()
@@ -247,6 +250,8 @@ def run_gpu(args):
         clk.mark(False)
     finally:
         clk.__exit__(None, None, None)
+        if args.profile_timed:
+            torch.cuda.cudart().cudaProfilerStop()
     launches = sum(s.launch_count() for s in solvers.values()) - launches0
     # a scheme whose timed steps produced rho <= 0, p <= 0 or NaN is excluded from value
     status = {}
@@ -261,7 +266,7 @@ def run_gpu(args):
 
     # the mixed form (FP32 fluxes, FP64 accumulation) of the schemes that have it
     mixed = {}
-    for n, kw in MIXED:
+    for n, kw in (MIXED if args.mixed else []):
         ms, tile = time_mixed(api, torch, grid, base, dev, kw, args)
         cu = cells / (ms * 1e-3)
         mixed[n] = {"cell_updates_per_s": cu, "ms_per_rk3_step": ms, "tile_lines": list(tile),
@@ -274,7 +279,7 @@ def run_gpu(args):
 
     # roofline of the dominant kernel: the MEG6 interface sweep, timed alone,
     # against the measured FP64 FMA throughput
-    roof = sweep_roofline(api, torch, grid, base, dev, args, measure_fma_peaks(local))
+    roof = sweep_roofline(api, torch, grid, base, dev, args, measure_fma_peaks(local)) if args.roofline else None
 
     # end to end through the C ABI with host buffers (pinned), one step per scheme
     host = torch.empty(base.shape, dtype=torch.float64, pin_memory=True)
@@ -302,7 +307,7 @@ def run_gpu(args):
     line = {
         "metric": METRIC,
         "value": value, "unit": "cell-updates/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32",
         "data": "synthetic",
         "config": dict(bench_config(names, ws), counted=ok,
                        excluded_nonphysical=[n for n in names if status[n] != "ok"]),
@@ -688,6 +693,12 @@ def main():
     ap.add_argument("--no-sod", dest="sod", action="store_false")
     ap.add_argument("--no-ramp", dest="ramp", action="store_false")
     ap.add_argument("--ramp-steps", type=int, default=20)
+    ap.add_argument("--no-mixed", dest="mixed", action="store_false")
+    ap.add_argument("--no-roofline", dest="roofline", action="store_false")
+    ap.add_argument("--profile-timed", action="store_true",
+                    help="cudaProfilerStart/Stop around the timed steps (ncu --profile-from-start off)")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
+                    help="form of the timed schemes (profiling; the headline is FP64)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

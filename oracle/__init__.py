@@ -172,14 +172,12 @@ class Oracle:
         self.nv = self.nd + 2
         self.shape = tuple(int(problem["n"][k]) for k in range(self.nd))[::-1]
         xyz = problem.get("xyz")
-        if xyz is not None and self.params.scheme == LAD_C6:
-            # the compact operators of LAD-C6 inside the curvilinear metrics are not
-            # defined here (the CUDA library rejects the pairing as well)
-            raise NotImplementedError("LAD-C6 on a curvilinear grid")
         self._xyz = None if xyz is None else np.ascontiguousarray(xyz, dtype=np.float64)
         L = lib()
         self._ctx = L.orc_create(ctypes.byref(self.params),
                                  None if self._xyz is None else _ptr(self._xyz))
+        if not self._ctx:
+            raise RuntimeError("orc_create failed")
         for (d, side), W in problem.get("inflow_profile", {}).items():
             Wp = np.ascontiguousarray(W, dtype=np.float64)
             if L.orc_set_inflow_profile(self._ctx, int(d), int(side), _ptr(Wp)) != 0:

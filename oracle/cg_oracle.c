@@ -1302,8 +1302,21 @@ static void filter_state(const ctx_t *c, double *U)
         b.lo[d] = 0; b.hi[d] = 1;
         FOR_BOX_PAR(b, i0, j0, k0) {
             long q0 = pidx(c, i0, j0, k0);
-            for (int v = 0; v < nv; ++v)
-                filter_line(n, periodic, c->p.alpha_f, Qp + v * c->NP + q0, s, out + v * c->NP + q0);
+            if (!c->p.curvilinear) {
+                for (int v = 0; v < nv; ++v)
+                    filter_line(n, periodic, c->p.alpha_f, Qp + v * c->NP + q0, s, out + v * c->NP + q0);
+                continue;
+            }
+            /* curvilinear: the filter acts on the transformed conserved vector
+             * Q/J, the quantity the discrete conservation law advances */
+            int P = n + 2 * GH;
+            double *ln = (double *)malloc(sizeof(double) * P), *lo = (double *)malloc(sizeof(double) * P);
+            for (int v = 0; v < nv; ++v) {
+                for (int t = -GH; t < n + GH; ++t) ln[t + GH] = Qp[v * c->NP + q0 + t * s] / c->jac[q0 + t * s];
+                filter_line(n, periodic, c->p.alpha_f, ln + GH, 1, lo + GH);
+                for (int t = 0; t < n; ++t) out[v * c->NP + q0 + t * s] = lo[t + GH] * c->jac[q0 + t * s];
+            }
+            free(ln); free(lo);
         }
         FOR_BOX_PAR(b0, i, j, k) {
             long q = pidx(c, i, j, k);
@@ -1488,11 +1501,54 @@ static double *eop(const ebox_t *e, const double *f, int d, int op, int six)
     return o;
 }
 
+/* Compact sixth-order (C6) derivative along d on the extended box: the
+ * operator of the LAD-C6 flux divergence, so that the metric identities hold
+ * for it (reading: the compact operator inside the metrics).  Non-periodic d:
+ * the system on nodes [0, n-1] with explicit E4 rows at both ends (reading f
+ * at -2 .. n+1), the E4 derivative at the other extended nodes (used only by
+ * the chain rule at ghost nodes).  Periodic d: the cyclic system on [0, n-1]
+ * applied to f minus its linear trend along the line (detrend = 1, for a
+ * coordinate: T = f_n - f_0, its period translation), plus T/n; the
+ * extended nodes by wrapping. */
+static double *eop_c6(const ebox_t *e, const double *f, int d, int periodic, int detrend)
+{
+    double *o = eop(e, f, d, 0, 0);
+    long s = estride(e, d);
+    int n = e->n[d], g = e->ge[d];
+    int lo[3], hi[3];
+    for (int a = 0; a < 3; ++a) { lo[a] = -e->ge[a]; hi[a] = e->n[a] + e->ge[a]; }
+    lo[d] = 0; hi[d] = 1;
+    double *gl = (double *)malloc(sizeof(double) * (n + 4)), *og = (double *)malloc(sizeof(double) * (n + 4));
+    for (int k = lo[2]; k < hi[2]; ++k)
+        for (int j = lo[1]; j < hi[1]; ++j)
+            for (int i = lo[0]; i < hi[0]; ++i) {
+                long q0 = eidx(e, i, j, k);
+                int ok = 1;
+                for (int t = -2; t <= n + 1; ++t) ok = ok && !isnan(f[q0 + t * s]);
+                if (!ok) continue;
+                if (!periodic) {
+                    compact_line(3, n, 0, 0, n - 1, f + q0, s, o + q0);
+                    continue;
+                }
+                double T = detrend ? f[q0 + (long)n * s] - f[q0] : 0.0;
+                for (int t = -2; t <= n + 1; ++t) gl[t + 2] = f[q0 + t * s] - T * (double)t / (double)n;
+                compact_line(3, n, 1, 0, n - 1, gl + 2, 1, og + 2);
+                for (int t = 0; t < n; ++t) o[q0 + t * s] = og[t + 2] + T / (double)n;
+                for (int t = 1; t <= g; ++t) {
+                    o[q0 - t * s] = o[q0 + imod(-t, n) * s];
+                    o[q0 + (n - 1 + t) * s] = o[q0 + imod(n - 1 + t, n) * s];
+                }
+            }
+    free(gl); free(og);
+    return o;
+}
+
 static void metrics_curvilinear(ctx_t *c, const double *xyz)
 {
     ORC_REGION(metrics);
     int nd = c->nd;
     int six = (c->p.scheme == ORC_MEG6 || c->p.scheme == ORC_MIG4);
+    int c6 = c->p.scheme == ORC_LAD_C6;
     ebox_t e;
     e.nd = nd;
     e.NE = 1;
@@ -1541,10 +1597,13 @@ static void metrics_curvilinear(ctx_t *c, const double *xyz)
                     }
                 }
     }
-    /* node derivatives dX[l][m] = D_l x_m */
+    /* node derivatives dX[l][m] = D_l x_m (LAD-C6: its own compact operator) */
+    int per[3];
+    for (int d = 0; d < 3; ++d) per[d] = d < nd && c->p.bc[d][0] == ORC_BC_PERIODIC;
+#define MOP(f, d) (c6 ? eop_c6(&e, (f), (d), per[d], 1) : eop(&e, (f), (d), 0, six))
     double *dX[3][3];
     for (int l = 0; l < nd; ++l)
-        for (int m = 0; m < nd; ++m) dX[l][m] = eop(&e, X[m], l, 0, six);
+        for (int m = 0; m < nd; ++m) dX[l][m] = MOP(X[m], l);
     double *node[3][3], *ifc[3][3], *vol = ealloc(&e);
     for (int l = 0; l < 3; ++l) for (int m = 0; m < 3; ++m) { node[l][m] = NULL; ifc[l][m] = NULL; }
     if (nd == 1) {
@@ -1560,23 +1619,50 @@ static void metrics_curvilinear(ctx_t *c, const double *xyz)
             vol[q] = dX[0][0][q] * dX[1][1][q] - dX[1][0][q] * dX[0][1][q];
         }
     } else {
-        /* products P[l'][m] = (D_{l'} x_a) x_b with (a, b) = (m+1, m+2) mod 3 */
+        /* Thomas-Lombard conservative form, (a, b) = (m+1, m+2) mod 3:
+         * xi_hat[l][m] = D_{l2}((D_{l1} x_a) x_b) - D_{l1}((D_{l2} x_a) x_b).
+         * LAD-C6 (cyclic compact operator along periodic directions): x_b is
+         * split into its periodic part and its linear trend s[d][b] k_d across
+         * periodic directions d; the trend's terms are exactly
+         * (D_{l1} x_a) s[l2][b] - (D_{l2} x_a) s[l1][b], and they cancel in the
+         * metric identities as the periodic part's do. */
+        double slope[3][3];
+        for (int d = 0; d < 3; ++d)
+            for (int b = 0; b < 3; ++b) slope[d][b] = c6 && per[d] ? c->p.period[d][b] / (double)c->n[d] : 0.0;
+        double *Xp[3];
+        for (int b = 0; b < 3; ++b) {
+            Xp[b] = X[b];
+            if (!c6) continue;
+            Xp[b] = ealloc(&e);
+            for (int k = -e.ge[2]; k < e.n[2] + e.ge[2]; ++k)
+                for (int j = -e.ge[1]; j < e.n[1] + e.ge[1]; ++j)
+                    for (int i = -e.ge[0]; i < e.n[0] + e.ge[0]; ++i) {
+                        long q = eidx(&e, i, j, k);
+                        Xp[b][q] = ((X[b][q] - slope[0][b] * (double)i) - slope[1][b] * (double)j) - slope[2][b] * (double)k;
+                    }
+        }
         double *Pp[3][3];
         for (int lp = 0; lp < 3; ++lp)
             for (int m = 0; m < 3; ++m) {
                 int a = (m + 1) % 3, b = (m + 2) % 3;
                 Pp[lp][m] = ealloc(&e);
-                for (long q = 0; q < e.NE; ++q) Pp[lp][m][q] = dX[lp][a][q] * X[b][q];
+                for (long q = 0; q < e.NE; ++q) Pp[lp][m][q] = dX[lp][a][q] * Xp[b][q];
             }
         for (int l = 0; l < 3; ++l) {
             int l1 = (l + 1) % 3, l2 = (l + 2) % 3;
             for (int m = 0; m < 3; ++m) {
-                double *A = eop(&e, Pp[l1][m], l2, 0, six), *B = eop(&e, Pp[l2][m], l1, 0, six);
+                int a = (m + 1) % 3, b = (m + 2) % 3;
+                double *A = c6 ? eop_c6(&e, Pp[l1][m], l2, per[l2], 0) : MOP(Pp[l1][m], l2);
+                double *B = c6 ? eop_c6(&e, Pp[l2][m], l1, per[l1], 0) : MOP(Pp[l2][m], l1);
                 node[l][m] = ealloc(&e);
                 for (long q = 0; q < e.NE; ++q) node[l][m][q] = A[q] - B[q];
+                if (c6)
+                    for (long q = 0; q < e.NE; ++q)
+                        node[l][m][q] = (node[l][m][q] + dX[l1][a][q] * slope[l2][b]) - dX[l2][a][q] * slope[l1][b];
                 free(A); free(B);
             }
         }
+        if (c6) for (int b = 0; b < 3; ++b) free(Xp[b]);
         for (long q = 0; q < e.NE; ++q) {
             double a11 = dX[0][0][q], a12 = dX[1][0][q], a13 = dX[2][0][q];
             double a21 = dX[0][1][q], a22 = dX[1][1][q], a23 = dX[2][1][q];
@@ -1604,11 +1690,11 @@ static void metrics_curvilinear(ctx_t *c, const double *xyz)
         for (int m = 0; m < nd; ++m) { free(dX[l][m]); free(node[l][m]); free(ifc[l][m]); }
     for (int m = 0; m < nd; ++m) free(X[m]);
     free(vol);
+#undef MOP
 }
 
 void *orc_create(const orc_params *p, const double *xyz)
 {
-    if (p->curvilinear && xyz != NULL && p->scheme == ORC_LAD_C6) return NULL;
     ctx_t *c = (ctx_t *)calloc(1, sizeof(ctx_t));
     c->p = *p;
     c->nd = p->ndim;

@@ -58,7 +58,8 @@ typedef struct {
 } orc_params;
 
 /* Context: holds the metrics (computed from the coordinates for curvilinear
- * grids).  xyz: ndim planes of node coordinates, or NULL for Cartesian. */
+ * grids; LAD-C6 with its own compact operator).  xyz: ndim planes of node
+ * coordinates, or NULL for Cartesian. */
 void *orc_create(const orc_params *p, const double *xyz);
 void orc_destroy(void *ctx);
 

@@ -340,7 +340,7 @@ def test_conservation_curvilinear_periodic(orc):
     W = np.stack([1.0 + 0.3 * np.sin(2 * math.pi * x) * np.cos(2 * math.pi * y), 0.5 + 0 * x,
                   0.2 + 0.1 * np.cos(2 * math.pi * y), 1.0 + 0.2 * np.sin(2 * math.pi * (x + y))])
     prob = inputs.field_on_curvilinear(xyz, per, W)
-    for scheme in ("MEG6", "LAD_E4"):
+    for scheme in ("MEG6", "LAD_E4", "LAD_C6"):
         o = orc.Oracle(prob, scheme=scheme)
         J = o.metrics()[0][-1]
         U, _, _ = o.advance(prob["U"], nsteps=6)
@@ -355,11 +355,11 @@ def test_freestream_preservation(orc, nd):
     if nd == 2:
         xyz, per = inputs.wavy_grid_2d(24, 20, amp=0.1)
         W0 = (1.0, 2.0 * math.sqrt(1.4) * math.cos(0.3), 2.0 * math.sqrt(1.4) * math.sin(0.3), 1.0)
-        schemes = ["MEG6", "MIG4", "LAD_E4", "HYBRID"]
+        schemes = ["MEG6", "MIG4", "LAD_E4", "LAD_C6", "HYBRID"]
     else:
         xyz, per = inputs.wavy_grid_3d((12, 12, 12), amp=0.06)
         W0 = (1.0, 1.5, 0.7, -0.4, 1.0)
-        schemes = ["MEG6", "LAD_E4"]
+        schemes = ["MEG6", "LAD_E4", "LAD_C6"]
     prob = inputs.uniform_flow_curvilinear(xyz, per, W0)
     for scheme in schemes:
         for extra in ([{}] if scheme != "HYBRID" else [dict(hybrid_mode=1, hyb_rho=-1.0),
@@ -381,7 +381,7 @@ def test_metrics_exact_on_affine_grid(orc):
     per = [[A[0, 0] * nx, A[1, 0] * nx], [A[0, 1] * ny, A[1, 1] * ny]]
     W = np.ones((4, ny, nx))
     prob = inputs.field_on_curvilinear(xyz, per, W)
-    for scheme in ("MEG6", "LAD_E4"):
+    for scheme in ("MEG6", "LAD_E4", "LAD_C6"):
         node, ifc = orc.Oracle(prob, scheme=scheme).metrics()
         # x = A xi: xi_hat = adj(A) (the metric divided by J), J = 1/det A
         adj = np.array([[A[1, 1], -A[0, 1]], [-A[1, 0], A[0, 0]]])
