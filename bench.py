@@ -12,8 +12,9 @@ every timed step sees the same flow.  value = cells x schemes x steps / time.
 N > 1: every rank runs the same workload on its own GPU (independent
 replicas, no exchange); value sums over ranks with the max-over-ranks time.
 
---impl reference times the FP64 CPU oracle on a bounded sample of the same
-workload (one RK3 step of each scheme on the triple point at 448 x 192).
+--impl reference times the FP64 CPU oracle (all host cores) on a bounded
+sample of the same workload (one RK3 step of each scheme on the triple point
+at 448 x 192).
 """
 import argparse
 import json
@@ -333,7 +334,8 @@ def _hybrid_kw(prob, precision):
                 hyb_p=0.5 * float(st[:, 3].min()), hybrid_buffer=1, precision=precision)
 
 
-RAMP_SCHEMES = [("LAD_E4", dict(scheme="LAD_E4")), ("MEG6", dict(scheme="MEG6")), ("MIG4", dict(scheme="MIG4")),
+RAMP_SCHEMES = [("LAD_E4", dict(scheme="LAD_E4")), ("LAD_C6", dict(scheme="LAD_C6")), ("MEG6", dict(scheme="MEG6")),
+                ("MIG4", dict(scheme="MIG4")),
                 ("HYBRID_GLOBAL", dict(scheme="HYBRID", hybrid_mode=0, hyb_rho=0.3)),
                 ("HYBRID_CELL", dict(scheme="HYBRID", hybrid_mode=1, hybrid_sensor=1, hyb_rho=0.3))]
 
@@ -343,7 +345,8 @@ def run_ramp(api, torch, dev, args):
     device), Sutherland viscosity, isothermal wall, inflow boundary-layer
     profile with frozen fluctuations: ms per RK3 step (with the device CFL
     step) per scheme in FP64 and in the mixed form, over args.ramp_steps steps
-    after one warm-up step, events on the launching stream."""
+    after one warm-up step, events on the launching stream; the speed ratios
+    between schemes beside the paper's (Sec. 4, A100, FP64)."""
     from paper_2511_18042_gb300 import inputs
     prob = inputs.compression_ramp()
     cells = prob["n"][0] * prob["n"][1] * prob["n"][2]
@@ -371,8 +374,16 @@ def run_ramp(api, torch, dev, args):
                         "status": s.sync_status()}
             del s, U
             torch.cuda.empty_cache()
-    ratios = {"MIG4_over_" + k: out["MIG4"]["ms_per_rk3_step"] / out[k]["ms_per_rk3_step"]
-              for k in ("LAD_E4", "HYBRID_GLOBAL", "HYBRID_CELL")}
+    # speed ratios (time of the first scheme / time of the second), FP64, beside
+    # the paper's A100 OpenACC figures for its LES ramps (context, not targets)
+    paper = {"MEG6_over_LAD_C6": "1.17-1.22", "MIG4_over_LAD_C6": "1.38-1.43", "MEG6_over_LAD_E4": "1.9-2.0",
+             "MIG4_over_LAD_E4": "2.2-2.3", "MEG6_over_HYBRID_GLOBAL": "1.67", "MEG6_over_HYBRID_CELL": None}
+    ratios = {}
+    for k, ctx in paper.items():
+        a, b = k.split("_over_")
+        ratios[k] = {"fp64": out[a]["ms_per_rk3_step"] / out[b]["ms_per_rk3_step"],
+                     "mixed": out[a + "_MIXED"]["ms_per_rk3_step"] / out[b + "_MIXED"]["ms_per_rk3_step"],
+                     "paper_a100_fp64": ctx}
     return {"workload": "M2.9 24-degree compression ramp 768x192x128 (%d cells), curvilinear, viscous; "
                         "%d RK3 steps from the initial boundary layer after one warm-up step" % (cells, args.ramp_steps),
             "per_scheme": out, "speed_ratios": ratios}
@@ -436,6 +447,23 @@ def run_batched(api, torch, dev, args, count=256, steps_per_solve=200, ref_steps
         stream.synchronize()
         return e0.elapsed_time(e1)
 
+    def full_solves():
+        """every member from its initial state, steps_per_solve RK3 steps
+        (after an eager step, the capture and a replay on the current path);
+        returns (ms, non-physical member indices)"""
+        for _ in range(3):
+            batch.step(stream)
+        stream.synchronize()
+        for s_ in solvers:
+            s_.sync_status(stream)
+        for U_, p in zip(states, probs):
+            U_.copy_(torch.as_tensor(p["U"]))
+        stream.synchronize()
+        ms = timed(steps_per_solve)
+        batch.sync(stream)
+        bad_ = [i for i, s_ in enumerate(solvers) if s_.sync_status(stream) != 0]
+        return ms, bad_
+
     with torch.cuda.stream(stream):
         for _ in range(3):  # eager, capture, first replay
             batch.step(stream)
@@ -444,25 +472,30 @@ def run_batched(api, torch, dev, args, count=256, steps_per_solve=200, ref_steps
         t0 = time.perf_counter()
         width = batch.autotune(stream)
         tune_s = time.perf_counter() - t0
-        for _ in range(3):  # recapture after tuning
-            batch.step(stream)
-        stream.synchronize()
-        for s_ in solvers:
-            s_.sync_status(stream)
-        # the full solves: every member from its initial state, 200 RK3 steps
-        for U_, p in zip(states, probs):
-            U_.copy_(torch.as_tensor(p["U"]))
-        stream.synchronize()
-        total_ms = timed(steps_per_solve)
-    status = [s_.sync_status(stream) for s_ in solvers]
-    bad = [i for i, rc in enumerate(status) if rc != 0]
+        path, path_launches = batch.path()
+        total_ms, bad = full_solves()
+        mixed_final = [states[i].clone() for i in range(acc_members)]
+        # the other work-table path, timed the same way
+        paths = {path: {"launches_per_step": path_launches, "seconds_for_all_solves": total_ms * 1e-3,
+                        "solves_per_s": (count - len(bad)) / (total_ms * 1e-3), "nonphysical_members": len(bad)}}
+        groups = max(1, path_launches // 41) if path == "table" else 1
+        for alt in ("persistent", "table"):
+            if alt in paths or path == "streams":
+                continue
+            try:
+                batch.set_path(alt, groups)
+            except RuntimeError as ex:
+                paths[alt] = {"unavailable": str(ex)}
+                continue
+            ms_alt, bad_alt = full_solves()
+            paths[alt] = {"launches_per_step": batch.path()[1], "seconds_for_all_solves": ms_alt * 1e-3,
+                          "solves_per_s": (count - len(bad_alt)) / (ms_alt * 1e-3),
+                          "nonphysical_members": len(bad_alt)}
     good = count - len(bad)
     shapes = {}
     for s_ in solvers:
         key = "x".join(str(v) for v in s_.tile_shape())
         shapes[key] = shapes.get(key, 0) + 1
-    path, path_launches = batch.path()
-    mixed_final = [states[i].clone() for i in range(acc_members)]
     del batch, solvers, states
     torch.cuda.empty_cache()
     # per-case FP64: each grid advanced on its own, one after the other
@@ -509,9 +542,12 @@ def run_batched(api, torch, dev, args, count=256, steps_per_solve=200, ref_steps
             "autotune": {"path": path, "launches_per_step": path_launches,
                          "streams": width, "tile_shapes": shapes, "seconds": tune_s,
                          "ms_per_rk3_step_default": ms_default,
-                         "note": "path: 'table' = one launch per phase of an RK stage for every member "
-                                 "(41 per step and member group); 'streams' = per-member launches on "
-                                 "the stream pool; default = the work table, untuned"},
+                         "note": "path: 'persistent' = one cooperative launch per RK stage (3 per step) "
+                                 "running the stage's phases with grid barriers; 'table' = one launch per "
+                                 "phase of an RK stage for every member (41 per step and member group); "
+                                 "'streams' = per-member launches on the stream pool; default = the work "
+                                 "table, untuned"},
+            "paths": paths,
             "accuracy_vs_fp64": {"members": len(l1), "steps": steps_per_solve,
                                  "density_l1_rel_max": max(l1) if l1 else None},
             "per_case_fp64": {"ms_per_rk3_step": ref_ms,
@@ -620,24 +656,94 @@ def sweep_roofline(api, torch, grid, base, dev, args, peaks):
     return roof
 
 
+def _cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.machine()
+
+
+def _oracle_rate(oracle, prob, kw, steps, U0=None):
+    """cell-updates/s of the oracle advancing prob by `steps` CFL RK3 steps."""
+    o = oracle.Oracle(prob, **kw)
+    U = prob["U"] if U0 is None else U0
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        U = o.rk3_step(U, o.cfl_dt(U))
+    sec = time.perf_counter() - t0
+    cells = math.prod(int(v) for v in prob["n"][:prob["ndim"]])
+    return cells * steps / sec, sec
+
+
 def cpu_baseline(names, sample=(448, 192)):
-    """The oracle as it stands, single thread, one RK3 step of each scheme on a
-    448 x 192 triple point (same physics, 1/16 of the cells)."""
+    """The oracle as it stands (plain FP64 C, OpenMP over the outer grid
+    loops, results independent of the thread count), timed on this host on
+    bounded samples of the workloads: the headline's one RK3 step of each
+    scheme on a 448 x 192 triple point (1/16 of the cells) from 20 MEG6 steps
+    of development, single-threaded and on all cores, and the cases of the
+    benchmark's other configurations on all cores (Sod to t = 0.2, a 448 x 192
+    triple point 10 steps, 10 batched Riemann problems 10 steps, a 96 x 48 x 32
+    compression ramp 2 steps)."""
     import oracle
     from paper_2511_18042_gb300 import inputs
+    ncores = oracle.set_threads(0)
     prob = inputs.triple_point(*sample)
     kws = dict(SCHEMES)
-    pre = oracle.Oracle(prob, scheme="MEG6")
-    U0, _, _ = pre.advance(prob["U"], nsteps=20)
+    oracle.set_threads(ncores)
+    U0, _, _ = oracle.Oracle(prob, scheme="MEG6").advance(prob["U"], nsteps=20)
+    res = {}
+    for th in (1, ncores):
+        oracle.set_threads(th)
+        t0 = time.perf_counter()
+        for n in names:
+            o = oracle.Oracle(prob, **kws[n])
+            o.rk3_step(U0, o.cfl_dt(U0))
+        res[th] = (sample[0] * sample[1] * len(names) / (time.perf_counter() - t0), time.perf_counter() - t0)
+    oracle.set_threads(ncores)
+    cases = {}
+    sod = inputs.shock_tube("sod", 400)
+    for n, kw in (("MEG6", dict(scheme="MEG6", cfl=0.5)), ("LAD_C6", dict(scheme="LAD_C6", cfl=0.1))):
+        o = oracle.Oracle(sod, **kw)
+        t0 = time.perf_counter()
+        _, _, k = o.advance(sod["U"], t_end=0.2)
+        sec = time.perf_counter() - t0
+        cases["sod_400_to_t0.2_" + n] = {"cell_updates_per_s": 400 * k / sec, "steps": k, "seconds": sec}
+    for n in ("MEG6", "LAD_E4", "HYBRID_CELL"):
+        r, sec = _oracle_rate(oracle, prob, kws[n], 10, U0)
+        cases["triple_point_448x192_10_steps_" + n] = {"cell_updates_per_s": r, "seconds": sec}
+    br = inputs.batched_riemann(count=10, seed=0)
     t0 = time.perf_counter()
-    for n in names:
-        o = oracle.Oracle(prob, **kws[n])
-        o.rk3_step(U0, o.cfl_dt(U0))
+    cells = 0
+    for p in br:
+        o = oracle.Oracle(p, **_hybrid_kw(p, 0))
+        U = p["U"]
+        for _ in range(10):
+            U = o.rk3_step(U, o.cfl_dt(U))
+        cells += p["n"][0] * p["n"][1] * 10
     sec = time.perf_counter() - t0
-    cells = sample[0] * sample[1] * len(names)
-    return {"value": cells / sec, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
-            "sample": "one RK3 step of each of %d schemes on a %dx%d triple point (1/16 of the cells), "
-                      "from 20 MEG6 steps of development; %.1f s" % (len(names), sample[0], sample[1], sec)}
+    cases["batched_riemann_10x10_steps_hybrid"] = {"cell_updates_per_s": cells / sec, "seconds": sec}
+    ramp = inputs.compression_ramp(96, 48, 32)
+    for n in ("LAD_E4", "MEG6"):
+        r, sec = _oracle_rate(oracle, ramp, dict(scheme=n), 2)
+        cases["ramp_96x48x32_2_steps_" + n] = {"cell_updates_per_s": r, "seconds": sec}
+    return {"value": res[ncores][0], "unit": "cell-updates/s", "cores": ncores, "kind": "oracle",
+            "sample": "one RK3 step of each of %d schemes on a %dx%d triple point (1/16 of the cells), from 20 MEG6 "
+                      "steps of development, on %d threads (%.2f s)" % (len(names), sample[0], sample[1], ncores,
+                                                                      res[ncores][1]),
+            "single_core": {"value": res[1][0], "seconds": res[1][1]},
+            "cores_all": ncores, "cpu_model": _cpu_model(), "cases_all_cores": cases}
 
 
 def run_reference(args):
@@ -647,6 +753,7 @@ def run_reference(args):
     names = [n for n, _ in SCHEMES if args.schemes is None or n in args.schemes.split(",")]
     import oracle
     from paper_2511_18042_gb300 import inputs
+    ncores = oracle.set_threads(0)
     sample = (448, 192)
     prob = inputs.triple_point(*sample)
     kws = dict(SCHEMES)
@@ -667,14 +774,15 @@ def run_reference(args):
     sec = (time.perf_counter() - t0) / args.steps
     cells = sample[0] * sample[1] * len(names)
     value = cells / sec
-    desc = ("FP64 CPU oracle, single thread: one RK3 step of each of %d schemes on a %dx%d triple point "
-            "(bounded sample of the 1792x768 workload)" % (len(names), sample[0], sample[1]))
+    desc = ("FP64 CPU oracle (OpenMP, %d threads): one RK3 step of each of %d schemes on a %dx%d triple point "
+            "(bounded sample of the 1792x768 workload)" % (ncores, len(names), sample[0], sample[1]))
     line = {"impl": "reference", "metric": METRIC,
             "value": value, "unit": "cell-updates/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
             "config": dict(bench_config(names, ws), sample="%dx%d triple point from its initial state" % sample),
-            "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": 1, "kind": "oracle", "sample": desc},
+            "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": ncores, "kind": "oracle",
+                             "sample": desc, "cpu_model": _cpu_model()},
             "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

@@ -235,6 +235,30 @@ CG_API int cg_batch_autotune(cg_batch *b, void *stream, int *width_out);
  * step (41 per group), or -1 for the stream pool (each member counts its own).  Before the
  * first cg_batch_step the table is not built yet and the path reads 0. */
 CG_API int cg_batch_path(const cg_batch *b, int *path_out, int *launches_out);
+/* Persistent path (*path_out = 2, *launches_out = 3): a work-table batch in one
+ * member group advances each RK stage in ONE cooperative launch (all blocks
+ * co-resident, as many as the occupancy allows on every SM): the stage's
+ * phases run one after another over their blocks with a grid barrier between
+ * them.  Every barrier wait is bounded (about a second); a wait that runs out
+ * ends the launch early with an error flag that cg_batch_sync reports.  The
+ * work table's members compute what they compute alone (bitwise in FP64).
+ * cg_batch_set_path chooses the path: 0 the stream pool, 1 the work table in
+ * `groups` member groups, 2 the persistent stages; CG_ERR_UNSUPPORTED where
+ * the batch does not qualify (the table needs 2D Cartesian inviscid
+ * per-interface hybrids of one precision; the persistent stage a tile shape
+ * of 4 or 8 lines in both directions).  The next cg_batch_step runs eagerly
+ * and the one after recaptures.  cg_batch_autotune times the persistent
+ * stages too and keeps the fastest path. */
+CG_API int cg_batch_set_path(cg_batch *b, int path, int groups);
+/* Synchronises the stream; CG_ERR_TIMEOUT (once, then cleared) if a
+ * persistent stage's barrier gave up waiting since the last call. */
+CG_API int cg_batch_sync(cg_batch *b, void *stream);
+/* Test hook of the bounded barrier wait: from the next cg_batch_step on, every
+ * barrier of the persistent stages waits for `extra` more arrivals than the
+ * launch has blocks (0 restores the normal count), so each wait runs out after
+ * about a second, sets the error flag and ends the launch; the members' states
+ * are then incomplete.  CG_ERR_UNSUPPORTED off the persistent path. */
+CG_API int cg_batch_debug_barrier(cg_batch *b, int extra);
 CG_API void cg_batch_destroy(cg_batch *b);
 
 /* Autotuner of the C-GBR sweep (MEG6, MIG4, hybrid; a no-op for LAD): for

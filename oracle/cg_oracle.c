@@ -116,16 +116,25 @@ static box_t box_grow(const ctx_t *c, int grow)
  * value is computed by the same arithmetic whatever the thread count, and no
  * floating-point sum runs across iterations, so results do not depend on it. */
 #ifdef _OPENMP
-#define FOR_BOX_PAR(b, i, j, k)                      \
-    _Pragma("omp parallel for collapse(3) schedule(static)") \
+#define ORC_PRAGMA(x) _Pragma(#x)
+/* loops of fewer than 512 iterations (nodes, or lines of a line loop) run
+ * on the calling thread: a parallel region would cost more than the loop */
+#define FOR_BOX_PAR(b, i, j, k)                                                          \
+    ORC_PRAGMA(omp parallel for collapse(3) schedule(static)                             \
+               if ((long)((b).hi[0] - (b).lo[0]) * ((b).hi[1] - (b).lo[1]) *             \
+                   ((b).hi[2] - (b).lo[2]) >= 512L))                                      \
     FOR_BOX(b, i, j, k)
+/* an element-wise loop over n values, shared the same way */
+#define ORC_PAR_FOR(n) ORC_PRAGMA(omp parallel for schedule(static) if ((long)(n) >= 65536L))
 #else
 #define FOR_BOX_PAR(b, i, j, k) FOR_BOX(b, i, j, k)
+#define ORC_PAR_FOR(n)
 #endif
 
 static double *padded(const ctx_t *c, int nc)
 {
     double *f = (double *)malloc(sizeof(double) * (size_t)c->NP * nc);
+    ORC_PAR_FOR(c->NP * nc)
     for (long q = 0; q < c->NP * nc; ++q) f[q] = NAN;
     return f;
 }
@@ -1348,10 +1357,13 @@ int orc_rk3_step(void *ctx, double *U, double dt)
     double *Us = (double *)malloc(sizeof(double) * M);
     memcpy(Un, U, sizeof(double) * M);
     rhs_internal(c, Un, R);
+    ORC_PAR_FOR(M)
     for (long q = 0; q < M; ++q) Us[q] = Un[q] + dt * R[q];
     rhs_internal(c, Us, R);
+    ORC_PAR_FOR(M)
     for (long q = 0; q < M; ++q) Us[q] = 0.75 * Un[q] + 0.25 * (Us[q] + dt * R[q]);
     rhs_internal(c, Us, R);
+    ORC_PAR_FOR(M)
     for (long q = 0; q < M; ++q) U[q] = (1.0 / 3.0) * Un[q] + (2.0 / 3.0) * (Us[q] + dt * R[q]);
     if (c->p.scheme == ORC_LAD_C6 && c->p.filter_on) filter_state(c, U);
     free(Un); free(R); free(Us);
@@ -1530,7 +1542,7 @@ static double *eop_c6(const ebox_t *e, const double *f, int d, int periodic, int
                     compact_line(3, n, 0, 0, n - 1, f + q0, s, o + q0);
                     continue;
                 }
-                double T = detrend ? f[q0 + (long)n * s] - f[q0] : 0.0;
+                double T = detrend ? f[q0 + (long)n * s] - f[q0] : (double)0.0;
                 for (int t = -2; t <= n + 1; ++t) gl[t + 2] = f[q0 + t * s] - T * (double)t / (double)n;
                 compact_line(3, n, 1, 0, n - 1, gl + 2, 1, og + 2);
                 for (int t = 0; t < n; ++t) o[q0 + t * s] = og[t + 2] + T / (double)n;
@@ -1628,7 +1640,7 @@ static void metrics_curvilinear(ctx_t *c, const double *xyz)
          * metric identities as the periodic part's do. */
         double slope[3][3];
         for (int d = 0; d < 3; ++d)
-            for (int b = 0; b < 3; ++b) slope[d][b] = c6 && per[d] ? c->p.period[d][b] / (double)c->n[d] : 0.0;
+            for (int b = 0; b < 3; ++b) slope[d][b] = c6 && per[d] ? c->p.period[d][b] / (double)c->n[d] : (double)0.0;
         double *Xp[3];
         for (int b = 0; b < 3; ++b) {
             Xp[b] = X[b];

@@ -81,6 +81,9 @@ _SIGS = {
     "cg_batch_destroy": (None, [ctypes.c_void_p]),
     "cg_batch_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
     "cg_batch_path": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "cg_batch_set_path": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    "cg_batch_sync": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "cg_batch_debug_barrier": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "cg_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "cg_tile_shape": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
     "cg_set_tile_shape": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),

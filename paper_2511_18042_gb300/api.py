@@ -263,11 +263,20 @@ class Batch:
         return w.value
 
     def path(self):
-        """("table", launches per step) on the work-table path, ("streams", None)
-        on the stream pool."""
+        """("persistent", 3) on the persistent stages, ("table", launches per
+        step) on the work-table path, ("streams", None) on the stream pool."""
         p, n = ctypes.c_int(), ctypes.c_int()
         nat.check(nat.lib().cg_batch_path(self._h, ctypes.byref(p), ctypes.byref(n)))
-        return ("table", n.value) if p.value == 1 else ("streams", None)
+        return {2: ("persistent", n.value), 1: ("table", n.value)}.get(p.value, ("streams", None))
+
+    def set_path(self, path, groups=1):
+        """path: "streams", "table" (in `groups` member groups) or "persistent"."""
+        code = {"streams": 0, "table": 1, "persistent": 2}[path]
+        nat.check(nat.lib().cg_batch_set_path(self._h, code, int(groups)))
+
+    def sync(self, stream=None):
+        """Synchronise; raises if a persistent stage's barrier wait ran out."""
+        nat.check(nat.lib().cg_batch_sync(self._h, _stream(stream)))
 
     def __del__(self):
         if getattr(self, "_h", None) and self._h.value:

@@ -473,13 +473,32 @@ static int compute_metrics(cg_solver* s, cudaStream_t st) {
     eb.NE *= eb.PE[d];
   }
   int six = (s->p.scheme == CG_MEG6 || s->p.scheme == CG_MIG4) ? 1 : 0;
+  const bool c6 = s->p.scheme == CG_LAD_C6;
   std::vector<double*> tmp;
+  size_t tmp_bytes = 0;
   auto alloc = [&](double** p) -> int {
     int rc = dalloc(p, (size_t)eb.NE);
-    if (!rc) tmp.push_back(*p);
+    if (!rc) { tmp.push_back(*p); tmp_bytes += (size_t)eb.NE * sizeof(double); }
     return rc;
   };
   int threads = 256, blocks = grid_blocks(eb.NE, threads);
+  int per[3] = {0, 0, 0};
+  for (int d = 0; d < nd; ++d) per[d] = g->bc[d][0] == CG_BC_PERIODIC;
+  // LAD-C6: line scratch of the compact metric operator (4 (n + 4) doubles a line)
+  double* c6scr = nullptr;
+  if (c6) {
+    size_t mx = 0;
+    for (int d = 0; d < nd; ++d) mx = std::max(mx, (size_t)(eb.NE / eb.PE[d]) * 4 * (size_t)(eb.n[d] + 4));
+    if (dalloc(&c6scr, mx)) return CG_ERR_OOM;
+    tmp.push_back(c6scr);
+    tmp_bytes += mx * sizeof(double);
+  }
+  // derivative of f along d with the scheme's metric operator into o
+  auto mop = [&](const double* f, int d, int detrend, double* o) {
+    km_op<<<blocks, threads, 0, st>>>(eb, f, d, 0, c6 ? 0 : six, o);
+    if (c6)
+      km_c6<<<grid_blocks(eb.NE / eb.PE[d], 128), 128, 0, st>>>(eb, f, d, per[d], detrend, o, c6scr);
+  };
   double* X[3] = {nullptr, nullptr, nullptr};
   for (int m = 0; m < nd; ++m) {
     if (alloc(&X[m])) return CG_ERR_OOM;
@@ -493,7 +512,7 @@ static int compute_metrics(cg_solver* s, cudaStream_t st) {
   for (int l = 0; l < nd; ++l)
     for (int m = 0; m < nd; ++m) {
       if (alloc(&dX[l][m])) return CG_ERR_OOM;
-      km_op<<<blocks, threads, 0, st>>>(eb, X[m], l, 0, six, dX[l][m]);
+      mop(X[m], l, 1, dX[l][m]);
     }
   double* node[3][3] = {};
   double* vol;
@@ -511,20 +530,37 @@ static int compute_metrics(cg_solver* s, cudaStream_t st) {
     km_lin<<<blocks, threads, 0, st>>>(eb, dX[0][1], nullptr, 2, node[1][0]);
     km_lin<<<blocks, threads, 0, st>>>(eb, dX[0][0], nullptr, 0, node[1][1]);
   } else {
+    // Thomas-Lombard form; LAD-C6 (cyclic compact operator) splits the
+    // undifferentiated coordinate into its periodic part and linear trend,
+    // whose terms (D_{l1} x_a) s[l2][b] - (D_{l2} x_a) s[l1][b] are added exactly
+    double slope[3][3] = {};
+    double* Xp[3] = {X[0], X[1], X[2]};
+    if (c6) {
+      for (int d = 0; d < 3; ++d)
+        for (int b = 0; b < 3; ++b) slope[d][b] = per[d] ? g->period[d][b] / (double)g->n[d] : 0.0;
+      for (int b = 0; b < 3; ++b) {
+        if (alloc(&Xp[b])) return CG_ERR_OOM;
+        km_detrend<<<blocks, threads, 0, st>>>(eb, X[b], slope[0][b], slope[1][b], slope[2][b], Xp[b]);
+      }
+    }
     double* P[3][3];
     for (int lp = 0; lp < 3; ++lp)
       for (int m = 0; m < 3; ++m) {
         if (alloc(&P[lp][m])) return CG_ERR_OOM;
-        km_lin<<<blocks, threads, 0, st>>>(eb, dX[lp][(m + 1) % 3], X[(m + 2) % 3], 1, P[lp][m]);
+        km_lin<<<blocks, threads, 0, st>>>(eb, dX[lp][(m + 1) % 3], Xp[(m + 2) % 3], 1, P[lp][m]);
       }
     double *A, *B;
     if (alloc(&A) || alloc(&B)) return CG_ERR_OOM;
     for (int l = 0; l < 3; ++l) {
       int l1 = (l + 1) % 3, l2 = (l + 2) % 3;
       for (int m = 0; m < 3; ++m) {
-        km_op<<<blocks, threads, 0, st>>>(eb, P[l1][m], l2, 0, six, A);
-        km_op<<<blocks, threads, 0, st>>>(eb, P[l2][m], l1, 0, six, B);
+        mop(P[l1][m], l2, 0, A);
+        mop(P[l2][m], l1, 0, B);
         km_lin<<<blocks, threads, 0, st>>>(eb, A, B, 3, node[l][m]);
+        if (c6) {
+          int a = (m + 1) % 3, b = (m + 2) % 3;
+          km_trend<<<blocks, threads, 0, st>>>(eb, dX[l1][a], slope[l2][b], dX[l2][a], slope[l1][b], node[l][m]);
+        }
       }
     }
   }
@@ -552,6 +588,7 @@ static int compute_metrics(cg_solver* s, cudaStream_t st) {
   CG_CUDA(cudaGetLastError());
   CG_CUDA(cudaStreamSynchronize(st));
   for (double* p : tmp) cudaFree(p);
+  t_dalloc_bytes -= tmp_bytes;  // set-up buffers: not held by the solver
   s->dg.xh = xh;
   s->dg.xt = xt;
   s->dg.jac = jac;
@@ -1123,8 +1160,6 @@ static int check_params(const cg_grid* g, const cg_params* p) {
   if (!(p->minf > 0.0)) return fail(CG_ERR_INVALID_ARG, "minf > 0 required");
   if (p->omega_window < 1 || p->omega_window > 4) return fail(CG_ERR_INVALID_ARG, "omega_window must be 1..4");
   if (p->hybrid_buffer < 0 || p->hybrid_buffer > 2) return fail(CG_ERR_INVALID_ARG, "hybrid_buffer must be 0..2");
-  if (g->curv && p->scheme == CG_LAD_C6)
-    return fail(CG_ERR_UNSUPPORTED, "LAD-C6 on curvilinear grids is not supported (the metric identities need the compact operator)");
   if (p->viscous && (!(p->re > 0.0) || !(p->pr > 0.0) || !(p->suth >= 0.0)))
     return fail(CG_ERR_INVALID_ARG, "viscous: re > 0, pr > 0 and suth >= 0 required");
   for (int d = 0; d < g->nd; ++d)

@@ -87,8 +87,12 @@ struct BatchTable {
   int lw[2] = {0, 0};
   int nm = 0;
   void* dmem = nullptr;
+  void* xmem = nullptr;      // per-member buffers of the table (second Gaussian pass, second node fluxes)
+  unsigned* bar = nullptr;   // persistent stage: barrier words [2], then the error flag
+  int blocks = 0;            // persistent stage: co-resident blocks (0: not available)
   TKind zero1, zero23, cfl, fin, prim[3], omega, field, troubled, grad, coef, gauss[2], nodeflux[2], hflux[2];
   TKind sweep[3][2];
+  PersistentStage pst[3];
 };
 
 static bool table_member_ok(const cg_solver* s, const cg_solver* s0, bool same_tiles = true) {
@@ -168,6 +172,21 @@ static int table_build_t(BatchTable& tb, cg_solver* const* sv, double* const* st
   std::vector<JobGauss<T>> ga[2] = {std::vector<JobGauss<T>>(nm), std::vector<JobGauss<T>>(nm)};
   std::vector<JobNodeflux<T>> nf[2] = {std::vector<JobNodeflux<T>>(nm), std::vector<JobNodeflux<T>>(nm)};
   std::vector<JobHflux<T>> hf[2] = {std::vector<JobHflux<T>>(nm), std::vector<JobHflux<T>>(nm)};
+  // buffers of the table's own: the Gaussian's second pass writes bt2/kp2
+  // (not the coefficient planes its first pass read) and the y node fluxes go
+  // to Fn1 (not the x node fluxes' buffer), so that within a stage no buffer is
+  // written after a phase read it (what a persistent stage needs); the
+  // arithmetic is the members' own
+  std::vector<size_t> xoff(nm + 1, 0);
+  for (int m = 0; m < nm; ++m) {
+    const cg_solver* s = sv[m];
+    size_t b = (2 * (size_t)s->N + (size_t)s->nv * s->lad.fbox[1].size()) * sizeof(T);
+    xoff[m + 1] = xoff[m] + (b + 255) / 256 * 256;
+  }
+  {
+    int rc = dalloc((char**)&tb.xmem, xoff[nm]);
+    if (rc) return rc;
+  }
   for (int m = 0; m < nm; ++m) {
     cg_solver* s = sv[m];
     LadBuffers& L = s->lad;
@@ -175,8 +194,10 @@ static int table_build_t(BatchTable& tb, cg_solver* const* sv, double* const* st
     T* fb = reinterpret_cast<T*>(L.fb);
     T* g = reinterpret_cast<T*>(L.gr);
     T* dv = reinterpret_cast<T*>(L.dv);
-    T* bt[2] = {reinterpret_cast<T*>(L.bt[0]), reinterpret_cast<T*>(L.bt[1])};
-    T* kp[2] = {reinterpret_cast<T*>(L.kp[0]), reinterpret_cast<T*>(L.kp[1])};
+    T* xm = reinterpret_cast<T*>(static_cast<char*>(tb.xmem) + xoff[m]);
+    T* bt[3] = {reinterpret_cast<T*>(L.bt[0]), reinterpret_cast<T*>(L.bt[1]), xm};
+    T* kp[3] = {reinterpret_cast<T*>(L.kp[0]), reinterpret_cast<T*>(L.kp[1]), xm + s->N};
+    T* Fn[2] = {reinterpret_cast<T*>(L.Fn), xm + 2 * s->N};
     JobOmega<T> o;
     o.g = s->dg;
     o.W = W;
@@ -204,14 +225,13 @@ static int table_build_t(BatchTable& tb, cg_solver* const* sv, double* const* st
     gr[m] = j;
     co[m] = JobCoef<T>{s->dg, W, fb, L.fbx, g, dv, L.b3, s->p.c_beta, s->p.c_kappa, bt[0], kp[0],
                        (unsigned)table_blocks(s->N)};
-    // the overbar along x then y: bt/kp 0 -> 1 -> 0
+    // the overbar along x then y: bt/kp 0 -> 1 -> 2
     ga[0][m] = JobGauss<T>{s->dg, 0, bt[0], kp[0], bt[1], kp[1], (unsigned)table_blocks(s->N)};
-    ga[1][m] = JobGauss<T>{s->dg, 1, bt[1], kp[1], bt[0], kp[0], (unsigned)table_blocks(s->N)};
+    ga[1][m] = JobGauss<T>{s->dg, 1, bt[1], kp[1], bt[2], kp[2], (unsigned)table_blocks(s->N)};
     for (int l = 0; l < 2; ++l) {
-      nf[l][m] = JobNodeflux<T>{s->dg, l, W, bt[0], kp[0], g, dv, L.b3, reinterpret_cast<T*>(L.Fn), L.fbox[l],
+      nf[l][m] = JobNodeflux<T>{s->dg, l, W, bt[2], kp[2], g, dv, L.b3, Fn[l], L.fbox[l],
                                 (unsigned)table_blocks(L.fbox[l].size())};
-      hf[l][m] = JobHflux<T>{s->dg, l, reinterpret_cast<const T*>(L.Fn), L.fbox[l],
-                             reinterpret_cast<T*>(s->hflux[l]), L.hbox[l],
+      hf[l][m] = JobHflux<T>{s->dg, l, Fn[l], L.fbox[l], reinterpret_cast<T*>(s->hflux[l]), L.hbox[l],
                              (unsigned)table_blocks(L.hbox[l].size())};
     }
   }
@@ -266,12 +286,52 @@ static int table_build_t(BatchTable& tb, cg_solver* const* sv, double* const* st
     r.k->total = r.total;
   }
   tb.dmem = dm;
+  // the three persistent stages: the same phases as the table's launches
+  if ((rc = dalloc(&tb.bar, 4))) return rc;
+  CG_CUDA(cudaMemset(tb.bar, 0, 4 * sizeof(unsigned)));
+  tb.blocks = tb.mixed ? persistent_blocks_f32_2(tb.lw[0], tb.lw[1]) : persistent_blocks_f64_2(tb.lw[0], tb.lw[1]);
+  auto ref = [](const TKind& k) { return PhaseRef{k.jobs, k.off, k.mem, k.total}; };
+  for (int k = 0; k < 3; ++k) {
+    PersistentStage& P = tb.pst[k];
+    P.zero = ref(k == 0 ? tb.zero1 : tb.zero23);
+    P.cfl = ref(tb.cfl);
+    P.fin = ref(tb.fin);
+    P.prim = ref(tb.prim[k]);
+    P.omega = ref(tb.omega);
+    P.field = ref(tb.field);
+    P.troubled = ref(tb.troubled);
+    P.grad = ref(tb.grad);
+    P.coef = ref(tb.coef);
+    for (int l = 0; l < 2; ++l) {
+      P.gauss[l] = ref(tb.gauss[l]);
+      P.nodeflux[l] = ref(tb.nodeflux[l]);
+      P.hflux[l] = ref(tb.hflux[l]);
+      P.sweep[l] = ref(tb.sweep[k][l]);
+    }
+    P.with_cfl = k == 0;
+    P.bar = tb.bar;
+    P.err = reinterpret_cast<int*>(tb.bar + 2);
+    P.expect = (unsigned)tb.blocks;
+  }
   return CG_OK;
 }
 
 static void table_free(BatchTable& tb) {
   if (tb.dmem) cudaFree(tb.dmem);
+  if (tb.xmem) cudaFree(tb.xmem);
+  if (tb.bar) cudaFree(tb.bar);
   tb = BatchTable();
+}
+
+// One RK3 step of every member in three cooperative launches (one per stage).
+static int table_step_persistent(const BatchTable& tb, cudaStream_t st) {
+  if (tb.blocks < 1) return fail(CG_ERR_UNSUPPORTED, "no persistent stage for this tile shape");
+  for (int k = 0; k < 3; ++k) {
+    int e = tb.mixed ? launch_persistent_f32_2(tb.lw[0], tb.lw[1], tb.pst[k], tb.blocks, st)
+                     : launch_persistent_f64_2(tb.lw[0], tb.lw[1], tb.pst[k], tb.blocks, st);
+    if (e) return fail(CG_ERR_CUDA, "persistent stage %d: %s", k + 1, cudaGetErrorString((cudaError_t)e));
+  }
+  return CG_OK;
 }
 
 // Builds the table if the batch qualifies (state 1), else marks it (-1).
@@ -359,6 +419,7 @@ static int table_launches(const BatchTable&) { return 3 * 13 + 2; }
 // stencils) overlap on the device.
 struct TableSet {
   int state = 0;  // 0: not built, 1: built, -1: the batch does not qualify
+  int persistent = 0;  // one group stepped by the persistent stages
   std::vector<BatchTable> t;
 };
 
@@ -366,6 +427,7 @@ static void tables_free(TableSet& ts) {
   for (auto& t : ts.t) table_free(t);
   ts.t.clear();
   ts.state = 0;
+  ts.persistent = 0;
 }
 
 static int tables_build(TableSet& ts, const std::vector<cg_solver*>& sv, const std::vector<double*>& states,
@@ -403,6 +465,7 @@ static int tables_build(TableSet& ts, const std::vector<cg_solver*>& sv, const s
 
 static int tables_step(const TableSet& ts, cudaStream_t st) {
   const int ng = (int)ts.t.size();
+  if (ng == 1 && ts.persistent) return table_step_persistent(ts.t[0], st);
   if (ng == 1) return table_step(ts.t[0], st);
   int rc = pool_ready();
   if (rc) return rc;
@@ -428,7 +491,18 @@ struct cg_batch {
   TableSet tables;           // work-table path (qualifying batches)
   int groups = 1;            // member groups of the work table, run concurrently
   int use_table = 1;         // 0: the stream pool even where the table qualifies
+  int persistent = 0;        // work table stepped by one persistent launch per stage
 };
+
+// the table set of the batch's current choice (built on first use)
+static int batch_tables(cg_batch* b) {
+  if (b->tables.state == 0) {
+    int rc = tables_build(b->tables, b->solvers, b->states, b->persistent ? 1 : b->groups);
+    if (rc) return rc;
+  }
+  if (b->tables.state == 1) b->tables.persistent = b->persistent && b->tables.t.size() == 1 && b->tables.t[0].blocks > 0;
+  return CG_OK;
+}
 
 extern "C" {
 
@@ -469,11 +543,9 @@ CG_API int cg_batch_step(cg_batch* b, void* stream) {
   if (!b->warm) {
     // first step runs eagerly: the work table, one-time kernel attributes and
     // the stream pool are set up here
-    if (b->tables.state == 0) {
-      int rc = tables_build(b->tables, b->solvers, b->states, b->groups);
-      if (rc) return rc;
-    }
-    int rc = batch_once(b, st);
+    int rc = batch_tables(b);
+    if (rc) return rc;
+    rc = batch_once(b, st);
     if (rc) return rc;
     b->warm = 1;
     return CG_OK;
@@ -485,6 +557,17 @@ CG_API int cg_batch_step(cg_batch* b, void* stream) {
     int rc = batch_once(b, st);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(st, &g);
+    if ((rc || e != cudaSuccess) && b->tables.persistent) {
+      // a cooperative launch this stream cannot capture: step by the table's launches
+      if (g) cudaGraphDestroy(g);
+      g = nullptr;
+      cudaGetLastError();
+      b->persistent = 0;
+      b->tables.persistent = 0;
+      CG_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+      rc = batch_once(b, st);
+      e = cudaStreamEndCapture(st, &g);
+    }
     if (rc) {
       if (g) cudaGraphDestroy(g);
       return rc;
@@ -623,18 +706,46 @@ CG_API int cg_batch_autotune(cg_batch* b, void* stream, int* width_out) {
     const int lx = tbest[0], ly = tbest[1];
     for (int ng : {2, 4, 8})
       if (rc == CG_OK && lx && ng <= count) rc = try_table(lx, ly, ng);
+    // one persistent launch per stage (one group, the chosen tile shape)
+    int pbest = 0;
+    if (rc == CG_OK && lx) {
+      for (cg_solver* s : b->solvers) {
+        s->sweep_lw[0] = lx;
+        s->sweep_lw[1] = ly;
+      }
+      rc = tables_build(b->tables, b->solvers, b->states, 1);
+      if (rc == CG_OK && b->tables.state == 1 && b->tables.t[0].blocks > 0) {
+        b->tables.persistent = 1;
+        float ms = 0.f;
+        int r = time_steps([&]() { return tables_step(b->tables, st); }, &ms);
+        if (r == CG_OK) {
+          if (ms < tbest_ms) {
+            tbest_ms = ms;
+            tbest[2] = 1;
+            pbest = 1;
+          }
+          rc = copy_states(false);
+        } else {
+          cudaGetLastError();  // a persistent stage that cannot be captured or launched: not a candidate
+          rc = copy_states(false);
+        }
+      }
+    }
     if (rc == CG_OK && tbest[0] && tbest_ms < best_ms) {
       for (cg_solver* s : b->solvers) {
         s->sweep_lw[0] = tbest[0];
         s->sweep_lw[1] = tbest[1];
       }
       b->groups = tbest[2];
+      b->persistent = pbest;
       rc = tables_build(b->tables, b->solvers, b->states, b->groups);
+      if (rc == CG_OK) rc = batch_tables(b);
       b->use_table = 1;
     } else {
       for (int i = 0; i < count; ++i)
         for (int d = 0; d < 3; ++d) b->solvers[i]->sweep_lw[d] = keep[i][d];
       tables_free(b->tables);
+      b->persistent = 0;
     }
   }
   if (e0) cudaEventDestroy(e0);
@@ -664,11 +775,58 @@ CG_API void cg_batch_destroy(cg_batch* b) {
 CG_API int cg_batch_path(const cg_batch* b, int* path_out, int* launches_out) {
   if (!b || !path_out) return fail(CG_ERR_INVALID_ARG, "null argument");
   const bool table = b->use_table && b->tables.state == 1;
-  *path_out = table ? 1 : 0;
+  const bool pers = table && b->tables.persistent;
+  *path_out = pers ? 2 : (table ? 1 : 0);
   int n = 0;
   if (table)
     for (const BatchTable& t : b->tables.t) n += table_launches(t);
-  if (launches_out) *launches_out = table ? n : -1;  // -1: per member, counted by the members
+  if (launches_out) *launches_out = pers ? 3 : (table ? n : -1);  // -1: per member, counted by the members
+  return CG_OK;
+}
+
+CG_API int cg_batch_set_path(cg_batch* b, int path, int groups) {
+  if (!b || path < 0 || path > 2 || groups < 1) return fail(CG_ERR_INVALID_ARG, "bad arguments");
+  tables_free(b->tables);
+  b->use_table = path > 0;
+  b->persistent = path == 2;
+  b->groups = path == 1 ? groups : 1;
+  if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+  if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+  b->warm = 0;
+  if (path > 0) {
+    int rc = batch_tables(b);
+    if (rc) return rc;
+    if (b->tables.state != 1) return fail(CG_ERR_UNSUPPORTED, "the batch does not qualify for the work table");
+    if (path == 2 && !b->tables.persistent)
+      return fail(CG_ERR_UNSUPPORTED, "no persistent stage for this batch's tile shape");
+  }
+  return CG_OK;
+}
+
+CG_API int cg_batch_debug_barrier(cg_batch* b, int extra) {
+  if (!b || extra < 0) return fail(CG_ERR_INVALID_ARG, "bad arguments");
+  if (!(b->tables.state == 1 && b->tables.persistent)) return fail(CG_ERR_UNSUPPORTED, "not on the persistent path");
+  for (BatchTable& t : b->tables.t)
+    for (int k = 0; k < 3; ++k) t.pst[k].expect = (unsigned)(t.blocks + extra);
+  if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+  if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+  b->warm = 0;
+  return CG_OK;
+}
+
+CG_API int cg_batch_sync(cg_batch* b, void* stream) {
+  if (!b) return fail(CG_ERR_INVALID_ARG, "null batch");
+  cudaStream_t st = (cudaStream_t)stream;
+  CG_CUDA(cudaStreamSynchronize(st));
+  for (BatchTable& t : b->tables.t) {
+    if (!t.bar) continue;
+    unsigned w[4];
+    CG_CUDA(cudaMemcpy(w, t.bar, sizeof w, cudaMemcpyDeviceToHost));
+    if (w[2]) {
+      CG_CUDA(cudaMemset(t.bar, 0, sizeof w));
+      return fail(CG_ERR_TIMEOUT, "a persistent stage's grid barrier gave up waiting");
+    }
+  }
   return CG_OK;
 }
 

@@ -69,7 +69,12 @@ struct JobFinish {
   double cfl;
   double* dt;
   __device__ void run(unsigned b) const {
-    if (threadIdx.x == 0) k_cfl_finish_body(vblock_1d(b, 1u), mx, cfl, dt, nullptr, 0.0);
+    if (threadIdx.x == 0) {
+      // the maximum read at L2 (an atomic): the same value, and no stale
+      // line in a persistent launch that zeroed and raised it
+      const unsigned long long v = atomicAdd(const_cast<unsigned long long*>(mx), 0ull);
+      k_cfl_finish_body(vblock_1d(b, 1u), &v, cfl, dt, nullptr, 0.0);
+    }
   }
 };
 

@@ -388,6 +388,20 @@ __global__ void k_rhs_c6(const T* __restrict__ f, Box fb, int nc, LineBuf lb, T*
   }
 }
 
+// The filtered quantity at a (possibly ghost) node: the conserved state, or,
+// on a curvilinear grid, the transformed conserved state Q/J that the
+// discrete conservation law advances (J from the padded metric planes).
+template <int ND>
+__device__ __forceinline__ void load_filtered(const DevGrid& g, const double* __restrict__ U, const int* c,
+                                              double* w) {
+  load_state<ND, true>(g, U, c[0], c[1], c[2], w);
+  if (g.curv) {
+    const double J = g.jac[plin(g, c[0], c[1], c[2])];
+#pragma unroll
+    for (int v = 0; v < ND + 2; ++v) w[v] = w[v] / J;
+  }
+}
+
 // Implicit-filter right-hand sides of the conserved state along lb.d:
 // non-periodic rows 0 and m-1 hold the ghost values at -1 and n; rows 1..n
 // hold sum_{m=0}^{4} (a_m/2)(f_{i+m} + f_{i-m}) of positions 0..n-1.
@@ -406,7 +420,7 @@ __global__ void k_rhs_filter(DevGrid g, const double* __restrict__ U, LineBuf lb
     int cc[3] = {c[0], c[1], c[2]};
     if (closure) {
       cc[lb.d] = pos;
-      load_state<ND, true>(g, U, cc[0], cc[1], cc[2], w[4]);
+      load_filtered<ND>(g, U, cc, w[4]);
 #pragma unroll
       for (int v = 0; v < NV; ++v) r[((long long)v * lb.m + i) * lb.nl + L] = w[4][v];
       continue;
@@ -414,7 +428,7 @@ __global__ void k_rhs_filter(DevGrid g, const double* __restrict__ U, LineBuf lb
 #pragma unroll
     for (int t = -4; t <= 4; ++t) {
       cc[lb.d] = pos + t;
-      load_state<ND, true>(g, U, cc[0], cc[1], cc[2], w[t + 4]);
+      load_filtered<ND>(g, U, cc, w[t + 4]);
     }
 #pragma unroll
     for (int v = 0; v < NV; ++v)
@@ -488,7 +502,7 @@ struct XTileFilter {
   double b0, b1, b2, b3, b4;
   int nc;
   static constexpr int HC = 0;
-  __device__ void load(const int* c, double* w) const { load_state<ND, true>(g, U, c[0], c[1], c[2], w); }
+  __device__ void load(const int* c, double* w) const { load_filtered<ND>(g, U, c, w); }
   __device__ double row(const double* w, int p, bool closure) const {
     if (closure) return w[p];
     return b0 * w[p] + b1 * (w[p + 1] + w[p - 1]) + b2 * (w[p + 2] + w[p - 2]) + b3 * (w[p + 3] + w[p - 3]) +
@@ -545,8 +559,9 @@ __global__ void k_filter_store(DevGrid g, const double* __restrict__ x, LineBuf 
     c[0] = (int)(q % g.n[0]);
     c[1] = (int)((q / g.n[0]) % g.n[1]);
     c[2] = (int)(q / ((long long)g.n[0] * g.n[1]));
+    const double J = g.curv ? g.jac[plin(g, c[0], c[1], c[2])] : 1.0;
 #pragma unroll
-    for (int v = 0; v < NV; ++v) U[v * g.N + q] = x[lb.at(v, c[lb.d], c)];
+    for (int v = 0; v < NV; ++v) U[v * g.N + q] = g.curv ? x[lb.at(v, c[lb.d], c)] * J : x[lb.at(v, c[lb.d], c)];
   }
 }
 

@@ -1,9 +1,10 @@
 // Grid metrics on the device (once per solver), Sec. 2.1: xi_hat = xi_x / J.
 //
 // Node metrics come from derivatives D of the node coordinates, D being the
-// scheme's own explicit first derivative (sixth order for C-GBR, E4 for LAD-E4
-// and the hybrid) so that the discrete metric identities hold for the flux
-// divergence actually used (freestream preservation).  2D: xi_x = y_eta,
+// scheme's own first derivative (explicit sixth order for C-GBR, E4 for LAD-E4
+// and the hybrid, the compact sixth-order C6 of the LAD-C6 flux divergence)
+// so that the discrete metric identities hold for the flux divergence
+// actually used (freestream preservation).  2D: xi_x = y_eta,
 // xi_y = -x_eta, eta_x = -y_xi, eta_y = x_xi.  3D: conservative
 // (Thomas-Lombard) form xi_x = (y_eta z)_zeta - (y_zeta z)_eta and its cyclic
 // permutations.  Interface metrics: the flux-form interpolant H of the node
@@ -162,6 +163,121 @@ __global__ void km_disp(EBox eb, DevGrid g, const double* __restrict__ X, int l,
     long long s = eb.stride(l);
     plane[e] = 0.5 * (X[q + s] - X[q - s]);
   }
+}
+
+// C6 compact derivative along d (the operator of the LAD-C6 flux divergence),
+// one thread per line of the extended box, written over the E4 values km_op
+// left in o.  Non-periodic d: rows [0, n-1], explicit E4 rows at both ends
+// (reading -2 .. n+1), interior rows (1/3, 1, 1/3) with the C6 right-hand
+// side; Thomas elimination.  Periodic d: the cyclic system (Sherman-Morrison)
+// on f minus its linear trend along the line (detrend = 1, a coordinate:
+// T = f_n - f_0), plus T/n; the extended nodes by wrapping.  A line with a
+// NaN in -2 .. n+1 is left as it is.  scr: 4 (n + 4) doubles per line.
+__global__ void km_c6(EBox eb, const double* __restrict__ f, int d, int periodic, int detrend,
+                      double* __restrict__ o, double* __restrict__ scr) {
+  const int n = eb.n[d], g = eb.ge[d];
+  const int a1 = d == 0 ? 1 : 0, a2 = d == 2 ? 1 : 2;  // transverse directions
+  const long long nl = (long long)eb.PE[a1] * eb.PE[a2];
+  const long long s = eb.stride(d);
+  const double a = 1.0 / 3.0;
+  for (long long L = blockIdx.x * (long long)blockDim.x + threadIdx.x; L < nl; L += (long long)gridDim.x * blockDim.x) {
+    int c[3];
+    c[d] = 0;
+    c[a1] = (int)(L % eb.PE[a1]) - eb.ge[a1];
+    c[a2] = (int)(L / eb.PE[a1]) - eb.ge[a2];
+    const long long q0 = eb.at(c[0], c[1], c[2]);
+    bool ok = true;
+    for (int t = -2; t <= n + 1; ++t) ok = ok && !isnan(f[q0 + (long long)t * s]);
+    if (!ok) continue;
+    const int m = n;
+    double* r = scr + L * 4 * (long long)(n + 4);
+    double* cp = r + (n + 4);
+    double* dp = cp + (n + 4);
+    double* z = dp + (n + 4);
+    if (!periodic) {
+      const double* fl = f + q0;
+      r[0] = d4(fl[-2 * s], fl[-s], fl[s], fl[2 * s]);
+      r[m - 1] = d4(fl[(m - 3) * s], fl[(m - 2) * s], fl[m * s], fl[(m + 1) * s]);
+      for (int i = 1; i < m - 1; ++i) {
+        const double* p = fl + (long long)i * s;
+        r[i] = (7.0 / 9.0) * (p[s] - p[-s]) + (1.0 / 36.0) * (p[2 * s] - p[-2 * s]);
+      }
+      // Thomas: closure rows decoupled (a = 0 there), unit diagonal
+      cp[0] = 0.0 / 1.0;
+      dp[0] = r[0] / 1.0;
+      for (int i = 1; i < m; ++i) {
+        const double ai = i == m - 1 ? 0.0 : a, ci = i == m - 1 ? 0.0 : a;
+        const double den = 1.0 - ai * cp[i - 1];
+        cp[i] = ci / den;
+        dp[i] = (r[i] - ai * dp[i - 1]) / den;
+      }
+      double x = dp[m - 1];
+      o[q0 + (long long)(m - 1) * s] = x;
+      for (int i = m - 2; i >= 0; --i) {
+        x = dp[i] - cp[i] * x;
+        o[q0 + (long long)i * s] = x;
+      }
+      continue;
+    }
+    const double T = detrend ? f[q0 + (long long)n * s] - f[q0] : 0.0;
+    // detrended values at -2 .. n+1 in z (z[t + 2])
+    for (int t = -2; t <= n + 1; ++t) z[t + 2] = f[q0 + (long long)t * s] - T * (double)t / (double)n;
+    for (int i = 0; i < m; ++i) {
+      const double* p = z + i + 2;
+      r[i] = (7.0 / 9.0) * (p[1] - p[-1]) + (1.0 / 36.0) * (p[2] - p[-2]);
+    }
+    // Sherman-Morrison: T + u v^T, u = (gam, 0 .. 0, a), v = (1, 0 .. 0, a / gam)
+    const double gam = -1.0;
+    auto diag = [&](int i) { return i == 0 ? 1.0 - gam : (i == m - 1 ? 1.0 - a * a / gam : 1.0); };
+    auto sub = [&](int i) { return i == 0 ? 0.0 : a; };
+    auto sup = [&](int i) { return i == m - 1 ? 0.0 : a; };
+    cp[0] = sup(0) / diag(0);
+    dp[0] = r[0] / diag(0);
+    for (int i = 1; i < m; ++i) {
+      const double den = diag(i) - sub(i) * cp[i - 1];
+      cp[i] = sup(i) / den;
+      dp[i] = (r[i] - sub(i) * dp[i - 1]) / den;
+    }
+    // x in r (overwrites the right-hand side), then z = T^{-1} u with the same cp
+    r[m - 1] = dp[m - 1];
+    for (int i = m - 2; i >= 0; --i) r[i] = dp[i] - cp[i] * r[i + 1];
+    {
+      const double u0 = gam;
+      dp[0] = u0 / diag(0);
+      for (int i = 1; i < m; ++i) {
+        const double den = diag(i) - sub(i) * cp[i - 1];
+        const double ui = i == m - 1 ? a : 0.0;
+        dp[i] = (ui - sub(i) * dp[i - 1]) / den;
+      }
+      z[m - 1] = dp[m - 1];
+      for (int i = m - 2; i >= 0; --i) z[i] = dp[i] - cp[i] * z[i + 1];
+    }
+    const double fact = (r[0] + a * r[m - 1] / gam) / (1.0 + z[0] + a * z[m - 1] / gam);
+    for (int i = 0; i < m; ++i) o[q0 + (long long)i * s] = (r[i] - fact * z[i]) + T / (double)n;
+    for (int t = 1; t <= g; ++t) {
+      int w0 = (-t) % n;
+      if (w0 < 0) w0 += n;
+      o[q0 - (long long)t * s] = o[q0 + (long long)w0 * s];
+      o[q0 + (long long)(n - 1 + t) * s] = o[q0 + (long long)((n - 1 + t) % n) * s];
+    }
+  }
+}
+
+// X - s0 i - s1 j - s2 k: the periodic part of a coordinate (its linear trends
+// across the periodic directions removed)
+__global__ void km_detrend(EBox eb, const double* __restrict__ X, double s0, double s1, double s2,
+                           double* __restrict__ o) {
+  EB_LOOP(eb, e) {
+    int c[3];
+    eb.coords(e, c);
+    o[e] = ((X[e] - s0 * (double)c[0]) - s1 * (double)c[1]) - s2 * (double)c[2];
+  }
+}
+
+// o = (o + d1 * s1) - d2 * s2: the trend terms of the Thomas-Lombard metrics
+__global__ void km_trend(EBox eb, const double* __restrict__ d1, double s1, const double* __restrict__ d2, double s2,
+                         double* __restrict__ o) {
+  EB_LOOP(eb, e) { o[e] = (o[e] + d1[e] * s1) - d2[e] * s2; }
 }
 
 }  // namespace cgk

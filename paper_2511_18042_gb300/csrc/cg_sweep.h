@@ -62,6 +62,32 @@ int launch_sweep_batched_f64_2(int dir, int lw, const SweepJob* jobs, const long
 int launch_sweep_batched_f32_2(int dir, int lw, const SweepJob* jobs, const long long* off, const int* mem,
                                long long total, cudaStream_t st);
 
+// ---------------------------------------------------------------- persistent stage
+// One RK stage of a work table in a single cooperative launch: every phase
+// (the jobs of one table launch) runs over its virtual blocks with a grid
+// barrier after it.  A phase: its job array, block offsets, block -> member
+// array and total blocks (device memory).
+struct PhaseRef {
+  const void* jobs = nullptr;
+  const long long* off = nullptr;
+  const int* mem = nullptr;
+  long long total = 0;
+};
+struct PersistentStage {
+  PhaseRef zero, cfl, fin, prim, omega, field, troubled, grad, coef, gauss[2], nodeflux[2], hflux[2], sweep[2];
+  int with_cfl;        // first stage: the members' CFL time steps
+  unsigned* bar;       // barrier: arrivals, generation (device, zero at rest)
+  int* err;            // set to 1 when a barrier wait gave up (bounded wait)
+  unsigned expect;     // arrivals a barrier waits for: the launch's blocks
+};
+// Blocks the persistent stage runs with (all co-resident: a cooperative
+// launch); 0 if the shape is not instantiated.
+int persistent_blocks_f64_2(int lw0, int lw1);
+int persistent_blocks_f32_2(int lw0, int lw1);
+// Enqueues one persistent stage with `blocks` blocks (cudaError_t value).
+int launch_persistent_f64_2(int lw0, int lw1, const PersistentStage& P, int blocks, cudaStream_t st);
+int launch_persistent_f32_2(int lw0, int lw1, const PersistentStage& P, int blocks, cudaStream_t st);
+
 inline int launch_sweep_any(int form, int nd, int dir, int lw, bool cart, bool compact, const DevGrid& g,
                             const GbrCfg& q, const StageArgs& A, cudaStream_t st) {
   if (form == kSweepContracted) {

@@ -107,5 +107,6 @@ def test_reference_arm_json_line():
     assert d["value"] > 0 and abs(d["ms_per_step"] - 448 * 192 * 2 / d["value"] * 1e3) <= 1e-6 * d["ms_per_step"]
     assert d["config"]["workload"] == bench.bench_config(["MEG6", "LAD_E4"], 1)["workload"]
     cb = d["cpu_baseline"]
-    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == d["value"] and cb["sample"]
+    assert cb["kind"] == "oracle" and cb["cores"] == os.cpu_count() and cb["value"] == d["value"] and cb["sample"]
+    assert cb["cpu_model"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}

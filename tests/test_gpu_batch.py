@@ -89,6 +89,8 @@ def test_work_table_after_autotune(api):
         same_member(a, b, kw)
     if path == "table":
         assert launches in (41, 82, 164, 328)  # 41 per member group
+    if path == "persistent":
+        assert launches == 3  # one cooperative launch per RK stage
 
 
 def test_multi_step_member_matches_oracle(orc, api):
@@ -128,3 +130,63 @@ def test_full_batch_sampled_members(api):
         a.advance(U, nsteps=4)
         torch.cuda.synchronize()
         same_member(U, Ub[m], dict(precision=1))
+
+
+@pytest.mark.parametrize("kw", [KW[1], KW[3], KW[2]], ids=["fp64", "fp64_buffer", "mixed"])
+def test_persistent_stages_equal_members_alone(api, kw):
+    """One cooperative launch per RK stage (the work table's phases with grid
+    barriers between them): every member equals the member stepped alone,
+    bitwise in FP64, within the mixed tolerance in the mixed form."""
+    probs = inputs.batched_riemann(count=10, seed=3, n_lo=24, n_hi=90)
+    solvers = [api.Solver.from_problem(p, **kw) for p in probs]
+    alone = [api.Solver.from_problem(p, **kw) for p in probs]
+    Ub = [to_dev(p["U"]) for p in probs]
+    Ua = [to_dev(p["U"]) for p in probs]
+    stream = torch.cuda.Stream()
+    batch = api.Batch(solvers, Ub)
+    batch.set_path("persistent")
+    with torch.cuda.stream(stream):
+        for _ in range(5):  # eager, capture + replay, replays
+            batch.step(stream)
+    batch.sync(stream)
+    assert batch.path() == ("persistent", 3)
+    for s, U in zip(alone, Ua):
+        s.advance(U, nsteps=5)
+    torch.cuda.synchronize()
+    for a, b in zip(Ua, Ub):
+        same_member(a, b, kw)
+    # and back to the table's launches: the same members again
+    batch.set_path("table")
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            batch.step(stream)
+    batch.sync(stream)
+    assert batch.path()[0] == "table"
+
+
+def test_persistent_barrier_wait_is_bounded(api):
+    """A barrier that waits for an arrival that never comes gives up after
+    about a second, the launch ends, and cg_batch_sync reports CG_ERR_TIMEOUT;
+    with the normal count restored the batch steps again."""
+    import ctypes
+    from paper_2511_18042_gb300 import _native as nat
+    kw = KW[1]
+    probs = inputs.batched_riemann(count=3, seed=3, n_lo=24, n_hi=40)
+    solvers = [api.Solver.from_problem(p, **kw) for p in probs]
+    Ub = [to_dev(p["U"]) for p in probs]
+    stream = torch.cuda.Stream()
+    batch = api.Batch(solvers, Ub)
+    batch.set_path("persistent")
+    assert nat.lib().cg_batch_debug_barrier(batch._h, 1) == 0
+    with torch.cuda.stream(stream):
+        batch.step(stream)  # eager: three stages, each ends at its first barrier
+    rc = nat.lib().cg_batch_sync(batch._h, ctypes.c_void_p(stream.cuda_stream))
+    assert rc == -6, nat.lib().cg_last_error()
+    assert nat.lib().cg_batch_debug_barrier(batch._h, 0) == 0
+    for U, p in zip(Ub, probs):
+        U.copy_(to_dev(p["U"]))
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            batch.step(stream)
+    batch.sync(stream)
+    assert all(torch.isfinite(U).all() for U in Ub)

@@ -154,12 +154,16 @@ def test_hybrid_limits_on_gpu(orc, api):
     assert rel_err(U, Uo) <= 1e-11
 
 
-@pytest.mark.parametrize("scheme,extra", [("LAD_E4", {}), ("HYBRID", dict(hybrid_mode=1, hyb_rho=1.05))])
+@pytest.mark.parametrize("scheme,extra", [("LAD_E4", {}), ("LAD_C6", dict(cfl=0.1)),
+                                          ("HYBRID", dict(hybrid_mode=1, hyb_rho=1.05))])
 def test_curvilinear_lad_and_hybrid(orc, api, scheme, extra):
     xyz, per = inputs.wavy_grid_2d(40, 36, amp=0.08)
     x, y = xyz
     W = np.stack([1.0 + 0.3 * np.sin(2 * math.pi * x) * np.cos(2 * math.pi * y), 0.5 + 0 * x,
                   0.2 + 0.1 * np.cos(2 * math.pi * y), 1.0 + 0.2 * np.sin(2 * math.pi * (x + y))])
+    if scheme == "LAD_C6":
+        from tests.test_gpu_gbr import _no_critical_nodes
+        W = _no_critical_nodes(W, xyz)
     prob = inputs.field_on_curvilinear(xyz, per, W)
     o, s = _pair(orc, api, prob, scheme=scheme, **extra)
     Uo, _, _ = o.advance(prob["U"], nsteps=5)

@@ -112,10 +112,13 @@ def _field3(P):
 
 
 @pytest.mark.parametrize("kw", [dict(scheme="MEG6"), dict(scheme="MIG4"), dict(scheme="LAD_E4"),
-                                dict(scheme="HYBRID", hybrid_mode=1, hyb_rho=1.05)])
+                                dict(scheme="LAD_C6"), dict(scheme="HYBRID", hybrid_mode=1, hyb_rho=1.05)])
 def test_3d_curvilinear_viscous_rhs(orc, api, kw):
     xyz, per = inputs.wavy_grid_3d((16, 12, 10), amp=0.05)
     W = _field3(xyz)
+    if kw.get("scheme") == "LAD_C6":  # no node at a critical point of e or rho (Eq. 6 length scales)
+        from tests.test_gpu_gbr import _no_critical_nodes
+        W = _no_critical_nodes(W, xyz)
     prob = inputs._viscous(inputs.field_on_curvilinear(xyz, per, W), 30.0, 0.3, 0.5, 1.0)
     s = _solver(api, prob, kw)
     o = orc.Oracle(prob, **kw)
@@ -144,7 +147,7 @@ def test_inflow_profile_parallel_flow_3d(orc, api):
         assert rel_err(s.rhs(to_dev(prob["U"])), o.rhs(prob["U"])) <= RHS_TOL(kw), kw
 
 
-RAMP_KW = [dict(scheme="MEG6"), dict(scheme="MIG4"), dict(scheme="LAD_E4"),
+RAMP_KW = [dict(scheme="MEG6"), dict(scheme="MIG4"), dict(scheme="LAD_E4"), dict(scheme="LAD_C6"),
            dict(scheme="HYBRID", hybrid_mode=0, hyb_rho=0.4), dict(scheme="HYBRID", hybrid_mode=1, hybrid_sensor=1,
                                                                    hyb_rho=0.4)]
 
@@ -166,7 +169,7 @@ def test_compression_ramp_fp64_matches_oracle(orc, api, ramp, kw):
     assert rel_err(Ug, Uo) <= 1e-11
 
 
-@pytest.mark.parametrize("kw", [dict(scheme="MEG6"), dict(scheme="MIG4"), dict(scheme="LAD_E4"),
+@pytest.mark.parametrize("kw", [dict(scheme="MEG6"), dict(scheme="MIG4"), dict(scheme="LAD_E4"), dict(scheme="LAD_C6"),
                                 dict(scheme="HYBRID", hybrid_mode=1, hybrid_sensor=1, hyb_rho=0.4)])
 def test_compression_ramp_mixed_form(orc, api, ramp, kw):
     s = api.Solver.from_problem(ramp, precision=1, **kw)
