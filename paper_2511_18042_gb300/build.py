@@ -23,7 +23,8 @@ for _nd in (1, 2, 3):
     UNITS.append(("cg_sweep_inst.cu", "cg_sweep_f64c_%d.o" % _nd,
                   ["-fmad=true", "-DCGK_SWEEP_ND=%d" % _nd, "-DCGK_SWEEP_UNIT=1"]))
     UNITS.append(("cg_sweep_inst.cu", "cg_sweep_f32_%d.o" % _nd,
-                  ["-fmad=true", "-DCGK_SWEEP_ND=%d" % _nd, "-DCGK_SWEEP_UNIT=2"]))
+                  ["-fmad=true", "-prec-div=false", "-prec-sqrt=false", "-DCGK_SWEEP_ND=%d" % _nd,
+                   "-DCGK_SWEEP_UNIT=2"]))
 NVCC_FLAGS = COMMON + FP64
 
 

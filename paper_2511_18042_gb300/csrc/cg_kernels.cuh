@@ -310,20 +310,48 @@ __device__ __forceinline__ void k_gbr_sweep_body(const VBlock& vb, const DevGrid
     i0 = vb.y * (TL - 1);
     nlines = 0;
   }
-  // coordinates of line l (the two other directions)
-  auto line_coords = [&](int l, int* c) -> bool {
+  // The tile's lines, computed once per block (the integer divisions and
+  // index products would otherwise be repeated for every staged value):
+  // coordinates of the two other directions (-1 in entry 0: no such line),
+  // the linear index of the line's node 0 in the state planes and in the
+  // sensor box; node x of the line is at base + x * stride.
+  __shared__ int s_lc[LW][3];
+  __shared__ long long s_lq[LW], s_lo[LW];
+  if (tid < LW) {
+    const int l = tid;
+    int c[3] = {0, 0, 0};
+    bool ok;
     if (DIR == 0) {
       long long L = (long long)vb.y * LW + l;
-      if (L >= nlines) return false;
-      c[1] = (int)(L % g.n[1]);
-      c[2] = (int)(L / g.n[1]);
+      ok = L < nlines;
+      if (ok) {
+        c[1] = (int)(L % g.n[1]);
+        c[2] = (int)(L / g.n[1]);
+      }
     } else {
       int x = vb.x * LW + l;
-      if (x >= g.n[0]) return false;
-      c[0] = x;
-      int o = DIR == 1 ? 2 : 1;
-      c[o] = vb.z;
+      ok = x < g.n[0];
+      if (ok) {
+        c[0] = x;
+        c[DIR == 1 ? 2 : 1] = vb.z;
+      }
     }
+    s_lc[l][0] = ok ? c[0] : -1;
+    s_lc[l][1] = c[1];
+    s_lc[l][2] = c[2];
+    c[DIR] = 0;
+    s_lq[l] = ok ? lin(g, c[0], c[1], c[2]) : 0;
+    s_lo[l] = ok ? A.omBox.at(c[0], c[1], c[2]) : 0;
+  }
+  __syncthreads();
+  const long long qs = DIR == 0 ? 1 : (DIR == 1 ? (long long)g.n[0] : (long long)g.n[0] * g.n[1]);
+  const long long os = DIR == 0 ? 1 : (DIR == 1 ? (long long)A.omBox.ext[0] : (long long)A.omBox.ext[0] * A.omBox.ext[1]);
+  // coordinates of line l (the two other directions)
+  auto line_coords = [&](int l, int* c) -> bool {
+    if (s_lc[l][0] < 0) return false;
+    c[0] = s_lc[l][0];
+    c[1] = s_lc[l][1];
+    c[2] = s_lc[l][2];
     return true;
   };
   (void)lc1;
@@ -349,14 +377,20 @@ __device__ __forceinline__ void k_gbr_sweep_body(const VBlock& vb, const DevGrid
     stage_tile = __syncthreads_or(any) != 0;
   }
   if (stage_tile) {
-    // 1. primitives of the tile (ghosts resolved by the boundary conditions)
+    // 1. primitives of the tile (ghosts resolved by the boundary conditions;
+    // interior nodes read directly, the same values)
     for (int e = tid; e < RW * LW; e += blockDim.x) {
       int r = DIR == 0 ? e % RW : e / LW;
       int l = DIR == 0 ? e / RW : e % LW;
       int c[3] = {0, 0, 0};
       T w[NV];
-      if (line_coords(l, c)) {
-        c[DIR] = i0 - 5 + r;
+      const int x = i0 - 5 + r;
+      if (line_coords(l, c) && x >= 0 && x < n) {
+        const long long q0 = s_lq[l] + (long long)x * qs;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) w[v] = MIX ? T(A.Wf[(long long)v * g.N + q0]) : T(A.W[(long long)v * g.N + q0]);
+      } else if (line_coords(l, c)) {
+        c[DIR] = x;
         if (MIX) load_state<ND, false, float, T>(g, A.Wf, c[0], c[1], c[2], w);
         else load_state<ND, false, double, T>(g, A.W, c[0], c[1], c[2], w);
       } else {
@@ -370,13 +404,9 @@ __device__ __forceinline__ void k_gbr_sweep_body(const VBlock& vb, const DevGrid
     for (int e = tid; e < RO * LW; e += blockDim.x) {
       int r = DIR == 0 ? e % RO : e / LW;
       int l = DIR == 0 ? e / RO : e % LW;
-      int c[3] = {0, 0, 0};
       T o = T(0);
       int x = i0 - 4 + r;
-      if (line_coords(l, c) && x <= n + 3) {
-        c[DIR] = x;
-        o = static_cast<const T*>(A.om)[A.omBox.at(c[0], c[1], c[2])];
-      }
+      if (s_lc[l][0] >= 0 && x <= n + 3) o = static_cast<const T*>(A.om)[s_lo[l] + (long long)x * os];
       sO[(DIR == 0) ? l * RO + r : r * LW + l] = o;
     }
     __syncthreads();
@@ -483,7 +513,7 @@ __device__ __forceinline__ void k_gbr_sweep_body(const VBlock& vb, const DevGrid
     int x = i0 + a;
     if (!line_coords(l, c) || x >= n) continue;
     c[DIR] = x;
-    long long qi = lin(g, c[0], c[1], c[2]);
+    long long qi = s_lq[l] + (long long)x * qs;
     double J = CART ? g.cjac : g.jac[plin(g, c[0], c[1], c[2])];
     double out[NV];
     // mixed form: the FP32 fluxes differenced and summed over the directions in
