@@ -216,8 +216,7 @@ def run_gpu(args):
             if events is not None:
                 events[n][0].record(stream)
             U[n].copy_(base)
-            s.cfl_dt(U[n], out=dt[n])
-            s.rk3_step(U[n], dt[n])
+            s.step(U[n], dt[n])
             if events is not None:
                 events[n][1].record(stream)
 
@@ -358,14 +357,12 @@ def run_ramp(api, torch, dev, args):
             s = api.Solver.from_problem(prob, grid=grid, precision=prec, **kw)
             U = base.clone()
             dtd = torch.zeros(2, dtype=torch.float64, device=dev)
-            s.cfl_dt(U, out=dtd)
-            s.rk3_step(U, dtd)
+            s.step(U, dtd)
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
             for _ in range(args.ramp_steps):
-                s.cfl_dt(U, out=dtd)
-                s.rk3_step(U, dtd)
+                s.step(U, dtd)
             e1.record()
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1) / args.ramp_steps
@@ -503,14 +500,12 @@ def run_batched(api, torch, dev, args, count=256, steps_per_solve=200, ref_steps
     ref_states = [torch.as_tensor(p["U"], device=dev) for p in probs]
     dts = [torch.zeros(2, dtype=torch.float64, device=dev) for _ in probs]
     for s, U, d in zip(ref_solvers, ref_states, dts):
-        s.cfl_dt(U, out=d)
-        s.rk3_step(U, d)
+        s.step(U, d)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(ref_steps):
         for s, U, d in zip(ref_solvers, ref_states, dts):
-            s.cfl_dt(U, out=d)
-            s.rk3_step(U, d)
+            s.step(U, d)
     torch.cuda.synchronize()
     ref_ms = (time.perf_counter() - t0) * 1e3 / ref_steps
     del ref_solvers, ref_states
@@ -585,8 +580,7 @@ def time_mixed(api, torch, grid, base, dev, kw, args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     for _ in range(max(3, args.warmup)):
         U.copy_(base)
-        s.cfl_dt(U, out=dtd)
-        s.rk3_step(U, dtd)
+        s.step(U, dtd)
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
     tot = 0.0
@@ -595,8 +589,7 @@ def time_mixed(api, torch, grid, base, dev, kw, args):
         flush.zero_()  # evict L2 (256 MB > 126 MB) between timed steps
         e0.record(stream)
         U.copy_(base)
-        s.cfl_dt(U, out=dtd)
-        s.rk3_step(U, dtd)
+        s.step(U, dtd)
         e1.record(stream)
         torch.cuda.synchronize()
         tot += e0.elapsed_time(e1)
@@ -613,15 +606,13 @@ def _sweep_ms(api, torch, grid, base, dev, args, form):
     dtd = torch.zeros(2, dtype=torch.float64, device=dev)
     for _ in range(2):
         U.copy_(base)
-        s.cfl_dt(U, out=dtd)
-        s.rk3_step(U, dtd)
+        s.step(U, dtd)
     torch.cuda.synchronize()
     s.timing_enable(True)
     reps = max(2, args.steps)
     for _ in range(reps):
         U.copy_(base)
-        s.cfl_dt(U, out=dtd)
-        s.rk3_step(U, dtd)
+        s.step(U, dtd)
     torch.cuda.synchronize()
     ms, n = s.timing_query(0)
     s.timing_enable(False)

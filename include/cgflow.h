@@ -155,6 +155,21 @@ CG_API int cg_rk3_step(cg_solver *s, double *U, double dt, void *stream);
 /* Same with dt read from device memory at run time (graph-capturable). */
 CG_API int cg_rk3_step_dev(cg_solver *s, double *U, const double *dt_dev, void *stream);
 
+/* The CFL step size of U (cg_cfl_dt) written to dt_dev (device memory), then
+ * one TVD-RK3 step of U in place with it (cg_rk3_step_dev): Sec. 3's time
+ * loop body.  The CFL maximum is reduced by stage 1's primitive kernel, so U
+ * is read once for both; the results are bitwise those of the two calls.
+ * Graph-capturable; nothing waits. */
+CG_API int cg_step_dev(cg_solver *s, double *U, double *dt_dev, void *stream);
+
+/* Diagnostic (no counterpart in the paper): the mixed form's FP64 <-> FP32
+ * conversions on the integer pipes, applied elementwise: f_out[i] = d_in[i]
+ * rounded to binary32 (nearest, ties to even), d_out[i] = f_in[i] widened to
+ * binary64.  All four arrays are device memory of n elements, owned by the
+ * caller; nothing waits.  They must equal the hardware conversions bit for bit. */
+CG_API int cg_convert_check(const double *d_in, float *f_out, const float *f_in, double *d_out, int64_t n,
+                            void *stream);
+
 /* CFL time step dt = cfl / max_i J sum_l (|xi_hat_l . u| + c |xi_hat_l|).
  * dt_on_device = 1: *dt_out is device memory, nothing waits; 0: host memory,
  * the call synchronises the stream. */

@@ -128,6 +128,13 @@ class Solver:
             nat.check(nat.lib().cg_rk3_step(self._h, _dptr(U), float(dt), _stream(stream)))
         return U
 
+    def step(self, U, dt, stream=None):
+        """CFL step size of U into the device scalar dt, then one RK3 step of
+        U with it (cg_step_dev: one read of U serves both)."""
+        self._check_state(U)
+        nat.check(nat.lib().cg_step_dev(self._h, _dptr(U), _dptr(dt), _stream(stream)))
+        return U
+
     def cfl_dt(self, U, out=None, stream=None):
         self._check_state(U)
         if out is not None:

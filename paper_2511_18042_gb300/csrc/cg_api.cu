@@ -235,6 +235,11 @@ struct cg_solver {
   double* dt = nullptr;             // device dt
   double* t = nullptr;              // device time
   unsigned long long* cflmax = nullptr;
+  // set by rk3 with a fused CFL step: the next primitive launch (stage 1's)
+  // also reduces the CFL maximum and writes dt (and t) here
+  bool prim_cfl = false;
+  double* prim_cfl_dt = nullptr;
+  double* prim_cfl_t = nullptr;
   unsigned int* bad_flag = nullptr;
   unsigned long long* bad_idx = nullptr;
   long long launches = 0;
@@ -761,9 +766,27 @@ static void launch_rhs_filter(const DevGrid& g, const double* U, const LineBuf& 
 
 // Primitives of Uc into W: FP64 storage, or FP32 for the mixed form (the
 // recovery itself is FP64 in both).
+// With a fused CFL step pending (rk3_cfl), the launch also reduces the CFL
+// maximum of Uc and the step size follows from it before anything reads dt.
 template <int ND>
 static void launch_prim(cg_solver* s, const double* Uc, cudaStream_t st) {
-  if (s->p.precision == CG_MIXED)
+  const bool mixed = s->p.precision == CG_MIXED;
+  if (s->prim_cfl) {
+    s->prim_cfl = false;
+    cudaMemsetAsync(s->cflmax, 0, sizeof(unsigned long long), st);
+    const int nb = grid_blocks(s->N, 256);
+    if (s->dg.curv) {
+      if (mixed) k_prim_cfl<ND, false, float><<<nb, 256, 0, st>>>(s->dg, Uc, reinterpret_cast<float*>(s->W), s->cflmax);
+      else k_prim_cfl<ND, false, double><<<nb, 256, 0, st>>>(s->dg, Uc, s->W, s->cflmax);
+    } else {
+      if (mixed) k_prim_cfl<ND, true, float><<<nb, 256, 0, st>>>(s->dg, Uc, reinterpret_cast<float*>(s->W), s->cflmax);
+      else k_prim_cfl<ND, true, double><<<nb, 256, 0, st>>>(s->dg, Uc, s->W, s->cflmax);
+    }
+    k_cfl_finish<<<1, 1, 0, st>>>(s->cflmax, s->p.cfl, s->prim_cfl_dt, s->prim_cfl_t, 0.0);
+    s->launches += 3;
+    return;
+  }
+  if (mixed)
     k_prim<ND, float><<<grid_blocks(s->N, 256), 256, 0, st>>>(s->dg, Uc, reinterpret_cast<float*>(s->W));
   else
     k_prim<ND, double><<<grid_blocks(s->N, 256), 256, 0, st>>>(s->dg, Uc, s->W);
@@ -882,6 +905,26 @@ template <int ND>
 static int rk3(cg_solver* s, double* U, cudaStream_t st) {
   int rc;
   if ((rc = stage<ND>(s, U, U, s->U1, 1, 1, st))) return rc;
+  if ((rc = stage<ND>(s, s->U1, U, s->U2, 1, 2, st))) return rc;
+  if ((rc = stage<ND>(s, s->U2, U, U, 1, 3, st))) return rc;
+  if (s->p.scheme == CG_LAD_C6 && s->p.filter_on) return lad_filter<ND>(s, U, st);
+  return CG_OK;
+}
+
+// The CFL step and one RK3 step with its dt: stage 1's primitive launch
+// reduces the CFL maximum of U (every stage path starts with that launch), so
+// the state is read once for both.  Results are bitwise those of cfl_launch
+// followed by rk3.
+template <int ND>
+static int rk3_cfl(cg_solver* s, double* U, double* dt_dev, double* t_dev, cudaStream_t st) {
+  s->prim_cfl = true;
+  s->prim_cfl_dt = dt_dev;
+  s->prim_cfl_t = t_dev;
+  int rc = stage<ND>(s, U, U, s->U1, 1, 1, st);
+  const bool unused = s->prim_cfl;
+  s->prim_cfl = false;
+  if (rc) return rc;
+  if (unused) return fail(CG_ERR_UNSUPPORTED, "stage 1 launched no primitive kernel");
   if ((rc = stage<ND>(s, s->U1, U, s->U2, 1, 2, st))) return rc;
   if ((rc = stage<ND>(s, s->U2, U, U, 1, 3, st))) return rc;
   if (s->p.scheme == CG_LAD_C6 && s->p.filter_on) return lad_filter<ND>(s, U, st);
@@ -1317,6 +1360,33 @@ CG_API int cg_rk3_step_dev(cg_solver* s, double* U, const double* dt_dev, void* 
   return CG_OK;
 }
 
+static __global__ void k_convert_check(const double* d_in, float* f_out, const float* f_in, double* d_out, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    f_out[i] = d2f_int(d_in[i]);
+    d_out[i] = f2d_int(f_in[i]);
+  }
+}
+
+CG_API int cg_convert_check(const double* d_in, float* f_out, const float* f_in, double* d_out, int64_t n, void* stream) {
+  if (n < 0 || (n > 0 && (!d_in || !f_out || !f_in || !d_out))) return fail(CG_ERR_INVALID_ARG, "null argument");
+  if (n == 0) return CG_OK;
+  k_convert_check<<<grid_blocks(n, 256), 256, 0, (cudaStream_t)stream>>>(d_in, f_out, f_in, d_out, (long long)n);
+  CG_CUDA(cudaGetLastError());
+  return CG_OK;
+}
+
+CG_API int cg_step_dev(cg_solver* s, double* U, double* dt_dev, void* stream) {
+  if (!s || !U || !dt_dev) return fail(CG_ERR_INVALID_ARG, "null argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  double* keep = s->dt;
+  s->dt = dt_dev;
+  int rc = DISPATCH_ND(s, rk3_cfl, s, U, dt_dev, nullptr, st);
+  s->dt = keep;
+  if (rc) return rc;
+  CG_CUDA(cudaGetLastError());
+  return CG_OK;
+}
+
 CG_API int cg_rk3_step(cg_solver* s, double* U, double dt, void* stream) {
   if (!s || !U) return fail(CG_ERR_INVALID_ARG, "null argument");
   if (!(dt >= 0.0)) return fail(CG_ERR_INVALID_ARG, "dt must be >= 0");
@@ -1385,8 +1455,7 @@ CG_API int cg_advance(cg_solver* s, double* U, int64_t nsteps, double t_end, dou
       if (rc) return rc;
       t += dt;
     } else {
-      DISPATCH_ND(s, cfl_launch, s, U, s->dt, s->t, 0.0, st);
-      int rc = DISPATCH_ND(s, rk3, s, U, st);
+      int rc = DISPATCH_ND(s, rk3_cfl, s, U, s->dt, s->t, st);
       if (rc) return rc;
     }
     ++k;

@@ -65,6 +65,22 @@ __device__ __forceinline__ T gconst(double d, float f) {
   else return d;
 }
 
+// Node coordinates of the linear index q (32-bit division when the grid has
+// fewer than 2^31 nodes: a 64-bit division by a variable costs several times more).
+__device__ __forceinline__ void node_coords(const DevGrid& g, long long q, int* c) {
+  if (g.N <= 0x7fffffffLL) {
+    const unsigned r = (unsigned)q, n0 = (unsigned)g.n[0], n1 = (unsigned)g.n[1];
+    const unsigned t = r / n0;
+    c[0] = (int)(r - t * n0);
+    c[1] = (int)(t % n1);
+    c[2] = (int)(t / n1);
+  } else {
+    c[0] = (int)(q % g.n[0]);
+    c[1] = (int)((q / g.n[0]) % g.n[1]);
+    c[2] = (int)(q / ((long long)g.n[0] * g.n[1]));
+  }
+}
+
 __device__ __forceinline__ long long lin(const DevGrid& g, int i, int j, int k) {
   return (long long)i + (long long)g.n[0] * ((long long)j + (long long)g.n[1] * (long long)k);
 }
@@ -164,16 +180,56 @@ __device__ __forceinline__ void cons_to_prim_g(const DevGrid& g, const double* Q
   W[ND + 1] = g.gm1 * (Q[ND + 1] - 0.5 * ke);
 }
 
+// ---------------------------------------------------------------- binary64 <-> binary32
+// Format conversions on the integer pipes.  On this part a hardware conversion
+// between FP64 and FP32 issues on the FP64 pipe, which runs at 2 instructions
+// per clock per SM against 64 for the integer pipes, so the mixed form's
+// FP64-bound kernels (recovery, RK update) convert with integer operations.
+// Both follow the IEEE 754 interchange formats (binary64: 1 sign, 11 exponent
+// bits with bias 1023, 52 fraction bits; binary32: 1, 8 with bias 127, 23)
+// and round to nearest, ties to even, so they return exactly what the
+// hardware conversion returns; inputs whose result is not a normal number or
+// zero (subnormal results, infinities, NaN, overflow) take the hardware
+// conversion through a call the compiler cannot predicate into the fast path.
+static __device__ __noinline__ float d2f_slow(double x) { return (float)x; }
+static __device__ __noinline__ double f2d_slow(float x) { return (double)x; }
+
+__device__ __forceinline__ float d2f_int(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned e = (hi >> 20) & 0x7ffu;
+  const unsigned sign = hi & 0x80000000u;
+  if (e >= 897u && e <= 1150u) {  // binary32 exponents -126..127: a normal result
+    // exponent rebiased (1023 -> 127) with the top 23 fraction bits below it
+    unsigned f = (((hi & 0x7fffffffu) - (896u << 20)) << 3) | (lo >> 29);
+    const unsigned rest = lo & 0x1fffffffu;  // the 29 dropped fraction bits
+    f += (rest > 0x10000000u || (rest == 0x10000000u && (f & 1u))) ? 1u : 0u;  // a carry may reach the
+    return __uint_as_float(sign | f);                                        // exponent (and infinity)
+  }
+  if (e <= 872u) return __uint_as_float(sign);  // |x| < 2^-150: rounds to a signed zero
+  return d2f_slow(x);
+}
+
+__device__ __forceinline__ double f2d_int(float x) {
+  const unsigned b = __float_as_uint(x);
+  const unsigned e = (b >> 23) & 0xffu;
+  if (e != 0u && e != 0xffu)  // normal: rebias the exponent (127 -> 1023), widen the fraction
+    return __hiloint2double((int)((b & 0x80000000u) | (((b >> 3) & 0x0fffffffu) + (896u << 20))), (int)(b << 29));
+  if ((b & 0x7fffffffu) == 0u) return __hiloint2double((int)(b & 0x80000000u), 0);
+  return f2d_slow(x);
+}
+
 // The mixed form's recovery: FP64 arithmetic for the cancellation in
 // E - rho|u|^2/2, with 1/rho from the FP32 reciprocal refined by one Newton
 // step in FP64 (r1 = r0 + r0 (1 - rho r0): relative error below 2e-14, far
 // under what the FP32 result keeps) instead of an IEEE FP64 division, which
 // on this part costs more FP64-pipe issue than the rest of the recovery.
 // Densities outside the FP32 normal range take the division.
+// Densities whose FP32 image or reciprocal would not be a normal float take
+// the division.  Conversions on the integer pipes (d2f_int, f2d_int).
 __device__ __forceinline__ double recip_refined(double x) {
-  const float xf = (float)x;
-  if (!(fabsf(xf) >= 1.2e-38f && fabsf(xf) <= 3.0e38f)) return 1.0 / x;
-  const double r = (double)__frcp_rn(xf);
+  const float xf = d2f_int(x);
+  if (!(fabsf(xf) >= 1e-37f && fabsf(xf) <= 1e37f)) return 1.0 / x;
+  const double r = f2d_int(__frcp_rn(xf));
   return __fma_rn(r, __fma_rn(-x, r, 1.0), r);
 }
 
@@ -182,14 +238,14 @@ __device__ __forceinline__ void cons_to_prim_mixed(double gm1, const double* Q, 
   const double rho = Q[0];
   const double r = recip_refined(rho);
   double ke = 0.0;
-  W[0] = (float)rho;
+  W[0] = d2f_int(rho);
 #pragma unroll
   for (int k = 0; k < ND; ++k) {
     const double u = Q[1 + k] * r;
-    W[1 + k] = (float)u;
+    W[1 + k] = d2f_int(u);
     ke = __fma_rn(Q[1 + k], u, ke);
   }
-  W[ND + 1] = (float)(gm1 * __fma_rn(-0.5, ke, Q[ND + 1]));
+  W[ND + 1] = d2f_int(gm1 * __fma_rn(-0.5, ke, Q[ND + 1]));
 }
 
 // Image of a state across an isothermal no-slip wall: velocity negated,

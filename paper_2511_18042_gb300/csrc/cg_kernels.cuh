@@ -46,6 +46,101 @@ struct StageArgs {
   const float* Gdf;           // mixed form: the compact gradients in FP32
 };
 
+// ---------------------------------------------------------------- stage epilogue
+// Non-physical test of the mixed form: the sign of rho p / (gamma-1) =
+// rho E - |m|^2/2 without a division.  An FP32 screen comes first: the float
+// images carry a relative error of 2^-24 each, so rho E - |m|^2/2 evaluated
+// in FP32 is within 4e-7 (rho E + |m|^2/2) of the exact value, and a margin of
+// 1e-5 of that sum proves the sign; only nodes without that margin take the
+// FP64 test.
+template <int ND>
+__device__ __forceinline__ bool mixed_nonphysical(const double* out) {
+  constexpr int IP = ND + 1;
+  const float r0 = d2f_int(out[0]), e0 = d2f_int(out[IP]);
+  float m2f = 0.f;
+#pragma unroll
+  for (int m = 0; m < ND; ++m) {
+    const float mm = d2f_int(out[1 + m]);
+    m2f = m2f + mm * mm;
+  }
+  const float re = r0 * e0, hm = 0.5f * m2f;
+  if (r0 > 0.f && re - hm > 1e-5f * (re + hm)) return false;
+  double m2 = out[1] * out[1];
+#pragma unroll
+  for (int m = 1; m < ND; ++m) m2 = __fma_rn(out[1 + m], out[1 + m], m2);
+  return !(out[0] > 0.0) || !(__fma_rn(out[0], out[IP], -0.5 * m2) > 0.0);
+}
+
+// The last direction's epilogue of one node from its stage totals tot[v] (the
+// directions' flux differences; FP32 in the mixed form, MIX): R = -J tot
+// (rk = 0) or the TVD-RK3 combination, and the non-physical test after stage
+// 3.  Each stage has its own branch: a selection between the stages'
+// formulas per value would issue all of them on the FP64 pipe.
+// * FP64 form: the oracle's operation order, r = -(J tot), then
+//   Un + dt r, or a Un + b (Uc + dt r).
+// * mixed form: the RK weights folded into one factor per node,
+//   U = a Un + b Uc - (b dt J) tot (Un alone in stage 1): one multiply and two
+//   multiply-adds per variable, the total widened on the integer pipes.
+template <int ND, bool MIX, typename TA>
+__device__ __forceinline__ void stage_epilogue(const DevGrid& g, const StageArgs& A, long long qi, double J,
+                                               const TA* tot) {
+  constexpr int NV = ND + 2, IP = ND + 1;
+  auto wide = [](TA t) -> double {
+    if constexpr (MIX) return f2d_int(t);
+    else return double(t);
+  };
+  if (!A.rk) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) A.R[v * g.N + qi] = -(J * wide(tot[v]));
+    return;
+  }
+  const double dt = *A.dt;
+  double out[NV];
+  if (A.stage == 1) {
+    const double cJ = -dt * J;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const double un = A.Un[v * g.N + qi];
+      if constexpr (MIX) {
+        out[v] = __fma_rn(cJ, wide(tot[v]), un);
+      } else {
+        const double r = -(J * wide(tot[v]));
+        out[v] = un + dt * r;
+      }
+      A.Uout[v * g.N + qi] = out[v];
+    }
+    return;
+  }
+  const double ca = A.stage == 2 ? 0.75 : (1.0 / 3.0), cb = A.stage == 2 ? 0.25 : (2.0 / 3.0);
+  const double cJ = -(cb * dt) * J;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const double un = A.Un[v * g.N + qi], uc = A.Uc[v * g.N + qi];
+    if constexpr (MIX) {
+      out[v] = __fma_rn(ca, un, __fma_rn(cb, uc, cJ * wide(tot[v])));
+    } else {
+      const double r = -(J * wide(tot[v]));
+      out[v] = ca * un + cb * (uc + dt * r);
+    }
+    A.Uout[v * g.N + qi] = out[v];
+  }
+  if (A.stage != 3) return;
+  bool bad;
+  if constexpr (MIX) {
+    bad = mixed_nonphysical<ND>(out);
+  } else {
+    double ke = out[1] * (out[1] / out[0]);
+#pragma unroll
+    for (int m = 1; m < ND; ++m) ke = ke + out[1 + m] * (out[1 + m] / out[0]);
+    double p = g.gm1 * (out[IP] - 0.5 * ke);
+    bad = !(out[0] > 0.0) || !(p > 0.0);
+  }
+  if (bad) {
+    atomicOr(A.bad_flag, 1u);
+    atomicMin(A.bad_idx, (unsigned long long)qi);
+  }
+}
+
 // ---------------------------------------------------------------- block coordinates
 // Each stage kernel is a body over the coordinates of its block plus a thin
 // __global__ wrapper that passes the hardware ones.  The batched stage
@@ -106,11 +201,20 @@ __device__ __forceinline__ void k_omega_body(const VBlock& vb, const DevGrid& g,
   for (long long e = vb.x * (long long)blockDim.x + threadIdx.x; e < tot;
        e += (long long)vb.gx * blockDim.x) {
     int c[3];
-    long long r = e;
-    c[0] = (int)(r % ob.ext[0]) - ob.off[0];
-    r /= ob.ext[0];
-    c[1] = (int)(r % ob.ext[1]) - ob.off[1];
-    c[2] = (int)(r / ob.ext[1]) - ob.off[2];
+    if (tot <= 0x7fffffffLL) {  // 32-bit index arithmetic (a 64-bit division costs several times more)
+      unsigned r = (unsigned)e;
+      const unsigned x0 = (unsigned)ob.ext[0], x1 = (unsigned)ob.ext[1];
+      c[0] = (int)(r % x0) - ob.off[0];
+      r /= x0;
+      c[1] = (int)(r % x1) - ob.off[1];
+      c[2] = (int)(r / x1) - ob.off[2];
+    } else {
+      long long r = e;
+      c[0] = (int)(r % ob.ext[0]) - ob.off[0];
+      r /= ob.ext[0];
+      c[1] = (int)(r % ob.ext[1]) - ob.off[1];
+      c[2] = (int)(r / ob.ext[1]) - ob.off[2];
+    }
     T phi = T(0);
     T du[3][3];  // du[l][k] = d u_k / d xi_l
     // nodes whose whole stencil is interior read the planes directly (the
@@ -283,7 +387,7 @@ __host__ __device__ constexpr int sweep_min_blocks() {
 template <int ND, int DIR, bool CART, bool COMPACT, typename T, int LW, int UNIT>
 __device__ __forceinline__ void k_gbr_sweep_body(const VBlock& vb, const DevGrid& g, const GbrCfg& q, const StageArgs& A) {
   static_assert((SWEEP_TL * LW) % 256 == 0, "a tile must hold a multiple of the block's threads");
-  constexpr int NV = ND + 2, IP = ND + 1;
+  constexpr int NV = ND + 2;
   constexpr bool MIX = sizeof(T) == 4;
   constexpr int TL = SWEEP_TL;
   constexpr int RW = TL + 9, RD = TL + 3, RDD = TL + 1, RO = TL + 7;
@@ -514,54 +618,24 @@ __device__ __forceinline__ void k_gbr_sweep_body(const VBlock& vb, const DevGrid
     if (!line_coords(l, c) || x >= n) continue;
     c[DIR] = x;
     long long qi = s_lq[l] + (long long)x * qs;
-    double J = CART ? g.cjac : g.jac[plin(g, c[0], c[1], c[2])];
-    double out[NV];
     // mixed form: the FP32 fluxes differenced and summed over the directions in
     // FP32 (acc read as float), the stage total carried into the FP64 update
     using TA = typename std::conditional<MIX, float, double>::type;
     TA* acc = reinterpret_cast<TA*>(A.acc);
+    TA tot[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       TA diff = MIX ? TA(sF[IX(v, a + 1, l, TL)] - sF[IX(v, a, l, TL)])
                     : TA((double)sF[IX(v, a + 1, l, TL)] - (double)sF[IX(v, a, l, TL)]);
-      TA tot = A.first ? diff : acc[v * g.N + qi] + diff;
-      if (!A.last) {
-        acc[v * g.N + qi] = tot;
-        continue;
-      }
-      double r = -(J * double(tot));
-      if (!A.rk) {
-        A.R[v * g.N + qi] = r;
-        continue;
-      }
-      double dt = *A.dt;
-      double un = A.Un[v * g.N + qi];
-      double o;
-      if (A.stage == 1) o = un + dt * r;
-      else if (A.stage == 2) o = 0.75 * un + 0.25 * (A.Uc[v * g.N + qi] + dt * r);
-      else o = (1.0 / 3.0) * un + (2.0 / 3.0) * (A.Uc[v * g.N + qi] + dt * r);
-      out[v] = o;
-      A.Uout[v * g.N + qi] = o;
+      tot[v] = A.first ? diff : acc[v * g.N + qi] + diff;
     }
-    if (A.last && A.rk && A.stage == 3) {
-      bool bad;
-      if (MIX) {  // sign of rho p / (gamma-1) = rho E - |m|^2 / 2, no division
-        double m2 = out[1] * out[1];
+    if (!A.last) {
 #pragma unroll
-        for (int m = 1; m < ND; ++m) m2 = m2 + out[1 + m] * out[1 + m];
-        bad = !(out[0] > 0.0) || !(out[0] * out[IP] - 0.5 * m2 > 0.0);
-      } else {
-        double ke = out[1] * (out[1] / out[0]);
-#pragma unroll
-        for (int m = 1; m < ND; ++m) ke = ke + out[1 + m] * (out[1 + m] / out[0]);
-        double p = g.gm1 * (out[IP] - 0.5 * ke);
-        bad = !(out[0] > 0.0) || !(p > 0.0);
-      }
-      if (bad) {
-        atomicOr(A.bad_flag, 1u);
-        atomicMin(A.bad_idx, (unsigned long long)qi);
-      }
+      for (int v = 0; v < NV; ++v) acc[v * g.N + qi] = tot[v];
+      continue;
     }
+    const double J = CART ? g.cjac : g.jac[plin(g, c[0], c[1], c[2])];
+    stage_epilogue<ND, MIX, TA>(g, A, qi, J, tot);
   }
 }
 
@@ -573,12 +647,62 @@ __global__ void __launch_bounds__(256, sweep_min_blocks<ND, CART, T>()) k_gbr_sw
 // ---------------------------------------------------------------- CFL
 // T = double: the exact FP64 rate.  T = float (mixed form): the primitives
 // (pressure recovery) in FP64, the sound speed and the spectral radii in FP32.
+// The rate of node q from its primitives w: J sum_l (|xi_hat_l . u| + c |xi_hat_l|).
+template <int ND, bool CART, typename T>
+__device__ __forceinline__ T cfl_rate(const DevGrid& g, long long q, const T* w) {
+  constexpr int IP = ND + 1;
+  T cs = sqrt(gconst<T>(g.gamma, g.f_gamma) * T(w[IP]) / T(w[0]));
+  T s = T(0);
+  T J;
+  if (CART) {
+    J = gconst<T>(g.cjac, g.f_cjac);
+#pragma unroll
+    for (int l = 0; l < ND; ++l) {
+      const T xh = gconst<T>(g.cxh[l], g.f_cxh[l]);
+      T t = fabs(xh * T(w[1 + l])) + cs * sqrt(xh * xh);
+      s = (l == 0) ? t : s + t;
+    }
+  } else {
+    int c[3];
+    node_coords(g, q, c);
+    long long pq = plin(g, c[0], c[1], c[2]);
+    J = T(g.jac[pq]);
+#pragma unroll
+    for (int l = 0; l < ND; ++l) {
+      T dot = T(0), mag = T(0);
+#pragma unroll
+      for (int m = 0; m < ND; ++m) {
+        T x = T(g.xh[(l * ND + m) * g.NP + pq]);
+        dot = (m == 0) ? x * T(w[1 + m]) : dot + x * T(w[1 + m]);
+        mag = (m == 0) ? x * x : mag + x * x;
+      }
+      T t = fabs(dot) + cs * sqrt(mag);
+      s = (l == 0) ? t : s + t;
+    }
+  }
+  return J * s;
+}
+
+// Block maximum of the threads' rates, then one atomic (non-negative doubles
+// order like their bits).  The running maximum is kept in T: the largest
+// float converted once equals the largest of the converted floats.
+template <typename T>
+__device__ __forceinline__ void cfl_block_max(T best, unsigned long long* __restrict__ mx) {
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) best = dmax(best, __shfl_xor_sync(0xffffffffu, best, o));
+  const double bestd = double(best);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = bestd;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double b = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) b = dmax(b, __shfl_xor_sync(0xffffffffu, b, o));
+    if (threadIdx.x == 0) atomicMax(mx, (unsigned long long)__double_as_longlong(b));
+  }
+}
+
 template <int ND, bool CART, typename T = double>
 __device__ __forceinline__ void k_cfl_max_body(const VBlock& vb, const DevGrid& g, const double* __restrict__ U, unsigned long long* __restrict__ mx) {
-  constexpr int NV = ND + 2, IP = ND + 1;
-  // the running maximum in T: the largest float converted once equals the
-  // largest of the converted floats (conversion keeps order), so the FP32 form
-  // compares in FP32 and the FP64 form is unchanged
+  constexpr int NV = ND + 2;
   T best = T(0);
   for (long long q = vb.x * (long long)blockDim.x + threadIdx.x; q < g.N;
        q += (long long)vb.gx * blockDim.x) {
@@ -591,50 +715,36 @@ __device__ __forceinline__ void k_cfl_max_body(const VBlock& vb, const DevGrid& 
     } else {
       cons_to_prim<ND>(g.gm1, Q, w);
     }
-    T cs = sqrt(gconst<T>(g.gamma, g.f_gamma) * T(w[IP]) / T(w[0]));
-    T s = T(0);
-    T J;
-    if (CART) {
-      J = gconst<T>(g.cjac, g.f_cjac);
-#pragma unroll
-      for (int l = 0; l < ND; ++l) {
-        const T xh = gconst<T>(g.cxh[l], g.f_cxh[l]);
-        T t = fabs(xh * T(w[1 + l])) + cs * sqrt(xh * xh);
-        s = (l == 0) ? t : s + t;
-      }
-    } else {
-      int k = (int)(q / ((long long)g.n[0] * g.n[1]));
-      int j = (int)((q / g.n[0]) % g.n[1]);
-      int i = (int)(q % g.n[0]);
-      long long pq = plin(g, i, j, k);
-      J = T(g.jac[pq]);
-#pragma unroll
-      for (int l = 0; l < ND; ++l) {
-        T dot = T(0), mag = T(0);
-#pragma unroll
-        for (int m = 0; m < ND; ++m) {
-          T x = T(g.xh[(l * ND + m) * g.NP + pq]);
-          dot = (m == 0) ? x * T(w[1 + m]) : dot + x * T(w[1 + m]);
-          mag = (m == 0) ? x * x : mag + x * x;
-        }
-        T t = fabs(dot) + cs * sqrt(mag);
-        s = (l == 0) ? t : s + t;
-      }
-    }
-    T r = J * s;
+    T r = cfl_rate<ND, CART, T>(g, q, w);
     if (r > best) best = r;
   }
-  // block max, then one atomic (non-negative doubles order like their bits)
-  __shared__ double red[32];
-  for (int o = 16; o > 0; o >>= 1) best = dmax(best, __shfl_xor_sync(0xffffffffu, best, o));
-  const double bestd = double(best);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = bestd;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    double b = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) b = dmax(b, __shfl_xor_sync(0xffffffffu, b, o));
-    if (threadIdx.x == 0) atomicMax(mx, (unsigned long long)__double_as_longlong(b));
+  cfl_block_max<T>(best, mx);
+}
+
+// The first stage's primitives and the step's CFL maximum from one pass over
+// the state: the same recovery and the same rate as k_prim and k_cfl_max, so
+// the stored primitives and the step size are bitwise those of the two kernels.
+template <int ND, bool CART, typename TW = double>
+__global__ void k_prim_cfl(DevGrid g, const double* __restrict__ U, TW* __restrict__ W, unsigned long long* __restrict__ mx) {
+  constexpr int NV = ND + 2;
+  TW best = TW(0);
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < g.N;
+       q += (long long)gridDim.x * blockDim.x) {
+    double Q[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Q[v] = U[v * g.N + q];
+    TW w[NV];
+    if constexpr (sizeof(TW) == 4) {
+      cons_to_prim_mixed<ND>(g.gm1, Q, w);
+    } else {
+      cons_to_prim<ND>(g.gm1, Q, w);
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) W[v * g.N + q] = w[v];
+    TW r = cfl_rate<ND, CART, TW>(g, q, w);
+    if (r > best) best = r;
   }
+  cfl_block_max<TW>(best, mx);
 }
 
 template <int ND, bool CART, typename T = double>

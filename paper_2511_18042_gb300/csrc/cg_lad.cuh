@@ -41,6 +41,14 @@ __device__ __forceinline__ void lad_fields(const DevGrid& g, const T* w, T* f) {
 }
 
 __device__ __forceinline__ void box_coords(const Box& b, long long e, int* c) {
+  if (b.size() <= 0x7fffffffLL) {  // 32-bit division, as node_coords
+    const unsigned r = (unsigned)e, x0 = (unsigned)b.ext[0], x1 = (unsigned)b.ext[1];
+    const unsigned t = r / x0;
+    c[0] = (int)(r - t * x0) - b.off[0];
+    c[1] = (int)(t % x1) - b.off[1];
+    c[2] = (int)(t / x1) - b.off[2];
+    return;
+  }
   c[0] = (int)(e % b.ext[0]) - b.off[0];
   long long r = e / b.ext[0];
   c[1] = (int)(r % b.ext[1]) - b.off[1];
@@ -166,9 +174,7 @@ __device__ __forceinline__ void k_lad_coef_body(const VBlock& vb, const DevGrid&
   long long bs = b3.size(), fs = fbx.size();
   for (long long q = vb.x * (long long)blockDim.x + threadIdx.x; q < g.N; q += (long long)vb.gx * blockDim.x) {
     int c[3];
-    c[0] = (int)(q % g.n[0]);
-    c[1] = (int)((q / g.n[0]) % g.n[1]);
-    c[2] = (int)(q / ((long long)g.n[0] * g.n[1]));
+    node_coords(g, q, c);
     long long e0 = b3.at(c[0], c[1], c[2]);
     T w[NV];
 #pragma unroll
@@ -267,9 +273,7 @@ __device__ __forceinline__ void k_gauss_body(const VBlock& vb, const DevGrid& g,
           A4 = T(107.0 / 103680.0);
   for (long long q = vb.x * (long long)blockDim.x + threadIdx.x; q < g.N; q += (long long)vb.gx * blockDim.x) {
     int c[3];
-    c[0] = (int)(q % g.n[0]);
-    c[1] = (int)((q / g.n[0]) % g.n[1]);
-    c[2] = (int)(q / ((long long)g.n[0] * g.n[1]));
+    node_coords(g, q, c);
     long long s[9];
     if (c[l] >= 4 && c[l] < g.n[l] - 4) {  // interior stencil: the nodes themselves
       const long long st = l == 0 ? 1 : (l == 1 ? (long long)g.n[0] : (long long)g.n[0] * g.n[1]);
@@ -479,64 +483,27 @@ __global__ void k_lad_viscoef(DevGrid g, const T* __restrict__ W, const T* __res
 
 // Stage epilogue shared by the LAD divergence kernels: tot = acc + D (or D),
 // then store acc, R = -J tot, or the RK combination.
-// FUSED (mixed form): the FP64 accumulation and RK combination with explicit
-// fused multiply-adds; otherwise the oracle's operation order.
-// FUSED (the mixed form) also sums the directions' flux differences in FP32:
+// FUSED (mixed form): stage_epilogue's mixed update; otherwise the oracle's
+// operation order.  FUSED also sums the directions' flux differences in FP32:
 // acc then holds FP32 values (the buffer read as float), and only the stage
 // total enters the FP64 residual and update.
 template <int ND, bool FUSED = false, typename TD = double>
 __device__ __forceinline__ void lad_epilogue(const DevGrid& g, const StageArgs& A, long long qi, const int* c,
                                              const TD* Dv) {
-  constexpr int NV = ND + 2, IP = ND + 1;
+  constexpr int NV = ND + 2;
   static_assert(FUSED || sizeof(TD) == 8, "the FP64 form accumulates in FP64");
   using TA = typename std::conditional<FUSED, float, double>::type;
   TA* acc = reinterpret_cast<TA*>(A.acc);
-  double J = g.curv ? g.jac[plin(g, c[0], c[1], c[2])] : g.cjac;
-  double out[NV];
+  TA tot[NV];
 #pragma unroll
-  for (int v = 0; v < NV; ++v) {
-    TA tot = A.first ? TA(Dv[v]) : acc[v * g.N + qi] + TA(Dv[v]);
-    if (!A.last) {
-      acc[v * g.N + qi] = tot;
-      continue;
-    }
-    double r = -(J * double(tot));
-    if (!A.rk) {
-      A.R[v * g.N + qi] = r;
-      continue;
-    }
-    double dt = *A.dt;
-    double un = A.Un[v * g.N + qi];
-    double o;
-    if (FUSED) {
-      if (A.stage == 1) o = __fma_rn(dt, r, un);
-      else if (A.stage == 2) o = __fma_rn(0.75, un, 0.25 * __fma_rn(dt, r, A.Uc[v * g.N + qi]));
-      else o = __fma_rn(1.0 / 3.0, un, (2.0 / 3.0) * __fma_rn(dt, r, A.Uc[v * g.N + qi]));
-    } else if (A.stage == 1) o = un + dt * r;
-    else if (A.stage == 2) o = 0.75 * un + 0.25 * (A.Uc[v * g.N + qi] + dt * r);
-    else o = (1.0 / 3.0) * un + (2.0 / 3.0) * (A.Uc[v * g.N + qi] + dt * r);
-    out[v] = o;
-    A.Uout[v * g.N + qi] = o;
+  for (int v = 0; v < NV; ++v) tot[v] = A.first ? TA(Dv[v]) : acc[v * g.N + qi] + TA(Dv[v]);
+  if (!A.last) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v * g.N + qi] = tot[v];
+    return;
   }
-  if (A.last && A.rk && A.stage == 3) {
-    bool bad;
-    if (FUSED) {  // sign of rho p / (gamma-1) = rho E - |m|^2 / 2, no division
-      double m2 = out[1] * out[1];
-#pragma unroll
-      for (int m = 1; m < ND; ++m) m2 = __fma_rn(out[1 + m], out[1 + m], m2);
-      bad = !(out[0] > 0.0) || !(__fma_rn(out[0], out[IP], -0.5 * m2) > 0.0);
-    } else {
-      double ke = out[1] * (out[1] / out[0]);
-#pragma unroll
-      for (int m = 1; m < ND; ++m) ke = ke + out[1 + m] * (out[1 + m] / out[0]);
-      double p = g.gm1 * (out[IP] - 0.5 * ke);
-      bad = !(out[0] > 0.0) || !(p > 0.0);
-    }
-    if (bad) {
-      atomicOr(A.bad_flag, 1u);
-      atomicMin(A.bad_idx, (unsigned long long)qi);
-    }
-  }
+  const double J = g.curv ? g.jac[plin(g, c[0], c[1], c[2])] : g.cjac;
+  stage_epilogue<ND, FUSED, TA>(g, A, qi, J, tot);
 }
 
 // E4 divergence of the node fluxes along l (explicit) or the compact result D.
@@ -548,9 +515,7 @@ __global__ void k_lad_div(DevGrid g, int l, const T* __restrict__ Fn, Box fb, co
   long long fs = fb.size();
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < g.N; q += (long long)gridDim.x * blockDim.x) {
     int c[3];
-    c[0] = (int)(q % g.n[0]);
-    c[1] = (int)((q / g.n[0]) % g.n[1]);
-    c[2] = (int)(q / ((long long)g.n[0] * g.n[1]));
+    node_coords(g, q, c);
     T Dv[NV];
     if (D) {
 #pragma unroll

@@ -251,8 +251,7 @@ static int lad_stage(cg_solver* s, const double* Uc, StageArgs A, cudaStream_t s
 template <int ND, typename T>
 static int lad_stage_t(cg_solver* s, const double* Uc, StageArgs A, cudaStream_t st) {
   int sch = s->p.scheme;
-  k_prim<ND, T><<<grid_blocks(s->N, 256), 256, 0, st>>>(s->dg, Uc, reinterpret_cast<T*>(s->W));
-  s->launches++;
+  launch_prim<ND>(s, Uc, st);  // T is the precision's type
   if (sch == CG_LAD_E4 || sch == CG_LAD_C6) return lad_pass<ND, T>(s, sch == CG_LAD_E4 ? 2 : 3, A, st, nullptr, 0);
   LadBuffers& L = s->lad;
   CG_CUDA(cudaMemsetAsync(s->hyb_flag, 0, sizeof(int), st));

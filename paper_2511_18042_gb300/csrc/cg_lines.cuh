@@ -556,9 +556,7 @@ __global__ void k_filter_store(DevGrid g, const double* __restrict__ x, LineBuf 
   constexpr int NV = ND + 2;
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < g.N; q += (long long)gridDim.x * blockDim.x) {
     int c[3];
-    c[0] = (int)(q % g.n[0]);
-    c[1] = (int)((q / g.n[0]) % g.n[1]);
-    c[2] = (int)(q / ((long long)g.n[0] * g.n[1]));
+    node_coords(g, q, c);
     const double J = g.curv ? g.jac[plin(g, c[0], c[1], c[2])] : 1.0;
 #pragma unroll
     for (int v = 0; v < NV; ++v) U[v * g.N + q] = g.curv ? x[lb.at(v, c[lb.d], c)] * J : x[lb.at(v, c[lb.d], c)];
