@@ -637,6 +637,18 @@ struct TimedRegion {
 template <int ND, bool CART, bool COMPACT>
 static void launch_omega(cg_solver* s, cudaStream_t st, const int* guard, int want) {
   long long tot = s->omBox.size();
+  if constexpr (ND >= 2 && !COMPACT) {
+    const Box& ob = s->omBox;
+    dim3 grid((unsigned)((ob.ext[0] + OMT_X - 1) / OMT_X), (unsigned)((ob.ext[1] + OMT_Y - 1) / OMT_Y),
+              ND == 3 ? (unsigned)ob.ext[2] : 1u);
+    if (s->p.precision == CG_MIXED)
+      k_omega_tile<ND, CART, float><<<grid, dim3(OMT_X, OMT_Y), 0, st>>>(
+          s->dg, reinterpret_cast<const float*>(s->W), reinterpret_cast<float*>(s->om), ob, guard, want);
+    else
+      k_omega_tile<ND, CART, double><<<grid, dim3(OMT_X, OMT_Y), 0, st>>>(s->dg, s->W, s->om, ob, guard, want);
+    s->launches++;
+    return;
+  }
   if (s->p.precision == CG_MIXED)
     k_omega<ND, CART, COMPACT, float><<<grid_blocks(tot, 128), 128, 0, st>>>(
         s->dg, reinterpret_cast<const float*>(s->W), reinterpret_cast<const float*>(s->G[0]),

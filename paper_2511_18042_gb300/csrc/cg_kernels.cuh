@@ -186,11 +186,68 @@ __global__ void k_prim(DevGrid g, const double* __restrict__ U, TW* __restrict__
 }
 
 // ---------------------------------------------------------------- sensor
+// Quotient of the sensor's ratios: IEEE division in FP64; in the mixed form's
+// FP32 sensor the fast reciprocal-multiply (2 ulp, denominators below 2^126:
+// sums of pressures and of squared velocity gradients).
+template <typename T>
+__device__ __forceinline__ T sensor_div(T a, T b) {
+  if constexpr (sizeof(T) == 4) return __fdividef(a, b);
+  else return a / b;
+}
+
 // Omega^d = phi * zeta on the box [-4, n+3]: phi the largest normalised
 // pressure second difference over the directions, zeta a Ducros ratio of the
 // dilatation (one in irrotational dilatation-free flow).
 // T = double: FP64 parity form; T = float: the mixed form's FP32 sensor
 // (FP64 primitives and gradients read, converted once).
+// Ducros ratio zeta = (div^2 + eps) / (div^2 + |curl|^2 + eps) from the
+// physical velocity gradients gu[k][m] = d u_k / d x_m.
+template <int ND, typename T>
+__device__ __forceinline__ T sensor_zeta(const T (&gu)[3][3]) {
+  T div = gu[0][0];
+#pragma unroll
+  for (int k = 1; k < ND; ++k) div = div + gu[k][k];
+  const T eps = T(1e-32);
+  if (ND == 1) return sensor_div(div * div + eps, div * div + eps);
+  if (ND == 2) {
+    T w3 = gu[1][0] - gu[0][1];
+    return sensor_div(div * div + eps, div * div + w3 * w3 + eps);
+  }
+  T w1 = gu[2][1] - gu[1][2], w2 = gu[0][2] - gu[2][0], w3 = gu[1][0] - gu[0][1];
+  return sensor_div(div * div + eps, div * div + (w1 * w1 + w2 * w2 + w3 * w3) + eps);
+}
+
+// Physical velocity gradients gu[k][m] = sum_l (J xi_hat[l][m]) du[l][k] from
+// the index-space ones du[l][k] = d u_k / d xi_l at node c.
+template <int ND, bool CART, typename T>
+__device__ __forceinline__ void sensor_gu(const DevGrid& g, const int* c, const T (&du)[3][3], T (&gu)[3][3]) {
+  if (CART) {
+#pragma unroll
+    for (int k = 0; k < ND; ++k)
+#pragma unroll
+      for (int m = 0; m < ND; ++m) gu[k][m] = T(g.cjac * g.cxh[m]) * du[m][k];
+  } else {
+    long long pq = plin(g, c[0], c[1], c[2]);
+    // J xi_hat: in the mixed form each factor is rounded to FP32 and the
+    // product taken there (FP32 arithmetic, two conversions, no FP64 multiply)
+    const T J = T(g.jac[pq]);
+    T xm[3][3];
+#pragma unroll
+    for (int l = 0; l < ND; ++l)
+#pragma unroll
+      for (int m = 0; m < ND; ++m) xm[l][m] = J * T(g.xh[(l * ND + m) * g.NP + pq]);
+#pragma unroll
+    for (int k = 0; k < ND; ++k)
+#pragma unroll
+      for (int m = 0; m < ND; ++m) {
+        T s = xm[0][m] * du[0][k];
+#pragma unroll
+        for (int l = 1; l < ND; ++l) s = s + xm[l][m] * du[l][k];
+        gu[k][m] = s;
+      }
+  }
+}
+
 template <int ND, bool CART, bool COMPACT, typename T = double>
 __device__ __forceinline__ void k_omega_body(const VBlock& vb, const DevGrid& g, const T* __restrict__ W, const T* __restrict__ G0,
                         const T* __restrict__ G1, const T* __restrict__ G2, LineBuf gb0,
@@ -231,7 +288,7 @@ __device__ __forceinline__ void k_omega_body(const VBlock& vb, const DevGrid& g,
         const long long st = l == 0 ? 1 : (l == 1 ? (long long)g.n[0] : (long long)g.n[0] * g.n[1]);
         const T* P = W + IP * g.N + q;
         const T pm = T(P[-st]), pp = T(P[st]);
-        T a = fabs(pp - T(2.0) * p0 + pm) / (pp + T(2.0) * p0 + pm);
+        T a = sensor_div(fabs(pp - T(2.0) * p0 + pm), pp + T(2.0) * p0 + pm);
         if (a > phi) phi = a;
         if (!COMPACT) {
 #pragma unroll
@@ -265,7 +322,7 @@ __device__ __forceinline__ void k_omega_body(const VBlock& vb, const DevGrid& g,
         load_state<ND, false, T, T>(g, W, a[0], a[1], a[2], s[t]);
       }
       const T pm = T(s[2][IP]), pp = T(s[3][IP]);
-      T a = fabs(pp - T(2.0) * p0 + pm) / (pp + T(2.0) * p0 + pm);
+      T a = sensor_div(fabs(pp - T(2.0) * p0 + pm), pp + T(2.0) * p0 + pm);
       if (a > phi) phi = a;
       if (!COMPACT) {
 #pragma unroll
@@ -280,48 +337,9 @@ __device__ __forceinline__ void k_omega_body(const VBlock& vb, const DevGrid& g,
       }
     }
     }
-    // physical velocity gradients gu[k][m] = sum_l (J xi_hat[l][m]) du[l][k]
     T gu[3][3];
-    if (CART) {
-#pragma unroll
-      for (int k = 0; k < ND; ++k)
-#pragma unroll
-        for (int m = 0; m < ND; ++m) gu[k][m] = T(g.cjac * g.cxh[m]) * du[m][k];
-    } else {
-      long long pq = plin(g, c[0], c[1], c[2]);
-      // J xi_hat: in the mixed form each factor is rounded to FP32 and the
-      // product taken there (FP32 arithmetic, two conversions, no FP64 multiply)
-      const T J = T(g.jac[pq]);
-      T xm[3][3];
-#pragma unroll
-      for (int l = 0; l < ND; ++l)
-#pragma unroll
-        for (int m = 0; m < ND; ++m) xm[l][m] = J * T(g.xh[(l * ND + m) * g.NP + pq]);
-#pragma unroll
-      for (int k = 0; k < ND; ++k)
-#pragma unroll
-        for (int m = 0; m < ND; ++m) {
-          T s = xm[0][m] * du[0][k];
-#pragma unroll
-          for (int l = 1; l < ND; ++l) s = s + xm[l][m] * du[l][k];
-          gu[k][m] = s;
-        }
-    }
-    T div = gu[0][0];
-#pragma unroll
-    for (int k = 1; k < ND; ++k) div = div + gu[k][k];
-    const T eps = T(1e-32);
-    T zeta;
-    if (ND == 1) {
-      zeta = (div * div + eps) / (div * div + eps);
-    } else if (ND == 2) {
-      T w3 = gu[1][0] - gu[0][1];
-      zeta = (div * div + eps) / (div * div + w3 * w3 + eps);
-    } else {
-      T w1 = gu[2][1] - gu[1][2], w2 = gu[0][2] - gu[2][0], w3 = gu[1][0] - gu[0][1];
-      zeta = (div * div + eps) / (div * div + (w1 * w1 + w2 * w2 + w3 * w3) + eps);
-    }
-    om[ob.at(c[0], c[1], c[2])] = phi * zeta;
+    sensor_gu<ND, CART, T>(g, c, du, gu);
+    om[ob.at(c[0], c[1], c[2])] = phi * sensor_zeta<ND, T>(gu);
   }
 }
 
@@ -330,6 +348,95 @@ __global__ void k_omega(DevGrid g, const T* __restrict__ W, const T* __restrict_
                         const T* __restrict__ G1, const T* __restrict__ G2, LineBuf gb0,
                         LineBuf gb1, LineBuf gb2, T* __restrict__ om, Box ob, const int* guard, int want) {
   k_omega_body<ND, CART, COMPACT, T>(hw_block(), g, W, G0, G1, G2, gb0, gb1, gb2, om, ob, guard, want);
+}
+
+// The sensor of explicit gradients (MEG6) in 2D and 3D on tiles of 32 x 8
+// nodes of the box (one z plane per block in 3D): pressure and velocities of
+// the tile and a halo of three nodes in x and y staged once in shared memory
+// (ghost positions through the boundary mapping, as load_state gives them),
+// the z neighbours read directly.  The same values and the same arithmetic in
+// the same order as k_omega_body, with one global load per staged value
+// instead of one per stencil point.
+constexpr int OMT_X = 32, OMT_Y = 8, OMT_H = 3;
+template <int ND, bool CART, typename T>
+__global__ void __launch_bounds__(OMT_X * OMT_Y) k_omega_tile(DevGrid g, const T* __restrict__ W, T* __restrict__ om, Box ob,
+                                                             const int* guard, int want) {
+  static_assert(ND >= 2, "tiles of x and y");
+  constexpr int NV = ND + 2, IP = ND + 1;
+  constexpr int SX = OMT_X + 2 * OMT_H, SY = OMT_Y + 2 * OMT_H;
+  __shared__ T sP[SY][SX];
+  __shared__ T sU[ND][SY][SX];
+  if (guard && *guard != want) return;
+  const int x0 = (int)blockIdx.x * OMT_X - ob.off[0], y0 = (int)blockIdx.y * OMT_Y - ob.off[1];
+  const int cz = ND == 3 ? (int)blockIdx.z - ob.off[2] : 0;
+  const bool zin = cz >= 0 && cz < (ND == 3 ? g.n[2] : 1);
+  const int tid = threadIdx.y * OMT_X + threadIdx.x;
+  for (int e = tid; e < SX * SY; e += OMT_X * OMT_Y) {
+    const int sy = e / SX, sx = e - sy * SX;
+    const int x = x0 - OMT_H + sx, y = y0 - OMT_H + sy;
+    T w[NV];
+    if (zin && x >= 0 && x < g.n[0] && y >= 0 && y < g.n[1]) {
+      const long long q = lin(g, x, y, cz);
+#pragma unroll
+      for (int v = 1; v < NV; ++v) w[v] = W[v * g.N + q];
+    } else {
+      load_state<ND, false, T, T>(g, W, x, y, cz, w);
+    }
+    sP[sy][sx] = w[IP];
+#pragma unroll
+    for (int k = 0; k < ND; ++k) sU[k][sy][sx] = w[1 + k];
+  }
+  __syncthreads();
+  const int ex = (int)blockIdx.x * OMT_X + threadIdx.x, ey = (int)blockIdx.y * OMT_Y + threadIdx.y;
+  if (ex >= ob.ext[0] || ey >= ob.ext[1]) return;
+  int c[3] = {x0 + (int)threadIdx.x, y0 + (int)threadIdx.y, cz};
+  const int tx = threadIdx.x + OMT_H, ty = threadIdx.y + OMT_H;
+  const T p0 = sP[ty][tx];
+  T phi = T(0);
+  T du[3][3];
+  {  // x
+    const T pm = sP[ty][tx - 1], pp = sP[ty][tx + 1];
+    T a = sensor_div(fabs(pp - T(2.0) * p0 + pm), pp + T(2.0) * p0 + pm);
+    if (a > phi) phi = a;
+#pragma unroll
+    for (int k = 0; k < ND; ++k)
+      du[0][k] = d6<T>(sU[k][ty][tx - 3], sU[k][ty][tx - 2], sU[k][ty][tx - 1], sU[k][ty][tx + 1], sU[k][ty][tx + 2],
+                       sU[k][ty][tx + 3]);
+  }
+  {  // y
+    const T pm = sP[ty - 1][tx], pp = sP[ty + 1][tx];
+    T a = sensor_div(fabs(pp - T(2.0) * p0 + pm), pp + T(2.0) * p0 + pm);
+    if (a > phi) phi = a;
+#pragma unroll
+    for (int k = 0; k < ND; ++k)
+      du[1][k] = d6<T>(sU[k][ty - 3][tx], sU[k][ty - 2][tx], sU[k][ty - 1][tx], sU[k][ty + 1][tx], sU[k][ty + 2][tx],
+                       sU[k][ty + 3][tx]);
+  }
+  if constexpr (ND == 3) {  // z: direct loads in the interior, the boundary mapping elsewhere
+    T s[6][NV];
+    const bool inner = c[0] >= 0 && c[0] < g.n[0] && c[1] >= 0 && c[1] < g.n[1] && c[2] >= 3 && c[2] < g.n[2] - 3;
+    if (inner) {
+      const long long q = lin(g, c[0], c[1], c[2]), st = (long long)g.n[0] * g.n[1];
+#pragma unroll
+      for (int t = 0; t < 6; ++t) {
+        const long long qt = q + (long long)(t < 3 ? t - 3 : t - 2) * st;
+#pragma unroll
+        for (int v = 1; v < NV; ++v) s[t][v] = W[v * g.N + qt];
+      }
+    } else {
+#pragma unroll 1
+      for (int t = 0; t < 6; ++t) load_state<ND, false, T, T>(g, W, c[0], c[1], c[2] + (t < 3 ? t - 3 : t - 2), s[t]);
+    }
+    const T pm = s[2][IP], pp = s[3][IP];
+    T a = sensor_div(fabs(pp - T(2.0) * p0 + pm), pp + T(2.0) * p0 + pm);
+    if (a > phi) phi = a;
+#pragma unroll
+    for (int k = 0; k < ND; ++k)
+      du[2][k] = d6<T>(s[0][1 + k], s[1][1 + k], s[2][1 + k], s[3][1 + k], s[4][1 + k], s[5][1 + k]);
+  }
+  T gu[3][3];
+  sensor_gu<ND, CART, T>(g, c, du, gu);
+  om[ob.at(c[0], c[1], c[2])] = phi * sensor_zeta<ND, T>(gu);
 }
 
 // ---------------------------------------------------------------- compact gradients
