@@ -240,6 +240,9 @@ struct cg_solver {
   bool prim_cfl = false;
   double* prim_cfl_dt = nullptr;
   double* prim_cfl_t = nullptr;
+  // set by the mixed form's deferred stage update: W already holds the
+  // primitives of the next stage's state, so its primitive launch is skipped
+  bool prim_ready = false;
   unsigned int* bad_flag = nullptr;
   unsigned long long* bad_idx = nullptr;
   long long launches = 0;
@@ -338,6 +341,8 @@ static void fill_devgrid(const cg_grid* g, const cg_params* p, DevGrid& d) {
   d.f_gm2 = (float)d.gm2;
   d.f_cjac = (float)d.cjac;
   for (int k = 0; k < 3; ++k) {
+    d.cjxh[k] = d.cjac * d.cxh[k];
+    d.f_cjxh[k] = (float)d.cjxh[k];
     d.f_cxh[k] = (float)d.cxh[k];
     d.f_ch[k] = (float)d.ch[k];
     d.f_cg2[k] = (float)d.cg2[k];
@@ -783,6 +788,10 @@ static void launch_rhs_filter(const DevGrid& g, const double* U, const LineBuf& 
 template <int ND>
 static void launch_prim(cg_solver* s, const double* Uc, cudaStream_t st) {
   const bool mixed = s->p.precision == CG_MIXED;
+  if (s->prim_ready) {
+    s->prim_ready = false;
+    return;
+  }
   if (s->prim_cfl) {
     s->prim_cfl = false;
     cudaMemsetAsync(s->cflmax, 0, sizeof(unsigned long long), st);
@@ -892,7 +901,30 @@ static int lad_filter(cg_solver* s, double* U, cudaStream_t st);
 static int lad_alloc(cg_solver* s);
 static void lad_free(LadBuffers& b);
 
-// RHS or RK stage: out = R (rk = 0) or the stage combination (rk = 1)
+// The mixed form's deferred update of stage stage_no (k_stage_update, the
+// increment form of TVD-RK3, its FP32 increment sum in the U1 buffer); before
+// stage 3 it writes the next stage's primitives into W instead of a state.
+template <int ND>
+static void launch_update(cg_solver* s, const StageArgs& A, int stage_no, cudaStream_t st) {
+  const bool next = stage_no < 3;
+  float* Z = reinterpret_cast<float*>(s->U1);
+  float* Wn = reinterpret_cast<float*>(s->W);
+  const int nb = grid_blocks(s->N, 256);
+  auto go = [&](auto cart) {
+    constexpr bool C = decltype(cart)::value;
+    if (stage_no == 1) k_stage_update<ND, C, 1><<<nb, 256, 0, st>>>(s->dg, A, Z, Wn);
+    else if (stage_no == 2) k_stage_update<ND, C, 2><<<nb, 256, 0, st>>>(s->dg, A, Z, Wn);
+    else k_stage_update<ND, C, 3><<<nb, 256, 0, st>>>(s->dg, A, Z, Wn);
+  };
+  if (s->dg.curv) go(std::false_type{});
+  else go(std::true_type{});
+  s->launches++;
+  s->prim_ready = next;
+}
+
+// RHS or RK stage: out = R (rk = 0) or the stage combination (rk = 1).  In the
+// mixed form an RK stage's fluxes only sum into acc, and k_stage_update
+// applies the FP64 residual and update as a pass of its own.
 template <int ND>
 static int stage(cg_solver* s, const double* Uc, const double* Un, double* out, int rk, int stage_no,
                  cudaStream_t st) {
@@ -904,23 +936,48 @@ static int stage(cg_solver* s, const double* Uc, const double* Un, double* out, 
   A.Un = Un;
   A.Uc = Uc;
   A.Uout = out;
+  A.defer = (rk && s->p.precision == CG_MIXED) ? 1 : 0;
+  // the deferred stages 2 and 3 start from the primitives the previous update wrote
+  if (A.defer && stage_no > 1 && !s->prim_ready) return fail(CG_ERR_UNSUPPORTED, "stage %d has no primitives", stage_no);
+  int rc;
   if (sch == CG_MEG6 || sch == CG_MIG4) {
     bool compact = sch == CG_MIG4;
     stage_prep_gbr<ND>(s, Uc, compact, st);
     if (s->p.viscous) visc_pass_any<ND>(s, A, st, false, nullptr, 0);
-    return gbr_sweeps<ND>(s, compact, A, st, !s->p.viscous);
+    rc = gbr_sweeps<ND>(s, compact, A, st, !s->p.viscous);
+  } else {
+    rc = lad_stage<ND>(s, Uc, A, st);
   }
-  return lad_stage<ND>(s, Uc, A, st);
+  if (rc) return rc;
+  if (A.defer) launch_update<ND>(s, A, stage_no, st);
+  return CG_OK;
 }
 
+// In the mixed form the stage states u1, u2 are not stored (k_stage_update
+// hands their primitives on in W), so stages 2 and 3 name U as their state.
 template <int ND>
-static int rk3(cg_solver* s, double* U, cudaStream_t st) {
+static int rk3_stages(cg_solver* s, double* U, cudaStream_t st) {
   int rc;
+  if (s->p.precision == CG_MIXED) {
+    if ((rc = stage<ND>(s, U, U, U, 1, 1, st))) return rc;
+    if ((rc = stage<ND>(s, U, U, U, 1, 2, st))) return rc;
+    if ((rc = stage<ND>(s, U, U, U, 1, 3, st))) return rc;
+    if (s->p.scheme == CG_LAD_C6 && s->p.filter_on) return lad_filter<ND>(s, U, st);
+    return CG_OK;
+  }
   if ((rc = stage<ND>(s, U, U, s->U1, 1, 1, st))) return rc;
   if ((rc = stage<ND>(s, s->U1, U, s->U2, 1, 2, st))) return rc;
   if ((rc = stage<ND>(s, s->U2, U, U, 1, 3, st))) return rc;
   if (s->p.scheme == CG_LAD_C6 && s->p.filter_on) return lad_filter<ND>(s, U, st);
   return CG_OK;
+}
+
+template <int ND>
+static int rk3(cg_solver* s, double* U, cudaStream_t st) {
+  s->prim_ready = false;
+  int rc = rk3_stages<ND>(s, U, st);
+  s->prim_ready = false;
+  return rc;
 }
 
 // The CFL step and one RK3 step with its dt: stage 1's primitive launch
@@ -929,18 +986,20 @@ static int rk3(cg_solver* s, double* U, cudaStream_t st) {
 // followed by rk3.
 template <int ND>
 static int rk3_cfl(cg_solver* s, double* U, double* dt_dev, double* t_dev, cudaStream_t st) {
+  s->prim_ready = false;
   s->prim_cfl = true;
   s->prim_cfl_dt = dt_dev;
   s->prim_cfl_t = t_dev;
-  int rc = stage<ND>(s, U, U, s->U1, 1, 1, st);
+  const bool mixed = s->p.precision == CG_MIXED;
+  int rc = stage<ND>(s, U, U, mixed ? U : s->U1, 1, 1, st);
   const bool unused = s->prim_cfl;
   s->prim_cfl = false;
-  if (rc) return rc;
-  if (unused) return fail(CG_ERR_UNSUPPORTED, "stage 1 launched no primitive kernel");
-  if ((rc = stage<ND>(s, s->U1, U, s->U2, 1, 2, st))) return rc;
-  if ((rc = stage<ND>(s, s->U2, U, U, 1, 3, st))) return rc;
-  if (s->p.scheme == CG_LAD_C6 && s->p.filter_on) return lad_filter<ND>(s, U, st);
-  return CG_OK;
+  if (!rc && unused) rc = fail(CG_ERR_UNSUPPORTED, "stage 1 launched no primitive kernel");
+  if (!rc) rc = stage<ND>(s, mixed ? U : s->U1, U, mixed ? U : s->U2, 1, 2, st);
+  if (!rc) rc = stage<ND>(s, mixed ? U : s->U2, U, U, 1, 3, st);
+  if (!rc && s->p.scheme == CG_LAD_C6 && s->p.filter_on) rc = lad_filter<ND>(s, U, st);
+  s->prim_ready = false;
+  return rc;
 }
 
 template <int ND>

@@ -30,6 +30,7 @@ struct DevGrid {
   // Cartesian constants
   double cxh[3];    // node metric xi_hat[l][l]
   double cjac;      // J
+  double cjxh[3];   // J xi_hat[l][l] (the product, as the sensor forms it)
   double ch[3];     // spacing (LAD displacement |Delta x_l|)
   // per-direction interface frame of a Cartesian grid (computed on the host
   // with the same operations as the per-interface frame of a curvilinear one)
@@ -52,7 +53,7 @@ struct DevGrid {
   // FP32 copies of the constants the mixed form's kernels use, rounded once on
   // the host: a conversion in the kernel would run on the FP64 pipe
   float f_gamma, f_gm1, f_gm2;
-  float f_cxh[3], f_cjac, f_ch[3];
+  float f_cxh[3], f_cjac, f_ch[3], f_cjxh[3];
   float f_cg2[3], f_cg[3], f_cig2[3];
   float f_cn[3][3], f_ct1[3][3], f_ct2[3][3];
 };
@@ -216,6 +217,13 @@ __device__ __forceinline__ double f2d_int(float x) {
     return __hiloint2double((int)((b & 0x80000000u) | (((b >> 3) & 0x0fffffffu) + (896u << 20))), (int)(b << 29));
   if ((b & 0x7fffffffu) == 0u) return __hiloint2double((int)(b & 0x80000000u), 0);
   return f2d_slow(x);
+}
+
+// A stored FP64 value in the arithmetic type T (the FP32 image through d2f_int).
+template <typename T>
+__device__ __forceinline__ T to_t(double x) {
+  if constexpr (sizeof(T) == 4) return d2f_int(x);
+  else return x;
 }
 
 // The mixed form's recovery: FP64 arithmetic for the cancellation in

@@ -25,6 +25,8 @@ struct StageArgs {
   LineBuf gdLB;
   double* acc;         // flux-difference accumulator (nv planes)
   int first, last;     // first / last direction of the stage
+  int defer;           // the last direction stores the total like the others; k_stage_update
+                       // applies the residual and RK update afterwards
   int rk;              // last direction: 1 = RK update, 0 = write R
   int stage;           // 1, 2, 3
   double* R;
@@ -78,12 +80,14 @@ __device__ __forceinline__ bool mixed_nonphysical(const double* out) {
 // formulas per value would issue all of them on the FP64 pipe.
 // * FP64 form: the oracle's operation order, r = -(J tot), then
 //   Un + dt r, or a Un + b (Uc + dt r).
-// * mixed form: the RK weights folded into one factor per node,
-//   U = a Un + b Uc - (b dt J) tot (Un alone in stage 1): one multiply and two
-//   multiply-adds per variable, the total widened on the integer pipes.
+// * mixed form: the stage increment z = -(b dt J) tot formed in FP32 (the
+//   precision of the FP32 total itself: the factor adds a relative 2e-7),
+//   widened on the integer pipes, and accumulated in FP64:
+//   U = a Un + b Uc + z (Un + z in stage 1), one FP64 add or two fused
+//   multiply-adds per variable.
 template <int ND, bool MIX, typename TA>
 __device__ __forceinline__ void stage_epilogue(const DevGrid& g, const StageArgs& A, long long qi, double J,
-                                               const TA* tot) {
+                                               const TA* tot, double (&out)[ND + 2]) {
   constexpr int NV = ND + 2, IP = ND + 1;
   auto wide = [](TA t) -> double {
     if constexpr (MIX) return f2d_int(t);
@@ -95,14 +99,14 @@ __device__ __forceinline__ void stage_epilogue(const DevGrid& g, const StageArgs
     return;
   }
   const double dt = *A.dt;
-  double out[NV];
   if (A.stage == 1) {
-    const double cJ = -dt * J;
+    [[maybe_unused]] float cJf = 0.f;
+    if constexpr (MIX) cJf = -(d2f_int(dt) * d2f_int(J));
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       const double un = A.Un[v * g.N + qi];
       if constexpr (MIX) {
-        out[v] = __fma_rn(cJ, wide(tot[v]), un);
+        out[v] = un + f2d_int(cJf * tot[v]);
       } else {
         const double r = -(J * wide(tot[v]));
         out[v] = un + dt * r;
@@ -112,12 +116,13 @@ __device__ __forceinline__ void stage_epilogue(const DevGrid& g, const StageArgs
     return;
   }
   const double ca = A.stage == 2 ? 0.75 : (1.0 / 3.0), cb = A.stage == 2 ? 0.25 : (2.0 / 3.0);
-  const double cJ = -(cb * dt) * J;
+  [[maybe_unused]] float cJf = 0.f;
+  if constexpr (MIX) cJf = -((A.stage == 2 ? 0.25f : (2.0f / 3.0f)) * d2f_int(dt)) * d2f_int(J);
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
     const double un = A.Un[v * g.N + qi], uc = A.Uc[v * g.N + qi];
     if constexpr (MIX) {
-      out[v] = __fma_rn(ca, un, __fma_rn(cb, uc, cJ * wide(tot[v])));
+      out[v] = __fma_rn(ca, un, __fma_rn(cb, uc, f2d_int(cJf * tot[v])));
     } else {
       const double r = -(J * wide(tot[v]));
       out[v] = ca * un + cb * (uc + dt * r);
@@ -225,17 +230,17 @@ __device__ __forceinline__ void sensor_gu(const DevGrid& g, const int* c, const 
 #pragma unroll
     for (int k = 0; k < ND; ++k)
 #pragma unroll
-      for (int m = 0; m < ND; ++m) gu[k][m] = T(g.cjac * g.cxh[m]) * du[m][k];
+      for (int m = 0; m < ND; ++m) gu[k][m] = gconst<T>(g.cjxh[m], g.f_cjxh[m]) * du[m][k];
   } else {
     long long pq = plin(g, c[0], c[1], c[2]);
-    // J xi_hat: in the mixed form each factor is rounded to FP32 and the
-    // product taken there (FP32 arithmetic, two conversions, no FP64 multiply)
-    const T J = T(g.jac[pq]);
+    // J xi_hat: in the mixed form each factor is rounded to FP32 (on the
+    // integer pipes) and the product taken there
+    const T J = to_t<T>(g.jac[pq]);
     T xm[3][3];
 #pragma unroll
     for (int l = 0; l < ND; ++l)
 #pragma unroll
-      for (int m = 0; m < ND; ++m) xm[l][m] = J * T(g.xh[(l * ND + m) * g.NP + pq]);
+      for (int m = 0; m < ND; ++m) xm[l][m] = J * to_t<T>(g.xh[(l * ND + m) * g.NP + pq]);
 #pragma unroll
     for (int k = 0; k < ND; ++k)
 #pragma unroll
@@ -508,6 +513,33 @@ __device__ __forceinline__ void k_gbr_sweep_body(const VBlock& vb, const DevGrid
   auto IX = [](int v, int r, int l, int rows) {
     return DIR == 0 ? (v * LW + l) * rows + r : (v * rows + r) * LW + l;
   };
+  // The mixed form in 2D (four FP32 components, 16 bytes a node) keeps the
+  // staged arrays node-major and moves a node's components with one 16-byte
+  // shared-memory access (consecutive threads take consecutive nodes, so the
+  // accesses stay free of bank conflicts); the other forms keep one plane per
+  // component.
+  constexpr bool VEC = MIX && NV == 4;
+  auto NX = [](int r, int l, int rows) { return DIR == 0 ? l * rows + r : r * LW + l; };
+  auto ldn = [&](const T* arr, int r, int l, int rows, T* w) {
+    if constexpr (VEC) {
+      const float4 f = reinterpret_cast<const float4*>(arr)[NX(r, l, rows)];
+      w[0] = f.x;
+      w[1] = f.y;
+      w[2] = f.z;
+      w[3] = f.w;
+    } else {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) w[v] = arr[IX(v, r, l, rows)];
+    }
+  };
+  auto stn = [&](T* arr, int r, int l, int rows, const T* w) {
+    if constexpr (VEC) {
+      reinterpret_cast<float4*>(arr)[NX(r, l, rows)] = make_float4(w[0], w[1], w[2], w[3]);
+    } else {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) arr[IX(v, r, l, rows)] = w[v];
+    }
+  };
   if (A.guard && *A.guard != A.guard_want) return;
   const int tid = threadIdx.x;
   const int n = g.n[DIR];
@@ -608,8 +640,7 @@ __device__ __forceinline__ void k_gbr_sweep_body(const VBlock& vb, const DevGrid
 #pragma unroll
         for (int v = 0; v < NV; ++v) w[v] = T(1);
       }
-#pragma unroll
-      for (int v = 0; v < NV; ++v) sW[IX(v, r, l, RW)] = w[v];
+      stn(sW, r, l, RW, w);
     }
     // sensor window values
     for (int e = tid; e < RO * LW; e += blockDim.x) {
@@ -625,30 +656,41 @@ __device__ __forceinline__ void k_gbr_sweep_body(const VBlock& vb, const DevGrid
     for (int e = tid; e < RD * LW; e += blockDim.x) {
       int r = DIR == 0 ? e % RD : e / LW;
       int l = DIR == 0 ? e / RD : e % LW;
+      T d[NV];
       if (!COMPACT) {
+        T m3[NV], m2[NV], m1[NV], p1[NV], p2[NV], p3[NV];
+        ldn(sW, r, l, RW, m3);
+        ldn(sW, r + 1, l, RW, m2);
+        ldn(sW, r + 2, l, RW, m1);
+        ldn(sW, r + 4, l, RW, p1);
+        ldn(sW, r + 5, l, RW, p2);
+        ldn(sW, r + 6, l, RW, p3);
 #pragma unroll
-        for (int v = 0; v < NV; ++v)
-          sD[IX(v, r, l, RD)] = d6(sW[IX(v, r, l, RW)], sW[IX(v, r + 1, l, RW)], sW[IX(v, r + 2, l, RW)],
-                                   sW[IX(v, r + 4, l, RW)], sW[IX(v, r + 5, l, RW)], sW[IX(v, r + 6, l, RW)]);
+        for (int v = 0; v < NV; ++v) d[v] = d6(m3[v], m2[v], m1[v], p1[v], p2[v], p3[v]);
       } else {
         int c[3] = {0, 0, 0};
         int x = i0 - 2 + r;
         bool ok = line_coords(l, c) && x <= n + 5;
 #pragma unroll
         for (int v = 0; v < NV; ++v)
-          sD[IX(v, r, l, RD)] = ok ? (MIX ? T(A.Gdf[A.gdLB.at(v, x, c)]) : T(A.Gd[A.gdLB.at(v, x, c)])) : T(0);
+          d[v] = ok ? (MIX ? T(A.Gdf[A.gdLB.at(v, x, c)]) : T(A.Gd[A.gdLB.at(v, x, c)])) : T(0);
       }
+      stn(sD, r, l, RD, d);
     }
     __syncthreads();
     // 3. second derivatives on nodes i0-1 .. i0+TL-1
     for (int e = tid; e < RDD * LW; e += blockDim.x) {
       int r = DIR == 0 ? e % RDD : e / LW;
       int l = DIR == 0 ? e / RDD : e % LW;
+      T wm[NV], w0[NV], wp[NV], dm[NV], dp[NV], dd[NV];
+      ldn(sW, r + 3, l, RW, wm);
+      ldn(sW, r + 4, l, RW, w0);
+      ldn(sW, r + 5, l, RW, wp);
+      ldn(sD, r, l, RD, dm);
+      ldn(sD, r + 2, l, RD, dp);
 #pragma unroll
-      for (int v = 0; v < NV; ++v)
-        sDD[IX(v, r, l, RDD)] = d2_from_grad(sW[IX(v, r + 3, l, RW)], sW[IX(v, r + 4, l, RW)],
-                                             sW[IX(v, r + 5, l, RW)], sD[IX(v, r, l, RD)],
-                                             sD[IX(v, r + 2, l, RD)]);
+      for (int v = 0; v < NV; ++v) dd[v] = d2_from_grad(wm[v], w0[v], wp[v], dm[v], dp[v]);
+      stn(sDD, r, l, RDD, dd);
     }
     __syncthreads();
   }
@@ -673,16 +715,12 @@ __device__ __forceinline__ void k_gbr_sweep_body(const VBlock& vb, const DevGrid
     if (use_gbr) {
       T Wst[6][NV], Wd[2][NV], Wdd[2][NV];
 #pragma unroll
-      for (int j = 0; j < 6; ++j)
+      for (int j = 0; j < 6; ++j) ldn(sW, a + 2 + j, l, RW, Wst[j]);
 #pragma unroll
-        for (int v = 0; v < NV; ++v) Wst[j][v] = sW[IX(v, a + 2 + j, l, RW)];
-#pragma unroll
-      for (int j = 0; j < 2; ++j)
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          Wd[j][v] = sD[IX(v, a + 1 + j, l, RD)];
-          Wdd[j][v] = sDD[IX(v, a + j, l, RDD)];
-        }
+      for (int j = 0; j < 2; ++j) {
+        ldn(sD, a + 1 + j, l, RD, Wd[j]);
+        ldn(sDD, a + j, l, RDD, Wdd[j]);
+      }
       T omb = sO[(DIR == 0) ? l * RO + a + 3 : (a + 3) * LW + l];
       for (int jj = 1 - q.window; jj <= q.window; ++jj) {
         T o = sO[(DIR == 0) ? l * RO + a + 3 + jj : (a + 3 + jj) * LW + l];
@@ -692,7 +730,7 @@ __device__ __forceinline__ void k_gbr_sweep_body(const VBlock& vb, const DevGrid
       if (!CART) {
         long long pq = plin(g, c[0], c[1], c[2]);
 #pragma unroll
-        for (int m = 0; m < ND; ++m) xi[m] = T(g.xt[(DIR * ND + m) * g.NP + pq]);
+        for (int m = 0; m < ND; ++m) xi[m] = to_t<T>(g.xt[(DIR * ND + m) * g.NP + pq]);
       }
       gbr_flux<ND, CART, DIR, T>(q, g, Wst, Wd, Wdd, omb, xi, F);
     } else if (ok) {
@@ -704,8 +742,7 @@ __device__ __forceinline__ void k_gbr_sweep_body(const VBlock& vb, const DevGrid
 #pragma unroll
       for (int v = 0; v < NV; ++v) F[v] = T(0);
     }
-#pragma unroll
-    for (int v = 0; v < NV; ++v) sF[IX(v, a, l, TL)] = F[v];
+    stn(sF, a, l, TL, F);
     if (A.iface_out && ok) {
       long long line = DIR == 0 ? (long long)c[1] + (long long)g.n[1] * c[2]
                                 : (DIR == 1 ? (long long)c[0] + (long long)g.n[0] * c[2]
@@ -730,25 +767,93 @@ __device__ __forceinline__ void k_gbr_sweep_body(const VBlock& vb, const DevGrid
     using TA = typename std::conditional<MIX, float, double>::type;
     TA* acc = reinterpret_cast<TA*>(A.acc);
     TA tot[NV];
+    T f0[NV], f1[NV];
+    ldn(sF, a, l, TL, f0);
+    ldn(sF, a + 1, l, TL, f1);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      TA diff = MIX ? TA(sF[IX(v, a + 1, l, TL)] - sF[IX(v, a, l, TL)])
-                    : TA((double)sF[IX(v, a + 1, l, TL)] - (double)sF[IX(v, a, l, TL)]);
+      const TA diff = TA(f1[v] - f0[v]);
       tot[v] = A.first ? diff : acc[v * g.N + qi] + diff;
     }
-    if (!A.last) {
+    if (!A.last || A.defer) {
 #pragma unroll
       for (int v = 0; v < NV; ++v) acc[v * g.N + qi] = tot[v];
       continue;
     }
     const double J = CART ? g.cjac : g.jac[plin(g, c[0], c[1], c[2])];
-    stage_epilogue<ND, MIX, TA>(g, A, qi, J, tot);
+    double out[NV];
+    stage_epilogue<ND, MIX, TA>(g, A, qi, J, tot, out);
   }
 }
 
 template <int ND, int DIR, bool CART, bool COMPACT, typename T, int LW, int UNIT>
 __global__ void __launch_bounds__(256, sweep_min_blocks<ND, CART, T>()) k_gbr_sweep(DevGrid g, GbrCfg q, StageArgs A) {
   k_gbr_sweep_body<ND, DIR, CART, COMPACT, T, LW, UNIT>(hw_block(), g, q, A);
+}
+
+// ---------------------------------------------------------------- deferred stage update
+// The mixed form's last step of an RK stage as one streaming pass, in the
+// increment form of the TVD-RK3 scheme: with k_s = dt L(u^(s-1)) the stage
+// increments (here -dt J times the stage total of the directions' FP32 flux
+// differences summed in acc, formed in FP32),
+//   u1 = un + k1,   u2 = un + (k1 + k2) / 4,   u^(n+1) = un + (k1 + k2) / 6 + 2 k3 / 3,
+// which is the Shu-Osher form u2 = 3/4 un + 1/4 (u1 + k2), u^(n+1) =
+// 1/3 un + 2/3 (u2 + k3) rearranged.  The increments and their running sum Z
+// = k1 (+ k2) stay FP32 (the precision of the fluxes they come from); each
+// stage state is un plus one widened increment, one FP64 add per variable.
+// Stages 1 and 2 store no state: the primitives of u1 and u2 (the recovery
+// of k_prim) go straight to Wn for the next stage, whose primitive launch is
+// skipped; stage 3 writes u^(n+1) and takes the non-physical test.
+template <int ND, bool CART, int STAGE>
+__global__ void __launch_bounds__(256, 6) k_stage_update(DevGrid g, StageArgs A, float* __restrict__ Z,
+                                                         float* __restrict__ Wn) {
+  constexpr int NV = ND + 2;
+  const float* acc = reinterpret_cast<const float*>(A.acc);
+  const float dtf = d2f_int(*A.dt);
+  constexpr int stage = STAGE;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < g.N;
+       q += (long long)gridDim.x * blockDim.x) {
+    double J;
+    if (CART) {
+      J = g.cjac;
+    } else {
+      int c[3];
+      node_coords(g, q, c);
+      J = g.jac[plin(g, c[0], c[1], c[2])];
+    }
+    const float cJ = -(dtf * d2f_int(J));
+    double out[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const long long i = v * g.N + q;
+      const float k = cJ * acc[i];
+      float inc;
+      if constexpr (stage == 1) {
+        Z[i] = k;
+        inc = k;
+      } else if constexpr (stage == 2) {
+        const float z = Z[i] + k;
+        Z[i] = z;
+        inc = 0.25f * z;
+      } else {
+        inc = (1.0f / 6.0f) * Z[i] + (2.0f / 3.0f) * k;
+      }
+      out[v] = A.Un[i] + f2d_int(inc);
+    }
+    if constexpr (stage == 3) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) A.Uout[v * g.N + q] = out[v];
+      if (mixed_nonphysical<ND>(out)) {
+        atomicOr(A.bad_flag, 1u);
+        atomicMin(A.bad_idx, (unsigned long long)q);
+      }
+    } else {
+      float w[NV];
+      cons_to_prim_mixed<ND>(g.gm1, out, w);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) Wn[v * g.N + q] = w[v];
+    }
+  }
 }
 
 // ---------------------------------------------------------------- CFL
@@ -773,13 +878,13 @@ __device__ __forceinline__ T cfl_rate(const DevGrid& g, long long q, const T* w)
     int c[3];
     node_coords(g, q, c);
     long long pq = plin(g, c[0], c[1], c[2]);
-    J = T(g.jac[pq]);
+    J = to_t<T>(g.jac[pq]);
 #pragma unroll
     for (int l = 0; l < ND; ++l) {
       T dot = T(0), mag = T(0);
 #pragma unroll
       for (int m = 0; m < ND; ++m) {
-        T x = T(g.xh[(l * ND + m) * g.NP + pq]);
+        T x = to_t<T>(g.xh[(l * ND + m) * g.NP + pq]);
         dot = (m == 0) ? x * T(w[1 + m]) : dot + x * T(w[1 + m]);
         mag = (m == 0) ? x * x : mag + x * x;
       }

@@ -232,13 +232,13 @@ __device__ __forceinline__ void k_lad_coef_body(const VBlock& vb, const DevGrid&
         pe = gconst<T>(g.ch[l], g.f_ch[l]) * G(ND + 2, l);
       } else {
         long long pq = plin(g, c[0], c[1], c[2]);
-        pe = T(g.dxl[(l * ND + 0) * g.NP + pq]) * G(ND + 2, 0);
+        pe = to_t<T>(g.dxl[(l * ND + 0) * g.NP + pq]) * G(ND + 2, 0);
 #pragma unroll
-        for (int m = 1; m < ND; ++m) pe = pe + T(g.dxl[(l * ND + m) * g.NP + pq]) * G(ND + 2, m);
+        for (int m = 1; m < ND; ++m) pe = pe + to_t<T>(g.dxl[(l * ND + m) * g.NP + pq]) * G(ND + 2, m);
         if (comp) {
-          pr = T(g.dxl[(l * ND + 0) * g.NP + pq]) * G(ND + 1, 0);
+          pr = to_t<T>(g.dxl[(l * ND + 0) * g.NP + pq]) * G(ND + 1, 0);
 #pragma unroll
-          for (int m = 1; m < ND; ++m) pr = pr + T(g.dxl[(l * ND + m) * g.NP + pq]) * G(ND + 1, m);
+          for (int m = 1; m < ND; ++m) pr = pr + to_t<T>(g.dxl[(l * ND + m) * g.NP + pq]) * G(ND + 1, m);
         }
       }
       T Dk = fabs(pe) / (gme + T(1e-32));
@@ -330,7 +330,7 @@ __device__ __forceinline__ void nodeflux_at(const DevGrid& g, int l, const T* __
     } else {
       long long pq = plin(g, c[0], c[1], c[2]);
 #pragma unroll
-      for (int m = 0; m < ND; ++m) xi[m] = T(g.xh[(l * ND + m) * g.NP + pq]);
+      for (int m = 0; m < ND; ++m) xi[m] = to_t<T>(g.xh[(l * ND + m) * g.NP + pq]);
     }
     T rho = w[0], p = w[IP];
     T fc[NV];
@@ -497,13 +497,14 @@ __device__ __forceinline__ void lad_epilogue(const DevGrid& g, const StageArgs& 
   TA tot[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) tot[v] = A.first ? TA(Dv[v]) : acc[v * g.N + qi] + TA(Dv[v]);
-  if (!A.last) {
+  if (!A.last || A.defer) {
 #pragma unroll
     for (int v = 0; v < NV; ++v) acc[v * g.N + qi] = tot[v];
     return;
   }
   const double J = g.curv ? g.jac[plin(g, c[0], c[1], c[2])] : g.cjac;
-  stage_epilogue<ND, FUSED, TA>(g, A, qi, J, tot);
+  double out[NV];
+  stage_epilogue<ND, FUSED, TA>(g, A, qi, J, tot, out);
 }
 
 // E4 divergence of the node fluxes along l (explicit) or the compact result D.
