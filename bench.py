@@ -267,9 +267,10 @@ def run_gpu(args):
     # the mixed form (FP32 fluxes, FP64 accumulation) of the schemes that have it
     mixed = {}
     for n, kw in (MIXED if args.mixed else []):
-        ms, tile = time_mixed(api, torch, grid, base, dev, kw, args)
-        cu = cells / (ms * 1e-3)
-        mixed[n] = {"cell_updates_per_s": cu, "ms_per_rk3_step": ms, "tile_lines": list(tile),
+        ms, ms_graph, tile = time_mixed(api, torch, grid, base, dev, kw, args)
+        cu = cells / (ms_graph * 1e-3)
+        mixed[n] = {"cell_updates_per_s": cu, "ms_per_rk3_step": ms_graph, "ms_per_rk3_step_eager": ms,
+                    "tile_lines": list(tile),
                     "hbm_frac_of_measured": cu * HBM_BYTES_PER_CELL_STEP / (_peaks()["hbm_gbs"] * 1e9)}
 
     sod = run_sod_latency(api, torch, dev) if args.sod else None
@@ -384,6 +385,34 @@ def run_ramp(api, torch, dev, args):
     return {"workload": "M2.9 24-degree compression ramp 768x192x128 (%d cells), curvilinear, viscous; "
                         "%d RK3 steps from the initial boundary layer after one warm-up step" % (cells, args.ramp_steps),
             "per_scheme": out, "speed_ratios": ratios}
+
+
+def run_profile_ramp(args):
+    """Profiling aid: one scheme on a compression ramp of the given size
+    (NXxNYxNZ:SCHEME:fp64|mixed), three warm-up steps, then one RK3 step
+    bracketed by cudaProfilerStart/Stop (for ncu --profile-from-start off).
+    Prints the step's time; not a bench line."""
+    import torch
+    from paper_2511_18042_gb300 import api, inputs
+    size, scheme, prec = args.profile_ramp.split(":")
+    nx, ny, nz = (int(v) for v in size.split("x"))
+    kw = dict(dict(RAMP_SCHEMES)[scheme], precision=1 if prec == "mixed" else 0)
+    prob = inputs.compression_ramp(nx, ny, nz)
+    s = api.Solver.from_problem(prob, **kw)
+    U = torch.as_tensor(prob["U"], device="cuda")
+    dtd = torch.zeros(2, dtype=torch.float64, device="cuda")
+    for _ in range(3):
+        s.step(U, dtd)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.cudart().cudaProfilerStart()
+    e0.record()
+    s.step(U, dtd)
+    e1.record()
+    torch.cuda.synchronize()
+    torch.cuda.cudart().cudaProfilerStop()
+    print(json.dumps({"profile_ramp": args.profile_ramp, "cells": nx * ny * nz, "ms_step": e0.elapsed_time(e1),
+                      "status": s.sync_status()}))
 
 
 def run_sod_latency(api, torch, dev, steps=200):
@@ -571,29 +600,45 @@ def run_serving(args, count=200, rates=(8.0, 16.0, 32.0, 64.0)):
 
 
 def time_mixed(api, torch, grid, base, dev, kw, args):
-    """ms per RK3 step (with CFL) of a mixed-precision solver on the bench state
-    (tile shape autotuned, L2 flushed between timed steps); returns (ms, tile)."""
+    """ms per RK3 step (with the CFL step) of a mixed-precision solver on the
+    bench state, tile shape autotuned.  Before each timed step the state is
+    restored and L2 flushed (256 MB written > 126 MB), so the timed region is
+    the step alone from cold caches: launched eagerly (cg_step_dev) and
+    replayed as a captured CUDA graph (cg_step_graph) on a side stream.
+    Returns (ms eager, ms graph, tile)."""
     s = api.Solver(grid, **kw)
     tile = s.autotune(base)
     U = torch.empty_like(base)
     dtd = torch.zeros(2, dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    for _ in range(max(3, args.warmup)):
-        U.copy_(base)
-        s.step(U, dtd)
-    torch.cuda.synchronize()
-    stream = torch.cuda.current_stream()
-    tot = 0.0
-    for _ in range(max(1, args.steps)):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        flush.zero_()  # evict L2 (256 MB > 126 MB) between timed steps
-        e0.record(stream)
-        U.copy_(base)
-        s.step(U, dtd)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        tot += e0.elapsed_time(e1)
-    return tot / max(1, args.steps), tile
+    gs = torch.cuda.Stream(device=dev)
+    gs.wait_stream(torch.cuda.current_stream())
+    res = []
+    for graph in (False, True):
+        with torch.cuda.stream(gs):
+            for _ in range(max(3, args.warmup)):
+                U.copy_(base)
+                if graph:
+                    s.step_graph(U, dtd, gs)
+                else:
+                    s.step(U, dtd, stream=gs)
+            gs.synchronize()
+            tot = 0.0
+            for _ in range(max(1, args.steps)):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                flush.zero_()
+                U.copy_(base)
+                flush.zero_()
+                e0.record(gs)
+                if graph:
+                    s.step_graph(U, dtd, gs)
+                else:
+                    s.step(U, dtd, stream=gs)
+                e1.record(gs)
+                gs.synchronize()
+                tot += e0.elapsed_time(e1)
+        res.append(tot / max(1, args.steps))
+    return res[0], res[1], tile
 
 
 def _sweep_ms(api, torch, grid, base, dev, args, form):
@@ -798,7 +843,14 @@ def main():
                     help="cudaProfilerStart/Stop around the timed steps (ncu --profile-from-start off)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                     help="form of the timed schemes (profiling; the headline is FP64)")
+    ap.add_argument("--profile-ramp", default=None, metavar="NXxNYxNZ:SCHEME:fp64|mixed",
+                    help="profiling aid: one ramp step of one scheme between cudaProfilerStart/Stop, then exit")
     args = ap.parse_args()
+    if args.profile_ramp:
+        from paper_2511_18042_gb300 import build
+        build.build()
+        run_profile_ramp(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

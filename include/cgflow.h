@@ -162,6 +162,16 @@ CG_API int cg_rk3_step_dev(cg_solver *s, double *U, const double *dt_dev, void *
  * Graph-capturable; nothing waits. */
 CG_API int cg_step_dev(cg_solver *s, double *U, double *dt_dev, void *stream);
 
+/* cg_step_dev replayed as a CUDA graph: the solver's first call steps
+ * eagerly; then the first call for a given (U, dt_dev) pair and tile shape
+ * captures the step on `stream` (which must not be the legacy default
+ * stream) and launches it, later calls launch the captured graph, which
+ * removes the per-kernel launch gaps of a latency-bound step.  The graph
+ * reads U and dt_dev through the pointers it was captured with; a call with
+ * other pointers, or after a tile-shape change, captures again.  With kernel
+ * timing on (cg_timing_enable) the step runs eagerly.  Nothing waits. */
+CG_API int cg_step_graph(cg_solver *s, double *U, double *dt_dev, void *stream);
+
 /* Diagnostic (no counterpart in the paper): the mixed form's FP64 <-> FP32
  * conversions on the integer pipes, applied elementwise: f_out[i] = d_in[i]
  * rounded to binary32 (nearest, ties to even), d_out[i] = f_in[i] widened to

@@ -135,6 +135,13 @@ class Solver:
         nat.check(nat.lib().cg_step_dev(self._h, _dptr(U), _dptr(dt), _stream(stream)))
         return U
 
+    def step_graph(self, U, dt, stream):
+        """step() replayed as a CUDA graph on a non-default stream (captured on
+        the first call for these U and dt tensors, cg_step_graph)."""
+        self._check_state(U)
+        nat.check(nat.lib().cg_step_graph(self._h, _dptr(U), _dptr(dt), _stream(stream)))
+        return U
+
     def cfl_dt(self, U, out=None, stream=None):
         self._check_state(U)
         if out is not None:

@@ -243,6 +243,12 @@ struct cg_solver {
   // set by the mixed form's deferred stage update: W already holds the
   // primitives of the next stage's state, so its primitive launch is skipped
   bool prim_ready = false;
+  // cg_step_graph: the captured CFL + RK3 step and what it was captured for
+  cudaGraphExec_t gexec = nullptr;
+  double* g_U = nullptr;
+  double* g_dt = nullptr;
+  int g_lw[3] = {0, 0, 0};
+  bool g_warm = false;  // an eager step ran (lazy allocations are made outside any capture)
   unsigned int* bad_flag = nullptr;
   unsigned long long* bad_idx = nullptr;
   long long launches = 0;
@@ -1253,6 +1259,7 @@ CG_API void cg_solver_destroy(cg_solver* s) {
     }
   }
   lad_free(s->lad);
+  if (s->gexec) cudaGraphExecDestroy(s->gexec);
   for (int d = 0; d < 3; ++d)
     for (int side = 0; side < 2; ++side)
       if (s->prof[d][side]) cudaFree(s->prof[d][side]);
@@ -1455,6 +1462,50 @@ CG_API int cg_step_dev(cg_solver* s, double* U, double* dt_dev, void* stream) {
   s->dt = keep;
   if (rc) return rc;
   CG_CUDA(cudaGetLastError());
+  return CG_OK;
+}
+
+CG_API int cg_step_graph(cg_solver* s, double* U, double* dt_dev, void* stream) {
+  if (!s || !U || !dt_dev) return fail(CG_ERR_INVALID_ARG, "null argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (st == nullptr) return fail(CG_ERR_INVALID_ARG, "graph replay needs a non-default stream");
+  if (s->timing) return cg_step_dev(s, U, dt_dev, stream);  // per-launch events: step eagerly
+  if (!s->g_warm) {  // the first step runs eagerly: buffers a scheme allocates on first use exist before capture
+    int rc = cg_step_dev(s, U, dt_dev, stream);
+    if (rc) return rc;
+    s->g_warm = true;
+    return CG_OK;
+  }
+  bool same = s->gexec && s->g_U == U && s->g_dt == dt_dev;
+  for (int d = 0; d < 3; ++d) same = same && s->g_lw[d] == s->sweep_lw[d];
+  if (!same) {
+    if (s->gexec) {
+      cudaGraphExecDestroy(s->gexec);
+      s->gexec = nullptr;
+    }
+    CG_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    double* keep = s->dt;
+    s->dt = dt_dev;
+    int rc = DISPATCH_ND(s, rk3_cfl, s, U, dt_dev, nullptr, st);
+    s->dt = keep;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(st, &g);
+    if (rc) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    if (e != cudaSuccess) return fail(CG_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&s->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      s->gexec = nullptr;
+      return fail(CG_ERR_CUDA, "graph instantiation: %s", cudaGetErrorString(e));
+    }
+    s->g_U = U;
+    s->g_dt = dt_dev;
+    for (int d = 0; d < 3; ++d) s->g_lw[d] = s->sweep_lw[d];
+  }
+  CG_CUDA(cudaGraphLaunch(s->gexec, st));
   return CG_OK;
 }
 

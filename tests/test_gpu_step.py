@@ -89,3 +89,48 @@ def test_advance_matches_steps(api):
     torch.cuda.synchronize()
     assert k == 4 and abs(t - tt) <= 1e-14 * tt
     assert torch.equal(Ua, Ub)
+
+
+@pytest.mark.parametrize("kw", [dict(scheme="MEG6", precision=1), dict(scheme="LAD_C6", precision=1),
+                                dict(scheme="HYBRID", hybrid_mode=1, hyb_rho=0.3, hybrid_sensor=1, precision=0)],
+                         ids=["MEG6-mixed", "LAD_C6-mixed", "HYBRID1-fp64"])
+def test_step_graph_equals_eager_steps(api, developed, kw):
+    """cg_step_graph (eager first call, then a captured step replayed) gives
+    the eager steps' results bit for bit, recaptures for another state tensor
+    and after a tile-shape change."""
+    prob, U0 = developed
+    a = api.Solver.from_problem(prob, **kw)
+    b = api.Solver.from_problem(prob, **kw)
+    Ua, Ub, Uc = U0.clone(), U0.clone(), U0.clone()
+    da = torch.zeros(2, dtype=torch.float64, device="cuda")
+    db = torch.zeros(2, dtype=torch.float64, device="cuda")
+    st = torch.cuda.Stream()
+    st.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(st):
+        for _ in range(4):
+            a.step_graph(Ua, da, st)
+            b.step(Ub, db, stream=st)
+        for _ in range(2):  # another state: a new capture
+            a.step_graph(Uc, da, st)
+    st.synchronize()
+    assert a.sync_status() == 0 and b.sync_status() == 0
+    assert torch.equal(_bits(Ua), _bits(Ub))
+    # Uc took two steps from U0 through its own capture
+    Ue = U0.clone()
+    with torch.cuda.stream(st):
+        for _ in range(2):
+            b.step(Ue, db, stream=st)
+    st.synchronize()
+    assert torch.equal(_bits(Uc), _bits(Ue))
+    # a tile-shape change recaptures
+    shape = a.tile_shape()
+    a.set_tile_shape([4] * len(shape) if shape[0] != 4 else [8] * len(shape))
+    Uf, Ug = U0.clone(), U0.clone()
+    c = api.Solver.from_problem(prob, **kw)
+    c.set_tile_shape(a.tile_shape())
+    with torch.cuda.stream(st):
+        for _ in range(2):
+            a.step_graph(Uf, da, st)
+            c.step(Ug, db, stream=st)
+    st.synchronize()
+    assert torch.equal(_bits(Uf), _bits(Ug))
