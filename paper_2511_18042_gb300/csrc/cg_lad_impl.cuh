@@ -317,6 +317,24 @@ static int lad_filter(cg_solver* s, double* U, cudaStream_t st) {
   if (!s->lad.lines) return fail(CG_ERR_UNSUPPORTED, "the implicit filter belongs to LAD-C6");
   double b[5];
   filter_coeffs(s->p.alpha_f, b);
+  if (s->p.precision == CG_MIXED) {  // increment form, FP32 line solves (FilterInc)
+    const FilterInc fc{(float)(b[1] - s->p.alpha_f), (float)b[2], (float)b[3], (float)b[4]};
+    float* x = reinterpret_cast<float*>(s->lad.lines);
+    for (int l = 0; l < ND; ++l) {
+      const LineBuf& lb = s->lad.filtLB[l];
+      if (use_tile(lb)) {
+        using Tl = XTileFilterInc<ND>;
+        k_rhs_tile<float, ND + 2, 4, Tl, float2><<<tile_grid(lb), XT_THREADS, 0, st>>>(lb, Tl{s->dg, U, fc, ND + 2}, x);
+      } else {
+        k_rhs_filter_inc<ND><<<grid_blocks((long long)lb.m * lb.nl, 256), 256, 0, st>>>(s->dg, U, lb, fc, x);
+      }
+      LineJob<float> job{&s->filt[l], x, lb.nl, ND + 2};
+      launch_lines(&job, 1, st);
+      k_filter_store_inc<ND><<<grid_blocks(s->N, 256), 256, 0, st>>>(s->dg, x, lb, U);
+      s->launches += 3;
+    }
+    return CG_OK;
+  }
   for (int l = 0; l < ND; ++l) {
     const LineBuf& lb = s->lad.filtLB[l];
     launch_rhs_filter<ND>(s->dg, U, lb, b, s->lad.lines, st);

@@ -451,11 +451,13 @@ __global__ void k_rhs_filter(DevGrid g, const double* __restrict__ U, LineBuf lb
 constexpr int XT_L = 16, XT_R = 32, XT_THREADS = 256;
 
 // H: reach of the interior rows' stencil, Tile::HC: reach of the closure rows.
-template <typename T, int NC, int H, class Tile>
+// TS: the staged type (the right-hand side's type T unless the tile stages
+// something else, e.g. the hi/lo pairs of the mixed filter).
+template <typename T, int NC, int H, class Tile, typename TS = T>
 __global__ void __launch_bounds__(XT_THREADS) k_rhs_tile(LineBuf lb, Tile tl, T* __restrict__ r) {
   constexpr int HM = H > Tile::HC ? H : Tile::HC;
   constexpr int W = XT_R + 2 * HM + 1;  // +1: spreads lines over banks
-  __shared__ T sw[NC][XT_L][W];
+  __shared__ TS sw[NC][XT_L][W];
   const long long L0 = (long long)blockIdx.x * XT_L;
   const int i0 = blockIdx.y * XT_R;
   const int i1 = min(lb.m, i0 + XT_R);
@@ -477,7 +479,7 @@ __global__ void __launch_bounds__(XT_THREADS) k_rhs_tile(LineBuf lb, Tile tl, T*
     int c[3] = {0, 0, 0};
     lb.coords(L0 + l, c);
     c[lb.d] = ws + p;
-    T w[NC];
+    TS w[NC];
     tl.load(c, w);
 #pragma unroll
     for (int v = 0; v < NC; ++v) sw[v][l][p] = w[v];
@@ -509,6 +511,83 @@ struct XTileFilter {
            b4 * (w[p + 4] + w[p - 4]);
   }
 };
+
+// ---------------------------------------------------------------- mixed filter
+// The mixed form's implicit filter in increment form: D = Qf - Q solves
+// alpha D_{i-1} + D_i + alpha D_{i+1} = sum_n c_n (Q_{i+n} + Q_{i-n} - 2 Q_i),
+// n = 1..4, with c_1 = b_1 - alpha and c_n = b_n otherwise (the filter's row
+// minus its left-hand side applied to Q; the b_n keep constants, so the
+// right-hand side is a sum of second differences), and D = 0 on the identity
+// rows of non-periodic lines.  Each FP64 value is split once into a float
+// pair hi + lo (hi its FP32 image, lo the FP32 image of the rest); the second
+// differences are formed from the pairs in FP32, hi differences first (exact
+// between values within a factor two, so a smooth field keeps the relative
+// precision of the difference itself), and the line systems are solved in
+// FP32.  The state update Q + D is FP64 (k_filter_store_inc).
+__device__ __forceinline__ float2 split_hilo(double x) {
+  const float hi = d2f_int(x);
+  return make_float2(hi, d2f_int(x - f2d_int(hi)));
+}
+
+struct FilterInc {
+  float c1, c2, c3, c4;
+  // w: the pairs at offsets -4..4 of the row's position, w[4] the centre
+  __device__ __forceinline__ float row(const float2* w) const {
+    const float2 o = w[4];
+    auto d2 = [&](int k) {
+      const float2 a = w[4 + k], b = w[4 - k];
+      return ((a.x - o.x) + (b.x - o.x)) + ((a.y + b.y) - 2.0f * o.y);
+    };
+    return c1 * d2(1) + c2 * d2(2) + c3 * d2(3) + c4 * d2(4);
+  }
+};
+
+template <int ND>
+struct XTileFilterInc {
+  DevGrid g;
+  const double* U;
+  FilterInc fc;
+  int nc;
+  static constexpr int HC = 0;
+  __device__ void load(const int* c, float2* w) const {
+    double q[ND + 2];
+    load_filtered<ND>(g, U, c, q);
+#pragma unroll
+    for (int v = 0; v < ND + 2; ++v) w[v] = split_hilo(q[v]);
+  }
+  __device__ float row(const float2* w, int p, bool closure) const { return closure ? 0.0f : fc.row(w + p - 4); }
+};
+
+// Per-row form of the same right-hand sides (line families of fewer lines than a tile).
+template <int ND>
+__global__ void k_rhs_filter_inc(DevGrid g, const double* __restrict__ U, LineBuf lb, FilterInc fc,
+                                 float* __restrict__ r) {
+  constexpr int NV = ND + 2;
+  LB_LOOP(lb, e) {
+    int i = (int)(e / lb.nl);
+    long long L = e % lb.nl;
+    int c[3] = {0, 0, 0};
+    lb.coords(L, c);
+    int pos = lb.periodic ? i : lb.lo + i;
+    if (!lb.periodic && (i == 0 || i == lb.m - 1)) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) r[((long long)v * lb.m + i) * lb.nl + L] = 0.0f;
+      continue;
+    }
+    float2 w[NV][9];
+    int cc[3] = {c[0], c[1], c[2]};
+#pragma unroll
+    for (int t = -4; t <= 4; ++t) {
+      cc[lb.d] = pos + t;
+      double q[NV];
+      load_filtered<ND>(g, U, cc, q);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) w[v][t + 4] = split_hilo(q[v]);
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) r[((long long)v * lb.m + i) * lb.nl + L] = fc.row(w[v]);
+  }
+}
 
 // MIG4 gradients of the primitives (the formula of k_rhs_mig4).
 template <int ND, typename TW, typename TR>
@@ -560,6 +639,23 @@ __global__ void k_filter_store(DevGrid g, const double* __restrict__ x, LineBuf 
     const double J = g.curv ? g.jac[plin(g, c[0], c[1], c[2])] : 1.0;
 #pragma unroll
     for (int v = 0; v < NV; ++v) U[v * g.N + q] = g.curv ? x[lb.at(v, c[lb.d], c)] * J : x[lb.at(v, c[lb.d], c)];
+  }
+}
+
+// The mixed filter's increments into the interior of the state:
+// Q += D (Q/J += D on a curvilinear grid: Q += J D), the sum in FP64.
+template <int ND>
+__global__ void k_filter_store_inc(DevGrid g, const float* __restrict__ x, LineBuf lb, double* __restrict__ U) {
+  constexpr int NV = ND + 2;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < g.N; q += (long long)gridDim.x * blockDim.x) {
+    int c[3];
+    node_coords(g, q, c);
+    const float J = g.curv ? d2f_int(g.jac[plin(g, c[0], c[1], c[2])]) : 1.0f;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const float d = x[lb.at(v, c[lb.d], c)];
+      U[v * g.N + q] = U[v * g.N + q] + f2d_int(g.curv ? J * d : d);
+    }
   }
 }
 
