@@ -80,6 +80,44 @@ __global__ void k_lad_fieldbuf(DevGrid g, const T* __restrict__ W, T* __restrict
   k_lad_fieldbuf_body<ND, T>(hw_block(), g, W, f, fbx);
 }
 
+// Physical gradients and dilatation at node c (index e of b3) from the
+// index-space derivatives d[l][f] = d f / d xi_l.
+template <int ND, bool CART, typename T>
+__device__ __forceinline__ void lad_grad_out(const DevGrid& g, const int* c, long long e, long long bs,
+                                             const T (&d)[3][ND + 3], T* __restrict__ gr, T* __restrict__ dv) {
+  constexpr int NF = ND + 3;
+  T div = T(0);
+  if (CART) {
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+#pragma unroll
+      for (int m = 0; m < ND; ++m) {
+        T v = gconst<T>(g.cjxh[m], g.f_cjxh[m]) * d[m][f];
+        gr[(f * ND + m) * bs + e] = v;
+        if (f < ND && m == f) div = (f == 0) ? v : div + v;
+      }
+  } else {
+    long long pq = plin(g, c[0], c[1], c[2]);
+    double J = g.jac[pq];
+    T xm[3][3];
+#pragma unroll
+    for (int l = 0; l < ND; ++l)
+#pragma unroll
+      for (int m = 0; m < ND; ++m) xm[l][m] = to_t<T>(J * g.xh[(l * ND + m) * g.NP + pq]);
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+#pragma unroll
+      for (int m = 0; m < ND; ++m) {
+        T sm = xm[0][m] * d[0][f];
+#pragma unroll
+        for (int l = 1; l < ND; ++l) sm = sm + xm[l][m] * d[l][f];
+        gr[(f * ND + m) * bs + e] = sm;
+        if (f < ND && m == f) div = (f == 0) ? sm : div + sm;
+      }
+  }
+  dv[e] = div;
+}
+
 // Physical gradients and dilatation on b3.  E4 differences the field buffer;
 // C6 reads the compact derivatives from the line buffers df.
 template <int ND, bool CART, bool C6, typename T = double>
@@ -111,37 +149,50 @@ __device__ __forceinline__ void k_lad_grad_body(const VBlock& vb, const DevGrid&
         }
       }
     }
-    T div = T(0);
-    if (CART) {
-#pragma unroll
-      for (int f = 0; f < NF; ++f)
-#pragma unroll
-        for (int m = 0; m < ND; ++m) {
-          T v = T(g.cjac * g.cxh[m]) * d[m][f];
-          gr[(f * ND + m) * bs + e] = v;
-          if (f < ND && m == f) div = (f == 0) ? v : div + v;
-        }
-    } else {
-      long long pq = plin(g, c[0], c[1], c[2]);
-      double J = g.jac[pq];
-      T xm[3][3];
-#pragma unroll
-      for (int l = 0; l < ND; ++l)
-#pragma unroll
-        for (int m = 0; m < ND; ++m) xm[l][m] = T(J * g.xh[(l * ND + m) * g.NP + pq]);
-#pragma unroll
-      for (int f = 0; f < NF; ++f)
-#pragma unroll
-        for (int m = 0; m < ND; ++m) {
-          T sm = xm[0][m] * d[0][f];
-#pragma unroll
-          for (int l = 1; l < ND; ++l) sm = sm + xm[l][m] * d[l][f];
-          gr[(f * ND + m) * bs + e] = sm;
-          if (f < ND && m == f) div = (f == 0) ? sm : div + sm;
-        }
-    }
-    dv[e] = div;
+    lad_grad_out<ND, CART, T>(g, c, e, bs, d, gr, dv);
   }
+}
+
+// The C6 form of k_lad_grad in 2D and 3D on tiles of 32 (x) x 8 (y) nodes of
+// b3, one z plane per block.  The x-line buffer holds a line's positions a
+// line count apart, so reading it node by node along x would touch one
+// sector per value; the tile stages its x derivatives with consecutive
+// threads on consecutive lines (consecutive y), then reads them from shared
+// memory.  The y and z buffers are read directly (consecutive x are
+// consecutive lines there).  Same values and arithmetic as k_lad_grad.
+constexpr int LGT_X = 32, LGT_Y = 8;
+template <int ND, bool CART, typename T>
+__global__ void __launch_bounds__(LGT_X * LGT_Y) k_lad_grad_xt(DevGrid g, const T* __restrict__ df0, const T* __restrict__ df1,
+                                                             const T* __restrict__ df2, LineBuf lb0, LineBuf lb1,
+                                                             LineBuf lb2, T* __restrict__ gr, T* __restrict__ dv, Box b3,
+                                                             const int* guard, int want) {
+  static_assert(ND >= 2, "tiles of x and y");
+  constexpr int NF = ND + 3;
+  __shared__ T sD[NF][LGT_Y][LGT_X + 1];
+  if (guard && *guard != want) return;
+  const int bx0 = (int)blockIdx.x * LGT_X, by0 = (int)blockIdx.y * LGT_Y;
+  const int cz = ND == 3 ? (int)blockIdx.z - b3.off[2] : 0;
+  const int tid = threadIdx.y * LGT_X + threadIdx.x;
+  {
+    const int ly = tid % LGT_Y, lx = tid / LGT_Y;  // consecutive threads: consecutive lines
+    if (bx0 + lx < b3.ext[0] && by0 + ly < b3.ext[1]) {
+      int c[3] = {bx0 + lx - b3.off[0], by0 + ly - b3.off[1], cz};
+#pragma unroll
+      for (int f = 0; f < NF; ++f) sD[f][ly][lx] = df0[lb0.at(f, c[0], c)];
+    }
+  }
+  __syncthreads();
+  const int ex = bx0 + (int)threadIdx.x, ey = by0 + (int)threadIdx.y;
+  if (ex >= b3.ext[0] || ey >= b3.ext[1]) return;
+  int c[3] = {ex - b3.off[0], ey - b3.off[1], cz};
+  T d[3][NF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    d[0][f] = sD[f][threadIdx.y][threadIdx.x];
+    d[1][f] = df1[lb1.at(f, c[1], c)];
+    if (ND == 3) d[2][f] = df2[lb2.at(f, c[2], c)];
+  }
+  lad_grad_out<ND, CART, T>(g, c, b3.at(c[0], c[1], c[2]), b3.size(), d, gr, dv);
 }
 
 template <int ND, bool CART, bool C6, typename T = double>
@@ -532,6 +583,40 @@ __global__ void k_lad_div(DevGrid g, int l, const T* __restrict__ Fn, Box fb, co
     }
     lad_epilogue<ND, sizeof(T) == 4, T>(g, A, q, c, Dv);
   }
+}
+
+// The C6 divergence along x (D from the x-line buffer) on tiles of 32 (x) x
+// 8 lines: the tile's D values are staged with consecutive threads on
+// consecutive lines, then each thread takes one node, as k_lad_div.
+template <int ND, typename T>
+__global__ void __launch_bounds__(LGT_X * LGT_Y) k_lad_div_xt(DevGrid g, const T* __restrict__ D, LineBuf DL, StageArgs A,
+                                                            const int* guard, int want) {
+  constexpr int NV = ND + 2;
+  __shared__ T sD[NV][LGT_Y][LGT_X + 1];
+  if (guard && *guard != want) return;
+  const int x0 = (int)blockIdx.x * LGT_X;
+  const long long L0 = (long long)blockIdx.y * LGT_Y + (long long)blockIdx.z * gridDim.y * LGT_Y;
+  const int tid = threadIdx.y * LGT_X + threadIdx.x;
+  {
+    const int ly = tid % LGT_Y, lx = tid / LGT_Y;
+    if (x0 + lx < g.n[0] && L0 + ly < DL.nl) {
+      int c[3] = {0, 0, 0};
+      DL.coords(L0 + ly, c);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) sD[v][ly][lx] = D[DL.at(v, x0 + lx, c)];
+    }
+  }
+  __syncthreads();
+  const int x = x0 + (int)threadIdx.x;
+  const long long L = L0 + threadIdx.y;
+  if (x >= g.n[0] || L >= DL.nl) return;
+  int c[3] = {0, 0, 0};
+  DL.coords(L, c);
+  c[0] = x;
+  T Dv[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) Dv[v] = sD[v][threadIdx.y][threadIdx.x];
+  lad_epilogue<ND, sizeof(T) == 4, T>(g, A, lin(g, c[0], c[1], c[2]), c, Dv);
 }
 
 // Troubled-node criterion of Sec. 5 at node (x, y, z) (ghost-resolved):

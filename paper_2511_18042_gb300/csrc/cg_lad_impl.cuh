@@ -101,13 +101,26 @@ static int lad_coeffs_run(cg_solver* s, int dkind, cudaStream_t st, const int* g
     s->launches++;
   }
   int gb = grid_blocks(L.b3.size(), 128);
+  const dim3 xt_grid((unsigned)((L.b3.ext[0] + LGT_X - 1) / LGT_X), (unsigned)((L.b3.ext[1] + LGT_Y - 1) / LGT_Y),
+                     ND == 3 ? (unsigned)L.b3.ext[2] : 1u);
+  const bool xt = ND >= 2 && c6;  // C6 in 2D/3D: the x lines through the tiled read
   if (s->dg.curv) {
-    if (c6) k_lad_grad<ND, false, true, T><<<gb, 128, 0, st>>>(s->dg, fb, L.fbx, df[0], df[1], df[2], L.dfLB[0], L.dfLB[1], L.dfLB[2], gr, dv, L.b3, guard, want);
+    if (xt) {
+      if constexpr (ND >= 2)
+        k_lad_grad_xt<ND, false, T><<<xt_grid, dim3(LGT_X, LGT_Y), 0, st>>>(s->dg, df[0], df[1], df[2], L.dfLB[0],
+                                                                           L.dfLB[1], L.dfLB[2], gr, dv, L.b3, guard, want);
+    }
+    else if (c6) k_lad_grad<ND, false, true, T><<<gb, 128, 0, st>>>(s->dg, fb, L.fbx, df[0], df[1], df[2], L.dfLB[0], L.dfLB[1], L.dfLB[2], gr, dv, L.b3, guard, want);
     else k_lad_grad<ND, false, false, T><<<gb, 128, 0, st>>>(s->dg, fb, L.fbx, df[0], df[1], df[2], L.dfLB[0], L.dfLB[1], L.dfLB[2], gr, dv, L.b3, guard, want);
     k_lad_coef<ND, false, T><<<grid_blocks(s->N, 128), 128, 0, st>>>(s->dg, reinterpret_cast<const T*>(s->W), fb, L.fbx, gr, dv, L.b3, s->p.c_beta,
                                                                      s->p.c_kappa, bt[0], kp[0], guard, want);
   } else {
-    if (c6) k_lad_grad<ND, true, true, T><<<gb, 128, 0, st>>>(s->dg, fb, L.fbx, df[0], df[1], df[2], L.dfLB[0], L.dfLB[1], L.dfLB[2], gr, dv, L.b3, guard, want);
+    if (xt) {
+      if constexpr (ND >= 2)
+        k_lad_grad_xt<ND, true, T><<<xt_grid, dim3(LGT_X, LGT_Y), 0, st>>>(s->dg, df[0], df[1], df[2], L.dfLB[0],
+                                                                           L.dfLB[1], L.dfLB[2], gr, dv, L.b3, guard, want);
+    }
+    else if (c6) k_lad_grad<ND, true, true, T><<<gb, 128, 0, st>>>(s->dg, fb, L.fbx, df[0], df[1], df[2], L.dfLB[0], L.dfLB[1], L.dfLB[2], gr, dv, L.b3, guard, want);
     else k_lad_grad<ND, true, false, T><<<gb, 128, 0, st>>>(s->dg, fb, L.fbx, df[0], df[1], df[2], L.dfLB[0], L.dfLB[1], L.dfLB[2], gr, dv, L.b3, guard, want);
     k_lad_coef<ND, true, T><<<grid_blocks(s->N, 128), 128, 0, st>>>(s->dg, reinterpret_cast<const T*>(s->W), fb, L.fbx, gr, dv, L.b3, s->p.c_beta,
                                                                     s->p.c_kappa, bt[0], kp[0], guard, want);
@@ -232,8 +245,16 @@ static int lad_pass(cg_solver* s, int dkind, StageArgs A, cudaStream_t st, const
       s->launches += 2;
       D = Dw;
     }
-    k_lad_div<ND, T><<<grid_blocks(s->N, 256), 256, 0, st>>>(s->dg, l, reinterpret_cast<const T*>(L.Fn), L.fbox[l], D, DL,
-                                                            A, guard, want);
+    if (ND >= 2 && l == 0 && D) {  // x lines: the tiled read of the line buffer
+      const long long ty = (DL.nl + LGT_Y - 1) / LGT_Y;
+      const unsigned gy = (unsigned)std::min<long long>(ty, 65535), gz = (unsigned)((ty + gy - 1) / gy);
+      if constexpr (ND >= 2)
+        k_lad_div_xt<ND, T><<<dim3((unsigned)((s->dg.n[0] + LGT_X - 1) / LGT_X), gy, gz), dim3(LGT_X, LGT_Y), 0, st>>>(
+            s->dg, D, DL, A, guard, want);
+    } else {
+      k_lad_div<ND, T><<<grid_blocks(s->N, 256), 256, 0, st>>>(s->dg, l, reinterpret_cast<const T*>(L.Fn), L.fbox[l], D,
+                                                              DL, A, guard, want);
+    }
     s->launches++;
   }
   return CG_OK;
