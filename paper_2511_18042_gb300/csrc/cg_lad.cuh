@@ -621,14 +621,45 @@ __global__ void __launch_bounds__(LGT_X * LGT_Y) k_lad_div_xt(DevGrid g, const T
 
 // Troubled-node criterion of Sec. 5 at node (x, y, z) (ghost-resolved):
 // rho < hyb_rho or p < hyb_p, or (with the sensor) Omega > threshold.
+// The criterion's thresholds in the stored type TW.  For FP32 storage they are
+// rounded outward (rho, p: up; Omega: down), so that for every float w,
+// w < hr holds exactly when w < hr_f and om > thr exactly when om > thr_f:
+// the FP32 comparisons take the FP64 decisions, without widening each
+// neighbour's state on the FP64 pipe.
+template <typename TW>
+struct TroubleThr {
+  TW hr, hp, thr;
+  __device__ explicit TroubleThr(double r, double p, double t) {
+    if constexpr (sizeof(TW) == 4) {
+      hr = f32_up(r);
+      hp = f32_up(p);
+      thr = f32_down(t);
+    } else {
+      hr = r;
+      hp = p;
+      thr = t;
+    }
+  }
+  __device__ static float f32_up(double x) {
+    float f = (float)x;
+    if ((double)f < x) f = nextafterf(f, INFINITY);
+    return f;
+  }
+  __device__ static float f32_down(double x) {
+    float f = (float)x;
+    if ((double)f > x) f = nextafterf(f, -INFINITY);
+    return f;
+  }
+};
+
 template <int ND, typename TW>
-__device__ __forceinline__ bool troubled_at(const DevGrid& g, const TW* __restrict__ W, double hr, double hp,
-                                            const TW* __restrict__ om, const Box& ob, double thr, int x, int y, int z) {
+__device__ __forceinline__ bool troubled_at(const DevGrid& g, const TW* __restrict__ W, const TroubleThr<TW>& th,
+                                            const TW* __restrict__ om, const Box& ob, int x, int y, int z) {
   constexpr int NV = ND + 2, IP = ND + 1;
-  double w[NV];
-  load_state<ND, false, TW, double>(g, W, x, y, z, w);
-  bool t = w[0] < hr || w[IP] < hp;
-  if (om && double(om[ob.at(x, y, z)]) > thr) t = true;
+  TW w[NV];
+  load_state<ND, false, TW, TW>(g, W, x, y, z, w);
+  bool t = w[0] < th.hr || w[IP] < th.hp;
+  if (om && om[ob.at(x, y, z)] > th.thr) t = true;
   return t;
 }
 
@@ -641,17 +672,18 @@ __device__ __forceinline__ void k_troubled_body(const VBlock& vb, const DevGrid&
                            Box ob, double thr, unsigned char* __restrict__ tr, Box tb, int* flag,
                            unsigned long long* count, int buf = 0) {
   unsigned long long local = 0;
+  const TroubleThr<TW> th(hr, hp, thr);
   BOX_LOOP(tb, e) {
     int c[3];
     box_coords(tb, e, c);
-    bool own = troubled_at<ND, TW>(g, W, hr, hp, om, ob, thr, c[0], c[1], c[2]);
+    bool own = troubled_at<ND, TW>(g, W, th, om, ob, c[0], c[1], c[2]);
     bool t = own;
     if (buf > 0 && tr) {
       const int bz = ND > 2 ? buf : 0, by = ND > 1 ? buf : 0;
       for (int dz = -bz; dz <= bz && !t; ++dz)
         for (int dy = -by; dy <= by && !t; ++dy)
           for (int dx = -buf; dx <= buf && !t; ++dx)
-            if (dx || dy || dz) t = troubled_at<ND, TW>(g, W, hr, hp, om, ob, thr, c[0] + dx, c[1] + dy, c[2] + dz);
+            if (dx || dy || dz) t = troubled_at<ND, TW>(g, W, th, om, ob, c[0] + dx, c[1] + dy, c[2] + dz);
     }
     if (tr) tr[e] = t ? 1 : 0;
     bool interior = true;

@@ -529,6 +529,20 @@ __device__ __forceinline__ float2 split_hilo(double x) {
   return make_float2(hi, d2f_int(x - f2d_int(hi)));
 }
 
+// The filtered variable of the mixed filter: Q, or Q/J on a curvilinear grid
+// formed as Q times the refined reciprocal of J (relative error below 2e-14,
+// far under the hi/lo pair's 48 bits) instead of five IEEE FP64 divisions.
+template <int ND>
+__device__ __forceinline__ void load_filtered_mixed(const DevGrid& g, const double* __restrict__ U, const int* c,
+                                                    double* w) {
+  load_state<ND, true>(g, U, c[0], c[1], c[2], w);
+  if (g.curv) {
+    const double r = recip_refined(g.jac[plin(g, c[0], c[1], c[2])]);
+#pragma unroll
+    for (int v = 0; v < ND + 2; ++v) w[v] = w[v] * r;
+  }
+}
+
 struct FilterInc {
   float c1, c2, c3, c4;
   // w: the pairs at offsets -4..4 of the row's position, w[4] the centre
@@ -551,7 +565,7 @@ struct XTileFilterInc {
   static constexpr int HC = 0;
   __device__ void load(const int* c, float2* w) const {
     double q[ND + 2];
-    load_filtered<ND>(g, U, c, q);
+    load_filtered_mixed<ND>(g, U, c, q);
 #pragma unroll
     for (int v = 0; v < ND + 2; ++v) w[v] = split_hilo(q[v]);
   }
@@ -580,7 +594,7 @@ __global__ void k_rhs_filter_inc(DevGrid g, const double* __restrict__ U, LineBu
     for (int t = -4; t <= 4; ++t) {
       cc[lb.d] = pos + t;
       double q[NV];
-      load_filtered<ND>(g, U, cc, q);
+      load_filtered_mixed<ND>(g, U, cc, q);
 #pragma unroll
       for (int v = 0; v < NV; ++v) w[v][t + 4] = split_hilo(q[v]);
     }
