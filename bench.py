@@ -57,7 +57,7 @@ METRIC = "cell-updates/s per scheme & % HBM roofline; batched solves/s, p50/p99 
 SWEEP_FLOP_PER_IFACE = 524.8
 # dram read + write per launch (mean of x and y) of the sweep form the roofline times,
 # from its ncu capture (profiles/); None until the current kernel has been captured
-SWEEP_TRAFFIC_BYTES = {"exact": 117.7e6, "contracted": 140.2e6}
+SWEEP_TRAFFIC_BYTES = {"exact": 118.0e6, "contracted": 140.2e6}
 ROOFLINE_FORM = "exact"  # the library default (fma_sweep = 0)
 FP64_PEAK_DERIVED_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12  # SMs x DFMA/clk x 2 flop x max clock (context only)
 HBM_BYTES_PER_CELL_STEP = 256.0  # minimal-traffic model, FP64 state, nv = 4, uniform grid
