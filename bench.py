@@ -14,7 +14,7 @@ replicas, no exchange); value sums over ranks with the max-over-ranks time.
 
 --impl reference times the FP64 CPU oracle (all host cores) on a bounded
 sample of the same workload (one RK3 step of each scheme on the triple point
-at 448 x 192).
+at 896 x 384, a quarter of the cells).
 """
 import argparse
 import json
@@ -57,6 +57,8 @@ METRIC = "cell-updates/s per scheme & % HBM roofline; batched solves/s, p50/p99 
 SWEEP_FLOP_PER_IFACE = 524.8
 # dram read + write per launch (mean of x and y) of the sweep form the roofline times,
 # from its ncu capture (profiles/); None until the current kernel has been captured
+# the bounded sample of the triple point on which the CPU oracle is timed
+CPU_SAMPLE = (896, 384)
 SWEEP_TRAFFIC_BYTES = {"exact": 118.0e6, "contracted": 140.2e6}
 ROOFLINE_FORM = "exact"  # the library default (fma_sweep = 0)
 FP64_PEAK_DERIVED_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12  # SMs x DFMA/clk x 2 flop x max clock (context only)
@@ -318,7 +320,7 @@ def run_gpu(args):
         "gpu_launches_timed_total": launches, "wall_s_timed": wall, "clocks": clk.summary(),
     }
     if rank == 0 and args.cpu_baseline and ws == 1:
-        line["cpu_baseline"] = cpu_baseline(names, sample=(448, 192))
+        line["cpu_baseline"] = cpu_baseline(names, sample=CPU_SAMPLE)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -723,30 +725,34 @@ def _oracle_rate(oracle, prob, kw, steps, U0=None):
     return cells * steps / sec, sec
 
 
-def cpu_baseline(names, sample=(448, 192)):
+def cpu_baseline(names, sample=None):
     """The oracle as it stands (plain FP64 C, OpenMP over the outer grid
     loops, results independent of the thread count), timed on this host on
-    bounded samples of the workloads: the headline's one RK3 step of each
-    scheme on a 448 x 192 triple point (1/16 of the cells) from 20 MEG6 steps
-    of development, single-threaded and on all cores, and the cases of the
-    benchmark's other configurations on all cores (Sod to t = 0.2, a 448 x 192
+    bounded samples of the workloads: the headline's RK3 steps of each scheme
+    (two on all cores, one single-threaded) on an 896 x 384 triple point (a
+    quarter of the cells) from 20 MEG6 steps of development, and the cases of the
+    benchmark's other configurations on all cores (Sod to t = 0.2, the same
     triple point 10 steps, 10 batched Riemann problems 10 steps, a 96 x 48 x 32
     compression ramp 2 steps)."""
     import oracle
     from paper_2511_18042_gb300 import inputs
+    sample = sample or CPU_SAMPLE
     ncores = oracle.set_threads(0)
     prob = inputs.triple_point(*sample)
     kws = dict(SCHEMES)
     oracle.set_threads(ncores)
     U0, _, _ = oracle.Oracle(prob, scheme="MEG6").advance(prob["U"], nsteps=20)
     res = {}
-    for th in (1, ncores):
+    for th, steps in ((1, 1), (ncores, 2)):
         oracle.set_threads(th)
+        orcs = [oracle.Oracle(prob, **kws[n]) for n in names]
         t0 = time.perf_counter()
-        for n in names:
-            o = oracle.Oracle(prob, **kws[n])
-            o.rk3_step(U0, o.cfl_dt(U0))
-        res[th] = (sample[0] * sample[1] * len(names) / (time.perf_counter() - t0), time.perf_counter() - t0)
+        for o in orcs:
+            U = U0
+            for _ in range(steps):
+                U = o.rk3_step(U, o.cfl_dt(U))
+        sec = time.perf_counter() - t0
+        res[th] = (sample[0] * sample[1] * len(names) * steps / sec, sec)
     oracle.set_threads(ncores)
     cases = {}
     sod = inputs.shock_tube("sod", 400)
@@ -758,7 +764,8 @@ def cpu_baseline(names, sample=(448, 192)):
         cases["sod_400_to_t0.2_" + n] = {"cell_updates_per_s": 400 * k / sec, "steps": k, "seconds": sec}
     for n in ("MEG6", "LAD_E4", "HYBRID_CELL"):
         r, sec = _oracle_rate(oracle, prob, kws[n], 10, U0)
-        cases["triple_point_448x192_10_steps_" + n] = {"cell_updates_per_s": r, "seconds": sec}
+        cases["triple_point_%dx%d_10_steps_%s" % (sample[0], sample[1], n)] = {"cell_updates_per_s": r,
+                                                                                "seconds": sec}
     br = inputs.batched_riemann(count=10, seed=0)
     t0 = time.perf_counter()
     cells = 0
@@ -775,9 +782,9 @@ def cpu_baseline(names, sample=(448, 192)):
         r, sec = _oracle_rate(oracle, ramp, dict(scheme=n), 2)
         cases["ramp_96x48x32_2_steps_" + n] = {"cell_updates_per_s": r, "seconds": sec}
     return {"value": res[ncores][0], "unit": "cell-updates/s", "cores": ncores, "kind": "oracle",
-            "sample": "one RK3 step of each of %d schemes on a %dx%d triple point (1/16 of the cells), from 20 MEG6 "
-                      "steps of development, on %d threads (%.2f s)" % (len(names), sample[0], sample[1], ncores,
-                                                                      res[ncores][1]),
+            "sample": "two RK3 steps of each of %d schemes on a %dx%d triple point (a quarter of the cells), from "
+                      "20 MEG6 steps of development, on %d threads (%.2f s)" % (len(names), sample[0], sample[1],
+                                                                              ncores, res[ncores][1]),
             "single_core": {"value": res[1][0], "seconds": res[1][1]},
             "cores_all": ncores, "cpu_model": _cpu_model(), "cases_all_cores": cases}
 
@@ -790,7 +797,7 @@ def run_reference(args):
     import oracle
     from paper_2511_18042_gb300 import inputs
     ncores = oracle.set_threads(0)
-    sample = (448, 192)
+    sample = CPU_SAMPLE
     prob = inputs.triple_point(*sample)
     kws = dict(SCHEMES)
     pre = oracle.Oracle(prob, scheme="MEG6")

@@ -104,7 +104,7 @@ def test_reference_arm_json_line():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == "cell-updates/s"
     assert d["higher_is_better"] is True and d["n_gpus"] == 1 and d["steps"] == 1
-    assert d["value"] > 0 and abs(d["ms_per_step"] - 448 * 192 * 2 / d["value"] * 1e3) <= 1e-6 * d["ms_per_step"]
+    assert d["value"] > 0 and abs(d["ms_per_step"] - bench.CPU_SAMPLE[0] * bench.CPU_SAMPLE[1] * 2 / d["value"] * 1e3) <= 1e-6 * d["ms_per_step"]
     assert d["config"]["workload"] == bench.bench_config(["MEG6", "LAD_E4"], 1)["workload"]
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] == os.cpu_count() and cb["value"] == d["value"] and cb["sample"]
