@@ -716,7 +716,17 @@ struct LineJob {
   T* x;
   long long nl;
   int ncomp;
+  C6Src<T> src{};  // f set: the partitioned solver forms the C6 right-hand sides itself
 };
+
+// Whether launch_lines takes the partitioned solver for these jobs (the one
+// that can form C6 right-hand sides itself).
+template <typename T>
+static bool lines_partitioned(const LineJob<T>* jobs, int n) {
+  bool part = true;
+  for (int j = 0; j < n; ++j) part = part && jobs[j].L->pc.P >= 4;
+  return part;
+}
 
 template <typename T>
 static void launch_lines(const LineJob<T>* jobs, int n, cudaStream_t st) {
@@ -729,6 +739,7 @@ static void launch_lines(const LineJob<T>* jobs, int n, cudaStream_t st) {
     int Pmax = 1;
     for (int j = 0; j < n; ++j) {
       J.pc[j] = part_coef<T>(*jobs[j].L);
+      J.src[j] = jobs[j].src;
       J.x[j] = jobs[j].x;
       J.nl[j] = jobs[j].nl;
       J.ncomp[j] = jobs[j].ncomp;

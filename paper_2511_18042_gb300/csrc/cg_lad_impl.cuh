@@ -91,11 +91,16 @@ static int lad_coeffs_run(cg_solver* s, int dkind, cudaStream_t st, const int* g
   T* df[3] = {reinterpret_cast<T*>(L.df[0]), reinterpret_cast<T*>(L.df[1]), reinterpret_cast<T*>(L.df[2])};
   if (c6) {
     LineJob<T> jobs[3];
+    for (int l = 0; l < ND; ++l) jobs[l] = LineJob<T>{&s->c6grad[l], df[l], L.dfLB[l].nl, ND + 3};
+    const bool fused = lines_partitioned(jobs, ND);  // the solver forms the right-hand sides
     for (int l = 0; l < ND; ++l) {
       const LineBuf& lb = L.dfLB[l];
-      launch_rhs_c6<ND, T>(fb, L.fbx, ND + 3, lb, df[l], st);
-      s->launches++;
-      jobs[l] = LineJob<T>{&s->c6grad[l], df[l], lb.nl, ND + 3};
+      if (fused) {
+        jobs[l].src = C6Src<T>{fb, L.fbx, L.fbx.size(), lb};
+      } else {
+        launch_rhs_c6<ND, T>(fb, L.fbx, ND + 3, lb, df[l], st);
+        s->launches++;
+      }
     }
     launch_lines(jobs, ND, st);
     s->launches++;
@@ -239,10 +244,15 @@ static int lad_pass(cg_solver* s, int dkind, StageArgs A, cudaStream_t st, const
     LineBuf DL = L.DLB[l];
     if (dkind == 3) {
       T* Dw = reinterpret_cast<T*>(L.D);
-      launch_rhs_c6<ND, T>(reinterpret_cast<const T*>(L.Fn), L.fbox[l], ND + 2, DL, Dw, st);
       LineJob<T> job{&s->c6flux[l], Dw, DL.nl, ND + 2};
+      if (lines_partitioned(&job, 1)) {  // the solver forms the right-hand sides
+        job.src = C6Src<T>{reinterpret_cast<const T*>(L.Fn), L.fbox[l], L.fbox[l].size(), DL};
+      } else {
+        launch_rhs_c6<ND, T>(reinterpret_cast<const T*>(L.Fn), L.fbox[l], ND + 2, DL, Dw, st);
+        s->launches++;
+      }
       launch_lines(&job, 1, st);
-      s->launches += 2;
+      s->launches++;
       D = Dw;
     }
     if (ND >= 2 && l == 0 && D) {  // x lines: the tiled read of the line buffer

@@ -198,9 +198,21 @@ struct PartCoefT {
 };
 using PartCoef = PartCoefT<double>;
 
+// The source of a C6 line family whose right-hand sides the partitioned
+// solver forms itself: nc planes of fs values of a node field on box fb,
+// differenced along lb.  f = null: the right-hand sides are already in x.
+template <typename T>
+struct C6Src {
+  const T* f = nullptr;
+  Box fb{};
+  long long fs = 0;
+  LineBuf lb{};
+};
+
 template <typename T>
 struct PartJobsT {
   PartCoefT<T> pc[3];
+  C6Src<T> src[3];
   T* x[3];
   long long nl[3];
   int ncomp[3];
@@ -243,6 +255,50 @@ __device__ __forceinline__ T part_forward(T* __restrict__ col, long long nl, con
   for (int i = i0 + nfull * B; i < i1; ++i) {
     y = fma_t(-aL[i], y, col[(long long)i * nl]) * rd[i];
     col[(long long)i * nl] = y;
+  }
+  return y;
+}
+
+// part_forward with the C6 right-hand side of each row formed on the way from
+// the source field along the line (fp: the column's component at position 0,
+// st: the stride between positions): r_i = 7/9 (f_{p+1} - f_{p-1}) +
+// 1/36 (f_{p+2} - f_{p-2}), or the E4 closure d4 on the end rows of a
+// non-periodic line, the expressions of k_rhs_c6 / XTileC6.  A window of the
+// five positions around the row slides along; the values entering it are
+// loaded B rows ahead.  The right-hand sides are never stored.
+template <typename T, int B>
+__device__ __forceinline__ T part_forward_c6(T* __restrict__ col, long long nl, const T* __restrict__ aL,
+                                             const T* __restrict__ rd, int i0, int i1, const T* __restrict__ fp,
+                                             long long st, int lo, int m, bool periodic) {
+  const int p0 = periodic ? i0 : lo + i0;
+  auto F = [&](int pos) { return fp[(long long)pos * st]; };
+  T w0 = F(p0 - 2), w1 = F(p0 - 1), w2 = F(p0), w3 = F(p0 + 1), w4 = F(p0 + 2);
+  T pre[B];
+#pragma unroll
+  for (int k = 0; k < B; ++k) pre[k] = (i0 + k + 1 < i1) ? F(p0 + 3 + k) : T(0);
+  T y = T(0);
+  for (int base = i0; base < i1; base += B) {
+    const int pb = p0 + (base - i0);
+    T nxt[B];
+#pragma unroll
+    for (int k = 0; k < B; ++k) nxt[k] = (base + B + k + 1 < i1) ? F(pb + B + 3 + k) : T(0);
+#pragma unroll
+    for (int k = 0; k < B; ++k) {
+      const int i = base + k;
+      if (i < i1) {
+        const bool closure = !periodic && (i == 0 || i == m - 1);
+        const T r = closure ? d4(w0, w1, w3, w4) : T(7.0 / 9.0) * (w3 - w1) + T(1.0 / 36.0) * (w4 - w0);
+        y = fma_t(-aL[i], y, r) * rd[i];
+        col[(long long)i * nl] = y;
+        w0 = w1;
+        w1 = w2;
+        w2 = w3;
+        w3 = w4;
+        w4 = pre[k];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < B; ++k) pre[k] = nxt[k];
   }
   return y;
 }
@@ -293,7 +349,19 @@ __global__ void __launch_bounds__(1024) k_tri_part(PartJobsT<T> J) {
   const int s = k * pc.q, e = min(pc.m, s + pc.q);
   const bool mine = active && k < pc.P && s < e;
   if (mine) {
-    T y = part_forward<T, PB>(col, nl, pc.aL, pc.rd, s, e);
+    const C6Src<T>& sr = J.src[j];
+    T y;
+    if (sr.f) {  // form the C6 right-hand sides on the way
+      int cc[3] = {0, 0, 0};
+      sr.lb.coords(c % nl, cc);
+      cc[sr.lb.d] = 0;
+      const int d = sr.lb.d;
+      const long long st = d == 0 ? 1 : (d == 1 ? (long long)sr.fb.ext[0] : (long long)sr.fb.ext[0] * sr.fb.ext[1]);
+      const T* fp = sr.f + (c / nl) * sr.fs + sr.fb.at(cc[0], cc[1], cc[2]);
+      y = part_forward_c6<T, PB>(col, nl, pc.aL, pc.rd, s, e, fp, st, sr.lb.lo, pc.m, pc.periodic != 0);
+    } else {
+      y = part_forward<T, PB>(col, nl, pc.aL, pc.rd, s, e);
+    }
     sYL[k][lane] = y;
     y = thomas_backward<T, PB>(col, nl, pc.cp, s, e - 2, y);
     sYF[k][lane] = y;
