@@ -25,8 +25,9 @@ static int lad_alloc(cg_solver* s) {
   if ((rc = dalloc(&L.fb, (size_t)nf * L.fbx.size())) || (rc = dalloc(&L.gr, (size_t)nf * nd * L.b3.size())) ||
       (rc = dalloc(&L.dv, (size_t)L.b3.size())) || (rc = dalloc(&L.bt[0], (size_t)s->N)) ||
       (rc = dalloc(&L.bt[1], (size_t)s->N)) || (rc = dalloc(&L.kp[0], (size_t)s->N)) ||
-      (rc = dalloc(&L.kp[1], (size_t)s->N)) || (rc = dalloc(&L.Fn, (size_t)nv * fmax)))
+      (rc = dalloc(&L.kp[1], (size_t)s->N)) || (rc = dalloc(&L.Fn, (size_t)nv * fmax * (sch == CG_LAD_C6 ? nd : 1))))
     return rc;
+  L.fstride = (size_t)nv * fmax;
   if (s->p.viscous) {
     L.vbx = make_box(s, 2, -1, 2);
     if ((rc = dalloc(&L.vco, (size_t)3 * L.vbx.size()))) return rc;
@@ -52,7 +53,10 @@ static int lad_alloc(cg_solver* s) {
       if ((rc = upload_line(s->c6flux[d], n, 1.0 / 3.0, cyc, 0, L.DLB[d].nl * nv))) return rc;
       if ((rc = upload_line(s->filt[d], cyc ? n : n + 2, s->p.alpha_f, cyc, -1, L.filtLB[d].nl * nv))) return rc;
     }
-    if ((rc = dalloc(&L.D, dmax)) || (rc = dalloc(&L.lines, fl))) return rc;
+    // LAD-C6: node fluxes and derivatives of every direction held at once (one
+    // launch solves all directions' flux lines)
+    if ((rc = dalloc(&L.D, dmax * nd)) || (rc = dalloc(&L.lines, fl))) return rc;
+    L.dstride = dmax;
   }
   if (sch == CG_HYBRID) {
     if ((rc = dalloc(&L.tr, (size_t)L.tbox.size()))) return rc;
@@ -146,14 +150,14 @@ static int lad_coeffs_run(cg_solver* s, int dkind, cudaStream_t st, const int* g
 }
 
 template <int ND, int MODE, typename T>
-static void lad_nodeflux_m(cg_solver* s, int l, cudaStream_t st, const int* guard, int want) {
+static void lad_nodeflux_m(cg_solver* s, int l, cudaStream_t st, const int* guard, int want, T* out) {
   LadBuffers& L = s->lad;
   int gb = grid_blocks(L.fbox[l].size(), 128);
   const T* bt = reinterpret_cast<const T*>(L.bt[0]);
   const T* kp = reinterpret_cast<const T*>(L.kp[0]);
   const T* gr = reinterpret_cast<const T*>(L.gr);
   const T* dv = reinterpret_cast<const T*>(L.dv);
-  T* Fn = reinterpret_cast<T*>(L.Fn);
+  T* Fn = out ? out : reinterpret_cast<T*>(L.Fn);
   const T* vco = reinterpret_cast<const T*>(L.vco);
   if (s->dg.curv)
     k_lad_nodeflux<ND, false, MODE, T><<<gb, 128, 0, st>>>(s->dg, l, reinterpret_cast<const T*>(s->W), bt, kp, gr, dv, L.b3, vco, L.vbx, Fn, L.fbox[l], guard, want);
@@ -179,11 +183,13 @@ static void lad_viscoef(cg_solver* s, cudaStream_t st, const int* guard, int wan
 
 // node fluxes along l: mode NF_LAD (artificial terms only), NF_LAD_VISC (plus
 // the physical viscosity) or NF_VISC (the physical viscous flux alone)
+// (out: where the fluxes go, the shared node-flux buffer when null)
 template <int ND, typename T = double>
-static void lad_nodeflux(cg_solver* s, int l, cudaStream_t st, const int* guard, int want, int mode = NF_LAD) {
-  if (mode == NF_VISC) lad_nodeflux_m<ND, NF_VISC, T>(s, l, st, guard, want);
-  else if (mode == NF_LAD_VISC) lad_nodeflux_m<ND, NF_LAD_VISC, T>(s, l, st, guard, want);
-  else lad_nodeflux_m<ND, NF_LAD, T>(s, l, st, guard, want);
+static void lad_nodeflux(cg_solver* s, int l, cudaStream_t st, const int* guard, int want, int mode = NF_LAD,
+                         T* out = nullptr) {
+  if (mode == NF_VISC) lad_nodeflux_m<ND, NF_VISC, T>(s, l, st, guard, want, out);
+  else if (mode == NF_LAD_VISC) lad_nodeflux_m<ND, NF_LAD_VISC, T>(s, l, st, guard, want, out);
+  else lad_nodeflux_m<ND, NF_LAD, T>(s, l, st, guard, want, out);
 }
 
 // E4 gradients of the LAD fields of the primitives in s->W (no coefficients)
@@ -236,25 +242,39 @@ static int lad_pass(cg_solver* s, int dkind, StageArgs A, cudaStream_t st, const
   if (rc) return rc;
   LadBuffers& L = s->lad;
   if (s->p.viscous) lad_viscoef<ND, T>(s, st, guard, want, true);
+  const int nfm = s->p.viscous ? NF_LAD_VISC : NF_LAD;
+  // C6: every direction's node fluxes and flux lines first (each in its own
+  // slice), solved in one launch when all are partitioned; then the divergences
+  const T* Dl[3] = {nullptr, nullptr, nullptr};
+  if (dkind == 3) {
+    LineJob<T> jobs[3];
+    const T* Fl[3];
+    for (int l = 0; l < ND; ++l) {
+      T* Fw = reinterpret_cast<T*>(L.Fn) + (size_t)l * L.fstride;
+      lad_nodeflux<ND, T>(s, l, st, guard, want, nfm, Fw);
+      Fl[l] = Fw;
+      T* Dw = reinterpret_cast<T*>(L.D) + (size_t)l * L.dstride;
+      jobs[l] = LineJob<T>{&s->c6flux[l], Dw, L.DLB[l].nl, ND + 2};
+      Dl[l] = Dw;
+    }
+    if (lines_partitioned(jobs, ND)) {  // the solver forms the right-hand sides
+      for (int l = 0; l < ND; ++l) jobs[l].src = C6Src<T>{Fl[l], L.fbox[l], L.fbox[l].size(), L.DLB[l]};
+      launch_lines(jobs, ND, st);
+      s->launches++;
+    } else {
+      for (int l = 0; l < ND; ++l) {
+        launch_rhs_c6<ND, T>(Fl[l], L.fbox[l], ND + 2, L.DLB[l], const_cast<T*>(Dl[l]), st);
+        launch_lines(&jobs[l], 1, st);
+        s->launches += 2;
+      }
+    }
+  }
   for (int l = 0; l < ND; ++l) {
     A.first = l == 0;
     A.last = l == ND - 1;
-    lad_nodeflux<ND, T>(s, l, st, guard, want, s->p.viscous ? NF_LAD_VISC : NF_LAD);
-    const T* D = nullptr;
+    if (dkind != 3) lad_nodeflux<ND, T>(s, l, st, guard, want, nfm);
+    const T* D = Dl[l];
     LineBuf DL = L.DLB[l];
-    if (dkind == 3) {
-      T* Dw = reinterpret_cast<T*>(L.D);
-      LineJob<T> job{&s->c6flux[l], Dw, DL.nl, ND + 2};
-      if (lines_partitioned(&job, 1)) {  // the solver forms the right-hand sides
-        job.src = C6Src<T>{reinterpret_cast<const T*>(L.Fn), L.fbox[l], L.fbox[l].size(), DL};
-      } else {
-        launch_rhs_c6<ND, T>(reinterpret_cast<const T*>(L.Fn), L.fbox[l], ND + 2, DL, Dw, st);
-        s->launches++;
-      }
-      launch_lines(&job, 1, st);
-      s->launches++;
-      D = Dw;
-    }
     if (ND >= 2 && l == 0 && D) {  // x lines: the tiled read of the line buffer
       const long long ty = (DL.nl + LGT_Y - 1) / LGT_Y;
       const unsigned gy = (unsigned)std::min<long long>(ty, 65535), gz = (unsigned)((ty + gy - 1) / gy);
