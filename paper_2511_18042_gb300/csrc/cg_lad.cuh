@@ -622,6 +622,52 @@ __global__ void __launch_bounds__(LGT_X * LGT_Y) k_lad_div_xt(DevGrid g, const T
   lad_epilogue<ND, sizeof(T) == 4, T>(g, A, lin(g, c[0], c[1], c[2]), c, Dv);
 }
 
+// The C6 divergences of all directions in one pass on the tiles of
+// k_lad_div_xt: the x derivatives staged through shared memory, the y (and z)
+// derivatives read directly, summed in the order of the per-direction
+// launches (x, then y, then z, in the accumulator's type), then one epilogue.
+template <int ND, typename T>
+__global__ void __launch_bounds__(LGT_X * LGT_Y) k_lad_div_all_xt(DevGrid g, const T* __restrict__ D0, LineBuf DL0,
+                                                                const T* __restrict__ D1, LineBuf DL1,
+                                                                const T* __restrict__ D2, LineBuf DL2, StageArgs A,
+                                                                const int* guard, int want) {
+  constexpr int NV = ND + 2;
+  using TA = typename std::conditional<sizeof(T) == 4, float, double>::type;
+  __shared__ T sD[NV][LGT_Y][LGT_X + 1];
+  if (guard && *guard != want) return;
+  const int x0 = (int)blockIdx.x * LGT_X;
+  const long long L0 = (long long)blockIdx.y * LGT_Y + (long long)blockIdx.z * gridDim.y * LGT_Y;
+  const int tid = threadIdx.y * LGT_X + threadIdx.x;
+  {
+    const int ly = tid % LGT_Y, lx = tid / LGT_Y;
+    if (x0 + lx < g.n[0] && L0 + ly < DL0.nl) {
+      int c[3] = {0, 0, 0};
+      DL0.coords(L0 + ly, c);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) sD[v][ly][lx] = D0[DL0.at(v, x0 + lx, c)];
+    }
+  }
+  __syncthreads();
+  const int x = x0 + (int)threadIdx.x;
+  const long long L = L0 + threadIdx.y;
+  if (x >= g.n[0] || L >= DL0.nl) return;
+  int c[3] = {0, 0, 0};
+  DL0.coords(L, c);
+  c[0] = x;
+  T Dv[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    TA t = TA(sD[v][threadIdx.y][threadIdx.x]);
+    t = t + TA(D1[DL1.at(v, c[1], c)]);
+    if (ND == 3) t = t + TA(D2[DL2.at(v, c[2], c)]);
+    Dv[v] = T(t);
+  }
+  StageArgs B = A;
+  B.first = 1;
+  B.last = 1;
+  lad_epilogue<ND, sizeof(T) == 4, T>(g, B, lin(g, c[0], c[1], c[2]), c, Dv);
+}
+
 // Troubled-node criterion of Sec. 5 at node (x, y, z) (ghost-resolved):
 // rho < hyb_rho or p < hyb_p, or (with the sensor) Omega > threshold.
 // The criterion's thresholds in the stored type TW.  For FP32 storage they are

@@ -269,6 +269,17 @@ static int lad_pass(cg_solver* s, int dkind, StageArgs A, cudaStream_t st, const
       }
     }
   }
+  if (ND >= 2 && dkind == 3) {  // all directions' divergences in one tiled pass
+    const LineBuf& DL = L.DLB[0];
+    const long long ty = (DL.nl + LGT_Y - 1) / LGT_Y;
+    const unsigned gy = (unsigned)std::min<long long>(ty, 65535), gz = (unsigned)((ty + gy - 1) / gy);
+    if constexpr (ND >= 2)
+      k_lad_div_all_xt<ND, T><<<dim3((unsigned)((s->dg.n[0] + LGT_X - 1) / LGT_X), gy, gz), dim3(LGT_X, LGT_Y), 0,
+                                st>>>(s->dg, Dl[0], L.DLB[0], Dl[1], L.DLB[1], Dl[2], L.DLB[ND == 3 ? 2 : 1], A, guard,
+                                      want);
+    s->launches++;
+    return CG_OK;
+  }
   for (int l = 0; l < ND; ++l) {
     A.first = l == 0;
     A.last = l == ND - 1;
@@ -381,7 +392,14 @@ static int lad_filter(cg_solver* s, double* U, cudaStream_t st) {
       }
       LineJob<float> job{&s->filt[l], x, lb.nl, ND + 2};
       launch_lines(&job, 1, st);
-      k_filter_store_inc<ND><<<grid_blocks(s->N, 256), 256, 0, st>>>(s->dg, x, lb, U);
+      if (ND >= 2 && l == 0) {  // x lines: the tiled read of the line buffer
+        const long long ty = (lb.nl + FST_Y - 1) / FST_Y;
+        const unsigned gy = (unsigned)std::min<long long>(ty, 65535), gz = (unsigned)((ty + gy - 1) / gy);
+        k_filter_store_inc_xt<ND><<<dim3((unsigned)((s->dg.n[0] + FST_X - 1) / FST_X), gy, gz), dim3(FST_X, FST_Y), 0,
+                                    st>>>(s->dg, x, lb, U);
+      } else {
+        k_filter_store_inc<ND><<<grid_blocks(s->N, 256), 256, 0, st>>>(s->dg, x, lb, U);
+      }
       s->launches += 3;
     }
     return CG_OK;

@@ -741,4 +741,42 @@ __global__ void k_filter_store_inc(DevGrid g, const float* __restrict__ x, LineB
   }
 }
 
+// k_filter_store_inc for lines along x on tiles of 32 positions x 8 lines:
+// the tile's increments are staged with consecutive threads on consecutive
+// lines (the x-line buffer keeps a line's positions a line count apart),
+// then each thread updates one node.
+constexpr int FST_X = 32, FST_Y = 8;
+template <int ND>
+__global__ void __launch_bounds__(FST_X * FST_Y) k_filter_store_inc_xt(DevGrid g, const float* __restrict__ x,
+                                                                       LineBuf lb, double* __restrict__ U) {
+  constexpr int NV = ND + 2;
+  __shared__ float sD[NV][FST_Y][FST_X + 1];
+  const int x0 = (int)blockIdx.x * FST_X;
+  const long long L0 = (long long)blockIdx.y * FST_Y + (long long)blockIdx.z * gridDim.y * FST_Y;
+  const int tid = threadIdx.y * FST_X + threadIdx.x;
+  {
+    const int ly = tid % FST_Y, lx = tid / FST_Y;
+    if (x0 + lx < g.n[0] && L0 + ly < lb.nl) {
+      int c[3] = {0, 0, 0};
+      lb.coords(L0 + ly, c);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) sD[v][ly][lx] = x[lb.at(v, x0 + lx, c)];
+    }
+  }
+  __syncthreads();
+  const int xi = x0 + (int)threadIdx.x;
+  const long long L = L0 + threadIdx.y;
+  if (xi >= g.n[0] || L >= lb.nl) return;
+  int c[3] = {0, 0, 0};
+  lb.coords(L, c);
+  c[0] = xi;
+  const long long q = lin(g, c[0], c[1], c[2]);
+  const float J = g.curv ? d2f_int(g.jac[plin(g, c[0], c[1], c[2])]) : 1.0f;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const float d = sD[v][threadIdx.y][threadIdx.x];
+    U[v * g.N + q] = U[v * g.N + q] + f2d_int(g.curv ? J * d : d);
+  }
+}
+
 }  // namespace cgk
