@@ -34,13 +34,14 @@ static int lad_alloc(cg_solver* s) {
   }
   if (sch == CG_LAD_C6) {
     size_t dmax = 0, fl = 0;
-    long long grad_cols = 0;
+    long long grad_cols = 0, flux_cols = 0;
     for (int d = 0; d < nd; ++d) {
       int n = s->dg.n[d];
       L.dfLB[d] = make_lines(s, d, -6, n + 12, 3);
       L.DLB[d] = make_lines(s, d, 0, n, 0);
       L.filtLB[d] = make_lines(s, d, -1, n + 2, 0);
       grad_cols += L.dfLB[d].nl * nf;
+      flux_cols += L.DLB[d].nl * nv;
     }
     for (int d = 0; d < nd; ++d) {
       bool cyc = s->grid->bc[d][0] == CG_BC_PERIODIC;
@@ -50,7 +51,8 @@ static int lad_alloc(cg_solver* s) {
       dmax = std::max(dmax, (size_t)nv * (size_t)L.DLB[d].m * (size_t)L.DLB[d].nl);
       fl = std::max(fl, (size_t)nv * (size_t)L.filtLB[d].m * (size_t)L.filtLB[d].nl);
       if ((rc = upload_line(s->c6grad[d], cyc ? n : n + 12, 1.0 / 3.0, cyc, -6, grad_cols))) return rc;
-      if ((rc = upload_line(s->c6flux[d], n, 1.0 / 3.0, cyc, 0, L.DLB[d].nl * nv))) return rc;
+      // all directions' flux lines are solved in one launch: partitions for their total
+      if ((rc = upload_line(s->c6flux[d], n, 1.0 / 3.0, cyc, 0, flux_cols))) return rc;
       if ((rc = upload_line(s->filt[d], cyc ? n : n + 2, s->p.alpha_f, cyc, -1, L.filtLB[d].nl * nv))) return rc;
     }
     // LAD-C6: node fluxes and derivatives of every direction held at once (one
