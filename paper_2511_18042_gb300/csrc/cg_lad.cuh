@@ -18,6 +18,7 @@ struct LadBuffers {
   double* Fn = nullptr;     // node fluxes along a direction: nv planes on fbox (positions [-2, n+1]);
                             // LAD-C6 holds every direction's (slices fstride apart)
   double* D = nullptr;      // C6 flux derivatives, one line buffer DLB per direction
+  Box ubx{};                // [-2, n+1] in every direction: the union of the node-flux boxes
   size_t fstride = 0;       // LAD-C6: values between the directions' node-flux slices of Fn
   size_t dstride = 0;       // values between the directions' slices of D
   double* df[3] = {nullptr, nullptr, nullptr};  // C6 computational derivatives of the fields (line buffers)
@@ -487,6 +488,41 @@ __device__ __forceinline__ void k_lad_nodeflux_body(const VBlock& vb, const DevG
     nodeflux_at<ND, CART, MODE, T>(g, l, W, bt, kp, gr, dv, b3, vco, vbx, c, F);
 #pragma unroll
     for (int v = 0; v < NV; ++v) Fn[v * fs + e] = F[v];
+  }
+}
+
+// The node fluxes of every direction in one pass over ub (the union of the
+// directions' boxes, positions [-2, n+1] in every direction): each node forms
+// all directions' fluxes (the loads they share, issued once) and stores those
+// whose box holds it; the values are those of k_lad_nodeflux.
+__device__ __forceinline__ bool box_holds(const Box& b, const int* c) {
+  return c[0] + b.off[0] >= 0 && c[0] + b.off[0] < b.ext[0] && c[1] + b.off[1] >= 0 && c[1] + b.off[1] < b.ext[1] &&
+         c[2] + b.off[2] >= 0 && c[2] + b.off[2] < b.ext[2];
+}
+
+template <int ND, bool CART, int MODE, typename T>
+__global__ void k_lad_nodeflux_all(DevGrid g, const T* __restrict__ W, const T* __restrict__ bt,
+                                   const T* __restrict__ kp, const T* __restrict__ gr, const T* __restrict__ dv, Box b3,
+                                   const T* __restrict__ vco, Box vbx, T* __restrict__ F0, Box fb0, T* __restrict__ F1,
+                                   Box fb1, T* __restrict__ F2, Box fb2, Box ub, const int* guard, int want) {
+  constexpr int NV = ND + 2;
+  if (guard && *guard != want) return;
+  const VBlock vb = hw_block();
+  BOX_LOOP(ub, e) {
+    int c[3];
+    box_coords(ub, e, c);
+    T F[3][NV];
+#pragma unroll
+    for (int l = 0; l < ND; ++l) nodeflux_at<ND, CART, MODE, T>(g, l, W, bt, kp, gr, dv, b3, vco, vbx, c, F[l]);
+#pragma unroll
+    for (int l = 0; l < ND; ++l) {
+      const Box& fb = l == 0 ? fb0 : (l == 1 ? fb1 : fb2);
+      T* Fo = l == 0 ? F0 : (l == 1 ? F1 : F2);
+      if (!box_holds(fb, c)) continue;
+      const long long fs = fb.size(), q = fb.at(c[0], c[1], c[2]);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) Fo[v * fs + q] = F[l][v];
+    }
   }
 }
 

@@ -11,6 +11,7 @@ static int lad_alloc(cg_solver* s) {
   L.fbx = make_box(s, 8, -1, 8);
   L.b3 = make_box(s, 3, -1, 3);
   L.tbox = make_box(s, 1, -1, 1);
+  L.ubx = make_box(s, 2, -1, 2);
   size_t fmax = 0;
   for (int d = 0; d < nd; ++d) {
     L.fbox[d] = make_box(s, 0, d, 2);
@@ -194,6 +195,34 @@ static void lad_nodeflux(cg_solver* s, int l, cudaStream_t st, const int* guard,
   else lad_nodeflux_m<ND, NF_LAD, T>(s, l, st, guard, want, out);
 }
 
+// node fluxes of every direction in one launch (k_lad_nodeflux_all), into out[l]
+template <int ND, int MODE, typename T>
+static void lad_nodeflux_all_m(cg_solver* s, cudaStream_t st, const int* guard, int want, T* const* out) {
+  LadBuffers& L = s->lad;
+  const Box& ub = L.ubx;  // [-2, n+1] in every direction
+  const int gb = grid_blocks(ub.size(), 128);
+  const T* W = reinterpret_cast<const T*>(s->W);
+  const T* bt = reinterpret_cast<const T*>(L.bt[0]);
+  const T* kp = reinterpret_cast<const T*>(L.kp[0]);
+  const T* gr = reinterpret_cast<const T*>(L.gr);
+  const T* dv = reinterpret_cast<const T*>(L.dv);
+  const T* vco = reinterpret_cast<const T*>(L.vco);
+  const Box& f2 = L.fbox[ND == 3 ? 2 : 0];
+  if (s->dg.curv)
+    k_lad_nodeflux_all<ND, false, MODE, T><<<gb, 128, 0, st>>>(s->dg, W, bt, kp, gr, dv, L.b3, vco, L.vbx, out[0],
+                                                               L.fbox[0], out[1], L.fbox[1], out[2], f2, ub, guard, want);
+  else
+    k_lad_nodeflux_all<ND, true, MODE, T><<<gb, 128, 0, st>>>(s->dg, W, bt, kp, gr, dv, L.b3, vco, L.vbx, out[0],
+                                                              L.fbox[0], out[1], L.fbox[1], out[2], f2, ub, guard, want);
+  s->launches++;
+}
+
+template <int ND, typename T>
+static void lad_nodeflux_all(cg_solver* s, cudaStream_t st, const int* guard, int want, int mode, T* const* out) {
+  if (mode == NF_LAD_VISC) lad_nodeflux_all_m<ND, NF_LAD_VISC, T>(s, st, guard, want, out);
+  else lad_nodeflux_all_m<ND, NF_LAD, T>(s, st, guard, want, out);
+}
+
 // E4 gradients of the LAD fields of the primitives in s->W (no coefficients)
 template <int ND, typename T>
 static void lad_grad_e4(cg_solver* s, cudaStream_t st, const int* guard, int want) {
@@ -251,10 +280,11 @@ static int lad_pass(cg_solver* s, int dkind, StageArgs A, cudaStream_t st, const
   if (dkind == 3) {
     LineJob<T> jobs[3];
     const T* Fl[3];
+    T* Fw[3] = {nullptr, nullptr, nullptr};
+    for (int l = 0; l < ND; ++l) Fw[l] = reinterpret_cast<T*>(L.Fn) + (size_t)l * L.fstride;
+    lad_nodeflux_all<ND, T>(s, st, guard, want, nfm, Fw);
     for (int l = 0; l < ND; ++l) {
-      T* Fw = reinterpret_cast<T*>(L.Fn) + (size_t)l * L.fstride;
-      lad_nodeflux<ND, T>(s, l, st, guard, want, nfm, Fw);
-      Fl[l] = Fw;
+      Fl[l] = Fw[l];
       T* Dw = reinterpret_cast<T*>(L.D) + (size_t)l * L.dstride;
       jobs[l] = LineJob<T>{&s->c6flux[l], Dw, L.DLB[l].nl, ND + 2};
       Dl[l] = Dw;
