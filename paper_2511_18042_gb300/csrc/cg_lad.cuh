@@ -15,11 +15,11 @@ struct LadBuffers {
   double* dv = nullptr;     // dilatation on b3
   double* bt[2] = {nullptr, nullptr};  // beta* (ping-pong, interior)
   double* kp[2] = {nullptr, nullptr};  // kappa*
-  double* Fn = nullptr;     // node fluxes along a direction: nv planes on fbox (positions [-2, n+1]);
-                            // LAD-C6 holds every direction's (slices fstride apart)
+  double* Fn = nullptr;     // node fluxes: nv planes on fbox (positions [-2, n+1]) per direction,
+                            // every direction's held at once (slices fstride apart)
   double* D = nullptr;      // C6 flux derivatives, one line buffer DLB per direction
   Box ubx{};                // [-2, n+1] in every direction: the union of the node-flux boxes
-  size_t fstride = 0;       // LAD-C6: values between the directions' node-flux slices of Fn
+  size_t fstride = 0;       // values between the directions' node-flux slices of Fn
   size_t dstride = 0;       // values between the directions' slices of D
   double* df[3] = {nullptr, nullptr, nullptr};  // C6 computational derivatives of the fields (line buffers)
   double* lines = nullptr;  // right-hand sides / solutions of the filter lines

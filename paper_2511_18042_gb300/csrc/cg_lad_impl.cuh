@@ -26,7 +26,7 @@ static int lad_alloc(cg_solver* s) {
   if ((rc = dalloc(&L.fb, (size_t)nf * L.fbx.size())) || (rc = dalloc(&L.gr, (size_t)nf * nd * L.b3.size())) ||
       (rc = dalloc(&L.dv, (size_t)L.b3.size())) || (rc = dalloc(&L.bt[0], (size_t)s->N)) ||
       (rc = dalloc(&L.bt[1], (size_t)s->N)) || (rc = dalloc(&L.kp[0], (size_t)s->N)) ||
-      (rc = dalloc(&L.kp[1], (size_t)s->N)) || (rc = dalloc(&L.Fn, (size_t)nv * fmax * (sch == CG_LAD_C6 ? nd : 1))))
+      (rc = dalloc(&L.kp[1], (size_t)s->N)) || (rc = dalloc(&L.Fn, (size_t)nv * fmax * nd)))
     return rc;
   L.fstride = (size_t)nv * fmax;
   if (s->p.viscous) {
@@ -312,10 +312,15 @@ static int lad_pass(cg_solver* s, int dkind, StageArgs A, cudaStream_t st, const
     s->launches++;
     return CG_OK;
   }
+  // E4: every direction's node fluxes in one pass too (slices of Fn)
+  T* Fe[3] = {nullptr, nullptr, nullptr};
+  if (dkind != 3) {
+    for (int l = 0; l < ND; ++l) Fe[l] = reinterpret_cast<T*>(L.Fn) + (size_t)l * L.fstride;
+    lad_nodeflux_all<ND, T>(s, st, guard, want, nfm, Fe);
+  }
   for (int l = 0; l < ND; ++l) {
     A.first = l == 0;
     A.last = l == ND - 1;
-    if (dkind != 3) lad_nodeflux<ND, T>(s, l, st, guard, want, nfm);
     const T* D = Dl[l];
     LineBuf DL = L.DLB[l];
     if (ND >= 2 && l == 0 && D) {  // x lines: the tiled read of the line buffer
@@ -325,8 +330,8 @@ static int lad_pass(cg_solver* s, int dkind, StageArgs A, cudaStream_t st, const
         k_lad_div_xt<ND, T><<<dim3((unsigned)((s->dg.n[0] + LGT_X - 1) / LGT_X), gy, gz), dim3(LGT_X, LGT_Y), 0, st>>>(
             s->dg, D, DL, A, guard, want);
     } else {
-      k_lad_div<ND, T><<<grid_blocks(s->N, 256), 256, 0, st>>>(s->dg, l, reinterpret_cast<const T*>(L.Fn), L.fbox[l], D,
-                                                              DL, A, guard, want);
+      k_lad_div<ND, T><<<grid_blocks(s->N, 256), 256, 0, st>>>(s->dg, l, Fe[l] ? Fe[l] : reinterpret_cast<const T*>(L.Fn),
+                                                              L.fbox[l], D, DL, A, guard, want);
     }
     s->launches++;
   }
