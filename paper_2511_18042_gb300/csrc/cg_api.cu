@@ -728,6 +728,17 @@ static bool lines_partitioned(const LineJob<T>* jobs, int n) {
   return part;
 }
 
+// Whether the solver should form the C6 right-hand sides itself: partitioned,
+// and with columns enough (32 an SM) that the longer chunk prologue (the
+// window and its look-ahead loads) is hidden; a latency-bound launch of a few
+// columns (a 1D tube) keeps the separate right-hand-side pass.
+template <typename T>
+static bool rhs_in_solver(const LineJob<T>* jobs, int n) {
+  long long cols = 0;
+  for (int j = 0; j < n; ++j) cols += jobs[j].nl * jobs[j].ncomp;
+  return lines_partitioned(jobs, n) && cols >= 152LL * 32;
+}
+
 template <typename T>
 static void launch_lines(const LineJob<T>* jobs, int n, cudaStream_t st) {
   bool part = true;

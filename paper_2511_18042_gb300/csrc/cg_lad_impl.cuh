@@ -99,7 +99,7 @@ static int lad_coeffs_run(cg_solver* s, int dkind, cudaStream_t st, const int* g
   if (c6) {
     LineJob<T> jobs[3];
     for (int l = 0; l < ND; ++l) jobs[l] = LineJob<T>{&s->c6grad[l], df[l], L.dfLB[l].nl, ND + 3};
-    const bool fused = lines_partitioned(jobs, ND);  // the solver forms the right-hand sides
+    const bool fused = rhs_in_solver(jobs, ND);  // the solver forms the right-hand sides
     for (int l = 0; l < ND; ++l) {
       const LineBuf& lb = L.dfLB[l];
       if (fused) {
@@ -289,7 +289,7 @@ static int lad_pass(cg_solver* s, int dkind, StageArgs A, cudaStream_t st, const
       jobs[l] = LineJob<T>{&s->c6flux[l], Dw, L.DLB[l].nl, ND + 2};
       Dl[l] = Dw;
     }
-    if (lines_partitioned(jobs, ND)) {  // the solver forms the right-hand sides
+    if (rhs_in_solver(jobs, ND)) {  // the solver forms the right-hand sides
       for (int l = 0; l < ND; ++l) jobs[l].src = C6Src<T>{Fl[l], L.fbox[l], L.fbox[l].size(), L.DLB[l]};
       launch_lines(jobs, ND, st);
       s->launches++;
