@@ -714,6 +714,7 @@ __global__ void __launch_bounds__(LGT_X * LGT_Y) k_lad_div_all_xt(DevGrid g, con
 template <typename TW>
 struct TroubleThr {
   TW hr, hp, thr;
+  TroubleThr() = default;
   __device__ explicit TroubleThr(double r, double p, double t) {
     if constexpr (sizeof(TW) == 4) {
       hr = f32_up(r);
@@ -757,7 +758,20 @@ __device__ __forceinline__ void k_troubled_body(const VBlock& vb, const DevGrid&
                            Box ob, double thr, unsigned char* __restrict__ tr, Box tb, int* flag,
                            unsigned long long* count, int buf = 0) {
   unsigned long long local = 0;
-  const TroubleThr<TW> th(hr, hp, thr);
+  // the thresholds in TW, rounded once per block (FP64 work) and shared
+  __shared__ TW s_th[3];
+  __syncthreads();  // a block running several members' jobs: the previous member's reads are done
+  if (threadIdx.x == 0) {
+    const TroubleThr<TW> t0(hr, hp, thr);
+    s_th[0] = t0.hr;
+    s_th[1] = t0.hp;
+    s_th[2] = t0.thr;
+  }
+  __syncthreads();
+  TroubleThr<TW> th;
+  th.hr = s_th[0];
+  th.hp = s_th[1];
+  th.thr = s_th[2];
   BOX_LOOP(tb, e) {
     int c[3];
     box_coords(tb, e, c);
