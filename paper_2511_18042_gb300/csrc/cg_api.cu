@@ -728,15 +728,16 @@ static bool lines_partitioned(const LineJob<T>* jobs, int n) {
   return part;
 }
 
-// Whether the solver should form the C6 right-hand sides itself: partitioned,
-// and with columns enough (32 an SM) that the longer chunk prologue (the
-// window and its look-ahead loads) is hidden; a latency-bound launch of a few
-// columns (a 1D tube) keeps the separate right-hand-side pass.
+// Whether the solver should form the C6 right-hand sides itself: always on
+// the one-thread-per-line path (taken when lines are many), and on the
+// partitioned path with columns enough (32 an SM) that the longer chunk
+// prologue (the window and its look-ahead loads) is hidden; a latency-bound
+// launch of a few columns (a 1D tube) keeps the separate right-hand-side pass.
 template <typename T>
 static bool rhs_in_solver(const LineJob<T>* jobs, int n) {
   long long cols = 0;
   for (int j = 0; j < n; ++j) cols += jobs[j].nl * jobs[j].ncomp;
-  return lines_partitioned(jobs, n) && cols >= 152LL * 32;
+  return !lines_partitioned(jobs, n) || cols >= 152LL * 32;
 }
 
 template <typename T>
@@ -765,6 +766,7 @@ static void launch_lines(const LineJob<T>* jobs, int n, cudaStream_t st) {
   J.start[0] = 0;
   for (int j = 0; j < n; ++j) {
     J.lc[j] = line_coef<T>(*jobs[j].L);
+    J.src[j] = jobs[j].src;
     J.x[j] = jobs[j].x;
     J.nl[j] = jobs[j].nl;
     J.ncomp[j] = jobs[j].ncomp;

@@ -14,6 +14,17 @@
 
 namespace cgk {
 
+// The source of a C6 line family whose right-hand sides the solver forms
+// itself: nc planes of fs values of a node field on box fb, differenced along
+// lb.  f = null: the right-hand sides are already in x.
+template <typename T>
+struct C6Src {
+  const T* f = nullptr;
+  Box fb{};
+  long long fs = 0;
+  LineBuf lb{};
+};
+
 // Up to three independent families of lines solved by one launch (e.g. the x
 // and y lines of a stage): job j covers columns [start_j, start_j + nl_j * ncomp_j).
 // T = double: the FP64 solves; T = float: the mixed form's FP32 gradient solves
@@ -21,6 +32,7 @@ namespace cgk {
 template <typename T>
 struct ThomasJobsT {
   LineCoefT<T> lc[3];
+  C6Src<T> src[3];
   T* x[3];
   long long nl[3];
   int ncomp[3];
@@ -30,6 +42,9 @@ struct ThomasJobsT {
 
 template <typename T>
 __device__ __forceinline__ void thomas_column(const LineCoefT<T>& lc, T* __restrict__ x, long long nl, long long t);
+template <typename T>
+__device__ __forceinline__ void thomas_column_c6(const LineCoefT<T>& lc, T* __restrict__ x, long long nl, long long t,
+                                                 const C6Src<T>& sr);
 
 // Thomas recurrence over every column (line x component) of x (in place).
 template <typename T>
@@ -38,7 +53,8 @@ __global__ void k_thomas_jobs(ThomasJobsT<T> J) {
   int j = 0;
   while (j + 1 < J.njobs && t >= J.start[j + 1]) ++j;
   if (t >= J.start[J.njobs]) return;
-  thomas_column<T>(J.lc[j], J.x[j], J.nl[j], t - J.start[j]);
+  if (J.src[j].f) thomas_column_c6<T>(J.lc[j], J.x[j], J.nl[j], t - J.start[j], J.src[j]);
+  else thomas_column<T>(J.lc[j], J.x[j], J.nl[j], t - J.start[j]);
 }
 
 // The recurrences below read row i+B..i+2B-1 (forward) or i-B..i-2B+1
@@ -173,6 +189,48 @@ __device__ __forceinline__ void thomas_column(const LineCoefT<T>& lc, T* __restr
   }
 }
 
+// thomas_column of a C6 line family whose right-hand sides are formed on the
+// way from the source field (c6_forward; the end rows of a non-periodic line
+// take the E4 closure, as XTileC6 does).  Same recurrences and results.
+template <typename T, int B>
+__device__ __forceinline__ T c6_forward(T* __restrict__ col, long long nl, const T* __restrict__ aL, T a,
+                                        const T* __restrict__ rd, int i0, int i1, T y, const T* __restrict__ fp,
+                                        long long st, int lo, int m, bool periodic);
+
+template <typename T>
+__device__ __forceinline__ void thomas_column_c6(const LineCoefT<T>& lc, T* __restrict__ x, long long nl, long long t,
+                                                 const C6Src<T>& sr) {
+  const long long comp = t / nl, L = t % nl;
+  T* col = x + comp * lc.m * nl + L;
+  int cc[3] = {0, 0, 0};
+  sr.lb.coords(L, cc);
+  cc[sr.lb.d] = 0;
+  const int d = sr.lb.d;
+  const long long st = d == 0 ? 1 : (d == 1 ? (long long)sr.fb.ext[0] : (long long)sr.fb.ext[0] * sr.fb.ext[1]);
+  const T* fp = sr.f + comp * sr.fs + sr.fb.at(cc[0], cc[1], cc[2]);
+  auto F = [&](int pos) { return fp[(long long)pos * st]; };
+  const T a = lc.a;
+  const int m = lc.m, lo = sr.lb.lo;
+  if (!lc.periodic) {
+    // rows 0 and m-1 are identity rows holding the E4 closure values
+    const T r0 = d4(F(lo - 2), F(lo - 1), F(lo + 1), F(lo + 2));
+    col[0] = r0;
+    c6_forward<T, 4>(col, nl, nullptr, a, lc.den, 1, m - 1, r0, fp, st, lo, m, false);
+    const int pl = lo + m - 1;
+    const T rl = d4(F(pl - 2), F(pl - 1), F(pl + 1), F(pl + 2));
+    col[(long long)(m - 1) * nl] = rl;
+    thomas_backward(col, nl, lc.cp, 0, m - 2, rl);
+  } else {
+    const T r0 = T(7.0 / 9.0) * (F(1) - F(-1)) + T(1.0 / 36.0) * (F(2) - F(-2));
+    T dp = r0 * lc.den[0];
+    col[0] = dp;
+    const T xlast = c6_forward<T, 4>(col, nl, nullptr, a, lc.den, 1, m, dp, fp, st, 0, m, true);
+    const T x0 = thomas_backward(col, nl, lc.cp, 0, m - 2, xlast);
+    const T fact = (x0 + a * xlast / lc.gam) / lc.fden;
+    thomas_correct(col, nl, lc.z, m, fact);
+  }
+}
+
 // ---------------------------------------------------------------- partitioned solves
 // For few columns (a 1D grid, few lines) one thread per column leaves the GPU
 // idle: each column is split into P chunks of q rows solved concurrently.
@@ -197,17 +255,6 @@ struct PartCoefT {
   int m, q, P, periodic;
 };
 using PartCoef = PartCoefT<double>;
-
-// The source of a C6 line family whose right-hand sides the partitioned
-// solver forms itself: nc planes of fs values of a node field on box fb,
-// differenced along lb.  f = null: the right-hand sides are already in x.
-template <typename T>
-struct C6Src {
-  const T* f = nullptr;
-  Box fb{};
-  long long fs = 0;
-  LineBuf lb{};
-};
 
 template <typename T>
 struct PartJobsT {
@@ -259,7 +306,9 @@ __device__ __forceinline__ T part_forward(T* __restrict__ col, long long nl, con
   return y;
 }
 
-// part_forward with the C6 right-hand side of each row formed on the way from
+// The forward elimination (part_forward with sub-diagonal aL, or thomas_forward
+// with the constant a when aL is null; y: the value before row i0) with the
+// C6 right-hand side of each row formed on the way from
 // the source field along the line (fp: the column's component at position 0,
 // st: the stride between positions): r_i = 7/9 (f_{p+1} - f_{p-1}) +
 // 1/36 (f_{p+2} - f_{p-2}), or the E4 closure d4 on the end rows of a
@@ -267,16 +316,15 @@ __device__ __forceinline__ T part_forward(T* __restrict__ col, long long nl, con
 // five positions around the row slides along; the values entering it are
 // loaded B rows ahead.  The right-hand sides are never stored.
 template <typename T, int B>
-__device__ __forceinline__ T part_forward_c6(T* __restrict__ col, long long nl, const T* __restrict__ aL,
-                                             const T* __restrict__ rd, int i0, int i1, const T* __restrict__ fp,
-                                             long long st, int lo, int m, bool periodic) {
+__device__ __forceinline__ T c6_forward(T* __restrict__ col, long long nl, const T* __restrict__ aL, T a,
+                                        const T* __restrict__ rd, int i0, int i1, T y, const T* __restrict__ fp,
+                                        long long st, int lo, int m, bool periodic) {
   const int p0 = periodic ? i0 : lo + i0;
   auto F = [&](int pos) { return fp[(long long)pos * st]; };
   T w0 = F(p0 - 2), w1 = F(p0 - 1), w2 = F(p0), w3 = F(p0 + 1), w4 = F(p0 + 2);
   T pre[B];
 #pragma unroll
   for (int k = 0; k < B; ++k) pre[k] = (i0 + k + 1 < i1) ? F(p0 + 3 + k) : T(0);
-  T y = T(0);
   for (int base = i0; base < i1; base += B) {
     const int pb = p0 + (base - i0);
     T nxt[B];
@@ -288,7 +336,7 @@ __device__ __forceinline__ T part_forward_c6(T* __restrict__ col, long long nl, 
       if (i < i1) {
         const bool closure = !periodic && (i == 0 || i == m - 1);
         const T r = closure ? d4(w0, w1, w3, w4) : T(7.0 / 9.0) * (w3 - w1) + T(1.0 / 36.0) * (w4 - w0);
-        y = fma_t(-aL[i], y, r) * rd[i];
+        y = fma_t(-(aL ? aL[i] : a), y, r) * rd[i];
         col[(long long)i * nl] = y;
         w0 = w1;
         w1 = w2;
@@ -358,7 +406,7 @@ __global__ void __launch_bounds__(1024) k_tri_part(PartJobsT<T> J) {
       const int d = sr.lb.d;
       const long long st = d == 0 ? 1 : (d == 1 ? (long long)sr.fb.ext[0] : (long long)sr.fb.ext[0] * sr.fb.ext[1]);
       const T* fp = sr.f + (c / nl) * sr.fs + sr.fb.at(cc[0], cc[1], cc[2]);
-      y = part_forward_c6<T, PB>(col, nl, pc.aL, pc.rd, s, e, fp, st, sr.lb.lo, pc.m, pc.periodic != 0);
+      y = c6_forward<T, PB>(col, nl, pc.aL, T(0), pc.rd, s, e, T(0), fp, st, sr.lb.lo, pc.m, pc.periodic != 0);
     } else {
       y = part_forward<T, PB>(col, nl, pc.aL, pc.rd, s, e);
     }
