@@ -716,11 +716,10 @@ struct LineJob {
   T* x;
   long long nl;
   int ncomp;
-  C6Src<T> src{};  // f set: the partitioned solver forms the C6 right-hand sides itself
+  C6Src<T> src{};  // f set: the solver forms the C6 right-hand sides itself
 };
 
-// Whether launch_lines takes the partitioned solver for these jobs (the one
-// that can form C6 right-hand sides itself).
+// Whether launch_lines takes the partitioned solver for these jobs.
 template <typename T>
 static bool lines_partitioned(const LineJob<T>* jobs, int n) {
   bool part = true;

@@ -544,7 +544,7 @@ __device__ __forceinline__ void k_gbr_sweep_body(const VBlock& vb, const DevGrid
   const int tid = threadIdx.x;
   const int n = g.n[DIR];
   // tile origin along DIR and line coordinates
-  int i0, lc1 = 0, lc2 = 0;  // lc1/lc2: coordinates of the other dims for line 0
+  int i0;
   long long nlines;
   if (DIR == 0) {
     i0 = vb.x * (TL - 1);
@@ -597,8 +597,6 @@ __device__ __forceinline__ void k_gbr_sweep_body(const VBlock& vb, const DevGrid
     c[2] = s_lc[l][2];
     return true;
   };
-  (void)lc1;
-  (void)lc2;
   // Per-interface hybrid: a tile none of whose interfaces takes the GBR flux
   // (no troubled node on either side of any of them) skips steps 1-3, whose
   // staged primitives, derivatives and sensor values only the GBR fluxes read.
